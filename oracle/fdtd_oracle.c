@@ -1,0 +1,662 @@
+/*
+ * fdtd_oracle.c -- plain FP64 CPU FDTD used to check the CUDA library.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may load or call
+ * this file: only tests/, __graft_entry__.smoke() and the cpu_baseline /
+ * reference legs of bench.py do.  It shares no code, header, table or
+ * helper with the CUDA library; the two meet only through the seeded input
+ * generators and the cell-owned field interchange layout described below.
+ *
+ * What it computes (Kuklin, "elecode", arXiv 2207.06908):
+ *   - Sec. 2.1, Eq. (maxwell), (maxwelle), (maxwellh): lossy Maxwell curl
+ *     equations with per-cell eps, sigma, mu.
+ *   - Sec. 2.1, Eq. (fdtdex), (fdtdhx): Yee staggered updates of E and H.
+ *     The loss term is taken in the semi-implicit (time-averaged sigma*E)
+ *     form of the textbook the paper cites; Eq. (fdtdex) prints the explicit
+ *     factor (1 - sigma dt / eps), which is unstable once sigma dt / eps > 2.
+ *   - Sec. 2.1 (sources): ideal lumped current source on one Yee edge,
+ *     J = I / dx^2 along +axis, I sampled at t_{n+1/2}.
+ *   - Sec. 2.2: CPML absorbing layer (CFS recursive convolution, Roden and
+ *     Gedney) terminated by PEC.
+ *   - Sec. 2.3: thin wire by modified material parameters around a
+ *     zero-tangential-E line: the radial E at the wire nodes get eps and
+ *     sigma times m, every H those E read (circumferential and axial) gets
+ *     mu / m, m = ln(dx / r0) / ln(dx / a), r0 = 0.23 dx, a <= r0.  The
+ *     paper gives only references for the formula; the H set is widened
+ *     beyond the circumferential H for stability (see orc_finalize).
+ *   - Sec. 4 model files ("calculate"): voltage = -sum E dl along a path,
+ *     current = loop integral of H around an edge.
+ *
+ * Layout.  Every component is a node-indexed FP64 array of
+ * (nx+1)(ny+1)(nz+1) entries, index (k*(ny+1)+j)*(nx+1)+i, holding
+ *   Ex(i+1/2,j,k) Ey(i,j+1/2,k) Ez(i,j,k+1/2)
+ *   Hx(i,j+1/2,k+1/2) Hy(i+1/2,j,k+1/2) Hz(i+1/2,j+1/2,k).
+ * Entries at index nx, ny or nz along an axis are on the far walls and stay
+ * zero.  Fields are exchanged with callers in the cell-owned layout: an
+ * nx*ny*nz array, x fastest, entry (i,j,k) = the component with those
+ * indices.
+ *
+ * Parity mode rounds every coefficient (ca, cb, db, the source factor, the
+ * CPML b, c, 1/kappa) and every source sample to FP32 before use, so a
+ * comparison with an FP32 GPU run measures arithmetic error only.  All
+ * arithmetic stays FP64.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_C0 299792458.0
+#define ORC_EPS0 8.8541878128e-12
+#define ORC_MU0 1.25663706212e-6
+#define ORC_R0_FRAC 0.23
+
+enum { EX = 0, EY, EZ, HX, HY, HZ };
+enum { PROBE_V = 0, PROBE_I = 1, PROBE_E = 2, PROBE_H = 3 };
+
+typedef struct { int axis, i, j, k, n; double radius; } orc_wire;
+typedef struct { int axis, i, j, k, n; double *cur; } orc_src;
+typedef struct { int kind, axis, i, j, k, n_edges; } orc_probe;
+
+typedef struct orc_grid {
+    int nx, ny, nz;
+    double dx, dt, courant;
+    int parity;
+    size_t sy, sz, ntot;       /* strides of the node-indexed arrays */
+    double *f[6];              /* Ex Ey Ez Hx Hy Hz */
+    /* materials per cell */
+    uint8_t *mat;
+    double *m_eps, *m_sig, *m_mu;
+    int n_mat;
+    /* coefficients per component position */
+    double *ca[3], *cb[3], *db[3];
+    /* CPML */
+    int d;
+    double order, kappa_max, alpha_max, alpha_order, sigma_max;
+    /* profile per axis u: E-position (integer node) and H-position
+     * (half-integer) b, c, 1/kappa, plus an "inside the layer" flag */
+    double *pe_b[3], *pe_c[3], *pe_ki[3];
+    double *ph_b[3], *ph_c[3], *ph_ki[3];
+    uint8_t *pe_on[3], *ph_on[3];
+    /* psi[comp][axis]: auxiliary field of component comp (0..5) for its
+     * derivative along axis; full node-indexed arrays, NULL on the diagonal */
+    double *psi[6][3];
+    /* wires, sources, probes */
+    orc_wire *wires; int n_wires;
+    orc_src *srcs; int n_srcs;
+    orc_probe *probes; int n_probes;
+    double *src_coef;          /* -cb/dx at each source edge */
+    int max_steps;
+    double *probe_out;         /* [n_probes][max_steps] */
+    long step;
+    int finalized;
+} orc_grid;
+
+static double r32(const orc_grid *g, double v) { return g->parity ? (double)(float)v : v; }
+
+static inline size_t IDX(const orc_grid *g, int i, int j, int k)
+{
+    return ((size_t)k * g->sz) + ((size_t)j * g->sy) + (size_t)i;
+}
+
+static inline int CELL(const orc_grid *g, int i, int j, int k)
+{
+    return (k * g->ny + j) * g->nx + i;
+}
+
+orc_grid *orc_create(int nx, int ny, int nz, double dx, double courant, int parity)
+{
+    if (nx < 2 || ny < 2 || nz < 2 || !(dx > 0) || !(courant > 0)) return NULL;
+    orc_grid *g = (orc_grid *)calloc(1, sizeof(orc_grid));
+    g->nx = nx; g->ny = ny; g->nz = nz; g->dx = dx; g->courant = courant;
+    /* Courant limit for a uniform cubic grid: c dt <= dx / sqrt(3) */
+    g->dt = courant * dx / (ORC_C0 * sqrt(3.0));
+    g->parity = parity;
+    g->sy = (size_t)(nx + 1);
+    g->sz = (size_t)(nx + 1) * (size_t)(ny + 1);
+    g->ntot = g->sz * (size_t)(nz + 1);
+    for (int c = 0; c < 6; c++) g->f[c] = (double *)calloc(g->ntot, sizeof(double));
+    g->mat = (uint8_t *)calloc((size_t)nx * ny * nz, 1);
+    g->n_mat = 1;
+    g->m_eps = (double *)malloc(sizeof(double)); g->m_eps[0] = 1.0;
+    g->m_sig = (double *)malloc(sizeof(double)); g->m_sig[0] = 0.0;
+    g->m_mu = (double *)malloc(sizeof(double)); g->m_mu[0] = 1.0;
+    return g;
+}
+
+void orc_destroy(orc_grid *g)
+{
+    if (!g) return;
+    for (int c = 0; c < 6; c++) free(g->f[c]);
+    for (int c = 0; c < 3; c++) { free(g->ca[c]); free(g->cb[c]); free(g->db[c]); }
+    for (int u = 0; u < 3; u++) {
+        free(g->pe_b[u]); free(g->pe_c[u]); free(g->pe_ki[u]); free(g->pe_on[u]);
+        free(g->ph_b[u]); free(g->ph_c[u]); free(g->ph_ki[u]); free(g->ph_on[u]);
+    }
+    for (int c = 0; c < 6; c++) for (int u = 0; u < 3; u++) free(g->psi[c][u]);
+    for (int s = 0; s < g->n_srcs; s++) free(g->srcs[s].cur);
+    free(g->srcs); free(g->wires); free(g->probes); free(g->src_coef); free(g->probe_out);
+    free(g->mat); free(g->m_eps); free(g->m_sig); free(g->m_mu);
+    free(g);
+}
+
+double orc_dt(const orc_grid *g) { return g->dt; }
+long orc_step_count(const orc_grid *g) { return g->step; }
+
+/* sigma_max <= 0 selects 0.8 (m+1) / (eta0 dx), the usual optimum for a
+ * polynomial grading of order m. */
+int orc_set_cpml(orc_grid *g, int d, double order, double kappa_max, double alpha_max,
+                 double alpha_order, double sigma_max)
+{
+    if (g->finalized) return -8;
+    if (d < 0 || 2 * d > g->nx || 2 * d > g->ny || 2 * d > g->nz) return -1;
+    g->d = d; g->order = order; g->kappa_max = kappa_max; g->alpha_max = alpha_max;
+    g->alpha_order = alpha_order;
+    if (sigma_max <= 0) {
+        double eta0 = sqrt(ORC_MU0 / ORC_EPS0);
+        sigma_max = 0.8 * (order + 1.0) / (eta0 * g->dx);
+    }
+    g->sigma_max = sigma_max;
+    return 0;
+}
+
+int orc_set_materials(orc_grid *g, const uint8_t *cell_mat, const double *eps_r,
+                      const double *sigma, const double *mu_r, int n_mat)
+{
+    if (g->finalized) return -8;
+    if (n_mat < 1 || n_mat > 256) return -1;
+    size_t nc = (size_t)g->nx * g->ny * g->nz;
+    for (size_t c = 0; c < nc; c++) if (cell_mat[c] >= n_mat) return -1;
+    memcpy(g->mat, cell_mat, nc);
+    free(g->m_eps); free(g->m_sig); free(g->m_mu);
+    g->m_eps = (double *)malloc(n_mat * sizeof(double));
+    g->m_sig = (double *)malloc(n_mat * sizeof(double));
+    g->m_mu = (double *)malloc(n_mat * sizeof(double));
+    memcpy(g->m_eps, eps_r, n_mat * sizeof(double));
+    memcpy(g->m_sig, sigma, n_mat * sizeof(double));
+    memcpy(g->m_mu, mu_r, n_mat * sizeof(double));
+    g->n_mat = n_mat;
+    return 0;
+}
+
+/* axis-aligned wire from node (i0,j0,k0) to node (i1,j1,k1) */
+int orc_add_wire(orc_grid *g, int i0, int j0, int k0, int i1, int j1, int k1, double radius)
+{
+    if (g->finalized) return -8;
+    int axis, n;
+    if (j0 == j1 && k0 == k1 && i1 > i0) { axis = 0; n = i1 - i0; }
+    else if (i0 == i1 && k0 == k1 && j1 > j0) { axis = 1; n = j1 - j0; }
+    else if (i0 == i1 && j0 == j1 && k1 > k0) { axis = 2; n = k1 - k0; }
+    else return -1;
+    /* m <= 1 (a <= r0): thicker wires would need the opposite stability rule */
+    if (!(radius > 0) || radius > ORC_R0_FRAC * g->dx * (1.0 + 1e-12)) return -1;
+    /* the wire and its neighbouring radial/circumferential components must
+     * lie strictly inside the walls */
+    int lo[3] = {i0, j0, k0}, hi[3] = {i1, j1, k1}, nn[3] = {g->nx, g->ny, g->nz};
+    for (int u = 0; u < 3; u++) {
+        if (u == axis) { if (lo[u] < 0 || hi[u] > nn[u]) return -1; }
+        else if (lo[u] < 1 || lo[u] > nn[u] - 1) return -1;
+    }
+    g->wires = (orc_wire *)realloc(g->wires, (g->n_wires + 1) * sizeof(orc_wire));
+    orc_wire w = {axis, i0, j0, k0, n, radius};
+    g->wires[g->n_wires++] = w;
+    return 0;
+}
+
+int orc_add_source(orc_grid *g, int i, int j, int k, int axis, const double *cur, int n)
+{
+    if (g->finalized) return -8;
+    if (axis < 0 || axis > 2 || n < 0) return -1;
+    int p[3] = {i, j, k}, nn[3] = {g->nx, g->ny, g->nz};
+    for (int u = 0; u < 3; u++) {
+        if (u == axis) { if (p[u] < 0 || p[u] >= nn[u]) return -1; }
+        else if (p[u] < 1 || p[u] > nn[u] - 1) return -1;
+    }
+    g->srcs = (orc_src *)realloc(g->srcs, (g->n_srcs + 1) * sizeof(orc_src));
+    orc_src s = {axis, i, j, k, n, NULL};
+    s.cur = (double *)malloc((n > 0 ? n : 1) * sizeof(double));
+    for (int t = 0; t < n; t++) s.cur[t] = r32(g, cur[t]);
+    g->srcs[g->n_srcs++] = s;
+    return 0;
+}
+
+int orc_add_probe(orc_grid *g, int kind, int i, int j, int k, int axis, int n_edges)
+{
+    if (g->finalized) return -8;
+    if (axis < 0 || axis > 2 || kind < 0 || kind > 3) return -1;
+    int p[3] = {i, j, k}, nn[3] = {g->nx, g->ny, g->nz};
+    for (int u = 0; u < 3; u++) if (p[u] < 0 || p[u] >= nn[u]) return -1;
+    if (kind == PROBE_V) { if (n_edges < 1 || p[axis] + n_edges > nn[axis]) return -1; }
+    else n_edges = 1;
+    if (kind == PROBE_I) {
+        for (int u = 0; u < 3; u++) if (u != axis && p[u] < 1) return -1;
+    }
+    g->probes = (orc_probe *)realloc(g->probes, (g->n_probes + 1) * sizeof(orc_probe));
+    orc_probe pr = {kind, axis, i, j, k, n_edges};
+    g->probes[g->n_probes++] = pr;
+    return 0;
+}
+
+/* material of cell (i,j,k); cells outside the grid are never asked for */
+static double cell_eps(const orc_grid *g, int i, int j, int k) { return g->m_eps[g->mat[CELL(g, i, j, k)]]; }
+static double cell_sig(const orc_grid *g, int i, int j, int k) { return g->m_sig[g->mat[CELL(g, i, j, k)]]; }
+static double cell_mu(const orc_grid *g, int i, int j, int k) { return g->m_mu[g->mat[CELL(g, i, j, k)]]; }
+
+/* CPML grading at depth rho (cells) into the layer, Roden-Gedney CFS form */
+static void cpml_coef(const orc_grid *g, double rho, double *b, double *c, double *ki)
+{
+    double x = rho / g->d;
+    double sig = g->sigma_max * pow(x, g->order);
+    double kap = 1.0 + (g->kappa_max - 1.0) * pow(x, g->order);
+    double alp = g->alpha_max * pow(1.0 - x, g->alpha_order);
+    double bb = exp(-(sig / kap + alp) * g->dt / ORC_EPS0);
+    double cc = (sig > 0) ? sig * (bb - 1.0) / (sig * kap + kap * kap * alp) : 0.0;
+    *b = bb; *c = cc; *ki = 1.0 / kap;
+}
+
+static void build_cpml(orc_grid *g)
+{
+    int nn[3] = {g->nx, g->ny, g->nz};
+    for (int u = 0; u < 3; u++) {
+        int n = nn[u];
+        g->pe_b[u] = (double *)calloc(n + 1, sizeof(double));
+        g->pe_c[u] = (double *)calloc(n + 1, sizeof(double));
+        g->pe_ki[u] = (double *)calloc(n + 1, sizeof(double));
+        g->pe_on[u] = (uint8_t *)calloc(n + 1, 1);
+        g->ph_b[u] = (double *)calloc(n + 1, sizeof(double));
+        g->ph_c[u] = (double *)calloc(n + 1, sizeof(double));
+        g->ph_ki[u] = (double *)calloc(n + 1, sizeof(double));
+        g->ph_on[u] = (uint8_t *)calloc(n + 1, 1);
+        for (int i = 0; i <= n; i++) {
+            g->pe_ki[u][i] = 1.0; g->ph_ki[u][i] = 1.0; g->pe_b[u][i] = 1.0; g->ph_b[u][i] = 1.0;
+        }
+        if (g->d == 0) continue;
+        int d = g->d;
+        /* integer node positions i: depth d - i on the low side, i - (n - d)
+         * on the high side; the layer interior is depth > 0 */
+        for (int i = 0; i <= n; i++) {
+            double rho = 0.0;
+            if (i < d) rho = d - i;
+            else if (i > n - d) rho = i - (n - d);
+            if (rho > 0) {
+                double b, c, ki; cpml_coef(g, rho, &b, &c, &ki);
+                g->pe_b[u][i] = r32(g, b); g->pe_c[u][i] = r32(g, c); g->pe_ki[u][i] = r32(g, ki);
+                g->pe_on[u][i] = 1;
+            }
+        }
+        /* half-integer positions i + 1/2, i = 0..n-1 */
+        for (int i = 0; i < n; i++) {
+            double rho = 0.0;
+            if (i < d) rho = d - (i + 0.5);
+            else if (i >= n - d) rho = (i + 0.5) - (n - d);
+            if (rho > 0) {
+                double b, c, ki; cpml_coef(g, rho, &b, &c, &ki);
+                g->ph_b[u][i] = r32(g, b); g->ph_c[u][i] = r32(g, c); g->ph_ki[u][i] = r32(g, ki);
+                g->ph_on[u][i] = 1;
+            }
+        }
+    }
+    if (g->d == 0) return;
+    /* psi arrays: component c has derivatives along the two other axes */
+    int comp_axis[6] = {0, 1, 2, 0, 1, 2};
+    for (int c = 0; c < 6; c++)
+        for (int u = 0; u < 3; u++)
+            if (u != comp_axis[c]) g->psi[c][u] = (double *)calloc(g->ntot, sizeof(double));
+}
+
+/* equivalent-radius factor of a thin wire of radius a (Sec. 2.3 reading) */
+static double wire_factor(const orc_grid *g, double a)
+{
+    return log(g->dx / (ORC_R0_FRAC * g->dx)) / log(g->dx / a);
+}
+
+/* true when E component comp at node-index q is updated (not on a wall) */
+static int e_interior(const orc_grid *g, int comp, const int q[3])
+{
+    int nn[3] = {g->nx, g->ny, g->nz};
+    for (int u = 0; u < 3; u++) {
+        if (u == comp) { if (q[u] < 0 || q[u] >= nn[u]) return 0; }
+        else if (q[u] < 1 || q[u] > nn[u] - 1) return 0;
+    }
+    return 1;
+}
+
+/* the four H entries read by the update of E component comp at q, in the
+ * order of the update stencils of update_e():
+ *   Ex(i+1/2,j,k): Hz[i][j][k], Hz[i][j-1][k], Hy[i][j][k], Hy[i][j][k-1]
+ *   Ey(i,j+1/2,k): Hx[i][j][k], Hx[i][j][k-1], Hz[i][j][k], Hz[i-1][j][k]
+ *   Ez(i,j,k+1/2): Hy[i][j][k], Hy[i-1][j][k], Hx[i][j][k], Hx[i][j-1][k] */
+static void e_stencil(int comp, const int q[3], int hc[4], int hp[4][3])
+{
+    int b = (comp + 1) % 3, c = (comp + 2) % 3;
+    /* E_comp reads H_c differenced along b and H_b differenced along c */
+    hc[0] = c; hc[1] = c; hc[2] = b; hc[3] = b;     /* H axis 0..2 */
+    for (int t = 0; t < 4; t++) { hp[t][0] = q[0]; hp[t][1] = q[1]; hp[t][2] = q[2]; }
+    hp[1][b] -= 1;
+    hp[3][c] -= 1;
+}
+
+int orc_finalize(orc_grid *g, int max_steps)
+{
+    if (g->finalized) return -8;
+    if (max_steps < 0) return -1;
+    int nx = g->nx, ny = g->ny, nz = g->nz;
+    size_t N = g->ntot;
+    /* 1. per-edge eps, sigma (mean over the 4 cells around the edge) and
+     *    per-face mu (mean over the 2 cells on either side) */
+    double *eps[3], *sig[3], *mu[3];
+    uint8_t *pec[3];
+    double *fac_e[3], *fac_h[3];
+    for (int c = 0; c < 3; c++) {
+        eps[c] = (double *)calloc(N, sizeof(double));
+        sig[c] = (double *)calloc(N, sizeof(double));
+        mu[c] = (double *)calloc(N, sizeof(double));
+        pec[c] = (uint8_t *)calloc(N, 1);
+        fac_e[c] = (double *)malloc(N * sizeof(double));
+        fac_h[c] = (double *)malloc(N * sizeof(double));
+        for (size_t q = 0; q < N; q++) { fac_e[c][q] = 1.0; fac_h[c][q] = 1.0; }
+    }
+    for (int k = 0; k <= nz; k++)
+        for (int j = 0; j <= ny; j++)
+            for (int i = 0; i <= nx; i++) {
+                size_t q = IDX(g, i, j, k);
+                /* Ex(i+1/2,j,k): cells (i, j-1|j, k-1|k) */
+                if (i < nx && j >= 1 && j < ny && k >= 1 && k < nz) {
+                    eps[0][q] = 0.25 * (cell_eps(g, i, j - 1, k - 1) + cell_eps(g, i, j, k - 1) +
+                                        cell_eps(g, i, j - 1, k) + cell_eps(g, i, j, k));
+                    sig[0][q] = 0.25 * (cell_sig(g, i, j - 1, k - 1) + cell_sig(g, i, j, k - 1) +
+                                        cell_sig(g, i, j - 1, k) + cell_sig(g, i, j, k));
+                }
+                /* Ey(i,j+1/2,k): cells (i-1|i, j, k-1|k) */
+                if (j < ny && i >= 1 && i < nx && k >= 1 && k < nz) {
+                    eps[1][q] = 0.25 * (cell_eps(g, i - 1, j, k - 1) + cell_eps(g, i, j, k - 1) +
+                                        cell_eps(g, i - 1, j, k) + cell_eps(g, i, j, k));
+                    sig[1][q] = 0.25 * (cell_sig(g, i - 1, j, k - 1) + cell_sig(g, i, j, k - 1) +
+                                        cell_sig(g, i - 1, j, k) + cell_sig(g, i, j, k));
+                }
+                /* Ez(i,j,k+1/2): cells (i-1|i, j-1|j, k) */
+                if (k < nz && i >= 1 && i < nx && j >= 1 && j < ny) {
+                    eps[2][q] = 0.25 * (cell_eps(g, i - 1, j - 1, k) + cell_eps(g, i, j - 1, k) +
+                                        cell_eps(g, i - 1, j, k) + cell_eps(g, i, j, k));
+                    sig[2][q] = 0.25 * (cell_sig(g, i - 1, j - 1, k) + cell_sig(g, i, j - 1, k) +
+                                        cell_sig(g, i - 1, j, k) + cell_sig(g, i, j, k));
+                }
+                /* Hx(i,j+1/2,k+1/2): cells i-1 and i */
+                if (i >= 1 && i < nx && j < ny && k < nz)
+                    mu[0][q] = 0.5 * (cell_mu(g, i - 1, j, k) + cell_mu(g, i, j, k));
+                /* Hy(i+1/2,j,k+1/2): cells j-1 and j */
+                if (j >= 1 && j < ny && i < nx && k < nz)
+                    mu[1][q] = 0.5 * (cell_mu(g, i, j - 1, k) + cell_mu(g, i, j, k));
+                /* Hz(i+1/2,j+1/2,k): cells k-1 and k */
+                if (k >= 1 && k < nz && i < nx && j < ny)
+                    mu[2][q] = 0.5 * (cell_mu(g, i, j, k - 1) + cell_mu(g, i, j, k));
+            }
+    /* 2. thin wires: on-wire E is PEC; the four radial E at every wire node
+     *    (end nodes included) get eps, sigma * m; every H that one of those
+     *    radial E reads in its update (the circumferential H of each
+     *    segment, the axial H at each node, and the circumferential H just
+     *    beyond each end) gets mu / m.  Giving mu/m to every H next to a
+     *    modified E keeps each E-H coupling at or below its unmodified
+     *    value, which keeps the scheme stable up to S = 1 (radial eps*m next
+     *    to an unmodified axial H is not).  Where two wires touch one
+     *    component the smaller m (thinner wire) is used once. */
+    for (int w = 0; w < g->n_wires; w++) {
+        orc_wire *wr = &g->wires[w];
+        double m = wire_factor(g, wr->radius);
+        int a = wr->axis, b = (a + 1) % 3, c = (a + 2) % 3;
+        for (int s = 0; s <= wr->n; s++) {
+            int p[3] = {wr->i, wr->j, wr->k};
+            p[a] += s;
+            /* radial E at node p: E_b at p and p - e_b; E_c at p and p - e_c */
+            for (int r = 0; r < 4; r++) {
+                int comp = (r < 2) ? b : c;
+                int q[3] = {p[0], p[1], p[2]};
+                q[comp] -= (r & 1);
+                if (!e_interior(g, comp, q)) continue;     /* wall: PEC anyway */
+                size_t iq = IDX(g, q[0], q[1], q[2]);
+                if (m < fac_e[comp][iq]) fac_e[comp][iq] = m;
+                /* the four H this E reads (its curl stencil) */
+                int hc[4], hp[4][3];
+                e_stencil(comp, q, hc, hp);
+                for (int t = 0; t < 4; t++) {
+                    size_t ih = IDX(g, hp[t][0], hp[t][1], hp[t][2]);
+                    if (m < fac_h[hc[t]][ih]) fac_h[hc[t]][ih] = m;
+                }
+            }
+            /* the on-wire edge E_a(p) of the segment p -> p + e_a is PEC */
+            if (s < wr->n) pec[a][IDX(g, p[0], p[1], p[2])] = 1;
+        }
+    }
+    /* 3. coefficients of the semi-implicit update (Eq. fdtdex with the loss
+     *    time-averaged) and of Eq. fdtdhx; 1/dx folded in */
+    double dt = g->dt, dx = g->dx;
+    for (int c = 0; c < 3; c++) {
+        g->ca[c] = (double *)calloc(N, sizeof(double));
+        g->cb[c] = (double *)calloc(N, sizeof(double));
+        g->db[c] = (double *)calloc(N, sizeof(double));
+        for (size_t q = 0; q < N; q++) {
+            if (eps[c][q] > 0 && !pec[c][q]) {
+                double e = ORC_EPS0 * eps[c][q] * fac_e[c][q];
+                double s = sig[c][q] * fac_e[c][q];
+                double a = s * dt / (2.0 * e);
+                g->ca[c][q] = r32(g, (1.0 - a) / (1.0 + a));
+                g->cb[c][q] = r32(g, dt / (e * dx) / (1.0 + a));
+            }
+            if (mu[c][q] > 0) {
+                double mm = ORC_MU0 * mu[c][q] / fac_h[c][q];
+                g->db[c][q] = r32(g, dt / (mm * dx));
+            }
+        }
+    }
+    /* source factor -cb/dx on each source edge (J = I/dx^2 in Eq. maxwell) */
+    g->src_coef = (double *)calloc(g->n_srcs > 0 ? g->n_srcs : 1, sizeof(double));
+    for (int s = 0; s < g->n_srcs; s++) {
+        orc_src *sr = &g->srcs[s];
+        size_t q = IDX(g, sr->i, sr->j, sr->k);
+        double cbq;
+        if (eps[sr->axis][q] > 0 && !pec[sr->axis][q]) {
+            double e = ORC_EPS0 * eps[sr->axis][q] * fac_e[sr->axis][q];
+            double sg = sig[sr->axis][q] * fac_e[sr->axis][q];
+            double a = sg * dt / (2.0 * e);
+            cbq = dt / (e * dx) / (1.0 + a);
+        } else {
+            cbq = 0.0;
+        }
+        g->src_coef[s] = r32(g, -cbq / dx);
+    }
+    for (int c = 0; c < 3; c++) { free(eps[c]); free(sig[c]); free(mu[c]); free(pec[c]); free(fac_e[c]); free(fac_h[c]); }
+    build_cpml(g);
+    g->max_steps = max_steps;
+    g->probe_out = (double *)calloc((size_t)(g->n_probes > 0 ? g->n_probes : 1) * (max_steps > 0 ? max_steps : 1), sizeof(double));
+    g->finalized = 1;
+    return 0;
+}
+
+/* ---- field exchange in the cell-owned layout ---- */
+int orc_set_field(orc_grid *g, int comp, const double *cells)
+{
+    if (comp < 0 || comp > 5) return -1;
+    for (int k = 0; k < g->nz; k++)
+        for (int j = 0; j < g->ny; j++)
+            for (int i = 0; i < g->nx; i++)
+                g->f[comp][IDX(g, i, j, k)] = cells[CELL(g, i, j, k)];
+    return 0;
+}
+
+int orc_get_field(const orc_grid *g, int comp, double *cells)
+{
+    if (comp < 0 || comp > 5) return -1;
+    for (int k = 0; k < g->nz; k++)
+        for (int j = 0; j < g->ny; j++)
+            for (int i = 0; i < g->nx; i++)
+                cells[CELL(g, i, j, k)] = g->f[comp][IDX(g, i, j, k)];
+    return 0;
+}
+
+int orc_get_coef(const orc_grid *g, int which, double *cells)
+{
+    /* which: 0..2 ca_x..z, 3..5 cb_x..z, 6..8 db_x..z */
+    if (!g->finalized || which < 0 || which > 8) return -1;
+    const double *src = which < 3 ? g->ca[which] : which < 6 ? g->cb[which - 3] : g->db[which - 6];
+    for (int k = 0; k < g->nz; k++)
+        for (int j = 0; j < g->ny; j++)
+            for (int i = 0; i < g->nx; i++)
+                cells[CELL(g, i, j, k)] = src[IDX(g, i, j, k)];
+    return 0;
+}
+
+/* ---- one time step ---- */
+
+/* one curl term along axis u: plain difference, or in the CPML layer
+ * d/kappa + psi with psi <- b psi + c d.  Differences are in field units
+ * (1/dx sits in the coefficients), so psi is kept in the same units. */
+static inline double term(double dif, double *psi, size_t q, int on, double b, double c, double ki)
+{
+    if (!on) return dif;
+    psi[q] = b * psi[q] + c * dif;
+    return dif * ki + psi[q];
+}
+
+static void update_h(orc_grid *g)
+{
+    int nx = g->nx, ny = g->ny, nz = g->nz;
+    double *Ex = g->f[EX], *Ey = g->f[EY], *Ez = g->f[EZ];
+    double *Hx = g->f[HX], *Hy = g->f[HY], *Hz = g->f[HZ];
+    size_t sy = g->sy, sz = g->sz;
+    /* Hx(i,j+1/2,k+1/2) += db [dEy/dz - dEz/dy]; i = 0 and nx are normal walls */
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 0; k < nz; k++)
+        for (int j = 0; j < ny; j++)
+            for (int i = 1; i < nx; i++) {
+                size_t q = IDX(g, i, j, k);
+                double tz = term(Ey[q + sz] - Ey[q], g->psi[HX][2], q, g->ph_on[2][k], g->ph_b[2][k], g->ph_c[2][k], g->ph_ki[2][k]);
+                double ty = term(Ez[q + sy] - Ez[q], g->psi[HX][1], q, g->ph_on[1][j], g->ph_b[1][j], g->ph_c[1][j], g->ph_ki[1][j]);
+                Hx[q] += g->db[0][q] * (tz - ty);
+            }
+    /* Hy(i+1/2,j,k+1/2) += db [dEz/dx - dEx/dz]; j = 0 and ny are walls */
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 0; k < nz; k++)
+        for (int j = 1; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                size_t q = IDX(g, i, j, k);
+                double tx = term(Ez[q + 1] - Ez[q], g->psi[HY][0], q, g->ph_on[0][i], g->ph_b[0][i], g->ph_c[0][i], g->ph_ki[0][i]);
+                double tz = term(Ex[q + sz] - Ex[q], g->psi[HY][2], q, g->ph_on[2][k], g->ph_b[2][k], g->ph_c[2][k], g->ph_ki[2][k]);
+                Hy[q] += g->db[1][q] * (tx - tz);
+            }
+    /* Hz(i+1/2,j+1/2,k) += db [dEx/dy - dEy/dx]; k = 0 and nz are walls */
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 1; k < nz; k++)
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                size_t q = IDX(g, i, j, k);
+                double ty = term(Ex[q + sy] - Ex[q], g->psi[HZ][1], q, g->ph_on[1][j], g->ph_b[1][j], g->ph_c[1][j], g->ph_ki[1][j]);
+                double tx = term(Ey[q + 1] - Ey[q], g->psi[HZ][0], q, g->ph_on[0][i], g->ph_b[0][i], g->ph_c[0][i], g->ph_ki[0][i]);
+                Hz[q] += g->db[2][q] * (ty - tx);
+            }
+}
+
+static void update_e(orc_grid *g)
+{
+    int nx = g->nx, ny = g->ny, nz = g->nz;
+    double *Ex = g->f[EX], *Ey = g->f[EY], *Ez = g->f[EZ];
+    double *Hx = g->f[HX], *Hy = g->f[HY], *Hz = g->f[HZ];
+    size_t sy = g->sy, sz = g->sz;
+    /* Ex(i+1/2,j,k) = ca Ex + cb [dHz/dy - dHy/dz]; j in (0,ny), k in (0,nz) */
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 1; k < nz; k++)
+        for (int j = 1; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                size_t q = IDX(g, i, j, k);
+                double ty = term(Hz[q] - Hz[q - sy], g->psi[EX][1], q, g->pe_on[1][j], g->pe_b[1][j], g->pe_c[1][j], g->pe_ki[1][j]);
+                double tz = term(Hy[q] - Hy[q - sz], g->psi[EX][2], q, g->pe_on[2][k], g->pe_b[2][k], g->pe_c[2][k], g->pe_ki[2][k]);
+                Ex[q] = g->ca[0][q] * Ex[q] + g->cb[0][q] * (ty - tz);
+            }
+    /* Ey(i,j+1/2,k) = ca Ey + cb [dHx/dz - dHz/dx]; i in (0,nx), k in (0,nz) */
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 1; k < nz; k++)
+        for (int j = 0; j < ny; j++)
+            for (int i = 1; i < nx; i++) {
+                size_t q = IDX(g, i, j, k);
+                double tz = term(Hx[q] - Hx[q - sz], g->psi[EY][2], q, g->pe_on[2][k], g->pe_b[2][k], g->pe_c[2][k], g->pe_ki[2][k]);
+                double tx = term(Hz[q] - Hz[q - 1], g->psi[EY][0], q, g->pe_on[0][i], g->pe_b[0][i], g->pe_c[0][i], g->pe_ki[0][i]);
+                Ey[q] = g->ca[1][q] * Ey[q] + g->cb[1][q] * (tz - tx);
+            }
+    /* Ez(i,j,k+1/2) = ca Ez + cb [dHy/dx - dHx/dy]; i in (0,nx), j in (0,ny) */
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 0; k < nz; k++)
+        for (int j = 1; j < ny; j++)
+            for (int i = 1; i < nx; i++) {
+                size_t q = IDX(g, i, j, k);
+                double tx = term(Hy[q] - Hy[q - 1], g->psi[EZ][0], q, g->pe_on[0][i], g->pe_b[0][i], g->pe_c[0][i], g->pe_ki[0][i]);
+                double ty = term(Hx[q] - Hx[q - sy], g->psi[EZ][1], q, g->pe_on[1][j], g->pe_b[1][j], g->pe_c[1][j], g->pe_ki[1][j]);
+                Ez[q] = g->ca[2][q] * Ez[q] + g->cb[2][q] * (tx - ty);
+            }
+    /* ideal current sources: -cb/dx * I(t_{n+1/2}) on the source edge */
+    for (int s = 0; s < g->n_srcs; s++) {
+        orc_src *sr = &g->srcs[s];
+        double I = (g->step < sr->n) ? sr->cur[g->step] : 0.0;
+        g->f[sr->axis][IDX(g, sr->i, sr->j, sr->k)] += g->src_coef[s] * I;
+    }
+    /* PEC walls: tangential E on the six faces is zero (the update loops
+     * never touch those entries; they are cleared in case the caller set
+     * them) */
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k <= nz; k++)
+        for (int j = 0; j <= ny; j++)
+            for (int i = 0; i <= nx; i++) {
+                size_t q = IDX(g, i, j, k);
+                if (j == 0 || j == ny || k == 0 || k == nz) Ex[q] = 0.0;
+                if (i == 0 || i == nx || k == 0 || k == nz) Ey[q] = 0.0;
+                if (i == 0 || i == nx || j == 0 || j == ny) Ez[q] = 0.0;
+            }
+}
+
+static double probe_value(const orc_grid *g, const orc_probe *p)
+{
+    double dx = g->dx;
+    if (p->kind == PROBE_E) return g->f[p->axis][IDX(g, p->i, p->j, p->k)];
+    if (p->kind == PROBE_H) return g->f[3 + p->axis][IDX(g, p->i, p->j, p->k)];
+    if (p->kind == PROBE_V) {
+        double v = 0.0;
+        int q[3] = {p->i, p->j, p->k};
+        for (int e = 0; e < p->n_edges; e++) {
+            v -= g->f[p->axis][IDX(g, q[0], q[1], q[2])] * dx;
+            q[p->axis]++;
+        }
+        return v;
+    }
+    /* PROBE_I: circulation of H around the edge, Ampere's law */
+    const double *Hx = g->f[HX], *Hy = g->f[HY], *Hz = g->f[HZ];
+    int i = p->i, j = p->j, k = p->k;
+    if (p->axis == 2)
+        return dx * (Hy[IDX(g, i, j, k)] - Hy[IDX(g, i - 1, j, k)] - Hx[IDX(g, i, j, k)] + Hx[IDX(g, i, j - 1, k)]);
+    if (p->axis == 0)
+        return dx * (Hz[IDX(g, i, j, k)] - Hz[IDX(g, i, j - 1, k)] - Hy[IDX(g, i, j, k)] + Hy[IDX(g, i, j, k - 1)]);
+    return dx * (Hx[IDX(g, i, j, k)] - Hx[IDX(g, i, j, k - 1)] - Hz[IDX(g, i, j, k)] + Hz[IDX(g, i - 1, j, k)]);
+}
+
+/* advance n full steps: H to n+1/2, record I/H probes, E to n+1 (with the
+ * sources at n+1/2), record V/E probes */
+int orc_step(orc_grid *g, int n)
+{
+    if (!g->finalized) return -8;
+    for (int s = 0; s < n; s++) {
+        update_h(g);
+        for (int p = 0; p < g->n_probes; p++)
+            if ((g->probes[p].kind == PROBE_I || g->probes[p].kind == PROBE_H) && g->step < g->max_steps)
+                g->probe_out[(size_t)p * g->max_steps + g->step] = probe_value(g, &g->probes[p]);
+        update_e(g);
+        for (int p = 0; p < g->n_probes; p++)
+            if ((g->probes[p].kind == PROBE_V || g->probes[p].kind == PROBE_E) && g->step < g->max_steps)
+                g->probe_out[(size_t)p * g->max_steps + g->step] = probe_value(g, &g->probes[p]);
+        g->step++;
+    }
+    return 0;
+}
+
+int orc_read_probe(const orc_grid *g, int p, double *out)
+{
+    if (p < 0 || p >= g->n_probes) return -1;
+    memcpy(out, g->probe_out + (size_t)p * g->max_steps, (size_t)g->max_steps * sizeof(double));
+    return 0;
+}

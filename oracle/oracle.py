@@ -1,0 +1,181 @@
+"""Python handle on the FP64 CPU FDTD oracle (fdtd_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and the
+cpu_baseline / reference legs of ``bench.py`` are the only callers.  The CUDA
+library never imports this module and this module never imports the
+library.
+
+The C file follows the paper's Sec. 2.1 (Eq. maxwell, maxwelle, maxwellh,
+fdtdex, fdtdhx), Sec. 2.2 (CPML), Sec. 2.3 (thin wires) and the "calculate"
+probes of the Sec. 4 model files; see its header for the readings taken.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fdtd_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liborc_fdtd.so")
+_lock = threading.Lock()
+_lib = None
+
+PROBE_V, PROBE_I, PROBE_E, PROBE_H = 0, 1, 2, 3
+EX, EY, EZ, HX, HY, HZ = range(6)
+
+C0 = 299792458.0
+EPS0 = 8.8541878128e-12
+MU0 = 1.25663706212e-6
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (FP64, OpenMP, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+           "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        I = ctypes.c_int
+        D = ctypes.c_double
+        dp = ctypes.POINTER(ctypes.c_double)
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        lib.orc_create.restype = P
+        lib.orc_create.argtypes = [I, I, I, D, D, I]
+        lib.orc_destroy.argtypes = [P]
+        lib.orc_dt.restype = D
+        lib.orc_dt.argtypes = [P]
+        lib.orc_step_count.restype = ctypes.c_long
+        lib.orc_step_count.argtypes = [P]
+        lib.orc_set_cpml.argtypes = [P, I, D, D, D, D, D]
+        lib.orc_set_materials.argtypes = [P, u8p, dp, dp, dp, I]
+        lib.orc_add_wire.argtypes = [P, I, I, I, I, I, I, D]
+        lib.orc_add_source.argtypes = [P, I, I, I, I, dp, I]
+        lib.orc_add_probe.argtypes = [P, I, I, I, I, I, I]
+        lib.orc_finalize.argtypes = [P, I]
+        lib.orc_set_field.argtypes = [P, I, dp]
+        lib.orc_get_field.argtypes = [P, I, dp]
+        lib.orc_get_coef.argtypes = [P, I, dp]
+        lib.orc_step.argtypes = [P, I]
+        lib.orc_read_probe.argtypes = [P, I, dp]
+        _lib = lib
+        return lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise ValueError(f"oracle {what} failed with status {rc}")
+
+
+class OracleGrid:
+    """One FP64 simulation domain.
+
+    Arrays are exchanged in the cell-owned layout: shape (nz, ny, nx), entry
+    [k, j, i] = Ex(i+1/2,j,k), Ey(i,j+1/2,k), Ez(i,j,k+1/2), Hx(i,j+1/2,k+1/2),
+    Hy(i+1/2,j,k+1/2) or Hz(i+1/2,j+1/2,k).
+    """
+
+    def __init__(self, nx, ny, nz, dx, courant=0.99, parity=False):
+        self._lib = _load()
+        self.shape = (nz, ny, nx)
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.dx = dx
+        h = self._lib.orc_create(nx, ny, nz, float(dx), float(courant), int(bool(parity)))
+        if not h:
+            raise ValueError("oracle rejected the grid")
+        self._h = h
+        self.n_probes = 0
+        self.max_steps = 0
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._lib.orc_destroy(h)
+            self._h = None
+
+    @property
+    def dt(self) -> float:
+        return self._lib.orc_dt(self._h)
+
+    @property
+    def step_count(self) -> int:
+        return self._lib.orc_step_count(self._h)
+
+    def set_cpml(self, cells, order=3.0, kappa_max=1.0, alpha_max=0.0, alpha_order=1.0,
+                 sigma_max=0.0):
+        _check(self._lib.orc_set_cpml(self._h, int(cells), order, kappa_max, alpha_max,
+                                      alpha_order, sigma_max), "set_cpml")
+
+    def set_materials(self, cell_material, eps_r, sigma, mu_r):
+        cm = np.ascontiguousarray(cell_material, dtype=np.uint8)
+        assert cm.shape == self.shape
+        e = np.ascontiguousarray(eps_r, dtype=np.float64)
+        s = np.ascontiguousarray(sigma, dtype=np.float64)
+        m = np.ascontiguousarray(mu_r, dtype=np.float64)
+        _check(self._lib.orc_set_materials(
+            self._h, cm.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+            _dptr(e), _dptr(s), _dptr(m), len(e)), "set_materials")
+
+    def add_wire(self, p0, p1, radius):
+        _check(self._lib.orc_add_wire(self._h, *map(int, p0), *map(int, p1), float(radius)),
+               "add_wire")
+
+    def add_source(self, node, axis, current):
+        cur = np.ascontiguousarray(current, dtype=np.float64)
+        _check(self._lib.orc_add_source(self._h, *map(int, node), int(axis), _dptr(cur),
+                                        len(cur)), "add_source")
+
+    def add_probe(self, kind, node, axis, n_edges=1):
+        _check(self._lib.orc_add_probe(self._h, int(kind), *map(int, node), int(axis),
+                                       int(n_edges)), "add_probe")
+        self.n_probes += 1
+        return self.n_probes - 1
+
+    def finalize(self, max_steps=0):
+        _check(self._lib.orc_finalize(self._h, int(max_steps)), "finalize")
+        self.max_steps = int(max_steps)
+
+    def set_field(self, comp, values):
+        v = np.ascontiguousarray(values, dtype=np.float64)
+        assert v.shape == self.shape
+        _check(self._lib.orc_set_field(self._h, int(comp), _dptr(v)), "set_field")
+
+    def get_field(self, comp) -> np.ndarray:
+        out = np.empty(self.shape, dtype=np.float64)
+        _check(self._lib.orc_get_field(self._h, int(comp), _dptr(out)), "get_field")
+        return out
+
+    def get_coef(self, which) -> np.ndarray:
+        out = np.empty(self.shape, dtype=np.float64)
+        _check(self._lib.orc_get_coef(self._h, int(which), _dptr(out)), "get_coef")
+        return out
+
+    def step(self, n):
+        _check(self._lib.orc_step(self._h, int(n)), "step")
+
+    def read_probe(self, p) -> np.ndarray:
+        out = np.empty(max(self.max_steps, 1), dtype=np.float64)
+        _check(self._lib.orc_read_probe(self._h, int(p), _dptr(out)), "read_probe")
+        return out[: self.max_steps]
