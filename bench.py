@@ -1,0 +1,304 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 FDTD hot path, in Gcell-updates/s.
+
+One bench step = one full Yee time step (H half-step, E half-step, CPML,
+thin-wire classes, current source, probes) of the whole grid.  Workload:
+the 256^3 grid of dx = 0.5 m with a 10-cell CPML, air over a soil
+half-space (eps_r 15, sigma 0.002 S/m), a 30 m vertical thin wire (r = 5 mm)
+fed at its base by a 1.2/50 us double-exponential current of 10 kA, and six
+probes; --steps defaults to the workload's 4000 steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: the path does not shard; N ranks run N independent replicas
+(weak scaling), value = all ranks' cell updates / the slowest rank's time.
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gcell-updates/s"
+UNIT = "Gcell/s"
+KERNEL_SRC = os.path.join(ROOT, "paper_2207_06908_gb300", "csrc", "fdtd_kernels.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def args_parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0,
+                    help="bound on the oracle's timed CPU work")
+    return ap.parse_args()
+
+
+def workload(n_steps):
+    from paper_2207_06908_gb300 import workloads
+    return workloads.config2(n_steps=n_steps)
+
+
+def workload_config(sc, steps):
+    return {"workload": "256^3 Yee grid dx=0.5m, 10-cell CPML, soil half-space (eps_r 15, sigma 2 mS/m), "
+                        "30 m thin wire r=5mm, 1.2/50us 10kA double-exponential source, 6 probes",
+            "grid": list(sc.n), "cpml_cells": sc.cpml, "courant": sc.courant, "steps_timed": steps,
+            "l2": "inputs larger than L2 (about 0.95 GB of fields, classes and CPML state per step)"}
+
+
+def bytes_per_step(sc):
+    """algorithmic DRAM bytes of one fused step: 6 fields read + 6 written
+    (FP32) and the class byte per cell, plus 4 CPML psi arrays read and
+    written per slab cell and axis"""
+    nx, ny, nz = sc.n
+    d = sc.cpml
+    slab = 2 * d * (ny * nz + nx * nz + nx * ny) if d else 0
+    return 49 * nx * ny * nz + 32 * slab
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_hash():
+    with open(KERNEL_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def recorded_traffic(cells):
+    """DRAM bytes per launch of the step kernel from the committed ncu
+    summary, scaled to this grid; None when the kernel changed since."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+    except Exception:
+        return None
+    if t.get("kernel_sha") != kernel_hash():
+        return None
+    return t["dram_bytes_per_launch"] * cells / t["cells"]
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region"""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_id):
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={dev_id}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.6)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if not self.p:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(sc, budget_s):
+    """the FP64 oracle as it stands, on the host cores, on a bounded number
+    of steps of the same grid"""
+    from oracle import oracle as O
+    o = O.OracleGrid.from_scenario(sc, parity=False)
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter() - t0
+    n = max(1, min(sc.n_steps - 1, int(budget_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    o.step(n)
+    dt = time.perf_counter() - t0
+    cells = sc.cells
+    return {"value": cells * n / dt / 1e9, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{n} FP64 steps of the full {sc.n[0]}x{sc.n[1]}x{sc.n[2]} workload grid "
+                      f"(after 1 untimed step; setup excluded), {dt:.1f} s"}
+
+
+def run_reference(a):
+    """--impl reference: the FP64 oracle timed on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sc = workload(a.steps + a.warmup)
+    from oracle import oracle as O
+    o = O.OracleGrid.from_scenario(sc, parity=False)
+    w = min(a.warmup, 1)
+    t0 = time.perf_counter()
+    o.step(max(w, 1))
+    t1 = (time.perf_counter() - t0) / max(w, 1)
+    n = max(1, min(a.steps, int(a.cpu_seconds * 3 / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    o.step(n)
+    dt = time.perf_counter() - t0
+    v = sc.cells * n / dt / 1e9
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": n, "warmup": w,
+            "ms_per_step": dt / n * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": workload_config(sc, n),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": f"{n} of {a.steps} requested FP64 steps of the full workload grid"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = args_parse()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+
+    from paper_2207_06908_gb300 import _build, fdtd
+    _build.build()
+
+    K, Wm = a.steps, max(3, a.warmup)
+    sc = workload(K + Wm)
+    stream = torch.cuda.current_stream()
+    g = fdtd.from_scenario(sc, probe_capacity=K + Wm)
+    g.step(Wm)
+    g.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    dev_uuid = None
+    try:
+        dev_uuid = str(torch.cuda.get_device_properties(local).uuid)
+        if not dev_uuid.startswith("GPU-"):
+            dev_uuid = "GPU-" + dev_uuid
+    except Exception:
+        dev_uuid = str(local)
+    clk = Clocks(dev_uuid)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    # sanity: the run stayed finite
+    probe = g.read_probe(0, 0, K + Wm)
+    finite = bool(all(math.isfinite(float(x)) for x in probe))
+    g.close()
+
+    cells = sc.cells
+    value = world * cells * K / (ms / 1e3) / 1e9
+    bps = bytes_per_step(sc)
+    peak, peak_kind = peaks()
+    achieved = bps / (ms / K / 1e3) / 1e9
+    traffic = recorded_traffic(cells)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_source": peak_kind,
+                "kernel": "step_kernel (per-step time incl. the source/probe kernel)",
+                "bytes_per_step": bps}
+
+    e2e = None
+    if not a.no_e2e:
+        # the whole job through the public API from host buffers: build the
+        # grid from the host material map / wire / source / probe arrays,
+        # upload, step K, read every probe waveform back to the host
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g2 = fdtd.from_scenario(sc, probe_capacity=K)
+        g2.step(K)
+        outs = [g2.read_probe(p, 0, K) for p in range(len(sc.probes))]
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        n_cls = g2.num_classes
+        g2.close()
+        nx, ny, nz = sc.n
+        pitch = (nx + 3) // 4 * 4
+        h2d = (pitch * ny * nz + n_cls * 9 * 4 + 6 * 4 * (nx + ny + nz)
+               + sum(len(s[2]) for s in sc.sources) * 4 + 32 * len(sc.sources) + 24 * len(sc.probes))
+        d2h = sum(o.nbytes for o in outs)
+        if world > 1:
+            t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": world * cells * K / t_e2e / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
+               "seconds": t_e2e, "includes": "grid setup, class building, upload, K steps, probe readback"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = cpu_baseline(sc, a.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
+                "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic", "config": workload_config(sc, K),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": 2 * K, "finite": finite}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

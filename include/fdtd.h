@@ -1,0 +1,172 @@
+/*
+ * fdtd.h -- C ABI of the GB300 (sm_103a) FDTD library.
+ *
+ * The library advances Maxwell's curl equations (Kuklin, "elecode",
+ * arXiv 2207.06908, Sec. 2.1, Eq. maxwell / maxwelle / maxwellh) on a
+ * uniform cubic Yee grid with the staggered updates of Eq. fdtdex and
+ * Eq. fdtdhx, in FP32 on one GPU.  Per-cell eps, sigma, mu come from a
+ * uint8 material map; thin wires (Sec. 2.3), ideal current sources
+ * (Sec. 2.1, "sources"), a CPML absorbing layer (Sec. 2.2) and the voltage /
+ * current probes of the Sec. 4 model files ("calculate") are supported.
+ *
+ * Conventions for every call:
+ *   - Return value: FDTD_OK (0) or a negative FDTD_E* code.  Nothing throws
+ *     across the ABI.  fdtd_last_error() gives a one-line reason.
+ *   - Host arrays passed in are copied before the call returns; the caller
+ *     keeps ownership.  Host arrays passed out are written by the call.
+ *   - A grid handle is owned by the library and freed by fdtd_destroy().
+ *   - Mutators (set_materials, add_*) fail with FDTD_ESTATE after
+ *     fdtd_finalize(); step/read/get/set fail with FDTD_ESTATE before it.
+ *   - Indices are node indices: node (i,j,k) sits at (i dx, j dx, k dx),
+ *     0 <= i <= nx.  Cell (i,j,k) is the cube above node (i,j,k) and owns
+ *     the six components Ex(i+1/2,j,k) Ey(i,j+1/2,k) Ez(i,j,k+1/2)
+ *     Hx(i,j+1/2,k+1/2) Hy(i+1/2,j,k+1/2) Hz(i+1/2,j+1/2,k).
+ *   - Field arrays exchanged with the host are nx*ny*nz floats, x fastest
+ *     (index (k*ny + j)*nx + i), entry = the component owned by that cell.
+ *     E is at t_n, H at t_{n-1/2} when n steps have been taken.
+ *   - The outer boundary is PEC: tangential E on the six faces is zero.
+ *     With a CPML the layer sits inside the grid, next to that wall.
+ *   - Work is queued on the CUDA stream given at creation; calls that return
+ *     host data synchronise that stream first.
+ */
+#ifndef FDTD_GB300_FDTD_H
+#define FDTD_GB300_FDTD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fdtd_grid fdtd_grid;
+
+/* One material: relative permittivity, conductivity (S/m), relative
+ * permeability.  eps_r > 0, sigma >= 0, mu_r > 0. */
+typedef struct {
+    double eps_r;
+    double sigma;
+    double mu_r;
+} fdtd_material;
+
+/* CPML layer (Sec. 2.2, convolutional PML of Roden and Gedney, CFS form).
+ * cells: thickness in cells on each of the six faces (0 = plain PEC box);
+ * order: polynomial grading m of sigma and kappa; kappa_max >= 1;
+ * alpha_max >= 0 (S/m) with grading order alpha_order;
+ * sigma_max <= 0 selects 0.8 (m + 1) / (eta0 dx). */
+typedef struct {
+    int cells;
+    double order;
+    double kappa_max;
+    double alpha_max;
+    double alpha_order;
+    double sigma_max;
+} fdtd_cpml;
+
+enum {
+    FDTD_OK = 0,
+    FDTD_EINVAL = -1,     /* bad argument, index out of range */
+    FDTD_ECOURANT = -2,   /* Courant number outside (0, 1] */
+    FDTD_ENOMEM = -3,     /* host or device allocation failed, or arena too small */
+    FDTD_ECUDA = -4,      /* a CUDA call failed */
+    FDTD_ECLASSES = -5,   /* more than 256 distinct coefficient classes */
+    FDTD_ETIMEOUT = -6,   /* a bounded device wait ran out */
+    FDTD_EDIVERGED = -7,  /* non-finite field detected */
+    FDTD_ESTATE = -8      /* call not allowed in the grid's current state */
+};
+
+enum {
+    FDTD_PROBE_V = 0,     /* voltage -sum E_axis dx over n_edges edges from node (i,j,k) along +axis, at t_{n+1} */
+    FDTD_PROBE_I = 1,     /* current: loop integral of H around the edge from node (i,j,k) along +axis, at t_{n+1/2} */
+    FDTD_PROBE_E = 2,     /* E component `axis` owned by cell (i,j,k), at t_{n+1} */
+    FDTD_PROBE_H = 3      /* H component `axis` owned by cell (i,j,k), at t_{n+1/2} */
+};
+
+/* Create a grid of nx*ny*nz cells of edge dx metres.  The time step is
+ * dt = courant * dx / (c0 sqrt 3), the Courant limit of the cubic Yee grid
+ * (Sec. 2.1) scaled by courant in (0, 1].  cpml may be NULL (PEC box).
+ * cuda_stream: a cudaStream_t (NULL = the legacy default stream) on which
+ * all device work of this grid is queued.  Every material starts as vacuum.
+ * nx, ny, nz >= 2 (>= 2*cells + 2 with a CPML).  *out receives the handle. */
+int fdtd_create_grid(int nx, int ny, int nz, double dx, double courant,
+                     const fdtd_cpml *cpml, void *cuda_stream, fdtd_grid **out);
+
+/* Material map (Sec. 4 model files, "block"): cell_material is nx*ny*nz
+ * bytes, x fastest, each < n_materials; table holds n_materials (1..256)
+ * entries.  E edges take the mean eps, sigma of the four cells around them,
+ * H faces the mean mu of the two cells on either side. */
+int fdtd_set_materials(fdtd_grid *g, const uint8_t *cell_material,
+                       const fdtd_material *table, int n_materials);
+
+/* Thin wire (Sec. 2.3; "wire(thin, ...)" in the Sec. 4 model files) along
+ * one axis from node (i0,j0,k0) to node (i1,j1,k1), i1>i0 or j1>j0 or k1>k0
+ * with the other two coordinates equal and strictly inside the grid
+ * (1..n-1).  The on-wire E edges become PEC.  Radius 0 < radius <= 0.23 dx:
+ * the radial E at each wire node take eps, sigma times
+ * m = ln(dx / 0.23 dx) / ln(dx / radius) and every H those E read takes
+ * mu / m.  Where two wires share a component the smaller m is used.
+ * *wire_id (may be NULL) receives the wire's index. */
+int fdtd_add_wire(fdtd_grid *g, int i0, int j0, int k0, int i1, int j1, int k1,
+                  double radius, int *wire_id);
+
+/* Ideal current source (Sec. 2.1 sources; "source(current, ...)" in the
+ * Sec. 4 model files) on the edge from node (i,j,k) along +axis (0,1,2):
+ * J = I / dx^2 along +axis, I(t_{n+1/2}) = current[n] for n < n_samples and
+ * 0 after.  The transverse node coordinates must lie in 1..n-1.
+ * r_internal must be 0 (non-ideal sources are not supported: FDTD_EINVAL).
+ * Samples are rounded to FP32.  *source_id (may be NULL) receives the index. */
+int fdtd_add_source(fdtd_grid *g, int i, int j, int k, int axis, double r_internal,
+                    const double *current, int n_samples, int *source_id);
+
+/* Probe (Sec. 4 model files, "calculate(voltage|current, ...)"), one of
+ * FDTD_PROBE_*.  For FDTD_PROBE_V, n_edges >= 1 edges from node (i,j,k)
+ * along +axis; ignored otherwise.  FDTD_PROBE_I needs the two transverse
+ * node coordinates >= 1.  *probe_id (may be NULL) receives the index. */
+int fdtd_add_probe(fdtd_grid *g, int kind, int i, int j, int k, int axis, int n_edges,
+                   int *probe_id);
+
+/* Device bytes fdtd_finalize() needs for probe_capacity recorded steps. */
+int fdtd_arena_bytes(const fdtd_grid *g, int probe_capacity, size_t *bytes);
+
+/* Build the coefficient classes, upload everything and zero the fields.
+ * probe_capacity: number of steps recorded per probe (steps beyond it are
+ * not recorded).  arena: device memory of at least fdtd_arena_bytes()
+ * bytes, 256-byte aligned, owned by the caller and kept alive until
+ * fdtd_destroy(); NULL makes the library allocate (and free) its own.
+ * Fails with FDTD_ECLASSES if more than 256 distinct coefficient sets
+ * occur. */
+int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_bytes);
+
+/* Queue n full time steps (H to n+1/2, E to n+1 with the sources, probes)
+ * on the grid's stream.  Returns launch errors only; does not synchronise. */
+int fdtd_step(fdtd_grid *g, int n);
+
+/* Wait for the grid's queued work; reports asynchronous CUDA errors. */
+int fdtd_synchronize(fdtd_grid *g);
+
+/* Copy count recorded samples of one probe, starting at step first_step,
+ * to host_out (count floats).  Synchronises. */
+int fdtd_read_probes(fdtd_grid *g, int probe_id, int first_step, int count, float *host_out);
+
+/* Copy one component (0..5 = Ex Ey Ez Hx Hy Hz) to / from a host array of
+ * nx*ny*nz floats.  Synchronises. */
+int fdtd_get_field(fdtd_grid *g, int component, float *host_out);
+int fdtd_set_field(fdtd_grid *g, int component, const float *host_in);
+
+/* Device address, row pitch (elements) and plane pitch (elements) of the
+ * current buffer of one component, for device-side consumers.  The address
+ * changes after every step (the update ping-pongs between two buffers). */
+int fdtd_field_device(fdtd_grid *g, int component, void **dptr, int *row_pitch,
+                      size_t *plane_pitch);
+
+double fdtd_get_dt(const fdtd_grid *g);
+long fdtd_get_step(const fdtd_grid *g);
+int fdtd_num_classes(const fdtd_grid *g);
+const char *fdtd_last_error(const fdtd_grid *g);
+void fdtd_destroy(fdtd_grid *g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDTD_GB300_FDTD_H */

@@ -45,6 +45,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_C0 299792458.0
 #define ORC_EPS0 8.8541878128e-12
@@ -141,6 +144,16 @@ void orc_destroy(orc_grid *g)
 }
 
 double orc_dt(const orc_grid *g) { return g->dt; }
+
+/* number of OpenMP threads the update loops use */
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 long orc_step_count(const orc_grid *g) { return g->step; }
 
 /* sigma_max <= 0 selects 0.8 (m+1) / (eta0 dx), the usual optimum for a

@@ -63,6 +63,8 @@ def _load():
         lib.orc_destroy.argtypes = [P]
         lib.orc_dt.restype = D
         lib.orc_dt.argtypes = [P]
+        lib.orc_num_threads.restype = ctypes.c_int
+        lib.orc_num_threads.argtypes = []
         lib.orc_step_count.restype = ctypes.c_long
         lib.orc_step_count.argtypes = [P]
         lib.orc_set_cpml.argtypes = [P, I, D, D, D, D, D]
@@ -78,6 +80,11 @@ def _load():
         lib.orc_read_probe.argtypes = [P, I, dp]
         _lib = lib
         return lib
+
+
+def num_threads() -> int:
+    """OpenMP threads the oracle's update loops run on."""
+    return _load().orc_num_threads()
 
 
 def _dptr(a: np.ndarray):
@@ -174,6 +181,30 @@ class OracleGrid:
 
     def step(self, n):
         _check(self._lib.orc_step(self._h, int(n)), "step")
+
+    @classmethod
+    def from_scenario(cls, sc, parity=True):
+        """Build from a problem description with the attributes n, dx,
+        courant, cpml, cell_material, materials [(eps_r, sigma, mu_r)],
+        wires [(p0, p1, radius)], sources [(node, axis, current)], probes
+        [(kind, node, axis, n_edges)], n_steps and fields (or None)."""
+        g = cls(*sc.n, sc.dx, courant=sc.courant, parity=parity)
+        if sc.cpml:
+            g.set_cpml(sc.cpml)
+        g.set_materials(sc.cell_material, [m[0] for m in sc.materials], [m[1] for m in sc.materials],
+                        [m[2] for m in sc.materials])
+        for p0, p1, r in sc.wires:
+            g.add_wire(p0, p1, r)
+        for node, axis, cur in sc.sources:
+            g.add_source(node, axis, cur)
+        for kind, node, axis, ne in sc.probes:
+            g.add_probe(kind, node, axis, ne)
+        g.finalize(sc.n_steps)
+        if sc.fields is not None:
+            # start from the FP32-rounded fields the GPU starts from
+            for c, f in enumerate(sc.fields):
+                g.set_field(c, np.asarray(f, dtype=np.float32).astype(np.float64))
+        return g
 
     def read_probe(self, p) -> np.ndarray:
         out = np.empty(max(self.max_steps, 1), dtype=np.float64)

@@ -1,0 +1,88 @@
+"""ctypes binding of the C ABI in include/fdtd.h (argument marshalling only).
+
+Every step of the path runs in the CUDA library; there is no CPU fallback.
+Loading fails with an exception when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import _build
+
+_lock = threading.Lock()
+_lib = None
+
+FDTD_OK = 0
+ERRORS = {
+    -1: "FDTD_EINVAL", -2: "FDTD_ECOURANT", -3: "FDTD_ENOMEM", -4: "FDTD_ECUDA",
+    -5: "FDTD_ECLASSES", -6: "FDTD_ETIMEOUT", -7: "FDTD_EDIVERGED", -8: "FDTD_ESTATE",
+}
+
+
+class FdtdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class CpmlParams(ctypes.Structure):
+    _fields_ = [("cells", ctypes.c_int), ("order", ctypes.c_double), ("kappa_max", ctypes.c_double),
+                ("alpha_max", ctypes.c_double), ("alpha_order", ctypes.c_double),
+                ("sigma_max", ctypes.c_double)]
+
+
+class Material(ctypes.Structure):
+    _fields_ = [("eps_r", ctypes.c_double), ("sigma", ctypes.c_double), ("mu_r", ctypes.c_double)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libfdtd_gb300.so (raises if it is not built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} is missing "
+                               "(run __graft_entry__.build() or python -m paper_2207_06908_gb300._build)")
+        lib = ctypes.CDLL(path)
+        P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+        ip = ctypes.POINTER(ctypes.c_int)
+        sig = {
+            "fdtd_create_grid": (I, [I, I, I, D, D, ctypes.POINTER(CpmlParams), P, ctypes.POINTER(P)]),
+            "fdtd_set_materials": (I, [P, P, ctypes.POINTER(Material), I]),
+            "fdtd_add_wire": (I, [P, I, I, I, I, I, I, D, ip]),
+            "fdtd_add_source": (I, [P, I, I, I, I, D, P, I, ip]),
+            "fdtd_add_probe": (I, [P, I, I, I, I, I, I, ip]),
+            "fdtd_arena_bytes": (I, [P, I, ctypes.POINTER(S)]),
+            "fdtd_finalize": (I, [P, I, P, S]),
+            "fdtd_step": (I, [P, I]),
+            "fdtd_synchronize": (I, [P]),
+            "fdtd_read_probes": (I, [P, I, I, I, P]),
+            "fdtd_get_field": (I, [P, I, P]),
+            "fdtd_set_field": (I, [P, I, P]),
+            "fdtd_field_device": (I, [P, I, ctypes.POINTER(P), ip, ctypes.POINTER(S)]),
+            "fdtd_get_dt": (D, [P]),
+            "fdtd_get_step": (ctypes.c_long, [P]),
+            "fdtd_num_classes": (I, [P]),
+            "fdtd_last_error": (ctypes.c_char_p, [P]),
+            "fdtd_destroy": (None, [P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def check(lib, handle, rc: int, what: str):
+    if rc != FDTD_OK:
+        msg = lib.fdtd_last_error(handle).decode() if handle else what
+        raise FdtdError(rc, f"{what}: {msg}")

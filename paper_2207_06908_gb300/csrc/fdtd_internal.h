@@ -1,0 +1,84 @@
+// fdtd_internal.h -- structures shared by the host runtime and the kernels
+// of the GB300 FDTD library (not part of the public C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace fdtd {
+
+// Coefficients of one class, in this order (1/dx folded into cb and db):
+//   ca_x ca_y ca_z  cb_x cb_y cb_z  db_x db_y db_z
+constexpr int kNumCoef = 9;
+constexpr int kMaxClasses = 256;
+
+// Auxiliary CPML fields, one per (component, derivative axis).  The slab of
+// axis u holds 2*d cells along u: s = i for i < d, s = i - (n - 2d) for
+// i >= n - d.  Layouts: x slab [k][j][s], y slab [k][s][i], z slab [s][j][i].
+enum Psi {
+    PSI_HY_X = 0, PSI_HZ_X, PSI_EY_X, PSI_EZ_X,
+    PSI_HX_Y, PSI_HZ_Y, PSI_EX_Y, PSI_EZ_Y,
+    PSI_HX_Z, PSI_HY_Z, PSI_EX_Z, PSI_EY_Z,
+    PSI_COUNT
+};
+
+// 1D CPML profile per axis, n entries each, indexed by the cell index i:
+//   E position (node i):      be, ce, kie
+//   H position (node i + 1/2): bh, ch, kih
+enum Prof { PR_BE = 0, PR_CE, PR_KIE, PR_BH, PR_CH, PR_KIH, PR_COUNT };
+
+struct StepArgs {
+    int nx, ny, nz;
+    int pitch;               // row pitch in elements (multiple of 4)
+    long long plane;         // plane pitch in elements (pitch * ny)
+    const float *Ein[3];
+    const float *Hin[3];
+    float *Eout[3];
+    float *Hout[3];
+    const uint8_t *cls;      // class per cell, same pitch as the fields
+    const float *table;      // [n_classes][kNumCoef]
+    int n_classes;
+    int d;                   // CPML cells (0 = none)
+    const float *prof[3];    // per axis: PR_COUNT arrays of n_axis floats
+    const float *psi_in[PSI_COUNT];
+    float *psi_out[PSI_COUNT];
+    int kz;                  // planes per z chunk
+};
+
+struct SourceDesc {
+    int comp;                // 0..2
+    long long idx;           // element index in the field arrays
+    float coef;              // -cb / dx of the edge
+    int n_samples;
+    long long sample_off;    // offset into the sample table
+};
+
+struct ProbeDesc {
+    int kind, axis;
+    int i, j, k, n_edges;
+};
+
+struct EdgeArgs {
+    int nx, ny, nz, pitch;
+    long long plane;
+    float dx;
+    float *E[3];             // fields after the stencil (t_{n+1}, t_{n+1/2})
+    const float *H[3];
+    const SourceDesc *src;
+    int n_src;
+    const float *samples;
+    const ProbeDesc *probes;
+    int n_probes;
+    float *probe_out;        // [n_probes][capacity]
+    int capacity;
+    long long *step;         // device step counter
+};
+
+// kernels.cu
+cudaError_t launch_step(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_edges(const EdgeArgs &a, cudaStream_t s);
+int step_tile_x();
+int step_tile_y();
+
+}  // namespace fdtd

@@ -1,0 +1,750 @@
+// fdtd_runtime.cu -- host side of the C ABI declared in include/fdtd.h.
+//
+// Owns the grid description, turns materials, PEC walls and thin wires into
+// per-cell coefficient classes (one byte per cell, <= 256 classes), builds
+// the CPML profiles, lays every device buffer out in one arena, and queues
+// time steps on the caller's stream, replaying a captured CUDA graph of a
+// fixed number of steps where it can.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <array>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "fdtd.h"
+#include "fdtd_internal.h"
+
+namespace {
+
+constexpr double kC0 = 299792458.0;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kMu0 = 1.25663706212e-6;
+constexpr double kR0 = 0.23;        // intrinsic radius of a zero-E line, in cells
+constexpr int kGraphSteps = 32;     // steps per captured graph (even)
+
+struct Wire { int axis, p[3], n; double radius; };
+struct Source { int axis, p[3]; std::vector<float> cur; };
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct fdtd_grid {
+    int nx = 0, ny = 0, nz = 0;
+    double dx = 0, dt = 0, courant = 0;
+    fdtd_cpml cpml{};
+    int d = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<uint8_t> mat;
+    std::vector<fdtd_material> table;
+    std::vector<Wire> wires;
+    std::vector<Source> srcs;
+    std::vector<fdtd::ProbeDesc> probes;
+    bool finalized = false;
+    int capacity = 0;
+    int pitch = 0;
+    long long plane = 0;
+    // device
+    void *arena = nullptr;
+    size_t arena_bytes = 0;
+    bool own_arena = false;
+    float *F[2][6] = {};
+    uint8_t *cls = nullptr;
+    float *table_d = nullptr;
+    int n_classes = 0;
+    float *prof[3] = {};
+    float *psi[2][fdtd::PSI_COUNT] = {};
+    fdtd::SourceDesc *src_d = nullptr;
+    float *samples_d = nullptr;
+    fdtd::ProbeDesc *probes_d = nullptr;
+    float *probe_out = nullptr;
+    long long *step_d = nullptr;
+    int parity = 0;
+    long step = 0;
+    int kz = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    std::string err;
+};
+
+namespace {
+
+int fail(fdtd_grid *g, int code, const std::string &msg)
+{
+    if (g) g->err = msg;
+    return code;
+}
+
+int cuda_fail(fdtd_grid *g, cudaError_t e, const char *what)
+{
+    return fail(g, FDTD_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// ---- device arena plan -------------------------------------------------
+struct Plan {
+    size_t field, cls, table, prof[3], psi[fdtd::PSI_COUNT], src, samples, probes, out, step, total;
+};
+
+size_t psi_elems(const fdtd_grid *g, int which)
+{
+    const size_t d2 = 2 * (size_t)g->d;
+    const int axis = which / 4;
+    if (g->d == 0) return 0;
+    if (axis == 0) return d2 * g->ny * g->nz;
+    if (axis == 1) return (size_t)g->nx * d2 * g->nz;
+    return (size_t)g->nx * g->ny * d2;
+}
+
+Plan make_plan(const fdtd_grid *g, int capacity)
+{
+    Plan p{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t at = off; off = align_up(off + bytes, 256); return at; };
+    const size_t cells = (size_t)g->plane * g->nz;
+    p.field = take(12 * cells * sizeof(float));
+    p.cls = take(cells);
+    p.table = take(fdtd::kMaxClasses * fdtd::kNumCoef * sizeof(float));
+    const int n[3] = {g->nx, g->ny, g->nz};
+    for (int u = 0; u < 3; ++u) p.prof[u] = take(fdtd::PR_COUNT * (size_t)n[u] * sizeof(float));
+    for (int q = 0; q < fdtd::PSI_COUNT; ++q) p.psi[q] = take(2 * psi_elems(g, q) * sizeof(float));
+    size_t ns = 0;
+    for (auto &s : g->srcs) ns += s.cur.size();
+    p.src = take(std::max<size_t>(1, g->srcs.size()) * sizeof(fdtd::SourceDesc));
+    p.samples = take(std::max<size_t>(1, ns) * sizeof(float));
+    p.probes = take(std::max<size_t>(1, g->probes.size()) * sizeof(fdtd::ProbeDesc));
+    p.out = take(std::max<size_t>(1, g->probes.size()) * (size_t)std::max(capacity, 1) * sizeof(float));
+    p.step = take(sizeof(long long));
+    p.total = off;
+    return p;
+}
+
+// ---- coefficient classes -----------------------------------------------
+// Cell (i,j,k) owns Ex(i+1/2,j,k) Ey(i,j+1/2,k) Ez(i,j,k+1/2) and
+// Hx(i,j+1/2,k+1/2) Hy(i+1/2,j,k+1/2) Hz(i+1/2,j+1/2,k).
+using Tuple = std::array<uint32_t, fdtd::kNumCoef>;
+
+uint64_t key(int comp, long long cell) { return ((uint64_t)comp << 56) | (uint64_t)cell; }
+
+struct WireMods {
+    std::unordered_map<uint64_t, double> fe, fh;   // (component, cell) -> factor
+    std::unordered_map<uint64_t, char> pec;         // (E component, cell)
+    std::vector<uint8_t> touched;                   // per cell: any entry above
+};
+
+bool e_updated(const fdtd_grid *g, int comp, const int q[3])
+{
+    const int n[3] = {g->nx, g->ny, g->nz};
+    for (int u = 0; u < 3; ++u) {
+        if (u == comp) { if (q[u] < 0 || q[u] >= n[u]) return false; }
+        else if (q[u] < 1 || q[u] > n[u] - 1) return false;
+    }
+    return true;
+}
+
+long long cell_of(const fdtd_grid *g, const int q[3]) { return ((long long)q[2] * g->ny + q[1]) * g->nx + q[0]; }
+
+void set_min(std::unordered_map<uint64_t, double> &m, uint64_t k, double v)
+{
+    auto it = m.find(k);
+    if (it == m.end() || v < it->second) m[k] = v;
+}
+
+// Thin wires (Sec. 2.3): the on-wire E edges are PEC; the radial E at each
+// wire node take eps, sigma * m; every H such a radial E reads in its update
+// takes mu / m (this keeps every E-H coupling at or below its unmodified
+// size, so S <= 1 stays stable).  The smaller m wins where wires meet.
+WireMods wire_mods(const fdtd_grid *g)
+{
+    WireMods w;
+    w.touched.assign((size_t)g->nx * g->ny * g->nz, 0);
+    auto touch = [&](const int q[3]) {
+        if (q[0] >= 0 && q[1] >= 0 && q[2] >= 0 && q[0] < g->nx && q[1] < g->ny && q[2] < g->nz)
+            w.touched[cell_of(g, q)] = 1;
+    };
+    for (const Wire &wr : g->wires) {
+        const double m = std::log(1.0 / kR0) / std::log(g->dx / wr.radius);
+        const int a = wr.axis;
+        for (int s = 0; s <= wr.n; ++s) {
+            int p[3] = {wr.p[0], wr.p[1], wr.p[2]};
+            p[a] += s;
+            for (int t = 1; t <= 2; ++t) {
+                const int c = (a + t) % 3;            // radial component
+                for (int back = 0; back < 2; ++back) {
+                    int q[3] = {p[0], p[1], p[2]};
+                    q[c] -= back;
+                    if (!e_updated(g, c, q)) continue;
+                    set_min(w.fe, key(c, cell_of(g, q)), m);
+                    touch(q);
+                    // E_c reads H_{c+2} at q and q - e_{c+1}, H_{c+1} at q and q - e_{c+2}
+                    const int h1 = (c + 2) % 3, h2 = (c + 1) % 3;
+                    int r[3];
+                    std::memcpy(r, q, sizeof r); set_min(w.fh, key(h1, cell_of(g, r)), m); touch(r);
+                    r[(c + 1) % 3] -= 1; set_min(w.fh, key(h1, cell_of(g, r)), m); touch(r);
+                    std::memcpy(r, q, sizeof r); set_min(w.fh, key(h2, cell_of(g, r)), m); touch(r);
+                    r[(c + 2) % 3] -= 1; set_min(w.fh, key(h2, cell_of(g, r)), m); touch(r);
+                }
+            }
+            if (s < wr.n) {
+                w.pec[key(a, cell_of(g, p))] = 1;
+                touch(p);
+            }
+        }
+    }
+    return w;
+}
+
+struct Coefs {
+    const fdtd_grid *g;
+    const WireMods *w;
+    double e_coef(double eps_r, double sigma, double f, double *cb) const
+    {
+        const double e = kEps0 * eps_r * f;
+        const double s = sigma * f;
+        const double a = s * g->dt / (2.0 * e);
+        *cb = g->dt / (e * g->dx) / (1.0 + a);
+        return (1.0 - a) / (1.0 + a);
+    }
+    double h_coef(double mu_r, double f) const { return g->dt / (kMu0 * mu_r / f * g->dx); }
+    const fdtd_material &M(int i, int j, int k) const
+    {
+        return g->table[g->mat[((size_t)k * g->ny + j) * g->nx + i]];
+    }
+    // E component c of cell (i,j,k): mean eps, sigma of its four cells
+    void e_mat(int c, int i, int j, int k, double *eps, double *sig) const
+    {
+        int di[4], dj[4], dk[4];
+        for (int t = 0; t < 4; ++t) { di[t] = i; dj[t] = j; dk[t] = k; }
+        const int b = (c + 1) % 3, cc = (c + 2) % 3;
+        int *D[3] = {di, dj, dk};
+        // cells offset by 0/-1 along the two transverse axes
+        D[b][1] -= 1; D[b][3] -= 1;
+        D[cc][2] -= 1; D[cc][3] -= 1;
+        double e = 0, s = 0;
+        for (int t = 0; t < 4; ++t) {
+            const fdtd_material &m = M(di[t], dj[t], dk[t]);
+            e += m.eps_r;
+            s += m.sigma;
+        }
+        *eps = e / 4.0;
+        *sig = s / 4.0;
+    }
+    // H component c of cell (i,j,k): mean mu of the cells on either side
+    double h_mat(int c, int i, int j, int k) const
+    {
+        int q[3] = {i, j, k};
+        const double m1 = M(q[0], q[1], q[2]).mu_r;
+        q[c] -= 1;
+        return 0.5 * (m1 + M(q[0], q[1], q[2]).mu_r);
+    }
+    // coefficient of E component c at cell q: returns false for PEC
+    bool e_of(int c, const int q[3], long long cell, double *ca, double *cb) const
+    {
+        if (!e_updated(g, c, q)) { *ca = 0; *cb = 0; return false; }
+        double f = 1.0;
+        if (w && w->touched[cell]) {
+            if (w->pec.count(key(c, cell))) { *ca = 0; *cb = 0; return false; }
+            auto it = w->fe.find(key(c, cell));
+            if (it != w->fe.end()) f = it->second;
+        }
+        double eps, sig;
+        e_mat(c, q[0], q[1], q[2], &eps, &sig);
+        *ca = e_coef(eps, sig, f, cb);
+        return true;
+    }
+    double h_of(int c, const int q[3], long long cell) const
+    {
+        if (q[c] < 1) return 0.0;           // normal H on a wall never changes
+        double f = 1.0;
+        if (w && w->touched[cell]) {
+            auto it = w->fh.find(key(c, cell));
+            if (it != w->fh.end()) f = it->second;
+        }
+        return h_coef(h_mat(c, q[0], q[1], q[2]), f);
+    }
+    void cell(int i, int j, int k, float out[fdtd::kNumCoef]) const
+    {
+        const int q[3] = {i, j, k};
+        const long long c = cell_of(g, q);
+        for (int comp = 0; comp < 3; ++comp) {
+            double ca, cb;
+            e_of(comp, q, c, &ca, &cb);
+            out[comp] = (float)ca;
+            out[3 + comp] = (float)cb;
+            out[6 + comp] = (float)h_of(comp, q, c);
+        }
+    }
+};
+
+int build_classes(fdtd_grid *g, std::vector<uint8_t> &cls, std::vector<float> &table,
+                  std::vector<double> &src_cb)
+{
+    WireMods w = wire_mods(g);
+    Coefs C{g, &w};
+    std::map<Tuple, int> ids;
+    table.clear();
+    auto id_of = [&](const float v[fdtd::kNumCoef]) -> int {
+        Tuple t;
+        std::memcpy(t.data(), v, sizeof t);
+        auto it = ids.find(t);
+        if (it != ids.end()) return it->second;
+        const int id = (int)ids.size();
+        ids.emplace(t, id);
+        table.insert(table.end(), v, v + fdtd::kNumCoef);
+        return id;
+    };
+    // class of a cell inside a uniform block of one material, per material
+    std::vector<int> uniform_id(g->table.size(), -1);
+    cls.assign((size_t)g->plane * g->nz, 0);
+    const int nx = g->nx, ny = g->ny, nz = g->nz;
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const size_t c = ((size_t)k * ny + j) * nx + i;
+                const uint8_t m0 = g->mat[c];
+                bool uni = i > 0 && j > 0 && k > 0 && !w.touched[c];
+                if (uni) {
+                    // every cell that any owned component averages over
+                    const size_t sx = 1, sy = nx, sz = (size_t)nx * ny;
+                    uni = g->mat[c - sx] == m0 && g->mat[c - sy] == m0 && g->mat[c - sz] == m0 &&
+                          g->mat[c - sx - sy] == m0 && g->mat[c - sx - sz] == m0 &&
+                          g->mat[c - sy - sz] == m0;
+                }
+                int id;
+                if (uni && uniform_id[m0] >= 0) {
+                    id = uniform_id[m0];
+                } else {
+                    float v[fdtd::kNumCoef];
+                    C.cell(i, j, k, v);
+                    id = id_of(v);
+                    if (uni) uniform_id[m0] = id;
+                }
+                if (id >= fdtd::kMaxClasses)
+                    return fail(g, FDTD_ECLASSES, "more than 256 distinct coefficient classes");
+                cls[(size_t)k * g->plane + (size_t)j * g->pitch + i] = (uint8_t)id;
+            }
+    g->n_classes = (int)ids.size();
+    src_cb.clear();
+    for (const Source &s : g->srcs) {
+        double ca, cb;
+        C.e_of(s.axis, s.p, cell_of(g, s.p), &ca, &cb);
+        src_cb.push_back(cb);
+    }
+    return FDTD_OK;
+}
+
+// ---- CPML profiles (Sec. 2.2, CFS recursive convolution) ----------------
+void cpml_point(const fdtd_grid *g, double rho, float *b, float *c, float *ki)
+{
+    const fdtd_cpml &p = g->cpml;
+    const double x = rho / g->d;
+    const double sig = p.sigma_max * std::pow(x, p.order);
+    const double kap = 1.0 + (p.kappa_max - 1.0) * std::pow(x, p.order);
+    const double alp = p.alpha_max * std::pow(1.0 - x, p.alpha_order);
+    const double bb = std::exp(-(sig / kap + alp) * g->dt / kEps0);
+    const double cc = sig > 0 ? sig * (bb - 1.0) / (sig * kap + kap * kap * alp) : 0.0;
+    *b = (float)bb;
+    *c = (float)cc;
+    *ki = (float)(1.0 / kap);
+}
+
+std::vector<float> cpml_profile(const fdtd_grid *g, int n)
+{
+    using namespace fdtd;
+    std::vector<float> pr(PR_COUNT * (size_t)n, 0.f);
+    for (int i = 0; i < n; ++i) {
+        pr[PR_BE * n + i] = 1.f; pr[PR_KIE * n + i] = 1.f;
+        pr[PR_BH * n + i] = 1.f; pr[PR_KIH * n + i] = 1.f;
+    }
+    if (g->d == 0) return pr;
+    const int d = g->d;
+    for (int i = 0; i < n; ++i) {
+        // E at node i: depth d - i (low side) or i - (n - d) (high side)
+        double re = i < d ? d - i : (i > n - d ? i - (n - d) : 0.0);
+        if (re > 0) cpml_point(g, re, &pr[PR_BE * n + i], &pr[PR_CE * n + i], &pr[PR_KIE * n + i]);
+        // H at node i + 1/2
+        double rh = i < d ? d - (i + 0.5) : (i >= n - d ? (i + 0.5) - (n - d) : 0.0);
+        if (rh > 0) cpml_point(g, rh, &pr[PR_BH * n + i], &pr[PR_CH * n + i], &pr[PR_KIH * n + i]);
+    }
+    return pr;
+}
+
+fdtd::StepArgs step_args(const fdtd_grid *g, int parity)
+{
+    fdtd::StepArgs a{};
+    a.nx = g->nx; a.ny = g->ny; a.nz = g->nz;
+    a.pitch = g->pitch; a.plane = g->plane;
+    for (int c = 0; c < 3; ++c) {
+        a.Ein[c] = g->F[parity][c];
+        a.Hin[c] = g->F[parity][3 + c];
+        a.Eout[c] = g->F[1 - parity][c];
+        a.Hout[c] = g->F[1 - parity][3 + c];
+    }
+    a.cls = g->cls;
+    a.table = g->table_d;
+    a.n_classes = g->n_classes;
+    a.d = g->d;
+    for (int u = 0; u < 3; ++u) a.prof[u] = g->prof[u];
+    for (int q = 0; q < fdtd::PSI_COUNT; ++q) {
+        a.psi_in[q] = g->psi[parity][q];
+        a.psi_out[q] = g->psi[1 - parity][q];
+    }
+    a.kz = g->kz;
+    return a;
+}
+
+fdtd::EdgeArgs edge_args(const fdtd_grid *g, int parity)
+{
+    fdtd::EdgeArgs e{};
+    e.nx = g->nx; e.ny = g->ny; e.nz = g->nz;
+    e.pitch = g->pitch; e.plane = g->plane;
+    e.dx = (float)g->dx;
+    for (int c = 0; c < 3; ++c) {
+        e.E[c] = g->F[1 - parity][c];
+        e.H[c] = g->F[1 - parity][3 + c];
+    }
+    e.src = g->src_d;
+    e.n_src = (int)g->srcs.size();
+    e.samples = g->samples_d;
+    e.probes = g->probes_d;
+    e.n_probes = (int)g->probes.size();
+    e.probe_out = g->probe_out;
+    e.capacity = g->capacity;
+    e.step = g->step_d;
+    return e;
+}
+
+cudaError_t enqueue_step(fdtd_grid *g, int parity, cudaStream_t s)
+{
+    cudaError_t e = fdtd::launch_step(step_args(g, parity), s);
+    if (e != cudaSuccess) return e;
+    if (!g->srcs.empty() || !g->probes.empty()) e = fdtd::launch_edges(edge_args(g, parity), s);
+    return e;
+}
+
+int check_open(fdtd_grid *g, bool want_finalized)
+{
+    if (!g) return FDTD_EINVAL;
+    if (g->finalized != want_finalized)
+        return fail(g, FDTD_ESTATE, want_finalized ? "grid not finalized" : "grid already finalized");
+    return FDTD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fdtd_create_grid(int nx, int ny, int nz, double dx, double courant, const fdtd_cpml *cpml,
+                     void *cuda_stream, fdtd_grid **out)
+{
+    if (!out) return FDTD_EINVAL;
+    *out = nullptr;
+    if (nx < 2 || ny < 2 || nz < 2 || !(dx > 0) || !std::isfinite(dx)) return FDTD_EINVAL;
+    if (!(courant > 0) || courant > 1.0) return FDTD_ECOURANT;
+    int d = cpml ? cpml->cells : 0;
+    if (d < 0) return FDTD_EINVAL;
+    if (d > 0 && (nx < 2 * d + 2 || ny < 2 * d + 2 || nz < 2 * d + 2)) return FDTD_EINVAL;
+    if (d > 0 && (cpml->kappa_max < 1.0 || cpml->alpha_max < 0 || cpml->order < 0)) return FDTD_EINVAL;
+    fdtd_grid *g = new (std::nothrow) fdtd_grid();
+    if (!g) return FDTD_ENOMEM;
+    g->nx = nx; g->ny = ny; g->nz = nz; g->dx = dx; g->courant = courant;
+    g->dt = courant * dx / (kC0 * std::sqrt(3.0));
+    g->d = d;
+    if (d > 0) {
+        g->cpml = *cpml;
+        if (g->cpml.sigma_max <= 0)
+            g->cpml.sigma_max = 0.8 * (g->cpml.order + 1.0) / (std::sqrt(kMu0 / kEps0) * dx);
+    }
+    g->stream = (cudaStream_t)cuda_stream;
+    g->pitch = (nx + 3) / 4 * 4;
+    g->plane = (long long)g->pitch * ny;
+    g->mat.assign((size_t)nx * ny * nz, 0);
+    g->table.push_back(fdtd_material{1.0, 0.0, 1.0});
+    *out = g;
+    return FDTD_OK;
+}
+
+int fdtd_set_materials(fdtd_grid *g, const uint8_t *cell_material, const fdtd_material *table,
+                       int n_materials)
+{
+    if (int rc = check_open(g, false)) return rc;
+    if (!cell_material || !table || n_materials < 1 || n_materials > 256)
+        return fail(g, FDTD_EINVAL, "bad material arguments");
+    for (int m = 0; m < n_materials; ++m)
+        if (!(table[m].eps_r > 0) || !(table[m].sigma >= 0) || !(table[m].mu_r > 0))
+            return fail(g, FDTD_EINVAL, "material " + std::to_string(m) + " out of range");
+    const size_t nc = g->mat.size();
+    for (size_t c = 0; c < nc; ++c)
+        if (cell_material[c] >= n_materials) return fail(g, FDTD_EINVAL, "material index out of range");
+    std::memcpy(g->mat.data(), cell_material, nc);
+    g->table.assign(table, table + n_materials);
+    return FDTD_OK;
+}
+
+int fdtd_add_wire(fdtd_grid *g, int i0, int j0, int k0, int i1, int j1, int k1, double radius,
+                  int *wire_id)
+{
+    if (int rc = check_open(g, false)) return rc;
+    Wire w{};
+    const int lo[3] = {i0, j0, k0}, hi[3] = {i1, j1, k1}, n[3] = {g->nx, g->ny, g->nz};
+    int axis = -1;
+    for (int u = 0; u < 3; ++u)
+        if (hi[u] != lo[u]) {
+            if (axis >= 0 || hi[u] < lo[u]) return fail(g, FDTD_EINVAL, "wire must run along +x, +y or +z");
+            axis = u;
+        }
+    if (axis < 0) return fail(g, FDTD_EINVAL, "wire has zero length");
+    for (int u = 0; u < 3; ++u) {
+        if (u == axis) { if (lo[u] < 0 || hi[u] > n[u]) return fail(g, FDTD_EINVAL, "wire outside the grid"); }
+        else if (lo[u] < 1 || lo[u] > n[u] - 1) return fail(g, FDTD_EINVAL, "wire must lie inside the walls");
+    }
+    if (!(radius > 0) || radius > kR0 * g->dx * (1.0 + 1e-12))
+        return fail(g, FDTD_EINVAL, "wire radius must be in (0, 0.23 dx]");
+    w.axis = axis;
+    std::memcpy(w.p, lo, sizeof w.p);
+    w.n = hi[axis] - lo[axis];
+    w.radius = radius;
+    g->wires.push_back(w);
+    if (wire_id) *wire_id = (int)g->wires.size() - 1;
+    return FDTD_OK;
+}
+
+int fdtd_add_source(fdtd_grid *g, int i, int j, int k, int axis, double r_internal,
+                    const double *current, int n_samples, int *source_id)
+{
+    if (int rc = check_open(g, false)) return rc;
+    if (axis < 0 || axis > 2 || n_samples < 0 || (n_samples > 0 && !current))
+        return fail(g, FDTD_EINVAL, "bad source arguments");
+    if (r_internal != 0.0) return fail(g, FDTD_EINVAL, "only ideal current sources (r_internal = 0)");
+    Source s;
+    s.axis = axis;
+    s.p[0] = i; s.p[1] = j; s.p[2] = k;
+    if (!e_updated(g, axis, s.p)) return fail(g, FDTD_EINVAL, "source edge on a wall or outside the grid");
+    s.cur.resize(n_samples);
+    for (int t = 0; t < n_samples; ++t) s.cur[t] = (float)current[t];
+    g->srcs.push_back(std::move(s));
+    if (source_id) *source_id = (int)g->srcs.size() - 1;
+    return FDTD_OK;
+}
+
+int fdtd_add_probe(fdtd_grid *g, int kind, int i, int j, int k, int axis, int n_edges, int *probe_id)
+{
+    if (int rc = check_open(g, false)) return rc;
+    if (kind < 0 || kind > 3 || axis < 0 || axis > 2) return fail(g, FDTD_EINVAL, "bad probe kind or axis");
+    const int p[3] = {i, j, k}, n[3] = {g->nx, g->ny, g->nz};
+    for (int u = 0; u < 3; ++u)
+        if (p[u] < 0 || p[u] >= n[u]) return fail(g, FDTD_EINVAL, "probe outside the grid");
+    if (kind == FDTD_PROBE_V) {
+        if (n_edges < 1 || p[axis] + n_edges > n[axis]) return fail(g, FDTD_EINVAL, "voltage path outside the grid");
+    } else {
+        n_edges = 1;
+    }
+    if (kind == FDTD_PROBE_I)
+        for (int u = 0; u < 3; ++u)
+            if (u != axis && p[u] < 1) return fail(g, FDTD_EINVAL, "current loop needs transverse index >= 1");
+    g->probes.push_back(fdtd::ProbeDesc{kind, axis, i, j, k, n_edges});
+    if (probe_id) *probe_id = (int)g->probes.size() - 1;
+    return FDTD_OK;
+}
+
+int fdtd_arena_bytes(const fdtd_grid *g, int probe_capacity, size_t *bytes)
+{
+    if (!g || !bytes || probe_capacity < 0) return FDTD_EINVAL;
+    *bytes = make_plan(g, probe_capacity).total;
+    return FDTD_OK;
+}
+
+int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_bytes)
+{
+    if (int rc = check_open(g, false)) return rc;
+    if (probe_capacity < 0) return fail(g, FDTD_EINVAL, "negative probe capacity");
+    std::vector<uint8_t> cls;
+    std::vector<float> table;
+    std::vector<double> src_cb;
+    if (int rc = build_classes(g, cls, table, src_cb)) return rc;
+
+    const Plan p = make_plan(g, probe_capacity);
+    if (arena) {
+        if (arena_bytes < p.total) return fail(g, FDTD_ENOMEM, "arena smaller than fdtd_arena_bytes()");
+        if ((uintptr_t)arena % 256) return fail(g, FDTD_EINVAL, "arena must be 256-byte aligned");
+        g->arena = arena;
+        g->own_arena = false;
+    } else {
+        cudaError_t e = cudaMalloc(&g->arena, p.total);
+        if (e != cudaSuccess) { g->arena = nullptr; return fail(g, FDTD_ENOMEM, "cudaMalloc of the arena failed"); }
+        g->own_arena = true;
+    }
+    g->arena_bytes = p.total;
+    char *base = (char *)g->arena;
+    const size_t cells = (size_t)g->plane * g->nz;
+    for (int b = 0; b < 2; ++b)
+        for (int c = 0; c < 6; ++c) g->F[b][c] = (float *)(base + p.field) + (size_t)(b * 6 + c) * cells;
+    g->cls = (uint8_t *)(base + p.cls);
+    g->table_d = (float *)(base + p.table);
+    for (int u = 0; u < 3; ++u) g->prof[u] = (float *)(base + p.prof[u]);
+    for (int q = 0; q < fdtd::PSI_COUNT; ++q) {
+        const size_t n = psi_elems(g, q);
+        g->psi[0][q] = n ? (float *)(base + p.psi[q]) : nullptr;
+        g->psi[1][q] = n ? (float *)(base + p.psi[q]) + n : nullptr;
+    }
+    g->src_d = (fdtd::SourceDesc *)(base + p.src);
+    g->samples_d = (float *)(base + p.samples);
+    g->probes_d = (fdtd::ProbeDesc *)(base + p.probes);
+    g->probe_out = (float *)(base + p.out);
+    g->step_d = (long long *)(base + p.step);
+    g->capacity = probe_capacity;
+
+
+    cudaStream_t s = g->stream;
+    cudaError_t e = cudaMemsetAsync(g->arena, 0, p.total, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->cls, cls.data(), cls.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->table_d, table.data(), table.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+    const int n[3] = {g->nx, g->ny, g->nz};
+    for (int u = 0; u < 3 && e == cudaSuccess; ++u) {
+        std::vector<float> pr = cpml_profile(g, n[u]);
+        e = cudaMemcpyAsync(g->prof[u], pr.data(), pr.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // pr goes out of scope
+    }
+    std::vector<fdtd::SourceDesc> sd;
+    std::vector<float> samples;
+    for (size_t q = 0; q < g->srcs.size(); ++q) {
+        const Source &src = g->srcs[q];
+        fdtd::SourceDesc d{};
+        d.comp = src.axis;
+        d.idx = (long long)src.p[2] * g->plane + (long long)src.p[1] * g->pitch + src.p[0];
+        d.coef = (float)(-src_cb[q] / g->dx);
+        d.n_samples = (int)src.cur.size();
+        d.sample_off = (long long)samples.size();
+        samples.insert(samples.end(), src.cur.begin(), src.cur.end());
+        sd.push_back(d);
+    }
+    if (e == cudaSuccess && !sd.empty())
+        e = cudaMemcpyAsync(g->src_d, sd.data(), sd.size() * sizeof(sd[0]), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !samples.empty())
+        e = cudaMemcpyAsync(g->samples_d, samples.data(), samples.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !g->probes.empty())
+        e = cudaMemcpyAsync(g->probes_d, g->probes.data(), g->probes.size() * sizeof(fdtd::ProbeDesc),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(g, e, "upload");
+    // z chunking: enough CTAs to fill 152 SMs several times over
+    const int cols = ((g->nx + fdtd::step_tile_x() - 1) / fdtd::step_tile_x()) *
+                     ((g->ny + fdtd::step_tile_y() - 1) / fdtd::step_tile_y());
+    int chunks = (4 * 152 * 2 + cols - 1) / cols;
+    chunks = std::max(1, std::min(chunks, g->nz / 8 > 0 ? g->nz / 8 : 1));
+    g->kz = (g->nz + chunks - 1) / chunks;
+    g->finalized = true;
+    return FDTD_OK;
+}
+
+int fdtd_step(fdtd_grid *g, int n)
+{
+    if (int rc = check_open(g, true)) return rc;
+    if (n < 0) return fail(g, FDTD_EINVAL, "negative step count");
+    while (n > 0) {
+        if (g->parity == 0 && n >= kGraphSteps) {
+            if (!g->graph) {
+                cudaError_t e = cudaSuccess;
+                if (!g->cap_stream) e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
+                cudaGraph_t graph = nullptr;
+                if (e == cudaSuccess) e = cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    for (int t = 0; t < kGraphSteps && e == cudaSuccess; ++t) e = enqueue_step(g, t & 1, g->cap_stream);
+                    cudaError_t e2 = cudaStreamEndCapture(g->cap_stream, &graph);
+                    if (e == cudaSuccess) e = e2;
+                }
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&g->graph, graph, 0);
+                if (graph) cudaGraphDestroy(graph);
+                if (e != cudaSuccess) { g->graph = nullptr; return cuda_fail(g, e, "graph capture"); }
+            }
+            cudaError_t e = cudaGraphLaunch(g->graph, g->stream);
+            if (e != cudaSuccess) return cuda_fail(g, e, "graph launch");
+            n -= kGraphSteps;
+            g->step += kGraphSteps;
+        } else {
+            cudaError_t e = enqueue_step(g, g->parity, g->stream);
+            if (e != cudaSuccess) return cuda_fail(g, e, "step launch");
+            g->parity ^= 1;
+            n -= 1;
+            g->step += 1;
+        }
+    }
+    return FDTD_OK;
+}
+
+int fdtd_synchronize(fdtd_grid *g)
+{
+    if (!g) return FDTD_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return cuda_fail(g, e, "synchronize");
+    return FDTD_OK;
+}
+
+int fdtd_read_probes(fdtd_grid *g, int probe_id, int first_step, int count, float *host_out)
+{
+    if (int rc = check_open(g, true)) return rc;
+    if (probe_id < 0 || probe_id >= (int)g->probes.size() || first_step < 0 || count < 0 ||
+        (long long)first_step + count > g->capacity || (count > 0 && !host_out))
+        return fail(g, FDTD_EINVAL, "probe range outside the recorded window");
+    if (int rc = fdtd_synchronize(g)) return rc;
+    if (count == 0) return FDTD_OK;
+    cudaError_t e = cudaMemcpy(host_out, g->probe_out + (size_t)probe_id * g->capacity + first_step,
+                               (size_t)count * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(g, e, "probe copy");
+    return FDTD_OK;
+}
+
+int fdtd_get_field(fdtd_grid *g, int component, float *host_out)
+{
+    if (int rc = check_open(g, true)) return rc;
+    if (component < 0 || component > 5 || !host_out) return fail(g, FDTD_EINVAL, "bad component");
+    if (int rc = fdtd_synchronize(g)) return rc;
+    cudaError_t e = cudaMemcpy2D(host_out, (size_t)g->nx * sizeof(float), g->F[g->parity][component],
+                                 (size_t)g->pitch * sizeof(float), (size_t)g->nx * sizeof(float),
+                                 (size_t)g->ny * g->nz, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(g, e, "field copy");
+    return FDTD_OK;
+}
+
+int fdtd_set_field(fdtd_grid *g, int component, const float *host_in)
+{
+    if (int rc = check_open(g, true)) return rc;
+    if (component < 0 || component > 5 || !host_in) return fail(g, FDTD_EINVAL, "bad component");
+    if (int rc = fdtd_synchronize(g)) return rc;
+    cudaError_t e = cudaMemcpy2D(g->F[g->parity][component], (size_t)g->pitch * sizeof(float), host_in,
+                                 (size_t)g->nx * sizeof(float), (size_t)g->nx * sizeof(float),
+                                 (size_t)g->ny * g->nz, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(g, e, "field copy");
+    return FDTD_OK;
+}
+
+int fdtd_field_device(fdtd_grid *g, int component, void **dptr, int *row_pitch, size_t *plane_pitch)
+{
+    if (int rc = check_open(g, true)) return rc;
+    if (component < 0 || component > 5 || !dptr) return fail(g, FDTD_EINVAL, "bad component");
+    *dptr = g->F[g->parity][component];
+    if (row_pitch) *row_pitch = g->pitch;
+    if (plane_pitch) *plane_pitch = (size_t)g->plane;
+    return FDTD_OK;
+}
+
+double fdtd_get_dt(const fdtd_grid *g) { return g ? g->dt : 0.0; }
+long fdtd_get_step(const fdtd_grid *g) { return g ? g->step : -1; }
+int fdtd_num_classes(const fdtd_grid *g) { return g ? g->n_classes : -1; }
+const char *fdtd_last_error(const fdtd_grid *g) { return g ? g->err.c_str() : "null grid"; }
+
+void fdtd_destroy(fdtd_grid *g)
+{
+    if (!g) return;
+    if (g->finalized) cudaStreamSynchronize(g->stream);
+    if (g->graph) cudaGraphExecDestroy(g->graph);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    if (g->own_arena && g->arena) cudaFree(g->arena);
+    delete g;
+}
+
+}  // extern "C"

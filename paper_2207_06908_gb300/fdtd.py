@@ -1,0 +1,188 @@
+"""Python face of the C ABI (include/fdtd.h): one ``Grid`` per simulation
+domain.  Argument marshalling only -- every update runs in the CUDA library.
+
+PyTorch supplies the CUDA stream and, by default, the device memory (one
+uint8 tensor that the library carves into fields, classes, CPML state,
+sources and probe buffers).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import CpmlParams, FdtdError, Material, check
+
+EX, EY, EZ, HX, HY, HZ = range(6)
+PROBE_V, PROBE_I, PROBE_E, PROBE_H = 0, 1, 2, 3
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Grid:
+    """A uniform cubic Yee grid of nx*ny*nz cells (Sec. 2.1 of the paper).
+
+    Host arrays use the cell-owned layout of shape (nz, ny, nx): entry
+    [k, j, i] is the component owned by cell (i, j, k).
+    """
+
+    def __init__(self, nx, ny, nz, dx, courant=0.99, cpml=None, stream=None):
+        self._lib = _lib.load()
+        self._h = None
+        self.shape = (nz, ny, nx)
+        self.nx, self.ny, self.nz, self.dx = nx, ny, nz, dx
+        self._arena = None
+        self.stream = stream
+        cp = None
+        if cpml:
+            p = dict(cells=cpml) if isinstance(cpml, int) else dict(cpml)
+            cp = CpmlParams(int(p["cells"]), float(p.get("order", 3.0)), float(p.get("kappa_max", 1.0)),
+                            float(p.get("alpha_max", 0.0)), float(p.get("alpha_order", 1.0)),
+                            float(p.get("sigma_max", 0.0)))
+        h = ctypes.c_void_p()
+        rc = self._lib.fdtd_create_grid(int(nx), int(ny), int(nz), float(dx), float(courant),
+                                        ctypes.byref(cp) if cp else None, _stream_ptr(stream),
+                                        ctypes.byref(h))
+        check(self._lib, None, rc, "fdtd_create_grid")
+        self._h = h
+        self.probe_capacity = 0
+
+    # -- lifetime --------------------------------------------------------
+    def close(self):
+        if self._h:
+            self._lib.fdtd_destroy(self._h)
+            self._h = None
+        self._arena = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- description -----------------------------------------------------
+    def set_materials(self, cell_material, table):
+        cm = np.ascontiguousarray(cell_material, dtype=np.uint8)
+        if cm.shape != self.shape:
+            raise ValueError(f"material map shape {cm.shape} != {self.shape}")
+        mats = (Material * len(table))(*[Material(float(e), float(s), float(m)) for e, s, m in table])
+        check(self._lib, self._h, self._lib.fdtd_set_materials(
+            self._h, cm.ctypes.data_as(ctypes.c_void_p), mats, len(table)), "set_materials")
+
+    def add_wire(self, p0, p1, radius):
+        wid = ctypes.c_int()
+        check(self._lib, self._h, self._lib.fdtd_add_wire(self._h, *map(int, p0), *map(int, p1),
+                                                          float(radius), ctypes.byref(wid)), "add_wire")
+        return wid.value
+
+    def add_source(self, node, axis, current, r_internal=0.0):
+        cur = np.ascontiguousarray(current, dtype=np.float64)
+        sid = ctypes.c_int()
+        check(self._lib, self._h, self._lib.fdtd_add_source(
+            self._h, *map(int, node), int(axis), float(r_internal), cur.ctypes.data_as(ctypes.c_void_p),
+            len(cur), ctypes.byref(sid)), "add_source")
+        return sid.value
+
+    def add_probe(self, kind, node, axis, n_edges=1):
+        pid = ctypes.c_int()
+        check(self._lib, self._h, self._lib.fdtd_add_probe(self._h, int(kind), *map(int, node), int(axis),
+                                                           int(n_edges), ctypes.byref(pid)), "add_probe")
+        return pid.value
+
+    def arena_bytes(self, probe_capacity):
+        b = ctypes.c_size_t()
+        check(self._lib, self._h, self._lib.fdtd_arena_bytes(self._h, int(probe_capacity), ctypes.byref(b)),
+              "arena_bytes")
+        return b.value
+
+    def finalize(self, probe_capacity=0, torch_arena=True):
+        """Build classes and upload.  With torch_arena the device memory is
+        one torch uint8 tensor owned by this object."""
+        ptr, nbytes = None, 0
+        if torch_arena:
+            import torch
+            nbytes = self.arena_bytes(probe_capacity)
+            self._arena = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+            base = self._arena.data_ptr()
+            ptr = ctypes.c_void_p((base + 255) // 256 * 256)
+        check(self._lib, self._h, self._lib.fdtd_finalize(self._h, int(probe_capacity), ptr, nbytes),
+              "finalize")
+        self.probe_capacity = int(probe_capacity)
+
+    # -- running ---------------------------------------------------------
+    def step(self, n=1):
+        check(self._lib, self._h, self._lib.fdtd_step(self._h, int(n)), "step")
+
+    def synchronize(self):
+        check(self._lib, self._h, self._lib.fdtd_synchronize(self._h), "synchronize")
+
+    def read_probe(self, probe_id, first=0, count=None):
+        if count is None:
+            count = self.probe_capacity - first
+        out = np.empty(max(count, 0), dtype=np.float32)
+        check(self._lib, self._h, self._lib.fdtd_read_probes(
+            self._h, int(probe_id), int(first), int(count), out.ctypes.data_as(ctypes.c_void_p)), "read_probes")
+        return out
+
+    def get_field(self, comp):
+        out = np.empty(self.shape, dtype=np.float32)
+        check(self._lib, self._h, self._lib.fdtd_get_field(self._h, int(comp),
+                                                           out.ctypes.data_as(ctypes.c_void_p)), "get_field")
+        return out
+
+    def set_field(self, comp, values):
+        v = np.ascontiguousarray(values, dtype=np.float32)
+        if v.shape != self.shape:
+            raise ValueError(f"field shape {v.shape} != {self.shape}")
+        check(self._lib, self._h, self._lib.fdtd_set_field(self._h, int(comp), v.ctypes.data_as(ctypes.c_void_p)),
+              "set_field")
+
+    def field_device(self, comp):
+        p = ctypes.c_void_p()
+        rp = ctypes.c_int()
+        pp = ctypes.c_size_t()
+        check(self._lib, self._h, self._lib.fdtd_field_device(self._h, int(comp), ctypes.byref(p),
+                                                              ctypes.byref(rp), ctypes.byref(pp)), "field_device")
+        return p.value, rp.value, pp.value
+
+    @property
+    def dt(self):
+        return self._lib.fdtd_get_dt(self._h)
+
+    @property
+    def step_count(self):
+        return self._lib.fdtd_get_step(self._h)
+
+    @property
+    def num_classes(self):
+        return self._lib.fdtd_num_classes(self._h)
+
+
+def from_scenario(sc, stream=None, probe_capacity=None, torch_arena=True):
+    """Build and finalize a Grid from a workloads.Scenario."""
+    g = Grid(*sc.n, sc.dx, courant=sc.courant, cpml=sc.cpml or None, stream=stream)
+    g.set_materials(sc.cell_material, sc.materials)
+    for p0, p1, r in sc.wires:
+        g.add_wire(p0, p1, r)
+    for node, axis, cur in sc.sources:
+        g.add_source(node, axis, cur)
+    for kind, node, axis, ne in sc.probes:
+        g.add_probe(kind, node, axis, ne)
+    g.finalize(sc.n_steps if probe_capacity is None else probe_capacity, torch_arena=torch_arena)
+    return g
+
+
+__all__ = ["Grid", "FdtdError", "from_scenario", "EX", "EY", "EZ", "HX", "HY", "HZ",
+           "PROBE_V", "PROBE_I", "PROBE_E", "PROBE_H"]

@@ -1,0 +1,282 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle and the bench.
+
+This module describes problems only: grid size, cell size, the material map
+painted from axis-aligned blocks (the paper's "block" command, later blocks
+winning), wires, source waveforms sampled in FP64 at t_{n+1/2}, probe
+placements and seeded random fields.  It holds none of the update
+arithmetic, coefficient rules or probe formulas of the method.
+
+Configurations (the paper publishes no dataset; these synthetic problems
+have the shapes of its grounding / lightning workloads):
+  config1: 48^3 PEC box, lossy half-space, one Ez source, 3 point probes
+  config2: 256^3, 10-cell CPML, air over soil, 30 m vertical thin wire fed
+           at its base by a 1.2/50 us double exponential (10 kA)
+  config3: 512x512x384, 12-cell CPML, two-layer soil, buried 8x8 thin-wire
+           mesh with a down-conductor and the current / voltage leads of the
+           paper's ground-potential-rise model
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+C0 = 299792458.0
+PROBE_V, PROBE_I, PROBE_E, PROBE_H = 0, 1, 2, 3
+
+
+@dataclasses.dataclass
+class Scenario:
+    name: str
+    n: tuple                      # (nx, ny, nz) cells
+    dx: float
+    courant: float
+    cpml: int                     # CPML cells (0 = PEC box)
+    cell_material: np.ndarray     # (nz, ny, nx) uint8
+    materials: list               # [(eps_r, sigma, mu_r)]
+    wires: list = dataclasses.field(default_factory=list)     # [(p0, p1, radius)]
+    sources: list = dataclasses.field(default_factory=list)   # [(node, axis, current[n])]
+    probes: list = dataclasses.field(default_factory=list)    # [(kind, node, axis, n_edges)]
+    n_steps: int = 0
+    fields: list | None = None    # optional initial [Ex,Ey,Ez,Hx,Hy,Hz] (nz,ny,nx) float32
+
+    @property
+    def cells(self) -> int:
+        return self.n[0] * self.n[1] * self.n[2]
+
+
+def time_step(dx: float, courant: float) -> float:
+    """The configured step: the fraction `courant` of the cubic-grid limit."""
+    return courant * dx / (C0 * math.sqrt(3.0))
+
+
+def sample_times(n_steps: int, dx: float, courant: float) -> np.ndarray:
+    """Source sample instants t_{n+1/2}, n = 0 .. n_steps-1."""
+    return (np.arange(n_steps, dtype=np.float64) + 0.5) * time_step(dx, courant)
+
+
+# ---- source waveforms (inputs; FP64) ------------------------------------
+def gaussian_derivative(t, tau, t0, peak=1.0):
+    """-sqrt(e) ((t-t0)/tau) exp(-(t-t0)^2 / (2 tau^2)), extreme value +-peak."""
+    x = (t - t0) / tau
+    return -peak * math.sqrt(math.e) * x * np.exp(-0.5 * x * x)
+
+
+def double_exponential_params(t_front=1.2e-6, t_half=50e-6):
+    """alpha, beta, k of I(t) = I0 k (exp(-alpha t) - exp(-beta t)) with a
+    front time 1.25 (t90 - t10) = t_front and the tail at half the peak at
+    t_half; k normalises the peak to 1.  Solved by nested bisection."""
+    def shape(alpha, beta):
+        tp = math.log(beta / alpha) / (beta - alpha)
+        peak = math.exp(-alpha * tp) - math.exp(-beta * tp)
+        return tp, peak
+
+    def crossing(alpha, beta, level, lo, hi):
+        f = lambda t: (math.exp(-alpha * t) - math.exp(-beta * t)) - level
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            if (f(lo) < 0) == (f(mid) < 0):
+                lo = mid
+            else:
+                hi = mid
+        return 0.5 * (lo + hi)
+
+    def metrics(alpha, beta):
+        tp, peak = shape(alpha, beta)
+        t10 = crossing(alpha, beta, 0.1 * peak, 0.0, tp)
+        t90 = crossing(alpha, beta, 0.9 * peak, 0.0, tp)
+        th = crossing(alpha, beta, 0.5 * peak, tp, 50 * t_half + 10 * tp)
+        # the tail crossing is decreasing: bisection above handles sign flips
+        return 1.25 * (t90 - t10), th, peak
+
+    alpha = math.log(2.0) / t_half
+    beta = 2.5 / t_front
+    for _ in range(60):
+        # beta from the front time at fixed alpha (front shrinks as beta grows)
+        lo, hi = beta / 8, beta * 8
+        for _ in range(80):
+            mid = math.sqrt(lo * hi)
+            if metrics(alpha, mid)[0] > t_front:
+                lo = mid
+            else:
+                hi = mid
+        beta = math.sqrt(lo * hi)
+        # alpha from the half-value time at fixed beta
+        lo, hi = alpha / 4, alpha * 4
+        for _ in range(80):
+            mid = math.sqrt(lo * hi)
+            if metrics(mid, beta)[1] > t_half:
+                lo = mid
+            else:
+                hi = mid
+        alpha = math.sqrt(lo * hi)
+    _, _, peak = metrics(alpha, beta)
+    return alpha, beta, 1.0 / peak
+
+
+def double_exponential(t, i0, alpha, beta, k):
+    return i0 * k * (np.exp(-alpha * t) - np.exp(-beta * t))
+
+
+def ramp(t, i0, t_rise):
+    """linear rise 0 -> i0 over t_rise, then flat"""
+    return i0 * np.clip(t / t_rise, 0.0, 1.0)
+
+
+# ---- material maps --------------------------------------------------------
+def paint_blocks(n, blocks, background=0):
+    """Material map from axis-aligned blocks of cells [(lo, hi, id)] with
+    lo/hi = (i, j, k) half-open; later blocks override earlier ones."""
+    nx, ny, nz = n
+    cm = np.full((nz, ny, nx), background, dtype=np.uint8)
+    for lo, hi, mid in blocks:
+        cm[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] = mid
+    return cm
+
+
+def zero_walls(fields, n):
+    """Zero tangential E on the low walls and normal H on the low walls, the
+    entries a PEC box keeps at zero."""
+    nx, ny, nz = n
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    masks = [(j == 0) | (k == 0), (i == 0) | (k == 0), (i == 0) | (j == 0), i == 0, j == 0, k == 0]
+    for f, m in zip(fields, masks):
+        f[m] = 0.0
+    return fields
+
+
+# ---- the configurations -----------------------------------------------------
+def config1(n_steps=500):
+    """48^3, dx = 0.1 m, PEC walls, soil (eps_r 10, sigma 0.01 S/m) in the
+    lower half, Gaussian-derivative current (tau = 20 dt) on one Ez edge,
+    three point E probes."""
+    n = (48, 48, 48)
+    dx, S = 0.1, 0.99
+    cm = paint_blocks(n, [((0, 0, 0), (48, 48, 24), 1)])
+    mats = [(1.0, 0.0, 1.0), (10.0, 0.01, 1.0)]
+    dt = time_step(dx, S)
+    tau = 20 * dt
+    cur = gaussian_derivative(sample_times(n_steps, dx, S), tau, 6 * tau)
+    return Scenario("config1_48cube_pec", n, dx, S, 0, cm, mats,
+                    sources=[((24, 24, 28), 2, cur)],
+                    probes=[(PROBE_E, (30, 24, 28), 2, 1), (PROBE_E, (24, 30, 20), 2, 1),
+                            (PROBE_E, (12, 36, 30), 0, 1)],
+                    n_steps=n_steps)
+
+
+def config2(n_steps=4000, n=256):
+    """256^3, dx = 0.5 m, 10-cell CPML; soil (eps_r 15, sigma 0.002) below
+    node k = n/2; vertical thin wire r = 5 mm, 30 m, base-fed by a 1.2/50 us
+    double exponential of 10 kA peak; probes: source-gap voltage and the wire
+    current at five heights.  `n` < 256 gives the same layout scaled down
+    (wire length capped to fit) for short parity runs."""
+    dx, S = 0.5, 0.99
+    nn = (n, n, n)
+    c = n // 2
+    cm = paint_blocks(nn, [((0, 0, 0), (n, n, c), 1)])
+    mats = [(1.0, 0.0, 1.0), (15.0, 0.002, 1.0)]
+    top = min(c + 61, n - 10 - 2)
+    alpha, beta, k = double_exponential_params(1.2e-6, 50e-6)
+    cur = double_exponential(sample_times(n_steps, dx, S), 10e3, alpha, beta, k)
+    heights = [h for h in (c + 1, c + 16, c + 31, c + 46, c + 60) if h < top]
+    probes = [(PROBE_V, (c, c, c), 2, 1)] + [(PROBE_I, (c, c, h), 2, 1) for h in heights]
+    return Scenario(f"config2_{n}cube_cpml10_wire", nn, dx, S, 10, cm, mats,
+                    wires=[((c, c, c + 1), (c, c, top), 0.005)],
+                    sources=[((c, c, c), 2, cur)],
+                    probes=probes, n_steps=n_steps)
+
+
+def config3(n_steps=8000, scale=1):
+    """512x512x384, dx = 0.25 m, 12-cell CPML; air above node k = 256,
+    layer 1 (eps_r 10, sigma 0.01) for cells 248..255, layer 2 (eps_r 30,
+    sigma 1e-3) below; buried 8x8 thin-wire mesh (10 m spacing, r = 6 mm,
+    0.5 m deep) with a 2.5 m down-conductor at (236, 236); current lead
+    along +x with a one-cell source gap, voltage lead along +y with a
+    one-cell probe gap, both running into the CPML (the layout of the
+    paper's ground-potential-rise model file); 1 kA ramp, 0.5 us rise."""
+    dx, S = 0.25, 0.99
+    nx, ny, nz = 512 // scale, 512 // scale, 384 // scale
+    d = max(4, 12 // scale)
+    surf = 256 // scale
+    cm = paint_blocks((nx, ny, nz), [((0, 0, 0), (nx, ny, surf), 2),
+                                     ((0, 0, surf - 8 // scale), (nx, ny, surf), 1)])
+    mats = [(1.0, 0.0, 1.0), (10.0, 0.01, 1.0), (30.0, 1e-3, 1.0)]
+    a = 0.006
+    kw = surf - max(1, 2 // scale)
+    lines = [116 // scale + (40 // scale) * q for q in range(8)]
+    wires = []
+    for y in lines:
+        wires.append(((lines[0], y, kw), (lines[-1], y, kw), a))
+    for x in lines:
+        wires.append(((x, lines[0], kw), (x, lines[-1], kw), a))
+    r = 236 // scale
+    top = kw + max(2, 10 // scale)
+    wires.append(((r, r, kw), (r, r, top), a))
+    wires.append(((r, r, top), (r + 2, r, top), 0.003))            # stub to the source gap
+    wires.append(((r + 3, r, top), (nx - d, r, top), 0.003))       # current lead
+    wires.append(((r, r, top), (r, r + 2, top), 0.003))            # stub to the probe gap
+    wires.append(((r, r + 3, top), (r, ny - d, top), 0.003))       # voltage lead
+    cur = ramp(sample_times(n_steps, dx, S), 1e3, 0.5e-6)
+    return Scenario(f"config3_{nx}x{ny}x{nz}_cpml{d}_mesh", (nx, ny, nz), dx, S, d, cm, mats,
+                    wires=wires, sources=[((r + 2, r, top), 0, cur)],
+                    probes=[(PROBE_V, (r, r + 2, top), 1, 1), (PROBE_I, (r + 2, r, top), 0, 1)],
+                    n_steps=n_steps)
+
+
+# ---- random problems for parity tests ---------------------------------------
+def random_fields(rng, n, scale_h=1.0 / 377.0):
+    nx, ny, nz = n
+    f = [rng.standard_normal((nz, ny, nx)).astype(np.float64) for _ in range(6)]
+    for c in range(3, 6):
+        f[c] *= scale_h
+    return zero_walls(f, n)
+
+
+def random_scenario(seed, n=(17, 17, 17), dx=0.1, courant=0.99, cpml=0, n_blocks=5, n_mat=4,
+                    n_wires=2, n_sources=2, n_probes=8, n_steps=40, fields=True):
+    """Random blocky media, thin wires, sources, probes and (optionally)
+    random initial fields, all from one seed."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = n
+    blocks = []
+    for _ in range(n_blocks):
+        lo = [int(rng.integers(0, m)) for m in n]
+        hi = [int(rng.integers(l + 1, m + 1)) for l, m in zip(lo, n)]
+        blocks.append((tuple(lo), tuple(hi), int(rng.integers(0, n_mat))))
+    cm = paint_blocks(n, blocks)
+    mats = [(float(rng.uniform(1.0, 20.0)), float(10 ** rng.uniform(-4, 0)), float(rng.uniform(1.0, 2.0)))
+            for _ in range(n_mat)]
+    lo_in = cpml + 1
+    wires = []
+    for _ in range(n_wires):
+        axis = int(rng.integers(0, 3))
+        p0 = [int(rng.integers(lo_in, m - lo_in)) for m in n]
+        length = int(rng.integers(1, max(2, n[axis] - lo_in - p0[axis])))
+        p1 = list(p0)
+        p1[axis] = min(p0[axis] + length, n[axis] - lo_in)
+        if p1[axis] <= p0[axis]:
+            continue
+        wires.append((tuple(p0), tuple(p1), float(dx * rng.uniform(0.005, 0.2))))
+    t = np.arange(n_steps)
+    sources = []
+    for _ in range(n_sources):
+        axis = int(rng.integers(0, 3))
+        node = [int(rng.integers(lo_in, m - lo_in)) for m in n]
+        w = rng.uniform(0.05, 0.4)
+        cur = rng.uniform(0.5, 2.0) * np.sin(w * t + rng.uniform(0, 6)) * np.exp(-t / rng.uniform(10, 40))
+        sources.append((tuple(node), axis, cur))
+    probes = []
+    for q in range(n_probes):
+        kind = q % 4
+        axis = int(rng.integers(0, 3))
+        node = [int(rng.integers(1, m - 1)) for m in n]
+        ne = 1
+        if kind == PROBE_V:
+            ne = int(rng.integers(1, max(2, n[axis] - node[axis])))
+        probes.append((kind, tuple(node), axis, ne))
+    sc = Scenario(f"random{seed}_{nx}x{ny}x{nz}", n, dx, courant, cpml, cm, mats, wires, sources, probes,
+                  n_steps)
+    if fields:
+        sc.fields = random_fields(rng, n)
+    return sc

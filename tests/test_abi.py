@@ -1,0 +1,93 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports
+every entry point that include/fdtd.h declares (CPU; no compute calls)."""
+import ctypes
+import os
+import re
+
+from paper_2207_06908_gb300 import _build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(fdtd_\w+)\s*\(", src))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    path = _build.build()
+    lib = ctypes.CDLL(path)
+    names = declared_symbols()
+    assert len(names) >= 18
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_oracle_builds():
+    from oracle import oracle
+    assert os.path.exists(oracle.build())
+
+
+def _lib():
+    from paper_2207_06908_gb300 import _lib as L
+    _build.build()
+    return L.load()
+
+
+def _grid(lib, n=(8, 8, 8), dx=0.1, S=0.99, cpml=None):
+    h = ctypes.c_void_p()
+    rc = lib.fdtd_create_grid(n[0], n[1], n[2], dx, S, cpml, None, ctypes.byref(h))
+    return rc, h
+
+
+def test_host_argument_checks():
+    """Host-side validation of the C ABI (no CUDA call is made)."""
+    lib = _lib()
+    rc, h = _grid(lib, S=1.01)
+    assert rc == -2 and not h.value                      # FDTD_ECOURANT
+    rc, h = _grid(lib, n=(1, 8, 8))
+    assert rc == -1
+    rc, h = _grid(lib)
+    assert rc == 0
+    try:
+        wid = ctypes.c_int()
+        assert lib.fdtd_add_wire(h, 2, 2, 1, 2, 2, 6, 0.005, ctypes.byref(wid)) == 0
+        assert lib.fdtd_add_wire(h, 2, 2, 1, 3, 2, 6, 0.005, None) == -1          # not axis-aligned
+        assert lib.fdtd_add_wire(h, 0, 2, 1, 0, 2, 6, 0.005, None) == -1          # on a wall
+        assert lib.fdtd_add_wire(h, 2, 2, 1, 2, 2, 6, 0.024, None) == -1          # thicker than 0.23 dx
+        assert b"0.23" in lib.fdtd_last_error(h)
+        cur = (ctypes.c_double * 4)(1, 2, 3, 4)
+        assert lib.fdtd_add_source(h, 3, 3, 3, 2, 0.0, cur, 4, None) == 0
+        assert lib.fdtd_add_source(h, 3, 3, 3, 2, 50.0, cur, 4, None) == -1        # non-ideal
+        assert lib.fdtd_add_source(h, 0, 3, 3, 2, 0.0, cur, 4, None) == -1         # wall edge
+        assert lib.fdtd_add_probe(h, 0, 3, 3, 3, 2, 5, None) == 0
+        assert lib.fdtd_add_probe(h, 0, 3, 3, 3, 2, 6, None) == -1                 # path leaves grid
+        assert lib.fdtd_add_probe(h, 1, 0, 3, 3, 2, 1, None) == -1                 # loop needs i >= 1
+        assert lib.fdtd_step(h, 1) == -8                                           # not finalized
+        nb = ctypes.c_size_t()
+        assert lib.fdtd_arena_bytes(h, 100, ctypes.byref(nb)) == 0 and nb.value > 12 * 8 * 8 * 8 * 4
+    finally:
+        lib.fdtd_destroy(h)
+
+
+def test_too_many_classes_rejected_before_any_device_work():
+    """More than 256 distinct coefficient sets -> FDTD_ECLASSES (host-side
+    class building runs before any allocation)."""
+    import numpy as np
+    from paper_2207_06908_gb300._lib import Material
+    lib = _lib()
+    rc, h = _grid(lib, n=(24, 24, 24))
+    try:
+        rng = np.random.default_rng(0)
+        cm = rng.integers(0, 40, size=24 ** 3).astype(np.uint8)
+        mats = (Material * 40)(*[Material(1.0 + q, 0.001 * q, 1.0) for q in range(40)])
+        assert lib.fdtd_set_materials(h, cm.ctypes.data_as(ctypes.c_void_p), mats, 40) == 0
+        assert lib.fdtd_finalize(h, 0, None, 0) == -5
+        assert lib.fdtd_set_materials(h, cm.ctypes.data_as(ctypes.c_void_p), mats, 30) == -1
+    finally:
+        lib.fdtd_destroy(h)

@@ -1,0 +1,135 @@
+"""GPU (FP32, through the C ABI) against the FP64 oracle in parity mode
+(coefficients and source samples rounded to FP32, arithmetic in FP64).
+
+Tolerances: relative L2 <= 1e-5 on every field component and <= 1e-4 on
+every probe waveform, on the same seeded inputs.
+"""
+import numpy as np
+import pytest
+
+from paper_2207_06908_gb300 import workloads as W
+from _scenario import oracle_from_scenario, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+FIELD_TOL = 1e-5
+PROBE_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def fdtd():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2207_06908_gb300 import fdtd as F
+    return F
+
+
+def run_gpu(F, sc, steps):
+    g = F.from_scenario(sc, probe_capacity=steps)
+    if sc.fields is not None:
+        for c, f in enumerate(sc.fields):
+            g.set_field(c, f)
+    g.step(steps)
+    fields = [g.get_field(c) for c in range(6)]
+    probes = [g.read_probe(p, 0, steps) for p in range(len(sc.probes))]
+    g.close()
+    return fields, probes
+
+
+def run_oracle(sc, steps):
+    o = oracle_from_scenario(sc, parity=True)
+    o.step(steps)
+    return [o.get_field(c) for c in range(6)], [o.read_probe(p)[:steps] for p in range(len(sc.probes))]
+
+
+def compare(gf, gp, of, op, field_tol=FIELD_TOL, probe_tol=PROBE_TOL):
+    errs = []
+    for c in range(6):
+        e = rel_l2(gf[c], of[c])
+        errs.append(e)
+        assert e <= field_tol, f"component {c}: rel L2 {e:.3e}"
+    for p in range(len(gp)):
+        if np.linalg.norm(op[p]) == 0:
+            assert np.all(gp[p] == 0)
+            continue
+        e = rel_l2(gp[p], op[p])
+        assert e <= probe_tol, f"probe {p}: rel L2 {e:.3e}"
+    return errs
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_pec_17cube(fdtd, seed):
+    """random blocky media, wires, sources, probes and fields; 17^3 spans
+    one full 32x8 tile row plus a ragged tail in y and two z chunks"""
+    sc = W.random_scenario(seed, n=(17, 17, 17), n_steps=60)
+    compare(*run_gpu(fdtd, sc, 60), *run_oracle(sc, 60))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_random_cpml_ragged(fdtd, seed):
+    """odd, non-multiple-of-tile sizes with a CPML on all faces"""
+    sc = W.random_scenario(100 + seed, n=(45, 21, 27), cpml=5, n_steps=70)
+    compare(*run_gpu(fdtd, sc, 70), *run_oracle(sc, 70))
+
+
+def test_smallest_grid(fdtd):
+    """degenerate 2x2x2 box: every E is a wall except none; H only"""
+    sc = W.random_scenario(7, n=(2, 3, 2), n_wires=0, n_sources=0, n_probes=0, n_steps=5)
+    compare(*run_gpu(fdtd, sc, 5), *run_oracle(sc, 5))
+
+
+def test_zero_steps_leaves_fields(fdtd):
+    sc = W.random_scenario(8, n=(9, 10, 11), n_steps=4)
+    g = fdtd.from_scenario(sc, probe_capacity=4)
+    for c, f in enumerate(sc.fields):
+        g.set_field(c, f)
+    g.step(0)
+    for c, f in enumerate(sc.fields):
+        assert np.array_equal(g.get_field(c), np.asarray(f, np.float32))
+    g.close()
+
+
+def test_config1_full(fdtd):
+    """48^3 PEC lossy half-space, Gaussian-derivative source, 500 steps"""
+    sc = W.config1()
+    gf, gp = run_gpu(fdtd, sc, sc.n_steps)
+    of, op = run_oracle(sc, sc.n_steps)
+    compare(gf, gp, of, op)
+
+
+def test_graph_and_direct_paths_agree(fdtd):
+    """fdtd_step replays a captured graph of 32 steps plus direct launches;
+    any split of the same step count gives bitwise the same state"""
+    sc = W.random_scenario(21, n=(40, 18, 33), cpml=4, n_steps=75)
+    a_f, a_p = run_gpu(fdtd, sc, 75)
+    g = fdtd.from_scenario(sc, probe_capacity=75)
+    for c, f in enumerate(sc.fields):
+        g.set_field(c, f)
+    for n in (1, 2, 33, 7, 32):
+        g.step(n)
+    b_f = [g.get_field(c) for c in range(6)]
+    b_p = [g.read_probe(p, 0, 75) for p in range(len(sc.probes))]
+    g.close()
+    for x, y in zip(a_f, b_f):
+        assert np.array_equal(x, y)
+    for x, y in zip(a_p, b_p):
+        assert np.array_equal(x, y)
+
+
+def test_config2_full_size_truncated(fdtd):
+    """256^3, 10-cell CPML, thin wire, source and probes: the bench workload
+    at full size, in the bench's launch path (one 32-step graph + direct
+    steps), from seeded random fields so every cell is active; 40 steps."""
+    steps = 40
+    sc = W.config2(n_steps=steps)
+    rng = np.random.default_rng(2024)
+    sc.fields = W.random_fields(rng, sc.n)
+    compare(*run_gpu(fdtd, sc, steps), *run_oracle(sc, steps))
+
+
+def test_config2_scaled_long_run(fdtd):
+    """the config-2 layout at 64^3 for 800 steps from rest: the source
+    drives the wire through the CPML window; probe waveforms match"""
+    sc = W.config2(n_steps=800, n=64)
+    compare(*run_gpu(fdtd, sc, 800), *run_oracle(sc, 800))
