@@ -49,6 +49,15 @@
 #include <omp.h>
 #endif
 
+/* Storage and update precision.  The oracle is FP64; the same source built
+ * with -DORC_REAL=float gives a plain FP32 evaluation of the identical
+ * algorithm, used only to size the rounding error FP32 storage cannot
+ * avoid (never as a reference). */
+#ifndef ORC_REAL
+#define ORC_REAL double
+#endif
+typedef ORC_REAL real;
+
 #define ORC_C0 299792458.0
 #define ORC_EPS0 8.8541878128e-12
 #define ORC_MU0 1.25663706212e-6
@@ -58,7 +67,7 @@ enum { EX = 0, EY, EZ, HX, HY, HZ };
 enum { PROBE_V = 0, PROBE_I = 1, PROBE_E = 2, PROBE_H = 3 };
 
 typedef struct { int axis, i, j, k, n; double radius; } orc_wire;
-typedef struct { int axis, i, j, k, n; double *cur; } orc_src;
+typedef struct { int axis, i, j, k, n; real *cur; } orc_src;
 typedef struct { int kind, axis, i, j, k, n_edges; } orc_probe;
 
 typedef struct orc_grid {
@@ -66,29 +75,29 @@ typedef struct orc_grid {
     double dx, dt, courant;
     int parity;
     size_t sy, sz, ntot;       /* strides of the node-indexed arrays */
-    double *f[6];              /* Ex Ey Ez Hx Hy Hz */
+    real *f[6];                /* Ex Ey Ez Hx Hy Hz */
     /* materials per cell */
     uint8_t *mat;
     double *m_eps, *m_sig, *m_mu;
     int n_mat;
     /* coefficients per component position */
-    double *ca[3], *cb[3], *db[3];
+    real *ca[3], *cb[3], *db[3];
     /* CPML */
     int d;
     double order, kappa_max, alpha_max, alpha_order, sigma_max;
     /* profile per axis u: E-position (integer node) and H-position
      * (half-integer) b, c, 1/kappa, plus an "inside the layer" flag */
-    double *pe_b[3], *pe_c[3], *pe_ki[3];
-    double *ph_b[3], *ph_c[3], *ph_ki[3];
+    real *pe_b[3], *pe_c[3], *pe_ki[3];
+    real *ph_b[3], *ph_c[3], *ph_ki[3];
     uint8_t *pe_on[3], *ph_on[3];
     /* psi[comp][axis]: auxiliary field of component comp (0..5) for its
      * derivative along axis; full node-indexed arrays, NULL on the diagonal */
-    double *psi[6][3];
+    real *psi[6][3];
     /* wires, sources, probes */
     orc_wire *wires; int n_wires;
     orc_src *srcs; int n_srcs;
     orc_probe *probes; int n_probes;
-    double *src_coef;          /* -cb/dx at each source edge */
+    real *src_coef;            /* -cb/dx at each source edge */
     int max_steps;
     double *probe_out;         /* [n_probes][max_steps] */
     long step;
@@ -118,7 +127,7 @@ orc_grid *orc_create(int nx, int ny, int nz, double dx, double courant, int pari
     g->sy = (size_t)(nx + 1);
     g->sz = (size_t)(nx + 1) * (size_t)(ny + 1);
     g->ntot = g->sz * (size_t)(nz + 1);
-    for (int c = 0; c < 6; c++) g->f[c] = (double *)calloc(g->ntot, sizeof(double));
+    for (int c = 0; c < 6; c++) g->f[c] = (real *)calloc(g->ntot, sizeof(real));
     g->mat = (uint8_t *)calloc((size_t)nx * ny * nz, 1);
     g->n_mat = 1;
     g->m_eps = (double *)malloc(sizeof(double)); g->m_eps[0] = 1.0;
@@ -227,7 +236,7 @@ int orc_add_source(orc_grid *g, int i, int j, int k, int axis, const double *cur
     }
     g->srcs = (orc_src *)realloc(g->srcs, (g->n_srcs + 1) * sizeof(orc_src));
     orc_src s = {axis, i, j, k, n, NULL};
-    s.cur = (double *)malloc((n > 0 ? n : 1) * sizeof(double));
+    s.cur = (real *)malloc((n > 0 ? n : 1) * sizeof(real));
     for (int t = 0; t < n; t++) s.cur[t] = r32(g, cur[t]);
     g->srcs[g->n_srcs++] = s;
     return 0;
@@ -272,13 +281,13 @@ static void build_cpml(orc_grid *g)
     int nn[3] = {g->nx, g->ny, g->nz};
     for (int u = 0; u < 3; u++) {
         int n = nn[u];
-        g->pe_b[u] = (double *)calloc(n + 1, sizeof(double));
-        g->pe_c[u] = (double *)calloc(n + 1, sizeof(double));
-        g->pe_ki[u] = (double *)calloc(n + 1, sizeof(double));
+        g->pe_b[u] = (real *)calloc(n + 1, sizeof(real));
+        g->pe_c[u] = (real *)calloc(n + 1, sizeof(real));
+        g->pe_ki[u] = (real *)calloc(n + 1, sizeof(real));
         g->pe_on[u] = (uint8_t *)calloc(n + 1, 1);
-        g->ph_b[u] = (double *)calloc(n + 1, sizeof(double));
-        g->ph_c[u] = (double *)calloc(n + 1, sizeof(double));
-        g->ph_ki[u] = (double *)calloc(n + 1, sizeof(double));
+        g->ph_b[u] = (real *)calloc(n + 1, sizeof(real));
+        g->ph_c[u] = (real *)calloc(n + 1, sizeof(real));
+        g->ph_ki[u] = (real *)calloc(n + 1, sizeof(real));
         g->ph_on[u] = (uint8_t *)calloc(n + 1, 1);
         for (int i = 0; i <= n; i++) {
             g->pe_ki[u][i] = 1.0; g->ph_ki[u][i] = 1.0; g->pe_b[u][i] = 1.0; g->ph_b[u][i] = 1.0;
@@ -314,7 +323,7 @@ static void build_cpml(orc_grid *g)
     int comp_axis[6] = {0, 1, 2, 0, 1, 2};
     for (int c = 0; c < 6; c++)
         for (int u = 0; u < 3; u++)
-            if (u != comp_axis[c]) g->psi[c][u] = (double *)calloc(g->ntot, sizeof(double));
+            if (u != comp_axis[c]) g->psi[c][u] = (real *)calloc(g->ntot, sizeof(real));
 }
 
 /* equivalent-radius factor of a thin wire of radius a (Sec. 2.3 reading) */
@@ -444,9 +453,9 @@ int orc_finalize(orc_grid *g, int max_steps)
      *    time-averaged) and of Eq. fdtdhx; 1/dx folded in */
     double dt = g->dt, dx = g->dx;
     for (int c = 0; c < 3; c++) {
-        g->ca[c] = (double *)calloc(N, sizeof(double));
-        g->cb[c] = (double *)calloc(N, sizeof(double));
-        g->db[c] = (double *)calloc(N, sizeof(double));
+        g->ca[c] = (real *)calloc(N, sizeof(real));
+        g->cb[c] = (real *)calloc(N, sizeof(real));
+        g->db[c] = (real *)calloc(N, sizeof(real));
         for (size_t q = 0; q < N; q++) {
             if (eps[c][q] > 0 && !pec[c][q]) {
                 double e = ORC_EPS0 * eps[c][q] * fac_e[c][q];
@@ -462,7 +471,7 @@ int orc_finalize(orc_grid *g, int max_steps)
         }
     }
     /* source factor -cb/dx on each source edge (J = I/dx^2 in Eq. maxwell) */
-    g->src_coef = (double *)calloc(g->n_srcs > 0 ? g->n_srcs : 1, sizeof(double));
+    g->src_coef = (real *)calloc(g->n_srcs > 0 ? g->n_srcs : 1, sizeof(real));
     for (int s = 0; s < g->n_srcs; s++) {
         orc_src *sr = &g->srcs[s];
         size_t q = IDX(g, sr->i, sr->j, sr->k);
@@ -510,7 +519,7 @@ int orc_get_coef(const orc_grid *g, int which, double *cells)
 {
     /* which: 0..2 ca_x..z, 3..5 cb_x..z, 6..8 db_x..z */
     if (!g->finalized || which < 0 || which > 8) return -1;
-    const double *src = which < 3 ? g->ca[which] : which < 6 ? g->cb[which - 3] : g->db[which - 6];
+    const real *src = which < 3 ? g->ca[which] : which < 6 ? g->cb[which - 3] : g->db[which - 6];
     for (int k = 0; k < g->nz; k++)
         for (int j = 0; j < g->ny; j++)
             for (int i = 0; i < g->nx; i++)
@@ -523,7 +532,7 @@ int orc_get_coef(const orc_grid *g, int which, double *cells)
 /* one curl term along axis u: plain difference, or in the CPML layer
  * d/kappa + psi with psi <- b psi + c d.  Differences are in field units
  * (1/dx sits in the coefficients), so psi is kept in the same units. */
-static inline double term(double dif, double *psi, size_t q, int on, double b, double c, double ki)
+static inline real term(real dif, real *psi, size_t q, int on, real b, real c, real ki)
 {
     if (!on) return dif;
     psi[q] = b * psi[q] + c * dif;
@@ -533,8 +542,8 @@ static inline double term(double dif, double *psi, size_t q, int on, double b, d
 static void update_h(orc_grid *g)
 {
     int nx = g->nx, ny = g->ny, nz = g->nz;
-    double *Ex = g->f[EX], *Ey = g->f[EY], *Ez = g->f[EZ];
-    double *Hx = g->f[HX], *Hy = g->f[HY], *Hz = g->f[HZ];
+    real *Ex = g->f[EX], *Ey = g->f[EY], *Ez = g->f[EZ];
+    real *Hx = g->f[HX], *Hy = g->f[HY], *Hz = g->f[HZ];
     size_t sy = g->sy, sz = g->sz;
     /* Hx(i,j+1/2,k+1/2) += db [dEy/dz - dEz/dy]; i = 0 and nx are normal walls */
 #pragma omp parallel for collapse(2) schedule(static)
@@ -542,8 +551,8 @@ static void update_h(orc_grid *g)
         for (int j = 0; j < ny; j++)
             for (int i = 1; i < nx; i++) {
                 size_t q = IDX(g, i, j, k);
-                double tz = term(Ey[q + sz] - Ey[q], g->psi[HX][2], q, g->ph_on[2][k], g->ph_b[2][k], g->ph_c[2][k], g->ph_ki[2][k]);
-                double ty = term(Ez[q + sy] - Ez[q], g->psi[HX][1], q, g->ph_on[1][j], g->ph_b[1][j], g->ph_c[1][j], g->ph_ki[1][j]);
+                real tz = term(Ey[q + sz] - Ey[q], g->psi[HX][2], q, g->ph_on[2][k], g->ph_b[2][k], g->ph_c[2][k], g->ph_ki[2][k]);
+                real ty = term(Ez[q + sy] - Ez[q], g->psi[HX][1], q, g->ph_on[1][j], g->ph_b[1][j], g->ph_c[1][j], g->ph_ki[1][j]);
                 Hx[q] += g->db[0][q] * (tz - ty);
             }
     /* Hy(i+1/2,j,k+1/2) += db [dEz/dx - dEx/dz]; j = 0 and ny are walls */
@@ -552,8 +561,8 @@ static void update_h(orc_grid *g)
         for (int j = 1; j < ny; j++)
             for (int i = 0; i < nx; i++) {
                 size_t q = IDX(g, i, j, k);
-                double tx = term(Ez[q + 1] - Ez[q], g->psi[HY][0], q, g->ph_on[0][i], g->ph_b[0][i], g->ph_c[0][i], g->ph_ki[0][i]);
-                double tz = term(Ex[q + sz] - Ex[q], g->psi[HY][2], q, g->ph_on[2][k], g->ph_b[2][k], g->ph_c[2][k], g->ph_ki[2][k]);
+                real tx = term(Ez[q + 1] - Ez[q], g->psi[HY][0], q, g->ph_on[0][i], g->ph_b[0][i], g->ph_c[0][i], g->ph_ki[0][i]);
+                real tz = term(Ex[q + sz] - Ex[q], g->psi[HY][2], q, g->ph_on[2][k], g->ph_b[2][k], g->ph_c[2][k], g->ph_ki[2][k]);
                 Hy[q] += g->db[1][q] * (tx - tz);
             }
     /* Hz(i+1/2,j+1/2,k) += db [dEx/dy - dEy/dx]; k = 0 and nz are walls */
@@ -562,8 +571,8 @@ static void update_h(orc_grid *g)
         for (int j = 0; j < ny; j++)
             for (int i = 0; i < nx; i++) {
                 size_t q = IDX(g, i, j, k);
-                double ty = term(Ex[q + sy] - Ex[q], g->psi[HZ][1], q, g->ph_on[1][j], g->ph_b[1][j], g->ph_c[1][j], g->ph_ki[1][j]);
-                double tx = term(Ey[q + 1] - Ey[q], g->psi[HZ][0], q, g->ph_on[0][i], g->ph_b[0][i], g->ph_c[0][i], g->ph_ki[0][i]);
+                real ty = term(Ex[q + sy] - Ex[q], g->psi[HZ][1], q, g->ph_on[1][j], g->ph_b[1][j], g->ph_c[1][j], g->ph_ki[1][j]);
+                real tx = term(Ey[q + 1] - Ey[q], g->psi[HZ][0], q, g->ph_on[0][i], g->ph_b[0][i], g->ph_c[0][i], g->ph_ki[0][i]);
                 Hz[q] += g->db[2][q] * (ty - tx);
             }
 }
@@ -571,8 +580,8 @@ static void update_h(orc_grid *g)
 static void update_e(orc_grid *g)
 {
     int nx = g->nx, ny = g->ny, nz = g->nz;
-    double *Ex = g->f[EX], *Ey = g->f[EY], *Ez = g->f[EZ];
-    double *Hx = g->f[HX], *Hy = g->f[HY], *Hz = g->f[HZ];
+    real *Ex = g->f[EX], *Ey = g->f[EY], *Ez = g->f[EZ];
+    real *Hx = g->f[HX], *Hy = g->f[HY], *Hz = g->f[HZ];
     size_t sy = g->sy, sz = g->sz;
     /* Ex(i+1/2,j,k) = ca Ex + cb [dHz/dy - dHy/dz]; j in (0,ny), k in (0,nz) */
 #pragma omp parallel for collapse(2) schedule(static)
@@ -580,8 +589,8 @@ static void update_e(orc_grid *g)
         for (int j = 1; j < ny; j++)
             for (int i = 0; i < nx; i++) {
                 size_t q = IDX(g, i, j, k);
-                double ty = term(Hz[q] - Hz[q - sy], g->psi[EX][1], q, g->pe_on[1][j], g->pe_b[1][j], g->pe_c[1][j], g->pe_ki[1][j]);
-                double tz = term(Hy[q] - Hy[q - sz], g->psi[EX][2], q, g->pe_on[2][k], g->pe_b[2][k], g->pe_c[2][k], g->pe_ki[2][k]);
+                real ty = term(Hz[q] - Hz[q - sy], g->psi[EX][1], q, g->pe_on[1][j], g->pe_b[1][j], g->pe_c[1][j], g->pe_ki[1][j]);
+                real tz = term(Hy[q] - Hy[q - sz], g->psi[EX][2], q, g->pe_on[2][k], g->pe_b[2][k], g->pe_c[2][k], g->pe_ki[2][k]);
                 Ex[q] = g->ca[0][q] * Ex[q] + g->cb[0][q] * (ty - tz);
             }
     /* Ey(i,j+1/2,k) = ca Ey + cb [dHx/dz - dHz/dx]; i in (0,nx), k in (0,nz) */
@@ -590,8 +599,8 @@ static void update_e(orc_grid *g)
         for (int j = 0; j < ny; j++)
             for (int i = 1; i < nx; i++) {
                 size_t q = IDX(g, i, j, k);
-                double tz = term(Hx[q] - Hx[q - sz], g->psi[EY][2], q, g->pe_on[2][k], g->pe_b[2][k], g->pe_c[2][k], g->pe_ki[2][k]);
-                double tx = term(Hz[q] - Hz[q - 1], g->psi[EY][0], q, g->pe_on[0][i], g->pe_b[0][i], g->pe_c[0][i], g->pe_ki[0][i]);
+                real tz = term(Hx[q] - Hx[q - sz], g->psi[EY][2], q, g->pe_on[2][k], g->pe_b[2][k], g->pe_c[2][k], g->pe_ki[2][k]);
+                real tx = term(Hz[q] - Hz[q - 1], g->psi[EY][0], q, g->pe_on[0][i], g->pe_b[0][i], g->pe_c[0][i], g->pe_ki[0][i]);
                 Ey[q] = g->ca[1][q] * Ey[q] + g->cb[1][q] * (tz - tx);
             }
     /* Ez(i,j,k+1/2) = ca Ez + cb [dHy/dx - dHx/dy]; i in (0,nx), j in (0,ny) */
@@ -600,14 +609,14 @@ static void update_e(orc_grid *g)
         for (int j = 1; j < ny; j++)
             for (int i = 1; i < nx; i++) {
                 size_t q = IDX(g, i, j, k);
-                double tx = term(Hy[q] - Hy[q - 1], g->psi[EZ][0], q, g->pe_on[0][i], g->pe_b[0][i], g->pe_c[0][i], g->pe_ki[0][i]);
-                double ty = term(Hx[q] - Hx[q - sy], g->psi[EZ][1], q, g->pe_on[1][j], g->pe_b[1][j], g->pe_c[1][j], g->pe_ki[1][j]);
+                real tx = term(Hy[q] - Hy[q - 1], g->psi[EZ][0], q, g->pe_on[0][i], g->pe_b[0][i], g->pe_c[0][i], g->pe_ki[0][i]);
+                real ty = term(Hx[q] - Hx[q - sy], g->psi[EZ][1], q, g->pe_on[1][j], g->pe_b[1][j], g->pe_c[1][j], g->pe_ki[1][j]);
                 Ez[q] = g->ca[2][q] * Ez[q] + g->cb[2][q] * (tx - ty);
             }
     /* ideal current sources: -cb/dx * I(t_{n+1/2}) on the source edge */
     for (int s = 0; s < g->n_srcs; s++) {
         orc_src *sr = &g->srcs[s];
-        double I = (g->step < sr->n) ? sr->cur[g->step] : 0.0;
+        real I = (g->step < sr->n) ? sr->cur[g->step] : (real)0;
         g->f[sr->axis][IDX(g, sr->i, sr->j, sr->k)] += g->src_coef[s] * I;
     }
     /* PEC walls: tangential E on the six faces is zero (the update loops
@@ -639,7 +648,7 @@ static double probe_value(const orc_grid *g, const orc_probe *p)
         return v;
     }
     /* PROBE_I: circulation of H around the edge, Ampere's law */
-    const double *Hx = g->f[HX], *Hy = g->f[HY], *Hz = g->f[HZ];
+    const real *Hx = g->f[HX], *Hy = g->f[HY], *Hz = g->f[HZ];
     int i = p->i, j = p->j, k = p->k;
     if (p->axis == 2)
         return dx * (Hy[IDX(g, i, j, k)] - Hy[IDX(g, i - 1, j, k)] - Hx[IDX(g, i, j, k)] + Hx[IDX(g, i, j - 1, k)]);

@@ -22,8 +22,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fdtd_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liborc_fdtd.so")
+_SO32 = os.path.join(_BUILD, "liborc_fdtd_f32.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 PROBE_V, PROBE_I, PROBE_E, PROBE_H = 0, 1, 2, 3
 EX, EY, EZ, HX, HY, HZ = range(6)
@@ -33,26 +34,33 @@ EPS0 = 8.8541878128e-12
 MU0 = 1.25663706212e-6
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (FP64, OpenMP, no FMA contraction)."""
-    os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_SO)
-            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
-        return _SO
-    tmp = _SO + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+def _build_one(so: str, defs: list[str], force: bool) -> str:
+    if (not force and os.path.exists(so)
+            and os.path.getmtime(so) >= os.path.getmtime(_SRC)):
+        return so
+    tmp = so + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", *defs,
            "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _SO)
-    return _SO
+    os.replace(tmp, so)
+    return so
 
 
-def _load():
-    global _lib
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP, no FMA contraction): the FP64
+    oracle, and the same source with FP32 storage and arithmetic, which
+    only serves to size the rounding error of FP32 field storage."""
+    os.makedirs(_BUILD, exist_ok=True)
+    _build_one(_SO32, ["-DORC_REAL=float"], force)
+    return _build_one(_SO, [], force)
+
+
+def _load(f32: bool = False):
     with _lock:
-        if _lib is not None:
-            return _lib
-        lib = ctypes.CDLL(build())
+        if f32 in _libs:
+            return _libs[f32]
+        build()
+        lib = ctypes.CDLL(_SO32 if f32 else _SO)
         P = ctypes.c_void_p
         I = ctypes.c_int
         D = ctypes.c_double
@@ -78,7 +86,7 @@ def _load():
         lib.orc_get_coef.argtypes = [P, I, dp]
         lib.orc_step.argtypes = [P, I]
         lib.orc_read_probe.argtypes = [P, I, dp]
-        _lib = lib
+        _libs[f32] = lib
         return lib
 
 
@@ -104,8 +112,11 @@ class OracleGrid:
     Hy(i+1/2,j,k+1/2) or Hz(i+1/2,j+1/2,k).
     """
 
-    def __init__(self, nx, ny, nz, dx, courant=0.99, parity=False):
-        self._lib = _load()
+    def __init__(self, nx, ny, nz, dx, courant=0.99, parity=False, f32=False):
+        """parity: round coefficients and source samples to FP32 (arithmetic
+        stays FP64).  f32: the FP32-storage build of the same algorithm (a
+        yardstick for FP32 rounding, not a reference)."""
+        self._lib = _load(f32)
         self.shape = (nz, ny, nx)
         self.nx, self.ny, self.nz = nx, ny, nz
         self.dx = dx
@@ -183,12 +194,12 @@ class OracleGrid:
         _check(self._lib.orc_step(self._h, int(n)), "step")
 
     @classmethod
-    def from_scenario(cls, sc, parity=True):
+    def from_scenario(cls, sc, parity=True, f32=False):
         """Build from a problem description with the attributes n, dx,
         courant, cpml, cell_material, materials [(eps_r, sigma, mu_r)],
         wires [(p0, p1, radius)], sources [(node, axis, current)], probes
         [(kind, node, axis, n_edges)], n_steps and fields (or None)."""
-        g = cls(*sc.n, sc.dx, courant=sc.courant, parity=parity)
+        g = cls(*sc.n, sc.dx, courant=sc.courant, parity=parity, f32=f32)
         if sc.cpml:
             g.set_cpml(sc.cpml)
         g.set_materials(sc.cell_material, [m[0] for m in sc.materials], [m[1] for m in sc.materials],

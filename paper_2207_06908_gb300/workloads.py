@@ -234,7 +234,7 @@ def random_fields(rng, n, scale_h=1.0 / 377.0):
 
 
 def random_scenario(seed, n=(17, 17, 17), dx=0.1, courant=0.99, cpml=0, n_blocks=5, n_mat=4,
-                    n_wires=2, n_sources=2, n_probes=8, n_steps=40, fields=True):
+                    n_wires=2, n_sources=2, n_probes=8, n_steps=40, fields=True, current_scale=1.0):
     """Random blocky media, thin wires, sources, probes and (optionally)
     random initial fields, all from one seed."""
     rng = np.random.default_rng(seed)
@@ -264,7 +264,7 @@ def random_scenario(seed, n=(17, 17, 17), dx=0.1, courant=0.99, cpml=0, n_blocks
         axis = int(rng.integers(0, 3))
         node = [int(rng.integers(lo_in, m - lo_in)) for m in n]
         w = rng.uniform(0.05, 0.4)
-        cur = rng.uniform(0.5, 2.0) * np.sin(w * t + rng.uniform(0, 6)) * np.exp(-t / rng.uniform(10, 40))
+        cur = current_scale * rng.uniform(0.5, 2.0) * np.sin(w * t + rng.uniform(0, 6)) * np.exp(-t / rng.uniform(10, 40))
         sources.append((tuple(node), axis, cur))
     probes = []
     for q in range(n_probes):
