@@ -1,0 +1,71 @@
+// fdtd_edges.cu -- ideal current sources (Kuklin, arXiv 2207.06908,
+// Sec. 2.1, J = I/dx^2 on one edge) and the probes of the Sec. 4 model files
+// ("calculate": voltage = -sum E dl along a path, current = loop integral of
+// H around an edge), applied right after the step kernel of the same step.
+// One CTA; a device-side step counter indexes the source samples and the
+// probe slots, so the launch can be replayed inside a CUDA graph.
+#include "fdtd_internal.h"
+
+namespace fdtd {
+namespace {
+
+__device__ __forceinline__ long long eidx(const EdgeArgs &a, int i, int j, int k)
+{
+    return (long long)k * a.plane + (long long)j * a.pitch + i;
+}
+
+__global__ void edge_kernel(const EdgeArgs a)
+{
+    __shared__ long long n_s;
+    if (threadIdx.x == 0) n_s = *a.step;
+    __syncthreads();
+    const long long n = n_s;
+    for (int q = threadIdx.x; q < a.n_src; q += blockDim.x) {
+        const SourceDesc sd = a.src[q];
+        const float I = n < sd.n_samples ? a.samples[sd.sample_off + n] : 0.f;
+        atomicAdd(a.E[sd.comp] + sd.idx, sd.coef * I);
+    }
+    __syncthreads();
+    if (n < a.capacity) {
+        for (int p = threadIdx.x; p < a.n_probes; p += blockDim.x) {
+            const ProbeDesc pr = a.probes[p];
+            float v = 0.f;
+            if (pr.kind == 2) {
+                v = a.E[pr.axis][eidx(a, pr.i, pr.j, pr.k)];
+            } else if (pr.kind == 3) {
+                v = a.H[pr.axis][eidx(a, pr.i, pr.j, pr.k)];
+            } else if (pr.kind == 0) {
+                int q[3] = {pr.i, pr.j, pr.k};
+                for (int e = 0; e < pr.n_edges; ++e) {
+                    v -= a.E[pr.axis][eidx(a, q[0], q[1], q[2])] * a.dx;
+                    q[pr.axis]++;
+                }
+            } else {
+                const float *Hx = a.H[0], *Hy = a.H[1], *Hz = a.H[2];
+                const int i = pr.i, j = pr.j, k = pr.k;
+                if (pr.axis == 2)
+                    v = a.dx * ((Hy[eidx(a, i, j, k)] - Hy[eidx(a, i - 1, j, k)]) -
+                                (Hx[eidx(a, i, j, k)] - Hx[eidx(a, i, j - 1, k)]));
+                else if (pr.axis == 0)
+                    v = a.dx * ((Hz[eidx(a, i, j, k)] - Hz[eidx(a, i, j - 1, k)]) -
+                                (Hy[eidx(a, i, j, k)] - Hy[eidx(a, i, j, k - 1)]));
+                else
+                    v = a.dx * ((Hx[eidx(a, i, j, k)] - Hx[eidx(a, i, j, k - 1)]) -
+                                (Hz[eidx(a, i, j, k)] - Hz[eidx(a, i - 1, j, k)]));
+            }
+            a.probe_out[(long long)p * a.capacity + n] = v;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *a.step = n + 1;
+}
+
+}  // namespace
+
+cudaError_t launch_edges(const EdgeArgs &a, cudaStream_t s)
+{
+    edge_kernel<<<1, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace fdtd

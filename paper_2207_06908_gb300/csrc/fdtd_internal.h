@@ -2,6 +2,7 @@
 // of the GB300 FDTD library (not part of the public C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -28,6 +29,23 @@ enum Psi {
 //   H position (node i + 1/2): bh, ch, kih
 enum Prof { PR_BE = 0, PR_CE, PR_KIE, PR_BH, PR_CH, PR_KIH, PR_COUNT };
 
+// Tile geometry of the step kernel, shared with the host (tensor-map boxes).
+namespace geom {
+constexpr int TX = 32, TY = 16;
+constexpr int XO = 4;                        // box column of the tile's x0 (E, H)
+constexpr int EBX = TX + 8, EBY = TY + 2;    // E box: x0-4 .. x0+TX+3, y0-1 .. y0+TY
+constexpr int HBX = TX + 4, HBY = TY + 1;    // H box: x0-4 .. x0+TX-1, y0-1 .. y0+TY-1
+constexpr int CXO = 16;                      // box column of x0 in the class box
+constexpr int CBX = TX + 16, CBY = TY + 1;   // class box: x0-16 .. x0+TX-1
+}  // namespace geom
+
+// TMA descriptors of the current input buffers: E (E box), H (H box), class
+struct TmaMaps {
+    CUtensorMap e[3];
+    CUtensorMap h[3];
+    CUtensorMap c;
+};
+
 struct StepArgs {
     int nx, ny, nz;
     int pitch;               // row pitch in elements (multiple of 4)
@@ -43,7 +61,11 @@ struct StepArgs {
     const float *prof[3];    // per axis: PR_COUNT arrays of n_axis floats
     const float *psi_in[PSI_COUNT];
     float *psi_out[PSI_COUNT];
-    int kz;                  // planes per z chunk
+    int kz;                  // planes per z block of a work item
+    int ncx, ncy;            // column tiles along x, y
+    int nitems;              // (z blocks) x (column tiles)
+    int *work;               // [2] work counter, finished-CTA counter (self-resetting)
+    int *err;                // set to 1 when a bounded wait gave up
 };
 
 struct SourceDesc {
@@ -75,10 +97,14 @@ struct EdgeArgs {
     long long *step;         // device step counter
 };
 
-// kernels.cu
-cudaError_t launch_step(const StepArgs &a, cudaStream_t s);
-cudaError_t launch_edges(const EdgeArgs &a, cudaStream_t s);
+// fdtd_step.cu
+cudaError_t launch_step(const TmaMaps &m, const StepArgs &a, int grid, cudaStream_t s);
 int step_tile_x();
 int step_tile_y();
+int step_threads();
+int step_smem_bytes();
+const void *step_kernel_ptr();
+// fdtd_edges.cu
+cudaError_t launch_edges(const EdgeArgs &a, cudaStream_t s);
 
 }  // namespace fdtd

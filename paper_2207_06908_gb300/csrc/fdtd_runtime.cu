@@ -15,6 +15,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "fdtd.h"
 #include "fdtd_internal.h"
 
@@ -63,6 +65,11 @@ struct fdtd_grid {
     fdtd::ProbeDesc *probes_d = nullptr;
     float *probe_out = nullptr;
     long long *step_d = nullptr;
+    int *work_d = nullptr;          // [2] step-kernel work counters
+    int *err_d = nullptr;           // bounded-wait failure flag
+    fdtd::TmaMaps maps[2];          // TMA descriptors of each input parity
+    int grid_ctas = 0;
+    int ncx = 0, ncy = 0, nitems = 0;
     int parity = 0;
     long step = 0;
     int kz = 0;
@@ -86,7 +93,7 @@ int cuda_fail(fdtd_grid *g, cudaError_t e, const char *what)
 
 // ---- device arena plan -------------------------------------------------
 struct Plan {
-    size_t field, cls, table, prof[3], psi[fdtd::PSI_COUNT], src, samples, probes, out, step, total;
+    size_t field, cls, table, prof[3], psi[fdtd::PSI_COUNT], src, samples, probes, out, step, work, total;
 };
 
 size_t psi_elems(const fdtd_grid *g, int which)
@@ -118,6 +125,7 @@ Plan make_plan(const fdtd_grid *g, int capacity)
     p.probes = take(std::max<size_t>(1, g->probes.size()) * sizeof(fdtd::ProbeDesc));
     p.out = take(std::max<size_t>(1, g->probes.size()) * (size_t)std::max(capacity, 1) * sizeof(float));
     p.step = take(sizeof(long long));
+    p.work = take(4 * sizeof(int));
     p.total = off;
     return p;
 }
@@ -393,6 +401,11 @@ fdtd::StepArgs step_args(const fdtd_grid *g, int parity)
         a.psi_out[q] = g->psi[1 - parity][q];
     }
     a.kz = g->kz;
+    a.ncx = g->ncx;
+    a.ncy = g->ncy;
+    a.nitems = g->nitems;
+    a.work = g->work_d;
+    a.err = g->err_d;
     return a;
 }
 
@@ -419,10 +432,69 @@ fdtd::EdgeArgs edge_args(const fdtd_grid *g, int parity)
 
 cudaError_t enqueue_step(fdtd_grid *g, int parity, cudaStream_t s)
 {
-    cudaError_t e = fdtd::launch_step(step_args(g, parity), s);
+    cudaError_t e = fdtd::launch_step(g->maps[parity], step_args(g, parity), g->grid_ctas, s);
     if (e != cudaSuccess) return e;
     if (!g->srcs.empty() || !g->probes.empty()) e = fdtd::launch_edges(edge_args(g, parity), s);
     return e;
+}
+
+// ---- TMA descriptors ----------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 3D tiled map over one pitched array (x fastest); out-of-range box
+// elements read as zero
+bool encode_map(CUtensorMap *m, void *base, CUtensorMapDataType dt, int esize, const fdtd_grid *g, int bx, int by)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)g->nx, (cuuint64_t)g->ny, (cuuint64_t)g->nz};
+    cuuint64_t strides[2] = {(cuuint64_t)g->pitch * esize, (cuuint64_t)g->plane * esize};
+    cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    return fn(m, dt, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int setup_step_kernel(fdtd_grid *g)
+{
+    using namespace fdtd::geom;
+    for (int p = 0; p < 2; ++p) {
+        for (int c = 0; c < 3; ++c) {
+            if (!encode_map(&g->maps[p].e[c], g->F[p][c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, EBX, EBY) ||
+                !encode_map(&g->maps[p].h[c], g->F[p][3 + c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, HBX, HBY))
+                return fail(g, FDTD_ECUDA, "cuTensorMapEncodeTiled failed for a field");
+        }
+        if (!encode_map(&g->maps[p].c, g->cls, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, g, CBX, CBY))
+            return fail(g, FDTD_ECUDA, "cuTensorMapEncodeTiled failed for the class map");
+    }
+    g->ncx = (g->nx + TX - 1) / TX;
+    g->ncy = (g->ny + TY - 1) / TY;
+    g->kz = std::min(g->nz, 16);
+    const int nzb = (g->nz + g->kz - 1) / g->kz;
+    g->nitems = g->ncx * g->ncy * nzb;
+    const int smem = fdtd::step_smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(fdtd::step_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int dev = 0, sms = 0, occ = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fdtd::step_kernel_ptr(), fdtd::step_threads(), smem);
+    if (e != cudaSuccess) return cuda_fail(g, e, "step kernel setup");
+    if (occ < 1) return fail(g, FDTD_ECUDA, "step kernel does not fit on an SM");
+    g->grid_ctas = std::max(1, std::min(sms * occ, g->nitems));
+    return FDTD_OK;
 }
 
 int check_open(fdtd_grid *g, bool want_finalized)
@@ -459,7 +531,7 @@ int fdtd_create_grid(int nx, int ny, int nz, double dx, double courant, const fd
             g->cpml.sigma_max = 0.8 * (g->cpml.order + 1.0) / (std::sqrt(kMu0 / kEps0) * dx);
     }
     g->stream = (cudaStream_t)cuda_stream;
-    g->pitch = (nx + 3) / 4 * 4;
+    g->pitch = (nx + 15) / 16 * 16;   // 16-byte rows even for the class bytes (TMA strides)
     g->plane = (long long)g->pitch * ny;
     g->mat.assign((size_t)nx * ny * nz, 0);
     g->table.push_back(fdtd_material{1.0, 0.0, 1.0});
@@ -595,6 +667,8 @@ int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_by
     g->probes_d = (fdtd::ProbeDesc *)(base + p.probes);
     g->probe_out = (float *)(base + p.out);
     g->step_d = (long long *)(base + p.step);
+    g->work_d = (int *)(base + p.work);
+    g->err_d = g->work_d + 2;
     g->capacity = probe_capacity;
 
 
@@ -631,12 +705,7 @@ int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_by
                             cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(g, e, "upload");
-    // z chunking: enough CTAs to fill 152 SMs several times over
-    const int cols = ((g->nx + fdtd::step_tile_x() - 1) / fdtd::step_tile_x()) *
-                     ((g->ny + fdtd::step_tile_y() - 1) / fdtd::step_tile_y());
-    int chunks = (4 * 152 * 2 + cols - 1) / cols;
-    chunks = std::max(1, std::min(chunks, g->nz / 8 > 0 ? g->nz / 8 : 1));
-    g->kz = (g->nz + chunks - 1) / chunks;
+    if (int rc = setup_step_kernel(g)) return rc;
     g->finalized = true;
     return FDTD_OK;
 }
@@ -681,6 +750,12 @@ int fdtd_synchronize(fdtd_grid *g)
     if (!g) return FDTD_EINVAL;
     cudaError_t e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) return cuda_fail(g, e, "synchronize");
+    if (g->finalized) {
+        int flag = 0;
+        e = cudaMemcpy(&flag, g->err_d, sizeof flag, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(g, e, "error flag read");
+        if (flag) return fail(g, FDTD_ETIMEOUT, "a bounded wait in the step kernel gave up");
+    }
     return FDTD_OK;
 }
 

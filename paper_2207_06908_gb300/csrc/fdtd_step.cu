@@ -1,0 +1,499 @@
+// fdtd_step.cu -- the fused Yee time step of the GB300 FDTD library
+// (sm_103a, FP32): Kuklin, arXiv 2207.06908, Sec. 2.1, Eq. fdtdhx (H half
+// step) then Eq. fdtdex (E half step, loss term time-averaged), with the
+// CPML of Sec. 2.2, over the whole grid in one launch.
+//
+// Structure (one launch per time step; fields ping-pong between buffers):
+//   - Work items are (z block, 32x16 column tile) pairs in z-block-major
+//     order, handed out by an atomic counter to a persistent grid of
+//     (SMs x resident CTAs); all CTAs march near the same z, so the halo
+//     planes one CTA loads are still in L2 when its neighbours load them.
+//   - One producer warp streams, plane by plane, three TMA 3D boxes into a
+//     4-stage shared-memory ring: E^n (tile + 1-cell halo on every side,
+//     x start rounded down to a 16-byte boundary), H^{n-1/2} (tile + low
+//     halo) and the class bytes.  Completion is tracked by mbarriers.
+//   - Eight consumer warps: lane = x column, each warp two rows.  Per
+//     plane k they form H^{n+1/2}(k) on the tile and its low-x / low-y
+//     halo (the halo is recomputed, never exchanged), store the owned H,
+//     then form E^{n+1}(k) from that H plane and the owned column's H of
+//     plane k-1 kept in registers.  E^n(k+1) of the owned cells stays in
+//     registers for the next plane.
+// DRAM traffic per cell and step: 6 FP32 reads + 6 writes + 1 class byte
+// (49 B) plus the CPML auxiliaries in the layer; every halo read is an L2
+// hit.  Every wait is bounded; on a timeout the kernel records an error
+// flag, drains its copies in flight and returns.
+#include <cuda.h>
+
+#include "fdtd_internal.h"
+
+namespace fdtd {
+namespace {
+
+using geom::TX;                        // tile width: one lane per column
+using geom::TY;                        // tile height
+constexpr int RW = 2;                  // rows per consumer warp
+constexpr int NCW = TY / RW;           // consumer warps
+constexpr int NCONS = NCW * 32;
+constexpr int NTHREADS = NCONS + 32;   // + one producer warp
+constexpr int NSTAGE = 4;
+
+using geom::XO;
+using geom::EBX;
+using geom::EBY;
+using geom::HBX;
+using geom::HBY;
+using geom::CXO;
+using geom::CBX;
+using geom::CBY;
+
+constexpr int al128(int v) { return (v + 127) / 128 * 128; }
+constexpr int E_COMP = al128(EBX * EBY * 4);
+constexpr int H_COMP = al128(HBX * HBY * 4);
+constexpr int C_BYTES = al128(CBX * CBY);
+constexpr int OFF_E = 0;
+constexpr int OFF_H = 3 * E_COMP;
+constexpr int OFF_C = OFF_H + 3 * H_COMP;
+constexpr int OFF_HDR = OFF_C + C_BYTES;
+constexpr int STAGE = al128(OFF_HDR + 16);
+constexpr uint32_t TX_E = 3u * EBX * EBY * 4;
+constexpr uint32_t TX_FULL = TX_E + 3u * HBX * HBY * 4 + CBX * CBY;
+
+constexpr int SM_HNEW = NSTAGE * STAGE;              // [2][3][HBY][HBX]
+constexpr int HNEW_PLANE = HBY * HBX;
+constexpr int SM_TAB = SM_HNEW + 2 * 3 * HNEW_PLANE * 4;
+constexpr int SM_BAR = SM_TAB + kMaxClasses * kNumCoef * 4;
+constexpr int SM_MISC = SM_BAR + 2 * NSTAGE * 8;      // abort flag, consumed count
+constexpr int SM_TOTAL = SM_MISC + 16;
+constexpr int SM_ALLOC = SM_TOTAL + 128;              // room to align the base to 128 B
+
+constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
+
+// ---- PTX helpers ----------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait on one mbarrier phase; gives up on timeout or when another
+// warp of the CTA has already given up
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort)
+{
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    while (true) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort) return false;
+        if (gtimer() - t0 > kWaitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void consumer_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(NCONS) : "memory");
+}
+
+// ---- stencil cores ----------------------------------------------------------
+__device__ __forceinline__ bool in_slab(int i, int n, int d) { return i < d || i >= n - d; }
+__device__ __forceinline__ int slab_idx(int i, int n, int d) { return i < d ? i : i - (n - 2 * d); }
+
+// CPML convolution term (Sec. 2.2): psi <- b psi + c dif, term = dif/kappa + psi
+__device__ __forceinline__ float cpml(float dif, const float *prof, int n, int which, int i, const float *pin,
+                                      float *pout, long long q, bool write)
+{
+    const float b = __ldg(prof + (which + 0) * n + i);
+    const float c = __ldg(prof + (which + 1) * n + i);
+    const float ki = __ldg(prof + (which + 2) * n + i);
+    const float p = b * __ldg(pin + q) + c * dif;
+    if (write) pout[q] = p;
+    return dif * ki + p;
+}
+
+// H^{n+1/2} of cell (i,j,k) from E^n around it (Eq. fdtdhx and its cyclic
+// analogues): Hx += db [dEy/dz - dEz/dy], Hy += db [dEz/dx - dEx/dz],
+// Hz += db [dEx/dy - dEy/dx]; differences in field units, 1/dx in db.
+__device__ __forceinline__ void h_core(const StepArgs &a, const float *t, int i, int j, int k, bool own,
+                                       float ex, float ey, float ez, float ey_x1, float ez_x1, float ex_y1,
+                                       float ez_y1, float ex_z1, float ey_z1, float hx0, float hy0, float hz0,
+                                       float &hx, float &hy, float &hz)
+{
+    float hx_z = ey_z1 - ey, hx_y = ez_y1 - ez;
+    float hy_x = ez_x1 - ez, hy_z = ex_z1 - ex;
+    float hz_y = ex_y1 - ex, hz_x = ey_x1 - ey;
+    const int d = a.d;
+    if (d > 0) {
+        if (in_slab(i, a.nx, d)) {
+            const long long q = ((long long)k * a.ny + j) * (2 * d) + slab_idx(i, a.nx, d);
+            hy_x = cpml(hy_x, a.prof[0], a.nx, PR_BH, i, a.psi_in[PSI_HY_X], a.psi_out[PSI_HY_X], q, own);
+            hz_x = cpml(hz_x, a.prof[0], a.nx, PR_BH, i, a.psi_in[PSI_HZ_X], a.psi_out[PSI_HZ_X], q, own);
+        }
+        if (in_slab(j, a.ny, d)) {
+            const long long q = ((long long)k * (2 * d) + slab_idx(j, a.ny, d)) * a.nx + i;
+            hx_y = cpml(hx_y, a.prof[1], a.ny, PR_BH, j, a.psi_in[PSI_HX_Y], a.psi_out[PSI_HX_Y], q, own);
+            hz_y = cpml(hz_y, a.prof[1], a.ny, PR_BH, j, a.psi_in[PSI_HZ_Y], a.psi_out[PSI_HZ_Y], q, own);
+        }
+        if (in_slab(k, a.nz, d)) {
+            const long long q = ((long long)slab_idx(k, a.nz, d) * a.ny + j) * a.nx + i;
+            hx_z = cpml(hx_z, a.prof[2], a.nz, PR_BH, k, a.psi_in[PSI_HX_Z], a.psi_out[PSI_HX_Z], q, own);
+            hy_z = cpml(hy_z, a.prof[2], a.nz, PR_BH, k, a.psi_in[PSI_HY_Z], a.psi_out[PSI_HY_Z], q, own);
+        }
+    }
+    hx = hx0 + t[6] * (hx_z - hx_y);
+    hy = hy0 + t[7] * (hy_x - hy_z);
+    hz = hz0 + t[8] * (hz_y - hz_x);
+}
+
+// E^{n+1} of cell (i,j,k) (Eq. fdtdex with sigma E time-averaged):
+// E = ca E + cb [curl_h H^{n+1/2}], 1/dx in cb.
+__device__ __forceinline__ void e_core(const StepArgs &a, const float *t, int i, int j, int k, float ex,
+                                       float ey, float ez, float hx, float hy, float hz, float hz_ym,
+                                       float hx_ym, float hz_xm, float hy_xm, float hx_zm, float hy_zm,
+                                       float &ex1, float &ey1, float &ez1)
+{
+    float ex_y = hz - hz_ym, ex_z = hy - hy_zm;
+    float ey_z = hx - hx_zm, ey_x = hz - hz_xm;
+    float ez_x = hy - hy_xm, ez_y = hx - hx_ym;
+    const int d = a.d;
+    if (d > 0) {
+        if (in_slab(i, a.nx, d)) {
+            const long long q = ((long long)k * a.ny + j) * (2 * d) + slab_idx(i, a.nx, d);
+            ey_x = cpml(ey_x, a.prof[0], a.nx, PR_BE, i, a.psi_in[PSI_EY_X], a.psi_out[PSI_EY_X], q, true);
+            ez_x = cpml(ez_x, a.prof[0], a.nx, PR_BE, i, a.psi_in[PSI_EZ_X], a.psi_out[PSI_EZ_X], q, true);
+        }
+        if (in_slab(j, a.ny, d)) {
+            const long long q = ((long long)k * (2 * d) + slab_idx(j, a.ny, d)) * a.nx + i;
+            ex_y = cpml(ex_y, a.prof[1], a.ny, PR_BE, j, a.psi_in[PSI_EX_Y], a.psi_out[PSI_EX_Y], q, true);
+            ez_y = cpml(ez_y, a.prof[1], a.ny, PR_BE, j, a.psi_in[PSI_EZ_Y], a.psi_out[PSI_EZ_Y], q, true);
+        }
+        if (in_slab(k, a.nz, d)) {
+            const long long q = ((long long)slab_idx(k, a.nz, d) * a.ny + j) * a.nx + i;
+            ex_z = cpml(ex_z, a.prof[2], a.nz, PR_BE, k, a.psi_in[PSI_EX_Z], a.psi_out[PSI_EX_Z], q, true);
+            ey_z = cpml(ey_z, a.prof[2], a.nz, PR_BE, k, a.psi_in[PSI_EY_Z], a.psi_out[PSI_EY_Z], q, true);
+        }
+    }
+    ex1 = t[0] * ex + t[3] * (ex_y - ex_z);
+    ey1 = t[1] * ey + t[4] * (ey_z - ey_x);
+    ez1 = t[2] * ez + t[5] * (ez_x - ez_y);
+}
+
+// ---- shared-memory views ----------------------------------------------------
+struct StageView {
+    char *p;
+    __device__ float e(int c, int row, int col) const { return reinterpret_cast<const float *>(p + OFF_E + c * E_COMP)[row * EBX + col]; }
+    __device__ float h(int c, int row, int col) const { return reinterpret_cast<const float *>(p + OFF_H + c * H_COMP)[row * HBX + col]; }
+    __device__ int cls(int row, int col) const { return reinterpret_cast<const uint8_t *>(p + OFF_C)[row * CBX + col]; }
+    __device__ int *hdr() const { return reinterpret_cast<int *>(p + OFF_HDR); }
+};
+
+struct Item {
+    int x0, y0, ka, kb;
+};
+
+__device__ __forceinline__ Item decode(const StepArgs &a, int item)
+{
+    const int ncols = a.ncx * a.ncy;
+    const int zb = item / ncols, col = item - zb * ncols;
+    Item it;
+    it.x0 = (col % a.ncx) * TX;
+    it.y0 = (col / a.ncx) * TY;
+    it.ka = zb * a.kz;
+    it.kb = min(it.ka + a.kz, a.nz);
+    return it;
+}
+
+__global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_constant__ TmaMaps m, const StepArgs a)
+{
+    extern __shared__ __align__(128) char smem_raw[];
+    // TMA destinations are kept 128-byte aligned
+    char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *tab = reinterpret_cast<float *>(smem + SM_TAB);
+    float *hnew = reinterpret_cast<float *>(smem + SM_HNEW);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SM_BAR);
+    volatile int *abort = reinterpret_cast<volatile int *>(smem + SM_MISC);
+    int *consumed = reinterpret_cast<int *>(smem + SM_MISC + 4);
+    int *issued = reinterpret_cast<int *>(smem + SM_MISC + 8);
+    auto full = [&](int s) { return smem_u32(&bars[s]); };
+    auto empty = [&](int s) { return smem_u32(&bars[NSTAGE + s]); };
+    auto stage = [&](uint32_t q) { return StageView{smem + (q % NSTAGE) * STAGE}; };
+
+    for (int q = threadIdx.x; q < a.n_classes * kNumCoef; q += NTHREADS) tab[q] = __ldg(a.table + q);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGE; ++s) {
+            mbar_init(full(s), 1);
+            mbar_init(empty(s), NCW);
+        }
+        *abort = 0;
+        *consumed = 0;
+        *issued = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == NCW) {
+        // ------------------------------ producer ------------------------------
+        if (lane == 0) {
+            uint32_t seq = 0;
+            bool ok = true;
+            auto next_stage = [&](uint32_t &s, uint32_t &ph) {
+                s = seq % NSTAGE;
+                ph = (seq / NSTAGE) & 1;
+                return mbar_wait(empty(s), ph ^ 1, abort);
+            };
+            while (ok) {
+                const int item = atomicAdd(a.work, 1);
+                if (item >= a.nitems) break;
+                const Item it = decode(a, item);
+                for (int z = it.ka - 1; z <= it.kb; ++z) {
+                    uint32_t s, ph;
+                    if (!next_stage(s, ph)) { ok = false; break; }
+                    char *st = smem + s * STAGE;
+                    int *hdr = reinterpret_cast<int *>(st + OFF_HDR);
+                    hdr[0] = item;
+                    hdr[1] = z;
+                    const bool e_only = (z == it.kb);
+                    mbar_expect_tx(full(s), e_only ? TX_E : TX_FULL);
+                    for (int c = 0; c < 3; ++c)
+                        tma_load_3d(smem_u32(st + OFF_E + c * E_COMP), &m.e[c], it.x0 - XO, it.y0 - 1, z, full(s));
+                    if (!e_only) {
+                        for (int c = 0; c < 3; ++c)
+                            tma_load_3d(smem_u32(st + OFF_H + c * H_COMP), &m.h[c], it.x0 - XO, it.y0 - 1, z, full(s));
+                        tma_load_3d(smem_u32(st + OFF_C), &m.c, it.x0 - CXO, it.y0 - 1, z, full(s));
+                    }
+                    ++seq;
+                }
+            }
+            if (ok) {
+                uint32_t s, ph;
+                if (next_stage(s, ph)) {
+                    int *hdr = reinterpret_cast<int *>(smem + s * STAGE + OFF_HDR);
+                    hdr[0] = -1;
+                    hdr[1] = 0;
+                    mbar_arrive(full(s));
+                    ++seq;
+                } else {
+                    ok = false;
+                }
+            }
+            if (!ok) {
+                *abort = 1;
+                atomicExch(a.err, 1);
+            }
+            *issued = (int)seq;
+            // the last CTA to finish handing out work resets the counters
+            __threadfence();
+            if (atomicAdd(a.work + 1, 1) == (int)gridDim.x - 1) {
+                a.work[0] = 0;
+                a.work[1] = 0;
+                __threadfence();
+            }
+        }
+    } else {
+        // ------------------------------ consumers -----------------------------
+        const int cw = warp;
+        const int lx = XO + lane;           // box column of the owned x
+        const int clx = CXO + lane;
+        uint32_t cseq = 0;
+        uint32_t hb = 0;                    // Hnew buffer index (alternates per plane)
+        auto hn = [&](uint32_t b, int c, int row, int col) -> float & {
+            return hnew[(b * 3 + c) * HNEW_PLANE + row * HBX + col];
+        };
+        auto release = [&](uint32_t q) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty(q % NSTAGE));
+        };
+        while (true) {
+            // first plane of the next item (or the end marker)
+            bool ok = mbar_wait(full(cseq % NSTAGE), (cseq / NSTAGE) & 1, abort);
+            if (!ok) *abort = 1;
+            consumer_sync();
+            if (*abort) break;
+            const StageView s0 = stage(cseq);
+            const int item = s0.hdr()[0];
+            if (item < 0) break;
+            const Item it = decode(a, item);
+            const uint32_t q0 = cseq;       // plane ka-1
+            ok = mbar_wait(full((q0 + 1) % NSTAGE), ((q0 + 1) / NSTAGE) & 1, abort);
+            if (!ok) *abort = 1;
+            consumer_sync();
+            if (*abort) break;
+            const StageView s1 = stage(q0 + 1);   // plane ka
+
+            float ecur[3][RW], hxp[RW], hyp[RW];
+            int rowj[RW];
+            for (int r = 0; r < RW; ++r) rowj[r] = it.y0 + cw * RW + r;
+            const int i = it.x0 + lane;
+            // owned E^n(ka) and, below the block, the owned Hx, Hy of plane ka-1
+            for (int r = 0; r < RW; ++r) {
+                const int row = 1 + cw * RW + r;
+                for (int c = 0; c < 3; ++c) ecur[c][r] = s1.e(c, row, lx);
+                hxp[r] = 0.f;
+                hyp[r] = 0.f;
+            }
+            if (it.ka > 0) {
+                for (int r = 0; r < RW; ++r) {
+                    const int row = 1 + cw * RW + r, j = rowj[r];
+                    if (i < a.nx && j < a.ny) {
+                        float hz;
+                        const float *t = tab + s0.cls(row, clx) * kNumCoef;
+                        h_core(a, t, i, j, it.ka - 1, false, s0.e(0, row, lx), s0.e(1, row, lx), s0.e(2, row, lx),
+                               s0.e(1, row, lx + 1), s0.e(2, row, lx + 1), s0.e(0, row + 1, lx), s0.e(2, row + 1, lx),
+                               ecur[0][r], ecur[1][r], s0.h(0, row, lx), s0.h(1, row, lx), s0.h(2, row, lx),
+                               hxp[r], hyp[r], hz);
+                    }
+                }
+            }
+            release(q0);
+            uint32_t qk = q0 + 1;           // stage of plane k
+            bool aborted = false;
+            for (int k = it.ka; k < it.kb; ++k) {
+                const uint32_t qk1 = qk + 1;
+                ok = mbar_wait(full(qk1 % NSTAGE), (qk1 / NSTAGE) & 1, abort);
+                if (!ok) *abort = 1;
+                const StageView sk = stage(qk), sk1 = stage(qk1);
+                float hnw[3][RW], enx[3][RW];
+                int cl[RW];
+                if (ok) {
+                    for (int r = 0; r < RW; ++r) {
+                        const int row = 1 + cw * RW + r, j = rowj[r];
+                        for (int c = 0; c < 3; ++c) enx[c][r] = sk1.e(c, row, lx);
+                        cl[r] = sk.cls(row, clx);
+                        const float ex_y1 = (r + 1 < RW) ? ecur[0][r + 1] : sk.e(0, row + 1, lx);
+                        const float ez_y1 = (r + 1 < RW) ? ecur[2][r + 1] : sk.e(2, row + 1, lx);
+                        const bool own = i < a.nx && j < a.ny;
+                        float hx = 0.f, hy = 0.f, hz = 0.f;
+                        if (own) {
+                            h_core(a, tab + cl[r] * kNumCoef, i, j, k, true, ecur[0][r], ecur[1][r], ecur[2][r],
+                                   sk.e(1, row, lx + 1), sk.e(2, row, lx + 1), ex_y1, ez_y1, enx[0][r], enx[1][r],
+                                   sk.h(0, row, lx), sk.h(1, row, lx), sk.h(2, row, lx), hx, hy, hz);
+                            const long long g = (long long)k * a.plane + (long long)j * a.pitch + i;
+                            a.Hout[0][g] = hx;
+                            a.Hout[1][g] = hy;
+                            a.Hout[2][g] = hz;
+                        }
+                        hnw[0][r] = hx;
+                        hnw[1][r] = hy;
+                        hnw[2][r] = hz;
+                        hn(hb, 0, row, lx) = hx;
+                        hn(hb, 1, row, lx) = hy;
+                        hn(hb, 2, row, lx) = hz;
+                    }
+                    // recomputed halo: low-y row (warp 0), low-x column (warp 1)
+                    int hrow = -1, hcol = 0, hi = 0, hj = 0;
+                    if (cw == 0) { hrow = 0; hcol = lx; hi = i; hj = it.y0 - 1; }
+                    else if (cw == 1 && lane < TY) { hrow = 1 + lane; hcol = XO - 1; hi = it.x0 - 1; hj = it.y0 + lane; }
+                    if (hrow >= 0) {
+                        float hx = 0.f, hy = 0.f, hz = 0.f;
+                        if (hi >= 0 && hj >= 0 && hi < a.nx && hj < a.ny) {
+                            const int ccol = hcol - XO + CXO;
+                            h_core(a, tab + sk.cls(hrow, ccol) * kNumCoef, hi, hj, k, false, sk.e(0, hrow, hcol),
+                                   sk.e(1, hrow, hcol), sk.e(2, hrow, hcol), sk.e(1, hrow, hcol + 1),
+                                   sk.e(2, hrow, hcol + 1), sk.e(0, hrow + 1, hcol), sk.e(2, hrow + 1, hcol),
+                                   sk1.e(0, hrow, hcol), sk1.e(1, hrow, hcol), sk.h(0, hrow, hcol),
+                                   sk.h(1, hrow, hcol), sk.h(2, hrow, hcol), hx, hy, hz);
+                        }
+                        hn(hb, 0, hrow, hcol) = hx;
+                        hn(hb, 1, hrow, hcol) = hy;
+                        hn(hb, 2, hrow, hcol) = hz;
+                    }
+                }
+                release(qk);                // this warp is done reading plane k's stage
+                consumer_sync();            // H^{n+1/2} plane k complete
+                if (*abort) { aborted = true; break; }
+                for (int r = 0; r < RW; ++r) {
+                    const int row = 1 + cw * RW + r, j = rowj[r];
+                    if (i < a.nx && j < a.ny) {
+                        const float hz_ym = r > 0 ? hnw[2][r - 1] : hn(hb, 2, row - 1, lx);
+                        const float hx_ym = r > 0 ? hnw[0][r - 1] : hn(hb, 0, row - 1, lx);
+                        float ex1, ey1, ez1;
+                        e_core(a, tab + cl[r] * kNumCoef, i, j, k, ecur[0][r], ecur[1][r], ecur[2][r], hnw[0][r],
+                               hnw[1][r], hnw[2][r], hz_ym, hx_ym, hn(hb, 2, row, lx - 1), hn(hb, 1, row, lx - 1),
+                               hxp[r], hyp[r], ex1, ey1, ez1);
+                        const long long g = (long long)k * a.plane + (long long)j * a.pitch + i;
+                        a.Eout[0][g] = ex1;
+                        a.Eout[1][g] = ey1;
+                        a.Eout[2][g] = ez1;
+                    }
+                    hxp[r] = hnw[0][r];
+                    hyp[r] = hnw[1][r];
+                    for (int c = 0; c < 3; ++c) ecur[c][r] = enx[c][r];
+                }
+                hb ^= 1u;
+                qk = qk1;
+            }
+            if (aborted) break;
+            release(qk);                    // plane kb (E only)
+            cseq = qk + 1;
+        }
+        if (threadIdx.x == 0) *consumed = (int)cseq;
+    }
+    __syncthreads();
+    // on an abort, wait (bounded) for copies still in flight before the
+    // shared memory is given back
+    if (threadIdx.x == 0 && *abort) {
+        atomicExch(a.err, 1);
+        const unsigned long long t0 = gtimer();
+        for (int q = *consumed; q < *issued; ++q) {
+            while (!mbar_try(full(q % NSTAGE), (q / NSTAGE) & 1))
+                if (gtimer() - t0 > kWaitNs) break;
+        }
+    }
+}
+
+}  // namespace
+
+int step_tile_x() { return TX; }
+int step_tile_y() { return TY; }
+int step_threads() { return NTHREADS; }
+int step_smem_bytes() { return SM_ALLOC; }
+const void *step_kernel_ptr() { return (const void *)step_tma_kernel; }
+
+cudaError_t launch_step(const TmaMaps &m, const StepArgs &a, int grid, cudaStream_t s)
+{
+    step_tma_kernel<<<grid, NTHREADS, SM_ALLOC, s>>>(m, a);
+    return cudaGetLastError();
+}
+
+}  // namespace fdtd
