@@ -14,9 +14,9 @@ namespace fdtd {
 constexpr int kNumCoef = 9;
 constexpr int kMaxClasses = 256;
 
-// Auxiliary CPML fields, one per (component, derivative axis).  The slab of
-// axis u holds 2*d cells along u: s = i for i < d, s = i - (n - 2d) for
-// i >= n - d.  Layouts: x slab [k][j][s], y slab [k][s][i], z slab [s][j][i].
+// Auxiliary CPML fields, one per (component, derivative axis), stored as
+// full arrays with the fields' pitch (only entries inside the layer of their
+// axis are ever read or written), so TMA boxes address them like the fields.
 enum Psi {
     PSI_HY_X = 0, PSI_HZ_X, PSI_EY_X, PSI_EZ_X,
     PSI_HX_Y, PSI_HZ_Y, PSI_EX_Y, PSI_EZ_Y,
@@ -40,10 +40,15 @@ constexpr int CBX = TX + 16, CBY = TY + 1;   // class box: x0-16 .. x0+TX-1
 }  // namespace geom
 
 // TMA descriptors of the current input buffers: E (E box), H (H box), class
+// plus the CPML auxiliaries of each axis u (slots u*2, u*2+1): H-type with
+// the H box, E-type with the tile box (x order: HY_X HZ_X | EY_X EZ_X,
+// y: HX_Y HZ_Y | EX_Y EZ_Y, z: HX_Z HY_Z | EX_Z EY_Z)
 struct TmaMaps {
     CUtensorMap e[3];
     CUtensorMap h[3];
     CUtensorMap c;
+    CUtensorMap ph[6];
+    CUtensorMap pe[6];
 };
 
 struct StepArgs {
@@ -102,7 +107,7 @@ cudaError_t launch_step(const TmaMaps &m, const StepArgs &a, int grid, cudaStrea
 int step_tile_x();
 int step_tile_y();
 int step_threads();
-int step_smem_bytes();
+int step_smem_bytes(int n_classes, int d);
 const void *step_kernel_ptr();
 // fdtd_edges.cu
 cudaError_t launch_edges(const EdgeArgs &a, cudaStream_t s);

@@ -96,14 +96,9 @@ struct Plan {
     size_t field, cls, table, prof[3], psi[fdtd::PSI_COUNT], src, samples, probes, out, step, work, total;
 };
 
-size_t psi_elems(const fdtd_grid *g, int which)
+size_t psi_elems(const fdtd_grid *g, int)
 {
-    const size_t d2 = 2 * (size_t)g->d;
-    const int axis = which / 4;
-    if (g->d == 0) return 0;
-    if (axis == 0) return d2 * g->ny * g->nz;
-    if (axis == 1) return (size_t)g->nx * d2 * g->nz;
-    return (size_t)g->nx * g->ny * d2;
+    return g->d == 0 ? 0 : (size_t)g->plane * g->nz;
 }
 
 Plan make_plan(const fdtd_grid *g, int capacity)
@@ -478,13 +473,22 @@ int setup_step_kernel(fdtd_grid *g)
         }
         if (!encode_map(&g->maps[p].c, g->cls, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, g, CBX, CBY))
             return fail(g, FDTD_ECUDA, "cuTensorMapEncodeTiled failed for the class map");
+        if (g->d > 0) {
+            using namespace fdtd;
+            const int hs[6] = {PSI_HY_X, PSI_HZ_X, PSI_HX_Y, PSI_HZ_Y, PSI_HX_Z, PSI_HY_Z};
+            const int es[6] = {PSI_EY_X, PSI_EZ_X, PSI_EX_Y, PSI_EZ_Y, PSI_EX_Z, PSI_EY_Z};
+            for (int q = 0; q < 6; ++q)
+                if (!encode_map(&g->maps[p].ph[q], g->psi[p][hs[q]], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, HBX, HBY) ||
+                    !encode_map(&g->maps[p].pe[q], g->psi[p][es[q]], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, TX, TY))
+                    return fail(g, FDTD_ECUDA, "cuTensorMapEncodeTiled failed for a CPML array");
+        }
     }
     g->ncx = (g->nx + TX - 1) / TX;
     g->ncy = (g->ny + TY - 1) / TY;
     g->kz = std::min(g->nz, 16);
     const int nzb = (g->nz + g->kz - 1) / g->kz;
     g->nitems = g->ncx * g->ncy * nzb;
-    const int smem = fdtd::step_smem_bytes();
+    const int smem = fdtd::step_smem_bytes(g->n_classes, g->d);
     cudaError_t e = cudaFuncSetAttribute(fdtd::step_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int dev = 0, sms = 0, occ = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);

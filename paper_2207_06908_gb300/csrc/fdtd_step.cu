@@ -35,7 +35,7 @@ constexpr int RW = 2;                  // rows per consumer warp
 constexpr int NCW = TY / RW;           // consumer warps
 constexpr int NCONS = NCW * 32;
 constexpr int NTHREADS = NCONS + 32;   // + one producer warp
-constexpr int NSTAGE = 4;
+constexpr int NSTAGE = 3;
 
 using geom::XO;
 using geom::EBX;
@@ -50,21 +50,28 @@ constexpr int al128(int v) { return (v + 127) / 128 * 128; }
 constexpr int E_COMP = al128(EBX * EBY * 4);
 constexpr int H_COMP = al128(HBX * HBY * 4);
 constexpr int C_BYTES = al128(CBX * CBY);
+constexpr int PE_BYTES = al128(TX * TY * 4);         // E-type psi box: the tile itself
 constexpr int OFF_E = 0;
 constexpr int OFF_H = 3 * E_COMP;
 constexpr int OFF_C = OFF_H + 3 * H_COMP;
-constexpr int OFF_HDR = OFF_C + C_BYTES;
+constexpr int OFF_PH = OFF_C + C_BYTES;              // 2 H-type psi boxes (H box geometry)
+constexpr int OFF_PE = OFF_PH + 2 * H_COMP;          // 2 E-type psi boxes
+constexpr int OFF_HDR = OFF_PE + 2 * PE_BYTES;
 constexpr int STAGE = al128(OFF_HDR + 16);
 constexpr uint32_t TX_E = 3u * EBX * EBY * 4;
 constexpr uint32_t TX_FULL = TX_E + 3u * HBX * HBY * 4 + CBX * CBY;
+constexpr uint32_t TX_PSI = 2u * HBX * HBY * 4 + 2u * TX * TY * 4;
 
 constexpr int SM_HNEW = NSTAGE * STAGE;              // [2][3][HBY][HBX]
 constexpr int HNEW_PLANE = HBY * HBX;
-constexpr int SM_TAB = SM_HNEW + 2 * 3 * HNEW_PLANE * 4;
-constexpr int SM_BAR = SM_TAB + kMaxClasses * kNumCoef * 4;
-constexpr int SM_MISC = SM_BAR + 2 * NSTAGE * 8;      // abort flag, consumed count
-constexpr int SM_TOTAL = SM_MISC + 16;
-constexpr int SM_ALLOC = SM_TOTAL + 128;              // room to align the base to 128 B
+constexpr int SM_BAR = SM_HNEW + 2 * 3 * HNEW_PLANE * 4;
+constexpr int SM_MISC = SM_BAR + 2 * NSTAGE * 8;      // abort flag, consumed / issued counts
+constexpr int SM_TAB = SM_MISC + 16;                  // coefficient table, then CPML profiles
+
+__host__ __device__ constexpr int smem_bytes(int n_classes, int d)
+{
+    return SM_TAB + n_classes * kNumCoef * 4 + 3 * PR_COUNT * 2 * d * 4 + 128;
+}
 
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
 
@@ -139,45 +146,68 @@ __device__ __forceinline__ void consumer_sync()
 __device__ __forceinline__ bool in_slab(int i, int n, int d) { return i < d || i >= n - d; }
 __device__ __forceinline__ int slab_idx(int i, int n, int d) { return i < d ? i : i - (n - 2 * d); }
 
+// Where the auxiliary CPML fields of one cell come from: the axis whose
+// slab the producer staged in shared memory (ph / pe: the two H-type and
+// two E-type boxes of that axis at this cell), else global memory.
+struct PsiCtx {
+    const float *prof;        // smem: [axis][PR_COUNT][2d]
+    int sax;                  // staged axis or -1
+    const float *ph0, *ph1;   // staged H-type values at this cell (if sax >= 0)
+    const float *pe0, *pe1;   // staged E-type values at this cell (own cells only)
+};
+
 // CPML convolution term (Sec. 2.2): psi <- b psi + c dif, term = dif/kappa + psi
-__device__ __forceinline__ float cpml(float dif, const float *prof, int n, int which, int i, const float *pin,
-                                      float *pout, long long q, bool write)
+__device__ __forceinline__ float cpml(float dif, const float *pr, int which, int s, int d2, float old,
+                                      float *pout, long long g, bool write)
 {
-    const float b = __ldg(prof + (which + 0) * n + i);
-    const float c = __ldg(prof + (which + 1) * n + i);
-    const float ki = __ldg(prof + (which + 2) * n + i);
-    const float p = b * __ldg(pin + q) + c * dif;
-    if (write) pout[q] = p;
+    const float b = pr[(which + 0) * d2 + s];
+    const float c = pr[(which + 1) * d2 + s];
+    const float ki = pr[(which + 2) * d2 + s];
+    const float p = b * old + c * dif;
+    if (write) pout[g] = p;
     return dif * ki + p;
 }
 
 // H^{n+1/2} of cell (i,j,k) from E^n around it (Eq. fdtdhx and its cyclic
 // analogues): Hx += db [dEy/dz - dEz/dy], Hy += db [dEz/dx - dEx/dz],
 // Hz += db [dEx/dy - dEy/dx]; differences in field units, 1/dx in db.
-__device__ __forceinline__ void h_core(const StepArgs &a, const float *t, int i, int j, int k, bool own,
-                                       float ex, float ey, float ez, float ey_x1, float ez_x1, float ex_y1,
-                                       float ez_y1, float ex_z1, float ey_z1, float hx0, float hy0, float hz0,
-                                       float &hx, float &hy, float &hz)
+__device__ __forceinline__ void h_core(const StepArgs &a, const float *t, const PsiCtx &P, int i, int j, int k,
+                                       long long g, bool own, float ex, float ey, float ez, float ey_x1,
+                                       float ez_x1, float ex_y1, float ez_y1, float ex_z1, float ey_z1, float hx0,
+                                       float hy0, float hz0, float &hx, float &hy, float &hz)
 {
     float hx_z = ey_z1 - ey, hx_y = ez_y1 - ez;
     float hy_x = ez_x1 - ez, hy_z = ex_z1 - ex;
     float hz_y = ex_y1 - ex, hz_x = ey_x1 - ey;
     const int d = a.d;
     if (d > 0) {
+        const int d2 = 2 * d;
         if (in_slab(i, a.nx, d)) {
-            const long long q = ((long long)k * a.ny + j) * (2 * d) + slab_idx(i, a.nx, d);
-            hy_x = cpml(hy_x, a.prof[0], a.nx, PR_BH, i, a.psi_in[PSI_HY_X], a.psi_out[PSI_HY_X], q, own);
-            hz_x = cpml(hz_x, a.prof[0], a.nx, PR_BH, i, a.psi_in[PSI_HZ_X], a.psi_out[PSI_HZ_X], q, own);
+            const float *pr = P.prof;
+            const int sl = slab_idx(i, a.nx, d);
+            const bool st = P.sax == 0;
+            const float o0 = st ? *P.ph0 : __ldg(a.psi_in[PSI_HY_X] + g);
+            const float o1 = st ? *P.ph1 : __ldg(a.psi_in[PSI_HZ_X] + g);
+            hy_x = cpml(hy_x, pr, PR_BH, sl, d2, o0, a.psi_out[PSI_HY_X], g, own);
+            hz_x = cpml(hz_x, pr, PR_BH, sl, d2, o1, a.psi_out[PSI_HZ_X], g, own);
         }
         if (in_slab(j, a.ny, d)) {
-            const long long q = ((long long)k * (2 * d) + slab_idx(j, a.ny, d)) * a.nx + i;
-            hx_y = cpml(hx_y, a.prof[1], a.ny, PR_BH, j, a.psi_in[PSI_HX_Y], a.psi_out[PSI_HX_Y], q, own);
-            hz_y = cpml(hz_y, a.prof[1], a.ny, PR_BH, j, a.psi_in[PSI_HZ_Y], a.psi_out[PSI_HZ_Y], q, own);
+            const float *pr = P.prof + PR_COUNT * d2;
+            const int sl = slab_idx(j, a.ny, d);
+            const bool st = P.sax == 1;
+            const float o0 = st ? *P.ph0 : __ldg(a.psi_in[PSI_HX_Y] + g);
+            const float o1 = st ? *P.ph1 : __ldg(a.psi_in[PSI_HZ_Y] + g);
+            hx_y = cpml(hx_y, pr, PR_BH, sl, d2, o0, a.psi_out[PSI_HX_Y], g, own);
+            hz_y = cpml(hz_y, pr, PR_BH, sl, d2, o1, a.psi_out[PSI_HZ_Y], g, own);
         }
         if (in_slab(k, a.nz, d)) {
-            const long long q = ((long long)slab_idx(k, a.nz, d) * a.ny + j) * a.nx + i;
-            hx_z = cpml(hx_z, a.prof[2], a.nz, PR_BH, k, a.psi_in[PSI_HX_Z], a.psi_out[PSI_HX_Z], q, own);
-            hy_z = cpml(hy_z, a.prof[2], a.nz, PR_BH, k, a.psi_in[PSI_HY_Z], a.psi_out[PSI_HY_Z], q, own);
+            const float *pr = P.prof + 2 * PR_COUNT * d2;
+            const int sl = slab_idx(k, a.nz, d);
+            const bool st = P.sax == 2;
+            const float o0 = st ? *P.ph0 : __ldg(a.psi_in[PSI_HX_Z] + g);
+            const float o1 = st ? *P.ph1 : __ldg(a.psi_in[PSI_HY_Z] + g);
+            hx_z = cpml(hx_z, pr, PR_BH, sl, d2, o0, a.psi_out[PSI_HX_Z], g, own);
+            hy_z = cpml(hy_z, pr, PR_BH, sl, d2, o1, a.psi_out[PSI_HY_Z], g, own);
         }
     }
     hx = hx0 + t[6] * (hx_z - hx_y);
@@ -187,30 +217,43 @@ __device__ __forceinline__ void h_core(const StepArgs &a, const float *t, int i,
 
 // E^{n+1} of cell (i,j,k) (Eq. fdtdex with sigma E time-averaged):
 // E = ca E + cb [curl_h H^{n+1/2}], 1/dx in cb.
-__device__ __forceinline__ void e_core(const StepArgs &a, const float *t, int i, int j, int k, float ex,
-                                       float ey, float ez, float hx, float hy, float hz, float hz_ym,
-                                       float hx_ym, float hz_xm, float hy_xm, float hx_zm, float hy_zm,
-                                       float &ex1, float &ey1, float &ez1)
+__device__ __forceinline__ void e_core(const StepArgs &a, const float *t, const PsiCtx &P, int i, int j, int k,
+                                       long long g, float ex, float ey, float ez, float hx, float hy, float hz,
+                                       float hz_ym, float hx_ym, float hz_xm, float hy_xm, float hx_zm,
+                                       float hy_zm, float &ex1, float &ey1, float &ez1)
 {
     float ex_y = hz - hz_ym, ex_z = hy - hy_zm;
     float ey_z = hx - hx_zm, ey_x = hz - hz_xm;
     float ez_x = hy - hy_xm, ez_y = hx - hx_ym;
     const int d = a.d;
     if (d > 0) {
+        const int d2 = 2 * d;
         if (in_slab(i, a.nx, d)) {
-            const long long q = ((long long)k * a.ny + j) * (2 * d) + slab_idx(i, a.nx, d);
-            ey_x = cpml(ey_x, a.prof[0], a.nx, PR_BE, i, a.psi_in[PSI_EY_X], a.psi_out[PSI_EY_X], q, true);
-            ez_x = cpml(ez_x, a.prof[0], a.nx, PR_BE, i, a.psi_in[PSI_EZ_X], a.psi_out[PSI_EZ_X], q, true);
+            const float *pr = P.prof;
+            const int sl = slab_idx(i, a.nx, d);
+            const bool st = P.sax == 0;
+            const float o0 = st ? *P.pe0 : __ldg(a.psi_in[PSI_EY_X] + g);
+            const float o1 = st ? *P.pe1 : __ldg(a.psi_in[PSI_EZ_X] + g);
+            ey_x = cpml(ey_x, pr, PR_BE, sl, d2, o0, a.psi_out[PSI_EY_X], g, true);
+            ez_x = cpml(ez_x, pr, PR_BE, sl, d2, o1, a.psi_out[PSI_EZ_X], g, true);
         }
         if (in_slab(j, a.ny, d)) {
-            const long long q = ((long long)k * (2 * d) + slab_idx(j, a.ny, d)) * a.nx + i;
-            ex_y = cpml(ex_y, a.prof[1], a.ny, PR_BE, j, a.psi_in[PSI_EX_Y], a.psi_out[PSI_EX_Y], q, true);
-            ez_y = cpml(ez_y, a.prof[1], a.ny, PR_BE, j, a.psi_in[PSI_EZ_Y], a.psi_out[PSI_EZ_Y], q, true);
+            const float *pr = P.prof + PR_COUNT * d2;
+            const int sl = slab_idx(j, a.ny, d);
+            const bool st = P.sax == 1;
+            const float o0 = st ? *P.pe0 : __ldg(a.psi_in[PSI_EX_Y] + g);
+            const float o1 = st ? *P.pe1 : __ldg(a.psi_in[PSI_EZ_Y] + g);
+            ex_y = cpml(ex_y, pr, PR_BE, sl, d2, o0, a.psi_out[PSI_EX_Y], g, true);
+            ez_y = cpml(ez_y, pr, PR_BE, sl, d2, o1, a.psi_out[PSI_EZ_Y], g, true);
         }
         if (in_slab(k, a.nz, d)) {
-            const long long q = ((long long)slab_idx(k, a.nz, d) * a.ny + j) * a.nx + i;
-            ex_z = cpml(ex_z, a.prof[2], a.nz, PR_BE, k, a.psi_in[PSI_EX_Z], a.psi_out[PSI_EX_Z], q, true);
-            ey_z = cpml(ey_z, a.prof[2], a.nz, PR_BE, k, a.psi_in[PSI_EY_Z], a.psi_out[PSI_EY_Z], q, true);
+            const float *pr = P.prof + 2 * PR_COUNT * d2;
+            const int sl = slab_idx(k, a.nz, d);
+            const bool st = P.sax == 2;
+            const float o0 = st ? *P.pe0 : __ldg(a.psi_in[PSI_EX_Z] + g);
+            const float o1 = st ? *P.pe1 : __ldg(a.psi_in[PSI_EY_Z] + g);
+            ex_z = cpml(ex_z, pr, PR_BE, sl, d2, o0, a.psi_out[PSI_EX_Z], g, true);
+            ey_z = cpml(ey_z, pr, PR_BE, sl, d2, o1, a.psi_out[PSI_EY_Z], g, true);
         }
     }
     ex1 = t[0] * ex + t[3] * (ex_y - ex_z);
@@ -224,8 +267,25 @@ struct StageView {
     __device__ float e(int c, int row, int col) const { return reinterpret_cast<const float *>(p + OFF_E + c * E_COMP)[row * EBX + col]; }
     __device__ float h(int c, int row, int col) const { return reinterpret_cast<const float *>(p + OFF_H + c * H_COMP)[row * HBX + col]; }
     __device__ int cls(int row, int col) const { return reinterpret_cast<const uint8_t *>(p + OFF_C)[row * CBX + col]; }
+    __device__ const float *ph(int slot, int row, int col) const { return reinterpret_cast<const float *>(p + OFF_PH + slot * H_COMP) + row * HBX + col; }
+    __device__ const float *pe(int slot, int row, int col) const { return reinterpret_cast<const float *>(p + OFF_PE + slot * PE_BYTES) + row * TX + col; }
     __device__ int *hdr() const { return reinterpret_cast<int *>(p + OFF_HDR); }
 };
+
+// the slab axis whose auxiliary fields are staged for plane z of a tile:
+// z when the plane is in the z layer, else x, else y when the tile (with
+// its low halo) touches that layer; -1 when none
+__device__ __forceinline__ int staged_axis(const StepArgs &a, int x0, int y0, int z)
+{
+    const int d = a.d;
+    if (d == 0 || z < 0 || z >= a.nz) return -1;
+    if (z < d || z >= a.nz - d) return 2;
+    const int xl = max(x0 - 1, 0), xh = min(x0 + TX, a.nx) - 1;
+    if (xl < d || xh >= a.nx - d) return 0;
+    const int yl = max(y0 - 1, 0), yh = min(y0 + TY, a.ny) - 1;
+    if (yl < d || yh >= a.ny - d) return 1;
+    return -1;
+}
 
 struct Item {
     int x0, y0, ka, kb;
@@ -250,6 +310,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
     char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *tab = reinterpret_cast<float *>(smem + SM_TAB);
+    float *prof = tab + a.n_classes * kNumCoef;   // [axis][PR_COUNT][2d], slab entries only
     float *hnew = reinterpret_cast<float *>(smem + SM_HNEW);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SM_BAR);
     volatile int *abort = reinterpret_cast<volatile int *>(smem + SM_MISC);
@@ -260,6 +321,15 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
     auto stage = [&](uint32_t q) { return StageView{smem + (q % NSTAGE) * STAGE}; };
 
     for (int q = threadIdx.x; q < a.n_classes * kNumCoef; q += NTHREADS) tab[q] = __ldg(a.table + q);
+    if (a.d > 0) {
+        const int d2 = 2 * a.d, per = PR_COUNT * d2;
+        for (int q = threadIdx.x; q < 3 * per; q += NTHREADS) {
+            const int u = q / per, w = (q - u * per) / d2, sl = q - u * per - w * d2;
+            const int n = u == 0 ? a.nx : (u == 1 ? a.ny : a.nz);
+            const int i = sl < a.d ? sl : n - d2 + sl;
+            prof[q] = __ldg(a.prof[u] + w * n + i);
+        }
+    }
     if (threadIdx.x == 0) {
         for (int s = 0; s < NSTAGE; ++s) {
             mbar_init(full(s), 1);
@@ -291,16 +361,26 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
                     if (!next_stage(s, ph)) { ok = false; break; }
                     char *st = smem + s * STAGE;
                     int *hdr = reinterpret_cast<int *>(st + OFF_HDR);
+                    const bool e_only = (z == it.kb);
+                    const int sax = e_only ? -1 : staged_axis(a, it.x0, it.y0, z);
                     hdr[0] = item;
                     hdr[1] = z;
-                    const bool e_only = (z == it.kb);
-                    mbar_expect_tx(full(s), e_only ? TX_E : TX_FULL);
+                    hdr[2] = sax;
+                    mbar_expect_tx(full(s), e_only ? TX_E : TX_FULL + (sax >= 0 ? TX_PSI : 0u));
                     for (int c = 0; c < 3; ++c)
                         tma_load_3d(smem_u32(st + OFF_E + c * E_COMP), &m.e[c], it.x0 - XO, it.y0 - 1, z, full(s));
                     if (!e_only) {
                         for (int c = 0; c < 3; ++c)
                             tma_load_3d(smem_u32(st + OFF_H + c * H_COMP), &m.h[c], it.x0 - XO, it.y0 - 1, z, full(s));
                         tma_load_3d(smem_u32(st + OFF_C), &m.c, it.x0 - CXO, it.y0 - 1, z, full(s));
+                    }
+                    if (sax >= 0) {
+                        for (int q = 0; q < 2; ++q) {
+                            tma_load_3d(smem_u32(st + OFF_PH + q * H_COMP), &m.ph[sax * 2 + q], it.x0 - XO,
+                                        it.y0 - 1, z, full(s));
+                            tma_load_3d(smem_u32(st + OFF_PE + q * PE_BYTES), &m.pe[sax * 2 + q], it.x0, it.y0, z,
+                                        full(s));
+                        }
                     }
                     ++seq;
                 }
@@ -378,7 +458,9 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
                     if (i < a.nx && j < a.ny) {
                         float hz;
                         const float *t = tab + s0.cls(row, clx) * kNumCoef;
-                        h_core(a, t, i, j, it.ka - 1, false, s0.e(0, row, lx), s0.e(1, row, lx), s0.e(2, row, lx),
+                        const PsiCtx P{prof, s0.hdr()[2], s0.ph(0, row, lx), s0.ph(1, row, lx), nullptr, nullptr};
+                        const long long g = (long long)(it.ka - 1) * a.plane + (long long)j * a.pitch + i;
+                        h_core(a, t, P, i, j, it.ka - 1, g, false, s0.e(0, row, lx), s0.e(1, row, lx), s0.e(2, row, lx),
                                s0.e(1, row, lx + 1), s0.e(2, row, lx + 1), s0.e(0, row + 1, lx), s0.e(2, row + 1, lx),
                                ecur[0][r], ecur[1][r], s0.h(0, row, lx), s0.h(1, row, lx), s0.h(2, row, lx),
                                hxp[r], hyp[r], hz);
@@ -393,6 +475,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
                 ok = mbar_wait(full(qk1 % NSTAGE), (qk1 / NSTAGE) & 1, abort);
                 if (!ok) *abort = 1;
                 const StageView sk = stage(qk), sk1 = stage(qk1);
+                const int sax = sk.hdr()[2];
                 float hnw[3][RW], enx[3][RW];
                 int cl[RW];
                 if (ok) {
@@ -405,10 +488,11 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
                         const bool own = i < a.nx && j < a.ny;
                         float hx = 0.f, hy = 0.f, hz = 0.f;
                         if (own) {
-                            h_core(a, tab + cl[r] * kNumCoef, i, j, k, true, ecur[0][r], ecur[1][r], ecur[2][r],
+                            const long long g = (long long)k * a.plane + (long long)j * a.pitch + i;
+                            const PsiCtx P{prof, sax, sk.ph(0, row, lx), sk.ph(1, row, lx), nullptr, nullptr};
+                            h_core(a, tab + cl[r] * kNumCoef, P, i, j, k, g, true, ecur[0][r], ecur[1][r], ecur[2][r],
                                    sk.e(1, row, lx + 1), sk.e(2, row, lx + 1), ex_y1, ez_y1, enx[0][r], enx[1][r],
                                    sk.h(0, row, lx), sk.h(1, row, lx), sk.h(2, row, lx), hx, hy, hz);
-                            const long long g = (long long)k * a.plane + (long long)j * a.pitch + i;
                             a.Hout[0][g] = hx;
                             a.Hout[1][g] = hy;
                             a.Hout[2][g] = hz;
@@ -428,7 +512,9 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
                         float hx = 0.f, hy = 0.f, hz = 0.f;
                         if (hi >= 0 && hj >= 0 && hi < a.nx && hj < a.ny) {
                             const int ccol = hcol - XO + CXO;
-                            h_core(a, tab + sk.cls(hrow, ccol) * kNumCoef, hi, hj, k, false, sk.e(0, hrow, hcol),
+                            const PsiCtx P{prof, sax, sk.ph(0, hrow, hcol), sk.ph(1, hrow, hcol), nullptr, nullptr};
+                            const long long g = (long long)k * a.plane + (long long)hj * a.pitch + hi;
+                            h_core(a, tab + sk.cls(hrow, ccol) * kNumCoef, P, hi, hj, k, g, false, sk.e(0, hrow, hcol),
                                    sk.e(1, hrow, hcol), sk.e(2, hrow, hcol), sk.e(1, hrow, hcol + 1),
                                    sk.e(2, hrow, hcol + 1), sk.e(0, hrow + 1, hcol), sk.e(2, hrow + 1, hcol),
                                    sk1.e(0, hrow, hcol), sk1.e(1, hrow, hcol), sk.h(0, hrow, hcol),
@@ -439,19 +525,19 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
                         hn(hb, 2, hrow, hcol) = hz;
                     }
                 }
-                release(qk);                // this warp is done reading plane k's stage
                 consumer_sync();            // H^{n+1/2} plane k complete
-                if (*abort) { aborted = true; break; }
+                if (*abort) { release(qk); aborted = true; break; }
                 for (int r = 0; r < RW; ++r) {
                     const int row = 1 + cw * RW + r, j = rowj[r];
                     if (i < a.nx && j < a.ny) {
                         const float hz_ym = r > 0 ? hnw[2][r - 1] : hn(hb, 2, row - 1, lx);
                         const float hx_ym = r > 0 ? hnw[0][r - 1] : hn(hb, 0, row - 1, lx);
                         float ex1, ey1, ez1;
-                        e_core(a, tab + cl[r] * kNumCoef, i, j, k, ecur[0][r], ecur[1][r], ecur[2][r], hnw[0][r],
+                        const long long g = (long long)k * a.plane + (long long)j * a.pitch + i;
+                        const PsiCtx P{prof, sax, nullptr, nullptr, sk.pe(0, row - 1, lane), sk.pe(1, row - 1, lane)};
+                        e_core(a, tab + cl[r] * kNumCoef, P, i, j, k, g, ecur[0][r], ecur[1][r], ecur[2][r], hnw[0][r],
                                hnw[1][r], hnw[2][r], hz_ym, hx_ym, hn(hb, 2, row, lx - 1), hn(hb, 1, row, lx - 1),
                                hxp[r], hyp[r], ex1, ey1, ez1);
-                        const long long g = (long long)k * a.plane + (long long)j * a.pitch + i;
                         a.Eout[0][g] = ex1;
                         a.Eout[1][g] = ey1;
                         a.Eout[2][g] = ez1;
@@ -460,6 +546,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
                     hyp[r] = hnw[1][r];
                     for (int c = 0; c < 3; ++c) ecur[c][r] = enx[c][r];
                 }
+                release(qk);                // this warp is done with plane k's stage
                 hb ^= 1u;
                 qk = qk1;
             }
@@ -487,12 +574,12 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
 int step_tile_x() { return TX; }
 int step_tile_y() { return TY; }
 int step_threads() { return NTHREADS; }
-int step_smem_bytes() { return SM_ALLOC; }
+int step_smem_bytes(int n_classes, int d) { return smem_bytes(n_classes, d); }
 const void *step_kernel_ptr() { return (const void *)step_tma_kernel; }
 
 cudaError_t launch_step(const TmaMaps &m, const StepArgs &a, int grid, cudaStream_t s)
 {
-    step_tma_kernel<<<grid, NTHREADS, SM_ALLOC, s>>>(m, a);
+    step_tma_kernel<<<grid, NTHREADS, smem_bytes(a.n_classes, a.d), s>>>(m, a);
     return cudaGetLastError();
 }
 
