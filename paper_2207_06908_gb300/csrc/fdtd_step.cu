@@ -12,12 +12,16 @@
 //     4-stage shared-memory ring: E^n (tile + 1-cell halo on every side,
 //     x start rounded down to a 16-byte boundary), H^{n-1/2} (tile + low
 //     halo) and the class bytes.  Completion is tracked by mbarriers.
-//   - Eight consumer warps: lane = x column, each warp two rows.  Per
-//     plane k they form H^{n+1/2}(k) on the tile and its low-x / low-y
-//     halo (the halo is recomputed, never exchanged), store the owned H,
-//     then form E^{n+1}(k) from that H plane and the owned column's H of
-//     plane k-1 kept in registers.  E^n(k+1) of the owned cells stays in
-//     registers for the next plane.
+//   - Eight row warps: lane = x column, each warp two rows.  Per plane k
+//     they form H^{n+1/2}(k) of their cells and store it, then E^{n+1}(k)
+//     from that H plane and the owned column's H of plane k-1 kept in
+//     registers; E^n(k+1) of the owned cells stays in registers for the
+//     next plane.  A ninth warp recomputes (never exchanges) H^{n+1/2} of
+//     the low-y row and low-x column halo meanwhile, so every warp has the
+//     same work between the two per-plane barriers.
+//   - Items that touch no CPML layer run a variant compiled without any
+//     CPML code; in the others the layer tests are hoisted per item, row
+//     and plane.
 // DRAM traffic per cell and step: 6 FP32 reads + 6 writes + 1 class byte
 // (49 B) plus the CPML auxiliaries in the layer; every halo read is an L2
 // hit.  Every wait is bounded; on a timeout the kernel records an error
@@ -32,9 +36,9 @@ namespace {
 using geom::TX;                        // tile width: one lane per column
 using geom::TY;                        // tile height
 constexpr int RW = 2;                  // rows per consumer warp
-constexpr int NCW = TY / RW;           // consumer warps
-constexpr int NCONS = NCW * 32;
-constexpr int NTHREADS = NCONS + 32;   // + one producer warp
+constexpr int NCW = TY / RW;           // row warps
+constexpr int NCONS = (NCW + 1) * 32;  // row warps + the halo warp
+constexpr int NTHREADS = NCONS + 32;   // + the producer warp
 constexpr int NSTAGE = 3;
 
 using geom::XO;
@@ -143,26 +147,23 @@ __device__ __forceinline__ void consumer_sync()
 }
 
 // ---- stencil cores ----------------------------------------------------------
-__device__ __forceinline__ bool in_slab(int i, int n, int d) { return i < d || i >= n - d; }
-__device__ __forceinline__ int slab_idx(int i, int n, int d) { return i < d ? i : i - (n - 2 * d); }
-
-// Where the auxiliary CPML fields of one cell come from: the axis whose
-// slab the producer staged in shared memory (ph / pe: the two H-type and
-// two E-type boxes of that axis at this cell), else global memory.
-struct PsiCtx {
-    const float *prof;        // smem: [axis][PR_COUNT][2d]
-    int sax;                  // staged axis or -1
-    const float *ph0, *ph1;   // staged H-type values at this cell (if sax >= 0)
-    const float *pe0, *pe1;   // staged E-type values at this cell (own cells only)
+// Layer membership of one cell, hoisted out of the per-cell work: slab
+// index per axis (-1 outside the layer) and, for the axis the producer
+// staged, the shared-memory slots of the cell's auxiliaries.
+struct Slab {
+    int sx, sy, sz;          // slab index along x, y, z or -1
+    int sax;                 // staged axis or -1
+    const float *ph0, *ph1;  // staged H-type auxiliaries of the cell
+    const float *pe0, *pe1;  // staged E-type auxiliaries of the cell (own cells)
 };
 
+__device__ __forceinline__ int slab_of(int i, int n, int d) { return i < d ? i : (i >= n - d ? i - (n - 2 * d) : -1); }
+
 // CPML convolution term (Sec. 2.2): psi <- b psi + c dif, term = dif/kappa + psi
-__device__ __forceinline__ float cpml(float dif, const float *pr, int which, int s, int d2, float old,
-                                      float *pout, long long g, bool write)
+__device__ __forceinline__ float cpml(float dif, const float *pr, int s, int d2, float old, float *pout,
+                                      long long g, bool write)
 {
-    const float b = pr[(which + 0) * d2 + s];
-    const float c = pr[(which + 1) * d2 + s];
-    const float ki = pr[(which + 2) * d2 + s];
+    const float b = pr[s], c = pr[d2 + s], ki = pr[2 * d2 + s];
     const float p = b * old + c * dif;
     if (write) pout[g] = p;
     return dif * ki + p;
@@ -171,7 +172,8 @@ __device__ __forceinline__ float cpml(float dif, const float *pr, int which, int
 // H^{n+1/2} of cell (i,j,k) from E^n around it (Eq. fdtdhx and its cyclic
 // analogues): Hx += db [dEy/dz - dEz/dy], Hy += db [dEz/dx - dEx/dz],
 // Hz += db [dEx/dy - dEy/dx]; differences in field units, 1/dx in db.
-__device__ __forceinline__ void h_core(const StepArgs &a, const float *t, const PsiCtx &P, int i, int j, int k,
+template <bool CPML>
+__device__ __forceinline__ void h_core(const StepArgs &a, const float *t, const float *prof, const Slab &L,
                                        long long g, bool own, float ex, float ey, float ez, float ey_x1,
                                        float ez_x1, float ex_y1, float ez_y1, float ex_z1, float ey_z1, float hx0,
                                        float hy0, float hz0, float &hx, float &hy, float &hz)
@@ -179,35 +181,31 @@ __device__ __forceinline__ void h_core(const StepArgs &a, const float *t, const 
     float hx_z = ey_z1 - ey, hx_y = ez_y1 - ez;
     float hy_x = ez_x1 - ez, hy_z = ex_z1 - ex;
     float hz_y = ex_y1 - ex, hz_x = ey_x1 - ey;
-    const int d = a.d;
-    if (d > 0) {
-        const int d2 = 2 * d;
-        if (in_slab(i, a.nx, d)) {
-            const float *pr = P.prof;
-            const int sl = slab_idx(i, a.nx, d);
-            const bool st = P.sax == 0;
-            const float o0 = st ? *P.ph0 : __ldg(a.psi_in[PSI_HY_X] + g);
-            const float o1 = st ? *P.ph1 : __ldg(a.psi_in[PSI_HZ_X] + g);
-            hy_x = cpml(hy_x, pr, PR_BH, sl, d2, o0, a.psi_out[PSI_HY_X], g, own);
-            hz_x = cpml(hz_x, pr, PR_BH, sl, d2, o1, a.psi_out[PSI_HZ_X], g, own);
+    if (CPML) {
+        const int d2 = 2 * a.d, per = PR_COUNT * d2;
+        if (L.sx >= 0) {
+            const float *pr = prof + PR_BH * d2;
+            const bool st = L.sax == 0;
+            const float o0 = st ? *L.ph0 : __ldg(a.psi_in[PSI_HY_X] + g);
+            const float o1 = st ? *L.ph1 : __ldg(a.psi_in[PSI_HZ_X] + g);
+            hy_x = cpml(hy_x, pr, L.sx, d2, o0, a.psi_out[PSI_HY_X], g, own);
+            hz_x = cpml(hz_x, pr, L.sx, d2, o1, a.psi_out[PSI_HZ_X], g, own);
         }
-        if (in_slab(j, a.ny, d)) {
-            const float *pr = P.prof + PR_COUNT * d2;
-            const int sl = slab_idx(j, a.ny, d);
-            const bool st = P.sax == 1;
-            const float o0 = st ? *P.ph0 : __ldg(a.psi_in[PSI_HX_Y] + g);
-            const float o1 = st ? *P.ph1 : __ldg(a.psi_in[PSI_HZ_Y] + g);
-            hx_y = cpml(hx_y, pr, PR_BH, sl, d2, o0, a.psi_out[PSI_HX_Y], g, own);
-            hz_y = cpml(hz_y, pr, PR_BH, sl, d2, o1, a.psi_out[PSI_HZ_Y], g, own);
+        if (L.sy >= 0) {
+            const float *pr = prof + per + PR_BH * d2;
+            const bool st = L.sax == 1;
+            const float o0 = st ? *L.ph0 : __ldg(a.psi_in[PSI_HX_Y] + g);
+            const float o1 = st ? *L.ph1 : __ldg(a.psi_in[PSI_HZ_Y] + g);
+            hx_y = cpml(hx_y, pr, L.sy, d2, o0, a.psi_out[PSI_HX_Y], g, own);
+            hz_y = cpml(hz_y, pr, L.sy, d2, o1, a.psi_out[PSI_HZ_Y], g, own);
         }
-        if (in_slab(k, a.nz, d)) {
-            const float *pr = P.prof + 2 * PR_COUNT * d2;
-            const int sl = slab_idx(k, a.nz, d);
-            const bool st = P.sax == 2;
-            const float o0 = st ? *P.ph0 : __ldg(a.psi_in[PSI_HX_Z] + g);
-            const float o1 = st ? *P.ph1 : __ldg(a.psi_in[PSI_HY_Z] + g);
-            hx_z = cpml(hx_z, pr, PR_BH, sl, d2, o0, a.psi_out[PSI_HX_Z], g, own);
-            hy_z = cpml(hy_z, pr, PR_BH, sl, d2, o1, a.psi_out[PSI_HY_Z], g, own);
+        if (L.sz >= 0) {
+            const float *pr = prof + 2 * per + PR_BH * d2;
+            const bool st = L.sax == 2;
+            const float o0 = st ? *L.ph0 : __ldg(a.psi_in[PSI_HX_Z] + g);
+            const float o1 = st ? *L.ph1 : __ldg(a.psi_in[PSI_HY_Z] + g);
+            hx_z = cpml(hx_z, pr, L.sz, d2, o0, a.psi_out[PSI_HX_Z], g, own);
+            hy_z = cpml(hy_z, pr, L.sz, d2, o1, a.psi_out[PSI_HY_Z], g, own);
         }
     }
     hx = hx0 + t[6] * (hx_z - hx_y);
@@ -217,7 +215,8 @@ __device__ __forceinline__ void h_core(const StepArgs &a, const float *t, const 
 
 // E^{n+1} of cell (i,j,k) (Eq. fdtdex with sigma E time-averaged):
 // E = ca E + cb [curl_h H^{n+1/2}], 1/dx in cb.
-__device__ __forceinline__ void e_core(const StepArgs &a, const float *t, const PsiCtx &P, int i, int j, int k,
+template <bool CPML>
+__device__ __forceinline__ void e_core(const StepArgs &a, const float *t, const float *prof, const Slab &L,
                                        long long g, float ex, float ey, float ez, float hx, float hy, float hz,
                                        float hz_ym, float hx_ym, float hz_xm, float hy_xm, float hx_zm,
                                        float hy_zm, float &ex1, float &ey1, float &ez1)
@@ -225,35 +224,31 @@ __device__ __forceinline__ void e_core(const StepArgs &a, const float *t, const 
     float ex_y = hz - hz_ym, ex_z = hy - hy_zm;
     float ey_z = hx - hx_zm, ey_x = hz - hz_xm;
     float ez_x = hy - hy_xm, ez_y = hx - hx_ym;
-    const int d = a.d;
-    if (d > 0) {
-        const int d2 = 2 * d;
-        if (in_slab(i, a.nx, d)) {
-            const float *pr = P.prof;
-            const int sl = slab_idx(i, a.nx, d);
-            const bool st = P.sax == 0;
-            const float o0 = st ? *P.pe0 : __ldg(a.psi_in[PSI_EY_X] + g);
-            const float o1 = st ? *P.pe1 : __ldg(a.psi_in[PSI_EZ_X] + g);
-            ey_x = cpml(ey_x, pr, PR_BE, sl, d2, o0, a.psi_out[PSI_EY_X], g, true);
-            ez_x = cpml(ez_x, pr, PR_BE, sl, d2, o1, a.psi_out[PSI_EZ_X], g, true);
+    if (CPML) {
+        const int d2 = 2 * a.d, per = PR_COUNT * d2;
+        if (L.sx >= 0) {
+            const float *pr = prof + PR_BE * d2;
+            const bool st = L.sax == 0;
+            const float o0 = st ? *L.pe0 : __ldg(a.psi_in[PSI_EY_X] + g);
+            const float o1 = st ? *L.pe1 : __ldg(a.psi_in[PSI_EZ_X] + g);
+            ey_x = cpml(ey_x, pr, L.sx, d2, o0, a.psi_out[PSI_EY_X], g, true);
+            ez_x = cpml(ez_x, pr, L.sx, d2, o1, a.psi_out[PSI_EZ_X], g, true);
         }
-        if (in_slab(j, a.ny, d)) {
-            const float *pr = P.prof + PR_COUNT * d2;
-            const int sl = slab_idx(j, a.ny, d);
-            const bool st = P.sax == 1;
-            const float o0 = st ? *P.pe0 : __ldg(a.psi_in[PSI_EX_Y] + g);
-            const float o1 = st ? *P.pe1 : __ldg(a.psi_in[PSI_EZ_Y] + g);
-            ex_y = cpml(ex_y, pr, PR_BE, sl, d2, o0, a.psi_out[PSI_EX_Y], g, true);
-            ez_y = cpml(ez_y, pr, PR_BE, sl, d2, o1, a.psi_out[PSI_EZ_Y], g, true);
+        if (L.sy >= 0) {
+            const float *pr = prof + per + PR_BE * d2;
+            const bool st = L.sax == 1;
+            const float o0 = st ? *L.pe0 : __ldg(a.psi_in[PSI_EX_Y] + g);
+            const float o1 = st ? *L.pe1 : __ldg(a.psi_in[PSI_EZ_Y] + g);
+            ex_y = cpml(ex_y, pr, L.sy, d2, o0, a.psi_out[PSI_EX_Y], g, true);
+            ez_y = cpml(ez_y, pr, L.sy, d2, o1, a.psi_out[PSI_EZ_Y], g, true);
         }
-        if (in_slab(k, a.nz, d)) {
-            const float *pr = P.prof + 2 * PR_COUNT * d2;
-            const int sl = slab_idx(k, a.nz, d);
-            const bool st = P.sax == 2;
-            const float o0 = st ? *P.pe0 : __ldg(a.psi_in[PSI_EX_Z] + g);
-            const float o1 = st ? *P.pe1 : __ldg(a.psi_in[PSI_EY_Z] + g);
-            ex_z = cpml(ex_z, pr, PR_BE, sl, d2, o0, a.psi_out[PSI_EX_Z], g, true);
-            ey_z = cpml(ey_z, pr, PR_BE, sl, d2, o1, a.psi_out[PSI_EY_Z], g, true);
+        if (L.sz >= 0) {
+            const float *pr = prof + 2 * per + PR_BE * d2;
+            const bool st = L.sax == 2;
+            const float o0 = st ? *L.pe0 : __ldg(a.psi_in[PSI_EX_Z] + g);
+            const float o1 = st ? *L.pe1 : __ldg(a.psi_in[PSI_EY_Z] + g);
+            ex_z = cpml(ex_z, pr, L.sz, d2, o0, a.psi_out[PSI_EX_Z], g, true);
+            ey_z = cpml(ey_z, pr, L.sz, d2, o1, a.psi_out[PSI_EY_Z], g, true);
         }
     }
     ex1 = t[0] * ex + t[3] * (ex_y - ex_z);
@@ -303,6 +298,174 @@ __device__ __forceinline__ Item decode(const StepArgs &a, int item)
     return it;
 }
 
+// does any cell the item updates or recomputes lie in a CPML layer
+__device__ __forceinline__ bool item_in_cpml(const StepArgs &a, const Item &it)
+{
+    const int d = a.d;
+    if (d == 0) return false;
+    if (it.ka - 1 < d || it.kb - 1 >= a.nz - d) return true;
+    const int xl = max(it.x0 - 1, 0), xh = min(it.x0 + TX, a.nx) - 1;
+    const int yl = max(it.y0 - 1, 0), yh = min(it.y0 + TY, a.ny) - 1;
+    return xl < d || xh >= a.nx - d || yl < d || yh >= a.ny - d;
+}
+
+// shared state of the consumer warps
+struct Cons {
+    const StepArgs *a;
+    char *smem;
+    const float *tab, *prof;
+    float *hnew;
+    uint64_t *bars;
+    volatile int *abort;
+    int warp, lane;
+    bool halo;               // the halo warp
+    __device__ uint32_t full(uint32_t q) const { return (uint32_t)__cvta_generic_to_shared(&bars[q % NSTAGE]); }
+    __device__ uint32_t empty(uint32_t q) const { return (uint32_t)__cvta_generic_to_shared(&bars[NSTAGE + q % NSTAGE]); }
+    __device__ StageView stage(uint32_t q) const { return StageView{smem + (q % NSTAGE) * STAGE}; }
+    __device__ float &hn(uint32_t b, int c, int row, int col) const { return hnew[(b * 3 + c) * HNEW_PLANE + row * HBX + col]; }
+    __device__ void release(uint32_t q) const
+    {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty(q));
+    }
+};
+
+// one work item: planes ka-1 .. kb are in stages q0 .. q0 + kb - ka + 1.
+// Returns false when a wait gave up (the CTA then aborts).
+template <bool CPML>
+__device__ __forceinline__ bool run_item(const Cons &C, const Item &it, uint32_t q0, uint32_t &hb)
+{
+    const StepArgs &a = *C.a;
+    const int lane = C.lane;
+    const int lx = XO + lane, clx = CXO + lane;
+    const int i = it.x0 + lane;
+    const int d = a.d;
+    const StageView s0 = C.stage(q0), s1 = C.stage(q0 + 1);
+    float ecur[3][RW], hxp[RW], hyp[RW];
+    int sy[RW];
+    const int sx = CPML ? slab_of(i, a.nx, d) : -1;
+    for (int r = 0; r < RW; ++r) {
+        sy[r] = CPML ? slab_of(it.y0 + C.warp * RW + r, a.ny, d) : -1;
+        hxp[r] = 0.f;
+        hyp[r] = 0.f;
+    }
+    if (!C.halo) {
+        // owned E^n(ka) and, below the block, the owned Hx, Hy of plane ka-1
+        for (int r = 0; r < RW; ++r) {
+            const int row = 1 + C.warp * RW + r;
+            for (int c = 0; c < 3; ++c) ecur[c][r] = s1.e(c, row, lx);
+        }
+        if (it.ka > 0) {
+            const int k = it.ka - 1;
+            const int sax = s0.hdr()[2];
+            for (int r = 0; r < RW; ++r) {
+                const int row = 1 + C.warp * RW + r, j = it.y0 + C.warp * RW + r;
+                if (i < a.nx && j < a.ny) {
+                    float hz;
+                    const Slab L{sx, sy[r], CPML ? slab_of(k, a.nz, d) : -1, sax, s0.ph(0, row, lx),
+                                 s0.ph(1, row, lx), nullptr, nullptr};
+                    const long long g = (long long)k * a.plane + (long long)j * a.pitch + i;
+                    h_core<CPML>(a, C.tab + s0.cls(row, clx) * kNumCoef, C.prof, L, g, false, s0.e(0, row, lx),
+                                 s0.e(1, row, lx), s0.e(2, row, lx), s0.e(1, row, lx + 1), s0.e(2, row, lx + 1),
+                                 s0.e(0, row + 1, lx), s0.e(2, row + 1, lx), ecur[0][r], ecur[1][r],
+                                 s0.h(0, row, lx), s0.h(1, row, lx), s0.h(2, row, lx), hxp[r], hyp[r], hz);
+                }
+            }
+        }
+    }
+    C.release(q0);
+    uint32_t qk = q0 + 1;
+    for (int k = it.ka; k < it.kb; ++k) {
+        const uint32_t qk1 = qk + 1;
+        const bool ok = mbar_wait(C.full(qk1), (qk1 / NSTAGE) & 1, C.abort);
+        if (!ok) *C.abort = 1;
+        const StageView sk = C.stage(qk), sk1 = C.stage(qk1);
+        const int sax = CPML ? sk.hdr()[2] : -1;
+        const int sz = CPML ? slab_of(k, a.nz, d) : -1;
+        float hnw[3][RW], enx[3][RW];
+        int cl[RW];
+        if (ok && !C.halo) {
+            for (int r = 0; r < RW; ++r) {
+                const int row = 1 + C.warp * RW + r, j = it.y0 + C.warp * RW + r;
+                for (int c = 0; c < 3; ++c) enx[c][r] = sk1.e(c, row, lx);
+                cl[r] = sk.cls(row, clx);
+                const float ex_y1 = (r + 1 < RW) ? ecur[0][r + 1] : sk.e(0, row + 1, lx);
+                const float ez_y1 = (r + 1 < RW) ? ecur[2][r + 1] : sk.e(2, row + 1, lx);
+                float hx = 0.f, hy = 0.f, hz = 0.f;
+                if (i < a.nx && j < a.ny) {
+                    const long long g = (long long)k * a.plane + (long long)j * a.pitch + i;
+                    const Slab L{sx, sy[r], sz, sax, sk.ph(0, row, lx), sk.ph(1, row, lx), nullptr, nullptr};
+                    h_core<CPML>(a, C.tab + cl[r] * kNumCoef, C.prof, L, g, true, ecur[0][r], ecur[1][r],
+                                 ecur[2][r], sk.e(1, row, lx + 1), sk.e(2, row, lx + 1), ex_y1, ez_y1, enx[0][r],
+                                 enx[1][r], sk.h(0, row, lx), sk.h(1, row, lx), sk.h(2, row, lx), hx, hy, hz);
+                    a.Hout[0][g] = hx;
+                    a.Hout[1][g] = hy;
+                    a.Hout[2][g] = hz;
+                }
+                hnw[0][r] = hx;
+                hnw[1][r] = hy;
+                hnw[2][r] = hz;
+                C.hn(hb, 0, row, lx) = hx;
+                C.hn(hb, 1, row, lx) = hy;
+                C.hn(hb, 2, row, lx) = hz;
+            }
+        } else if (ok) {
+            // halo warp: low-y row (all lanes), then low-x column (TY lanes)
+            for (int pass = 0; pass < 2; ++pass) {
+                int hrow, hcol, hi, hj;
+                if (pass == 0) { hrow = 0; hcol = lx; hi = i; hj = it.y0 - 1; }
+                else { hrow = 1 + lane; hcol = XO - 1; hi = it.x0 - 1; hj = it.y0 + lane; }
+                if (pass == 1 && lane >= TY) break;
+                float hx = 0.f, hy = 0.f, hz = 0.f;
+                if (hi >= 0 && hj >= 0 && hi < a.nx && hj < a.ny) {
+                    const long long g = (long long)k * a.plane + (long long)hj * a.pitch + hi;
+                    const Slab L{CPML ? slab_of(hi, a.nx, d) : -1, CPML ? slab_of(hj, a.ny, d) : -1, sz, sax,
+                                 sk.ph(0, hrow, hcol), sk.ph(1, hrow, hcol), nullptr, nullptr};
+                    h_core<CPML>(a, C.tab + sk.cls(hrow, hcol - XO + CXO) * kNumCoef, C.prof, L, g, false,
+                                 sk.e(0, hrow, hcol), sk.e(1, hrow, hcol), sk.e(2, hrow, hcol),
+                                 sk.e(1, hrow, hcol + 1), sk.e(2, hrow, hcol + 1), sk.e(0, hrow + 1, hcol),
+                                 sk.e(2, hrow + 1, hcol), sk1.e(0, hrow, hcol), sk1.e(1, hrow, hcol),
+                                 sk.h(0, hrow, hcol), sk.h(1, hrow, hcol), sk.h(2, hrow, hcol), hx, hy, hz);
+                }
+                C.hn(hb, 0, hrow, hcol) = hx;
+                C.hn(hb, 1, hrow, hcol) = hy;
+                C.hn(hb, 2, hrow, hcol) = hz;
+            }
+        }
+        consumer_sync();            // H^{n+1/2} of plane k complete (tile + halo)
+        if (*C.abort) {
+            C.release(qk);
+            return false;
+        }
+        if (!C.halo) {
+            for (int r = 0; r < RW; ++r) {
+                const int row = 1 + C.warp * RW + r, j = it.y0 + C.warp * RW + r;
+                if (i < a.nx && j < a.ny) {
+                    const float hz_ym = r > 0 ? hnw[2][r - 1] : C.hn(hb, 2, row - 1, lx);
+                    const float hx_ym = r > 0 ? hnw[0][r - 1] : C.hn(hb, 0, row - 1, lx);
+                    const long long g = (long long)k * a.plane + (long long)j * a.pitch + i;
+                    const Slab L{sx, sy[r], sz, sax, nullptr, nullptr, sk.pe(0, row - 1, lane), sk.pe(1, row - 1, lane)};
+                    float ex1, ey1, ez1;
+                    e_core<CPML>(a, C.tab + cl[r] * kNumCoef, C.prof, L, g, ecur[0][r], ecur[1][r], ecur[2][r],
+                                 hnw[0][r], hnw[1][r], hnw[2][r], hz_ym, hx_ym, C.hn(hb, 2, row, lx - 1),
+                                 C.hn(hb, 1, row, lx - 1), hxp[r], hyp[r], ex1, ey1, ez1);
+                    a.Eout[0][g] = ex1;
+                    a.Eout[1][g] = ey1;
+                    a.Eout[2][g] = ez1;
+                }
+                hxp[r] = hnw[0][r];
+                hyp[r] = hnw[1][r];
+                for (int c = 0; c < 3; ++c) ecur[c][r] = enx[c][r];
+            }
+        }
+        C.release(qk);              // this warp is done with plane k's stage
+        hb ^= 1u;
+        qk = qk1;
+    }
+    C.release(qk);                  // plane kb (E only)
+    return true;
+}
+
 __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_constant__ TmaMaps m, const StepArgs a)
 {
     extern __shared__ __align__(128) char smem_raw[];
@@ -318,7 +481,6 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
     int *issued = reinterpret_cast<int *>(smem + SM_MISC + 8);
     auto full = [&](int s) { return smem_u32(&bars[s]); };
     auto empty = [&](int s) { return smem_u32(&bars[NSTAGE + s]); };
-    auto stage = [&](uint32_t q) { return StageView{smem + (q % NSTAGE) * STAGE}; };
 
     for (int q = threadIdx.x; q < a.n_classes * kNumCoef; q += NTHREADS) tab[q] = __ldg(a.table + q);
     if (a.d > 0) {
@@ -333,7 +495,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
     if (threadIdx.x == 0) {
         for (int s = 0; s < NSTAGE; ++s) {
             mbar_init(full(s), 1);
-            mbar_init(empty(s), NCW);
+            mbar_init(empty(s), NCW + 1);
         }
         *abort = 0;
         *consumed = 0;
@@ -342,7 +504,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
     }
     __syncthreads();
 
-    if (warp == NCW) {
+    if (warp == NCW + 1) {
         // ------------------------------ producer ------------------------------
         if (lane == 0) {
             uint32_t seq = 0;
@@ -411,148 +573,26 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
             }
         }
     } else {
-        // ------------------------------ consumers -----------------------------
-        const int cw = warp;
-        const int lx = XO + lane;           // box column of the owned x
-        const int clx = CXO + lane;
-        uint32_t cseq = 0;
-        uint32_t hb = 0;                    // Hnew buffer index (alternates per plane)
-        auto hn = [&](uint32_t b, int c, int row, int col) -> float & {
-            return hnew[(b * 3 + c) * HNEW_PLANE + row * HBX + col];
-        };
-        auto release = [&](uint32_t q) {
-            __syncwarp();
-            if (lane == 0) mbar_arrive(empty(q % NSTAGE));
-        };
+        // ------------------------- row warps and halo warp -------------------------
+        Cons C{&a, smem, tab, prof, hnew, bars, abort, warp, lane, warp == NCW};
+        uint32_t cseq = 0, hb = 0;
         while (true) {
             // first plane of the next item (or the end marker)
-            bool ok = mbar_wait(full(cseq % NSTAGE), (cseq / NSTAGE) & 1, abort);
+            bool ok = mbar_wait(C.full(cseq), (cseq / NSTAGE) & 1, abort);
             if (!ok) *abort = 1;
             consumer_sync();
             if (*abort) break;
-            const StageView s0 = stage(cseq);
-            const int item = s0.hdr()[0];
+            const int item = C.stage(cseq).hdr()[0];
             if (item < 0) break;
             const Item it = decode(a, item);
-            const uint32_t q0 = cseq;       // plane ka-1
-            ok = mbar_wait(full((q0 + 1) % NSTAGE), ((q0 + 1) / NSTAGE) & 1, abort);
+            const uint32_t q0 = cseq;
+            ok = mbar_wait(C.full(q0 + 1), ((q0 + 1) / NSTAGE) & 1, abort);
             if (!ok) *abort = 1;
             consumer_sync();
             if (*abort) break;
-            const StageView s1 = stage(q0 + 1);   // plane ka
-
-            float ecur[3][RW], hxp[RW], hyp[RW];
-            int rowj[RW];
-            for (int r = 0; r < RW; ++r) rowj[r] = it.y0 + cw * RW + r;
-            const int i = it.x0 + lane;
-            // owned E^n(ka) and, below the block, the owned Hx, Hy of plane ka-1
-            for (int r = 0; r < RW; ++r) {
-                const int row = 1 + cw * RW + r;
-                for (int c = 0; c < 3; ++c) ecur[c][r] = s1.e(c, row, lx);
-                hxp[r] = 0.f;
-                hyp[r] = 0.f;
-            }
-            if (it.ka > 0) {
-                for (int r = 0; r < RW; ++r) {
-                    const int row = 1 + cw * RW + r, j = rowj[r];
-                    if (i < a.nx && j < a.ny) {
-                        float hz;
-                        const float *t = tab + s0.cls(row, clx) * kNumCoef;
-                        const PsiCtx P{prof, s0.hdr()[2], s0.ph(0, row, lx), s0.ph(1, row, lx), nullptr, nullptr};
-                        const long long g = (long long)(it.ka - 1) * a.plane + (long long)j * a.pitch + i;
-                        h_core(a, t, P, i, j, it.ka - 1, g, false, s0.e(0, row, lx), s0.e(1, row, lx), s0.e(2, row, lx),
-                               s0.e(1, row, lx + 1), s0.e(2, row, lx + 1), s0.e(0, row + 1, lx), s0.e(2, row + 1, lx),
-                               ecur[0][r], ecur[1][r], s0.h(0, row, lx), s0.h(1, row, lx), s0.h(2, row, lx),
-                               hxp[r], hyp[r], hz);
-                    }
-                }
-            }
-            release(q0);
-            uint32_t qk = q0 + 1;           // stage of plane k
-            bool aborted = false;
-            for (int k = it.ka; k < it.kb; ++k) {
-                const uint32_t qk1 = qk + 1;
-                ok = mbar_wait(full(qk1 % NSTAGE), (qk1 / NSTAGE) & 1, abort);
-                if (!ok) *abort = 1;
-                const StageView sk = stage(qk), sk1 = stage(qk1);
-                const int sax = sk.hdr()[2];
-                float hnw[3][RW], enx[3][RW];
-                int cl[RW];
-                if (ok) {
-                    for (int r = 0; r < RW; ++r) {
-                        const int row = 1 + cw * RW + r, j = rowj[r];
-                        for (int c = 0; c < 3; ++c) enx[c][r] = sk1.e(c, row, lx);
-                        cl[r] = sk.cls(row, clx);
-                        const float ex_y1 = (r + 1 < RW) ? ecur[0][r + 1] : sk.e(0, row + 1, lx);
-                        const float ez_y1 = (r + 1 < RW) ? ecur[2][r + 1] : sk.e(2, row + 1, lx);
-                        const bool own = i < a.nx && j < a.ny;
-                        float hx = 0.f, hy = 0.f, hz = 0.f;
-                        if (own) {
-                            const long long g = (long long)k * a.plane + (long long)j * a.pitch + i;
-                            const PsiCtx P{prof, sax, sk.ph(0, row, lx), sk.ph(1, row, lx), nullptr, nullptr};
-                            h_core(a, tab + cl[r] * kNumCoef, P, i, j, k, g, true, ecur[0][r], ecur[1][r], ecur[2][r],
-                                   sk.e(1, row, lx + 1), sk.e(2, row, lx + 1), ex_y1, ez_y1, enx[0][r], enx[1][r],
-                                   sk.h(0, row, lx), sk.h(1, row, lx), sk.h(2, row, lx), hx, hy, hz);
-                            a.Hout[0][g] = hx;
-                            a.Hout[1][g] = hy;
-                            a.Hout[2][g] = hz;
-                        }
-                        hnw[0][r] = hx;
-                        hnw[1][r] = hy;
-                        hnw[2][r] = hz;
-                        hn(hb, 0, row, lx) = hx;
-                        hn(hb, 1, row, lx) = hy;
-                        hn(hb, 2, row, lx) = hz;
-                    }
-                    // recomputed halo: low-y row (warp 0), low-x column (warp 1)
-                    int hrow = -1, hcol = 0, hi = 0, hj = 0;
-                    if (cw == 0) { hrow = 0; hcol = lx; hi = i; hj = it.y0 - 1; }
-                    else if (cw == 1 && lane < TY) { hrow = 1 + lane; hcol = XO - 1; hi = it.x0 - 1; hj = it.y0 + lane; }
-                    if (hrow >= 0) {
-                        float hx = 0.f, hy = 0.f, hz = 0.f;
-                        if (hi >= 0 && hj >= 0 && hi < a.nx && hj < a.ny) {
-                            const int ccol = hcol - XO + CXO;
-                            const PsiCtx P{prof, sax, sk.ph(0, hrow, hcol), sk.ph(1, hrow, hcol), nullptr, nullptr};
-                            const long long g = (long long)k * a.plane + (long long)hj * a.pitch + hi;
-                            h_core(a, tab + sk.cls(hrow, ccol) * kNumCoef, P, hi, hj, k, g, false, sk.e(0, hrow, hcol),
-                                   sk.e(1, hrow, hcol), sk.e(2, hrow, hcol), sk.e(1, hrow, hcol + 1),
-                                   sk.e(2, hrow, hcol + 1), sk.e(0, hrow + 1, hcol), sk.e(2, hrow + 1, hcol),
-                                   sk1.e(0, hrow, hcol), sk1.e(1, hrow, hcol), sk.h(0, hrow, hcol),
-                                   sk.h(1, hrow, hcol), sk.h(2, hrow, hcol), hx, hy, hz);
-                        }
-                        hn(hb, 0, hrow, hcol) = hx;
-                        hn(hb, 1, hrow, hcol) = hy;
-                        hn(hb, 2, hrow, hcol) = hz;
-                    }
-                }
-                consumer_sync();            // H^{n+1/2} plane k complete
-                if (*abort) { release(qk); aborted = true; break; }
-                for (int r = 0; r < RW; ++r) {
-                    const int row = 1 + cw * RW + r, j = rowj[r];
-                    if (i < a.nx && j < a.ny) {
-                        const float hz_ym = r > 0 ? hnw[2][r - 1] : hn(hb, 2, row - 1, lx);
-                        const float hx_ym = r > 0 ? hnw[0][r - 1] : hn(hb, 0, row - 1, lx);
-                        float ex1, ey1, ez1;
-                        const long long g = (long long)k * a.plane + (long long)j * a.pitch + i;
-                        const PsiCtx P{prof, sax, nullptr, nullptr, sk.pe(0, row - 1, lane), sk.pe(1, row - 1, lane)};
-                        e_core(a, tab + cl[r] * kNumCoef, P, i, j, k, g, ecur[0][r], ecur[1][r], ecur[2][r], hnw[0][r],
-                               hnw[1][r], hnw[2][r], hz_ym, hx_ym, hn(hb, 2, row, lx - 1), hn(hb, 1, row, lx - 1),
-                               hxp[r], hyp[r], ex1, ey1, ez1);
-                        a.Eout[0][g] = ex1;
-                        a.Eout[1][g] = ey1;
-                        a.Eout[2][g] = ez1;
-                    }
-                    hxp[r] = hnw[0][r];
-                    hyp[r] = hnw[1][r];
-                    for (int c = 0; c < 3; ++c) ecur[c][r] = enx[c][r];
-                }
-                release(qk);                // this warp is done with plane k's stage
-                hb ^= 1u;
-                qk = qk1;
-            }
-            if (aborted) break;
-            release(qk);                    // plane kb (E only)
-            cseq = qk + 1;
+            const bool done = item_in_cpml(a, it) ? run_item<true>(C, it, q0, hb) : run_item<false>(C, it, q0, hb);
+            if (!done) break;
+            cseq = q0 + 2 + (it.kb - it.ka);
         }
         if (threadIdx.x == 0) *consumed = (int)cseq;
     }
