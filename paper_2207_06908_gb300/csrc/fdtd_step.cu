@@ -8,10 +8,12 @@
 //     order, handed out by an atomic counter to a persistent grid of
 //     (SMs x resident CTAs); all CTAs march near the same z, so the halo
 //     planes one CTA loads are still in L2 when its neighbours load them.
-//   - One producer warp streams, plane by plane, three TMA 3D boxes into a
-//     4-stage shared-memory ring: E^n (tile + 1-cell halo on every side,
-//     x start rounded down to a 16-byte boundary), H^{n-1/2} (tile + low
-//     halo) and the class bytes.  Completion is tracked by mbarriers.
+//   - One producer warp streams, plane by plane, TMA 3D boxes into two
+//     shared-memory rings tracked by mbarriers: E^n (tile + 1-cell halo on
+//     every side, x start rounded down to a 16-byte boundary) into a
+//     4-slot ring (two planes in use, two in flight), and H^{n-1/2} (tile +
+//     low halo), the class bytes and, in a CPML layer, the auxiliary fields
+//     of one axis into a 3-slot ring (one in use, two in flight).
 //   - Eight row warps: lane = x column, each warp two rows.  Per plane k
 //     they form H^{n+1/2}(k) of their cells and store it, then E^{n+1}(k)
 //     from that H plane and the owned column's H of plane k-1 kept in
@@ -39,7 +41,8 @@ constexpr int RW = 2;                  // rows per consumer warp
 constexpr int NCW = TY / RW;           // row warps
 constexpr int NCONS = (NCW + 1) * 32;  // row warps + the halo warp
 constexpr int NTHREADS = NCONS + 32;   // + the producer warp
-constexpr int NSTAGE = 3;
+constexpr int NE = 4;                  // E-plane ring: planes k, k+1 in use, two ahead
+constexpr int NH = 3;                  // H / class / CPML ring: plane k in use, two ahead
 
 using geom::XO;
 using geom::EBX;
@@ -55,22 +58,27 @@ constexpr int E_COMP = al128(EBX * EBY * 4);
 constexpr int H_COMP = al128(HBX * HBY * 4);
 constexpr int C_BYTES = al128(CBX * CBY);
 constexpr int PE_BYTES = al128(TX * TY * 4);         // E-type psi box: the tile itself
-constexpr int OFF_E = 0;
-constexpr int OFF_H = 3 * E_COMP;
-constexpr int OFF_C = OFF_H + 3 * H_COMP;
-constexpr int OFF_PH = OFF_C + C_BYTES;              // 2 H-type psi boxes (H box geometry)
-constexpr int OFF_PE = OFF_PH + 2 * H_COMP;          // 2 E-type psi boxes
-constexpr int OFF_HDR = OFF_PE + 2 * PE_BYTES;
-constexpr int STAGE = al128(OFF_HDR + 16);
+// E slot: three E boxes and a header (item, plane, staged axis)
+constexpr int OFF_HDR = 3 * E_COMP;
+constexpr int ESLOT = al128(OFF_HDR + 16);
+// H slot: three H boxes, the class box, 2 H-type and 2 E-type psi boxes
+constexpr int OFF_H = 0;
+constexpr int OFF_C = 3 * H_COMP;
+constexpr int OFF_PH = OFF_C + C_BYTES;
+constexpr int OFF_PE = OFF_PH + 2 * H_COMP;
+constexpr int HSLOT = al128(OFF_PE + 2 * PE_BYTES);
 constexpr uint32_t TX_E = 3u * EBX * EBY * 4;
-constexpr uint32_t TX_FULL = TX_E + 3u * HBX * HBY * 4 + CBX * CBY;
+constexpr uint32_t TX_H = 3u * HBX * HBY * 4 + CBX * CBY;
 constexpr uint32_t TX_PSI = 2u * HBX * HBY * 4 + 2u * TX * TY * 4;
 
-constexpr int SM_HNEW = NSTAGE * STAGE;              // [2][3][HBY][HBX]
+constexpr int SM_EH = 0;
+constexpr int SM_HH = NE * ESLOT;
+constexpr int SM_HNEW = SM_HH + NH * HSLOT;           // [2][3][HBY][HBX]
 constexpr int HNEW_PLANE = HBY * HBX;
 constexpr int SM_BAR = SM_HNEW + 2 * 3 * HNEW_PLANE * 4;
-constexpr int SM_MISC = SM_BAR + 2 * NSTAGE * 8;      // abort flag, consumed / issued counts
-constexpr int SM_TAB = SM_MISC + 16;                  // coefficient table, then CPML profiles
+constexpr int NBAR = 2 * NE + 2 * NH;                 // fullE, emptyE, fullH, emptyH
+constexpr int SM_MISC = SM_BAR + NBAR * 8;            // abort flag, consumed / issued counts
+constexpr int SM_TAB = SM_MISC + 32;                  // coefficient table, then CPML profiles
 
 __host__ __device__ constexpr int smem_bytes(int n_classes, int d)
 {
@@ -257,14 +265,17 @@ __device__ __forceinline__ void e_core(const StepArgs &a, const float *t, const 
 }
 
 // ---- shared-memory views ----------------------------------------------------
-struct StageView {
+struct EView {
     char *p;
-    __device__ float e(int c, int row, int col) const { return reinterpret_cast<const float *>(p + OFF_E + c * E_COMP)[row * EBX + col]; }
+    __device__ float e(int c, int row, int col) const { return reinterpret_cast<const float *>(p + c * E_COMP)[row * EBX + col]; }
+    __device__ int *hdr() const { return reinterpret_cast<int *>(p + OFF_HDR); }
+};
+struct HView {
+    char *p;
     __device__ float h(int c, int row, int col) const { return reinterpret_cast<const float *>(p + OFF_H + c * H_COMP)[row * HBX + col]; }
     __device__ int cls(int row, int col) const { return reinterpret_cast<const uint8_t *>(p + OFF_C)[row * CBX + col]; }
     __device__ const float *ph(int slot, int row, int col) const { return reinterpret_cast<const float *>(p + OFF_PH + slot * H_COMP) + row * HBX + col; }
     __device__ const float *pe(int slot, int row, int col) const { return reinterpret_cast<const float *>(p + OFF_PE + slot * PE_BYTES) + row * TX + col; }
-    __device__ int *hdr() const { return reinterpret_cast<int *>(p + OFF_HDR); }
 };
 
 // the slab axis whose auxiliary fields are staged for plane z of a tile:
@@ -319,28 +330,34 @@ struct Cons {
     volatile int *abort;
     int warp, lane;
     bool halo;               // the halo warp
-    __device__ uint32_t full(uint32_t q) const { return (uint32_t)__cvta_generic_to_shared(&bars[q % NSTAGE]); }
-    __device__ uint32_t empty(uint32_t q) const { return (uint32_t)__cvta_generic_to_shared(&bars[NSTAGE + q % NSTAGE]); }
-    __device__ StageView stage(uint32_t q) const { return StageView{smem + (q % NSTAGE) * STAGE}; }
+    __device__ uint32_t bar(int b) const { return (uint32_t)__cvta_generic_to_shared(&bars[b]); }
+    __device__ uint32_t fullE(uint32_t q) const { return bar(q % NE); }
+    __device__ uint32_t emptyE(uint32_t q) const { return bar(NE + q % NE); }
+    __device__ uint32_t fullH(uint32_t q) const { return bar(2 * NE + q % NH); }
+    __device__ uint32_t emptyH(uint32_t q) const { return bar(2 * NE + NH + q % NH); }
+    __device__ EView ev(uint32_t q) const { return EView{smem + SM_EH + (q % NE) * ESLOT}; }
+    __device__ HView hv(uint32_t q) const { return HView{smem + SM_HH + (q % NH) * HSLOT}; }
     __device__ float &hn(uint32_t b, int c, int row, int col) const { return hnew[(b * 3 + c) * HNEW_PLANE + row * HBX + col]; }
-    __device__ void release(uint32_t q) const
+    __device__ void arrive(uint32_t b) const
     {
         __syncwarp();
-        if (lane == 0) mbar_arrive(empty(q));
+        if (lane == 0) mbar_arrive(b);
     }
+    __device__ bool waitE(uint32_t q) const { return mbar_wait(fullE(q), (q / NE) & 1, abort); }
+    __device__ bool waitH(uint32_t q) const { return mbar_wait(fullH(q), (q / NH) & 1, abort); }
 };
 
-// one work item: planes ka-1 .. kb are in stages q0 .. q0 + kb - ka + 1.
-// Returns false when a wait gave up (the CTA then aborts).
+// one work item.  Its planes ka-1 .. kb occupy E slots qe0 .. qe0+kb-ka+1
+// and planes ka-1 .. kb-1 H slots qh0 .. qh0+kb-ka.  Returns false when a
+// wait gave up (the CTA then aborts).
 template <bool CPML>
-__device__ __forceinline__ bool run_item(const Cons &C, const Item &it, uint32_t q0, uint32_t &hb)
+__device__ __forceinline__ bool run_item(const Cons &C, const Item &it, uint32_t qe0, uint32_t qh0, uint32_t &hb)
 {
     const StepArgs &a = *C.a;
     const int lane = C.lane;
     const int lx = XO + lane, clx = CXO + lane;
     const int i = it.x0 + lane;
     const int d = a.d;
-    const StageView s0 = C.stage(q0), s1 = C.stage(q0 + 1);
     float ecur[3][RW], hxp[RW], hyp[RW];
     int sy[RW];
     const int sx = CPML ? slab_of(i, a.nx, d) : -1;
@@ -349,55 +366,62 @@ __device__ __forceinline__ bool run_item(const Cons &C, const Item &it, uint32_t
         hxp[r] = 0.f;
         hyp[r] = 0.f;
     }
-    if (!C.halo) {
+    bool ok = C.waitH(qh0);
+    if (!ok) *C.abort = 1;
+    if (ok && !C.halo) {
+        const EView e0 = C.ev(qe0), e1 = C.ev(qe0 + 1);
+        const HView h0 = C.hv(qh0);
         // owned E^n(ka) and, below the block, the owned Hx, Hy of plane ka-1
         for (int r = 0; r < RW; ++r) {
             const int row = 1 + C.warp * RW + r;
-            for (int c = 0; c < 3; ++c) ecur[c][r] = s1.e(c, row, lx);
+            for (int c = 0; c < 3; ++c) ecur[c][r] = e1.e(c, row, lx);
         }
         if (it.ka > 0) {
             const int k = it.ka - 1;
-            const int sax = s0.hdr()[2];
+            const int sax = e0.hdr()[2];
             for (int r = 0; r < RW; ++r) {
                 const int row = 1 + C.warp * RW + r, j = it.y0 + C.warp * RW + r;
                 if (i < a.nx && j < a.ny) {
                     float hz;
-                    const Slab L{sx, sy[r], CPML ? slab_of(k, a.nz, d) : -1, sax, s0.ph(0, row, lx),
-                                 s0.ph(1, row, lx), nullptr, nullptr};
+                    const Slab L{sx, sy[r], CPML ? slab_of(k, a.nz, d) : -1, sax, h0.ph(0, row, lx),
+                                 h0.ph(1, row, lx), nullptr, nullptr};
                     const long long g = (long long)k * a.plane + (long long)j * a.pitch + i;
-                    h_core<CPML>(a, C.tab + s0.cls(row, clx) * kNumCoef, C.prof, L, g, false, s0.e(0, row, lx),
-                                 s0.e(1, row, lx), s0.e(2, row, lx), s0.e(1, row, lx + 1), s0.e(2, row, lx + 1),
-                                 s0.e(0, row + 1, lx), s0.e(2, row + 1, lx), ecur[0][r], ecur[1][r],
-                                 s0.h(0, row, lx), s0.h(1, row, lx), s0.h(2, row, lx), hxp[r], hyp[r], hz);
+                    h_core<CPML>(a, C.tab + h0.cls(row, clx) * kNumCoef, C.prof, L, g, false, e0.e(0, row, lx),
+                                 e0.e(1, row, lx), e0.e(2, row, lx), e0.e(1, row, lx + 1), e0.e(2, row, lx + 1),
+                                 e0.e(0, row + 1, lx), e0.e(2, row + 1, lx), ecur[0][r], ecur[1][r],
+                                 h0.h(0, row, lx), h0.h(1, row, lx), h0.h(2, row, lx), hxp[r], hyp[r], hz);
                 }
             }
         }
     }
-    C.release(q0);
-    uint32_t qk = q0 + 1;
+    C.arrive(C.emptyE(qe0));
+    C.arrive(C.emptyH(qh0));
+    if (!ok) return false;
     for (int k = it.ka; k < it.kb; ++k) {
-        const uint32_t qk1 = qk + 1;
-        const bool ok = mbar_wait(C.full(qk1), (qk1 / NSTAGE) & 1, C.abort);
+        const uint32_t t = (uint32_t)(k - it.ka);
+        const uint32_t qe = qe0 + 1 + t, qh = qh0 + 1 + t;     // plane k
+        ok = C.waitE(qe + 1) && C.waitH(qh);
         if (!ok) *C.abort = 1;
-        const StageView sk = C.stage(qk), sk1 = C.stage(qk1);
-        const int sax = CPML ? sk.hdr()[2] : -1;
+        const EView ek = C.ev(qe), ek1 = C.ev(qe + 1);
+        const HView hk = C.hv(qh);
+        const int sax = CPML ? ek.hdr()[2] : -1;
         const int sz = CPML ? slab_of(k, a.nz, d) : -1;
         float hnw[3][RW], enx[3][RW];
         int cl[RW];
         if (ok && !C.halo) {
             for (int r = 0; r < RW; ++r) {
                 const int row = 1 + C.warp * RW + r, j = it.y0 + C.warp * RW + r;
-                for (int c = 0; c < 3; ++c) enx[c][r] = sk1.e(c, row, lx);
-                cl[r] = sk.cls(row, clx);
-                const float ex_y1 = (r + 1 < RW) ? ecur[0][r + 1] : sk.e(0, row + 1, lx);
-                const float ez_y1 = (r + 1 < RW) ? ecur[2][r + 1] : sk.e(2, row + 1, lx);
+                for (int c = 0; c < 3; ++c) enx[c][r] = ek1.e(c, row, lx);
+                cl[r] = hk.cls(row, clx);
+                const float ex_y1 = (r + 1 < RW) ? ecur[0][r + 1] : ek.e(0, row + 1, lx);
+                const float ez_y1 = (r + 1 < RW) ? ecur[2][r + 1] : ek.e(2, row + 1, lx);
                 float hx = 0.f, hy = 0.f, hz = 0.f;
                 if (i < a.nx && j < a.ny) {
                     const long long g = (long long)k * a.plane + (long long)j * a.pitch + i;
-                    const Slab L{sx, sy[r], sz, sax, sk.ph(0, row, lx), sk.ph(1, row, lx), nullptr, nullptr};
+                    const Slab L{sx, sy[r], sz, sax, hk.ph(0, row, lx), hk.ph(1, row, lx), nullptr, nullptr};
                     h_core<CPML>(a, C.tab + cl[r] * kNumCoef, C.prof, L, g, true, ecur[0][r], ecur[1][r],
-                                 ecur[2][r], sk.e(1, row, lx + 1), sk.e(2, row, lx + 1), ex_y1, ez_y1, enx[0][r],
-                                 enx[1][r], sk.h(0, row, lx), sk.h(1, row, lx), sk.h(2, row, lx), hx, hy, hz);
+                                 ecur[2][r], ek.e(1, row, lx + 1), ek.e(2, row, lx + 1), ex_y1, ez_y1, enx[0][r],
+                                 enx[1][r], hk.h(0, row, lx), hk.h(1, row, lx), hk.h(2, row, lx), hx, hy, hz);
                     a.Hout[0][g] = hx;
                     a.Hout[1][g] = hy;
                     a.Hout[2][g] = hz;
@@ -420,12 +444,12 @@ __device__ __forceinline__ bool run_item(const Cons &C, const Item &it, uint32_t
                 if (hi >= 0 && hj >= 0 && hi < a.nx && hj < a.ny) {
                     const long long g = (long long)k * a.plane + (long long)hj * a.pitch + hi;
                     const Slab L{CPML ? slab_of(hi, a.nx, d) : -1, CPML ? slab_of(hj, a.ny, d) : -1, sz, sax,
-                                 sk.ph(0, hrow, hcol), sk.ph(1, hrow, hcol), nullptr, nullptr};
-                    h_core<CPML>(a, C.tab + sk.cls(hrow, hcol - XO + CXO) * kNumCoef, C.prof, L, g, false,
-                                 sk.e(0, hrow, hcol), sk.e(1, hrow, hcol), sk.e(2, hrow, hcol),
-                                 sk.e(1, hrow, hcol + 1), sk.e(2, hrow, hcol + 1), sk.e(0, hrow + 1, hcol),
-                                 sk.e(2, hrow + 1, hcol), sk1.e(0, hrow, hcol), sk1.e(1, hrow, hcol),
-                                 sk.h(0, hrow, hcol), sk.h(1, hrow, hcol), sk.h(2, hrow, hcol), hx, hy, hz);
+                                 hk.ph(0, hrow, hcol), hk.ph(1, hrow, hcol), nullptr, nullptr};
+                    h_core<CPML>(a, C.tab + hk.cls(hrow, hcol - XO + CXO) * kNumCoef, C.prof, L, g, false,
+                                 ek.e(0, hrow, hcol), ek.e(1, hrow, hcol), ek.e(2, hrow, hcol),
+                                 ek.e(1, hrow, hcol + 1), ek.e(2, hrow, hcol + 1), ek.e(0, hrow + 1, hcol),
+                                 ek.e(2, hrow + 1, hcol), ek1.e(0, hrow, hcol), ek1.e(1, hrow, hcol),
+                                 hk.h(0, hrow, hcol), hk.h(1, hrow, hcol), hk.h(2, hrow, hcol), hx, hy, hz);
                 }
                 C.hn(hb, 0, hrow, hcol) = hx;
                 C.hn(hb, 1, hrow, hcol) = hy;
@@ -433,8 +457,9 @@ __device__ __forceinline__ bool run_item(const Cons &C, const Item &it, uint32_t
             }
         }
         consumer_sync();            // H^{n+1/2} of plane k complete (tile + halo)
+        C.arrive(C.emptyE(qe));     // E(k) is not read again
         if (*C.abort) {
-            C.release(qk);
+            C.arrive(C.emptyH(qh));
             return false;
         }
         if (!C.halo) {
@@ -444,7 +469,7 @@ __device__ __forceinline__ bool run_item(const Cons &C, const Item &it, uint32_t
                     const float hz_ym = r > 0 ? hnw[2][r - 1] : C.hn(hb, 2, row - 1, lx);
                     const float hx_ym = r > 0 ? hnw[0][r - 1] : C.hn(hb, 0, row - 1, lx);
                     const long long g = (long long)k * a.plane + (long long)j * a.pitch + i;
-                    const Slab L{sx, sy[r], sz, sax, nullptr, nullptr, sk.pe(0, row - 1, lane), sk.pe(1, row - 1, lane)};
+                    const Slab L{sx, sy[r], sz, sax, nullptr, nullptr, hk.pe(0, row - 1, lane), hk.pe(1, row - 1, lane)};
                     float ex1, ey1, ez1;
                     e_core<CPML>(a, C.tab + cl[r] * kNumCoef, C.prof, L, g, ecur[0][r], ecur[1][r], ecur[2][r],
                                  hnw[0][r], hnw[1][r], hnw[2][r], hz_ym, hx_ym, C.hn(hb, 2, row, lx - 1),
@@ -458,11 +483,10 @@ __device__ __forceinline__ bool run_item(const Cons &C, const Item &it, uint32_t
                 for (int c = 0; c < 3; ++c) ecur[c][r] = enx[c][r];
             }
         }
-        C.release(qk);              // this warp is done with plane k's stage
+        C.arrive(C.emptyH(qh));     // this warp is done with plane k's H slot
         hb ^= 1u;
-        qk = qk1;
     }
-    C.release(qk);                  // plane kb (E only)
+    C.arrive(C.emptyE(qe0 + 1 + (uint32_t)(it.kb - it.ka)));   // plane kb (E only)
     return true;
 }
 
@@ -477,10 +501,11 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
     float *hnew = reinterpret_cast<float *>(smem + SM_HNEW);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SM_BAR);
     volatile int *abort = reinterpret_cast<volatile int *>(smem + SM_MISC);
-    int *consumed = reinterpret_cast<int *>(smem + SM_MISC + 4);
-    int *issued = reinterpret_cast<int *>(smem + SM_MISC + 8);
-    auto full = [&](int s) { return smem_u32(&bars[s]); };
-    auto empty = [&](int s) { return smem_u32(&bars[NSTAGE + s]); };
+    int *cons_e = reinterpret_cast<int *>(smem + SM_MISC + 4);
+    int *cons_h = reinterpret_cast<int *>(smem + SM_MISC + 8);
+    int *iss_e = reinterpret_cast<int *>(smem + SM_MISC + 12);
+    int *iss_h = reinterpret_cast<int *>(smem + SM_MISC + 16);
+    Cons C{&a, smem, tab, prof, hnew, bars, abort, warp, lane, warp == NCW};
 
     for (int q = threadIdx.x; q < a.n_classes * kNumCoef; q += NTHREADS) tab[q] = __ldg(a.table + q);
     if (a.d > 0) {
@@ -493,13 +518,16 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
         }
     }
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NSTAGE; ++s) {
-            mbar_init(full(s), 1);
-            mbar_init(empty(s), NCW + 1);
+        for (int q = 0; q < NE; ++q) {
+            mbar_init(C.fullE(q), 1);
+            mbar_init(C.emptyE(q), NCW + 1);
+        }
+        for (int q = 0; q < NH; ++q) {
+            mbar_init(C.fullH(q), 1);
+            mbar_init(C.emptyH(q), NCW + 1);
         }
         *abort = 0;
-        *consumed = 0;
-        *issued = 0;
+        *cons_e = *cons_h = *iss_e = *iss_h = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -507,54 +535,52 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
     if (warp == NCW + 1) {
         // ------------------------------ producer ------------------------------
         if (lane == 0) {
-            uint32_t seq = 0;
+            uint32_t qe = 0, qh = 0;
             bool ok = true;
-            auto next_stage = [&](uint32_t &s, uint32_t &ph) {
-                s = seq % NSTAGE;
-                ph = (seq / NSTAGE) & 1;
-                return mbar_wait(empty(s), ph ^ 1, abort);
-            };
             while (ok) {
                 const int item = atomicAdd(a.work, 1);
                 if (item >= a.nitems) break;
                 const Item it = decode(a, item);
                 for (int z = it.ka - 1; z <= it.kb; ++z) {
-                    uint32_t s, ph;
-                    if (!next_stage(s, ph)) { ok = false; break; }
-                    char *st = smem + s * STAGE;
-                    int *hdr = reinterpret_cast<int *>(st + OFF_HDR);
                     const bool e_only = (z == it.kb);
                     const int sax = e_only ? -1 : staged_axis(a, it.x0, it.y0, z);
+                    if (!mbar_wait(C.emptyE(qe), ((qe / NE) & 1) ^ 1, abort)) { ok = false; break; }
+                    char *es = smem + SM_EH + (qe % NE) * ESLOT;
+                    int *hdr = reinterpret_cast<int *>(es + OFF_HDR);
                     hdr[0] = item;
                     hdr[1] = z;
                     hdr[2] = sax;
-                    mbar_expect_tx(full(s), e_only ? TX_E : TX_FULL + (sax >= 0 ? TX_PSI : 0u));
+                    mbar_expect_tx(C.fullE(qe), TX_E);
                     for (int c = 0; c < 3; ++c)
-                        tma_load_3d(smem_u32(st + OFF_E + c * E_COMP), &m.e[c], it.x0 - XO, it.y0 - 1, z, full(s));
-                    if (!e_only) {
-                        for (int c = 0; c < 3; ++c)
-                            tma_load_3d(smem_u32(st + OFF_H + c * H_COMP), &m.h[c], it.x0 - XO, it.y0 - 1, z, full(s));
-                        tma_load_3d(smem_u32(st + OFF_C), &m.c, it.x0 - CXO, it.y0 - 1, z, full(s));
-                    }
+                        tma_load_3d(smem_u32(es + c * E_COMP), &m.e[c], it.x0 - XO, it.y0 - 1, z, C.fullE(qe));
+                    ++qe;
+                    if (e_only) continue;
+                    if (!mbar_wait(C.emptyH(qh), ((qh / NH) & 1) ^ 1, abort)) { ok = false; break; }
+                    char *hs = smem + SM_HH + (qh % NH) * HSLOT;
+                    mbar_expect_tx(C.fullH(qh), TX_H + (sax >= 0 ? TX_PSI : 0u));
+                    for (int c = 0; c < 3; ++c)
+                        tma_load_3d(smem_u32(hs + OFF_H + c * H_COMP), &m.h[c], it.x0 - XO, it.y0 - 1, z, C.fullH(qh));
+                    tma_load_3d(smem_u32(hs + OFF_C), &m.c, it.x0 - CXO, it.y0 - 1, z, C.fullH(qh));
                     if (sax >= 0) {
                         for (int q = 0; q < 2; ++q) {
-                            tma_load_3d(smem_u32(st + OFF_PH + q * H_COMP), &m.ph[sax * 2 + q], it.x0 - XO,
-                                        it.y0 - 1, z, full(s));
-                            tma_load_3d(smem_u32(st + OFF_PE + q * PE_BYTES), &m.pe[sax * 2 + q], it.x0, it.y0, z,
-                                        full(s));
+                            tma_load_3d(smem_u32(hs + OFF_PH + q * H_COMP), &m.ph[sax * 2 + q], it.x0 - XO,
+                                        it.y0 - 1, z, C.fullH(qh));
+                            tma_load_3d(smem_u32(hs + OFF_PE + q * PE_BYTES), &m.pe[sax * 2 + q], it.x0, it.y0, z,
+                                        C.fullH(qh));
                         }
                     }
-                    ++seq;
+                    ++qh;
                 }
             }
             if (ok) {
-                uint32_t s, ph;
-                if (next_stage(s, ph)) {
-                    int *hdr = reinterpret_cast<int *>(smem + s * STAGE + OFF_HDR);
+                // end marker: an E slot whose header carries item -1
+                if (mbar_wait(C.emptyE(qe), ((qe / NE) & 1) ^ 1, abort)) {
+                    int *hdr = reinterpret_cast<int *>(smem + SM_EH + (qe % NE) * ESLOT + OFF_HDR);
                     hdr[0] = -1;
                     hdr[1] = 0;
-                    mbar_arrive(full(s));
-                    ++seq;
+                    hdr[2] = -1;
+                    mbar_arrive(C.fullE(qe));
+                    ++qe;
                 } else {
                     ok = false;
                 }
@@ -563,7 +589,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
                 *abort = 1;
                 atomicExch(a.err, 1);
             }
-            *issued = (int)seq;
+            *iss_e = (int)qe;
+            *iss_h = (int)qh;
             // the last CTA to finish handing out work resets the counters
             __threadfence();
             if (atomicAdd(a.work + 1, 1) == (int)gridDim.x - 1) {
@@ -574,27 +601,30 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
         }
     } else {
         // ------------------------- row warps and halo warp -------------------------
-        Cons C{&a, smem, tab, prof, hnew, bars, abort, warp, lane, warp == NCW};
-        uint32_t cseq = 0, hb = 0;
+        uint32_t ce = 0, ch = 0, hb = 0;
         while (true) {
             // first plane of the next item (or the end marker)
-            bool ok = mbar_wait(C.full(cseq), (cseq / NSTAGE) & 1, abort);
+            bool ok = C.waitE(ce);
             if (!ok) *abort = 1;
             consumer_sync();
             if (*abort) break;
-            const int item = C.stage(cseq).hdr()[0];
+            const int item = C.ev(ce).hdr()[0];
             if (item < 0) break;
             const Item it = decode(a, item);
-            const uint32_t q0 = cseq;
-            ok = mbar_wait(C.full(q0 + 1), ((q0 + 1) / NSTAGE) & 1, abort);
+            ok = C.waitE(ce + 1);
             if (!ok) *abort = 1;
             consumer_sync();
             if (*abort) break;
-            const bool done = item_in_cpml(a, it) ? run_item<true>(C, it, q0, hb) : run_item<false>(C, it, q0, hb);
+            const bool done = item_in_cpml(a, it) ? run_item<true>(C, it, ce, ch, hb)
+                                                  : run_item<false>(C, it, ce, ch, hb);
             if (!done) break;
-            cseq = q0 + 2 + (it.kb - it.ka);
+            ce += (uint32_t)(it.kb - it.ka) + 2;
+            ch += (uint32_t)(it.kb - it.ka) + 1;
         }
-        if (threadIdx.x == 0) *consumed = (int)cseq;
+        if (threadIdx.x == 0) {
+            *cons_e = (int)ce;
+            *cons_h = (int)ch;
+        }
     }
     __syncthreads();
     // on an abort, wait (bounded) for copies still in flight before the
@@ -602,10 +632,12 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
     if (threadIdx.x == 0 && *abort) {
         atomicExch(a.err, 1);
         const unsigned long long t0 = gtimer();
-        for (int q = *consumed; q < *issued; ++q) {
-            while (!mbar_try(full(q % NSTAGE), (q / NSTAGE) & 1))
+        for (int q = *cons_e; q < *iss_e; ++q)
+            while (!mbar_try(C.fullE(q), (q / NE) & 1))
                 if (gtimer() - t0 > kWaitNs) break;
-        }
+        for (int q = *cons_h; q < *iss_h; ++q)
+            while (!mbar_try(C.fullH(q), (q / NH) & 1))
+                if (gtimer() - t0 > kWaitNs) break;
     }
 }
 
