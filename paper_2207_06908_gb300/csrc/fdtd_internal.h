@@ -40,15 +40,24 @@ constexpr int CBX = TX + 16, CBY = TY + 1;   // class box: x0-16 .. x0+TX-1
 }  // namespace geom
 
 // TMA descriptors of the current input buffers: E (E box), H (H box), class
-// plus the CPML auxiliaries of each axis u (slots u*2, u*2+1): H-type with
-// the H box, E-type with the tile box (x order: HY_X HZ_X | EY_X EZ_X,
-// y: HX_Y HZ_Y | EX_Y EZ_Y, z: HX_Z HY_Z | EX_Z EY_Z)
+// plus the CPML auxiliaries: z layer with the H box (HX_Z, HY_Z) and the
+// tile box (EX_Z, EY_Z); x layer (HY_X, HZ_X | EY_X, EZ_X) with a box
+// narrowed to the layer along x; y layer (HX_Y, HZ_Y | EX_Y, EZ_Y) with a
+// box narrowed to the layer along y
 struct TmaMaps {
     CUtensorMap e[3];
     CUtensorMap h[3];
     CUtensorMap c;
-    CUtensorMap ph[6];
-    CUtensorMap pe[6];
+    CUtensorMap zh[2], ze[2];
+    CUtensorMap xh[2], xe[2];
+    CUtensorMap yh[2], ye[2];
+};
+
+// geometry of the staged CPML boxes (host-computed for the grid's layer)
+struct PsiGeom {
+    int w;                   // x-layer box width (cells, multiple of 4)
+    int hy;                  // y-layer box height (rows)
+    int xb, yb;              // bytes of one x / y box slot (128-aligned)
 };
 
 struct StepArgs {
@@ -67,10 +76,17 @@ struct StepArgs {
     const float *psi_in[PSI_COUNT];
     float *psi_out[PSI_COUNT];
     int kz;                  // planes per z block of a work item
+    int zlo, zhi;            // planes of this launch: [zlo, zhi) and [zlo2, zhi2)
+    int zlo2, zhi2;
     int ncx, ncy;            // column tiles along x, y
     int nitems;              // (z blocks) x (column tiles)
     int *work;               // [2] work counter, finished-CTA counter (self-resetting)
     int *err;                // set to 1 when a bounded wait gave up
+    PsiGeom pg;
+    int region;              // bytes of the staged-auxiliary region of one H slot
+    int ox, oy;              // byte offsets of the x and y box groups in that region
+    int zxy;                 // 1: stage the z layer together with x / y
+    int nh;                  // slots of the H / class / CPML ring (2 or 3)
 };
 
 struct SourceDesc {
@@ -107,8 +123,12 @@ cudaError_t launch_step(const TmaMaps &m, const StepArgs &a, int grid, cudaStrea
 int step_tile_x();
 int step_tile_y();
 int step_threads();
-int step_smem_bytes(int n_classes, int d);
-const void *step_kernel_ptr();
+int step_smem_bytes(int n_classes, int d, int region, int nh);
+PsiGeom step_psi_geom(int d);
+// region size and box-group offsets for a launch that stages z alone
+// (zxy = 0) or z together with the x / y layers (zxy = 1)
+void step_region(const PsiGeom &pg, int zxy, int *region, int *ox, int *oy);
+const void *step_kernel_ptr(int nh);
 // fdtd_edges.cu
 cudaError_t launch_edges(const EdgeArgs &a, cudaStream_t s);
 

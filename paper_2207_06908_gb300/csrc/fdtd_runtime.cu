@@ -65,11 +65,20 @@ struct fdtd_grid {
     fdtd::ProbeDesc *probes_d = nullptr;
     float *probe_out = nullptr;
     long long *step_d = nullptr;
-    int *work_d = nullptr;          // [2] step-kernel work counters
+    int *work_d = nullptr;          // [2 per launch] step-kernel work counters
     int *err_d = nullptr;           // bounded-wait failure flag
     fdtd::TmaMaps maps[2];          // TMA descriptors of each input parity
-    int grid_ctas = 0;
-    int ncx = 0, ncy = 0, nitems = 0;
+    fdtd::PsiGeom pg{};             // staged CPML box geometry
+    // The step runs as one launch over the planes between the z layers and,
+    // with a CPML, a second launch over the z-layer planes whose shared
+    // memory holds the z, x and y auxiliaries at once.  Both read only the
+    // input buffers and write disjoint planes.
+    struct LaunchCfg {
+        int zlo, zhi, zlo2, zhi2, kz, nitems, grid, region, ox, oy, zxy, nh;
+        int *work;
+    } lc[2] = {};
+    int n_launch = 0;
+    int ncx = 0, ncy = 0;
     int parity = 0;
     long step = 0;
     int kz = 0;
@@ -120,7 +129,7 @@ Plan make_plan(const fdtd_grid *g, int capacity)
     p.probes = take(std::max<size_t>(1, g->probes.size()) * sizeof(fdtd::ProbeDesc));
     p.out = take(std::max<size_t>(1, g->probes.size()) * (size_t)std::max(capacity, 1) * sizeof(float));
     p.step = take(sizeof(long long));
-    p.work = take(4 * sizeof(int));
+    p.work = take(8 * sizeof(int));
     p.total = off;
     return p;
 }
@@ -375,7 +384,7 @@ std::vector<float> cpml_profile(const fdtd_grid *g, int n)
     return pr;
 }
 
-fdtd::StepArgs step_args(const fdtd_grid *g, int parity)
+fdtd::StepArgs step_args(const fdtd_grid *g, int parity, int launch)
 {
     fdtd::StepArgs a{};
     a.nx = g->nx; a.ny = g->ny; a.nz = g->nz;
@@ -395,12 +404,23 @@ fdtd::StepArgs step_args(const fdtd_grid *g, int parity)
         a.psi_in[q] = g->psi[parity][q];
         a.psi_out[q] = g->psi[1 - parity][q];
     }
-    a.kz = g->kz;
+    const auto &L = g->lc[launch];
+    a.kz = L.kz;
+    a.zlo = L.zlo;
+    a.zhi = L.zhi;
+    a.zlo2 = L.zlo2;
+    a.zhi2 = L.zhi2;
     a.ncx = g->ncx;
     a.ncy = g->ncy;
-    a.nitems = g->nitems;
-    a.work = g->work_d;
+    a.nitems = L.nitems;
+    a.work = L.work;
     a.err = g->err_d;
+    a.pg = g->pg;
+    a.region = L.region;
+    a.ox = L.ox;
+    a.oy = L.oy;
+    a.zxy = L.zxy;
+    a.nh = L.nh;
     return a;
 }
 
@@ -427,7 +447,9 @@ fdtd::EdgeArgs edge_args(const fdtd_grid *g, int parity)
 
 cudaError_t enqueue_step(fdtd_grid *g, int parity, cudaStream_t s)
 {
-    cudaError_t e = fdtd::launch_step(g->maps[parity], step_args(g, parity), g->grid_ctas, s);
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < g->n_launch && e == cudaSuccess; ++l)
+        e = fdtd::launch_step(g->maps[parity], step_args(g, parity, l), g->lc[l].grid, s);
     if (e != cudaSuccess) return e;
     if (!g->srcs.empty() || !g->probes.empty()) e = fdtd::launch_edges(edge_args(g, parity), s);
     return e;
@@ -465,6 +487,7 @@ bool encode_map(CUtensorMap *m, void *base, CUtensorMapDataType dt, int esize, c
 int setup_step_kernel(fdtd_grid *g)
 {
     using namespace fdtd::geom;
+    g->pg = fdtd::step_psi_geom(g->d);
     for (int p = 0; p < 2; ++p) {
         for (int c = 0; c < 3; ++c) {
             if (!encode_map(&g->maps[p].e[c], g->F[p][c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, EBX, EBY) ||
@@ -475,29 +498,71 @@ int setup_step_kernel(fdtd_grid *g)
             return fail(g, FDTD_ECUDA, "cuTensorMapEncodeTiled failed for the class map");
         if (g->d > 0) {
             using namespace fdtd;
-            const int hs[6] = {PSI_HY_X, PSI_HZ_X, PSI_HX_Y, PSI_HZ_Y, PSI_HX_Z, PSI_HY_Z};
-            const int es[6] = {PSI_EY_X, PSI_EZ_X, PSI_EX_Y, PSI_EZ_Y, PSI_EX_Z, PSI_EY_Z};
-            for (int q = 0; q < 6; ++q)
-                if (!encode_map(&g->maps[p].ph[q], g->psi[p][hs[q]], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, HBX, HBY) ||
-                    !encode_map(&g->maps[p].pe[q], g->psi[p][es[q]], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, TX, TY))
+            const auto F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+            const int w = g->pg.w, hy = g->pg.hy;
+            struct { CUtensorMap *m; int psi, bx, by; } maps[12] = {
+                {&g->maps[p].zh[0], PSI_HX_Z, HBX, HBY}, {&g->maps[p].zh[1], PSI_HY_Z, HBX, HBY},
+                {&g->maps[p].ze[0], PSI_EX_Z, TX, TY},   {&g->maps[p].ze[1], PSI_EY_Z, TX, TY},
+                {&g->maps[p].xh[0], PSI_HY_X, w, HBY},   {&g->maps[p].xh[1], PSI_HZ_X, w, HBY},
+                {&g->maps[p].xe[0], PSI_EY_X, w, HBY},   {&g->maps[p].xe[1], PSI_EZ_X, w, HBY},
+                {&g->maps[p].yh[0], PSI_HX_Y, HBX, hy},  {&g->maps[p].yh[1], PSI_HZ_Y, HBX, hy},
+                {&g->maps[p].ye[0], PSI_EX_Y, HBX, hy},  {&g->maps[p].ye[1], PSI_EZ_Y, HBX, hy}};
+            for (auto &mm : maps)
+                if (!encode_map(mm.m, g->psi[p][mm.psi], F32, 4, g, mm.bx, mm.by))
                     return fail(g, FDTD_ECUDA, "cuTensorMapEncodeTiled failed for a CPML array");
         }
     }
     g->ncx = (g->nx + TX - 1) / TX;
     g->ncy = (g->ny + TY - 1) / TY;
-    g->kz = std::min(g->nz, 16);
-    const int nzb = (g->nz + g->kz - 1) / g->kz;
-    g->nitems = g->ncx * g->ncy * nzb;
-    const int smem = fdtd::step_smem_bytes(g->n_classes, g->d);
-    cudaError_t e = cudaFuncSetAttribute(fdtd::step_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    int dev = 0, sms = 0, occ = 0;
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    const int cols = g->ncx * g->ncy, d = g->d;
+    int dev = 0, sms = 0, smem_per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fdtd::step_kernel_ptr(), fdtd::step_threads(), smem);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e != cudaSuccess) return cuda_fail(g, e, "device query");
+    int max_smem = 0;
+    for (int l = 0; l < 2; ++l) {
+        auto &L = g->lc[l];
+        L = {};
+        L.work = g->work_d + 2 * l;
+        if (l == 0) {            // planes between the z layers (all planes without a CPML)
+            L.zlo = d;
+            L.zhi = g->nz - d;
+            L.kz = std::min(L.zhi - L.zlo, 16);
+            L.zxy = 0;
+        } else {                 // the two z layers, one block each
+            if (d == 0) break;
+            L.zlo = 0;
+            L.zhi = d;
+            L.zlo2 = g->nz - d;
+            L.zhi2 = g->nz;
+            L.kz = d;
+            L.zxy = 1;
+        }
+        const int nzb = (L.zhi - L.zlo + L.kz - 1) / L.kz + (L.zhi2 - L.zlo2 + L.kz - 1) / L.kz;
+        L.nitems = cols * nzb;
+        fdtd::step_region(g->pg, L.zxy, &L.region, &L.ox, &L.oy);
+        // three H slots (two planes of lookahead) unless that costs the
+        // second resident CTA per SM
+        L.nh = 3;
+        if (2 * (fdtd::step_smem_bytes(g->n_classes, d, L.region, 3) + 1024) > smem_per_sm &&
+            2 * (fdtd::step_smem_bytes(g->n_classes, d, L.region, 2) + 1024) <= smem_per_sm)
+            L.nh = 2;
+        max_smem = std::max(max_smem, fdtd::step_smem_bytes(g->n_classes, d, L.region, L.nh));
+        g->n_launch = l + 1;
+    }
+    for (int nh = 2; nh <= 3 && e == cudaSuccess; ++nh)
+        e = cudaFuncSetAttribute(fdtd::step_kernel_ptr(nh), cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     if (e != cudaSuccess) return cuda_fail(g, e, "step kernel setup");
-    if (occ < 1) return fail(g, FDTD_ECUDA, "step kernel does not fit on an SM");
-    g->grid_ctas = std::max(1, std::min(sms * occ, g->nitems));
+    for (int l = 0; l < g->n_launch; ++l) {
+        auto &L = g->lc[l];
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fdtd::step_kernel_ptr(L.nh), fdtd::step_threads(),
+                                                          fdtd::step_smem_bytes(g->n_classes, d, L.region, L.nh));
+        if (e != cudaSuccess) return cuda_fail(g, e, "step kernel occupancy");
+        if (occ < 1) return fail(g, FDTD_ECUDA, "step kernel does not fit on an SM");
+        L.grid = std::max(1, std::min(sms * occ, L.nitems));
+    }
     return FDTD_OK;
 }
 
@@ -672,7 +737,7 @@ int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_by
     g->probe_out = (float *)(base + p.out);
     g->step_d = (long long *)(base + p.step);
     g->work_d = (int *)(base + p.work);
-    g->err_d = g->work_d + 2;
+    g->err_d = g->work_d + 4;
     g->capacity = probe_capacity;
 
 

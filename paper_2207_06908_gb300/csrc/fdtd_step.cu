@@ -30,6 +30,8 @@
 // flag, drains its copies in flight and returns.
 #include <cuda.h>
 
+#include <algorithm>
+
 #include "fdtd_internal.h"
 
 namespace fdtd {
@@ -42,7 +44,8 @@ constexpr int NCW = TY / RW;           // row warps
 constexpr int NCONS = (NCW + 1) * 32;  // row warps + the halo warp
 constexpr int NTHREADS = NCONS + 32;   // + the producer warp
 constexpr int NE = 4;                  // E-plane ring: planes k, k+1 in use, two ahead
-constexpr int NH = 3;                  // H / class / CPML ring: plane k in use, two ahead
+constexpr int NH_MAX = 3;              // H / class / CPML ring: plane k in use, up to two ahead
+                                       // (a launch whose auxiliary region is large uses 2)
 
 using geom::XO;
 using geom::EBX;
@@ -58,31 +61,47 @@ constexpr int E_COMP = al128(EBX * EBY * 4);
 constexpr int H_COMP = al128(HBX * HBY * 4);
 constexpr int C_BYTES = al128(CBX * CBY);
 constexpr int PE_BYTES = al128(TX * TY * 4);         // E-type psi box: the tile itself
-// E slot: three E boxes and a header (item, plane, staged axis)
+// E slot: three E boxes and a header (item, plane, staged-layer flags,
+// x-box start, y-box start)
 constexpr int OFF_HDR = 3 * E_COMP;
-constexpr int ESLOT = al128(OFF_HDR + 16);
-// H slot: three H boxes, the class box, 2 H-type and 2 E-type psi boxes
+constexpr int ESLOT = al128(OFF_HDR + 32);
+// H slot: three H boxes, the class box, then the staged-auxiliary region
+// (grid dependent size).  In a z-layer plane the region holds the z boxes
+// (2 H-type with the H box, 2 E-type with the tile box); elsewhere the x
+// boxes (4, narrowed along x) followed by the y boxes (4, narrowed along y).
 constexpr int OFF_H = 0;
 constexpr int OFF_C = 3 * H_COMP;
-constexpr int OFF_PH = OFF_C + C_BYTES;
-constexpr int OFF_PE = OFF_PH + 2 * H_COMP;
-constexpr int HSLOT = al128(OFF_PE + 2 * PE_BYTES);
+constexpr int OFF_PSI = OFF_C + C_BYTES;
+constexpr int Z_BYTES = 2 * H_COMP + 2 * PE_BYTES;
 constexpr uint32_t TX_E = 3u * EBX * EBY * 4;
 constexpr uint32_t TX_H = 3u * HBX * HBY * 4 + CBX * CBY;
-constexpr uint32_t TX_PSI = 2u * HBX * HBY * 4 + 2u * TX * TY * 4;
+constexpr uint32_t TX_Z = 2u * HBX * HBY * 4 + 2u * TX * TY * 4;
+constexpr int F_Z = 1, F_X = 2, F_Y = 4;              // staged-layer flags
 
+__host__ __device__ constexpr int hslot_bytes(int region) { return al128(OFF_PSI + region); }
+
+// block-level layout: E ring, H ring, H^{n+1/2} planes, barriers, misc,
+// coefficient table, CPML profiles
 constexpr int SM_EH = 0;
 constexpr int SM_HH = NE * ESLOT;
-constexpr int SM_HNEW = SM_HH + NH * HSLOT;           // [2][3][HBY][HBX]
 constexpr int HNEW_PLANE = HBY * HBX;
-constexpr int SM_BAR = SM_HNEW + 2 * 3 * HNEW_PLANE * 4;
-constexpr int NBAR = 2 * NE + 2 * NH;                 // fullE, emptyE, fullH, emptyH
-constexpr int SM_MISC = SM_BAR + NBAR * 8;            // abort flag, consumed / issued counts
-constexpr int SM_TAB = SM_MISC + 32;                  // coefficient table, then CPML profiles
+constexpr int HNEW_BYTES = 2 * 3 * HNEW_PLANE * 4;     // [2][3][HBY][HBX]
+constexpr int NBAR = 2 * NE + 2 * NH_MAX;             // fullE, emptyE, fullH, emptyH
+struct Layout {
+    int hslot, hnew, bar, misc, tab;
+    __host__ __device__ Layout(int region, int nh)
+    {
+        hslot = hslot_bytes(region);
+        hnew = SM_HH + nh * hslot;
+        bar = hnew + HNEW_BYTES;
+        misc = bar + NBAR * 8;
+        tab = misc + 32;
+    }
+};
 
-__host__ __device__ constexpr int smem_bytes(int n_classes, int d)
+__host__ __device__ inline int smem_bytes(int n_classes, int d, int region, int nh)
 {
-    return SM_TAB + n_classes * kNumCoef * 4 + 3 * PR_COUNT * 2 * d * 4 + 128;
+    return Layout(region, nh).tab + n_classes * kNumCoef * 4 + 3 * PR_COUNT * 2 * d * 4 + 128;
 }
 
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
@@ -156,13 +175,13 @@ __device__ __forceinline__ void consumer_sync()
 
 // ---- stencil cores ----------------------------------------------------------
 // Layer membership of one cell, hoisted out of the per-cell work: slab
-// index per axis (-1 outside the layer) and, for the axis the producer
-// staged, the shared-memory slots of the cell's auxiliaries.
+// index per axis (-1 outside the layer) and, per axis, the cell's entry in
+// the staged boxes (null when not staged: read from global memory).
 struct Slab {
     int sx, sy, sz;          // slab index along x, y, z or -1
-    int sax;                 // staged axis or -1
-    const float *ph0, *ph1;  // staged H-type auxiliaries of the cell
-    const float *pe0, *pe1;  // staged E-type auxiliaries of the cell (own cells)
+    const float *base;       // staged-auxiliary region of the plane's H slot
+    int xo, yo;              // float offsets of the cell in the first x / y box, or -1
+    int zo, zeo;             // float offsets in the first z H-type / E-type box, or -1
 };
 
 __device__ __forceinline__ int slab_of(int i, int n, int d) { return i < d ? i : (i >= n - d ? i - (n - 2 * d) : -1); }
@@ -193,25 +212,22 @@ __device__ __forceinline__ void h_core(const StepArgs &a, const float *t, const 
         const int d2 = 2 * a.d, per = PR_COUNT * d2;
         if (L.sx >= 0) {
             const float *pr = prof + PR_BH * d2;
-            const bool st = L.sax == 0;
-            const float o0 = st ? *L.ph0 : __ldg(a.psi_in[PSI_HY_X] + g);
-            const float o1 = st ? *L.ph1 : __ldg(a.psi_in[PSI_HZ_X] + g);
+            const float o0 = L.xo >= 0 ? L.base[L.xo] : __ldg(a.psi_in[PSI_HY_X] + g);
+            const float o1 = L.xo >= 0 ? L.base[L.xo + a.pg.xb / 4] : __ldg(a.psi_in[PSI_HZ_X] + g);
             hy_x = cpml(hy_x, pr, L.sx, d2, o0, a.psi_out[PSI_HY_X], g, own);
             hz_x = cpml(hz_x, pr, L.sx, d2, o1, a.psi_out[PSI_HZ_X], g, own);
         }
         if (L.sy >= 0) {
             const float *pr = prof + per + PR_BH * d2;
-            const bool st = L.sax == 1;
-            const float o0 = st ? *L.ph0 : __ldg(a.psi_in[PSI_HX_Y] + g);
-            const float o1 = st ? *L.ph1 : __ldg(a.psi_in[PSI_HZ_Y] + g);
+            const float o0 = L.yo >= 0 ? L.base[L.yo] : __ldg(a.psi_in[PSI_HX_Y] + g);
+            const float o1 = L.yo >= 0 ? L.base[L.yo + a.pg.yb / 4] : __ldg(a.psi_in[PSI_HZ_Y] + g);
             hx_y = cpml(hx_y, pr, L.sy, d2, o0, a.psi_out[PSI_HX_Y], g, own);
             hz_y = cpml(hz_y, pr, L.sy, d2, o1, a.psi_out[PSI_HZ_Y], g, own);
         }
         if (L.sz >= 0) {
             const float *pr = prof + 2 * per + PR_BH * d2;
-            const bool st = L.sax == 2;
-            const float o0 = st ? *L.ph0 : __ldg(a.psi_in[PSI_HX_Z] + g);
-            const float o1 = st ? *L.ph1 : __ldg(a.psi_in[PSI_HY_Z] + g);
+            const float o0 = L.zo >= 0 ? L.base[L.zo] : __ldg(a.psi_in[PSI_HX_Z] + g);
+            const float o1 = L.zo >= 0 ? L.base[L.zo + H_COMP / 4] : __ldg(a.psi_in[PSI_HY_Z] + g);
             hx_z = cpml(hx_z, pr, L.sz, d2, o0, a.psi_out[PSI_HX_Z], g, own);
             hy_z = cpml(hy_z, pr, L.sz, d2, o1, a.psi_out[PSI_HY_Z], g, own);
         }
@@ -236,25 +252,22 @@ __device__ __forceinline__ void e_core(const StepArgs &a, const float *t, const 
         const int d2 = 2 * a.d, per = PR_COUNT * d2;
         if (L.sx >= 0) {
             const float *pr = prof + PR_BE * d2;
-            const bool st = L.sax == 0;
-            const float o0 = st ? *L.pe0 : __ldg(a.psi_in[PSI_EY_X] + g);
-            const float o1 = st ? *L.pe1 : __ldg(a.psi_in[PSI_EZ_X] + g);
+            const float o0 = L.xo >= 0 ? L.base[L.xo + 2 * (a.pg.xb / 4)] : __ldg(a.psi_in[PSI_EY_X] + g);
+            const float o1 = L.xo >= 0 ? L.base[L.xo + 3 * (a.pg.xb / 4)] : __ldg(a.psi_in[PSI_EZ_X] + g);
             ey_x = cpml(ey_x, pr, L.sx, d2, o0, a.psi_out[PSI_EY_X], g, true);
             ez_x = cpml(ez_x, pr, L.sx, d2, o1, a.psi_out[PSI_EZ_X], g, true);
         }
         if (L.sy >= 0) {
             const float *pr = prof + per + PR_BE * d2;
-            const bool st = L.sax == 1;
-            const float o0 = st ? *L.pe0 : __ldg(a.psi_in[PSI_EX_Y] + g);
-            const float o1 = st ? *L.pe1 : __ldg(a.psi_in[PSI_EZ_Y] + g);
+            const float o0 = L.yo >= 0 ? L.base[L.yo + 2 * (a.pg.yb / 4)] : __ldg(a.psi_in[PSI_EX_Y] + g);
+            const float o1 = L.yo >= 0 ? L.base[L.yo + 3 * (a.pg.yb / 4)] : __ldg(a.psi_in[PSI_EZ_Y] + g);
             ex_y = cpml(ex_y, pr, L.sy, d2, o0, a.psi_out[PSI_EX_Y], g, true);
             ez_y = cpml(ez_y, pr, L.sy, d2, o1, a.psi_out[PSI_EZ_Y], g, true);
         }
         if (L.sz >= 0) {
             const float *pr = prof + 2 * per + PR_BE * d2;
-            const bool st = L.sax == 2;
-            const float o0 = st ? *L.pe0 : __ldg(a.psi_in[PSI_EX_Z] + g);
-            const float o1 = st ? *L.pe1 : __ldg(a.psi_in[PSI_EY_Z] + g);
+            const float o0 = L.zeo >= 0 ? L.base[L.zeo] : __ldg(a.psi_in[PSI_EX_Z] + g);
+            const float o1 = L.zeo >= 0 ? L.base[L.zeo + PE_BYTES / 4] : __ldg(a.psi_in[PSI_EY_Z] + g);
             ex_z = cpml(ex_z, pr, L.sz, d2, o0, a.psi_out[PSI_EX_Z], g, true);
             ey_z = cpml(ey_z, pr, L.sz, d2, o1, a.psi_out[PSI_EY_Z], g, true);
         }
@@ -274,23 +287,72 @@ struct HView {
     char *p;
     __device__ float h(int c, int row, int col) const { return reinterpret_cast<const float *>(p + OFF_H + c * H_COMP)[row * HBX + col]; }
     __device__ int cls(int row, int col) const { return reinterpret_cast<const uint8_t *>(p + OFF_C)[row * CBX + col]; }
-    __device__ const float *ph(int slot, int row, int col) const { return reinterpret_cast<const float *>(p + OFF_PH + slot * H_COMP) + row * HBX + col; }
-    __device__ const float *pe(int slot, int row, int col) const { return reinterpret_cast<const float *>(p + OFF_PE + slot * PE_BYTES) + row * TX + col; }
+    __device__ const float *psi() const { return reinterpret_cast<const float *>(p + OFF_PSI); }
 };
 
-// the slab axis whose auxiliary fields are staged for plane z of a tile:
-// z when the plane is in the z layer, else x, else y when the tile (with
-// its low halo) touches that layer; -1 when none
-__device__ __forceinline__ int staged_axis(const StepArgs &a, int x0, int y0, int z)
+// staging of one plane, copied out of its E-slot header (the E slot may be
+// handed back to the producer before the plane's E half step)
+struct Stg {
+    int f, xs, ys;
+    __device__ explicit Stg(const int *hdr) : f(hdr[2]), xs(hdr[3]), ys(hdr[4]) {}
+    __device__ Stg(int f_, int xs_, int ys_) : f(f_), xs(xs_), ys(ys_) {}
+};
+
+// Offsets of cell (i, j) at H-box position (row, col) in the x / y boxes of
+// an item (-1 when the cell is outside that layer or outside the box); they
+// depend on the tile only, so they are formed once per item.
+__device__ __forceinline__ int x_off(const StepArgs &a, const Stg &sg, int i, int row)
+{
+    return (slab_of(i, a.nx, a.d) >= 0 && i >= sg.xs && i < sg.xs + a.pg.w) ? a.ox / 4 + row * a.pg.w + (i - sg.xs)
+                                                                             : -1;
+}
+__device__ __forceinline__ int y_off(const StepArgs &a, const Stg &sg, int x0, int i, int j)
+{
+    return (slab_of(j, a.ny, a.d) >= 0 && j >= sg.ys && j < sg.ys + a.pg.hy)
+               ? a.oy / 4 + (j - sg.ys) * HBX + (i - (x0 - XO))
+               : -1;
+}
+
+// the staging of one plane applied to a cell's precomputed offsets
+__device__ __forceinline__ Slab slab_in(const Stg &sg, const HView &hv, int sx, int sy, int sz, int xo, int yo,
+                                        int zo, int zeo)
+{
+    const bool z = sg.f & F_Z;
+    return Slab{sx, sy, sz, hv.psi(), (sg.f & F_X) ? xo : -1, (sg.f & F_Y) ? yo : -1, z ? zo : -1, z ? zeo : -1};
+}
+
+// x / y layer boxes of a tile (with its low halo): whether the tile touches
+// the layer and where the box narrowed to the layer starts
+__device__ __forceinline__ int tile_boxes(const StepArgs &a, int x0, int y0, int &xs, int &ys)
 {
     const int d = a.d;
-    if (d == 0 || z < 0 || z >= a.nz) return -1;
-    if (z < d || z >= a.nz - d) return 2;
+    int f = 0;
+    xs = 0;
+    ys = 0;
     const int xl = max(x0 - 1, 0), xh = min(x0 + TX, a.nx) - 1;
-    if (xl < d || xh >= a.nx - d) return 0;
+    if (xl < d) { f |= F_X; xs = x0 - XO; }
+    else if (xh >= a.nx - d) { f |= F_X; xs = max(x0 - 1, a.nx - d) & ~3; }
     const int yl = max(y0 - 1, 0), yh = min(y0 + TY, a.ny) - 1;
-    if (yl < d || yh >= a.ny - d) return 1;
-    return -1;
+    if (yl < d) { f |= F_Y; ys = y0 - 1; }
+    else if (yh >= a.ny - d) { f |= F_Y; ys = max(y0 - 1, a.ny - d); }
+    return f;
+}
+
+// staged-layer flags and box starts of plane z of a tile: the x and / or y
+// layer boxes of the tile, and the z boxes when the plane is in the z
+// layer (alone, unless the launch has room for all three)
+__device__ __forceinline__ void staging(const StepArgs &a, int x0, int y0, int z, int &f, int &xs, int &ys)
+{
+    f = 0;
+    xs = 0;
+    ys = 0;
+    if (a.d == 0 || z < 0 || z >= a.nz) return;
+    const bool zs = z < a.d || z >= a.nz - a.d;
+    if (zs && !a.zxy) {
+        f = F_Z;
+        return;
+    }
+    f = tile_boxes(a, x0, y0, xs, ys) | (zs ? F_Z : 0);
 }
 
 struct Item {
@@ -304,8 +366,14 @@ __device__ __forceinline__ Item decode(const StepArgs &a, int item)
     Item it;
     it.x0 = (col % a.ncx) * TX;
     it.y0 = (col / a.ncx) * TY;
-    it.ka = zb * a.kz;
-    it.kb = min(it.ka + a.kz, a.nz);
+    const int nzb1 = (a.zhi - a.zlo + a.kz - 1) / a.kz;
+    if (zb < nzb1) {
+        it.ka = a.zlo + zb * a.kz;
+        it.kb = min(it.ka + a.kz, a.zhi);
+    } else {
+        it.ka = a.zlo2 + (zb - nzb1) * a.kz;
+        it.kb = min(it.ka + a.kz, a.zhi2);
+    }
     return it;
 }
 
@@ -321,6 +389,7 @@ __device__ __forceinline__ bool item_in_cpml(const StepArgs &a, const Item &it)
 }
 
 // shared state of the consumer warps
+template <int NH>
 struct Cons {
     const StepArgs *a;
     char *smem;
@@ -330,13 +399,14 @@ struct Cons {
     volatile int *abort;
     int warp, lane;
     bool halo;               // the halo warp
+    int hslot;               // bytes per H slot
     __device__ uint32_t bar(int b) const { return (uint32_t)__cvta_generic_to_shared(&bars[b]); }
     __device__ uint32_t fullE(uint32_t q) const { return bar(q % NE); }
     __device__ uint32_t emptyE(uint32_t q) const { return bar(NE + q % NE); }
     __device__ uint32_t fullH(uint32_t q) const { return bar(2 * NE + q % NH); }
-    __device__ uint32_t emptyH(uint32_t q) const { return bar(2 * NE + NH + q % NH); }
+    __device__ uint32_t emptyH(uint32_t q) const { return bar(2 * NE + NH_MAX + q % NH); }
     __device__ EView ev(uint32_t q) const { return EView{smem + SM_EH + (q % NE) * ESLOT}; }
-    __device__ HView hv(uint32_t q) const { return HView{smem + SM_HH + (q % NH) * HSLOT}; }
+    __device__ HView hv(uint32_t q) const { return HView{smem + SM_HH + (q % NH) * hslot}; }
     __device__ float &hn(uint32_t b, int c, int row, int col) const { return hnew[(b * 3 + c) * HNEW_PLANE + row * HBX + col]; }
     __device__ void arrive(uint32_t b) const
     {
@@ -350,8 +420,8 @@ struct Cons {
 // one work item.  Its planes ka-1 .. kb occupy E slots qe0 .. qe0+kb-ka+1
 // and planes ka-1 .. kb-1 H slots qh0 .. qh0+kb-ka.  Returns false when a
 // wait gave up (the CTA then aborts).
-template <bool CPML>
-__device__ __forceinline__ bool run_item(const Cons &C, const Item &it, uint32_t qe0, uint32_t qh0, uint32_t &hb)
+template <bool CPML, int NH>
+__device__ __forceinline__ bool run_item(const Cons<NH> &C, const Item &it, uint32_t qe0, uint32_t qh0, uint32_t &hb)
 {
     const StepArgs &a = *C.a;
     const int lane = C.lane;
@@ -359,12 +429,29 @@ __device__ __forceinline__ bool run_item(const Cons &C, const Item &it, uint32_t
     const int i = it.x0 + lane;
     const int d = a.d;
     float ecur[3][RW], hxp[RW], hyp[RW];
-    int sy[RW];
+    int sy[RW], xo[RW], yo[RW];
     const int sx = CPML ? slab_of(i, a.nx, d) : -1;
+    Stg tb(0, 0, 0);                // the tile's x / y layer boxes
+    if (CPML) tb.f = tile_boxes(a, it.x0, it.y0, tb.xs, tb.ys);
     for (int r = 0; r < RW; ++r) {
-        sy[r] = CPML ? slab_of(it.y0 + C.warp * RW + r, a.ny, d) : -1;
+        const int row = 1 + C.warp * RW + r, j = it.y0 + C.warp * RW + r;
+        sy[r] = CPML ? slab_of(j, a.ny, d) : -1;
+        xo[r] = (CPML && (tb.f & F_X)) ? x_off(a, tb, i, row) : -1;
+        yo[r] = (CPML && (tb.f & F_Y)) ? y_off(a, tb, it.x0, i, j) : -1;
         hxp[r] = 0.f;
         hyp[r] = 0.f;
+    }
+    // halo cells of the halo warp: pass 0 = (i, y0-1), pass 1 = (x0-1, y0+lane)
+    int hxo[2] = {-1, -1}, hyo[2] = {-1, -1};
+    if (CPML && C.halo) {
+        if (tb.f & F_X) {
+            hxo[0] = x_off(a, tb, i, 0);
+            hxo[1] = x_off(a, tb, it.x0 - 1, 1 + lane);
+        }
+        if (tb.f & F_Y) {
+            hyo[0] = y_off(a, tb, it.x0, i, it.y0 - 1);
+            hyo[1] = y_off(a, tb, it.x0, it.x0 - 1, it.y0 + lane);
+        }
     }
     bool ok = C.waitH(qh0);
     if (!ok) *C.abort = 1;
@@ -378,13 +465,13 @@ __device__ __forceinline__ bool run_item(const Cons &C, const Item &it, uint32_t
         }
         if (it.ka > 0) {
             const int k = it.ka - 1;
-            const int sax = e0.hdr()[2];
             for (int r = 0; r < RW; ++r) {
                 const int row = 1 + C.warp * RW + r, j = it.y0 + C.warp * RW + r;
                 if (i < a.nx && j < a.ny) {
                     float hz;
-                    const Slab L{sx, sy[r], CPML ? slab_of(k, a.nz, d) : -1, sax, h0.ph(0, row, lx),
-                                 h0.ph(1, row, lx), nullptr, nullptr};
+                    const Slab L = CPML ? slab_in(Stg(e0.hdr()), h0, sx, sy[r], slab_of(k, a.nz, d), xo[r], yo[r],
+                                                  row * HBX + lx, -1)
+                                        : Slab{-1, -1, -1, nullptr, -1, -1, -1, -1};
                     const long long g = (long long)k * a.plane + (long long)j * a.pitch + i;
                     h_core<CPML>(a, C.tab + h0.cls(row, clx) * kNumCoef, C.prof, L, g, false, e0.e(0, row, lx),
                                  e0.e(1, row, lx), e0.e(2, row, lx), e0.e(1, row, lx + 1), e0.e(2, row, lx + 1),
@@ -404,8 +491,8 @@ __device__ __forceinline__ bool run_item(const Cons &C, const Item &it, uint32_t
         if (!ok) *C.abort = 1;
         const EView ek = C.ev(qe), ek1 = C.ev(qe + 1);
         const HView hk = C.hv(qh);
-        const int sax = CPML ? ek.hdr()[2] : -1;
         const int sz = CPML ? slab_of(k, a.nz, d) : -1;
+        const Stg sg(ek.hdr());
         float hnw[3][RW], enx[3][RW];
         int cl[RW];
         if (ok && !C.halo) {
@@ -418,7 +505,9 @@ __device__ __forceinline__ bool run_item(const Cons &C, const Item &it, uint32_t
                 float hx = 0.f, hy = 0.f, hz = 0.f;
                 if (i < a.nx && j < a.ny) {
                     const long long g = (long long)k * a.plane + (long long)j * a.pitch + i;
-                    const Slab L{sx, sy[r], sz, sax, hk.ph(0, row, lx), hk.ph(1, row, lx), nullptr, nullptr};
+                    const Slab L = CPML ? slab_in(sg, hk, sx, sy[r], sz, xo[r], yo[r], row * HBX + lx,
+                                                  (2 * H_COMP) / 4 + (row - 1) * TX + lane)
+                                        : Slab{-1, -1, -1, nullptr, -1, -1, -1, -1};
                     h_core<CPML>(a, C.tab + cl[r] * kNumCoef, C.prof, L, g, true, ecur[0][r], ecur[1][r],
                                  ecur[2][r], ek.e(1, row, lx + 1), ek.e(2, row, lx + 1), ex_y1, ez_y1, enx[0][r],
                                  enx[1][r], hk.h(0, row, lx), hk.h(1, row, lx), hk.h(2, row, lx), hx, hy, hz);
@@ -443,8 +532,9 @@ __device__ __forceinline__ bool run_item(const Cons &C, const Item &it, uint32_t
                 float hx = 0.f, hy = 0.f, hz = 0.f;
                 if (hi >= 0 && hj >= 0 && hi < a.nx && hj < a.ny) {
                     const long long g = (long long)k * a.plane + (long long)hj * a.pitch + hi;
-                    const Slab L{CPML ? slab_of(hi, a.nx, d) : -1, CPML ? slab_of(hj, a.ny, d) : -1, sz, sax,
-                                 hk.ph(0, hrow, hcol), hk.ph(1, hrow, hcol), nullptr, nullptr};
+                    const Slab L = CPML ? slab_in(sg, hk, slab_of(hi, a.nx, d), slab_of(hj, a.ny, d), sz, hxo[pass],
+                                                  hyo[pass], hrow * HBX + hcol, -1)
+                                        : Slab{-1, -1, -1, nullptr, -1, -1, -1, -1};
                     h_core<CPML>(a, C.tab + hk.cls(hrow, hcol - XO + CXO) * kNumCoef, C.prof, L, g, false,
                                  ek.e(0, hrow, hcol), ek.e(1, hrow, hcol), ek.e(2, hrow, hcol),
                                  ek.e(1, hrow, hcol + 1), ek.e(2, hrow, hcol + 1), ek.e(0, hrow + 1, hcol),
@@ -469,7 +559,9 @@ __device__ __forceinline__ bool run_item(const Cons &C, const Item &it, uint32_t
                     const float hz_ym = r > 0 ? hnw[2][r - 1] : C.hn(hb, 2, row - 1, lx);
                     const float hx_ym = r > 0 ? hnw[0][r - 1] : C.hn(hb, 0, row - 1, lx);
                     const long long g = (long long)k * a.plane + (long long)j * a.pitch + i;
-                    const Slab L{sx, sy[r], sz, sax, nullptr, nullptr, hk.pe(0, row - 1, lane), hk.pe(1, row - 1, lane)};
+                    const Slab L = CPML ? slab_in(sg, hk, sx, sy[r], sz, xo[r], yo[r], row * HBX + lx,
+                                                  (2 * H_COMP) / 4 + (row - 1) * TX + lane)
+                                        : Slab{-1, -1, -1, nullptr, -1, -1, -1, -1};
                     float ex1, ey1, ez1;
                     e_core<CPML>(a, C.tab + cl[r] * kNumCoef, C.prof, L, g, ecur[0][r], ecur[1][r], ecur[2][r],
                                  hnw[0][r], hnw[1][r], hnw[2][r], hz_ym, hx_ym, C.hn(hb, 2, row, lx - 1),
@@ -490,22 +582,24 @@ __device__ __forceinline__ bool run_item(const Cons &C, const Item &it, uint32_t
     return true;
 }
 
+template <int NH>
 __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_constant__ TmaMaps m, const StepArgs a)
 {
     extern __shared__ __align__(128) char smem_raw[];
     // TMA destinations are kept 128-byte aligned
     char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *tab = reinterpret_cast<float *>(smem + SM_TAB);
+    const Layout Lo(a.region, NH);
+    float *tab = reinterpret_cast<float *>(smem + Lo.tab);
     float *prof = tab + a.n_classes * kNumCoef;   // [axis][PR_COUNT][2d], slab entries only
-    float *hnew = reinterpret_cast<float *>(smem + SM_HNEW);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SM_BAR);
-    volatile int *abort = reinterpret_cast<volatile int *>(smem + SM_MISC);
-    int *cons_e = reinterpret_cast<int *>(smem + SM_MISC + 4);
-    int *cons_h = reinterpret_cast<int *>(smem + SM_MISC + 8);
-    int *iss_e = reinterpret_cast<int *>(smem + SM_MISC + 12);
-    int *iss_h = reinterpret_cast<int *>(smem + SM_MISC + 16);
-    Cons C{&a, smem, tab, prof, hnew, bars, abort, warp, lane, warp == NCW};
+    float *hnew = reinterpret_cast<float *>(smem + Lo.hnew);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + Lo.bar);
+    volatile int *abort = reinterpret_cast<volatile int *>(smem + Lo.misc);
+    int *cons_e = reinterpret_cast<int *>(smem + Lo.misc + 4);
+    int *cons_h = reinterpret_cast<int *>(smem + Lo.misc + 8);
+    int *iss_e = reinterpret_cast<int *>(smem + Lo.misc + 12);
+    int *iss_h = reinterpret_cast<int *>(smem + Lo.misc + 16);
+    Cons<NH> C{&a, smem, tab, prof, hnew, bars, abort, warp, lane, warp == NCW, Lo.hslot};
 
     for (int q = threadIdx.x; q < a.n_classes * kNumCoef; q += NTHREADS) tab[q] = __ldg(a.table + q);
     if (a.d > 0) {
@@ -543,30 +637,49 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
                 const Item it = decode(a, item);
                 for (int z = it.ka - 1; z <= it.kb; ++z) {
                     const bool e_only = (z == it.kb);
-                    const int sax = e_only ? -1 : staged_axis(a, it.x0, it.y0, z);
+                    int f = 0, xs = 0, ys = 0;
+                    if (!e_only) staging(a, it.x0, it.y0, z, f, xs, ys);
                     if (!mbar_wait(C.emptyE(qe), ((qe / NE) & 1) ^ 1, abort)) { ok = false; break; }
                     char *es = smem + SM_EH + (qe % NE) * ESLOT;
                     int *hdr = reinterpret_cast<int *>(es + OFF_HDR);
                     hdr[0] = item;
                     hdr[1] = z;
-                    hdr[2] = sax;
+                    hdr[2] = f;
+                    hdr[3] = xs;
+                    hdr[4] = ys;
                     mbar_expect_tx(C.fullE(qe), TX_E);
                     for (int c = 0; c < 3; ++c)
                         tma_load_3d(smem_u32(es + c * E_COMP), &m.e[c], it.x0 - XO, it.y0 - 1, z, C.fullE(qe));
                     ++qe;
                     if (e_only) continue;
                     if (!mbar_wait(C.emptyH(qh), ((qh / NH) & 1) ^ 1, abort)) { ok = false; break; }
-                    char *hs = smem + SM_HH + (qh % NH) * HSLOT;
-                    mbar_expect_tx(C.fullH(qh), TX_H + (sax >= 0 ? TX_PSI : 0u));
+                    char *hs = smem + SM_HH + (qh % NH) * Lo.hslot;
+                    const uint32_t txb = TX_H + ((f & F_Z) ? TX_Z : 0u) +
+                                         ((f & F_X) ? 4u * a.pg.w * HBY * 4 : 0u) +
+                                         ((f & F_Y) ? 4u * HBX * a.pg.hy * 4 : 0u);
+                    const uint32_t fb = C.fullH(qh);
+                    mbar_expect_tx(fb, txb);
                     for (int c = 0; c < 3; ++c)
-                        tma_load_3d(smem_u32(hs + OFF_H + c * H_COMP), &m.h[c], it.x0 - XO, it.y0 - 1, z, C.fullH(qh));
-                    tma_load_3d(smem_u32(hs + OFF_C), &m.c, it.x0 - CXO, it.y0 - 1, z, C.fullH(qh));
-                    if (sax >= 0) {
+                        tma_load_3d(smem_u32(hs + OFF_H + c * H_COMP), &m.h[c], it.x0 - XO, it.y0 - 1, z, fb);
+                    tma_load_3d(smem_u32(hs + OFF_C), &m.c, it.x0 - CXO, it.y0 - 1, z, fb);
+                    char *ps = hs + OFF_PSI;
+                    if (f & F_Z) {
                         for (int q = 0; q < 2; ++q) {
-                            tma_load_3d(smem_u32(hs + OFF_PH + q * H_COMP), &m.ph[sax * 2 + q], it.x0 - XO,
-                                        it.y0 - 1, z, C.fullH(qh));
-                            tma_load_3d(smem_u32(hs + OFF_PE + q * PE_BYTES), &m.pe[sax * 2 + q], it.x0, it.y0, z,
-                                        C.fullH(qh));
+                            tma_load_3d(smem_u32(ps + q * H_COMP), &m.zh[q], it.x0 - XO, it.y0 - 1, z, fb);
+                            tma_load_3d(smem_u32(ps + 2 * H_COMP + q * PE_BYTES), &m.ze[q], it.x0, it.y0, z, fb);
+                        }
+                    }
+                    if (f & F_X) {
+                        for (int q = 0; q < 2; ++q) {
+                            tma_load_3d(smem_u32(ps + a.ox + q * a.pg.xb), &m.xh[q], xs, it.y0 - 1, z, fb);
+                            tma_load_3d(smem_u32(ps + a.ox + (2 + q) * a.pg.xb), &m.xe[q], xs, it.y0 - 1, z, fb);
+                        }
+                    }
+                    if (f & F_Y) {
+                        char *py = ps + a.oy;
+                        for (int q = 0; q < 2; ++q) {
+                            tma_load_3d(smem_u32(py + q * a.pg.yb), &m.yh[q], it.x0 - XO, ys, z, fb);
+                            tma_load_3d(smem_u32(py + (2 + q) * a.pg.yb), &m.ye[q], it.x0 - XO, ys, z, fb);
                         }
                     }
                     ++qh;
@@ -615,8 +728,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
             if (!ok) *abort = 1;
             consumer_sync();
             if (*abort) break;
-            const bool done = item_in_cpml(a, it) ? run_item<true>(C, it, ce, ch, hb)
-                                                  : run_item<false>(C, it, ce, ch, hb);
+            const bool done = item_in_cpml(a, it) ? run_item<true, NH>(C, it, ce, ch, hb)
+                                                  : run_item<false, NH>(C, it, ce, ch, hb);
             if (!done) break;
             ce += (uint32_t)(it.kb - it.ka) + 2;
             ch += (uint32_t)(it.kb - it.ka) + 1;
@@ -646,12 +759,42 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
 int step_tile_x() { return TX; }
 int step_tile_y() { return TY; }
 int step_threads() { return NTHREADS; }
-int step_smem_bytes(int n_classes, int d) { return smem_bytes(n_classes, d); }
-const void *step_kernel_ptr() { return (const void *)step_tma_kernel; }
+int step_smem_bytes(int n_classes, int d, int region, int nh) { return smem_bytes(n_classes, d, region, nh); }
+
+PsiGeom step_psi_geom(int d)
+{
+    PsiGeom pg{};
+    if (d == 0) return pg;
+    pg.w = std::min(HBX, (d + 4 + 3) / 4 * 4);
+    pg.hy = std::min(HBY, d + 1);
+    pg.xb = al128(pg.w * HBY * 4);
+    pg.yb = al128(HBX * pg.hy * 4);
+    return pg;
+}
+
+void step_region(const PsiGeom &pg, int zxy, int *region, int *ox, int *oy)
+{
+    if (pg.w == 0) {
+        *region = *ox = *oy = 0;
+    } else if (zxy) {
+        *ox = Z_BYTES;
+        *oy = Z_BYTES + 4 * pg.xb;
+        *region = *oy + 4 * pg.yb;
+    } else {
+        *ox = 0;
+        *oy = 4 * pg.xb;
+        *region = std::max(Z_BYTES, *oy + 4 * pg.yb);
+    }
+}
+const void *step_kernel_ptr(int nh) { return nh == 2 ? (const void *)step_tma_kernel<2> : (const void *)step_tma_kernel<3>; }
 
 cudaError_t launch_step(const TmaMaps &m, const StepArgs &a, int grid, cudaStream_t s)
 {
-    step_tma_kernel<<<grid, NTHREADS, smem_bytes(a.n_classes, a.d), s>>>(m, a);
+    const int smem = smem_bytes(a.n_classes, a.d, a.region, a.nh);
+    if (a.nh == 2)
+        step_tma_kernel<2><<<grid, NTHREADS, smem, s>>>(m, a);
+    else
+        step_tma_kernel<3><<<grid, NTHREADS, smem, s>>>(m, a);
     return cudaGetLastError();
 }
 
