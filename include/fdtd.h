@@ -144,6 +144,39 @@ int fdtd_step(fdtd_grid *g, int n);
 /* Wait for the grid's queued work; reports asynchronous CUDA errors. */
 int fdtd_synchronize(fdtd_grid *g);
 
+/* Size, in ints, of the device array fdtd_step_noalloc() uses as scratch. */
+#define FDTD_NOALLOC_SCRATCH_INTS 64
+
+/* fdtd_step_noalloc: the same n time steps as fdtd_step(), for callers that
+ * cannot allocate device memory.  The paper has no counterpart: this is a
+ * library entry point, not part of the method.
+ *
+ * Who needs it: a caller whose device memory is owned entirely by another
+ * allocator (a framework's caching pool that must not be bypassed), a
+ * real-time loop that cannot afford cudaMalloc's latency and implicit
+ * synchronisation, or a process held to a fixed device-memory budget.  Such
+ * a caller hands fdtd_finalize() an arena it obtained elsewhere and steps
+ * with this function, which calls no cudaMalloc, cudaFree or other
+ * allocating routine and never builds a CUDA graph: it queues plain kernel
+ * launches (and one cudaMemsetAsync) on the grid's stream.
+ *
+ * The step kernel's scratch -- two work-distribution counters per launch and
+ * the flag of a bounded wait that gave up, at most 5 ints today -- lives in
+ * a file-scope device array of FDTD_NOALLOC_SCRATCH_INTS ints (256 bytes)
+ * that every GPU which loads the library holds until the process exits.
+ * The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call on a device shares the array and
+ * keeps the last call's contents: each call clears the counters on the
+ * grid's stream before its first launch, and the error flag is read (and
+ * cleared) by fdtd_synchronize() on a grid that used this entry point.
+ * Calls that overlap on the GPU (grids stepped through this entry point on
+ * different streams at the same time) race on the array.
+ *
+ * Returns FDTD_EINVAL if the grid needs more scratch than the array holds,
+ * FDTD_ESTATE before fdtd_finalize(), FDTD_ECUDA on a launch error. */
+int fdtd_step_noalloc(fdtd_grid *g, int n);
+
 /* Copy count recorded samples of one probe, starting at step first_step,
  * to host_out (count floats).  Synchronises. */
 int fdtd_read_probes(fdtd_grid *g, int probe_id, int first_step, int count, float *host_out);

@@ -63,6 +63,7 @@ def load():
             "fdtd_arena_bytes": (I, [P, I, ctypes.POINTER(S)]),
             "fdtd_finalize": (I, [P, I, P, S]),
             "fdtd_step": (I, [P, I]),
+            "fdtd_step_noalloc": (I, [P, I]),
             "fdtd_synchronize": (I, [P]),
             "fdtd_read_probes": (I, [P, I, I, I, P]),
             "fdtd_get_field": (I, [P, I, P]),

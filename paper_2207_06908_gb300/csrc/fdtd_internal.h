@@ -133,3 +133,10 @@ const void *step_kernel_ptr(int nh);
 cudaError_t launch_edges(const EdgeArgs &a, cudaStream_t s);
 
 }  // namespace fdtd
+
+struct fdtd_grid;
+namespace fdtd {
+// fdtd_runtime.cu, for fdtd_noalloc.cu
+int step_with_scratch(fdtd_grid *g, int n, int *scratch, int scratch_ints);
+int set_error(fdtd_grid *g, int code, const char *msg);
+}  // namespace fdtd

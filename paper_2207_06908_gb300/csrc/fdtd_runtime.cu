@@ -79,6 +79,7 @@ struct fdtd_grid {
     } lc[2] = {};
     int n_launch = 0;
     int ncx = 0, ncy = 0;
+    int *noalloc_err = nullptr;     // error slot of the scratch fdtd_step_noalloc() used
     int parity = 0;
     long step = 0;
     int kz = 0;
@@ -576,6 +577,42 @@ int check_open(fdtd_grid *g, bool want_finalized)
 
 }  // namespace
 
+namespace fdtd {
+
+int set_error(fdtd_grid *g, int code, const char *msg) { return fail(g, code, msg); }
+
+// n steps by direct launches, with the step kernel's work counters (two per
+// launch) and its error flag taken from `scratch` (scratch_ints ints) instead
+// of the grid's arena; nothing is allocated.  The counters are cleared on the
+// grid's stream first; the error flag is left for fdtd_synchronize().
+int step_with_scratch(fdtd_grid *g, int n, int *scratch, int scratch_ints)
+{
+    if (int rc = check_open(g, true)) return rc;
+    if (n < 0) return fail(g, FDTD_EINVAL, "negative step count");
+    const int need = 2 * g->n_launch + 1;
+    if (need > scratch_ints)
+        return fail(g, FDTD_EINVAL, "the step needs more scratch than the static array holds");
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 2 * g->n_launch * sizeof(int), g->stream);
+    if (e != cudaSuccess) return cuda_fail(g, e, "scratch clear");
+    g->noalloc_err = scratch + 2 * g->n_launch;
+    for (; n > 0; --n) {
+        for (int l = 0; l < g->n_launch && e == cudaSuccess; ++l) {
+            StepArgs a = step_args(g, g->parity, l);
+            a.work = scratch + 2 * l;
+            a.err = g->noalloc_err;
+            e = launch_step(g->maps[g->parity], a, g->lc[l].grid, g->stream);
+        }
+        if (e == cudaSuccess && (!g->srcs.empty() || !g->probes.empty()))
+            e = launch_edges(edge_args(g, g->parity), g->stream);
+        if (e != cudaSuccess) return cuda_fail(g, e, "step launch");
+        g->parity ^= 1;
+        g->step += 1;
+    }
+    return FDTD_OK;
+}
+
+}  // namespace fdtd
+
 extern "C" {
 
 int fdtd_create_grid(int nx, int ny, int nz, double dx, double courant, const fdtd_cpml *cpml,
@@ -824,6 +861,14 @@ int fdtd_synchronize(fdtd_grid *g)
         e = cudaMemcpy(&flag, g->err_d, sizeof flag, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(g, e, "error flag read");
         if (flag) return fail(g, FDTD_ETIMEOUT, "a bounded wait in the step kernel gave up");
+        if (g->noalloc_err) {
+            e = cudaMemcpy(&flag, g->noalloc_err, sizeof flag, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(g, e, "error flag read");
+            if (flag) {
+                cudaMemset(g->noalloc_err, 0, sizeof flag);
+                return fail(g, FDTD_ETIMEOUT, "a bounded wait in the step kernel gave up (fdtd_step_noalloc)");
+            }
+        }
     }
     return FDTD_OK;
 }

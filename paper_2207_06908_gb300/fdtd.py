@@ -125,6 +125,11 @@ class Grid:
     def step(self, n=1):
         check(self._lib, self._h, self._lib.fdtd_step(self._h, int(n)), "step")
 
+    def step_noalloc(self, n=1):
+        """n steps through fdtd_step_noalloc (no device allocation; the step
+        kernel's scratch is a static device array shared by all such calls)."""
+        check(self._lib, self._h, self._lib.fdtd_step_noalloc(self._h, int(n)), "step_noalloc")
+
     def synchronize(self):
         check(self._lib, self._h, self._lib.fdtd_synchronize(self._h), "synchronize")
 
