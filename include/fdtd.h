@@ -192,6 +192,38 @@ int fdtd_set_field(fdtd_grid *g, int component, const float *host_in);
 int fdtd_field_device(fdtd_grid *g, int component, void **dptr, int *row_pitch,
                       size_t *plane_pitch);
 
+/* ---- batched engine -------------------------------------------------
+ * Many independent finalized grids (domains of different sizes, media,
+ * wires, layers) advanced together -- the soil and grounding sweeps of
+ * Sec. 4.1.  Every step is one persistent launch of the step kernel over the
+ * work items of all domains (plus one over their CPML z-layer planes when
+ * they have a CPML) and one source / probe launch with a CTA per domain;
+ * fdtd_batch_step replays a captured CUDA graph of 32 steps.  The results
+ * are those of stepping each grid alone with fdtd_step. */
+typedef struct fdtd_batch fdtd_batch;
+
+/* grids: n_grids finalized grids, all at the same step count, on the current
+ * device; the batch reads their device state and keeps pointers to them (they
+ * must outlive it and must not be stepped by other calls meanwhile).
+ * cuda_stream: the stream the batch queues on.  Allocates a small device
+ * table (about 7 KB per domain).  FDTD_ESTATE if a grid is not finalized or
+ * the step counts differ. */
+int fdtd_batch_create(int n_grids, fdtd_grid *const *grids, void *cuda_stream, fdtd_batch **out);
+
+/* Queue n steps of every domain on the batch stream (asynchronous).  Each
+ * grid's step count advances by n. */
+int fdtd_batch_step(fdtd_batch *b, int n);
+
+/* Wait for the batch stream; FDTD_ETIMEOUT if a bounded wait gave up. */
+int fdtd_batch_synchronize(fdtd_batch *b);
+
+/* Persistent CTAs and work items of launch 0 (planes between the z layers)
+ * or 1 (z-layer planes). */
+int fdtd_batch_launch_info(const fdtd_batch *b, int launch, int *ctas, int *items);
+
+const char *fdtd_batch_last_error(const fdtd_batch *b);
+void fdtd_batch_destroy(fdtd_batch *b);
+
 double fdtd_get_dt(const fdtd_grid *g);
 long fdtd_get_step(const fdtd_grid *g);
 int fdtd_num_classes(const fdtd_grid *g);

@@ -74,6 +74,12 @@ def load():
             "fdtd_num_classes": (I, [P]),
             "fdtd_last_error": (ctypes.c_char_p, [P]),
             "fdtd_destroy": (None, [P]),
+            "fdtd_batch_create": (I, [I, P, P, ctypes.POINTER(P)]),
+            "fdtd_batch_step": (I, [P, I]),
+            "fdtd_batch_synchronize": (I, [P]),
+            "fdtd_batch_launch_info": (I, [P, I, ip, ip]),
+            "fdtd_batch_last_error": (ctypes.c_char_p, [P]),
+            "fdtd_batch_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)

@@ -14,7 +14,7 @@ __device__ __forceinline__ long long eidx(const EdgeArgs &a, int i, int j, int k
     return (long long)k * a.plane + (long long)j * a.pitch + i;
 }
 
-__global__ void edge_kernel(const EdgeArgs a)
+__device__ __forceinline__ void edge_body(const EdgeArgs &a)
 {
     __shared__ long long n_s;
     if (threadIdx.x == 0) n_s = *a.step;
@@ -60,11 +60,27 @@ __global__ void edge_kernel(const EdgeArgs a)
     if (threadIdx.x == 0) *a.step = n + 1;
 }
 
+__global__ void edge_kernel(const EdgeArgs a) { edge_body(a); }
+
+__global__ void edge_batch_kernel(const EdgeArgs *e, int parity)
+{
+    __shared__ EdgeArgs a;
+    if (threadIdx.x == 0) a = e[2 * blockIdx.x + parity];
+    __syncthreads();
+    if (a.n_src > 0 || a.n_probes > 0) edge_body(a);
+}
+
 }  // namespace
 
 cudaError_t launch_edges(const EdgeArgs &a, cudaStream_t s)
 {
     edge_kernel<<<1, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_edges_batch(const EdgeArgs *e, int n_domains, int parity, cudaStream_t s)
+{
+    edge_batch_kernel<<<n_domains, 128, 0, s>>>(e, parity);
     return cudaGetLastError();
 }
 

@@ -80,12 +80,39 @@ struct StepArgs {
     int zlo2, zhi2;
     int ncx, ncy;            // column tiles along x, y
     int nitems;              // (z blocks) x (column tiles)
-    int *work;               // [2] work counter, finished-CTA counter (self-resetting)
-    int *err;                // set to 1 when a bounded wait gave up
     PsiGeom pg;
-    int region;              // bytes of the staged-auxiliary region of one H slot
+    int region;              // bytes of the staged-auxiliary region this domain needs
     int ox, oy;              // byte offsets of the x and y box groups in that region
     int zxy;                 // 1: stage the z layer together with x / y
+};
+
+// One domain of a step launch, in device memory (the launch reads the
+// arguments and TMA descriptors of the domain each work item belongs to).
+struct DomainSlot {
+    TmaMaps m[2];            // descriptors of input parity 0, 1
+    StepArgs a[2][2];        // [launch: 0 = planes between the z layers, 1 = z layers][input parity]
+};
+
+// One domain passed in the kernel's own parameters (single-grid launches).
+struct SingleArgs {
+    TmaMaps m;
+    StepArgs a;
+};
+
+// One launch of the step kernel over one or more domains (doms == nullptr:
+// the single domain of SingleArgs, items 0 .. nitems-1).  Work items of
+// domain d are the global items item_start[d] .. item_start[d+1]-1.
+struct BatchArgs {
+    const DomainSlot *doms;
+    const int *item_start;   // [n_domains + 1]
+    int n_domains;
+    int nitems;
+    int launch;              // 0 or 1 (selects StepArgs a[launch])
+    int parity;              // input parity of this step
+    int *work;               // [2] work counter, finished-CTA counter (self-resetting)
+    int *err;                // set to 1 when a bounded wait gave up
+    int max_classes, max_d;  // shared-memory sizing over the domains
+    int region;              // staged-auxiliary region (max over the domains)
     int nh;                  // slots of the H / class / CPML ring (2 or 3)
 };
 
@@ -119,7 +146,7 @@ struct EdgeArgs {
 };
 
 // fdtd_step.cu
-cudaError_t launch_step(const TmaMaps &m, const StepArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_step(const SingleArgs &one, const BatchArgs &b, int grid, cudaStream_t s);
 int step_tile_x();
 int step_tile_y();
 int step_threads();
@@ -128,9 +155,11 @@ PsiGeom step_psi_geom(int d);
 // region size and box-group offsets for a launch that stages z alone
 // (zxy = 0) or z together with the x / y layers (zxy = 1)
 void step_region(const PsiGeom &pg, int zxy, int *region, int *ox, int *oy);
-const void *step_kernel_ptr(int nh);
+const void *step_kernel_ptr(int nh, bool batch);
 // fdtd_edges.cu
 cudaError_t launch_edges(const EdgeArgs &a, cudaStream_t s);
+// one CTA per domain: e[2 * d + parity]
+cudaError_t launch_edges_batch(const EdgeArgs *e, int n_domains, int parity, cudaStream_t s);
 
 }  // namespace fdtd
 

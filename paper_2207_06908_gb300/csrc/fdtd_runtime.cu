@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <array>
 #include <string>
 #include <unordered_map>
@@ -68,6 +69,10 @@ struct fdtd_grid {
     int *work_d = nullptr;          // [2 per launch] step-kernel work counters
     int *err_d = nullptr;           // bounded-wait failure flag
     fdtd::TmaMaps maps[2];          // TMA descriptors of each input parity
+    fdtd::DomainSlot *slot_d = nullptr;   // this grid as a one-domain step launch
+    int *item_start_d = nullptr;          // [launch][2]: {0, items}
+    fdtd::DomainSlot slot_h;              // host copy (also read by batches)
+    fdtd::EdgeArgs edge_h[2];             // edge-kernel arguments per input parity
     fdtd::PsiGeom pg{};             // staged CPML box geometry
     // The step runs as one launch over the planes between the z layers and,
     // with a CPML, a second launch over the z-layer planes whose shared
@@ -103,7 +108,8 @@ int cuda_fail(fdtd_grid *g, cudaError_t e, const char *what)
 
 // ---- device arena plan -------------------------------------------------
 struct Plan {
-    size_t field, cls, table, prof[3], psi[fdtd::PSI_COUNT], src, samples, probes, out, step, work, total;
+    size_t field, cls, table, prof[3], psi[fdtd::PSI_COUNT], src, samples, probes, out, step, work, slot, items,
+        total;
 };
 
 size_t psi_elems(const fdtd_grid *g, int)
@@ -131,6 +137,8 @@ Plan make_plan(const fdtd_grid *g, int capacity)
     p.out = take(std::max<size_t>(1, g->probes.size()) * (size_t)std::max(capacity, 1) * sizeof(float));
     p.step = take(sizeof(long long));
     p.work = take(8 * sizeof(int));
+    p.slot = take(sizeof(fdtd::DomainSlot));
+    p.items = take(4 * sizeof(int));
     p.total = off;
     return p;
 }
@@ -414,14 +422,11 @@ fdtd::StepArgs step_args(const fdtd_grid *g, int parity, int launch)
     a.ncx = g->ncx;
     a.ncy = g->ncy;
     a.nitems = L.nitems;
-    a.work = L.work;
-    a.err = g->err_d;
     a.pg = g->pg;
     a.region = L.region;
     a.ox = L.ox;
     a.oy = L.oy;
     a.zxy = L.zxy;
-    a.nh = L.nh;
     return a;
 }
 
@@ -446,11 +451,39 @@ fdtd::EdgeArgs edge_args(const fdtd_grid *g, int parity)
     return e;
 }
 
+fdtd::SingleArgs single_args(const fdtd_grid *g, int parity, int l)
+{
+    fdtd::SingleArgs one;
+    one.m = g->slot_h.m[parity];
+    one.a = g->slot_h.a[l][parity];
+    return one;
+}
+
+// launch l of one step of this grid alone
+fdtd::BatchArgs grid_launch(const fdtd_grid *g, int parity, int l, int *work, int *err)
+{
+    fdtd::BatchArgs b{};
+    b.doms = nullptr;               // single domain: arguments travel in the kernel parameters
+    b.item_start = nullptr;
+    b.n_domains = 1;
+    b.nitems = g->lc[l].nitems;
+    b.launch = l;
+    b.parity = parity;
+    b.work = work;
+    b.err = err;
+    b.max_classes = g->n_classes;
+    b.max_d = g->d;
+    b.region = g->lc[l].region;
+    b.nh = g->lc[l].nh;
+    return b;
+}
+
 cudaError_t enqueue_step(fdtd_grid *g, int parity, cudaStream_t s)
 {
     cudaError_t e = cudaSuccess;
     for (int l = 0; l < g->n_launch && e == cudaSuccess; ++l)
-        e = fdtd::launch_step(g->maps[parity], step_args(g, parity, l), g->lc[l].grid, s);
+        e = fdtd::launch_step(single_args(g, parity, l), grid_launch(g, parity, l, g->lc[l].work, g->err_d),
+                              g->lc[l].grid, s);
     if (e != cudaSuccess) return e;
     if (!g->srcs.empty() || !g->probes.empty()) e = fdtd::launch_edges(edge_args(g, parity), s);
     return e;
@@ -483,6 +516,23 @@ bool encode_map(CUtensorMap *m, void *base, CUtensorMapDataType dt, int esize, c
     cuuint32_t es[3] = {1, 1, 1};
     return fn(m, dt, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Raise (never lower) a step kernel's dynamic shared-memory limit: grids and
+// batches created earlier keep launching with their own sizes.
+cudaError_t ensure_smem(const void *kernel, int bytes)
+{
+    static std::mutex lock;
+    static std::map<std::pair<int, const void *>, int> set;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> guard(lock);
+    int &cur = set[{dev, kernel}];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
 }
 
 int setup_step_kernel(fdtd_grid *g)
@@ -552,13 +602,12 @@ int setup_step_kernel(fdtd_grid *g)
         max_smem = std::max(max_smem, fdtd::step_smem_bytes(g->n_classes, d, L.region, L.nh));
         g->n_launch = l + 1;
     }
-    for (int nh = 2; nh <= 3 && e == cudaSuccess; ++nh)
-        e = cudaFuncSetAttribute(fdtd::step_kernel_ptr(nh), cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    for (int nh = 2; nh <= 3 && e == cudaSuccess; ++nh) e = ensure_smem(fdtd::step_kernel_ptr(nh, false), max_smem);
     if (e != cudaSuccess) return cuda_fail(g, e, "step kernel setup");
     for (int l = 0; l < g->n_launch; ++l) {
         auto &L = g->lc[l];
         int occ = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fdtd::step_kernel_ptr(L.nh), fdtd::step_threads(),
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fdtd::step_kernel_ptr(L.nh, false), fdtd::step_threads(),
                                                           fdtd::step_smem_bytes(g->n_classes, d, L.region, L.nh));
         if (e != cudaSuccess) return cuda_fail(g, e, "step kernel occupancy");
         if (occ < 1) return fail(g, FDTD_ECUDA, "step kernel does not fit on an SM");
@@ -596,12 +645,9 @@ int step_with_scratch(fdtd_grid *g, int n, int *scratch, int scratch_ints)
     if (e != cudaSuccess) return cuda_fail(g, e, "scratch clear");
     g->noalloc_err = scratch + 2 * g->n_launch;
     for (; n > 0; --n) {
-        for (int l = 0; l < g->n_launch && e == cudaSuccess; ++l) {
-            StepArgs a = step_args(g, g->parity, l);
-            a.work = scratch + 2 * l;
-            a.err = g->noalloc_err;
-            e = launch_step(g->maps[g->parity], a, g->lc[l].grid, g->stream);
-        }
+        for (int l = 0; l < g->n_launch && e == cudaSuccess; ++l)
+            e = launch_step(single_args(g, g->parity, l), grid_launch(g, g->parity, l, scratch + 2 * l, g->noalloc_err),
+                            g->lc[l].grid, g->stream);
         if (e == cudaSuccess && (!g->srcs.empty() || !g->probes.empty()))
             e = launch_edges(edge_args(g, g->parity), g->stream);
         if (e != cudaSuccess) return cuda_fail(g, e, "step launch");
@@ -775,6 +821,8 @@ int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_by
     g->step_d = (long long *)(base + p.step);
     g->work_d = (int *)(base + p.work);
     g->err_d = g->work_d + 4;
+    g->slot_d = (fdtd::DomainSlot *)(base + p.slot);
+    g->item_start_d = (int *)(base + p.items);
     g->capacity = probe_capacity;
 
 
@@ -812,6 +860,20 @@ int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_by
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(g, e, "upload");
     if (int rc = setup_step_kernel(g)) return rc;
+    // the grid as a one-domain step launch: descriptors and arguments per
+    // launch and input parity, item ranges {0, items} per launch
+    std::memset(&g->slot_h, 0, sizeof g->slot_h);
+    int items[4] = {0, 0, 0, 0};
+    for (int par = 0; par < 2; ++par) {
+        g->slot_h.m[par] = g->maps[par];
+        for (int l = 0; l < g->n_launch; ++l) g->slot_h.a[l][par] = step_args(g, par, l);
+        g->edge_h[par] = edge_args(g, par);
+    }
+    for (int l = 0; l < g->n_launch; ++l) items[2 * l + 1] = g->lc[l].nitems;
+    e = cudaMemcpyAsync(g->slot_d, &g->slot_h, sizeof g->slot_h, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->item_start_d, items, sizeof items, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(g, e, "upload of the launch descriptors");
     g->finalized = true;
     return FDTD_OK;
 }
@@ -934,6 +996,235 @@ void fdtd_destroy(fdtd_grid *g)
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     if (g->own_arena && g->arena) cudaFree(g->arena);
     delete g;
+}
+
+}  // extern "C"
+
+// ---- batched engine ----------------------------------------------------
+// Many finalized grids advanced together: each step is one persistent
+// launch of the step kernel over the work items of every domain (and one
+// over their z-layer planes when they have a CPML), then one source / probe
+// launch with a CTA per domain.  fdtd_batch_step replays a captured graph.
+struct fdtd_batch {
+    std::vector<fdtd_grid *> grids;
+    cudaStream_t stream = nullptr;
+    void *mem = nullptr;
+    fdtd::DomainSlot *doms = nullptr;
+    int *item_start[2] = {};
+    fdtd::EdgeArgs *edges = nullptr;
+    int *work = nullptr;            // [2 per launch]
+    int *errf = nullptr;
+    int nitems[2] = {}, grid[2] = {}, region[2] = {}, nh[2] = {};
+    int max_classes = 0, max_d = 0, n_launch = 0;
+    bool has_edges = false;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int parity = 0;
+    long step = 0;
+    std::string err;
+};
+
+namespace {
+
+int bfail(fdtd_batch *b, int code, const std::string &msg)
+{
+    if (b) b->err = msg;
+    return code;
+}
+
+cudaError_t batch_enqueue(fdtd_batch *b, int parity, cudaStream_t s)
+{
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < b->n_launch && e == cudaSuccess; ++l) {
+        if (b->nitems[l] == 0) continue;
+        fdtd::BatchArgs a{};
+        a.doms = b->doms;
+        a.item_start = b->item_start[l];
+        a.n_domains = (int)b->grids.size();
+        a.nitems = b->nitems[l];
+        a.launch = l;
+        a.parity = parity;
+        a.work = b->work + 2 * l;
+        a.err = b->errf;
+        a.max_classes = b->max_classes;
+        a.max_d = b->max_d;
+        a.region = b->region[l];
+        a.nh = b->nh[l];
+        static const fdtd::SingleArgs none{};
+        e = fdtd::launch_step(none, a, b->grid[l], s);
+    }
+    if (e == cudaSuccess && b->has_edges)
+        e = fdtd::launch_edges_batch(b->edges, (int)b->grids.size(), parity, s);
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fdtd_batch_create(int n, fdtd_grid *const *grids, void *cuda_stream, fdtd_batch **out)
+{
+    if (!out || n < 1 || !grids) return FDTD_EINVAL;
+    *out = nullptr;
+    fdtd_batch *b = new (std::nothrow) fdtd_batch();
+    if (!b) return FDTD_ENOMEM;
+    b->stream = (cudaStream_t)cuda_stream;
+    for (int q = 0; q < n; ++q) {
+        fdtd_grid *g = grids[q];
+        if (!g || !g->finalized) { delete b; return FDTD_ESTATE; }
+        if (g->parity != grids[0]->parity || g->step != grids[0]->step) { delete b; return FDTD_ESTATE; }
+        b->grids.push_back(g);
+    }
+    b->parity = grids[0]->parity;
+    b->step = grids[0]->step;
+    // launch sizing over all domains
+    std::vector<int> starts[2];
+    for (int l = 0; l < 2; ++l) starts[l].push_back(0);
+    for (fdtd_grid *g : b->grids) {
+        b->max_classes = std::max(b->max_classes, g->n_classes);
+        b->max_d = std::max(b->max_d, g->d);
+        b->n_launch = std::max(b->n_launch, g->n_launch);
+        b->has_edges = b->has_edges || !g->srcs.empty() || !g->probes.empty();
+        for (int l = 0; l < 2; ++l) {
+            const int items = l < g->n_launch ? g->lc[l].nitems : 0;
+            starts[l].push_back(starts[l].back() + items);
+            if (l < g->n_launch) b->region[l] = std::max(b->region[l], g->lc[l].region);
+        }
+    }
+    int dev = 0, sms = 0, smem_per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    int max_smem = 0;
+    for (int l = 0; l < b->n_launch && e == cudaSuccess; ++l) {
+        b->nitems[l] = starts[l].back();
+        b->nh[l] = 3;
+        if (2 * (fdtd::step_smem_bytes(b->max_classes, b->max_d, b->region[l], 3) + 1024) > smem_per_sm &&
+            2 * (fdtd::step_smem_bytes(b->max_classes, b->max_d, b->region[l], 2) + 1024) <= smem_per_sm)
+            b->nh[l] = 2;
+        max_smem = std::max(max_smem, fdtd::step_smem_bytes(b->max_classes, b->max_d, b->region[l], b->nh[l]));
+    }
+    for (int nh = 2; nh <= 3 && e == cudaSuccess; ++nh) e = ensure_smem(fdtd::step_kernel_ptr(nh, true), max_smem);
+    for (int l = 0; l < b->n_launch && e == cudaSuccess; ++l) {
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &occ, fdtd::step_kernel_ptr(b->nh[l], true), fdtd::step_threads(),
+            fdtd::step_smem_bytes(b->max_classes, b->max_d, b->region[l], b->nh[l]));
+        if (e == cudaSuccess && occ < 1) { delete b; return FDTD_ECUDA; }
+        b->grid[l] = std::max(1, std::min(sms * std::max(occ, 1), b->nitems[l]));
+    }
+    if (e != cudaSuccess) { delete b; return FDTD_ECUDA; }
+    // device tables
+    const size_t nd = b->grids.size();
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t at = off; off = align_up(off + bytes, 256); return at; };
+    const size_t o_doms = take(nd * sizeof(fdtd::DomainSlot));
+    const size_t o_s0 = take((nd + 1) * sizeof(int));
+    const size_t o_s1 = take((nd + 1) * sizeof(int));
+    const size_t o_edges = take(2 * nd * sizeof(fdtd::EdgeArgs));
+    const size_t o_work = take(8 * sizeof(int));
+    if (cudaMalloc(&b->mem, off) != cudaSuccess) { delete b; return FDTD_ENOMEM; }
+    char *base = (char *)b->mem;
+    b->doms = (fdtd::DomainSlot *)(base + o_doms);
+    b->item_start[0] = (int *)(base + o_s0);
+    b->item_start[1] = (int *)(base + o_s1);
+    b->edges = (fdtd::EdgeArgs *)(base + o_edges);
+    b->work = (int *)(base + o_work);
+    b->errf = b->work + 4;
+    std::vector<fdtd::DomainSlot> slots(nd);
+    std::vector<fdtd::EdgeArgs> edges(2 * nd);
+    for (size_t q = 0; q < nd; ++q) {
+        slots[q] = b->grids[q]->slot_h;
+        edges[2 * q] = b->grids[q]->edge_h[0];
+        edges[2 * q + 1] = b->grids[q]->edge_h[1];
+    }
+    cudaStream_t s = b->stream;
+    e = cudaMemsetAsync(b->mem, 0, off, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->doms, slots.data(), nd * sizeof(fdtd::DomainSlot), cudaMemcpyHostToDevice, s);
+    for (int l = 0; l < 2 && e == cudaSuccess; ++l)
+        e = cudaMemcpyAsync(b->item_start[l], starts[l].data(), (nd + 1) * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->edges, edges.data(), 2 * nd * sizeof(fdtd::EdgeArgs), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    // the grids' own work must be finished before the batch reads them
+    for (fdtd_grid *g : b->grids)
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) { cudaFree(b->mem); delete b; return FDTD_ECUDA; }
+    *out = b;
+    return FDTD_OK;
+}
+
+int fdtd_batch_step(fdtd_batch *b, int n)
+{
+    if (!b) return FDTD_EINVAL;
+    if (n < 0) return bfail(b, FDTD_EINVAL, "negative step count");
+    const int n0 = n;
+    while (n > 0) {
+        if (b->parity == 0 && n >= kGraphSteps) {
+            if (!b->graph) {
+                cudaError_t e = cudaSuccess;
+                if (!b->cap) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+                cudaGraph_t graph = nullptr;
+                if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    for (int t = 0; t < kGraphSteps && e == cudaSuccess; ++t) e = batch_enqueue(b, t & 1, b->cap);
+                    cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+                    if (e == cudaSuccess) e = e2;
+                }
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, graph, 0);
+                if (graph) cudaGraphDestroy(graph);
+                if (e != cudaSuccess) {
+                    b->graph = nullptr;
+                    return bfail(b, FDTD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+                }
+            }
+            cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+            if (e != cudaSuccess) return bfail(b, FDTD_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+            n -= kGraphSteps;
+        } else {
+            cudaError_t e = batch_enqueue(b, b->parity, b->stream);
+            if (e != cudaSuccess) return bfail(b, FDTD_ECUDA, std::string("step launch: ") + cudaGetErrorString(e));
+            b->parity ^= 1;
+            n -= 1;
+        }
+    }
+    b->step += n0;
+    for (fdtd_grid *g : b->grids) {
+        g->parity = b->parity;
+        g->step = b->step;
+    }
+    return FDTD_OK;
+}
+
+int fdtd_batch_synchronize(fdtd_batch *b)
+{
+    if (!b) return FDTD_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, FDTD_ECUDA, std::string("synchronize: ") + cudaGetErrorString(e));
+    int flag = 0;
+    e = cudaMemcpy(&flag, b->errf, sizeof flag, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return bfail(b, FDTD_ECUDA, "error flag read");
+    if (flag) return bfail(b, FDTD_ETIMEOUT, "a bounded wait in the step kernel gave up");
+    return FDTD_OK;
+}
+
+int fdtd_batch_launch_info(const fdtd_batch *b, int launch, int *ctas, int *items)
+{
+    if (!b || launch < 0 || launch > 1) return FDTD_EINVAL;
+    if (ctas) *ctas = launch < b->n_launch ? b->grid[launch] : 0;
+    if (items) *items = launch < b->n_launch ? b->nitems[launch] : 0;
+    return FDTD_OK;
+}
+
+const char *fdtd_batch_last_error(const fdtd_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+void fdtd_batch_destroy(fdtd_batch *b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->mem) cudaFree(b->mem);
+    delete b;
 }
 
 }  // extern "C"

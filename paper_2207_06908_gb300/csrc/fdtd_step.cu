@@ -64,7 +64,7 @@ constexpr int PE_BYTES = al128(TX * TY * 4);         // E-type psi box: the tile
 // E slot: three E boxes and a header (item, plane, staged-layer flags,
 // x-box start, y-box start)
 constexpr int OFF_HDR = 3 * E_COMP;
-constexpr int ESLOT = al128(OFF_HDR + 32);
+constexpr int ESLOT = al128(OFF_HDR + 32);   // header: item, plane, flags, x start, y start, domain
 // H slot: three H boxes, the class box, then the staged-auxiliary region
 // (grid dependent size).  In a z-layer plane the region holds the z boxes
 // (2 H-type with the H box, 2 E-type with the tile box); elsewhere the x
@@ -101,7 +101,8 @@ struct Layout {
 
 __host__ __device__ inline int smem_bytes(int n_classes, int d, int region, int nh)
 {
-    return Layout(region, nh).tab + n_classes * kNumCoef * 4 + 3 * PR_COUNT * 2 * d * 4 + 128;
+    return Layout(region, nh).tab + al128(sizeof(StepArgs)) + n_classes * kNumCoef * 4 + 3 * PR_COUNT * 2 * d * 4 +
+           128;
 }
 
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
@@ -582,16 +583,33 @@ __device__ __forceinline__ bool run_item(const Cons<NH> &C, const Item &it, uint
     return true;
 }
 
-template <int NH>
-__global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_constant__ TmaMaps m, const StepArgs a)
+// domain of global work item q: item_start[d] <= q < item_start[d + 1]
+__device__ __forceinline__ int find_domain(const int *item_start, int n, int q)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(item_start + mid) <= q) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// BATCH = false: one domain whose arguments and descriptors are the kernel's
+// own parameters (constant bank); BATCH = true: a table of domains in global
+// memory, the current domain's arguments staged in shared memory.
+template <int NH, bool BATCH>
+__global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_constant__ SingleArgs S,
+                                                              const BatchArgs B)
 {
     extern __shared__ __align__(128) char smem_raw[];
     // TMA destinations are kept 128-byte aligned
     char *smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const Layout Lo(a.region, NH);
-    float *tab = reinterpret_cast<float *>(smem + Lo.tab);
-    float *prof = tab + a.n_classes * kNumCoef;   // [axis][PR_COUNT][2d], slab entries only
+    const Layout Lo(B.region, NH);
+    StepArgs *sa = reinterpret_cast<StepArgs *>(smem + Lo.tab);          // current domain's arguments
+    float *tab = reinterpret_cast<float *>(smem + Lo.tab + al128(sizeof(StepArgs)));
+    float *prof = tab + B.max_classes * kNumCoef;  // [axis][PR_COUNT][2d], slab entries only
     float *hnew = reinterpret_cast<float *>(smem + Lo.hnew);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + Lo.bar);
     volatile int *abort = reinterpret_cast<volatile int *>(smem + Lo.misc);
@@ -599,16 +617,20 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
     int *cons_h = reinterpret_cast<int *>(smem + Lo.misc + 8);
     int *iss_e = reinterpret_cast<int *>(smem + Lo.misc + 12);
     int *iss_h = reinterpret_cast<int *>(smem + Lo.misc + 16);
-    Cons<NH> C{&a, smem, tab, prof, hnew, bars, abort, warp, lane, warp == NCW, Lo.hslot};
+    Cons<NH> C{BATCH ? sa : &S.a, smem, tab, prof, hnew, bars, abort, warp, lane, warp == NCW, Lo.hslot};
 
-    for (int q = threadIdx.x; q < a.n_classes * kNumCoef; q += NTHREADS) tab[q] = __ldg(a.table + q);
-    if (a.d > 0) {
-        const int d2 = 2 * a.d, per = PR_COUNT * d2;
-        for (int q = threadIdx.x; q < 3 * per; q += NTHREADS) {
-            const int u = q / per, w = (q - u * per) / d2, sl = q - u * per - w * d2;
-            const int n = u == 0 ? a.nx : (u == 1 ? a.ny : a.nz);
-            const int i = sl < a.d ? sl : n - d2 + sl;
-            prof[q] = __ldg(a.prof[u] + w * n + i);
+    if (!BATCH) {
+        // the one domain's coefficient table and CPML profiles, once
+        const StepArgs &ga = S.a;
+        for (int q = threadIdx.x; q < ga.n_classes * kNumCoef; q += NTHREADS) tab[q] = __ldg(ga.table + q);
+        if (ga.d > 0) {
+            const int d2 = 2 * ga.d, per = PR_COUNT * d2;
+            for (int q = threadIdx.x; q < 3 * per; q += NTHREADS) {
+                const int u = q / per, w = (q - u * per) / d2, sl = q - u * per - w * d2;
+                const int n = u == 0 ? ga.nx : (u == 1 ? ga.ny : ga.nz);
+                const int i = sl < ga.d ? sl : n - d2 + sl;
+                prof[q] = __ldg(ga.prof[u] + w * n + i);
+            }
         }
     }
     if (threadIdx.x == 0) {
@@ -632,8 +654,12 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
             uint32_t qe = 0, qh = 0;
             bool ok = true;
             while (ok) {
-                const int item = atomicAdd(a.work, 1);
-                if (item >= a.nitems) break;
+                const int gitem = atomicAdd(B.work, 1);
+                if (gitem >= B.nitems) break;
+                const int dom = BATCH ? find_domain(B.item_start, B.n_domains, gitem) : 0;
+                const StepArgs &a = BATCH ? B.doms[dom].a[B.launch][B.parity] : S.a;
+                const TmaMaps &m = BATCH ? B.doms[dom].m[B.parity] : S.m;
+                const int item = BATCH ? gitem - __ldg(B.item_start + dom) : gitem;
                 const Item it = decode(a, item);
                 for (int z = it.ka - 1; z <= it.kb; ++z) {
                     const bool e_only = (z == it.kb);
@@ -647,6 +673,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
                     hdr[2] = f;
                     hdr[3] = xs;
                     hdr[4] = ys;
+                    hdr[5] = dom;
                     mbar_expect_tx(C.fullE(qe), TX_E);
                     for (int c = 0; c < 3; ++c)
                         tma_load_3d(smem_u32(es + c * E_COMP), &m.e[c], it.x0 - XO, it.y0 - 1, z, C.fullE(qe));
@@ -691,7 +718,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
                     int *hdr = reinterpret_cast<int *>(smem + SM_EH + (qe % NE) * ESLOT + OFF_HDR);
                     hdr[0] = -1;
                     hdr[1] = 0;
-                    hdr[2] = -1;
+                    hdr[2] = 0;
+                    hdr[5] = -1;
                     mbar_arrive(C.fullE(qe));
                     ++qe;
                 } else {
@@ -700,29 +728,54 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
             }
             if (!ok) {
                 *abort = 1;
-                atomicExch(a.err, 1);
+                atomicExch(B.err, 1);
             }
             *iss_e = (int)qe;
             *iss_h = (int)qh;
             // the last CTA to finish handing out work resets the counters
             __threadfence();
-            if (atomicAdd(a.work + 1, 1) == (int)gridDim.x - 1) {
-                a.work[0] = 0;
-                a.work[1] = 0;
+            if (atomicAdd(B.work + 1, 1) == (int)gridDim.x - 1) {
+                B.work[0] = 0;
+                B.work[1] = 0;
                 __threadfence();
             }
         }
     } else {
         // ------------------------- row warps and halo warp -------------------------
         uint32_t ce = 0, ch = 0, hb = 0;
+        int cur = -1;                   // domain whose arguments are staged
+        const int tid = threadIdx.x;
         while (true) {
             // first plane of the next item (or the end marker)
             bool ok = C.waitE(ce);
             if (!ok) *abort = 1;
             consumer_sync();
             if (*abort) break;
-            const int item = C.ev(ce).hdr()[0];
+            const int *hdr = C.ev(ce).hdr();
+            const int item = hdr[0], dom = hdr[5];
             if (item < 0) break;
+            if (BATCH && dom != cur) {
+                // stage this domain's arguments, coefficient table and CPML profiles
+                const DomainSlot &D = B.doms[dom];
+                const int *src = reinterpret_cast<const int *>(&D.a[B.launch][B.parity]);
+                int *dst = reinterpret_cast<int *>(sa);
+                for (int q = tid; q < (int)(sizeof(StepArgs) / 4); q += NCONS) dst[q] = __ldg(src + q);
+                const StepArgs &ga = D.a[B.launch][B.parity];
+                const int ncoef = ga.n_classes * kNumCoef;
+                for (int q = tid; q < ncoef; q += NCONS) tab[q] = __ldg(ga.table + q);
+                if (ga.d > 0) {
+                    const int d2 = 2 * ga.d, per = PR_COUNT * d2;
+                    for (int q = tid; q < 3 * per; q += NCONS) {
+                        const int u = q / per, w = (q - u * per) / d2, sl = q - u * per - w * d2;
+                        const int n = u == 0 ? ga.nx : (u == 1 ? ga.ny : ga.nz);
+                        const int i = sl < ga.d ? sl : n - d2 + sl;
+                        prof[q] = __ldg(ga.prof[u] + w * n + i);
+                    }
+                }
+                cur = dom;
+                consumer_sync();
+            }
+            const StepArgs &a = *C.a;
             const Item it = decode(a, item);
             ok = C.waitE(ce + 1);
             if (!ok) *abort = 1;
@@ -743,7 +796,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
     // on an abort, wait (bounded) for copies still in flight before the
     // shared memory is given back
     if (threadIdx.x == 0 && *abort) {
-        atomicExch(a.err, 1);
+        atomicExch(B.err, 1);
         const unsigned long long t0 = gtimer();
         for (int q = *cons_e; q < *iss_e; ++q)
             while (!mbar_try(C.fullE(q), (q / NE) & 1))
@@ -786,15 +839,23 @@ void step_region(const PsiGeom &pg, int zxy, int *region, int *ox, int *oy)
         *region = std::max(Z_BYTES, *oy + 4 * pg.yb);
     }
 }
-const void *step_kernel_ptr(int nh) { return nh == 2 ? (const void *)step_tma_kernel<2> : (const void *)step_tma_kernel<3>; }
-
-cudaError_t launch_step(const TmaMaps &m, const StepArgs &a, int grid, cudaStream_t s)
+const void *step_kernel_ptr(int nh, bool batch)
 {
-    const int smem = smem_bytes(a.n_classes, a.d, a.region, a.nh);
-    if (a.nh == 2)
-        step_tma_kernel<2><<<grid, NTHREADS, smem, s>>>(m, a);
-    else
-        step_tma_kernel<3><<<grid, NTHREADS, smem, s>>>(m, a);
+    if (batch) return nh == 2 ? (const void *)step_tma_kernel<2, true> : (const void *)step_tma_kernel<3, true>;
+    return nh == 2 ? (const void *)step_tma_kernel<2, false> : (const void *)step_tma_kernel<3, false>;
+}
+
+cudaError_t launch_step(const SingleArgs &one, const BatchArgs &b, int grid, cudaStream_t s)
+{
+    const int smem = smem_bytes(b.max_classes, b.max_d, b.region, b.nh);
+    const bool batch = b.doms != nullptr;
+    if (b.nh == 2) {
+        if (batch) step_tma_kernel<2, true><<<grid, NTHREADS, smem, s>>>(one, b);
+        else step_tma_kernel<2, false><<<grid, NTHREADS, smem, s>>>(one, b);
+    } else {
+        if (batch) step_tma_kernel<3, true><<<grid, NTHREADS, smem, s>>>(one, b);
+        else step_tma_kernel<3, false><<<grid, NTHREADS, smem, s>>>(one, b);
+    }
     return cudaGetLastError();
 }
 

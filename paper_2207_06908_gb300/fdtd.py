@@ -175,6 +175,48 @@ class Grid:
         return self._lib.fdtd_num_classes(self._h)
 
 
+class Batch:
+    """Advance many finalized grids together (the batched engine of the C
+    ABI): one persistent launch per step over all domains, graph-replayed."""
+
+    def __init__(self, grids, stream=None):
+        self._lib = _lib.load()
+        self.grids = list(grids)
+        arr = (ctypes.c_void_p * len(self.grids))(*[g._h for g in self.grids])
+        h = ctypes.c_void_p()
+        rc = self._lib.fdtd_batch_create(len(self.grids), arr, _stream_ptr(stream), ctypes.byref(h))
+        if rc != 0:
+            raise FdtdError(rc, "fdtd_batch_create")
+        self._h = h
+
+    def _check(self, rc, what):
+        if rc != 0:
+            raise FdtdError(rc, f"{what}: {self._lib.fdtd_batch_last_error(self._h).decode()}")
+
+    def step(self, n=1):
+        self._check(self._lib.fdtd_batch_step(self._h, int(n)), "batch_step")
+
+    def synchronize(self):
+        self._check(self._lib.fdtd_batch_synchronize(self._h), "batch_synchronize")
+
+    def launch_info(self, launch):
+        c, i = ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.fdtd_batch_launch_info(self._h, int(launch), ctypes.byref(c), ctypes.byref(i)),
+                    "batch_launch_info")
+        return c.value, i.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.fdtd_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def from_scenario(sc, stream=None, probe_capacity=None, torch_arena=True):
     """Build and finalize a Grid from a workloads.Scenario."""
     g = Grid(*sc.n, sc.dx, courant=sc.courant, cpml=sc.cpml or None, stream=stream)
@@ -189,5 +231,5 @@ def from_scenario(sc, stream=None, probe_capacity=None, torch_arena=True):
     return g
 
 
-__all__ = ["Grid", "FdtdError", "from_scenario", "EX", "EY", "EZ", "HX", "HY", "HZ",
+__all__ = ["Grid", "Batch", "FdtdError", "from_scenario", "EX", "EY", "EZ", "HX", "HY", "HZ",
            "PROBE_V", "PROBE_I", "PROBE_E", "PROBE_H"]

@@ -14,6 +14,10 @@ have the shapes of its grounding / lightning workloads):
   config3: 512x512x384, 12-cell CPML, two-layer soil, buried 8x8 thin-wire
            mesh with a down-conductor and the current / voltage leads of the
            paper's ground-potential-rise model
+  config4: 256 grounding-rod domains of uneven size (side 48..128, 8-cell
+           CPML, random soil), 2000 steps each; 512-sample impedance output
+  surrogate_inputs / grounding_domain: the config-4 generator with the six
+           surrogate parameters drawn as well
 """
 from __future__ import annotations
 
@@ -280,3 +284,97 @@ def random_scenario(seed, n=(17, 17, 17), dx=0.1, courant=0.99, cpml=0, n_blocks
     if fields:
         sc.fields = random_fields(rng, n)
     return sc
+
+
+# ---- grounding-electrode domains (the batched and surrogate workloads) -----
+GROUND_DX = 0.25          # m; fixed so every domain spans the same time window
+GROUND_CPML = 8
+GROUND_STEPS = 2000
+GROUND_SAMPLES = 512
+LEAD_RADIUS = 0.003
+
+
+def grounding_domain(n, eps_r, sigma, length, radius, depth, rise, n_steps=GROUND_STEPS, name="ground"):
+    """One grounding-electrode domain of n^3 cells, dx = 0.25 m, 8-cell CPML:
+    soil (eps_r, sigma) below the surface node n - 14, air above; a vertical
+    rod of the given length and radius whose top is `depth` m below the
+    surface at the domain centre; a riser (same radius) up to 1 m above the
+    surface; from its top a current lead along +x with a one-cell source gap
+    two cells out and a voltage lead along +y with a one-cell probe gap two
+    cells out, both running into the CPML (the layout of the paper's
+    ground-potential-rise model file); a 1 kA linear ramp of the given rise
+    time on the source gap.  Probes: gap voltage and source current."""
+    dx = GROUND_DX
+    d = GROUND_CPML
+    c = n // 2
+    ks = n - 14                                    # surface node
+    kd = ks - int(round(depth / dx))               # rod top node
+    lc = max(1, int(round(length / dx)))
+    kb = kd - lc                                   # rod bottom node
+    if kb < d + 2:
+        raise ValueError("rod does not fit the domain")
+    kt = ks + 4                                    # riser top, 1 m above the surface
+    cm = paint_blocks((n, n, n), [((0, 0, 0), (n, n, ks), 1)])
+    mats = [(1.0, 0.0, 1.0), (float(eps_r), float(sigma), 1.0)]
+    wires = [((c, c, kb), (c, c, kd), radius),     # rod
+             ((c, c, kd), (c, c, kt), radius),     # riser
+             ((c, c, kt), (c + 2, c, kt), LEAD_RADIUS),
+             ((c + 3, c, kt), (n - d, c, kt), LEAD_RADIUS),
+             ((c, c, kt), (c, c + 2, kt), LEAD_RADIUS),
+             ((c, c + 3, kt), (c, n - d, kt), LEAD_RADIUS)]
+    cur = ramp(sample_times(n_steps, dx, 0.99), 1e3, rise)
+    return Scenario(name, (n, n, n), dx, 0.99, d, cm, mats, wires=wires,
+                    sources=[((c + 2, c, kt), 0, cur)],
+                    probes=[(PROBE_V, (c, c + 2, kt), 1, 1), (PROBE_I, (c + 2, c, kt), 0, 1)],
+                    n_steps=n_steps)
+
+
+def config4(n_domains=256, seed=0, n_steps=GROUND_STEPS, n_range=(48, 128)):
+    """The batched workload: n_domains rods, side ~ U{48..128} cells,
+    eps_r ~ U[4, 40], log10 sigma ~ U[-4, -1], r = 8 mm at the surface,
+    L ~ U[1, min(10, 0.25 (N - 28))] m, 1 kA ramp of 0.25 us rise."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for q in range(n_domains):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        eps = float(rng.uniform(4.0, 40.0))
+        sig = float(10 ** rng.uniform(-4.0, -1.0))
+        lmax = min(10.0, GROUND_DX * (n - 28))
+        length = float(rng.uniform(1.0, lmax))
+        out.append(grounding_domain(n, eps, sig, length, 0.008, 0.0, 0.25e-6, n_steps, name=f"rod{q}_n{n}"))
+    return out
+
+
+SURROGATE_N = 64          # domain side used for the surrogate's runs
+
+
+def surrogate_inputs(seed):
+    """The six surrogate parameters of one seeded run: eps_r ~ U[4, 40],
+    log10 sigma ~ U[-4, -1], rod length (m), radius ~ U[4, 16] mm, burial
+    depth of the rod top ~ U[0, 1] m, rise time ~ U[0.1, 0.5] us; the length
+    is drawn from U[1, Lmax - depth] with Lmax the config-4 cap of the
+    64-cell domain."""
+    rng = np.random.default_rng(seed)
+    eps = float(rng.uniform(4.0, 40.0))
+    lsig = float(rng.uniform(-4.0, -1.0))
+    radius = float(rng.uniform(0.004, 0.016))
+    depth = float(rng.uniform(0.0, 1.0))
+    rise = float(rng.uniform(0.1e-6, 0.5e-6))
+    lmax = min(10.0, GROUND_DX * (SURROGATE_N - 28)) - depth
+    length = float(rng.uniform(1.0, lmax))
+    return np.array([eps, lsig, length, radius, depth, rise])
+
+
+def surrogate_domain(params, n_steps=GROUND_STEPS):
+    eps, lsig, length, radius, depth, rise = [float(v) for v in params]
+    return grounding_domain(SURROGATE_N, eps, 10 ** lsig, length, radius, depth, rise, n_steps)
+
+
+def impedance_waveform(v_gap, dt, n_samples=GROUND_SAMPLES, i_peak=1e3):
+    """Output of a grounding run: the gap voltage (sampled at t_{n+1}) over
+    the peak current, linearly interpolated to n_samples uniform instants of
+    [0, n_steps dt]."""
+    v = np.asarray(v_gap, dtype=np.float64)
+    t_src = (np.arange(len(v)) + 1.0) * dt
+    t = np.linspace(0.0, len(v) * dt, n_samples)
+    return np.interp(t, np.concatenate([[0.0], t_src]), np.concatenate([[0.0], v])) / i_peak

@@ -1,0 +1,88 @@
+"""Batched engine: many independent domains advanced by one persistent launch
+per step.  It must give exactly the results of stepping each grid alone, and
+match the FP64 oracle on grounding domains of the batched workload's shape."""
+import numpy as np
+import pytest
+
+from paper_2207_06908_gb300 import workloads as W
+from _scenario import oracle_from_scenario, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fdtd():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2207_06908_gb300 import fdtd as F
+    return F
+
+
+def build(F, sc, steps):
+    g = F.from_scenario(sc, probe_capacity=steps)
+    if sc.fields is not None:
+        for c, f in enumerate(sc.fields):
+            g.set_field(c, f)
+    return g
+
+
+def test_batch_equals_individual_grids(fdtd):
+    """uneven sizes, with and without CPML, wires, sources, probes; 45 steps
+    (one 32-step graph + direct launches): bitwise equal to fdtd_step"""
+    scs = [W.random_scenario(200 + q, n=n, cpml=c, n_steps=45)
+           for q, (n, c) in enumerate([((17, 17, 17), 0), ((45, 21, 27), 5), ((33, 40, 18), 3),
+                                       ((64, 16, 30), 0), ((20, 35, 41), 4)])]
+    steps = 45
+    alone = []
+    for sc in scs:
+        g = build(fdtd, sc, steps)
+        g.step(steps)
+        alone.append(([g.get_field(c) for c in range(6)], [g.read_probe(p) for p in range(len(sc.probes))]))
+        g.close()
+    grids = [build(fdtd, sc, steps) for sc in scs]
+    b = fdtd.Batch(grids)
+    b.step(steps)
+    b.synchronize()
+    for g, sc, (fa, pa) in zip(grids, scs, alone):
+        assert g.step_count == steps
+        for c in range(6):
+            assert np.array_equal(g.get_field(c), fa[c])
+        for p in range(len(sc.probes)):
+            assert np.array_equal(g.read_probe(p), pa[p])
+    b.close()
+    for g in grids:
+        g.close()
+
+
+def test_batch_grounding_domains_vs_oracle(fdtd):
+    """three grounding-rod domains of the batched workload (48..56 cells,
+    8-cell CPML, random soil, rod, riser and leads), 300 steps from rest:
+    gap voltage and source current within 1e-4 of the FP64 oracle"""
+    rng = np.random.default_rng(7)
+    scs = []
+    for n in (48, 52, 56):
+        scs.append(W.grounding_domain(n, rng.uniform(4, 40), 10 ** rng.uniform(-4, -1),
+                                      rng.uniform(1.0, 0.25 * (n - 28)), 0.008, 0.0, 0.25e-6, n_steps=300))
+    grids = [fdtd.from_scenario(sc, probe_capacity=300) for sc in scs]
+    b = fdtd.Batch(grids)
+    b.step(300)
+    b.synchronize()
+    for g, sc in zip(grids, scs):
+        o = oracle_from_scenario(sc, parity=True)
+        o.step(300)
+        for p in range(len(sc.probes)):
+            assert rel_l2(g.read_probe(p), o.read_probe(p)) <= 1e-4
+    b.close()
+    for g in grids:
+        g.close()
+
+
+def test_batch_rejects_mismatched_steps(fdtd):
+    a = build(fdtd, W.random_scenario(1, n=(10, 10, 10), n_steps=4), 4)
+    c = build(fdtd, W.random_scenario(2, n=(12, 10, 9), n_steps=4), 4)
+    a.step(1)
+    with pytest.raises(fdtd.FdtdError):
+        fdtd.Batch([a, c])
+    a.close()
+    c.close()
