@@ -125,6 +125,11 @@ int fdtd_add_source(fdtd_grid *g, int i, int j, int k, int axis, double r_intern
 int fdtd_add_probe(fdtd_grid *g, int kind, int i, int j, int k, int axis, int n_edges,
                    int *probe_id);
 
+/* Planes per work item of the step kernel (the depth of a 32x16 column
+ * tile; 0 = the default 16).  Tuning only; results do not depend on it.
+ * Before fdtd_finalize(); FDTD_EINVAL outside 0..256. */
+int fdtd_set_block(fdtd_grid *g, int planes);
+
 /* Device bytes fdtd_finalize() needs for probe_capacity recorded steps. */
 int fdtd_arena_bytes(const fdtd_grid *g, int probe_capacity, size_t *bytes);
 

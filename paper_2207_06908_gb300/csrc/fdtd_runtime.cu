@@ -84,6 +84,7 @@ struct fdtd_grid {
     } lc[2] = {};
     int n_launch = 0;
     int ncx = 0, ncy = 0;
+    int block = 0;                  // planes per work item (0 = default)
     int *noalloc_err = nullptr;     // error slot of the scratch fdtd_step_noalloc() used
     int parity = 0;
     long step = 0;
@@ -579,7 +580,7 @@ int setup_step_kernel(fdtd_grid *g)
         if (l == 0) {            // planes between the z layers (all planes without a CPML)
             L.zlo = d;
             L.zhi = g->nz - d;
-            L.kz = std::min(L.zhi - L.zlo, 16);
+            L.kz = std::min(L.zhi - L.zlo, g->block > 0 ? g->block : 16);
             L.zxy = 0;
         } else {                 // the two z layers, one block each
             if (d == 0) break;
@@ -771,6 +772,14 @@ int fdtd_add_probe(fdtd_grid *g, int kind, int i, int j, int k, int axis, int n_
             if (u != axis && p[u] < 1) return fail(g, FDTD_EINVAL, "current loop needs transverse index >= 1");
     g->probes.push_back(fdtd::ProbeDesc{kind, axis, i, j, k, n_edges});
     if (probe_id) *probe_id = (int)g->probes.size() - 1;
+    return FDTD_OK;
+}
+
+int fdtd_set_block(fdtd_grid *g, int planes)
+{
+    if (int rc = check_open(g, false)) return rc;
+    if (planes < 0 || planes > 256) return fail(g, FDTD_EINVAL, "planes per work item outside 0..256");
+    g->block = planes;
     return FDTD_OK;
 }
 

@@ -101,6 +101,10 @@ class Grid:
                                                            int(n_edges), ctypes.byref(pid)), "add_probe")
         return pid.value
 
+    def set_block(self, planes):
+        """planes per work item of the step kernel (tuning; 0 = default)"""
+        check(self._lib, self._h, self._lib.fdtd_set_block(self._h, int(planes)), "set_block")
+
     def arena_bytes(self, probe_capacity):
         b = ctypes.c_size_t()
         check(self._lib, self._h, self._lib.fdtd_arena_bytes(self._h, int(probe_capacity), ctypes.byref(b)),
@@ -217,9 +221,11 @@ class Batch:
             pass
 
 
-def from_scenario(sc, stream=None, probe_capacity=None, torch_arena=True):
+def from_scenario(sc, stream=None, probe_capacity=None, torch_arena=True, block=0):
     """Build and finalize a Grid from a workloads.Scenario."""
     g = Grid(*sc.n, sc.dx, courant=sc.courant, cpml=sc.cpml or None, stream=stream)
+    if block:
+        g.set_block(block)
     g.set_materials(sc.cell_material, sc.materials)
     for p0, p1, r in sc.wires:
         g.add_wire(p0, p1, r)
