@@ -1,0 +1,65 @@
+/*
+ * fdtd_mlp.h -- C ABI of the surrogate-network kernels (sm_103a).
+ *
+ * The paper has no learned component; this boundary serves the surrogate
+ * that maps grounding-electrode parameters to transient impedance
+ * waveforms produced by the FDTD path (an addition of this library).  It is
+ * a plain multilayer perceptron: layers y = act(x W^T + b) with BF16
+ * operands and FP32 accumulation on the tensor cores, GELU in its erf form,
+ * mean-squared-error loss and Adam.
+ *
+ * Conventions for every call:
+ *   - All array arguments are device pointers; row-major, rows = samples.
+ *   - Weights of a layer with k inputs and n outputs are wt [n x k] (BF16,
+ *     one output per row); bias [n] FP32.
+ *   - Work is queued on cuda_stream (a cudaStream_t, NULL = legacy default);
+ *     nothing synchronises.  Nothing is allocated.
+ *   - Return value 0, FDTD_EINVAL (-1) for bad sizes / null required
+ *     pointers, FDTD_ECUDA (-4) for a launch error.
+ */
+#ifndef FDTD_GB300_MLP_H
+#define FDTD_GB300_MLP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { FDTD_ACT_NONE = 0, FDTD_ACT_GELU = 1 };
+
+/* y = act(z), z = x wt^T + bias.  x: rows x k, BF16 (x_is_bf16 = 1) or FP32
+ * (rounded to BF16 on load).  Outputs, each optional (NULL): y_bf16 and
+ * y_f32 (rows x n), z_f32 (rows x n, the pre-activation the backward pass
+ * needs). */
+int fdtd_mlp_forward(const void *x, int x_is_bf16, int rows, int k, const void *wt, const float *bias, int n,
+                     int act, void *y_bf16, float *y_f32, float *z_f32, void *cuda_stream);
+
+/* Backward of one layer.  dy = dL/dy (rows x n, FP32); z the layer's
+ * pre-activation (needed for GELU; may be NULL for FDTD_ACT_NONE).
+ * dz_scratch (rows x n FP32, caller memory) receives dz = dy * act'(z).
+ * Outputs, each optional: dw = dz^T x (n x k, FP32), db = column sums of dz
+ * (n), dx = dz wt (rows x k, FP32).  dz and x enter the tensor cores as
+ * BF16. */
+int fdtd_mlp_backward(const void *x, int x_is_bf16, const float *z, const float *dy, int rows, int k, int n,
+                      int act, const void *wt, float *dz_scratch, float *dw, float *db, float *dx,
+                      void *cuda_stream);
+
+/* Adam step on count FP32 parameters w with moments m, v and gradient g
+ * (step t >= 1): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * w -= lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps) + lr wd w.
+ * w_bf16 (optional) receives the updated weights rounded to BF16. */
+int fdtd_mlp_adam(float *w, float *m, float *v, const float *g, void *w_bf16, int count, float lr, float beta1,
+                  float beta2, float eps, float weight_decay, int t, void *cuda_stream);
+
+/* Mean-squared error: loss[0] += scale * sum (y - target)^2 (atomic; clear
+ * it first), dy = 2 scale (y - target); count elements. */
+int fdtd_mlp_mse(const float *y, const float *target, int count, float scale, float *dy, float *loss,
+                 void *cuda_stream);
+
+/* FP32 -> BF16 conversion (round to nearest even) of count elements. */
+int fdtd_mlp_to_bf16(const float *src, void *dst, int count, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDTD_GB300_MLP_H */

@@ -81,6 +81,12 @@ def load():
             "fdtd_batch_launch_info": (I, [P, I, ip, ip]),
             "fdtd_batch_last_error": (ctypes.c_char_p, [P]),
             "fdtd_batch_destroy": (None, [P]),
+            "fdtd_mlp_forward": (I, [P, I, I, I, P, P, I, I, P, P, P, P]),
+            "fdtd_mlp_backward": (I, [P, I, P, P, I, I, I, I, P, P, P, P, P, P]),
+            "fdtd_mlp_adam": (I, [P, P, P, P, P, I, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                  ctypes.c_float, ctypes.c_float, I, P]),
+            "fdtd_mlp_mse": (I, [P, P, I, ctypes.c_float, P, P, P]),
+            "fdtd_mlp_to_bf16": (I, [P, P, I, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)

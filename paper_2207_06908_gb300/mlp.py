@@ -1,0 +1,58 @@
+"""Surrogate-network layer calls on torch tensors (argument marshalling
+only; the arithmetic runs in the library's BF16 tensor-core kernels, see
+include/fdtd_mlp.h).  Tensors must be contiguous CUDA tensors."""
+from __future__ import annotations
+
+import ctypes
+
+from . import _lib
+
+ACT_NONE, ACT_GELU = 0, 1
+
+
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise _lib.FdtdError(rc, what)
+
+
+def forward(x, wt, bias, act, y_bf16=None, y_f32=None, z_f32=None):
+    import torch
+    lib = _lib.load()
+    rows, k = x.shape
+    n = wt.shape[0]
+    _check(lib.fdtd_mlp_forward(_p(x), int(x.dtype == torch.bfloat16), rows, k, _p(wt), _p(bias), n, act,
+                                _p(y_bf16), _p(y_f32), _p(z_f32), _stream()), "mlp_forward")
+
+
+def backward(x, z, dy, wt, act, dz, dw=None, db=None, dx=None):
+    import torch
+    lib = _lib.load()
+    rows, k = x.shape
+    n = dy.shape[1]
+    _check(lib.fdtd_mlp_backward(_p(x), int(x.dtype == torch.bfloat16), _p(z), _p(dy), rows, k, n, act, _p(wt),
+                                 _p(dz), _p(dw), _p(db), _p(dx), _stream()), "mlp_backward")
+
+
+def adam(w, m, v, g, w_bf16, lr, t, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0):
+    lib = _lib.load()
+    _check(lib.fdtd_mlp_adam(_p(w), _p(m), _p(v), _p(g), _p(w_bf16), w.numel(), lr, beta1, beta2, eps,
+                             weight_decay, int(t), _stream()), "mlp_adam")
+
+
+def mse(y, target, scale, dy, loss):
+    lib = _lib.load()
+    _check(lib.fdtd_mlp_mse(_p(y), _p(target), y.numel(), scale, _p(dy), _p(loss), _stream()), "mlp_mse")
+
+
+def to_bf16(src, dst):
+    lib = _lib.load()
+    _check(lib.fdtd_mlp_to_bf16(_p(src), _p(dst), src.numel(), _stream()), "mlp_to_bf16")

@@ -1,0 +1,76 @@
+"""Pins of the FP64 network oracle (CPU): GELU closed-form values, the
+backward pass against central finite differences, the first Adam step's
+closed form, and BF16 rounding against its definition."""
+import math
+
+import numpy as np
+
+from oracle import mlp_oracle as M
+
+
+def test_gelu_values():
+    # z Phi(z): Phi(0) = 1/2, Phi(1) = 0.841344746068543, Phi(-1) = 0.158655253931457
+    assert M.gelu(np.array(0.0)) == 0.0
+    assert abs(M.gelu(np.array(1.0)) - 0.841344746068543) < 1e-14
+    assert abs(M.gelu(np.array(-1.0)) + 0.158655253931457) < 1e-14
+    assert abs(M.gelu_grad(np.array(0.0)) - 0.5) < 1e-15
+    z = np.linspace(-4, 4, 81)
+    h = 1e-6
+    fd = (M.gelu(z + h) - M.gelu(z - h)) / (2 * h)
+    assert np.max(np.abs(fd - M.gelu_grad(z))) < 1e-8
+
+
+def make_net(rng, sizes):
+    layers = []
+    for k, n in zip(sizes[:-1], sizes[1:]):
+        layers.append((rng.standard_normal((n, k)) / math.sqrt(k), rng.standard_normal(n) * 0.1))
+    acts = ["gelu"] * (len(sizes) - 2) + ["none"]
+    return layers, acts
+
+
+def test_backward_matches_finite_differences():
+    rng = np.random.default_rng(0)
+    layers, acts = make_net(rng, [6, 9, 7, 5])
+    x = rng.standard_normal((11, 6))
+    t = rng.standard_normal((11, 5))
+
+    def loss(ls, xx):
+        return M.mse(M.forward(xx, ls, acts)[2], t, 1.0 / t.size)[0]
+
+    _, _, y = M.forward(x, layers, acts)
+    _, dout = M.mse(y, t, 1.0 / t.size)
+    grads, dx = M.backward(x, layers, acts, dout)
+    h = 1e-6
+    for l, (W, b) in enumerate(layers):
+        for (i, j) in [(0, 0), (W.shape[0] - 1, W.shape[1] - 1), (1, 2 % W.shape[1])]:
+            Wp = [(w.copy(), bb.copy()) for w, bb in layers]
+            Wm = [(w.copy(), bb.copy()) for w, bb in layers]
+            Wp[l][0][i, j] += h
+            Wm[l][0][i, j] -= h
+            fd = (loss(Wp, x) - loss(Wm, x)) / (2 * h)
+            assert abs(fd - grads[l][0][i, j]) < 1e-7 * max(1.0, abs(fd))
+        bp = [(w.copy(), bb.copy()) for w, bb in layers]
+        bm = [(w.copy(), bb.copy()) for w, bb in layers]
+        bp[l][1][0] += h
+        bm[l][1][0] -= h
+        assert abs((loss(bp, x) - loss(bm, x)) / (2 * h) - grads[l][1][0]) < 1e-7
+    xp, xm = x.copy(), x.copy()
+    xp[3, 2] += h
+    xm[3, 2] -= h
+    assert abs((loss(layers, xp) - loss(layers, xm)) / (2 * h) - dx[3, 2]) < 1e-7
+
+
+def test_adam_first_step_is_signed_lr():
+    """with m = v = 0, t = 1 and eps -> 0 the first step is -lr sign(g)"""
+    g = np.array([0.3, -2.0, 1e-3])
+    w, m, v = M.adam(np.zeros(3), np.zeros(3), np.zeros(3), g, 0.01, 0.9, 0.999, 1e-15, 0.0, 1)
+    np.testing.assert_allclose(w, -0.01 * np.sign(g), rtol=1e-9)
+
+
+def test_bf16_rounding():
+    # exactly representable values survive; 1 + 2^-8 is halfway between 1 and 1 + 2^-7 -> even (1)
+    assert M.bf16(np.array(1.5)) == 1.5
+    assert M.bf16(np.array(1.0 + 2.0 ** -8)) == 1.0
+    assert M.bf16(np.array(1.0 + 3 * 2.0 ** -8)) == 1.0 + 2.0 ** -6
+    x = np.random.default_rng(1).standard_normal(1000)
+    assert np.max(np.abs(M.bf16(x) - x) / np.abs(x)) <= 2.0 ** -8
