@@ -50,10 +50,24 @@ int fdtd_mlp_backward(const void *x, int x_is_bf16, const float *z, const float 
 int fdtd_mlp_adam(float *w, float *m, float *v, const float *g, void *w_bf16, int count, float lr, float beta1,
                   float beta2, float eps, float weight_decay, int t, void *cuda_stream);
 
-/* Mean-squared error: loss[0] += scale * sum (y - target)^2 (atomic; clear
- * it first), dy = 2 scale (y - target); count elements. */
-int fdtd_mlp_mse(const float *y, const float *target, int count, float scale, float *dy, float *loss,
-                 void *cuda_stream);
+/* Weighted squared error over rows x cols (row-major): loss[0] += scale *
+ * sum_r w_r sum_c (y - target)^2 (atomic; clear it first) and
+ * dy = 2 scale w_r (y - target).  row_weight [rows] may be NULL (w_r = 1);
+ * with w_r = 1 / ||target_r||^2 the loss is the sum of squared relative L2
+ * errors of the rows.  dy and loss are each optional. */
+int fdtd_mlp_mse(const float *y, const float *target, const float *row_weight, int rows, int cols, float scale,
+                 float *dy, float *loss, void *cuda_stream);
+
+/* err[r] = ||y_r - target_r|| / ||target_r|| (the plain norm of the
+ * difference when target_r is zero), rows x cols row-major. */
+int fdtd_mlp_row_rel_err(const float *y, const float *target, int rows, int cols, float *err, void *cuda_stream);
+
+/* dst[r, :] = src[idx[r], :] for r < rows (FP32 rows of cols entries; idx
+ * int32, each in range of src -- not checked). */
+int fdtd_mlp_gather_rows(const float *src, const int *idx, int rows, int cols, float *dst, void *cuda_stream);
+
+/* y[r, :] *= scale[r] in place. */
+int fdtd_mlp_scale_rows(float *y, const float *scale, int rows, int cols, void *cuda_stream);
 
 /* FP32 -> BF16 conversion (round to nearest even) of count elements. */
 int fdtd_mlp_to_bf16(const float *src, void *dst, int count, void *cuda_stream);

@@ -55,9 +55,11 @@ def backward(x, layers, acts, dout):
     return grads, d
 
 
-def mse(y, t, scale):
+def mse(y, t, scale, row_weight=None):
+    """scale * sum_r w_r ||y_r - t_r||^2 and its gradient with respect to y"""
     e = np.asarray(y, np.float64) - np.asarray(t, np.float64)
-    return scale * float(np.sum(e * e)), 2.0 * scale * e
+    w = np.ones(e.shape[0]) if row_weight is None else np.asarray(row_weight, np.float64)
+    return scale * float(np.sum(w[:, None] * e * e)), 2.0 * scale * w[:, None] * e
 
 
 def adam(w, m, v, g, lr, b1, b2, eps, wd, t):

@@ -85,7 +85,10 @@ def load():
             "fdtd_mlp_backward": (I, [P, I, P, P, I, I, I, I, P, P, P, P, P, P]),
             "fdtd_mlp_adam": (I, [P, P, P, P, P, I, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                   ctypes.c_float, ctypes.c_float, I, P]),
-            "fdtd_mlp_mse": (I, [P, P, I, ctypes.c_float, P, P, P]),
+            "fdtd_mlp_mse": (I, [P, P, P, I, I, ctypes.c_float, P, P, P]),
+            "fdtd_mlp_row_rel_err": (I, [P, P, I, I, P, P]),
+            "fdtd_mlp_gather_rows": (I, [P, P, I, I, P, P]),
+            "fdtd_mlp_scale_rows": (I, [P, P, I, I, P]),
             "fdtd_mlp_to_bf16": (I, [P, P, I, P]),
         }
         for name, (res, args) in sig.items():

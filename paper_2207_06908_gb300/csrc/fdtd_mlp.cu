@@ -156,13 +156,17 @@ __global__ void adam_kernel(float *w, float *m, float *v, const float *g, __nv_b
     }
 }
 
-__global__ void mse_kernel(const float *y, const float *t, int count, float scale, float *dy, float *loss)
+// one block per row: loss += scale w_r sum_c e^2, dy = 2 scale w_r e
+__global__ void mse_kernel(const float *y, const float *t, const float *row_w, int cols, float scale, float *dy,
+                           float *loss)
 {
     __shared__ float part[256];
+    const size_t base = (size_t)blockIdx.x * cols;
+    const float w = row_w ? row_w[blockIdx.x] : 1.f;
     float s = 0.f;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x) {
-        const float e = y[q] - t[q];
-        if (dy) dy[q] = 2.f * scale * e;
+    for (int c = threadIdx.x; c < cols; c += blockDim.x) {
+        const float e = y[base + c] - t[base + c];
+        if (dy) dy[base + c] = 2.f * scale * w * e;
         s += e * e;
     }
     part[threadIdx.x] = s;
@@ -171,7 +175,49 @@ __global__ void mse_kernel(const float *y, const float *t, int count, float scal
         if ((int)threadIdx.x < h) part[threadIdx.x] += part[threadIdx.x + h];
         __syncthreads();
     }
-    if (threadIdx.x == 0 && loss) atomicAdd(loss, scale * part[0]);
+    if (threadIdx.x == 0 && loss) atomicAdd(loss, scale * w * part[0]);
+}
+
+// one block per row: err_r = ||y_r - t_r|| / ||t_r||
+__global__ void row_rel_err_kernel(const float *y, const float *t, int cols, float *err)
+{
+    __shared__ float pe[256], pt[256];
+    const size_t base = (size_t)blockIdx.x * cols;
+    float se = 0.f, st = 0.f;
+    for (int c = threadIdx.x; c < cols; c += blockDim.x) {
+        const float e = y[base + c] - t[base + c];
+        se += e * e;
+        st += t[base + c] * t[base + c];
+    }
+    pe[threadIdx.x] = se;
+    pt[threadIdx.x] = st;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            pe[threadIdx.x] += pe[threadIdx.x + h];
+            pt[threadIdx.x] += pt[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) err[blockIdx.x] = pt[0] > 0.f ? sqrtf(pe[0] / pt[0]) : sqrtf(pe[0]);
+}
+
+__global__ void gather_rows_kernel(const float *src, const int *idx, int rows, int cols, float *dst)
+{
+    const long long total = (long long)rows * cols;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long r = q / cols;
+        dst[q] = src[(long long)idx[r] * cols + (q - r * cols)];
+    }
+}
+
+__global__ void scale_rows_kernel(float *y, const float *s, int rows, int cols)
+{
+    const long long total = (long long)rows * cols;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x)
+        y[q] *= s[q / cols];
 }
 
 __global__ void to_bf16_kernel(const float *src, __nv_bfloat16 *dst, int count)
@@ -251,13 +297,37 @@ int fdtd_mlp_adam(float *w, float *m, float *v, const float *g, void *w_bf16, in
     return rc(cudaGetLastError());
 }
 
-int fdtd_mlp_mse(const float *y, const float *target, int count, float scale, float *dy, float *loss,
-                 void *cuda_stream)
+int fdtd_mlp_mse(const float *y, const float *target, const float *row_weight, int rows, int cols, float scale,
+                 float *dy, float *loss, void *cuda_stream)
 {
-    if (!y || !target || count < 0) return FDTD_EINVAL;
-    if (count == 0) return FDTD_OK;
-    mse_kernel<<<std::min(grid1d(count), 1024), 256, 0, (cudaStream_t)cuda_stream>>>(y, target, count, scale, dy,
-                                                                                    loss);
+    if (!y || !target || rows < 0 || cols < 0) return FDTD_EINVAL;
+    if (rows == 0 || cols == 0) return FDTD_OK;
+    mse_kernel<<<rows, 256, 0, (cudaStream_t)cuda_stream>>>(y, target, row_weight, cols, scale, dy, loss);
+    return rc(cudaGetLastError());
+}
+
+int fdtd_mlp_row_rel_err(const float *y, const float *target, int rows, int cols, float *err, void *cuda_stream)
+{
+    if (!y || !target || !err || rows < 0 || cols < 0) return FDTD_EINVAL;
+    if (rows == 0) return FDTD_OK;
+    row_rel_err_kernel<<<rows, 256, 0, (cudaStream_t)cuda_stream>>>(y, target, cols, err);
+    return rc(cudaGetLastError());
+}
+
+int fdtd_mlp_gather_rows(const float *src, const int *idx, int rows, int cols, float *dst, void *cuda_stream)
+{
+    if (!src || !idx || !dst || rows < 0 || cols < 0) return FDTD_EINVAL;
+    if ((long long)rows * cols == 0) return FDTD_OK;
+    gather_rows_kernel<<<grid1d((long long)rows * cols), 256, 0, (cudaStream_t)cuda_stream>>>(src, idx, rows, cols,
+                                                                                            dst);
+    return rc(cudaGetLastError());
+}
+
+int fdtd_mlp_scale_rows(float *y, const float *scale, int rows, int cols, void *cuda_stream)
+{
+    if (!y || !scale || rows < 0 || cols < 0) return FDTD_EINVAL;
+    if ((long long)rows * cols == 0) return FDTD_OK;
+    scale_rows_kernel<<<grid1d((long long)rows * cols), 256, 0, (cudaStream_t)cuda_stream>>>(y, scale, rows, cols);
     return rc(cudaGetLastError());
 }
 

@@ -48,9 +48,29 @@ def adam(w, m, v, g, w_bf16, lr, t, beta1=0.9, beta2=0.999, eps=1e-8, weight_dec
                              weight_decay, int(t), _stream()), "mlp_adam")
 
 
-def mse(y, target, scale, dy, loss):
+def mse(y, target, scale, dy, loss, row_weight=None):
     lib = _lib.load()
-    _check(lib.fdtd_mlp_mse(_p(y), _p(target), y.numel(), scale, _p(dy), _p(loss), _stream()), "mlp_mse")
+    rows, cols = y.shape
+    _check(lib.fdtd_mlp_mse(_p(y), _p(target), _p(row_weight), rows, cols, scale, _p(dy), _p(loss), _stream()),
+           "mlp_mse")
+
+
+def row_rel_err(y, target, err):
+    lib = _lib.load()
+    rows, cols = y.shape
+    _check(lib.fdtd_mlp_row_rel_err(_p(y), _p(target), rows, cols, _p(err), _stream()), "mlp_row_rel_err")
+
+
+def gather_rows(src, idx, dst):
+    lib = _lib.load()
+    _check(lib.fdtd_mlp_gather_rows(_p(src), _p(idx), idx.numel(), src.shape[1], _p(dst), _stream()),
+           "mlp_gather_rows")
+
+
+def scale_rows(y, scale):
+    lib = _lib.load()
+    rows, cols = y.shape
+    _check(lib.fdtd_mlp_scale_rows(_p(y), _p(scale), rows, cols, _stream()), "mlp_scale_rows")
 
 
 def to_bf16(src, dst):

@@ -294,6 +294,12 @@ GROUND_SAMPLES = 512
 LEAD_RADIUS = 0.003
 
 
+def grounding_cells(length, depth):
+    """(rod length, burial depth of its top) in cells of GROUND_DX: the
+    discrete geometry the domain builder uses."""
+    return max(1, int(round(length / GROUND_DX))), int(round(depth / GROUND_DX))
+
+
 def grounding_domain(n, eps_r, sigma, length, radius, depth, rise, n_steps=GROUND_STEPS, name="ground"):
     """One grounding-electrode domain of n^3 cells, dx = 0.25 m, 8-cell CPML:
     soil (eps_r, sigma) below the surface node n - 14, air above; a vertical
@@ -308,8 +314,8 @@ def grounding_domain(n, eps_r, sigma, length, radius, depth, rise, n_steps=GROUN
     d = GROUND_CPML
     c = n // 2
     ks = n - 14                                    # surface node
-    kd = ks - int(round(depth / dx))               # rod top node
-    lc = max(1, int(round(length / dx)))
+    lc, dc = grounding_cells(length, depth)
+    kd = ks - dc                                   # rod top node
     kb = kd - lc                                   # rod bottom node
     if kb < d + 2:
         raise ValueError("rod does not fit the domain")

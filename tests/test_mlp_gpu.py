@@ -103,7 +103,8 @@ def test_network_gradients_vs_oracle(env):
         ins.append(yb if l < len(layers) - 1 else yf)
     loss = torch.zeros(1, **f32)
     dy = torch.empty((rows, 512), **f32)
-    mlp.mse(ins[-1], dev(torch, t, torch.float32), scale, dy, loss)
+    rw = 1.0 / np.sum(t.astype(np.float32).astype(np.float64) ** 2, axis=1)
+    mlp.mse(ins[-1], dev(torch, t, torch.float32), scale, dy, loss, dev(torch, rw, torch.float32))
     grads = [None] * len(layers)
     for l in range(len(layers) - 1, -1, -1):
         n, k = layers[l][0].shape
@@ -115,7 +116,7 @@ def test_network_gradients_vs_oracle(env):
         dy = dx
     torch.cuda.synchronize()
     _, _, yo = M.forward(x, layers, acts)
-    lo, dout = M.mse(yo, t, scale)
+    lo, dout = M.mse(yo, t, scale, rw)
     ref, _ = M.backward(x, layers, acts, dout)
     assert abs(loss.item() - lo) <= 1e-2 * lo
     for l in range(len(layers)):
@@ -140,3 +141,36 @@ def test_adam_step(env):
     assert rel(md.cpu().numpy(), mr) <= 1e-6
     assert rel(vd.cpu().numpy(), vr) <= 1e-6
     np.testing.assert_array_equal(wb.float().cpu().numpy(), M.bf16(wd_.cpu().numpy()).astype(np.float32))
+
+
+def test_row_kernels(env):
+    """weighted squared error, per-row relative error, row gather and row
+    scaling on a ragged shape"""
+    torch, mlp = env
+    rng = np.random.default_rng(8)
+    rows, cols = 37, 515
+    y = rng.standard_normal((rows, cols)).astype(np.float32).astype(np.float64)
+    t = rng.standard_normal((rows, cols)).astype(np.float32).astype(np.float64)
+    t[3] = 0.0
+    w = rng.uniform(0.5, 2.0, rows).astype(np.float32).astype(np.float64)
+    f32 = dict(dtype=torch.float32, device="cuda")
+    yd, td, wd = dev(torch, y, torch.float32), dev(torch, t, torch.float32), dev(torch, w, torch.float32)
+    loss, dy, err = torch.zeros(1, **f32), torch.empty((rows, cols), **f32), torch.empty(rows, **f32)
+    mlp.mse(yd, td, 0.25, dy, loss, wd)
+    mlp.row_rel_err(yd, td, err)
+    idx = rng.integers(0, rows, 50).astype(np.int32)
+    g = torch.empty((50, cols), **f32)
+    mlp.gather_rows(yd, torch.tensor(idx, device="cuda"), g)
+    s = rng.uniform(-3, 3, rows)
+    ys = yd.clone()
+    mlp.scale_rows(ys, dev(torch, s, torch.float32))
+    torch.cuda.synchronize()
+    lo, dref = M.mse(y, t, 0.25, w)
+    assert loss.item() == pytest.approx(lo, rel=1e-5)
+    assert rel(dy.cpu().numpy(), dref) <= 1e-6
+    e = np.linalg.norm(y - t, axis=1)
+    nt = np.linalg.norm(t, axis=1)
+    ref = np.where(nt > 0, e / np.where(nt > 0, nt, 1), e)
+    np.testing.assert_allclose(err.cpu().numpy(), ref, rtol=1e-5)
+    np.testing.assert_array_equal(g.cpu().numpy(), y[idx].astype(np.float32))
+    assert rel(ys.cpu().numpy(), y * s.astype(np.float32)[:, None]) <= 1e-7

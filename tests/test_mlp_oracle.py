@@ -4,6 +4,7 @@ closed form, and BF16 rounding against its definition."""
 import math
 
 import numpy as np
+import pytest
 
 from oracle import mlp_oracle as M
 
@@ -74,3 +75,21 @@ def test_bf16_rounding():
     assert M.bf16(np.array(1.0 + 3 * 2.0 ** -8)) == 1.0 + 2.0 ** -6
     x = np.random.default_rng(1).standard_normal(1000)
     assert np.max(np.abs(M.bf16(x) - x) / np.abs(x)) <= 2.0 ** -8
+
+
+def test_weighted_mse_is_sum_of_squared_relative_errors():
+    """with w_r = 1/||t_r||^2 the weighted loss is sum_r (||y_r - t_r|| / ||t_r||)^2;
+    its gradient matches central differences"""
+    rng = np.random.default_rng(4)
+    y, t = rng.standard_normal((5, 9)), rng.standard_normal((5, 9)) * 3
+    w = 1.0 / np.sum(t * t, axis=1)
+    loss, dy = M.mse(y, t, 0.5, w)
+    rel = np.linalg.norm(y - t, axis=1) / np.linalg.norm(t, axis=1)
+    assert loss == pytest.approx(0.5 * np.sum(rel ** 2), rel=1e-12)
+    h = 1e-6
+    for r, c in [(0, 0), (2, 5), (4, 8)]:
+        yp, ym = y.copy(), y.copy()
+        yp[r, c] += h
+        ym[r, c] -= h
+        fd = (M.mse(yp, t, 0.5, w)[0] - M.mse(ym, t, 0.5, w)[0]) / (2 * h)
+        assert dy[r, c] == pytest.approx(fd, rel=1e-7)
