@@ -36,6 +36,44 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 }  // namespace
 
+// The z-layer launch and the launch over the planes between the layers
+// update disjoint planes from the previous step's buffers only, so one step
+// runs them concurrently: the z layers on a side stream forked from the
+// step's stream and joined back to it before the source / probe kernel.
+struct Fork {
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaError_t init()
+    {
+        cudaError_t e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+        if (e != cudaSuccess) destroy();
+        return e;
+    }
+    void destroy()
+    {
+        if (join) cudaEventDestroy(join);
+        if (fork) cudaEventDestroy(fork);
+        if (side) cudaStreamDestroy(side);
+        side = nullptr;
+        fork = join = nullptr;
+    }
+    // launch_a on the side stream and launch_b on s, both after the work
+    // already queued on s; s continues after both
+    template <class A, class B>
+    cudaError_t run(cudaStream_t s, A launch_a, B launch_b) const
+    {
+        cudaError_t e = cudaEventRecord(fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork, 0);
+        if (e == cudaSuccess) e = launch_a(side);
+        if (e == cudaSuccess) e = cudaEventRecord(join, side);
+        if (e == cudaSuccess) e = launch_b(s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, join, 0);
+        return e;
+    }
+};
+
 struct fdtd_grid {
     int nx = 0, ny = 0, nz = 0;
     double dx = 0, dt = 0, courant = 0;
@@ -90,6 +128,7 @@ struct fdtd_grid {
     long step = 0;
     int kz = 0;
     cudaStream_t cap_stream = nullptr;
+    Fork fk;                      // concurrent z-layer launch (two-launch grids)
     cudaGraphExec_t graph = nullptr;
     std::string err;
 };
@@ -482,9 +521,17 @@ fdtd::BatchArgs grid_launch(const fdtd_grid *g, int parity, int l, int *work, in
 cudaError_t enqueue_step(fdtd_grid *g, int parity, cudaStream_t s)
 {
     cudaError_t e = cudaSuccess;
-    for (int l = 0; l < g->n_launch && e == cudaSuccess; ++l)
-        e = fdtd::launch_step(single_args(g, parity, l), grid_launch(g, parity, l, g->lc[l].work, g->err_d),
-                              g->lc[l].grid, s);
+    auto launch = [g, parity](int l) {
+        return [g, parity, l](cudaStream_t st) {
+            return fdtd::launch_step(single_args(g, parity, l), grid_launch(g, parity, l, g->lc[l].work, g->err_d),
+                                     g->lc[l].grid, st);
+        };
+    };
+    if (g->n_launch == 2 && g->fk.side) {
+        e = g->fk.run(s, launch(1), launch(0));
+    } else {
+        for (int l = 0; l < g->n_launch && e == cudaSuccess; ++l) e = launch(l)(s);
+    }
     if (e != cudaSuccess) return e;
     if (!g->srcs.empty() || !g->probes.empty()) e = fdtd::launch_edges(edge_args(g, parity), s);
     return e;
@@ -869,6 +916,10 @@ int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_by
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(g, e, "upload");
     if (int rc = setup_step_kernel(g)) return rc;
+    if (g->n_launch == 2 && !g->fk.side) {
+        e = g->fk.init();
+        if (e != cudaSuccess) return cuda_fail(g, e, "side stream");
+    }
     // the grid as a one-domain step launch: descriptors and arguments per
     // launch and input parity, item ranges {0, items} per launch
     std::memset(&g->slot_h, 0, sizeof g->slot_h);
@@ -1003,6 +1054,7 @@ void fdtd_destroy(fdtd_grid *g)
     if (g->finalized) cudaStreamSynchronize(g->stream);
     if (g->graph) cudaGraphExecDestroy(g->graph);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    g->fk.destroy();
     if (g->own_arena && g->arena) cudaFree(g->arena);
     delete g;
 }
@@ -1027,6 +1079,7 @@ struct fdtd_batch {
     int max_classes = 0, max_d = 0, n_launch = 0;
     bool has_edges = false;
     cudaStream_t cap = nullptr;
+    Fork fk;                        // concurrent z-layer launch
     cudaGraphExec_t graph = nullptr;
     int parity = 0;
     long step = 0;
@@ -1041,26 +1094,34 @@ int bfail(fdtd_batch *b, int code, const std::string &msg)
     return code;
 }
 
+cudaError_t batch_launch(const fdtd_batch *b, int parity, int l, cudaStream_t s)
+{
+    fdtd::BatchArgs a{};
+    a.doms = b->doms;
+    a.item_start = b->item_start[l];
+    a.n_domains = (int)b->grids.size();
+    a.nitems = b->nitems[l];
+    a.launch = l;
+    a.parity = parity;
+    a.work = b->work + 2 * l;
+    a.err = b->errf;
+    a.max_classes = b->max_classes;
+    a.max_d = b->max_d;
+    a.region = b->region[l];
+    a.nh = b->nh[l];
+    static const fdtd::SingleArgs none{};
+    return fdtd::launch_step(none, a, b->grid[l], s);
+}
+
 cudaError_t batch_enqueue(fdtd_batch *b, int parity, cudaStream_t s)
 {
     cudaError_t e = cudaSuccess;
-    for (int l = 0; l < b->n_launch && e == cudaSuccess; ++l) {
-        if (b->nitems[l] == 0) continue;
-        fdtd::BatchArgs a{};
-        a.doms = b->doms;
-        a.item_start = b->item_start[l];
-        a.n_domains = (int)b->grids.size();
-        a.nitems = b->nitems[l];
-        a.launch = l;
-        a.parity = parity;
-        a.work = b->work + 2 * l;
-        a.err = b->errf;
-        a.max_classes = b->max_classes;
-        a.max_d = b->max_d;
-        a.region = b->region[l];
-        a.nh = b->nh[l];
-        static const fdtd::SingleArgs none{};
-        e = fdtd::launch_step(none, a, b->grid[l], s);
+    auto launch = [b, parity](int l) { return [b, parity, l](cudaStream_t st) { return batch_launch(b, parity, l, st); }; };
+    if (b->fk.side) {
+        e = b->fk.run(s, launch(1), launch(0));
+    } else {
+        for (int l = 0; l < b->n_launch && e == cudaSuccess; ++l)
+            if (b->nitems[l] > 0) e = launch(l)(s);
     }
     if (e == cudaSuccess && b->has_edges)
         e = fdtd::launch_edges_batch(b->edges, (int)b->grids.size(), parity, s);
@@ -1157,6 +1218,7 @@ int fdtd_batch_create(int n, fdtd_grid *const *grids, void *cuda_stream, fdtd_ba
     // the grids' own work must be finished before the batch reads them
     for (fdtd_grid *g : b->grids)
         if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e == cudaSuccess && b->n_launch == 2 && b->nitems[0] > 0 && b->nitems[1] > 0) e = b->fk.init();
     if (e != cudaSuccess) { cudaFree(b->mem); delete b; return FDTD_ECUDA; }
     *out = b;
     return FDTD_OK;
@@ -1232,6 +1294,7 @@ void fdtd_batch_destroy(fdtd_batch *b)
     cudaStreamSynchronize(b->stream);
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->cap) cudaStreamDestroy(b->cap);
+    b->fk.destroy();
     if (b->mem) cudaFree(b->mem);
     delete b;
 }

@@ -57,6 +57,17 @@ using geom::CBX;
 using geom::CBY;
 
 constexpr int al128(int v) { return (v + 127) / 128 * 128; }
+
+// Shared-memory copy of a class's coefficients: three float4 rows
+// {db_x, db_y, db_z, 0}, {ca_x, ca_y, ca_z, 0}, {cb_x, cb_y, cb_z, 0}, so the
+// H half step reads one 16-byte row and the E half step two (the global
+// table keeps kNumCoef floats per class: ca[3], cb[3], db[3]).
+constexpr int kTabStride = 12;
+__device__ __forceinline__ int tab_src(int slot)
+{
+    const int r = slot >> 2, c = slot & 3;
+    return c == 3 ? -1 : (r == 0 ? 6 + c : (r == 1 ? c : 3 + c));
+}
 constexpr int E_COMP = al128(EBX * EBY * 4);
 constexpr int H_COMP = al128(HBX * HBY * 4);
 constexpr int C_BYTES = al128(CBX * CBY);
@@ -101,7 +112,7 @@ struct Layout {
 
 __host__ __device__ inline int smem_bytes(int n_classes, int d, int region, int nh)
 {
-    return Layout(region, nh).tab + al128(sizeof(StepArgs)) + n_classes * kNumCoef * 4 + 3 * PR_COUNT * 2 * d * 4 +
+    return Layout(region, nh).tab + al128(sizeof(StepArgs)) + n_classes * kTabStride * 4 + 3 * PR_COUNT * 2 * d * 4 +
            128;
 }
 
@@ -201,7 +212,7 @@ __device__ __forceinline__ float cpml(float dif, const float *pr, int s, int d2,
 // analogues): Hx += db [dEy/dz - dEz/dy], Hy += db [dEz/dx - dEx/dz],
 // Hz += db [dEx/dy - dEy/dx]; differences in field units, 1/dx in db.
 template <bool CPML>
-__device__ __forceinline__ void h_core(const StepArgs &a, const float *t, const float *prof, const Slab &L,
+__device__ __forceinline__ void h_core(const StepArgs &a, const float4 *t, const float *prof, const Slab &L,
                                        long long g, bool own, float ex, float ey, float ez, float ey_x1,
                                        float ez_x1, float ex_y1, float ez_y1, float ex_z1, float ey_z1, float hx0,
                                        float hy0, float hz0, float &hx, float &hy, float &hz)
@@ -233,15 +244,16 @@ __device__ __forceinline__ void h_core(const StepArgs &a, const float *t, const 
             hy_z = cpml(hy_z, pr, L.sz, d2, o1, a.psi_out[PSI_HY_Z], g, own);
         }
     }
-    hx = hx0 + t[6] * (hx_z - hx_y);
-    hy = hy0 + t[7] * (hy_x - hy_z);
-    hz = hz0 + t[8] * (hz_y - hz_x);
+    const float4 db = t[0];
+    hx = hx0 + db.x * (hx_z - hx_y);
+    hy = hy0 + db.y * (hy_x - hy_z);
+    hz = hz0 + db.z * (hz_y - hz_x);
 }
 
 // E^{n+1} of cell (i,j,k) (Eq. fdtdex with sigma E time-averaged):
 // E = ca E + cb [curl_h H^{n+1/2}], 1/dx in cb.
 template <bool CPML>
-__device__ __forceinline__ void e_core(const StepArgs &a, const float *t, const float *prof, const Slab &L,
+__device__ __forceinline__ void e_core(const StepArgs &a, const float4 *t, const float *prof, const Slab &L,
                                        long long g, float ex, float ey, float ez, float hx, float hy, float hz,
                                        float hz_ym, float hx_ym, float hz_xm, float hy_xm, float hx_zm,
                                        float hy_zm, float &ex1, float &ey1, float &ez1)
@@ -273,9 +285,10 @@ __device__ __forceinline__ void e_core(const StepArgs &a, const float *t, const 
             ey_z = cpml(ey_z, pr, L.sz, d2, o1, a.psi_out[PSI_EY_Z], g, true);
         }
     }
-    ex1 = t[0] * ex + t[3] * (ex_y - ex_z);
-    ey1 = t[1] * ey + t[4] * (ey_z - ey_x);
-    ez1 = t[2] * ez + t[5] * (ez_x - ez_y);
+    const float4 ca = t[1], cb = t[2];
+    ex1 = ca.x * ex + cb.x * (ex_y - ex_z);
+    ey1 = ca.y * ey + cb.y * (ey_z - ey_x);
+    ez1 = ca.z * ez + cb.z * (ez_x - ez_y);
 }
 
 // ---- shared-memory views ----------------------------------------------------
@@ -402,6 +415,7 @@ struct Cons {
     bool halo;               // the halo warp
     int hslot;               // bytes per H slot
     __device__ uint32_t bar(int b) const { return (uint32_t)__cvta_generic_to_shared(&bars[b]); }
+    __device__ const float4 *coef(int cls) const { return reinterpret_cast<const float4 *>(tab + cls * kTabStride); }
     __device__ uint32_t fullE(uint32_t q) const { return bar(q % NE); }
     __device__ uint32_t emptyE(uint32_t q) const { return bar(NE + q % NE); }
     __device__ uint32_t fullH(uint32_t q) const { return bar(2 * NE + q % NH); }
@@ -474,7 +488,7 @@ __device__ __forceinline__ bool run_item(const Cons<NH> &C, const Item &it, uint
                                                   row * HBX + lx, -1)
                                         : Slab{-1, -1, -1, nullptr, -1, -1, -1, -1};
                     const long long g = (long long)k * a.plane + (long long)j * a.pitch + i;
-                    h_core<CPML>(a, C.tab + h0.cls(row, clx) * kNumCoef, C.prof, L, g, false, e0.e(0, row, lx),
+                    h_core<CPML>(a, C.coef(h0.cls(row, clx)), C.prof, L, g, false, e0.e(0, row, lx),
                                  e0.e(1, row, lx), e0.e(2, row, lx), e0.e(1, row, lx + 1), e0.e(2, row, lx + 1),
                                  e0.e(0, row + 1, lx), e0.e(2, row + 1, lx), ecur[0][r], ecur[1][r],
                                  h0.h(0, row, lx), h0.h(1, row, lx), h0.h(2, row, lx), hxp[r], hyp[r], hz);
@@ -509,7 +523,7 @@ __device__ __forceinline__ bool run_item(const Cons<NH> &C, const Item &it, uint
                     const Slab L = CPML ? slab_in(sg, hk, sx, sy[r], sz, xo[r], yo[r], row * HBX + lx,
                                                   (2 * H_COMP) / 4 + (row - 1) * TX + lane)
                                         : Slab{-1, -1, -1, nullptr, -1, -1, -1, -1};
-                    h_core<CPML>(a, C.tab + cl[r] * kNumCoef, C.prof, L, g, true, ecur[0][r], ecur[1][r],
+                    h_core<CPML>(a, C.coef(cl[r]), C.prof, L, g, true, ecur[0][r], ecur[1][r],
                                  ecur[2][r], ek.e(1, row, lx + 1), ek.e(2, row, lx + 1), ex_y1, ez_y1, enx[0][r],
                                  enx[1][r], hk.h(0, row, lx), hk.h(1, row, lx), hk.h(2, row, lx), hx, hy, hz);
                     a.Hout[0][g] = hx;
@@ -536,7 +550,7 @@ __device__ __forceinline__ bool run_item(const Cons<NH> &C, const Item &it, uint
                     const Slab L = CPML ? slab_in(sg, hk, slab_of(hi, a.nx, d), slab_of(hj, a.ny, d), sz, hxo[pass],
                                                   hyo[pass], hrow * HBX + hcol, -1)
                                         : Slab{-1, -1, -1, nullptr, -1, -1, -1, -1};
-                    h_core<CPML>(a, C.tab + hk.cls(hrow, hcol - XO + CXO) * kNumCoef, C.prof, L, g, false,
+                    h_core<CPML>(a, C.coef(hk.cls(hrow, hcol - XO + CXO)), C.prof, L, g, false,
                                  ek.e(0, hrow, hcol), ek.e(1, hrow, hcol), ek.e(2, hrow, hcol),
                                  ek.e(1, hrow, hcol + 1), ek.e(2, hrow, hcol + 1), ek.e(0, hrow + 1, hcol),
                                  ek.e(2, hrow + 1, hcol), ek1.e(0, hrow, hcol), ek1.e(1, hrow, hcol),
@@ -564,7 +578,7 @@ __device__ __forceinline__ bool run_item(const Cons<NH> &C, const Item &it, uint
                                                   (2 * H_COMP) / 4 + (row - 1) * TX + lane)
                                         : Slab{-1, -1, -1, nullptr, -1, -1, -1, -1};
                     float ex1, ey1, ez1;
-                    e_core<CPML>(a, C.tab + cl[r] * kNumCoef, C.prof, L, g, ecur[0][r], ecur[1][r], ecur[2][r],
+                    e_core<CPML>(a, C.coef(cl[r]), C.prof, L, g, ecur[0][r], ecur[1][r], ecur[2][r],
                                  hnw[0][r], hnw[1][r], hnw[2][r], hz_ym, hx_ym, C.hn(hb, 2, row, lx - 1),
                                  C.hn(hb, 1, row, lx - 1), hxp[r], hyp[r], ex1, ey1, ez1);
                     a.Eout[0][g] = ex1;
@@ -609,7 +623,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
     const Layout Lo(B.region, NH);
     StepArgs *sa = reinterpret_cast<StepArgs *>(smem + Lo.tab);          // current domain's arguments
     float *tab = reinterpret_cast<float *>(smem + Lo.tab + al128(sizeof(StepArgs)));
-    float *prof = tab + B.max_classes * kNumCoef;  // [axis][PR_COUNT][2d], slab entries only
+    float *prof = tab + B.max_classes * kTabStride;  // [axis][PR_COUNT][2d], slab entries only
     float *hnew = reinterpret_cast<float *>(smem + Lo.hnew);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + Lo.bar);
     volatile int *abort = reinterpret_cast<volatile int *>(smem + Lo.misc);
@@ -622,7 +636,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
     if (!BATCH) {
         // the one domain's coefficient table and CPML profiles, once
         const StepArgs &ga = S.a;
-        for (int q = threadIdx.x; q < ga.n_classes * kNumCoef; q += NTHREADS) tab[q] = __ldg(ga.table + q);
+        for (int q = threadIdx.x; q < ga.n_classes * kTabStride; q += NTHREADS) {
+            const int cl = q / kTabStride, src = tab_src(q - cl * kTabStride);
+            tab[q] = src < 0 ? 0.f : __ldg(ga.table + cl * kNumCoef + src);
+        }
         if (ga.d > 0) {
             const int d2 = 2 * ga.d, per = PR_COUNT * d2;
             for (int q = threadIdx.x; q < 3 * per; q += NTHREADS) {
@@ -761,8 +778,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
                 int *dst = reinterpret_cast<int *>(sa);
                 for (int q = tid; q < (int)(sizeof(StepArgs) / 4); q += NCONS) dst[q] = __ldg(src + q);
                 const StepArgs &ga = D.a[B.launch][B.parity];
-                const int ncoef = ga.n_classes * kNumCoef;
-                for (int q = tid; q < ncoef; q += NCONS) tab[q] = __ldg(ga.table + q);
+                for (int q = tid; q < ga.n_classes * kTabStride; q += NCONS) {
+                    const int cl = q / kTabStride, src = tab_src(q - cl * kTabStride);
+                    tab[q] = src < 0 ? 0.f : __ldg(ga.table + cl * kNumCoef + src);
+                }
                 if (ga.d > 0) {
                     const int d2 = 2 * ga.d, per = PR_COUNT * d2;
                     for (int q = tid; q < 3 * per; q += NCONS) {
