@@ -151,7 +151,7 @@ int step_tile_x();
 int step_tile_y();
 int step_threads();
 int step_smem_bytes(int n_classes, int d, int region, int nh);
-PsiGeom step_psi_geom(int d);
+PsiGeom step_psi_geom(int d, int nx, int ny);
 // region size and box-group offsets for a launch that stages z alone
 // (zxy = 0) or z together with the x / y layers (zxy = 1)
 void step_region(const PsiGeom &pg, int zxy, int *region, int *ox, int *oy);

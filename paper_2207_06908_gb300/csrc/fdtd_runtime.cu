@@ -586,7 +586,7 @@ cudaError_t ensure_smem(const void *kernel, int bytes)
 int setup_step_kernel(fdtd_grid *g)
 {
     using namespace fdtd::geom;
-    g->pg = fdtd::step_psi_geom(g->d);
+    g->pg = fdtd::step_psi_geom(g->d, g->nx, g->ny);
     for (int p = 0; p < 2; ++p) {
         for (int c = 0; c < 3; ++c) {
             if (!encode_map(&g->maps[p].e[c], g->F[p][c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, EBX, EBY) ||

@@ -198,24 +198,37 @@ struct Slab {
 
 __device__ __forceinline__ int slab_of(int i, int n, int d) { return i < d ? i : (i >= n - d ? i - (n - 2 * d) : -1); }
 
-// CPML convolution term (Sec. 2.2): psi <- b psi + c dif, term = dif/kappa + psi
-__device__ __forceinline__ float cpml(float dif, const float *pr, int s, int d2, float old, float *pout,
-                                      long long g, bool write)
+// CPML convolution of the two differences along one axis (Sec. 2.2): with
+// the profile b, c, 1/kappa of the cell's slab entry s,
+// psi <- b psi + c dif, dif <- dif / kappa + psi.  The profile values are
+// read once for both differences, before any store.
+template <bool WRITE>
+__device__ __forceinline__ void cpml2(float &d0, float &d1, const float *pr, int s, int d2, float o0, float o1,
+                                      float *out0, float *out1, long long g)
 {
     const float b = pr[s], c = pr[d2 + s], ki = pr[2 * d2 + s];
-    const float p = b * old + c * dif;
-    if (write) pout[g] = p;
-    return dif * ki + p;
+    const float p0 = b * o0 + c * d0, p1 = b * o1 + c * d1;
+    if (WRITE) {
+        out0[g] = p0;
+        out1[g] = p1;
+    }
+    d0 = d0 * ki + p0;
+    d1 = d1 * ki + p1;
 }
 
 // H^{n+1/2} of cell (i,j,k) from E^n around it (Eq. fdtdhx and its cyclic
 // analogues): Hx += db [dEy/dz - dEz/dy], Hy += db [dEz/dx - dEx/dz],
 // Hz += db [dEx/dy - dEy/dx]; differences in field units, 1/dx in db.
-template <bool CPML>
+// STAGED: every auxiliary the cell needs is in the staged boxes (true of
+// the cells an item updates); otherwise one outside them is read from
+// global memory.  WRITE: the cell is one the
+// item updates, so the new auxiliaries are stored (halo and warm-up cells
+// are recomputed only).
+template <bool CPML, bool STAGED, bool WRITE>
 __device__ __forceinline__ void h_core(const StepArgs &a, const float4 *t, const float *prof, const Slab &L,
-                                       long long g, bool own, float ex, float ey, float ez, float ey_x1,
-                                       float ez_x1, float ex_y1, float ez_y1, float ex_z1, float ey_z1, float hx0,
-                                       float hy0, float hz0, float &hx, float &hy, float &hz)
+                                       long long g, float ex, float ey, float ez, float ey_x1, float ez_x1,
+                                       float ex_y1, float ez_y1, float ex_z1, float ey_z1, float hx0, float hy0,
+                                       float hz0, float &hx, float &hy, float &hz)
 {
     float hx_z = ey_z1 - ey, hx_y = ez_y1 - ez;
     float hy_x = ez_x1 - ez, hy_z = ex_z1 - ex;
@@ -223,25 +236,23 @@ __device__ __forceinline__ void h_core(const StepArgs &a, const float4 *t, const
     if (CPML) {
         const int d2 = 2 * a.d, per = PR_COUNT * d2;
         if (L.sx >= 0) {
-            const float *pr = prof + PR_BH * d2;
-            const float o0 = L.xo >= 0 ? L.base[L.xo] : __ldg(a.psi_in[PSI_HY_X] + g);
-            const float o1 = L.xo >= 0 ? L.base[L.xo + a.pg.xb / 4] : __ldg(a.psi_in[PSI_HZ_X] + g);
-            hy_x = cpml(hy_x, pr, L.sx, d2, o0, a.psi_out[PSI_HY_X], g, own);
-            hz_x = cpml(hz_x, pr, L.sx, d2, o1, a.psi_out[PSI_HZ_X], g, own);
+            const int q = a.pg.xb >> 2;
+            const float o0 = (STAGED || L.xo >= 0) ? L.base[L.xo] : __ldg(a.psi_in[PSI_HY_X] + g);
+            const float o1 = (STAGED || L.xo >= 0) ? L.base[L.xo + q] : __ldg(a.psi_in[PSI_HZ_X] + g);
+            cpml2<WRITE>(hy_x, hz_x, prof + PR_BH * d2, L.sx, d2, o0, o1, a.psi_out[PSI_HY_X], a.psi_out[PSI_HZ_X], g);
         }
         if (L.sy >= 0) {
-            const float *pr = prof + per + PR_BH * d2;
-            const float o0 = L.yo >= 0 ? L.base[L.yo] : __ldg(a.psi_in[PSI_HX_Y] + g);
-            const float o1 = L.yo >= 0 ? L.base[L.yo + a.pg.yb / 4] : __ldg(a.psi_in[PSI_HZ_Y] + g);
-            hx_y = cpml(hx_y, pr, L.sy, d2, o0, a.psi_out[PSI_HX_Y], g, own);
-            hz_y = cpml(hz_y, pr, L.sy, d2, o1, a.psi_out[PSI_HZ_Y], g, own);
+            const int q = a.pg.yb >> 2;
+            const float o0 = (STAGED || L.yo >= 0) ? L.base[L.yo] : __ldg(a.psi_in[PSI_HX_Y] + g);
+            const float o1 = (STAGED || L.yo >= 0) ? L.base[L.yo + q] : __ldg(a.psi_in[PSI_HZ_Y] + g);
+            cpml2<WRITE>(hx_y, hz_y, prof + per + PR_BH * d2, L.sy, d2, o0, o1, a.psi_out[PSI_HX_Y],
+                       a.psi_out[PSI_HZ_Y], g);
         }
         if (L.sz >= 0) {
-            const float *pr = prof + 2 * per + PR_BH * d2;
-            const float o0 = L.zo >= 0 ? L.base[L.zo] : __ldg(a.psi_in[PSI_HX_Z] + g);
-            const float o1 = L.zo >= 0 ? L.base[L.zo + H_COMP / 4] : __ldg(a.psi_in[PSI_HY_Z] + g);
-            hx_z = cpml(hx_z, pr, L.sz, d2, o0, a.psi_out[PSI_HX_Z], g, own);
-            hy_z = cpml(hy_z, pr, L.sz, d2, o1, a.psi_out[PSI_HY_Z], g, own);
+            const float o0 = (STAGED || L.zo >= 0) ? L.base[L.zo] : __ldg(a.psi_in[PSI_HX_Z] + g);
+            const float o1 = (STAGED || L.zo >= 0) ? L.base[L.zo + H_COMP / 4] : __ldg(a.psi_in[PSI_HY_Z] + g);
+            cpml2<WRITE>(hx_z, hy_z, prof + 2 * per + PR_BH * d2, L.sz, d2, o0, o1, a.psi_out[PSI_HX_Z],
+                       a.psi_out[PSI_HY_Z], g);
         }
     }
     const float4 db = t[0];
@@ -251,7 +262,8 @@ __device__ __forceinline__ void h_core(const StepArgs &a, const float4 *t, const
 }
 
 // E^{n+1} of cell (i,j,k) (Eq. fdtdex with sigma E time-averaged):
-// E = ca E + cb [curl_h H^{n+1/2}], 1/dx in cb.
+// E = ca E + cb [curl_h H^{n+1/2}], 1/dx in cb.  Only cells the item
+// updates, whose auxiliaries are staged.
 template <bool CPML>
 __device__ __forceinline__ void e_core(const StepArgs &a, const float4 *t, const float *prof, const Slab &L,
                                        long long g, float ex, float ey, float ez, float hx, float hy, float hz,
@@ -264,26 +276,18 @@ __device__ __forceinline__ void e_core(const StepArgs &a, const float4 *t, const
     if (CPML) {
         const int d2 = 2 * a.d, per = PR_COUNT * d2;
         if (L.sx >= 0) {
-            const float *pr = prof + PR_BE * d2;
-            const float o0 = L.xo >= 0 ? L.base[L.xo + 2 * (a.pg.xb / 4)] : __ldg(a.psi_in[PSI_EY_X] + g);
-            const float o1 = L.xo >= 0 ? L.base[L.xo + 3 * (a.pg.xb / 4)] : __ldg(a.psi_in[PSI_EZ_X] + g);
-            ey_x = cpml(ey_x, pr, L.sx, d2, o0, a.psi_out[PSI_EY_X], g, true);
-            ez_x = cpml(ez_x, pr, L.sx, d2, o1, a.psi_out[PSI_EZ_X], g, true);
+            const int q = a.pg.xb >> 2;
+            cpml2<true>(ey_x, ez_x, prof + PR_BE * d2, L.sx, d2, L.base[L.xo + 2 * q], L.base[L.xo + 3 * q],
+                        a.psi_out[PSI_EY_X], a.psi_out[PSI_EZ_X], g);
         }
         if (L.sy >= 0) {
-            const float *pr = prof + per + PR_BE * d2;
-            const float o0 = L.yo >= 0 ? L.base[L.yo + 2 * (a.pg.yb / 4)] : __ldg(a.psi_in[PSI_EX_Y] + g);
-            const float o1 = L.yo >= 0 ? L.base[L.yo + 3 * (a.pg.yb / 4)] : __ldg(a.psi_in[PSI_EZ_Y] + g);
-            ex_y = cpml(ex_y, pr, L.sy, d2, o0, a.psi_out[PSI_EX_Y], g, true);
-            ez_y = cpml(ez_y, pr, L.sy, d2, o1, a.psi_out[PSI_EZ_Y], g, true);
+            const int q = a.pg.yb >> 2;
+            cpml2<true>(ex_y, ez_y, prof + per + PR_BE * d2, L.sy, d2, L.base[L.yo + 2 * q], L.base[L.yo + 3 * q],
+                        a.psi_out[PSI_EX_Y], a.psi_out[PSI_EZ_Y], g);
         }
-        if (L.sz >= 0) {
-            const float *pr = prof + 2 * per + PR_BE * d2;
-            const float o0 = L.zeo >= 0 ? L.base[L.zeo] : __ldg(a.psi_in[PSI_EX_Z] + g);
-            const float o1 = L.zeo >= 0 ? L.base[L.zeo + PE_BYTES / 4] : __ldg(a.psi_in[PSI_EY_Z] + g);
-            ex_z = cpml(ex_z, pr, L.sz, d2, o0, a.psi_out[PSI_EX_Z], g, true);
-            ey_z = cpml(ey_z, pr, L.sz, d2, o1, a.psi_out[PSI_EY_Z], g, true);
-        }
+        if (L.sz >= 0)
+            cpml2<true>(ex_z, ey_z, prof + 2 * per + PR_BE * d2, L.sz, d2, L.base[L.zeo],
+                        L.base[L.zeo + PE_BYTES / 4], a.psi_out[PSI_EX_Z], a.psi_out[PSI_EY_Z], g);
     }
     const float4 ca = t[1], cb = t[2];
     ex1 = ca.x * ex + cb.x * (ex_y - ex_z);
@@ -488,7 +492,7 @@ __device__ __forceinline__ bool run_item(const Cons<NH> &C, const Item &it, uint
                                                   row * HBX + lx, -1)
                                         : Slab{-1, -1, -1, nullptr, -1, -1, -1, -1};
                     const long long g = (long long)k * a.plane + (long long)j * a.pitch + i;
-                    h_core<CPML>(a, C.coef(h0.cls(row, clx)), C.prof, L, g, false, e0.e(0, row, lx),
+                    h_core<CPML, false, false>(a, C.coef(h0.cls(row, clx)), C.prof, L, g, e0.e(0, row, lx),
                                  e0.e(1, row, lx), e0.e(2, row, lx), e0.e(1, row, lx + 1), e0.e(2, row, lx + 1),
                                  e0.e(0, row + 1, lx), e0.e(2, row + 1, lx), ecur[0][r], ecur[1][r],
                                  h0.h(0, row, lx), h0.h(1, row, lx), h0.h(2, row, lx), hxp[r], hyp[r], hz);
@@ -523,7 +527,7 @@ __device__ __forceinline__ bool run_item(const Cons<NH> &C, const Item &it, uint
                     const Slab L = CPML ? slab_in(sg, hk, sx, sy[r], sz, xo[r], yo[r], row * HBX + lx,
                                                   (2 * H_COMP) / 4 + (row - 1) * TX + lane)
                                         : Slab{-1, -1, -1, nullptr, -1, -1, -1, -1};
-                    h_core<CPML>(a, C.coef(cl[r]), C.prof, L, g, true, ecur[0][r], ecur[1][r],
+                    h_core<CPML, true, true>(a, C.coef(cl[r]), C.prof, L, g, ecur[0][r], ecur[1][r],
                                  ecur[2][r], ek.e(1, row, lx + 1), ek.e(2, row, lx + 1), ex_y1, ez_y1, enx[0][r],
                                  enx[1][r], hk.h(0, row, lx), hk.h(1, row, lx), hk.h(2, row, lx), hx, hy, hz);
                     a.Hout[0][g] = hx;
@@ -550,7 +554,7 @@ __device__ __forceinline__ bool run_item(const Cons<NH> &C, const Item &it, uint
                     const Slab L = CPML ? slab_in(sg, hk, slab_of(hi, a.nx, d), slab_of(hj, a.ny, d), sz, hxo[pass],
                                                   hyo[pass], hrow * HBX + hcol, -1)
                                         : Slab{-1, -1, -1, nullptr, -1, -1, -1, -1};
-                    h_core<CPML>(a, C.coef(hk.cls(hrow, hcol - XO + CXO)), C.prof, L, g, false,
+                    h_core<CPML, false, false>(a, C.coef(hk.cls(hrow, hcol - XO + CXO)), C.prof, L, g,
                                  ek.e(0, hrow, hcol), ek.e(1, hrow, hcol), ek.e(2, hrow, hcol),
                                  ek.e(1, hrow, hcol + 1), ek.e(2, hrow, hcol + 1), ek.e(0, hrow + 1, hcol),
                                  ek.e(2, hrow + 1, hcol), ek1.e(0, hrow, hcol), ek1.e(1, hrow, hcol),
@@ -833,12 +837,20 @@ int step_tile_y() { return TY; }
 int step_threads() { return NTHREADS; }
 int step_smem_bytes(int n_classes, int d, int region, int nh) { return smem_bytes(n_classes, d, region, nh); }
 
-PsiGeom step_psi_geom(int d)
+PsiGeom step_psi_geom(int d, int nx, int ny)
 {
     PsiGeom pg{};
     if (d == 0) return pg;
-    pg.w = std::min(HBX, (d + 4 + 3) / 4 * 4);
-    pg.hy = std::min(HBY, d + 1);
+    // a tile that meets both layers of an axis (grids narrower than about a
+    // tile plus two layers) stages its whole H box along that axis, so the
+    // staged boxes always hold every auxiliary of the cells an item updates
+    bool both_x = false, both_y = false;
+    for (int x0 = 0; x0 < nx; x0 += TX)
+        both_x |= std::max(x0 - 1, 0) < d && std::min(x0 + TX, nx) - 1 >= nx - d;
+    for (int y0 = 0; y0 < ny; y0 += TY)
+        both_y |= std::max(y0 - 1, 0) < d && std::min(y0 + TY, ny) - 1 >= ny - d;
+    pg.w = both_x ? HBX : std::min(HBX, (d + 4 + 3) / 4 * 4);
+    pg.hy = both_y ? HBY : std::min(HBY, d + 1);
     pg.xb = al128(pg.w * HBY * 4);
     pg.yb = al128(HBX * pg.hy * 4);
     return pg;
