@@ -229,6 +229,24 @@ int fdtd_batch_launch_info(const fdtd_batch *b, int launch, int *ctas, int *item
 const char *fdtd_batch_last_error(const fdtd_batch *b);
 void fdtd_batch_destroy(fdtd_batch *b);
 
+/* Checkpoint / resume of a finalized grid (a library addition; the paper's
+ * solver has no counterpart).  The state is everything the step reads that
+ * changes while stepping: the six fields, the twelve CPML auxiliaries (when
+ * the grid has a CPML), the probe record [n_probes x probe_capacity] and the
+ * step count.  Stepping a grid after fdtd_load_state continues bit for bit
+ * as the grid that saved the state did.
+ *   fdtd_save_state: host_buf NULL -> *bytes = the size needed, FDTD_OK;
+ *     otherwise *bytes is the buffer size on entry (FDTD_EINVAL, with the
+ *     size needed in *bytes, when too small) and the bytes written on return.
+ *     Synchronises the grid's stream.
+ *   fdtd_load_state: the grid must have the same sizes, CPML thickness,
+ *     probe count and probe capacity as the one that saved (FDTD_EINVAL
+ *     otherwise, or for a buffer that is not a saved state).  Materials,
+ *     wires and sources are the caller's to rebuild identically; they are
+ *     not part of the state.  Synchronises the grid's stream. */
+int fdtd_save_state(fdtd_grid *g, void *host_buf, size_t *bytes);
+int fdtd_load_state(fdtd_grid *g, const void *host_buf, size_t bytes);
+
 double fdtd_get_dt(const fdtd_grid *g);
 long fdtd_get_step(const fdtd_grid *g);
 int fdtd_num_classes(const fdtd_grid *g);

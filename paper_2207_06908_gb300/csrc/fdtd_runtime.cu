@@ -1046,6 +1046,92 @@ int fdtd_field_device(fdtd_grid *g, int component, void **dptr, int *row_pitch, 
 double fdtd_get_dt(const fdtd_grid *g) { return g ? g->dt : 0.0; }
 long fdtd_get_step(const fdtd_grid *g) { return g ? g->step : -1; }
 int fdtd_num_classes(const fdtd_grid *g) { return g ? g->n_classes : -1; }
+// ---- checkpoint / resume ----------------------------------------------------
+namespace {
+constexpr uint32_t kStateMagic = 0x53544446u;     // "FDTS"
+constexpr uint32_t kStateVersion = 1;
+struct StateHeader {
+    uint32_t magic, version;
+    int32_t nx, ny, nz, d, n_probes, capacity, n_psi, pad;
+    int64_t step;
+};
+
+size_t state_bytes(const fdtd_grid *g, int n_psi)
+{
+    const size_t cells = (size_t)g->nx * g->ny * g->nz;
+    return sizeof(StateHeader) + (6 + (size_t)n_psi) * cells * sizeof(float) +
+           g->probes.size() * (size_t)g->capacity * sizeof(float);
+}
+
+// one cell-owned array between host (dense) and device (row pitch)
+cudaError_t copy_array(fdtd_grid *g, float *dev, char *host, bool to_host)
+{
+    const size_t row = (size_t)g->nx * sizeof(float), dpitch = (size_t)g->pitch * sizeof(float);
+    const size_t rows = (size_t)g->ny * g->nz;
+    return to_host ? cudaMemcpy2D(host, row, dev, dpitch, row, rows, cudaMemcpyDeviceToHost)
+                   : cudaMemcpy2D(dev, dpitch, host, row, row, rows, cudaMemcpyHostToDevice);
+}
+}  // namespace
+
+int fdtd_save_state(fdtd_grid *g, void *host_buf, size_t *bytes)
+{
+    if (int rc = check_open(g, true)) return rc;
+    if (!bytes) return fail(g, FDTD_EINVAL, "null size pointer");
+    const int n_psi = g->d > 0 ? fdtd::PSI_COUNT : 0;
+    const size_t need = state_bytes(g, n_psi);
+    if (!host_buf) {
+        *bytes = need;
+        return FDTD_OK;
+    }
+    if (*bytes < need) {
+        *bytes = need;
+        return fail(g, FDTD_EINVAL, "state buffer too small");
+    }
+    if (int rc = fdtd_synchronize(g)) return rc;
+    StateHeader h{kStateMagic, kStateVersion, g->nx, g->ny, g->nz, g->d, (int32_t)g->probes.size(), g->capacity,
+                  n_psi, 0, (int64_t)g->step};
+    char *p = static_cast<char *>(host_buf);
+    std::memcpy(p, &h, sizeof h);
+    p += sizeof h;
+    const size_t arr = (size_t)g->nx * g->ny * g->nz * sizeof(float);
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < 6 && e == cudaSuccess; ++c, p += arr) e = copy_array(g, g->F[g->parity][c], p, true);
+    for (int q = 0; q < n_psi && e == cudaSuccess; ++q, p += arr) e = copy_array(g, g->psi[g->parity][q], p, true);
+    const size_t pbytes = g->probes.size() * (size_t)g->capacity * sizeof(float);
+    if (e == cudaSuccess && pbytes) e = cudaMemcpy(p, g->probe_out, pbytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(g, e, "state copy");
+    *bytes = need;
+    return FDTD_OK;
+}
+
+int fdtd_load_state(fdtd_grid *g, const void *host_buf, size_t bytes)
+{
+    if (int rc = check_open(g, true)) return rc;
+    if (!host_buf || bytes < sizeof(StateHeader)) return fail(g, FDTD_EINVAL, "no state");
+    StateHeader h;
+    std::memcpy(&h, host_buf, sizeof h);
+    const int n_psi = g->d > 0 ? fdtd::PSI_COUNT : 0;
+    if (h.magic != kStateMagic || h.version != kStateVersion) return fail(g, FDTD_EINVAL, "not a saved state");
+    if (h.nx != g->nx || h.ny != g->ny || h.nz != g->nz || h.d != g->d || h.n_probes != (int)g->probes.size() ||
+        h.capacity != g->capacity || h.n_psi != n_psi || h.step < 0)
+        return fail(g, FDTD_EINVAL, "state was saved from a differently shaped grid");
+    if (bytes < state_bytes(g, n_psi)) return fail(g, FDTD_EINVAL, "state truncated");
+    if (int rc = fdtd_synchronize(g)) return rc;
+    const char *p = static_cast<const char *>(host_buf) + sizeof h;
+    const size_t arr = (size_t)g->nx * g->ny * g->nz * sizeof(float);
+    char *q = const_cast<char *>(p);
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < 6 && e == cudaSuccess; ++c, q += arr) e = copy_array(g, g->F[g->parity][c], q, false);
+    for (int a = 0; a < n_psi && e == cudaSuccess; ++a, q += arr) e = copy_array(g, g->psi[g->parity][a], q, false);
+    const size_t pbytes = g->probes.size() * (size_t)g->capacity * sizeof(float);
+    if (e == cudaSuccess && pbytes) e = cudaMemcpy(g->probe_out, q, pbytes, cudaMemcpyHostToDevice);
+    const long long step = h.step;
+    if (e == cudaSuccess) e = cudaMemcpy(g->step_d, &step, sizeof step, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(g, e, "state copy");
+    g->step = (long)h.step;
+    return FDTD_OK;
+}
+
 const char *fdtd_last_error(const fdtd_grid *g) { return g ? g->err.c_str() : "null grid"; }
 
 void fdtd_destroy(fdtd_grid *g)

@@ -158,6 +158,18 @@ class Grid:
         check(self._lib, self._h, self._lib.fdtd_set_field(self._h, int(comp), v.ctypes.data_as(ctypes.c_void_p)),
               "set_field")
 
+    def save_state(self):
+        """the grid's checkpoint (fields, CPML auxiliaries, probe record,
+        step count) as bytes"""
+        n = ctypes.c_size_t()
+        check(self._lib, self._h, self._lib.fdtd_save_state(self._h, None, ctypes.byref(n)), "save_state")
+        buf = ctypes.create_string_buffer(n.value)
+        check(self._lib, self._h, self._lib.fdtd_save_state(self._h, buf, ctypes.byref(n)), "save_state")
+        return buf.raw[:n.value]
+
+    def load_state(self, state):
+        check(self._lib, self._h, self._lib.fdtd_load_state(self._h, state, len(state)), "load_state")
+
     def field_device(self, comp):
         p = ctypes.c_void_p()
         rp = ctypes.c_int()

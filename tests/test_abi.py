@@ -69,6 +69,10 @@ def test_host_argument_checks():
         assert lib.fdtd_add_probe(h, 0, 3, 3, 3, 2, 6, None) == -1                 # path leaves grid
         assert lib.fdtd_add_probe(h, 1, 0, 3, 3, 2, 1, None) == -1                 # loop needs i >= 1
         assert lib.fdtd_step(h, 1) == -8                                           # not finalized
+        nbytes = ctypes.c_size_t()
+        assert lib.fdtd_save_state(h, None, ctypes.byref(nbytes)) == -8            # not finalized
+        assert lib.fdtd_load_state(h, b"x" * 64, 64) == -8
+        assert lib.fdtd_save_state(None, None, ctypes.byref(nbytes)) == -1
         nb = ctypes.c_size_t()
         assert lib.fdtd_arena_bytes(h, 100, ctypes.byref(nb)) == 0 and nb.value > 12 * 8 * 8 * 8 * 4
     finally:
