@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Gcell-updates/s"
 UNIT = "Gcell/s"
-KERNEL_SRC = os.path.join(ROOT, "paper_2207_06908_gb300", "csrc", "fdtd_step.cu")
+KERNEL_SRC = [os.path.join(ROOT, "paper_2207_06908_gb300", "csrc", f) for f in ("fdtd_step.cu", "fdtd_runtime.cu")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
 FALLBACK_HBM_GBS = 6800.0
 
@@ -86,8 +86,13 @@ def peaks():
 
 
 def kernel_hash():
-    with open(KERNEL_SRC, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """hash of the step kernel and of the runtime that sets its launch
+    shapes: recorded DRAM traffic is valid only for the same sources"""
+    h = hashlib.sha256()
+    for path in KERNEL_SRC:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def recorded_traffic(cells):
@@ -100,7 +105,9 @@ def recorded_traffic(cells):
         return None
     if t.get("kernel_sha") != kernel_hash():
         return None
-    return t["dram_bytes_per_launch"] * cells / t["cells"]
+    if t.get("cells") != cells:
+        return None
+    return t["dram_bytes_per_step"]
 
 
 class Clocks:

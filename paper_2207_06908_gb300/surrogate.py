@@ -368,6 +368,21 @@ def dataset(lo, hi, cache=None, log=None):
     return X, Y
 
 
+def nearest_neighbour_error(X_train, Y_train, X, Y):
+    """The method without the network, as a baseline: answer each input with
+    the FDTD waveform of the nearest training input (Euclidean distance of
+    the encoded features).  Returns the relative L2 error per row (host
+    evaluation of a baseline; not part of the surrogate)."""
+    Ft, F = features(X_train).astype(np.float64), features(X).astype(np.float64)
+    err = np.empty(len(F))
+    for lo in range(0, len(F), 256):
+        d2 = ((F[lo:lo + 256, None, :] - Ft[None, :, :]) ** 2).sum(-1)
+        nn = np.argmin(d2, axis=1)
+        y = np.asarray(Y[lo:lo + 256], np.float64)
+        err[lo:lo + 256] = np.linalg.norm(np.asarray(Y_train, np.float64)[nn] - y, axis=1) / np.linalg.norm(y, axis=1)
+    return err
+
+
 def main(argv=None):
     import argparse
     import json
@@ -393,7 +408,11 @@ def main(argv=None):
     wave, err = sur.predict(Xh)
     rel = np.linalg.norm(wave - Yh, axis=1) / np.linalg.norm(Yh, axis=1)
     acc = (err <= sur.threshold) & in_range(Xh)
-    rep = dict(data_s=t1 - t0, train_s=t2 - t1, threshold=sur.threshold, heldout=dict(
+    nn = nearest_neighbour_error(Xt[:len(Xt) - N_CAL], Yt[:len(Xt) - N_CAL], Xh, Yh)
+    rep = dict(data_s=t1 - t0, train_s=t2 - t1, threshold=sur.threshold,
+               nearest_neighbour=dict(median=float(np.median(nn)), mean=float(nn.mean()),
+                                      p99=float(np.percentile(nn, 99)), frac_le_2pct=float(np.mean(nn <= 0.02))),
+               heldout=dict(
         n=len(Xh), median=float(np.median(rel)), mean=float(rel.mean()), p99=float(np.percentile(rel, 99)),
         max=float(rel.max()), frac_le_2pct=float(np.mean(rel <= 0.02)), accepted=float(acc.mean()),
         max_accepted=float(rel[acc].max()) if acc.any() else None), **sur.meta)
