@@ -258,8 +258,10 @@ def run_batch_bench(a):
 
 
 def l2_flusher(torch):
-    """a buffer twice the 129 MB L2; writing it evicts every cached line"""
-    buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    """a 1 GB buffer (eight times the 129 MB L2); writing it evicts every
+    cached line and keeps the GPU busy long enough (about 0.15 ms) for the
+    host to queue the timed work behind it"""
+    buf = torch.empty(256 * 1024 * 1024, dtype=torch.float32, device="cuda")
     return lambda: buf.fill_(1.0)
 
 
@@ -282,18 +284,20 @@ def run_surrogate_bench(a):
     stream = torch.cuda.current_stream()
     # held-out-distribution inputs (seeds after the training seeds)
     X = np.stack([W.surrogate_inputs(s) for s in range(S.HELDOUT_SEEDS[0], S.HELDOUT_SEEDS[0] + B)])
-    f_dev = torch.tensor(S.features(X), device="cuda")
+    x_dev, replay, _ = sur.predict_graph(B)
+    x_dev.copy_(torch.from_numpy(S.features(X)))
     flush = l2_flusher(torch)
     for _ in range(Wm):
-        sur.predict_device(f_dev)
-    # surrogate: device-resident inputs, L2 flushed between timed iterations
+        replay()
+    # surrogate: device-resident inputs, both networks replayed from one
+    # captured graph, L2 flushed between timed iterations
     clk = Clocks(0)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     torch.cuda.synchronize()
     for e0, e1 in ev:
         flush()
         e0.record(stream)
-        sur.predict_device(f_dev)
+        replay()
         e1.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
@@ -334,14 +338,17 @@ def run_surrogate_bench(a):
     acc = acc_all[:n_eval]
     final = np.where(acc, rel, 0.0)
     value = 1.0 / ((1.0 - f_fb) / s_sur + f_fb / s_fdtd)
-    # end to end through the public call: host parameters in, host waveforms and bounds out
-    e2e_t = []
-    for i in range(max(3, K // 10) + 2):
+    # end to end through the public call: host parameters in, host
+    # waveforms out, the rejected inputs re-run by the FDTD engine inside
+    # the call (the first call is untimed: graph capture, tile tuning)
+    sur.predict_with_fallback(X)
+    e2e_t, n_fb = [], 0
+    for i in range(3):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        wv, eb = sur.predict(X)
+        wv, acc_e = sur.predict_with_fallback(X)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_t = e2e_t[2:]
+        n_fb += int((~acc_e).sum())
     e2e_s = B * len(e2e_t) / sum(e2e_t)
     # FP64 network oracle on the host cores, bounded sample
     layers = [(w.astype(np.float64), b.astype(np.float64)) for w, b in
@@ -360,7 +367,7 @@ def run_surrogate_bench(a):
             "config": {"workload": f"grounding-rod surrogate, MLP 6-256-256-256-512 GELU + error head 6-64-64-1, "
                                    f"inference batch {B}; FDTD comparison on {n_eval} of the same inputs "
                                    f"(64^3 domains, dx 0.25 m, 8-cell CPML, {W.GROUND_STEPS} steps)",
-                       "batch": B, "l2": "flushed between timed iterations (256 MB write)"},
+                       "batch": B, "l2": "flushed between timed iterations (1 GB write)"},
             "surrogate_sims_s": s_sur, "fdtd_sims_s": s_fdtd, "fallback_fraction": f_fb,
             "speedup_vs_fdtd": value / s_fdtd,
             "waveform_rel_l2": {"n": n_eval, "median": float(np.median(rel)), "mean": float(rel.mean()),
@@ -371,11 +378,14 @@ def run_surrogate_bench(a):
                          "kernel": f"gemm_kernel, {B}x256 @ 256x512 output layer, {lay_ms * 1e3:.1f} us"},
             "e2e": {"value": e2e_s, "unit": "sims/s", "h2d_bytes_per_step": B * 6 * 4,
                     "d2h_bytes_per_step": B * 512 * 4 + B * 4,
-                    "includes": "host feature encoding, upload, both networks, waveform and bound readback"},
+                    "includes": f"predict_with_fallback on the {B} inputs: host feature encoding, upload, both "
+                                f"networks, readback, and FDTD runs (build, upload, {W.GROUND_STEPS} steps, "
+                                f"probe readback) of the {n_fb // 3} rejected inputs per call"},
             "cpu_baseline": {"value": cpu_rate, "unit": "sims/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"{reps} FP64 forward passes of the waveform network over the {B} inputs"},
             "clocks": clocks, "gpu_launches": 8 * K}
     print(json.dumps(line), flush=True)
+    del replay
 
 
 def main():

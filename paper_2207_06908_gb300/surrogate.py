@@ -95,19 +95,23 @@ class Network:
         self.v = [torch.zeros_like(p) for p in self.params]
         self.g = [torch.zeros_like(p) for p in self.params]
         self.t = 0
-        self._rows = 0
+        self._bufs = {}
 
     def _buffers(self, rows):
-        if rows == self._rows:
-            return
-        torch = self.torch
-        f32 = dict(dtype=torch.float32, device="cuda")
-        self.z = [torch.empty((rows, n), **f32) for n in self.sizes[1:]]
-        self.hb = [torch.empty((rows, n), dtype=torch.bfloat16, device="cuda") for n in self.sizes[1:-1]]
-        self.out = torch.empty((rows, self.sizes[-1]), **f32)
-        self.dz = [torch.empty((rows, n), **f32) for n in self.sizes[1:]]
-        self.dh = [torch.empty((rows, n), **f32) for n in self.sizes[1:-1]]
-        self._rows = rows
+        """activation and gradient buffers, one set per row count and kept
+        for the network's lifetime (a captured graph of a forward pass keeps
+        pointing at the set of its batch size)"""
+        if rows not in self._bufs:
+            torch = self.torch
+            f32 = dict(dtype=torch.float32, device="cuda")
+            self._bufs[rows] = dict(
+                z=[torch.empty((rows, n), **f32) for n in self.sizes[1:]],
+                hb=[torch.empty((rows, n), dtype=torch.bfloat16, device="cuda") for n in self.sizes[1:-1]],
+                out=torch.empty((rows, self.sizes[-1]), **f32),
+                dz=[torch.empty((rows, n), **f32) for n in self.sizes[1:]],
+                dh=[torch.empty((rows, n), **f32) for n in self.sizes[1:-1]])
+        b = self._bufs[rows]
+        self.z, self.hb, self.out, self.dz, self.dh = b["z"], b["hb"], b["out"], b["dz"], b["dh"]
 
     def forward(self, x):
         """x: [rows, k0] FP32 (rounded to BF16 on load).  Returns the FP32
@@ -230,7 +234,8 @@ class Surrogate:
     def __init__(self, main, head, threshold, meta=None):
         self.main, self.head, self.threshold = main, head, float(threshold)
         self.meta = dict(meta or {})
-        self._unit = None
+        self._units = {}                # output scale per batch size (kept: graphs point at them)
+        self._graphs = {}
 
     # -- inference ---------------------------------------------------------
     def predict_device(self, f_dev):
@@ -239,19 +244,40 @@ class Surrogate:
         import torch
         from . import mlp
         B = f_dev.shape[0]
-        if self._unit is None or self._unit.numel() < B:
-            self._unit = torch.full((B,), Y_UNIT, dtype=torch.float32, device="cuda")
+        if B not in self._units:
+            self._units[B] = torch.full((B,), Y_UNIT, dtype=torch.float32, device="cuda")
         wave = self.main.forward(f_dev)
-        mlp.scale_rows(wave, self._unit[:B])
+        mlp.scale_rows(wave, self._units[B])
         log_err = self.head.forward(f_dev)
         return wave, log_err.reshape(-1)
+
+    def predict_graph(self, batch):
+        """A CUDA graph of predict_device for `batch` rows, captured once per
+        batch size: returns (input buffer [batch, 6], replay, outputs).  Copy
+        encoded features into the input buffer, call replay(), read the
+        outputs (device tensors, overwritten by the next replay)."""
+        import torch
+        if batch not in self._graphs:
+            x = torch.zeros((batch, N_IN), dtype=torch.float32, device="cuda")
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                self.predict_device(x)          # allocates the layer buffers outside the capture
+            torch.cuda.current_stream().wait_stream(side)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                wave, log_err = self.predict_device(x)
+            self._graphs[batch] = (x, g, (wave, log_err))
+        x, g, outs = self._graphs[batch]
+        return x, g.replay, outs
 
     def predict(self, params):
         """waveforms [B, 512] (ohm) and the error head's predicted relative
         L2 error [B] for parameter rows [B, 6] (host arrays)."""
-        import torch
-        f = torch.tensor(features(params), device="cuda")
-        wave, log_err = self.predict_device(f)
+        f = features(params)
+        x, replay, (wave, log_err) = self.predict_graph(len(f))
+        x.copy_(__import__("torch").from_numpy(f), non_blocking=False)
+        replay()
         return wave.cpu().numpy(), np.exp(log_err.cpu().numpy())
 
     def predict_with_fallback(self, params, max_err=None, per_batch=512):
