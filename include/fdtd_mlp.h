@@ -16,6 +16,10 @@
  *     nothing synchronises.  Nothing is allocated.
  *   - Return value 0, FDTD_EINVAL (-1) for bad sizes / null required
  *     pointers, FDTD_ECUDA (-4) for a launch error.
+ *   - Forward layers with k <= 256 run on the tcgen05 tensor cores (TMEM
+ *     accumulator); their one wait (for the MMA chain) is bounded: when it
+ *     runs out the layer skips its outputs and records the failure, which
+ *     fdtd_mlp_check() reports.
  */
 #ifndef FDTD_GB300_MLP_H
 #define FDTD_GB300_MLP_H
@@ -68,6 +72,11 @@ int fdtd_mlp_gather_rows(const float *src, const int *idx, int rows, int cols, f
 
 /* y[r, :] *= scale[r] in place. */
 int fdtd_mlp_scale_rows(float *y, const float *scale, int rows, int cols, void *cuda_stream);
+
+/* Synchronise cuda_stream and report whether a bounded wait inside a
+ * network kernel ran out since the last call: FDTD_OK, FDTD_ETIMEOUT (-6,
+ * the flag is then cleared) or FDTD_ECUDA. */
+int fdtd_mlp_check(void *cuda_stream);
 
 /* FP32 -> BF16 conversion (round to nearest even) of count elements. */
 int fdtd_mlp_to_bf16(const float *src, void *dst, int count, void *cuda_stream);

@@ -92,6 +92,7 @@ def load():
             "fdtd_mlp_gather_rows": (I, [P, P, I, I, P, P]),
             "fdtd_mlp_scale_rows": (I, [P, P, I, I, P]),
             "fdtd_mlp_to_bf16": (I, [P, P, I, P]),
+            "fdtd_mlp_check": (I, [P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)

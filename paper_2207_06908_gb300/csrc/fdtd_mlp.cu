@@ -1,16 +1,20 @@
 // fdtd_mlp.cu -- surrogate-network kernels (BF16 operands, FP32 accumulate).
 //
-// One tiled GEMM serves the forward layer (x wt^T), the input gradient
-// (dz wt) and the weight gradient (dz^T x): operands are addressed through
-// element strides, staged into shared memory as BF16 with k contiguous, and
-// multiplied with mma.sync m16n8k16 (BF16 x BF16 -> FP32).  The forward
-// epilogue adds the bias and applies GELU (erf form, CUDA's erff).  Small
-// element-wise kernels form dz = dy * act'(z), the bias gradient, the MSE
-// loss and the Adam update.
+// Forward layers (x wt^T + bias, GELU) run on the fifth-generation tensor
+// cores: one CTA per 128 x 128 output tile stages the whole K extent of
+// both operands in shared memory (no-swizzle K-major core-matrix layout),
+// one thread issues the tcgen05.mma chain into a TMEM accumulator, and the
+// four warps read it back with tcgen05.ld for the bias / GELU epilogue.
+// The gradients (dz wt and dz^T x, whose operands are not K-major in
+// memory) use a tiled mma.sync m16n8k16 GEMM that addresses its operands
+// through element strides.  Small element-wise kernels form
+// dz = dy * act'(z), the bias gradient, the losses and the Adam update.
 #include <cuda_bf16.h>
 #include <math.h>
 
 #include <algorithm>
+#include <cstdint>
+#include <mutex>
 
 #include "fdtd.h"
 #include "fdtd_mlp.h"
@@ -226,6 +230,200 @@ __global__ void to_bf16_kernel(const float *src, __nv_bfloat16 *dst, int count)
         dst[q] = __float2bfloat16_rn(src[q]);
 }
 
+// ---- tcgen05 forward layer ---------------------------------------------------
+constexpr int TC_M = 128, TC_N = 128, TC_KMAX = 256, TC_THREADS = 128;
+constexpr int TC_SMEM = 2 * TC_M * TC_KMAX * 2 + 1024 + 64;   // A and B tiles, alignment, barrier, TMEM slot
+constexpr unsigned long long TC_WAIT_NS = 1000000000ull;      // 1 s per wait
+
+__device__ int g_mlp_err;     // a bounded wait ran out (read and cleared by fdtd_mlp_check)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
+{
+    const unsigned long long t0 = gtimer();
+    while (!mbar_try(bar, parity))
+        if (gtimer() - t0 > TC_WAIT_NS) return false;
+    return true;
+}
+
+// shared-memory matrix descriptor: start, leading (K-direction) and stride
+// (8-row-group) byte offsets, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: D FP32, A and B both BF16 and
+// K-major, M = TC_M, N = TC_N
+constexpr uint32_t TC_IDESC =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+// eight consecutive elements (k .. k+7) of row r of a rows x K matrix as
+// BF16, zero outside it; vec: 16-byte loads are valid (BF16, K % 8 == 0,
+// 16-byte aligned base)
+template <typename T>
+__device__ __forceinline__ uint4 load8(const T *M, int rows, int K, int r, int k, bool vec)
+{
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (r >= rows || k >= K) return v;
+    if (sizeof(T) == 2 && vec) return __ldg(reinterpret_cast<const uint4 *>(M + (size_t)r * K + k));
+    float f[8];
+    for (int j = 0; j < 8; ++j) {
+        const int kk = k + j;
+        f[j] = kk < K ? (sizeof(T) == 2 ? __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(M + (size_t)r * K + kk))
+                                        : (float)*reinterpret_cast<const float *>(M + (size_t)r * K + kk))
+                      : 0.f;
+    }
+    v.x = pack2(f[0], f[1]);
+    v.y = pack2(f[2], f[3]);
+    v.z = pack2(f[4], f[5]);
+    v.w = pack2(f[6], f[7]);
+    return v;
+}
+
+template <typename TA>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_forward_kernel(const TA *__restrict__ X, int rows, int K, int Kp, bool xvec, const __nv_bfloat16 *__restrict__ Wt,
+                      bool wvec, const float *__restrict__ bias, int N, int act, __nv_bfloat16 *yb, float *yf,
+                      float *zf)
+{
+    extern __shared__ __align__(1024) char smraw[];
+    char *sm = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
+    char *As = sm;
+    char *Bs = sm + TC_M * Kp * 2;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(Bs + TC_N * Kp * 2);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * TC_N;
+    const int kgs = Kp / 8;
+    const uint32_t sbo = (uint32_t)Kp * 16;   // bytes between 8-row groups; k groups are 128 B apart
+    // both operands into the core-matrix layout: chunk (row r, k group g)
+    // = 8 elements of one row, 16 bytes at (r / 8) sbo + g 128 + (r % 8) 16
+    for (int q = tid; q < TC_M * kgs; q += TC_THREADS) {
+        const int r = q / kgs, g = q - r * kgs;
+        *reinterpret_cast<uint4 *>(As + (r >> 3) * sbo + g * 128 + (r & 7) * 16) = load8(X, rows, K, m0 + r, g * 8, xvec);
+        *reinterpret_cast<uint4 *>(Bs + (r >> 3) * sbo + g * 128 + (r & 7) * 16) = load8(Wt, N, K, n0 + r, g * 8, wvec);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(TC_N));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 32) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    if (tid == 0) {
+        const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+        for (int k0 = 0; k0 < Kp; k0 += 16) {
+            const uint64_t ad = smem_desc(a0 + k0 * 16, 128, sbo), bd = smem_desc(b0 + k0 * 16, 128, sbo);
+            const uint32_t acc = k0 > 0 ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc)
+                : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                     : "memory");
+    }
+    bool ok = mbar_wait_bounded(smem_u32(bar), 0);
+    ok = __syncthreads_and(ok);
+    if (!ok) {
+        if (tid == 0) atomicExch(&g_mlp_err, 1);
+        mbar_wait_bounded(smem_u32(bar), 0);   // the chain still in flight, bounded again
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const int m = m0 + warp * 32 + lane;
+        for (int c = 0; c < TC_N && n0 + c < N; c += 16) {
+            uint32_t v[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (m < rows) {
+                for (int j = 0; j < 16; ++j) {
+                    const int n = n0 + c + j;
+                    if (n >= N) break;
+                    const float z = __uint_as_float(v[j]) + (bias ? __ldg(bias + n) : 0.f);
+                    const float y = act == FDTD_ACT_GELU ? gelu(z) : z;
+                    const size_t o = (size_t)m * N + n;
+                    if (zf) zf[o] = z;
+                    if (yf) yf[o] = y;
+                    if (yb) yb[o] = __float2bfloat16_rn(y);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N) : "memory");
+    }
+}
+
+template <typename TA>
+cudaError_t tc_forward(const TA *x, int rows, int K, const __nv_bfloat16 *wt, const float *bias, int N, int act,
+                       __nv_bfloat16 *yb, float *yf, float *zf, cudaStream_t s)
+{
+    static std::mutex mu;
+    static bool ready[2][64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 64) return cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        bool &r = ready[sizeof(TA) == 2][dev];
+        if (!r) {
+            e = cudaFuncSetAttribute(tc_forward_kernel<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+            if (e != cudaSuccess) return e;
+            r = true;
+        }
+    }
+    const int Kp = (K + 15) / 16 * 16;
+    const bool xvec = sizeof(TA) == 2 && K % 8 == 0 && (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+    const bool wvec = K % 8 == 0 && (reinterpret_cast<uintptr_t>(wt) & 15) == 0;
+    dim3 grid((rows + TC_M - 1) / TC_M, (N + TC_N - 1) / TC_N);
+    tc_forward_kernel<TA><<<grid, TC_THREADS, TC_SMEM, s>>>(x, rows, K, Kp, xvec, wt, wvec, bias, N, act, yb, yf, zf);
+    return cudaGetLastError();
+}
+
 template <typename TA, typename TB>
 cudaError_t gemm(const TA *A, long long sam, long long sak, const TB *B, long long sbk, long long sbn, int M, int N,
                  int K, const Epi &ep, cudaStream_t s)
@@ -250,10 +448,32 @@ int fdtd_mlp_forward(const void *x, int x_is_bf16, int rows, int k, const void *
     Epi ep{0, bias, act, static_cast<__nv_bfloat16 *>(y_bf16), y_f32, z_f32, n};
     const auto *w = static_cast<const __nv_bfloat16 *>(wt);
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (k <= TC_KMAX) {       // tensor-core path (every layer of the surrogate networks)
+        if (x_is_bf16)
+            return rc(tc_forward(static_cast<const __nv_bfloat16 *>(x), rows, k, w, bias, n, act,
+                                 static_cast<__nv_bfloat16 *>(y_bf16), y_f32, z_f32, s));
+        return rc(tc_forward(static_cast<const float *>(x), rows, k, w, bias, n, act,
+                             static_cast<__nv_bfloat16 *>(y_bf16), y_f32, z_f32, s));
+    }
     // B(k, n) = wt[n * k + k']
     if (x_is_bf16)
         return rc(gemm(static_cast<const __nv_bfloat16 *>(x), k, 1, w, 1, k, rows, n, k, ep, s));
     return rc(gemm(static_cast<const float *>(x), k, 1, w, 1, k, rows, n, k, ep, s));
+}
+
+int fdtd_mlp_check(void *cuda_stream)
+{
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return FDTD_ECUDA;
+    int flag = 0;
+    e = cudaMemcpyFromSymbol(&flag, g_mlp_err, sizeof flag);
+    if (e != cudaSuccess) return FDTD_ECUDA;
+    if (flag) {
+        const int zero = 0;
+        e = cudaMemcpyToSymbol(g_mlp_err, &zero, sizeof zero);
+        return e == cudaSuccess ? FDTD_ETIMEOUT : FDTD_ECUDA;
+    }
+    return FDTD_OK;
 }
 
 int fdtd_mlp_backward(const void *x, int x_is_bf16, const float *z, const float *dy, int rows, int k, int n,

@@ -76,3 +76,9 @@ def scale_rows(y, scale):
 def to_bf16(src, dst):
     lib = _lib.load()
     _check(lib.fdtd_mlp_to_bf16(_p(src), _p(dst), src.numel(), _stream()), "mlp_to_bf16")
+
+
+def check():
+    """synchronise the current stream; raise if a bounded wait inside a
+    network kernel ran out since the last check"""
+    _check(_lib.load().fdtd_mlp_check(_stream()), "mlp kernels")

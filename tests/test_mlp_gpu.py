@@ -31,7 +31,7 @@ def dev(torch, a, dtype):
 
 
 @pytest.mark.parametrize("rows,k,n,act", [(300, 70, 130, 1), (64, 256, 256, 1), (4096, 6, 256, 1),
-                                          (257, 256, 512, 0), (1, 13, 7, 1)])
+                                          (257, 256, 512, 0), (1, 13, 7, 1), (129, 64, 1, 0), (200, 300, 40, 1)])
 def test_forward_layer(env, rows, k, n, act):
     torch, mlp = env
     rng = np.random.default_rng(rows + k + n)
@@ -43,7 +43,7 @@ def test_forward_layer(env, rows, k, n, act):
     yf = torch.empty((rows, n), dtype=torch.float32, device="cuda")
     zf = torch.empty((rows, n), dtype=torch.float32, device="cuda")
     mlp.forward(xd, Wd, bd, act, yb, yf, zf)
-    torch.cuda.synchronize()
+    mlp.check()
     _, zs, y = M.forward(x, [(W, b)], ["gelu" if act else "none"])
     assert rel(zf.cpu().numpy(), zs[0]) <= 1e-4
     assert rel(yf.cpu().numpy(), y) <= 1e-4
@@ -174,3 +174,19 @@ def test_row_kernels(env):
     np.testing.assert_allclose(err.cpu().numpy(), ref, rtol=1e-5)
     np.testing.assert_array_equal(g.cpu().numpy(), y[idx].astype(np.float32))
     assert rel(ys.cpu().numpy(), y * s.astype(np.float32)[:, None]) <= 1e-7
+
+
+def test_forward_layer_fp32_input(env):
+    """FP32 inputs are rounded to BF16 on load (the first surrogate layer)"""
+    torch, mlp = env
+    rng = np.random.default_rng(77)
+    rows, k, n = 515, 6, 256
+    x = rng.uniform(-1, 1, (rows, k)).astype(np.float32).astype(np.float64)
+    W = M.bf16(rng.standard_normal((n, k)) / np.sqrt(k))
+    b = rng.standard_normal(n).astype(np.float32).astype(np.float64)
+    yf = torch.empty((rows, n), dtype=torch.float32, device="cuda")
+    mlp.forward(dev(torch, x, torch.float32), dev(torch, W, torch.bfloat16), dev(torch, b, torch.float32), 1,
+                None, yf, None)
+    mlp.check()
+    _, _, y = M.forward(M.bf16(x), [(W, b)], ["gelu"])
+    assert rel(yf.cpu().numpy(), y) <= 1e-4
