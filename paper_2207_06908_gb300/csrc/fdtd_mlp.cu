@@ -216,12 +216,14 @@ __global__ void gather_rows_kernel(const float *src, const int *idx, int rows, i
     }
 }
 
+// block row r = blockIdx.y (grid-strided), columns across the x dimension
 __global__ void scale_rows_kernel(float *y, const float *s, int rows, int cols)
 {
-    const long long total = (long long)rows * cols;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
-         q += (long long)gridDim.x * blockDim.x)
-        y[q] *= s[q / cols];
+    for (int r = blockIdx.y; r < rows; r += gridDim.y) {
+        const float f = __ldg(s + r);
+        float *yr = y + (size_t)r * cols;
+        for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x) yr[c] *= f;
+    }
 }
 
 __global__ void to_bf16_kernel(const float *src, __nv_bfloat16 *dst, int count)
@@ -231,8 +233,12 @@ __global__ void to_bf16_kernel(const float *src, __nv_bfloat16 *dst, int count)
 }
 
 // ---- tcgen05 forward layer ---------------------------------------------------
-constexpr int TC_M = 128, TC_N = 128, TC_KMAX = 256, TC_THREADS = 128;
-constexpr int TC_SMEM = 2 * TC_M * TC_KMAX * 2 + 1024 + 64;   // A and B tiles, alignment, barrier, TMEM slot
+constexpr int TC_M = 128, TC_N = 64, TC_KMAX = 256, TC_THREADS = 256;   // 8 warps: 4 lane groups x 2 column halves
+// dynamic shared memory: alignment slack, a 1 KB header (barrier, TMEM
+// slot), then the A and B tiles (up to K = TC_KMAX); the epilogue's
+// transpose buffers (8 x 32 x TC_TS floats) reuse the start of the tile
+// area.  About 98 KB: two CTAs per SM.
+constexpr int TC_SMEM = 1024 + 1024 + (TC_M + TC_N) * TC_KMAX * 2;
 constexpr unsigned long long TC_WAIT_NS = 1000000000ull;      // 1 s per wait
 
 __device__ int g_mlp_err;     // a bounded wait ran out (read and cleared by fdtd_mlp_check)
@@ -307,29 +313,121 @@ __device__ __forceinline__ uint4 load8(const T *M, int rows, int K, int r, int k
     return v;
 }
 
+constexpr int TC_TS = 36;    // floats per row of a warp's 32 x 32 transpose buffer (16-byte rows, no conflicts)
+static_assert(TC_THREADS / 32 * 32 * TC_TS * 4 <= (TC_M + TC_N) * TC_KMAX * 2, "transpose buffers fit the tile area");
+
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&v)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// lane l holds columns n .. n+31 of row mrow + l; write them to out (row
+// pitch N) as 128-byte row segments: pass i stores rows 4i + l/8, lane
+// l % 8 covering four columns
+__device__ __forceinline__ void store_f32(float *T, const float (&x)[32], float *out, int mrow, int rows, int n,
+                                          int N, int lane)
+{
+    for (int j = 0; j < 32; j += 4)
+        *reinterpret_cast<float4 *>(T + lane * TC_TS + j) = make_float4(x[j], x[j + 1], x[j + 2], x[j + 3]);
+    __syncwarp();
+    const int cc = (lane & 7) * 4;
+    const bool vec = (N & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+    for (int i = 0; i < 8; ++i) {
+        const int rr = i * 4 + (lane >> 3), m = mrow + rr;
+        if (m >= rows) continue;
+        const float4 q = *reinterpret_cast<const float4 *>(T + rr * TC_TS + cc);
+        float *o = out + (size_t)m * N + n + cc;
+        if (vec && n + cc + 3 < N) {
+            *reinterpret_cast<float4 *>(o) = q;
+        } else {
+            const float e[4] = {q.x, q.y, q.z, q.w};
+            for (int u = 0; u < 4; ++u)
+                if (n + cc + u < N) o[u] = e[u];
+        }
+    }
+    __syncwarp();
+}
+
+// as store_f32 for BF16 outputs: 64-byte row segments, pass i stores rows
+// 8i + l/4, lane l % 4 covering eight columns
+__device__ __forceinline__ void store_bf16(float *T, const float (&x)[32], __nv_bfloat16 *out, int mrow, int rows,
+                                           int n, int N, int lane)
+{
+    uint32_t *Tu = reinterpret_cast<uint32_t *>(T);
+    for (int j = 0; j < 32; j += 8)
+        *reinterpret_cast<uint4 *>(Tu + lane * TC_TS + j / 2) =
+            make_uint4(pack2(x[j], x[j + 1]), pack2(x[j + 2], x[j + 3]), pack2(x[j + 4], x[j + 5]),
+                       pack2(x[j + 6], x[j + 7]));
+    __syncwarp();
+    const int cc = (lane & 3) * 8;
+    const bool vec = (N & 7) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+    for (int i = 0; i < 4; ++i) {
+        const int rr = i * 8 + (lane >> 2), m = mrow + rr;
+        if (m >= rows) continue;
+        const uint4 q = *reinterpret_cast<const uint4 *>(Tu + rr * TC_TS + cc / 2);
+        __nv_bfloat16 *o = out + (size_t)m * N + n + cc;
+        if (vec && n + cc + 7 < N) {
+            *reinterpret_cast<uint4 *>(o) = q;
+        } else {
+            const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&q);
+            for (int u = 0; u < 8; ++u)
+                if (n + cc + u < N) o[u] = e[u];
+        }
+    }
+    __syncwarp();
+}
+
+template <typename T>
+__device__ __forceinline__ void stage_operand(char *dst, const T *M, int rows, int K, int r0, int tile_rows, int kgs,
+                                              uint32_t sbo, bool vec, int tid)
+{
+    for (int q = tid; q < tile_rows * kgs; q += TC_THREADS) {
+        const int r = q / kgs, g = q - r * kgs;
+        char *d = dst + (r >> 3) * sbo + g * 128 + (r & 7) * 16;
+        if (sizeof(T) == 2 && vec) {
+            const bool in = r0 + r < rows && g * 8 < K;   // K % 8 == 0: a chunk is wholly in or out
+            const T *src = in ? M + (size_t)(r0 + r) * K + g * 8 : M;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(d)), "l"(src),
+                         "r"(in ? 16 : 0)
+                         : "memory");
+        } else {
+            *reinterpret_cast<uint4 *>(d) = load8(M, rows, K, r0 + r, g * 8, false);
+        }
+    }
+}
+
 template <typename TA>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TC_THREADS, 2)
     tc_forward_kernel(const TA *__restrict__ X, int rows, int K, int Kp, bool xvec, const __nv_bfloat16 *__restrict__ Wt,
                       bool wvec, const float *__restrict__ bias, int N, int act, __nv_bfloat16 *yb, float *yf,
                       float *zf)
 {
     extern __shared__ __align__(1024) char smraw[];
     char *sm = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
-    char *As = sm;
-    char *Bs = sm + TC_M * Kp * 2;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(Bs + TC_N * Kp * 2);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + 8);
+    char *As = sm + 1024;
+    char *Bs = As + TC_M * Kp * 2;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * TC_N;
     const int kgs = Kp / 8;
     const uint32_t sbo = (uint32_t)Kp * 16;   // bytes between 8-row groups; k groups are 128 B apart
     // both operands into the core-matrix layout: chunk (row r, k group g)
-    // = 8 elements of one row, 16 bytes at (r / 8) sbo + g 128 + (r % 8) 16
-    for (int q = tid; q < TC_M * kgs; q += TC_THREADS) {
-        const int r = q / kgs, g = q - r * kgs;
-        *reinterpret_cast<uint4 *>(As + (r >> 3) * sbo + g * 128 + (r & 7) * 16) = load8(X, rows, K, m0 + r, g * 8, xvec);
-        *reinterpret_cast<uint4 *>(Bs + (r >> 3) * sbo + g * 128 + (r & 7) * 16) = load8(Wt, N, K, n0 + r, g * 8, wvec);
-    }
+    // = 8 elements of one row, 16 bytes at (r / 8) sbo + g 128 + (r % 8) 16.
+    // BF16 rows that allow it are copied with asynchronous 16-byte copies,
+    // all of a thread's in flight at once (zero-filled outside the matrix);
+    // others are converted through registers.
+    stage_operand(As, X, rows, K, m0, TC_M, kgs, sbo, xvec, tid);
+    stage_operand(Bs, Wt, N, K, n0, TC_N, kgs, sbo, wvec, tid);
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -366,27 +464,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
-        const int m = m0 + warp * 32 + lane;
-        for (int c = 0; c < TC_N && n0 + c < N; c += 16) {
-            uint32_t v[16];
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (m < rows) {
-                for (int j = 0; j < 16; ++j) {
-                    const int n = n0 + c + j;
-                    if (n >= N) break;
-                    const float z = __uint_as_float(v[j]) + (bias ? __ldg(bias + n) : 0.f);
-                    const float y = act == FDTD_ACT_GELU ? gelu(z) : z;
-                    const size_t o = (size_t)m * N + n;
-                    if (zf) zf[o] = z;
-                    if (yf) yf[o] = y;
-                    if (yb) yb[o] = __float2bfloat16_rn(y);
-                }
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (its 32 rows)
+        // and accumulator columns 32 (w / 4) .. +31; bias and activation in
+        // registers, then each output is transposed through the warp's
+        // shared buffer in the (now idle) operand area and stored as whole
+        // row segments
+        const int lg = warp & 3, c = (warp >> 2) * 32;
+        float *T = reinterpret_cast<float *>(As) + warp * 32 * TC_TS;
+        const int mrow = m0 + lg * 32;
+        if (n0 + c < N) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)c, v);
+            float z[32], y[32];
+            for (int j = 0; j < 32; ++j) {
+                const int n = n0 + c + j;
+                z[j] = __uint_as_float(v[j]) + ((bias && n < N) ? __ldg(bias + n) : 0.f);
+                y[j] = act == FDTD_ACT_GELU ? gelu(z[j]) : z[j];
             }
+            if (zf) store_f32(T, z, zf, mrow, rows, n0 + c, N, lane);
+            if (yf) store_f32(T, y, yf, mrow, rows, n0 + c, N, lane);
+            if (yb) store_bf16(T, y, yb, mrow, rows, n0 + c, N, lane);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -547,7 +644,8 @@ int fdtd_mlp_scale_rows(float *y, const float *scale, int rows, int cols, void *
 {
     if (!y || !scale || rows < 0 || cols < 0) return FDTD_EINVAL;
     if ((long long)rows * cols == 0) return FDTD_OK;
-    scale_rows_kernel<<<grid1d((long long)rows * cols), 256, 0, (cudaStream_t)cuda_stream>>>(y, scale, rows, cols);
+    const dim3 grid((unsigned)std::min((cols + 255) / 256, 64), (unsigned)std::min(rows, 65535));
+    scale_rows_kernel<<<grid, 256, 0, (cudaStream_t)cuda_stream>>>(y, scale, rows, cols);
     return rc(cudaGetLastError());
 }
 

@@ -113,9 +113,10 @@ class Network:
         b = self._bufs[rows]
         self.z, self.hb, self.out, self.dz, self.dh = b["z"], b["hb"], b["out"], b["dz"], b["dh"]
 
-    def forward(self, x):
+    def forward(self, x, keep=True):
         """x: [rows, k0] FP32 (rounded to BF16 on load).  Returns the FP32
-        output buffer [rows, n_last] (reused by the next call)."""
+        output buffer [rows, n_last] (reused by the next call).  keep: store
+        the pre-activations the backward pass needs (not for inference)."""
         rows = x.shape[0]
         self._buffers(rows)
         self.x = x
@@ -124,7 +125,7 @@ class Network:
         for l in range(L):
             last = l == L - 1
             self.mlp.forward(h, self.Wb[l], self.b[l], self.acts[l], None if last else self.hb[l],
-                             self.out if last else None, self.z[l])
+                             self.out if last else None, self.z[l] if keep else None)
             h = None if last else self.hb[l]
         return self.out
 
@@ -246,9 +247,9 @@ class Surrogate:
         B = f_dev.shape[0]
         if B not in self._units:
             self._units[B] = torch.full((B,), Y_UNIT, dtype=torch.float32, device="cuda")
-        wave = self.main.forward(f_dev)
+        wave = self.main.forward(f_dev, keep=False)
         mlp.scale_rows(wave, self._units[B])
-        log_err = self.head.forward(f_dev)
+        log_err = self.head.forward(f_dev, keep=False)
         return wave, log_err.reshape(-1)
 
     def predict_graph(self, batch):

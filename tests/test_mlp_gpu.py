@@ -31,7 +31,8 @@ def dev(torch, a, dtype):
 
 
 @pytest.mark.parametrize("rows,k,n,act", [(300, 70, 130, 1), (64, 256, 256, 1), (4096, 6, 256, 1),
-                                          (257, 256, 512, 0), (1, 13, 7, 1), (129, 64, 1, 0), (200, 300, 40, 1)])
+                                          (257, 256, 512, 0), (1, 13, 7, 1), (129, 64, 1, 0), (200, 300, 40, 1),
+                                          (131, 24, 200, 1)])
 def test_forward_layer(env, rows, k, n, act):
     torch, mlp = env
     rng = np.random.default_rng(rows + k + n)
