@@ -5,8 +5,9 @@ uniform instants).  Marshalling and host-side bookkeeping only; every step
 runs in the CUDA library.
 
 The tile depth (planes per work item) of each domain comes from a small
-autotuner: it times the candidates on the GPU for a size class once and
-keeps the winners in a JSON cache next to this file.
+autotuner: for each 16-cell size class it times the candidates on a batch of
+copies of a representative domain (the regime the depth serves) once and
+keeps the winners in a JSON cache in the build folder.
 """
 from __future__ import annotations
 
@@ -19,7 +20,7 @@ import numpy as np
 from . import fdtd, workloads as W
 
 _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tuning.json")
-CANDIDATES = (8, 12, 16, 24, 32)
+CANDIDATES = (8, 12, 16, 24, 32, 48)
 
 
 def size_class(n: int) -> int:
@@ -43,30 +44,37 @@ def _store_cache(c):
     os.replace(tmp, _CACHE)
 
 
-def tune_block(n: int, steps: int = 64, force: bool = False) -> int:
-    """Planes per work item for n^3 grounding domains: the candidate with the
-    shortest measured step on a representative domain (cached)."""
+def tune_block(n: int, steps: int = 32, force: bool = False) -> int:
+    """Planes per work item for n^3 grounding domains advanced in a batch:
+    the candidate with the shortest measured step of a batch of copies of a
+    representative domain (enough copies that the batch, not one domain,
+    fills the GPU, as in the batches this serves; cached)."""
     import torch
-    key = f"ground_n{size_class(n)}"
+    key = f"ground_batch_n{size_class(n)}"
     cache = _load_cache()
     if key in cache and not force:
         return int(cache[key])
-    sc = W.grounding_domain(size_class(n), 15.0, 1e-3, 1.0, 0.008, 0.0, 0.25e-6, n_steps=steps + 8)
-    best, best_t = 16, float("inf")
+    m = size_class(n)
+    copies = int(max(8, min(64, 4.0e7 // m ** 3)))
+    sc = W.grounding_domain(m, 15.0, 1e-3, 1.0, 0.008, 0.0, 0.25e-6, n_steps=steps + 8)
+    best, best_t = 8, float("inf")
     for kz in CANDIDATES:
-        if kz > size_class(n):
+        if kz > m:
             continue
-        g = fdtd.from_scenario(sc, probe_capacity=steps + 8, block=kz)
-        g.step(8)
-        g.synchronize()
+        grids = [fdtd.from_scenario(sc, probe_capacity=steps + 8, block=kz) for _ in range(copies)]
+        b = fdtd.Batch(grids)
+        b.step(8)
+        b.synchronize()
         s = torch.cuda.current_stream()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(s)
-        g.step(steps)
+        b.step(steps)
         e1.record(s)
-        torch.cuda.synchronize()
+        b.synchronize()
         t = e0.elapsed_time(e1)
-        g.close()
+        b.close()
+        for g in grids:
+            g.close()
         if t < best_t:
             best, best_t = kz, t
     cache[key] = best
