@@ -229,6 +229,17 @@ int fdtd_batch_launch_info(const fdtd_batch *b, int launch, int *ctas, int *item
 const char *fdtd_batch_last_error(const fdtd_batch *b);
 void fdtd_batch_destroy(fdtd_batch *b);
 
+/* Self-test of the bounded waits (a library addition).  Every wait of the
+ * step kernel on an mbarrier gives up after 2 s, records the failure, drains
+ * its copies in flight and returns, so that fdtd_synchronize() reports
+ * FDTD_ETIMEOUT instead of the GPU hanging.  This call runs the same wait
+ * routine on an mbarrier phase that nothing completes, with a limit of
+ * `seconds` (0 < seconds <= 10), on cuda_stream, and synchronises it.
+ * Returns FDTD_ETIMEOUT when the wait gave up as designed (the expected
+ * result), FDTD_OK if it completed, FDTD_EINVAL for a bad limit,
+ * FDTD_ECUDA on a CUDA error.  The context stays usable afterwards. */
+int fdtd_selftest_wait(double seconds, void *cuda_stream);
+
 /* Checkpoint / resume of a finalized grid (a library addition; the paper's
  * solver has no counterpart).  The state is everything the step reads that
  * changes while stepping: the six fields, the twelve CPML auxiliaries (when

@@ -32,6 +32,7 @@
 
 #include <algorithm>
 
+#include "fdtd.h"
 #include "fdtd_internal.h"
 
 namespace fdtd {
@@ -157,18 +158,41 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// bounded wait on one mbarrier phase; gives up on timeout or when another
-// warp of the CTA has already given up
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort)
+// bounded wait on one mbarrier phase; gives up on timeout (limit_ns) or when
+// another warp of the CTA has already given up
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort,
+                                          unsigned long long limit_ns = kWaitNs)
 {
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = gtimer();
     while (true) {
         if (mbar_try(bar, parity)) return true;
         if (*abort) return false;
-        if (gtimer() - t0 > kWaitNs) return false;
+        if (gtimer() - t0 > limit_ns) return false;
     }
 }
+
+// Self-test of the bounded wait: one thread waits, through mbar_wait, on an
+// mbarrier phase that nothing will complete, gives up after limit_ns and
+// records that in *flag (the step kernel's timeout path, without a step).
+__global__ void wait_selftest_kernel(unsigned long long limit_ns, int *flag)
+{
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        abort_flag = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const bool ok = mbar_wait(smem_u32(&bar), 0, &abort_flag, limit_ns);
+        *flag = ok ? 2 : 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar)) : "memory");
+}
+
+__device__ int g_selftest_flag;
 
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z,
                                             uint32_t bar)
@@ -891,3 +915,21 @@ cudaError_t launch_step(const SingleArgs &one, const BatchArgs &b, int grid, cud
 }
 
 }  // namespace fdtd
+
+extern "C" int fdtd_selftest_wait(double seconds, void *cuda_stream)
+{
+    if (!(seconds > 0.0) || seconds > 10.0) return FDTD_EINVAL;
+    int *flag = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void **>(&flag), fdtd::g_selftest_flag);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+        fdtd::wait_selftest_kernel<<<1, 32, 0, s>>>((unsigned long long)(seconds * 1e9), flag);
+        e = cudaGetLastError();
+    }
+    int v = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&v, flag, sizeof v, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return FDTD_ECUDA;
+    return v == 1 ? FDTD_ETIMEOUT : (v == 2 ? FDTD_OK : FDTD_ECUDA);
+}
