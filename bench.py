@@ -42,8 +42,9 @@ def args_parse():
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "surrogate"],
-                    help="single: the 256^3 grid (headline); batch: 256 grounding domains in one batch")
+    ap.add_argument("--workload", default="single", choices=["single", "config3", "batch", "surrogate"],
+                    help="single: the 256^3 grid (headline); config3: the 512x512x384 buried-mesh grid; "
+                         "batch: 256 grounding domains in one batch; surrogate: the learned surrogate vs FDTD")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n", type=int, default=256,
@@ -53,16 +54,23 @@ def args_parse():
     return ap.parse_args()
 
 
-def workload(n_steps, n=256):
+def workload(n_steps, n=256, name="single"):
     from paper_2207_06908_gb300 import workloads
+    if name == "config3":
+        return workloads.config3(n_steps=n_steps)
     return workloads.config2(n_steps=n_steps, n=n)
 
 
 def workload_config(sc, steps):
-    return {"workload": f"{sc.n[0]}^3 Yee grid dx=0.5m, 10-cell CPML, soil half-space (eps_r 15, sigma 2 mS/m), "
-                        "30 m thin wire r=5mm, 1.2/50us 10kA double-exponential source, 6 probes",
-            "grid": list(sc.n), "cpml_cells": sc.cpml, "courant": sc.courant, "steps_timed": steps,
-            "l2": "inputs larger than L2 (about 0.95 GB of fields, classes and CPML state per step)"}
+    gb = bytes_per_step(sc) / 1e9
+    if sc.n == (512, 512, 384):
+        desc = ("512x512x384 Yee grid dx=0.25m, 12-cell CPML, two-layer soil, buried 8x8 thin-wire mesh "
+                "(r=6mm) with down-conductor, current and voltage leads, 1 kA 0.5us ramp source")
+    else:
+        desc = (f"{sc.n[0]}^3 Yee grid dx=0.5m, 10-cell CPML, soil half-space (eps_r 15, sigma 2 mS/m), "
+                "30 m thin wire r=5mm, 1.2/50us 10kA double-exponential source, 6 probes")
+    return {"workload": desc, "grid": list(sc.n), "cpml_cells": sc.cpml, "courant": sc.courant, "steps_timed": steps,
+            "l2": f"inputs larger than L2 (about {gb:.2f} GB of fields, classes and CPML state per step)"}
 
 
 def bytes_per_step(sc):
@@ -179,7 +187,7 @@ def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    sc = workload(a.steps + a.warmup, a.n)
+    sc = workload(a.steps + a.warmup, a.n, a.workload if a.workload in ("single", "config3") else "single")
     from oracle import oracle as O
     o = O.OracleGrid.from_scenario(sc, parity=False)
     w = 2
@@ -413,7 +421,9 @@ def main():
     _build.build()
 
     K, Wm = a.steps, max(3, a.warmup)
-    sc = workload(K + Wm, a.n)
+    if a.workload == "config3" and K == 4000:
+        K = 8000                       # the 512x512x384 workload's own length
+    sc = workload(K + Wm, a.n, a.workload)
     stream = torch.cuda.current_stream()
     g = fdtd.from_scenario(sc, probe_capacity=K + Wm)
     g.step(Wm)

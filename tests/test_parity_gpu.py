@@ -167,6 +167,19 @@ def test_config2_full_size_random_fields_no_source(fdtd):
     compare(*run_gpu(fdtd, sc, steps), *run_oracle(sc, steps))
 
 
+def test_config3_full_size_random_fields_no_source(fdtd):
+    """512x512x384, 12-cell CPML, two-layer soil, the buried 8x8 wire mesh,
+    down-conductor and leads (the largest workload, 100.7 M cells) at full
+    size without its source, from seeded random fields: fields within 1e-5
+    and probes within 1e-4 after 12 steps"""
+    steps = 12
+    sc = W.config3(n_steps=steps)
+    sc.sources = []
+    rng = np.random.default_rng(2026)
+    sc.fields = W.random_fields(rng, sc.n)
+    compare(*run_gpu(fdtd, sc, steps), *run_oracle(sc, steps))
+
+
 def test_config2_scaled_long_run(fdtd):
     """the config-2 layout at 64^3 for 800 steps from rest: the source
     drives the wire through the CPML window (from rest: the field bar of
