@@ -26,6 +26,19 @@
  *     beyond the circumferential H for stability (see orc_finalize).
  *   - Sec. 4 model files ("calculate"): voltage = -sum E dl along a path,
  *     current = loop integral of H around an edge.
+ *   - Dispersive media (the paper's "Dispersive media" subsection): a
+ *     multi-term Debye permittivity eps(w) = eps_inf + sum_p deps_p /
+ *     (1 + j w tau_p) plus static sigma, by the auxiliary differential
+ *     equation method of the references it cites (Okoniewski et al.;
+ *     Taflove and Hagness): per pole a polarisation current J_p kept at the
+ *     E time levels t_n, with tau_p dJ_p/dt + J_p = eps0 deps_p dE/dt taken
+ *     by the trapezoidal rule over [t_n, t_{n+1}]; Ampere's law at
+ *     t_{n+1/2} uses the mean of J_p^n and J_p^{n+1}.  Readings (the
+ *     paper is silent): an E edge takes the mean over its four cells of each
+ *     pole's deps (zero for cells without that pole) and the deps-weighted
+ *     mean of its tau; a thin wire scales the whole complex permittivity
+ *     (eps_inf, sigma and every deps_p) by its factor m.  The interface
+ *     averaging of poles is parity unpinned against the paper.
  *
  * Layout.  Every component is a node-indexed FP64 array of
  * (nx+1)(ny+1)(nz+1) entries, index (k*(ny+1)+j)*(nx+1)+i, holding
@@ -62,6 +75,7 @@ typedef ORC_REAL real;
 #define ORC_EPS0 8.8541878128e-12
 #define ORC_MU0 1.25663706212e-6
 #define ORC_R0_FRAC 0.23
+#define ORC_MAXP 4                 /* Debye poles per material */
 
 enum { EX = 0, EY, EZ, HX, HY, HZ };
 enum { PROBE_V = 0, PROBE_I = 1, PROBE_E = 2, PROBE_H = 3 };
@@ -98,6 +112,14 @@ typedef struct orc_grid {
     orc_src *srcs; int n_srcs;
     orc_probe *probes; int n_probes;
     real *src_coef;            /* -cb/dx at each source edge */
+    /* Debye media: poles per material (deps_p, tau_p; deps 0 = no pole);
+     * per E edge and pole: cj (E^{n+1} += cj J^n), k and be (J^{n+1} =
+     * k J^n + be (E^{n+1} - E^n)) and the current J_p^n (at the E time
+     * level); allocated when any material has a pole */
+    double m_deps[256][ORC_MAXP], m_tau[256][ORC_MAXP];
+    int has_debye;
+    real *dcj[3][ORC_MAXP], *dk[3][ORC_MAXP], *dbe[3][ORC_MAXP], *J[3][ORC_MAXP];
+    real *eprev[3];
     int max_steps;
     double *probe_out;         /* [n_probes][max_steps] */
     long step;
@@ -146,6 +168,10 @@ void orc_destroy(orc_grid *g)
         free(g->ph_b[u]); free(g->ph_c[u]); free(g->ph_ki[u]); free(g->ph_on[u]);
     }
     for (int c = 0; c < 6; c++) for (int u = 0; u < 3; u++) free(g->psi[c][u]);
+    for (int c = 0; c < 3; c++) {
+        free(g->eprev[c]);
+        for (int p = 0; p < ORC_MAXP; p++) { free(g->dcj[c][p]); free(g->dk[c][p]); free(g->dbe[c][p]); free(g->J[c][p]); }
+    }
     for (int s = 0; s < g->n_srcs; s++) free(g->srcs[s].cur);
     free(g->srcs); free(g->wires); free(g->probes); free(g->src_coef); free(g->probe_out);
     free(g->mat); free(g->m_eps); free(g->m_sig); free(g->m_mu);
@@ -198,6 +224,22 @@ int orc_set_materials(orc_grid *g, const uint8_t *cell_mat, const double *eps_r,
     memcpy(g->m_sig, sigma, n_mat * sizeof(double));
     memcpy(g->m_mu, mu_r, n_mat * sizeof(double));
     g->n_mat = n_mat;
+    return 0;
+}
+
+/* Debye poles of material `mat`: deps[p] (relative, >= 0) and tau[p] (s,
+ * > 0), p < n_poles <= ORC_MAXP; later poles are cleared */
+int orc_set_debye(orc_grid *g, int mat, int n_poles, const double *deps, const double *tau)
+{
+    if (g->finalized) return -8;
+    if (mat < 0 || mat > 255 || n_poles < 0 || n_poles > ORC_MAXP) return -1;
+    for (int p = 0; p < n_poles; p++)
+        if (!(deps[p] >= 0) || !(tau[p] > 0)) return -1;
+    for (int p = 0; p < ORC_MAXP; p++) {
+        g->m_deps[mat][p] = p < n_poles ? deps[p] : 0.0;
+        g->m_tau[mat][p] = p < n_poles ? tau[p] : 1.0;
+        if (g->m_deps[mat][p] > 0) g->has_debye = 1;
+    }
     return 0;
 }
 
@@ -263,6 +305,79 @@ int orc_add_probe(orc_grid *g, int kind, int i, int j, int k, int axis, int n_ed
 static double cell_eps(const orc_grid *g, int i, int j, int k) { return g->m_eps[g->mat[CELL(g, i, j, k)]]; }
 static double cell_sig(const orc_grid *g, int i, int j, int k) { return g->m_sig[g->mat[CELL(g, i, j, k)]]; }
 static double cell_mu(const orc_grid *g, int i, int j, int k) { return g->m_mu[g->mat[CELL(g, i, j, k)]]; }
+
+/* the four cells around E edge comp at node (i,j,k) (the same cells whose
+ * eps and sigma are averaged) */
+static void edge_cells(int comp, int i, int j, int k, int cell[4][3])
+{
+    for (int t = 0; t < 4; t++) {
+        int a = t & 1, b = t >> 1;
+        if (comp == 0) { cell[t][0] = i; cell[t][1] = j - 1 + a; cell[t][2] = k - 1 + b; }
+        else if (comp == 1) { cell[t][0] = i - 1 + a; cell[t][1] = j; cell[t][2] = k - 1 + b; }
+        else { cell[t][0] = i - 1 + a; cell[t][1] = j - 1 + b; cell[t][2] = k; }
+    }
+}
+
+/* Debye poles of an E edge: deps = mean over its four cells, tau = the
+ * deps-weighted mean over the cells that have the pole */
+static void edge_poles(const orc_grid *g, int comp, int i, int j, int k, double deps[ORC_MAXP],
+                       double tau[ORC_MAXP])
+{
+    int cell[4][3];
+    edge_cells(comp, i, j, k, cell);
+    for (int p = 0; p < ORC_MAXP; p++) {
+        double sd = 0.0, st = 0.0;
+        for (int t = 0; t < 4; t++) {
+            int m = g->mat[CELL(g, cell[t][0], cell[t][1], cell[t][2])];
+            sd += g->m_deps[m][p];
+            st += g->m_deps[m][p] * g->m_tau[m][p];
+        }
+        deps[p] = 0.25 * sd;
+        tau[p] = sd > 0 ? st / sd : 1.0;
+    }
+}
+
+/* coefficients of one E edge: eps (relative, averaged), sigma, wire factor
+ * m; poles (deps relative, tau) when the edge is dispersive.  Without poles
+ * the semi-implicit loss form ca = (1-a)/(1+a), cb = dt/(eps dx)/(1+a),
+ * a = sigma dt / (2 eps); with poles the ADE form
+ *   D = 2 eps + sum beta_p + sigma dt,
+ *   ca = (2 eps + sum beta_p - sigma dt) / D,  cb = 2 dt / (D dx),
+ *   cj_p = -dt (1 + k_p) / D,  k_p = (2 tau_p - dt) / (2 tau_p + dt),
+ *   be_p = beta_p / dt,  beta_p = 2 eps0 deps_p dt / (2 tau_p + dt),
+ * with eps, sigma and every deps scaled by m. */
+static int e_coefs(const orc_grid *g, double eps_r, double sig, double m, const double *deps, const double *tau,
+                   double *ca, double *cb, double cj[ORC_MAXP], double kk[ORC_MAXP], double be[ORC_MAXP])
+{
+    double dt = g->dt, dx = g->dx;
+    double e = ORC_EPS0 * eps_r * m, s = sig * m;
+    int disp = 0;
+    for (int p = 0; p < ORC_MAXP; p++) {
+        cj[p] = kk[p] = be[p] = 0.0;
+        if (deps && deps[p] > 0) disp = 1;
+    }
+    if (!disp) {
+        double a = s * dt / (2.0 * e);
+        *ca = (1.0 - a) / (1.0 + a);
+        *cb = dt / (e * dx) / (1.0 + a);
+        return 0;
+    }
+    double beta[ORC_MAXP], sb = 0.0;
+    for (int p = 0; p < ORC_MAXP; p++) {
+        beta[p] = 2.0 * ORC_EPS0 * deps[p] * m * dt / (2.0 * tau[p] + dt);
+        kk[p] = deps[p] > 0 ? (2.0 * tau[p] - dt) / (2.0 * tau[p] + dt) : 0.0;
+        sb += beta[p];
+    }
+    double D = 2.0 * e + sb + s * dt;
+    *ca = (2.0 * e + sb - s * dt) / D;
+    *cb = 2.0 * dt / (D * dx);
+    for (int p = 0; p < ORC_MAXP; p++) {
+        if (!(deps[p] > 0)) continue;
+        cj[p] = -dt * (1.0 + kk[p]) / D;
+        be[p] = beta[p] / dt;
+    }
+    return 1;
+}
 
 /* CPML grading at depth rho (cells) into the layer, Roden-Gedney CFS form */
 static void cpml_coef(const orc_grid *g, double rho, double *b, double *c, double *ki)
@@ -452,17 +567,38 @@ int orc_finalize(orc_grid *g, int max_steps)
     /* 3. coefficients of the semi-implicit update (Eq. fdtdex with the loss
      *    time-averaged) and of Eq. fdtdhx; 1/dx folded in */
     double dt = g->dt, dx = g->dx;
+    if (g->has_debye) {
+        for (int c = 0; c < 3; c++) {
+            g->eprev[c] = (real *)calloc(N, sizeof(real));
+            for (int p = 0; p < ORC_MAXP; p++) {
+                g->dcj[c][p] = (real *)calloc(N, sizeof(real));
+                g->dk[c][p] = (real *)calloc(N, sizeof(real));
+                g->dbe[c][p] = (real *)calloc(N, sizeof(real));
+                g->J[c][p] = (real *)calloc(N, sizeof(real));
+            }
+        }
+    }
     for (int c = 0; c < 3; c++) {
         g->ca[c] = (real *)calloc(N, sizeof(real));
         g->cb[c] = (real *)calloc(N, sizeof(real));
         g->db[c] = (real *)calloc(N, sizeof(real));
         for (size_t q = 0; q < N; q++) {
             if (eps[c][q] > 0 && !pec[c][q]) {
-                double e = ORC_EPS0 * eps[c][q] * fac_e[c][q];
-                double s = sig[c][q] * fac_e[c][q];
-                double a = s * dt / (2.0 * e);
-                g->ca[c][q] = r32(g, (1.0 - a) / (1.0 + a));
-                g->cb[c][q] = r32(g, dt / (e * dx) / (1.0 + a));
+                double deps[ORC_MAXP], tau[ORC_MAXP], ca, cb, cj[ORC_MAXP], kk[ORC_MAXP], be[ORC_MAXP];
+                if (g->has_debye) {
+                    int k = (int)(q / g->sz), j = (int)((q % g->sz) / g->sy), i = (int)(q % g->sy);
+                    edge_poles(g, c, i, j, k, deps, tau);
+                }
+                int disp = e_coefs(g, eps[c][q], sig[c][q], fac_e[c][q], g->has_debye ? deps : NULL, tau, &ca, &cb,
+                                   cj, kk, be);
+                g->ca[c][q] = r32(g, ca);
+                g->cb[c][q] = r32(g, cb);
+                if (disp)
+                    for (int p = 0; p < ORC_MAXP; p++) {
+                        g->dcj[c][p][q] = r32(g, cj[p]);
+                        g->dk[c][p][q] = r32(g, kk[p]);
+                        g->dbe[c][p][q] = r32(g, be[p]);
+                    }
             }
             if (mu[c][q] > 0) {
                 double mm = ORC_MU0 * mu[c][q] / fac_h[c][q];
@@ -477,10 +613,10 @@ int orc_finalize(orc_grid *g, int max_steps)
         size_t q = IDX(g, sr->i, sr->j, sr->k);
         double cbq;
         if (eps[sr->axis][q] > 0 && !pec[sr->axis][q]) {
-            double e = ORC_EPS0 * eps[sr->axis][q] * fac_e[sr->axis][q];
-            double sg = sig[sr->axis][q] * fac_e[sr->axis][q];
-            double a = sg * dt / (2.0 * e);
-            cbq = dt / (e * dx) / (1.0 + a);
+            double deps[ORC_MAXP], tau[ORC_MAXP], ca, cj[ORC_MAXP], kk[ORC_MAXP], be[ORC_MAXP];
+            if (g->has_debye) edge_poles(g, sr->axis, sr->i, sr->j, sr->k, deps, tau);
+            e_coefs(g, eps[sr->axis][q], sig[sr->axis][q], fac_e[sr->axis][q], g->has_debye ? deps : NULL, tau, &ca,
+                    &cbq, cj, kk, be);
         } else {
             cbq = 0.0;
         }
@@ -577,12 +713,22 @@ static void update_h(orc_grid *g)
             }
 }
 
+/* E^{n+1} += sum_p cj_p J_p^n at node q of component c */
+static inline real debye_add(const orc_grid *g, int c, size_t q, real e)
+{
+    for (int p = 0; p < ORC_MAXP; p++) e += g->dcj[c][p][q] * g->J[c][p][q];
+    return e;
+}
+
 static void update_e(orc_grid *g)
 {
     int nx = g->nx, ny = g->ny, nz = g->nz;
     real *Ex = g->f[EX], *Ey = g->f[EY], *Ez = g->f[EZ];
     real *Hx = g->f[HX], *Hy = g->f[HY], *Hz = g->f[HZ];
     size_t sy = g->sy, sz = g->sz;
+    const int deb = g->has_debye;
+    if (deb)
+        for (int c = 0; c < 3; c++) memcpy(g->eprev[c], g->f[c], g->ntot * sizeof(real));
     /* Ex(i+1/2,j,k) = ca Ex + cb [dHz/dy - dHy/dz]; j in (0,ny), k in (0,nz) */
 #pragma omp parallel for collapse(2) schedule(static)
     for (int k = 1; k < nz; k++)
@@ -592,6 +738,7 @@ static void update_e(orc_grid *g)
                 real ty = term(Hz[q] - Hz[q - sy], g->psi[EX][1], q, g->pe_on[1][j], g->pe_b[1][j], g->pe_c[1][j], g->pe_ki[1][j]);
                 real tz = term(Hy[q] - Hy[q - sz], g->psi[EX][2], q, g->pe_on[2][k], g->pe_b[2][k], g->pe_c[2][k], g->pe_ki[2][k]);
                 Ex[q] = g->ca[0][q] * Ex[q] + g->cb[0][q] * (ty - tz);
+                if (deb) Ex[q] = debye_add(g, 0, q, Ex[q]);
             }
     /* Ey(i,j+1/2,k) = ca Ey + cb [dHx/dz - dHz/dx]; i in (0,nx), k in (0,nz) */
 #pragma omp parallel for collapse(2) schedule(static)
@@ -602,6 +749,7 @@ static void update_e(orc_grid *g)
                 real tz = term(Hx[q] - Hx[q - sz], g->psi[EY][2], q, g->pe_on[2][k], g->pe_b[2][k], g->pe_c[2][k], g->pe_ki[2][k]);
                 real tx = term(Hz[q] - Hz[q - 1], g->psi[EY][0], q, g->pe_on[0][i], g->pe_b[0][i], g->pe_c[0][i], g->pe_ki[0][i]);
                 Ey[q] = g->ca[1][q] * Ey[q] + g->cb[1][q] * (tz - tx);
+                if (deb) Ey[q] = debye_add(g, 1, q, Ey[q]);
             }
     /* Ez(i,j,k+1/2) = ca Ez + cb [dHy/dx - dHx/dy]; i in (0,nx), j in (0,ny) */
 #pragma omp parallel for collapse(2) schedule(static)
@@ -612,6 +760,7 @@ static void update_e(orc_grid *g)
                 real tx = term(Hy[q] - Hy[q - 1], g->psi[EZ][0], q, g->pe_on[0][i], g->pe_b[0][i], g->pe_c[0][i], g->pe_ki[0][i]);
                 real ty = term(Hx[q] - Hx[q - sy], g->psi[EZ][1], q, g->pe_on[1][j], g->pe_b[1][j], g->pe_c[1][j], g->pe_ki[1][j]);
                 Ez[q] = g->ca[2][q] * Ez[q] + g->cb[2][q] * (tx - ty);
+                if (deb) Ez[q] = debye_add(g, 2, q, Ez[q]);
             }
     /* ideal current sources: -cb/dx * I(t_{n+1/2}) on the source edge */
     for (int s = 0; s < g->n_srcs; s++) {
@@ -631,6 +780,39 @@ static void update_e(orc_grid *g)
                 if (i == 0 || i == nx || k == 0 || k == nz) Ey[q] = 0.0;
                 if (i == 0 || i == nx || j == 0 || j == ny) Ez[q] = 0.0;
             }
+    /* polarisation currents to t_{n+1} from the final E^{n+1} (sources
+     * included): J_p^{n+1} = k_p J_p^n + be_p (E^{n+1} - E^n) */
+    if (deb)
+        for (int c = 0; c < 3; c++)
+            for (int p = 0; p < ORC_MAXP; p++) {
+                real *Jp = g->J[c][p];
+                const real *kk = g->dk[c][p], *be = g->dbe[c][p], *e1 = g->f[c], *e0 = g->eprev[c];
+#pragma omp parallel for schedule(static)
+                for (size_t q = 0; q < g->ntot; q++) Jp[q] = kk[q] * Jp[q] + be[q] * (e1[q] - e0[q]);
+            }
+}
+
+/* set the polarisation current J_p^n (E time level) of pole p of E component c
+ * (cell-owned layout); only after finalize, on a grid with Debye media */
+int orc_set_debye_current(orc_grid *g, int comp, int pole, const double *cells)
+{
+    if (!g->finalized || !g->has_debye || comp < 0 || comp > 2 || pole < 0 || pole >= ORC_MAXP) return -1;
+    for (int k = 0; k < g->nz; k++)
+        for (int j = 0; j < g->ny; j++)
+            for (int i = 0; i < g->nx; i++)
+                g->J[comp][pole][IDX(g, i, j, k)] = cells[CELL(g, i, j, k)];
+    return 0;
+}
+
+/* polarisation current of pole p of E component c, cell-owned layout */
+int orc_get_debye_current(const orc_grid *g, int comp, int pole, double *cells)
+{
+    if (comp < 0 || comp > 2 || pole < 0 || pole >= ORC_MAXP) return -1;
+    for (int k = 0; k < g->nz; k++)
+        for (int j = 0; j < g->ny; j++)
+            for (int i = 0; i < g->nx; i++)
+                cells[CELL(g, i, j, k)] = g->has_debye ? g->J[comp][pole][IDX(g, i, j, k)] : 0.0;
+    return 0;
 }
 
 static double probe_value(const orc_grid *g, const orc_probe *p)

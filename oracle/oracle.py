@@ -86,6 +86,9 @@ def _load(f32: bool = False):
         lib.orc_get_coef.argtypes = [P, I, dp]
         lib.orc_step.argtypes = [P, I]
         lib.orc_read_probe.argtypes = [P, I, dp]
+        lib.orc_set_debye.argtypes = [P, I, I, dp, dp]
+        lib.orc_get_debye_current.argtypes = [P, I, I, dp]
+        lib.orc_set_debye_current.argtypes = [P, I, I, dp]
         _libs[f32] = lib
         return lib
 
@@ -156,6 +159,24 @@ class OracleGrid:
             self._h, cm.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
             _dptr(e), _dptr(s), _dptr(m), len(e)), "set_materials")
 
+    def set_debye(self, material, deps, tau):
+        """Debye poles (relative delta eps, tau in s) of one material"""
+        d = np.ascontiguousarray(deps, dtype=np.float64)
+        t = np.ascontiguousarray(tau, dtype=np.float64)
+        _check(self._lib.orc_set_debye(self._h, int(material), len(d), _dptr(d), _dptr(t)), "set_debye")
+
+    def set_debye_current(self, comp, pole, values):
+        """J_p at the current E time level t_n of E component comp
+        (cell-owned layout)"""
+        v = np.ascontiguousarray(values, dtype=np.float64)
+        assert v.shape == self.shape
+        _check(self._lib.orc_set_debye_current(self._h, int(comp), int(pole), _dptr(v)), "set_debye_current")
+
+    def get_debye_current(self, comp, pole) -> np.ndarray:
+        out = np.empty(self.shape, dtype=np.float64)
+        _check(self._lib.orc_get_debye_current(self._h, int(comp), int(pole), _dptr(out)), "get_debye_current")
+        return out
+
     def add_wire(self, p0, p1, radius):
         _check(self._lib.orc_add_wire(self._h, *map(int, p0), *map(int, p1), float(radius)),
                "add_wire")
@@ -198,12 +219,15 @@ class OracleGrid:
         """Build from a problem description with the attributes n, dx,
         courant, cpml, cell_material, materials [(eps_r, sigma, mu_r)],
         wires [(p0, p1, radius)], sources [(node, axis, current)], probes
-        [(kind, node, axis, n_edges)], n_steps and fields (or None)."""
+        [(kind, node, axis, n_edges)], n_steps, fields (or None) and debye
+        {material: (deps, tau)} (optional)."""
         g = cls(*sc.n, sc.dx, courant=sc.courant, parity=parity, f32=f32)
         if sc.cpml:
             g.set_cpml(sc.cpml)
         g.set_materials(sc.cell_material, [m[0] for m in sc.materials], [m[1] for m in sc.materials],
                         [m[2] for m in sc.materials])
+        for mat, (deps, tau) in (getattr(sc, "debye", None) or {}).items():
+            g.set_debye(mat, deps, tau)
         for p0, p1, r in sc.wires:
             g.add_wire(p0, p1, r)
         for node, axis, cur in sc.sources:

@@ -44,6 +44,7 @@ class Scenario:
     probes: list = dataclasses.field(default_factory=list)    # [(kind, node, axis, n_edges)]
     n_steps: int = 0
     fields: list | None = None    # optional initial [Ex,Ey,Ez,Hx,Hy,Hz] (nz,ny,nx) float32
+    debye: dict = dataclasses.field(default_factory=dict)     # {material: (deps [P], tau [P] s)}
 
     @property
     def cells(self) -> int:
