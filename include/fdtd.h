@@ -98,6 +98,19 @@ int fdtd_create_grid(int nx, int ny, int nz, double dx, double courant,
 int fdtd_set_materials(fdtd_grid *g, const uint8_t *cell_material,
                        const fdtd_material *table, int n_materials);
 
+/* Debye poles of material `material` (the paper's "Dispersive media"
+ * subsection: a multi-term Debye permittivity eps(w) = eps_inf + sum_p
+ * deps_p / (1 + j w tau_p), eps_inf and the static sigma being the
+ * material's eps_r and sigma, simulated by the auxiliary differential
+ * equation method the paper cites).  delta_eps[p] (relative, >= 0) and
+ * tau[p] (s, > 0) for p < n_poles <= 4; a later call replaces the poles.
+ * Before fdtd_finalize (FDTD_ESTATE after), FDTD_EINVAL for bad values.
+ * Each E edge takes, per pole index, the mean of its four cells' deps (zero
+ * for a cell without the pole) and their deps-weighted mean tau; a thin
+ * wire scales eps, sigma and every deps of its radial edges by its factor.
+ * Grids with poles cannot join a batch (fdtd_batch_create: FDTD_EINVAL). */
+int fdtd_set_debye(fdtd_grid *g, int material, int n_poles, const double *delta_eps, const double *tau);
+
 /* Thin wire (Sec. 2.3; "wire(thin, ...)" in the Sec. 4 model files) along
  * one axis from node (i0,j0,k0) to node (i1,j1,k1), i1>i0 or j1>j0 or k1>k0
  * with the other two coordinates equal and strictly inside the grid

@@ -82,6 +82,7 @@ def load():
             "fdtd_batch_last_error": (ctypes.c_char_p, [P]),
             "fdtd_batch_destroy": (None, [P]),
             "fdtd_selftest_wait": (I, [ctypes.c_double, P]),
+            "fdtd_set_debye": (I, [P, I, I, P, P]),
             "fdtd_save_state": (I, [P, P, ctypes.POINTER(ctypes.c_size_t)]),
             "fdtd_load_state": (I, [P, P, ctypes.c_size_t]),
             "fdtd_mlp_forward": (I, [P, I, I, I, P, P, I, I, P, P, P, P]),

@@ -1,7 +1,8 @@
 // fdtd_edges.cu -- ideal current sources (Kuklin, arXiv 2207.06908,
 // Sec. 2.1, J = I/dx^2 on one edge) and the probes of the Sec. 4 model files
 // ("calculate": voltage = -sum E dl along a path, current = loop integral of
-// H around an edge), applied right after the step kernel of the same step.
+// H around an edge), applied right after the step kernel (and, with Debye
+// media, the dispersive-media kernel) of the same step.
 // One CTA; a device-side step counter indexes the source samples and the
 // probe slots, so the launch can be replayed inside a CUDA graph.
 #include "fdtd_internal.h"
@@ -23,7 +24,14 @@ __device__ __forceinline__ void edge_body(const EdgeArgs &a)
     for (int q = threadIdx.x; q < a.n_src; q += blockDim.x) {
         const SourceDesc sd = a.src[q];
         const float I = n < sd.n_samples ? a.samples[sd.sample_off + n] : 0.f;
-        atomicAdd(a.E[sd.comp] + sd.idx, sd.coef * I);
+        const float add = sd.coef * I;
+        atomicAdd(a.E[sd.comp] + sd.idx, add);
+        // a dispersive edge: the currents already advanced with E^{n+1}
+        // before the source; they take its share, be_p times the increment
+        if (sd.jidx >= 0 && a.J)
+            for (int p = 0; p < a.npoles; ++p)
+                if (sd.be[p] != 0.f)
+                    atomicAdd(a.J + (long long)(sd.comp * a.npoles + p) * a.jstride + sd.jidx, sd.be[p] * add);
     }
     __syncthreads();
     if (n < a.capacity) {

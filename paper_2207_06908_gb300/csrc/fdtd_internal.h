@@ -116,12 +116,32 @@ struct BatchArgs {
     int nh;                  // slots of the H / class / CPML ring (2 or 3)
 };
 
+// Debye media: up to kMaxPoles poles per edge; per cell one record of
+// [E component][pole]{cj, k, be} (E^{n+1} += cj J^n, J^{n+1} = k J^n +
+// be (E^{n+1} - E^n)); record 0 = no dispersive component
+constexpr int kMaxPoles = 4;
+constexpr int kDebyeRec = 3 * kMaxPoles * 3;
+
 struct SourceDesc {
     int comp;                // 0..2
     long long idx;           // element index in the field arrays
     float coef;              // -cb / dx of the edge
     int n_samples;
     long long sample_off;    // offset into the sample table
+    long long jidx;          // element index in the Debye current arrays, or -1
+    float be[kMaxPoles];     // be of the edge's poles (dispersive edge)
+};
+
+struct DebyeArgs {
+    const float *Ein[3];     // E^n (the step's input buffers)
+    float *Eout[3];          // E^{n+1} from the step kernels, completed in place
+    float *J;                // [3 * npoles][jstride] polarisation currents, box layout
+    long long jstride;       // elements per current array (box planes x plane)
+    int npoles;
+    const uint8_t *dcls;     // per box element: record index
+    const float *table;      // [n_rec][kDebyeRec]
+    int n_rec;
+    long long off;           // field element index of the box's first element
 };
 
 struct ProbeDesc {
@@ -143,6 +163,9 @@ struct EdgeArgs {
     float *probe_out;        // [n_probes][capacity]
     int capacity;
     long long *step;         // device step counter
+    float *J;                // Debye currents (sources on dispersive edges), or null
+    long long jstride;
+    int npoles;
 };
 
 // fdtd_step.cu
@@ -158,6 +181,7 @@ void step_region(const PsiGeom &pg, int zxy, int *region, int *ox, int *oy);
 const void *step_kernel_ptr(int nh, bool batch);
 // fdtd_edges.cu
 cudaError_t launch_edges(const EdgeArgs &a, cudaStream_t s);
+cudaError_t launch_debye(const DebyeArgs &a, cudaStream_t s);
 // one CTA per domain: e[2 * d + parity]
 cudaError_t launch_edges_batch(const EdgeArgs *e, int n_domains, int parity, cudaStream_t s);
 

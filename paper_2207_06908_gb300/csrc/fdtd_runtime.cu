@@ -82,6 +82,9 @@ struct fdtd_grid {
     cudaStream_t stream = nullptr;
     std::vector<uint8_t> mat;
     std::vector<fdtd_material> table;
+    // Debye poles per material index: deps[0..3], tau[4..7] (deps 0 = none)
+    std::vector<std::array<double, 2 * fdtd::kMaxPoles>> poles =
+        std::vector<std::array<double, 2 * fdtd::kMaxPoles>>(256, {0, 0, 0, 0, 1, 1, 1, 1});
     std::vector<Wire> wires;
     std::vector<Source> srcs;
     std::vector<fdtd::ProbeDesc> probes;
@@ -129,6 +132,13 @@ struct fdtd_grid {
     int kz = 0;
     cudaStream_t cap_stream = nullptr;
     Fork fk;                      // concurrent z-layer launch (two-launch grids)
+    // Debye media: planes [dz0, dz1) hold every dispersive edge; npoles
+    // current arrays per E component over those planes, a record byte per
+    // element and the record table
+    int npoles = 0, dz0 = 0, dz1 = 0, n_drec = 0;
+    float *J = nullptr;
+    uint8_t *dcls_d = nullptr;
+    float *dtable_d = nullptr;
     cudaGraphExec_t graph = nullptr;
     std::string err;
 };
@@ -149,8 +159,34 @@ int cuda_fail(fdtd_grid *g, cudaError_t e, const char *what)
 // ---- device arena plan -------------------------------------------------
 struct Plan {
     size_t field, cls, table, prof[3], psi[fdtd::PSI_COUNT], src, samples, probes, out, step, work, slot, items,
-        total;
+        J, dcls, dtable, total;
 };
+
+// poles used by the grid (the largest pole count of a material some cell
+// has) and the planes [z0, z1) that hold its dispersive edges: an edge
+// averages the cells on its low side, so a cell with poles at plane k makes
+// edges of planes k and k + 1 dispersive
+int debye_extent(const fdtd_grid *g, int *z0, int *z1)
+{
+    std::vector<int> np(g->table.size(), 0);
+    for (size_t m = 0; m < g->table.size(); ++m)
+        for (int p = 0; p < fdtd::kMaxPoles; ++p)
+            if (g->poles[m][p] > 0) np[m] = p + 1;
+    int P = 0, kmin = g->nz, kmax = -1;
+    const size_t per = (size_t)g->nx * g->ny;
+    for (size_t c = 0; c < g->mat.size(); ++c) {
+        const int m = g->mat[c];
+        if (m < (int)np.size() && np[m] > 0) {
+            P = std::max(P, np[m]);
+            const int k = (int)(c / per);
+            kmin = std::min(kmin, k);
+            kmax = std::max(kmax, k);
+        }
+    }
+    *z0 = P ? kmin : 0;
+    *z1 = P ? std::min(g->nz, kmax + 2) : 0;
+    return P;
+}
 
 size_t psi_elems(const fdtd_grid *g, int)
 {
@@ -179,6 +215,12 @@ Plan make_plan(const fdtd_grid *g, int capacity)
     p.work = take(8 * sizeof(int));
     p.slot = take(sizeof(fdtd::DomainSlot));
     p.items = take(4 * sizeof(int));
+    int z0, z1;
+    const int P = debye_extent(g, &z0, &z1);
+    const size_t box = (size_t)(z1 - z0) * g->plane;
+    p.J = take(std::max<size_t>(1, 3 * (size_t)P * box) * sizeof(float));
+    p.dcls = take(std::max<size_t>(1, box));
+    p.dtable = take(fdtd::kMaxClasses * fdtd::kDebyeRec * sizeof(float));
     p.total = off;
     return p;
 }
@@ -269,6 +311,56 @@ struct Coefs {
         *cb = g->dt / (e * g->dx) / (1.0 + a);
         return (1.0 - a) / (1.0 + a);
     }
+    // dispersive edge (ADE form): with eps, sigma and every deps scaled by
+    // the wire factor f, D = 2 eps + sum beta_p + sigma dt,
+    // ca = (2 eps + sum beta_p - sigma dt) / D, cb = 2 dt / (D dx),
+    // cj_p = -dt (1 + k_p) / D, k_p = (2 tau_p - dt) / (2 tau_p + dt),
+    // be_p = beta_p / dt, beta_p = 2 eps0 deps_p dt / (2 tau_p + dt)
+    double e_coef_debye(double eps_r, double sigma, double f, const double *deps, const double *tau, double *cb,
+                        double *cj, double *kk, double *be) const
+    {
+        const double dt = g->dt;
+        const double e = kEps0 * eps_r * f, s = sigma * f;
+        double beta[fdtd::kMaxPoles], sb = 0.0;
+        for (int p = 0; p < fdtd::kMaxPoles; ++p) {
+            beta[p] = 2.0 * kEps0 * deps[p] * f * dt / (2.0 * tau[p] + dt);
+            kk[p] = deps[p] > 0 ? (2.0 * tau[p] - dt) / (2.0 * tau[p] + dt) : 0.0;
+            sb += beta[p];
+        }
+        const double D = 2.0 * e + sb + s * dt;
+        *cb = 2.0 * dt / (D * g->dx);
+        for (int p = 0; p < fdtd::kMaxPoles; ++p) {
+            cj[p] = deps[p] > 0 ? -dt * (1.0 + kk[p]) / D : 0.0;
+            be[p] = deps[p] > 0 ? beta[p] / dt : 0.0;
+        }
+        return (2.0 * e + sb - s * dt) / D;
+    }
+    // Debye poles of E component c of cell (i,j,k): each pole's deps is the
+    // mean over the four cells the edge averages (zero where a cell lacks
+    // the pole), its tau the deps-weighted mean over those that have it
+    bool e_poles(int c, int i, int j, int k, double *deps, double *tau) const
+    {
+        int cell[4][3];
+        for (int t = 0; t < 4; ++t) {
+            const int a = t & 1, b = t >> 1;
+            if (c == 0) { cell[t][0] = i; cell[t][1] = j - 1 + a; cell[t][2] = k - 1 + b; }
+            else if (c == 1) { cell[t][0] = i - 1 + a; cell[t][1] = j; cell[t][2] = k - 1 + b; }
+            else { cell[t][0] = i - 1 + a; cell[t][1] = j - 1 + b; cell[t][2] = k; }
+        }
+        bool any = false;
+        for (int p = 0; p < fdtd::kMaxPoles; ++p) {
+            double sd = 0.0, st = 0.0;
+            for (int t = 0; t < 4; ++t) {
+                const int m = g->mat[((size_t)cell[t][2] * g->ny + cell[t][1]) * g->nx + cell[t][0]];
+                sd += g->poles[m][p];
+                st += g->poles[m][p] * g->poles[m][fdtd::kMaxPoles + p];
+            }
+            deps[p] = 0.25 * sd;
+            tau[p] = sd > 0 ? st / sd : 1.0;
+            any |= deps[p] > 0;
+        }
+        return any;
+    }
     double h_coef(double mu_r, double f) const { return g->dt / (kMu0 * mu_r / f * g->dx); }
     const fdtd_material &M(int i, int j, int k) const
     {
@@ -301,9 +393,14 @@ struct Coefs {
         q[c] -= 1;
         return 0.5 * (m1 + M(q[0], q[1], q[2]).mu_r);
     }
-    // coefficient of E component c at cell q: returns false for PEC
-    bool e_of(int c, const int q[3], long long cell, double *ca, double *cb) const
+    // coefficient of E component c at cell q: returns false for PEC.
+    // debye (optional, 3 * kMaxPoles doubles {cj, k, be} per pole) is filled
+    // for a dispersive edge and zeroed otherwise; *disp tells which
+    bool e_of(int c, const int q[3], long long cell, double *ca, double *cb, double *debye = nullptr,
+              bool *disp = nullptr) const
     {
+        if (debye) for (int t = 0; t < 3 * fdtd::kMaxPoles; ++t) debye[t] = 0.0;
+        if (disp) *disp = false;
         if (!e_updated(g, c, q)) { *ca = 0; *cb = 0; return false; }
         double f = 1.0;
         if (w && w->touched[cell]) {
@@ -313,6 +410,19 @@ struct Coefs {
         }
         double eps, sig;
         e_mat(c, q[0], q[1], q[2], &eps, &sig);
+        double deps[fdtd::kMaxPoles], tau[fdtd::kMaxPoles];
+        if (g->npoles && e_poles(c, q[0], q[1], q[2], deps, tau)) {
+            double cj[fdtd::kMaxPoles], kk[fdtd::kMaxPoles], be[fdtd::kMaxPoles];
+            *ca = e_coef_debye(eps, sig, f, deps, tau, cb, cj, kk, be);
+            if (debye)
+                for (int p = 0; p < fdtd::kMaxPoles; ++p) {
+                    debye[3 * p] = cj[p];
+                    debye[3 * p + 1] = kk[p];
+                    debye[3 * p + 2] = be[p];
+                }
+            if (disp) *disp = true;
+            return true;
+        }
         *ca = e_coef(eps, sig, f, cb);
         return true;
     }
@@ -326,23 +436,47 @@ struct Coefs {
         }
         return h_coef(h_mat(c, q[0], q[1], q[2]), f);
     }
-    void cell(int i, int j, int k, float out[fdtd::kNumCoef]) const
+    // the cell's coefficient tuple and its Debye record (all zero when no
+    // owned E component is dispersive); returns whether the record is used
+    bool cell(int i, int j, int k, float out[fdtd::kNumCoef], float rec[fdtd::kDebyeRec]) const
     {
         const int q[3] = {i, j, k};
         const long long c = cell_of(g, q);
+        bool any = false;
         for (int comp = 0; comp < 3; ++comp) {
-            double ca, cb;
-            e_of(comp, q, c, &ca, &cb);
+            double ca, cb, d[3 * fdtd::kMaxPoles];
+            bool disp = false;
+            e_of(comp, q, c, &ca, &cb, d, &disp);
             out[comp] = (float)ca;
             out[3 + comp] = (float)cb;
             out[6 + comp] = (float)h_of(comp, q, c);
+            for (int t = 0; t < 3 * fdtd::kMaxPoles; ++t) rec[comp * 3 * fdtd::kMaxPoles + t] = (float)d[t];
+            any |= disp;
         }
+        return any;
     }
 };
 
 int build_classes(fdtd_grid *g, std::vector<uint8_t> &cls, std::vector<float> &table,
-                  std::vector<double> &src_cb)
+                  std::vector<double> &src_cb, std::vector<uint8_t> &dcls, std::vector<float> &dtable,
+                  std::vector<std::array<double, 3 * fdtd::kMaxPoles>> &src_debye)
 {
+    g->npoles = debye_extent(g, &g->dz0, &g->dz1);
+    using Rec = std::array<uint32_t, fdtd::kDebyeRec>;
+    std::map<Rec, int> dids;
+    dtable.assign(fdtd::kDebyeRec, 0.f);          // record 0: no dispersive component
+    dids.emplace(Rec{}, 0);
+    auto did_of = [&](const float r[fdtd::kDebyeRec]) -> int {
+        Rec t;
+        std::memcpy(t.data(), r, sizeof t);
+        auto it = dids.find(t);
+        if (it != dids.end()) return it->second;
+        const int id = (int)dids.size();
+        dids.emplace(t, id);
+        dtable.insert(dtable.end(), r, r + fdtd::kDebyeRec);
+        return id;
+    };
+    dcls.assign((size_t)g->plane * g->nz, 0);
     WireMods w = wire_mods(g);
     Coefs C{g, &w};
     std::map<Tuple, int> ids;
@@ -358,7 +492,7 @@ int build_classes(fdtd_grid *g, std::vector<uint8_t> &cls, std::vector<float> &t
         return id;
     };
     // class of a cell inside a uniform block of one material, per material
-    std::vector<int> uniform_id(g->table.size(), -1);
+    std::vector<int> uniform_id(g->table.size(), -1), uniform_did(g->table.size(), 0);
     cls.assign((size_t)g->plane * g->nz, 0);
     const int nx = g->nx, ny = g->ny, nz = g->nz;
     for (int k = 0; k < nz; ++k)
@@ -374,25 +508,34 @@ int build_classes(fdtd_grid *g, std::vector<uint8_t> &cls, std::vector<float> &t
                           g->mat[c - sx - sy] == m0 && g->mat[c - sx - sz] == m0 &&
                           g->mat[c - sy - sz] == m0;
                 }
-                int id;
+                int id, did = 0;
                 if (uni && uniform_id[m0] >= 0) {
                     id = uniform_id[m0];
+                    did = uniform_did[m0];
                 } else {
-                    float v[fdtd::kNumCoef];
-                    C.cell(i, j, k, v);
+                    float v[fdtd::kNumCoef], r[fdtd::kDebyeRec];
+                    if (C.cell(i, j, k, v, r)) did = did_of(r);
                     id = id_of(v);
-                    if (uni) uniform_id[m0] = id;
+                    if (uni) { uniform_id[m0] = id; uniform_did[m0] = did; }
                 }
                 if (id >= fdtd::kMaxClasses)
                     return fail(g, FDTD_ECLASSES, "more than 256 distinct coefficient classes");
+                if (did >= fdtd::kMaxClasses)
+                    return fail(g, FDTD_ECLASSES, "more than 255 distinct dispersive-media records");
                 cls[(size_t)k * g->plane + (size_t)j * g->pitch + i] = (uint8_t)id;
+                dcls[(size_t)k * g->plane + (size_t)j * g->pitch + i] = (uint8_t)did;
             }
     g->n_classes = (int)ids.size();
+    g->n_drec = (int)dids.size();
     src_cb.clear();
+    src_debye.clear();
     for (const Source &s : g->srcs) {
         double ca, cb;
-        C.e_of(s.axis, s.p, cell_of(g, s.p), &ca, &cb);
+        std::array<double, 3 * fdtd::kMaxPoles> d{};
+        bool disp = false;
+        C.e_of(s.axis, s.p, cell_of(g, s.p), &ca, &cb, d.data(), &disp);
         src_cb.push_back(cb);
+        src_debye.push_back(d);
     }
     return FDTD_OK;
 }
@@ -488,7 +631,27 @@ fdtd::EdgeArgs edge_args(const fdtd_grid *g, int parity)
     e.probe_out = g->probe_out;
     e.capacity = g->capacity;
     e.step = g->step_d;
+    e.J = g->npoles ? g->J : nullptr;
+    e.jstride = (long long)(g->dz1 - g->dz0) * g->plane;
+    e.npoles = g->npoles;
     return e;
+}
+
+fdtd::DebyeArgs debye_args(const fdtd_grid *g, int parity)
+{
+    fdtd::DebyeArgs a{};
+    for (int c = 0; c < 3; ++c) {
+        a.Ein[c] = g->F[parity][c];
+        a.Eout[c] = g->F[1 - parity][c];
+    }
+    a.J = g->J;
+    a.jstride = (long long)(g->dz1 - g->dz0) * g->plane;
+    a.npoles = g->npoles;
+    a.dcls = g->dcls_d;
+    a.table = g->dtable_d;
+    a.n_rec = g->n_drec;
+    a.off = (long long)g->dz0 * g->plane;
+    return a;
 }
 
 fdtd::SingleArgs single_args(const fdtd_grid *g, int parity, int l)
@@ -532,6 +695,7 @@ cudaError_t enqueue_step(fdtd_grid *g, int parity, cudaStream_t s)
     } else {
         for (int l = 0; l < g->n_launch && e == cudaSuccess; ++l) e = launch(l)(s);
     }
+    if (e == cudaSuccess && g->npoles) e = fdtd::launch_debye(debye_args(g, parity), s);
     if (e != cudaSuccess) return e;
     if (!g->srcs.empty() || !g->probes.empty()) e = fdtd::launch_edges(edge_args(g, parity), s);
     return e;
@@ -696,6 +860,7 @@ int step_with_scratch(fdtd_grid *g, int n, int *scratch, int scratch_ints)
         for (int l = 0; l < g->n_launch && e == cudaSuccess; ++l)
             e = launch_step(single_args(g, g->parity, l), grid_launch(g, g->parity, l, scratch + 2 * l, g->noalloc_err),
                             g->lc[l].grid, g->stream);
+        if (e == cudaSuccess && g->npoles) e = launch_debye(debye_args(g, g->parity), g->stream);
         if (e == cudaSuccess && (!g->srcs.empty() || !g->probes.empty()))
             e = launch_edges(edge_args(g, g->parity), g->stream);
         if (e != cudaSuccess) return cuda_fail(g, e, "step launch");
@@ -753,6 +918,23 @@ int fdtd_set_materials(fdtd_grid *g, const uint8_t *cell_material, const fdtd_ma
         if (cell_material[c] >= n_materials) return fail(g, FDTD_EINVAL, "material index out of range");
     std::memcpy(g->mat.data(), cell_material, nc);
     g->table.assign(table, table + n_materials);
+    return FDTD_OK;
+}
+
+int fdtd_set_debye(fdtd_grid *g, int material, int n_poles, const double *delta_eps, const double *tau)
+{
+    if (int rc = check_open(g, false)) return rc;
+    if (material < 0 || material > 255 || n_poles < 0 || n_poles > fdtd::kMaxPoles ||
+        (n_poles > 0 && (!delta_eps || !tau)))
+        return fail(g, FDTD_EINVAL, "bad Debye arguments");
+    for (int p = 0; p < n_poles; ++p)
+        if (!(delta_eps[p] >= 0) || !(tau[p] > 0))
+            return fail(g, FDTD_EINVAL, "Debye pole " + std::to_string(p) + " out of range");
+    auto &P = g->poles[material];
+    for (int p = 0; p < fdtd::kMaxPoles; ++p) {
+        P[p] = p < n_poles ? delta_eps[p] : 0.0;
+        P[fdtd::kMaxPoles + p] = p < n_poles ? tau[p] : 1.0;
+    }
     return FDTD_OK;
 }
 
@@ -841,10 +1023,11 @@ int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_by
 {
     if (int rc = check_open(g, false)) return rc;
     if (probe_capacity < 0) return fail(g, FDTD_EINVAL, "negative probe capacity");
-    std::vector<uint8_t> cls;
-    std::vector<float> table;
+    std::vector<uint8_t> cls, dcls;
+    std::vector<float> table, dtable;
     std::vector<double> src_cb;
-    if (int rc = build_classes(g, cls, table, src_cb)) return rc;
+    std::vector<std::array<double, 3 * fdtd::kMaxPoles>> src_debye;
+    if (int rc = build_classes(g, cls, table, src_cb, dcls, dtable, src_debye)) return rc;
 
     const Plan p = make_plan(g, probe_capacity);
     if (arena) {
@@ -879,6 +1062,9 @@ int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_by
     g->err_d = g->work_d + 4;
     g->slot_d = (fdtd::DomainSlot *)(base + p.slot);
     g->item_start_d = (int *)(base + p.items);
+    g->J = (float *)(base + p.J);
+    g->dcls_d = (uint8_t *)(base + p.dcls);
+    g->dtable_d = (float *)(base + p.dtable);
     g->capacity = probe_capacity;
 
 
@@ -887,6 +1073,12 @@ int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_by
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->cls, cls.data(), cls.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g->table_d, table.data(), table.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && g->npoles) {
+        const size_t box = (size_t)(g->dz1 - g->dz0) * g->plane;
+        e = cudaMemcpyAsync(g->dcls_d, dcls.data() + (size_t)g->dz0 * g->plane, box, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(g->dtable_d, dtable.data(), dtable.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+    }
     const int n[3] = {g->nx, g->ny, g->nz};
     for (int u = 0; u < 3 && e == cudaSuccess; ++u) {
         std::vector<float> pr = cpml_profile(g, n[u]);
@@ -903,6 +1095,13 @@ int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_by
         d.coef = (float)(-src_cb[q] / g->dx);
         d.n_samples = (int)src.cur.size();
         d.sample_off = (long long)samples.size();
+        d.jidx = -1;
+        bool disp = false;
+        for (int p2 = 0; p2 < fdtd::kMaxPoles; ++p2) {
+            d.be[p2] = (float)src_debye[q][3 * p2 + 2];
+            disp |= d.be[p2] != 0.f;
+        }
+        if (disp) d.jidx = d.idx - (long long)g->dz0 * g->plane;
         samples.insert(samples.end(), src.cur.begin(), src.cur.end());
         sd.push_back(d);
     }
@@ -1049,18 +1248,20 @@ int fdtd_num_classes(const fdtd_grid *g) { return g ? g->n_classes : -1; }
 // ---- checkpoint / resume ----------------------------------------------------
 namespace {
 constexpr uint32_t kStateMagic = 0x53544446u;     // "FDTS"
-constexpr uint32_t kStateVersion = 1;
+constexpr uint32_t kStateVersion = 2;
 struct StateHeader {
     uint32_t magic, version;
-    int32_t nx, ny, nz, d, n_probes, capacity, n_psi, pad;
+    int32_t nx, ny, nz, d, n_probes, capacity, n_psi, npoles, dz0, dz1;
     int64_t step;
 };
+
+size_t debye_elems(const fdtd_grid *g) { return 3 * (size_t)g->npoles * (size_t)(g->dz1 - g->dz0) * g->plane; }
 
 size_t state_bytes(const fdtd_grid *g, int n_psi)
 {
     const size_t cells = (size_t)g->nx * g->ny * g->nz;
     return sizeof(StateHeader) + (6 + (size_t)n_psi) * cells * sizeof(float) +
-           g->probes.size() * (size_t)g->capacity * sizeof(float);
+           g->probes.size() * (size_t)g->capacity * sizeof(float) + debye_elems(g) * sizeof(float);
 }
 
 // one cell-owned array between host (dense) and device (row pitch)
@@ -1089,7 +1290,7 @@ int fdtd_save_state(fdtd_grid *g, void *host_buf, size_t *bytes)
     }
     if (int rc = fdtd_synchronize(g)) return rc;
     StateHeader h{kStateMagic, kStateVersion, g->nx, g->ny, g->nz, g->d, (int32_t)g->probes.size(), g->capacity,
-                  n_psi, 0, (int64_t)g->step};
+                  n_psi, g->npoles, g->dz0, g->dz1, (int64_t)g->step};
     char *p = static_cast<char *>(host_buf);
     std::memcpy(p, &h, sizeof h);
     p += sizeof h;
@@ -1099,6 +1300,8 @@ int fdtd_save_state(fdtd_grid *g, void *host_buf, size_t *bytes)
     for (int q = 0; q < n_psi && e == cudaSuccess; ++q, p += arr) e = copy_array(g, g->psi[g->parity][q], p, true);
     const size_t pbytes = g->probes.size() * (size_t)g->capacity * sizeof(float);
     if (e == cudaSuccess && pbytes) e = cudaMemcpy(p, g->probe_out, pbytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && debye_elems(g))
+        e = cudaMemcpy(p + pbytes, g->J, debye_elems(g) * sizeof(float), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(g, e, "state copy");
     *bytes = need;
     return FDTD_OK;
@@ -1113,7 +1316,8 @@ int fdtd_load_state(fdtd_grid *g, const void *host_buf, size_t bytes)
     const int n_psi = g->d > 0 ? fdtd::PSI_COUNT : 0;
     if (h.magic != kStateMagic || h.version != kStateVersion) return fail(g, FDTD_EINVAL, "not a saved state");
     if (h.nx != g->nx || h.ny != g->ny || h.nz != g->nz || h.d != g->d || h.n_probes != (int)g->probes.size() ||
-        h.capacity != g->capacity || h.n_psi != n_psi || h.step < 0)
+        h.capacity != g->capacity || h.n_psi != n_psi || h.npoles != g->npoles || h.dz0 != g->dz0 ||
+        h.dz1 != g->dz1 || h.step < 0)
         return fail(g, FDTD_EINVAL, "state was saved from a differently shaped grid");
     if (bytes < state_bytes(g, n_psi)) return fail(g, FDTD_EINVAL, "state truncated");
     if (int rc = fdtd_synchronize(g)) return rc;
@@ -1125,6 +1329,8 @@ int fdtd_load_state(fdtd_grid *g, const void *host_buf, size_t bytes)
     for (int a = 0; a < n_psi && e == cudaSuccess; ++a, q += arr) e = copy_array(g, g->psi[g->parity][a], q, false);
     const size_t pbytes = g->probes.size() * (size_t)g->capacity * sizeof(float);
     if (e == cudaSuccess && pbytes) e = cudaMemcpy(g->probe_out, q, pbytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && debye_elems(g))
+        e = cudaMemcpy(g->J, q + pbytes, debye_elems(g) * sizeof(float), cudaMemcpyHostToDevice);
     const long long step = h.step;
     if (e == cudaSuccess) e = cudaMemcpy(g->step_d, &step, sizeof step, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(g, e, "state copy");
@@ -1228,6 +1434,7 @@ int fdtd_batch_create(int n, fdtd_grid *const *grids, void *cuda_stream, fdtd_ba
     for (int q = 0; q < n; ++q) {
         fdtd_grid *g = grids[q];
         if (!g || !g->finalized) { delete b; return FDTD_ESTATE; }
+        if (g->npoles) { delete b; return FDTD_EINVAL; }      // dispersive media run on their own
         if (g->parity != grids[0]->parity || g->step != grids[0]->step) { delete b; return FDTD_ESTATE; }
         b->grids.push_back(g);
     }

@@ -81,6 +81,17 @@ class Grid:
         check(self._lib, self._h, self._lib.fdtd_set_materials(
             self._h, cm.ctypes.data_as(ctypes.c_void_p), mats, len(table)), "set_materials")
 
+    def set_debye(self, material, delta_eps, tau):
+        """Debye poles (relative delta eps, tau in s; at most 4) of one
+        material; its eps_r and sigma are eps_inf and the static sigma"""
+        d = np.ascontiguousarray(delta_eps, dtype=np.float64)
+        t = np.ascontiguousarray(tau, dtype=np.float64)
+        if d.shape != t.shape:
+            raise ValueError("delta_eps and tau differ in length")
+        check(self._lib, self._h, self._lib.fdtd_set_debye(self._h, int(material), len(d),
+                                                           d.ctypes.data_as(ctypes.c_void_p),
+                                                           t.ctypes.data_as(ctypes.c_void_p)), "set_debye")
+
     def add_wire(self, p0, p1, radius):
         wid = ctypes.c_int()
         check(self._lib, self._h, self._lib.fdtd_add_wire(self._h, *map(int, p0), *map(int, p1),
@@ -239,6 +250,8 @@ def from_scenario(sc, stream=None, probe_capacity=None, torch_arena=True, block=
     if block:
         g.set_block(block)
     g.set_materials(sc.cell_material, sc.materials)
+    for mat, (deps, tau) in (getattr(sc, "debye", None) or {}).items():
+        g.set_debye(mat, deps, tau)
     for p0, p1, r in sc.wires:
         g.add_wire(p0, p1, r)
     for node, axis, cur in sc.sources:

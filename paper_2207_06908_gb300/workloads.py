@@ -287,6 +287,38 @@ def random_scenario(seed, n=(17, 17, 17), dx=0.1, courant=0.99, cpml=0, n_blocks
     return sc
 
 
+def with_random_debye(sc, seed, materials=(1, 2), max_poles=4):
+    """give some materials of a scenario random Debye poles: deps ~ U[1, 40],
+    tau = dt x U[5, 200] (relaxation times from a few to hundreds of steps)"""
+    rng = np.random.default_rng(seed)
+    dt = time_step(sc.dx, sc.courant)
+    sc.debye = {}
+    for m in materials:
+        if m >= len(sc.materials):
+            continue
+        n_p = int(rng.integers(1, max_poles + 1))
+        sc.debye[m] = ([float(v) for v in rng.uniform(1.0, 40.0, n_p)],
+                       [float(v) for v in dt * rng.uniform(5.0, 200.0, n_p)])
+    return sc
+
+
+# Four-term Debye fit of a measured soil (the paper's table of Debye
+# parameters for its buried-wire ground-potential-rise measurement):
+# eps_inf 16.381, sigma_0 2.684 mS/m, poles (deps, tau).
+PAPER_SOIL = dict(eps_inf=16.381, sigma=2.684e-3,
+                  deps=[92.103, 20.825, 374.768, 10.387], tau=[7.404e-6, 1.062e-6, 2.162e-5, 1.008e-8])
+
+
+def debye_soil(n_steps=4000, n=256):
+    """The 256^3 thin-wire workload (config2 layout) over a dispersive soil:
+    the lower half is the four-pole Debye soil above, the upper half air."""
+    sc = config2(n_steps=n_steps, n=n)
+    sc.name = f"debye_soil_{n}"
+    sc.materials = [sc.materials[0], (PAPER_SOIL["eps_inf"], PAPER_SOIL["sigma"], 1.0)]
+    sc.debye = {1: (list(PAPER_SOIL["deps"]), list(PAPER_SOIL["tau"]))}
+    return sc
+
+
 # ---- grounding-electrode domains (the batched and surrogate workloads) -----
 GROUND_DX = 0.25          # m; fixed so every domain spans the same time window
 GROUND_CPML = 8
