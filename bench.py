@@ -42,7 +42,7 @@ def args_parse():
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="single", choices=["single", "config3", "batch", "surrogate"],
+    ap.add_argument("--workload", default="single", choices=["single", "config3", "debye", "batch", "surrogate"],
                     help="single: the 256^3 grid (headline); config3: the 512x512x384 buried-mesh grid; "
                          "batch: 256 grounding domains in one batch; surrogate: the learned surrogate vs FDTD")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -58,12 +58,17 @@ def workload(n_steps, n=256, name="single"):
     from paper_2207_06908_gb300 import workloads
     if name == "config3":
         return workloads.config3(n_steps=n_steps)
+    if name == "debye":
+        return workloads.debye_soil(n_steps=n_steps, n=n)
     return workloads.config2(n_steps=n_steps, n=n)
 
 
 def workload_config(sc, steps):
     gb = bytes_per_step(sc) / 1e9
-    if sc.n == (512, 512, 384):
+    if getattr(sc, "debye", None):
+        desc = (f"{sc.n[0]}^3 Yee grid dx=0.5m, 10-cell CPML, air over a four-pole Debye soil (eps_inf 16.381, "
+                "sigma 2.684 mS/m, the paper's measured-soil fit), 30 m thin wire r=5mm, 1.2/50us 10kA source, 6 probes")
+    elif sc.n == (512, 512, 384):
         desc = ("512x512x384 Yee grid dx=0.25m, 12-cell CPML, two-layer soil, buried 8x8 thin-wire mesh "
                 "(r=6mm) with down-conductor, current and voltage leads, 1 kA 0.5us ramp source")
     else:
@@ -73,14 +78,41 @@ def workload_config(sc, steps):
             "l2": f"inputs larger than L2 (about {gb:.2f} GB of fields, classes and CPML state per step)"}
 
 
+def debye_bytes(sc):
+    """algorithmic DRAM bytes of the dispersive-media kernel per step: a
+    record byte per cell of the planes holding dispersive edges, and per
+    dispersive E edge E^n read, E^{n+1} read and written, and each pole's
+    current read and written (12 + 8 P bytes)"""
+    poles = getattr(sc, "debye", None) or {}
+    if not poles:
+        return 0
+    import numpy as np
+    P = max(len(d) for d, _ in poles.values())
+    nx, ny, nz = sc.n
+    has = np.zeros(256, bool)
+    for m, (d, _) in poles.items():
+        has[m] = any(v > 0 for v in d)
+    cp = np.pad(has[sc.cell_material], ((1, 0), (1, 0), (1, 0)))     # [k+1, j+1, i+1]; index 0 = outside
+    # E edges owned by cell (i,j,k) average cells: Ex (i, j-1|j, k-1|k), Ey (i-1|i, j, k-1|k), Ez (i-1|i, j-1|j, k)
+    c = cp[1:, 1:, 1:]
+    ex = c | cp[1:, :-1, 1:] | cp[:-1, 1:, 1:] | cp[:-1, :-1, 1:]
+    ey = c | cp[1:, 1:, :-1] | cp[:-1, 1:, 1:] | cp[:-1, 1:, :-1]
+    ez = c | cp[1:, 1:, :-1] | cp[1:, :-1, 1:] | cp[1:, :-1, :-1]
+    ks = np.nonzero(c.any(axis=(1, 2)))[0]
+    box_planes = min(nz, int(ks.max()) + 2) - int(ks.min())
+    pitch = (nx + 15) // 16 * 16
+    n_edges = int(ex[1:, 1:, :].sum() + ey[1:, :, 1:].sum() + ez[:, 1:, 1:].sum())   # interior edges
+    return box_planes * pitch * ny + n_edges * (12 + 8 * P)
+
+
 def bytes_per_step(sc):
-    """algorithmic DRAM bytes of one fused step: 6 fields read + 6 written
-    (FP32) and the class byte per cell, plus 4 CPML psi arrays read and
-    written per slab cell and axis"""
+    """algorithmic DRAM bytes of one step: 6 fields read + 6 written (FP32)
+    and the class byte per cell, plus 4 CPML psi arrays read and written per
+    slab cell and axis, plus the dispersive-media kernel's bytes"""
     nx, ny, nz = sc.n
     d = sc.cpml
     slab = 2 * d * (ny * nz + nx * nz + nx * ny) if d else 0
-    return 49 * nx * ny * nz + 32 * slab
+    return 49 * nx * ny * nz + 32 * slab + debye_bytes(sc)
 
 
 def peaks():
@@ -103,7 +135,7 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(cells):
+def recorded_traffic(cells, scenario):
     """DRAM bytes per launch of the step kernel from the committed ncu
     summary, scaled to this grid; None when the kernel changed since."""
     try:
@@ -113,7 +145,7 @@ def recorded_traffic(cells):
         return None
     if t.get("kernel_sha") != kernel_hash():
         return None
-    if t.get("cells") != cells:
+    if t.get("cells") != cells or t.get("scenario") != scenario:
         return None
     return t["dram_bytes_per_step"]
 
@@ -187,7 +219,7 @@ def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    sc = workload(a.steps + a.warmup, a.n, a.workload if a.workload in ("single", "config3") else "single")
+    sc = workload(a.steps + a.warmup, a.n, a.workload if a.workload in ("single", "config3", "debye") else "single")
     from oracle import oracle as O
     o = O.OracleGrid.from_scenario(sc, parity=False)
     w = 2
@@ -466,7 +498,7 @@ def main():
     bps = bytes_per_step(sc)
     peak, peak_kind = peaks()
     achieved = bps / (ms / K / 1e3) / 1e9
-    traffic = recorded_traffic(cells)
+    traffic = recorded_traffic(cells, sc.name)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": peak_kind,
                 "kernel": "step_kernel (per-step time incl. the source/probe kernel)",
@@ -509,7 +541,7 @@ def main():
                 "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic", "config": workload_config(sc, K),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": 3 * K, "finite": finite}
+                "gpu_launches": (4 if getattr(sc, "debye", None) else 3) * K, "finite": finite}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
