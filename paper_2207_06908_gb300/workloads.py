@@ -319,6 +319,51 @@ def debye_soil(n_steps=4000, n=256):
     return sc
 
 
+# Four-term Debye fits of three soil layers (the paper's table of Debye
+# parameters computed for its apparent-resistivity example): per layer
+# (eps_inf, sigma_0 S/m, deps[4], tau[4] s), top to bottom.
+PAPER_LAYERS = [
+    (15.767, 5.0e-3, [839.441, 143.901, 66.971, 31.515], [3.096e-5, 4.068e-6, 7.217e-7, 9.141e-8]),
+    (13.488, 2.5e-3, [593.525, 101.748, 47.348, 22.273], [3.096e-5, 4.066e-6, 7.212e-7, 9.132e-8]),
+    (11.884, 1.25e-3, [419.744, 71.960, 33.494, 15.757], [3.097e-5, 4.069e-6, 7.218e-7, 9.140e-8]),
+]
+
+
+def three_layer_array(n_steps=400, rise=0.37e-6):
+    """The electrode-array example of the paper's apparent-resistivity
+    section: a 5 x 5 x 4 m domain at dx = 0.05 m (100 x 100 x 80 cells),
+    10-cell CPML, three 1 m Debye soil layers (PAPER_LAYERS, top layer
+    against the surface at 3 m) under air; four vertical rods of radius 8 mm
+    from 2.95 m to 3.15 m at (1, 1), (2, 1), (4, 3) and (4, 4) m; a current
+    lead (r = 3 mm) from the first rod's top towards the second with a
+    one-cell source gap at x = 1.45 m, and a voltage lead from the third rod
+    towards the fourth with a one-cell probe gap at y = 3.45 m.  The source
+    is a 1 A linear ramp of the given rise time (the paper drives a Heidler
+    pulse).  Probes: voltage across the probe gap, current in the source
+    gap."""
+    dx = 0.05
+    n = (100, 100, 80)
+    ks = 60                                       # surface node (3 m)
+    cm = paint_blocks(n, [((0, 0, 0), (100, 100, 20), 3), ((0, 0, 20), (100, 100, 40), 2),
+                          ((0, 0, 40), (100, 100, ks), 1)])
+    mats = [(1.0, 0.0, 1.0)] + [(e, s, 1.0) for e, s, _, _ in PAPER_LAYERS]
+    debye = {m + 1: (list(d), list(t)) for m, (_, _, d, t) in enumerate(PAPER_LAYERS)}
+    kb, kt = ks - 1, ks + 3                       # rods: 2.95 m .. 3.15 m
+    rod = 0.008
+    lead = 0.003
+    wires = [((20, 20, kb), (20, 20, kt), rod), ((40, 20, kb), (40, 20, kt), rod),
+             ((80, 60, kb), (80, 60, kt), rod), ((80, 80, kb), (80, 80, kt), rod),
+             ((20, 20, kt), (29, 20, kt), lead), ((30, 20, kt), (40, 20, kt), lead),
+             ((80, 60, kt), (80, 69, kt), lead), ((80, 70, kt), (80, 80, kt), lead)]
+    cur = ramp(sample_times(n_steps, dx, 0.99), 1.0, rise)
+    sc = Scenario("three_layer_array", n, dx, 0.99, 10, cm, mats, wires=wires,
+                  sources=[((29, 20, kt), 0, cur)],
+                  probes=[(PROBE_V, (80, 69, kt), 1, 1), (PROBE_I, (29, 20, kt), 0, 1)],
+                  n_steps=n_steps)
+    sc.debye = debye
+    return sc
+
+
 # ---- grounding-electrode domains (the batched and surrogate workloads) -----
 GROUND_DX = 0.25          # m; fixed so every domain spans the same time window
 GROUND_CPML = 8

@@ -149,3 +149,23 @@ def test_debye_soil_full_size_random_fields_no_source(fdtd):
     sc.sources = []
     sc.fields = W.random_fields(np.random.default_rng(2027), sc.n)
     compare(*run_gpu(fdtd, sc, 24), *run_oracle(sc, 24))
+
+
+def test_three_layer_electrode_array_from_rest(fdtd):
+    """the paper's apparent-resistivity geometry: three four-pole Debye
+    layers, four rods with current and voltage leads, CPML; 400 steps from
+    rest.  Probes within 1e-4; fields within the from-rest bar (twice the
+    FP32-storage error of the same algorithm, floor 1e-5)"""
+    from oracle.oracle import OracleGrid
+    steps = 400
+    sc = W.three_layer_array(n_steps=steps)
+    gf, gp = run_gpu(fdtd, sc, steps)
+    of, op = run_oracle(sc, steps)
+    assert np.abs(op[0]).max() > 0              # the far voltage gap has seen the field
+    y = OracleGrid.from_scenario(sc, parity=True, f32=True)
+    y.step(steps)
+    for c in range(6):
+        bar = max(FIELD_TOL, 2.0 * rel_l2(y.get_field(c), of[c]))
+        assert rel_l2(gf[c], of[c]) <= bar, c
+    for p in range(len(gp)):
+        assert rel_l2(gp[p], op[p]) <= PROBE_TOL, p
