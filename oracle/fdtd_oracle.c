@@ -15,7 +15,16 @@
  *     form of the textbook the paper cites; Eq. (fdtdex) prints the explicit
  *     factor (1 - sigma dt / eps), which is unstable once sigma dt / eps > 2.
  *   - Sec. 2.1 (sources): ideal lumped current source on one Yee edge,
- *     J = I / dx^2 along +axis, I sampled at t_{n+1/2}.
+ *     J = I / dx^2 along +axis, I sampled at t_{n+1/2}; non-ideal current
+ *     source (internal resistance R in parallel: an extra conductance
+ *     1 / (R dx) on the edge, so the edge current is I + E dx / R);
+ *     voltage sources (V = -E dx across the edge): ideal ones force
+ *     E^{n+1} = -V(t_{n+1}) / dx, ones with internal resistance R in series
+ *     act through their Norton equivalent, a current V(t_{n+1/2}) / R in
+ *     parallel with R; lumped resistors and capacitors on one edge (current
+ *     E dx / R and C dx dE/dt: an extra conductivity 1 / (R dx) and
+ *     permittivity C / dx on that edge), the lumped-element forms of the
+ *     textbook the paper cites.
  *   - Sec. 2.2: CPML absorbing layer (CFS recursive convolution, Roden and
  *     Gedney) terminated by PEC.
  *   - Sec. 2.3: thin wire by modified material parameters around a
@@ -81,7 +90,8 @@ enum { EX = 0, EY, EZ, HX, HY, HZ };
 enum { PROBE_V = 0, PROBE_I = 1, PROBE_E = 2, PROBE_H = 3 };
 
 typedef struct { int axis, i, j, k, n; double radius; } orc_wire;
-typedef struct { int axis, i, j, k, n; real *cur; } orc_src;
+typedef struct { int axis, i, j, k, n; real *cur; int hard; } orc_src;   /* hard: ideal voltage source */
+typedef struct { int axis, i, j, k; double e_add, s_add; } orc_lump;      /* extra eps (F/m), sigma (S/m) */
 typedef struct { int kind, axis, i, j, k, n_edges; } orc_probe;
 
 typedef struct orc_grid {
@@ -110,6 +120,8 @@ typedef struct orc_grid {
     /* wires, sources, probes */
     orc_wire *wires; int n_wires;
     orc_src *srcs; int n_srcs;
+    orc_lump *lumps; int n_lumps;
+    real *hard_coef;           /* -1/dx per hard source (0 for current sources) */
     orc_probe *probes; int n_probes;
     real *src_coef;            /* -cb/dx at each source edge */
     /* Debye media: poles per material (deps_p, tau_p; deps 0 = no pole);
@@ -174,6 +186,7 @@ void orc_destroy(orc_grid *g)
     }
     for (int s = 0; s < g->n_srcs; s++) free(g->srcs[s].cur);
     free(g->srcs); free(g->wires); free(g->probes); free(g->src_coef); free(g->probe_out);
+    free(g->lumps); free(g->hard_coef);
     free(g->mat); free(g->m_eps); free(g->m_sig); free(g->m_mu);
     free(g);
 }
@@ -267,21 +280,69 @@ int orc_add_wire(orc_grid *g, int i0, int j0, int k0, int i1, int j1, int k1, do
     return 0;
 }
 
-int orc_add_source(orc_grid *g, int i, int j, int k, int axis, const double *cur, int n)
+static int edge_ok(const orc_grid *g, int i, int j, int k, int axis)
 {
-    if (g->finalized) return -8;
-    if (axis < 0 || axis > 2 || n < 0) return -1;
+    if (axis < 0 || axis > 2) return 0;
     int p[3] = {i, j, k}, nn[3] = {g->nx, g->ny, g->nz};
     for (int u = 0; u < 3; u++) {
-        if (u == axis) { if (p[u] < 0 || p[u] >= nn[u]) return -1; }
-        else if (p[u] < 1 || p[u] > nn[u] - 1) return -1;
+        if (u == axis) { if (p[u] < 0 || p[u] >= nn[u]) return 0; }
+        else if (p[u] < 1 || p[u] > nn[u] - 1) return 0;
     }
+    return 1;
+}
+
+static int add_lump(orc_grid *g, int i, int j, int k, int axis, double e_add, double s_add)
+{
+    g->lumps = (orc_lump *)realloc(g->lumps, (g->n_lumps + 1) * sizeof(orc_lump));
+    orc_lump l = {axis, i, j, k, e_add, s_add};
+    g->lumps[g->n_lumps++] = l;
+    return 0;
+}
+
+static int push_src(orc_grid *g, int i, int j, int k, int axis, const double *v, int n, double scale, int hard)
+{
     g->srcs = (orc_src *)realloc(g->srcs, (g->n_srcs + 1) * sizeof(orc_src));
-    orc_src s = {axis, i, j, k, n, NULL};
+    orc_src s = {axis, i, j, k, n, NULL, hard};
     s.cur = (real *)malloc((n > 0 ? n : 1) * sizeof(real));
-    for (int t = 0; t < n; t++) s.cur[t] = r32(g, cur[t]);
+    for (int t = 0; t < n; t++) s.cur[t] = r32(g, v[t] * scale);
     g->srcs[g->n_srcs++] = s;
     return 0;
+}
+
+/* current source on the edge from node (i,j,k) along +axis; r_internal > 0:
+ * in parallel with that resistance (ohm) */
+int orc_add_source_r(orc_grid *g, int i, int j, int k, int axis, double r_internal, const double *cur, int n)
+{
+    if (g->finalized) return -8;
+    if (n < 0 || !edge_ok(g, i, j, k, axis) || !(r_internal >= 0)) return -1;
+    if (r_internal > 0) add_lump(g, i, j, k, axis, 0.0, 1.0 / (r_internal * g->dx));
+    return push_src(g, i, j, k, axis, cur, n, 1.0, 0);
+}
+
+int orc_add_source(orc_grid *g, int i, int j, int k, int axis, const double *cur, int n)
+{
+    return orc_add_source_r(g, i, j, k, axis, 0.0, cur, n);
+}
+
+/* voltage source across the edge (V = -E dx): r_internal = 0 ideal (volt[n]
+ * is V at t_{n+1}), > 0 in series with that resistance (volt[n] at
+ * t_{n+1/2}, applied as the current volt / r in parallel with r) */
+int orc_add_vsource(orc_grid *g, int i, int j, int k, int axis, double r_internal, const double *volt, int n)
+{
+    if (g->finalized) return -8;
+    if (n < 0 || !edge_ok(g, i, j, k, axis) || !(r_internal >= 0)) return -1;
+    if (r_internal == 0) return push_src(g, i, j, k, axis, volt, n, 1.0, 1);
+    add_lump(g, i, j, k, axis, 0.0, 1.0 / (r_internal * g->dx));
+    return push_src(g, i, j, k, axis, volt, n, 1.0 / r_internal, 0);
+}
+
+/* lumped resistor (ohm, 0 = none) and / or capacitor (F, 0 = none) on the
+ * edge from node (i,j,k) along +axis */
+int orc_add_lumped(orc_grid *g, int i, int j, int k, int axis, double resistance, double capacitance)
+{
+    if (g->finalized) return -8;
+    if (!edge_ok(g, i, j, k, axis) || !(resistance >= 0) || !(capacitance >= 0)) return -1;
+    return add_lump(g, i, j, k, axis, capacitance / g->dx, resistance > 0 ? 1.0 / (resistance * g->dx) : 0.0);
 }
 
 int orc_add_probe(orc_grid *g, int kind, int i, int j, int k, int axis, int n_edges)
@@ -345,12 +406,14 @@ static void edge_poles(const orc_grid *g, int comp, int i, int j, int k, double 
  *   ca = (2 eps + sum beta_p - sigma dt) / D,  cb = 2 dt / (D dx),
  *   cj_p = -dt (1 + k_p) / D,  k_p = (2 tau_p - dt) / (2 tau_p + dt),
  *   be_p = beta_p / dt,  beta_p = 2 eps0 deps_p dt / (2 tau_p + dt),
- * with eps, sigma and every deps scaled by m. */
-static int e_coefs(const orc_grid *g, double eps_r, double sig, double m, const double *deps, const double *tau,
-                   double *ca, double *cb, double cj[ORC_MAXP], double kk[ORC_MAXP], double be[ORC_MAXP])
+ * with eps, sigma and every deps scaled by m, and e_add, s_add (lumped
+ * capacitance / dx, conductance / dx) added after the scaling. */
+static int e_coefs(const orc_grid *g, double eps_r, double sig, double m, double e_add, double s_add,
+                   const double *deps, const double *tau, double *ca, double *cb, double cj[ORC_MAXP],
+                   double kk[ORC_MAXP], double be[ORC_MAXP])
 {
     double dt = g->dt, dx = g->dx;
-    double e = ORC_EPS0 * eps_r * m, s = sig * m;
+    double e = ORC_EPS0 * eps_r * m + e_add, s = sig * m + s_add;
     int disp = 0;
     for (int p = 0; p < ORC_MAXP; p++) {
         cj[p] = kk[p] = be[p] = 0.0;
@@ -567,6 +630,17 @@ int orc_finalize(orc_grid *g, int max_steps)
     /* 3. coefficients of the semi-implicit update (Eq. fdtdex with the loss
      *    time-averaged) and of Eq. fdtdhx; 1/dx folded in */
     double dt = g->dt, dx = g->dx;
+    /* lumped elements and internal resistances: extra eps, sigma per edge */
+    double *le[3] = {NULL, NULL, NULL}, *ls[3] = {NULL, NULL, NULL};
+    if (g->n_lumps) {
+        for (int c = 0; c < 3; c++) { le[c] = (double *)calloc(N, sizeof(double)); ls[c] = (double *)calloc(N, sizeof(double)); }
+        for (int l = 0; l < g->n_lumps; l++) {
+            const orc_lump *lp = &g->lumps[l];
+            size_t q = IDX(g, lp->i, lp->j, lp->k);
+            le[lp->axis][q] += lp->e_add;
+            ls[lp->axis][q] += lp->s_add;
+        }
+    }
     if (g->has_debye) {
         for (int c = 0; c < 3; c++) {
             g->eprev[c] = (real *)calloc(N, sizeof(real));
@@ -589,8 +663,8 @@ int orc_finalize(orc_grid *g, int max_steps)
                     int k = (int)(q / g->sz), j = (int)((q % g->sz) / g->sy), i = (int)(q % g->sy);
                     edge_poles(g, c, i, j, k, deps, tau);
                 }
-                int disp = e_coefs(g, eps[c][q], sig[c][q], fac_e[c][q], g->has_debye ? deps : NULL, tau, &ca, &cb,
-                                   cj, kk, be);
+                int disp = e_coefs(g, eps[c][q], sig[c][q], fac_e[c][q], le[c] ? le[c][q] : 0.0,
+                                   ls[c] ? ls[c][q] : 0.0, g->has_debye ? deps : NULL, tau, &ca, &cb, cj, kk, be);
                 g->ca[c][q] = r32(g, ca);
                 g->cb[c][q] = r32(g, cb);
                 if (disp)
@@ -615,13 +689,17 @@ int orc_finalize(orc_grid *g, int max_steps)
         if (eps[sr->axis][q] > 0 && !pec[sr->axis][q]) {
             double deps[ORC_MAXP], tau[ORC_MAXP], ca, cj[ORC_MAXP], kk[ORC_MAXP], be[ORC_MAXP];
             if (g->has_debye) edge_poles(g, sr->axis, sr->i, sr->j, sr->k, deps, tau);
-            e_coefs(g, eps[sr->axis][q], sig[sr->axis][q], fac_e[sr->axis][q], g->has_debye ? deps : NULL, tau, &ca,
-                    &cbq, cj, kk, be);
+            e_coefs(g, eps[sr->axis][q], sig[sr->axis][q], fac_e[sr->axis][q], le[sr->axis] ? le[sr->axis][q] : 0.0,
+                    ls[sr->axis] ? ls[sr->axis][q] : 0.0, g->has_debye ? deps : NULL, tau, &ca, &cbq, cj, kk, be);
         } else {
             cbq = 0.0;
         }
         g->src_coef[s] = r32(g, -cbq / dx);
     }
+    g->hard_coef = (real *)calloc(g->n_srcs > 0 ? g->n_srcs : 1, sizeof(real));
+    for (int s = 0; s < g->n_srcs; s++)
+        if (g->srcs[s].hard) g->hard_coef[s] = r32(g, -1.0 / dx);
+    for (int c = 0; c < 3; c++) { free(le[c]); free(ls[c]); }
     for (int c = 0; c < 3; c++) { free(eps[c]); free(sig[c]); free(mu[c]); free(pec[c]); free(fac_e[c]); free(fac_h[c]); }
     build_cpml(g);
     g->max_steps = max_steps;
@@ -762,11 +840,19 @@ static void update_e(orc_grid *g)
                 Ez[q] = g->ca[2][q] * Ez[q] + g->cb[2][q] * (tx - ty);
                 if (deb) Ez[q] = debye_add(g, 2, q, Ez[q]);
             }
-    /* ideal current sources: -cb/dx * I(t_{n+1/2}) on the source edge */
+    /* current sources: -cb/dx * I(t_{n+1/2}) on the source edge; then ideal
+     * voltage sources force E^{n+1} = -V(t_{n+1}) / dx */
     for (int s = 0; s < g->n_srcs; s++) {
         orc_src *sr = &g->srcs[s];
+        if (sr->hard) continue;
         real I = (g->step < sr->n) ? sr->cur[g->step] : (real)0;
         g->f[sr->axis][IDX(g, sr->i, sr->j, sr->k)] += g->src_coef[s] * I;
+    }
+    for (int s = 0; s < g->n_srcs; s++) {
+        orc_src *sr = &g->srcs[s];
+        if (!sr->hard) continue;
+        real V = (g->step < sr->n) ? sr->cur[g->step] : (real)0;
+        g->f[sr->axis][IDX(g, sr->i, sr->j, sr->k)] = g->hard_coef[s] * V;
     }
     /* PEC walls: tangential E on the six faces is zero (the update loops
      * never touch those entries; they are cleared in case the caller set

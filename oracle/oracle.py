@@ -87,6 +87,9 @@ def _load(f32: bool = False):
         lib.orc_step.argtypes = [P, I]
         lib.orc_read_probe.argtypes = [P, I, dp]
         lib.orc_set_debye.argtypes = [P, I, I, dp, dp]
+        lib.orc_add_source_r.argtypes = [P, I, I, I, I, D, dp, I]
+        lib.orc_add_vsource.argtypes = [P, I, I, I, I, D, dp, I]
+        lib.orc_add_lumped.argtypes = [P, I, I, I, I, D, D]
         lib.orc_get_debye_current.argtypes = [P, I, I, dp]
         lib.orc_set_debye_current.argtypes = [P, I, I, dp]
         _libs[f32] = lib
@@ -181,10 +184,22 @@ class OracleGrid:
         _check(self._lib.orc_add_wire(self._h, *map(int, p0), *map(int, p1), float(radius)),
                "add_wire")
 
-    def add_source(self, node, axis, current):
+    def add_source(self, node, axis, current, r_internal=0.0):
+        """current source (A at t_{n+1/2}); r_internal > 0: in parallel"""
         cur = np.ascontiguousarray(current, dtype=np.float64)
-        _check(self._lib.orc_add_source(self._h, *map(int, node), int(axis), _dptr(cur),
-                                        len(cur)), "add_source")
+        _check(self._lib.orc_add_source_r(self._h, *map(int, node), int(axis), float(r_internal), _dptr(cur),
+                                          len(cur)), "add_source")
+
+    def add_voltage_source(self, node, axis, voltage, r_internal=0.0):
+        """voltage source V = -E dx across the edge: ideal (r_internal = 0,
+        V at t_{n+1}) or with a series resistance (V at t_{n+1/2})"""
+        v = np.ascontiguousarray(voltage, dtype=np.float64)
+        _check(self._lib.orc_add_vsource(self._h, *map(int, node), int(axis), float(r_internal), _dptr(v),
+                                         len(v)), "add_voltage_source")
+
+    def add_lumped(self, node, axis, resistance=0.0, capacitance=0.0):
+        _check(self._lib.orc_add_lumped(self._h, *map(int, node), int(axis), float(resistance),
+                                        float(capacitance)), "add_lumped")
 
     def add_probe(self, kind, node, axis, n_edges=1):
         _check(self._lib.orc_add_probe(self._h, int(kind), *map(int, node), int(axis),
@@ -230,8 +245,13 @@ class OracleGrid:
             g.set_debye(mat, deps, tau)
         for p0, p1, r in sc.wires:
             g.add_wire(p0, p1, r)
-        for node, axis, cur in sc.sources:
-            g.add_source(node, axis, cur)
+        for src in sc.sources:
+            node, axis, cur = src[:3]
+            g.add_source(node, axis, cur, *(src[3:4]))
+        for node, axis, volt, r in getattr(sc, "vsources", None) or []:
+            g.add_voltage_source(node, axis, volt, r)
+        for node, axis, res, cap in getattr(sc, "lumped", None) or []:
+            g.add_lumped(node, axis, res, cap)
         for kind, node, axis, ne in sc.probes:
             g.add_probe(kind, node, axis, ne)
         g.finalize(sc.n_steps)

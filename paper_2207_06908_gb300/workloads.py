@@ -40,11 +40,13 @@ class Scenario:
     cell_material: np.ndarray     # (nz, ny, nx) uint8
     materials: list               # [(eps_r, sigma, mu_r)]
     wires: list = dataclasses.field(default_factory=list)     # [(p0, p1, radius)]
-    sources: list = dataclasses.field(default_factory=list)   # [(node, axis, current[n])]
+    sources: list = dataclasses.field(default_factory=list)   # [(node, axis, current[n] (, r_internal))]
     probes: list = dataclasses.field(default_factory=list)    # [(kind, node, axis, n_edges)]
     n_steps: int = 0
     fields: list | None = None    # optional initial [Ex,Ey,Ez,Hx,Hy,Hz] (nz,ny,nx) float32
     debye: dict = dataclasses.field(default_factory=dict)     # {material: (deps [P], tau [P] s)}
+    vsources: list = dataclasses.field(default_factory=list)  # [(node, axis, voltage[n], r_internal)]
+    lumped: list = dataclasses.field(default_factory=list)    # [(node, axis, resistance, capacitance)]
 
     @property
     def cells(self) -> int:
@@ -122,6 +124,17 @@ def double_exponential_params(t_front=1.2e-6, t_half=50e-6):
 
 def double_exponential(t, i0, alpha, beta, k):
     return i0 * k * (np.exp(-alpha * t) - np.exp(-beta * t))
+
+
+def heidler(t, i0, tau1, tau2, n):
+    """Heidler lightning-current function (Heidler and Cvetic, the waveform
+    class the paper's lightning examples use):
+    i(t) = (i0 / eta) (t/tau1)^n / (1 + (t/tau1)^n) exp(-t/tau2) for t > 0,
+    eta = exp(-(tau1/tau2) (n tau2/tau1)^(1/n)) the peak correction."""
+    t = np.asarray(t, dtype=np.float64)
+    eta = math.exp(-(tau1 / tau2) * (n * tau2 / tau1) ** (1.0 / n))
+    x = np.where(t > 0, t / tau1, 0.0) ** n
+    return np.where(t > 0, i0 / eta * x / (1.0 + x) * np.exp(-np.maximum(t, 0.0) / tau2), 0.0)
 
 
 def ramp(t, i0, t_rise):
