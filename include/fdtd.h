@@ -122,14 +122,38 @@ int fdtd_set_debye(fdtd_grid *g, int material, int n_poles, const double *delta_
 int fdtd_add_wire(fdtd_grid *g, int i0, int j0, int k0, int i1, int j1, int k1,
                   double radius, int *wire_id);
 
-/* Ideal current source (Sec. 2.1 sources; "source(current, ...)" in the
- * Sec. 4 model files) on the edge from node (i,j,k) along +axis (0,1,2):
- * J = I / dx^2 along +axis, I(t_{n+1/2}) = current[n] for n < n_samples and
- * 0 after.  The transverse node coordinates must lie in 1..n-1.
- * r_internal must be 0 (non-ideal sources are not supported: FDTD_EINVAL).
- * Samples are rounded to FP32.  *source_id (may be NULL) receives the index. */
+/* Current source (Sec. 2.1 sources: ideal and non-ideal current sources;
+ * "source(current, ...)" in the Sec. 4 model files) on the edge from node
+ * (i,j,k) along +axis (0,1,2): J = I / dx^2 along +axis, I(t_{n+1/2}) =
+ * current[n] for n < n_samples and 0 after.  The transverse node
+ * coordinates must lie in 1..n-1.  r_internal (ohm): 0 = ideal; > 0 = the
+ * source's internal resistance in parallel, an extra conductivity
+ * 1 / (r_internal dx) on the edge.  Samples are rounded to FP32.
+ * *source_id (may be NULL) receives the index; voltage sources share the
+ * numbering. */
 int fdtd_add_source(fdtd_grid *g, int i, int j, int k, int axis, double r_internal,
                     const double *current, int n_samples, int *source_id);
+
+/* Voltage source across the edge from node (i,j,k) along +axis (Sec. 2.1:
+ * ideal and non-ideal voltage sources), its voltage V = -E dx (the sign of
+ * a voltage probe on that edge).  r_internal = 0: ideal, E^{n+1} of the edge
+ * is set to -voltage[n] / dx after the step (voltage[n] = V(t_{n+1}));
+ * r_internal > 0: in series with that resistance, applied as its Norton
+ * equivalent, a current voltage[n] / r_internal (at t_{n+1/2}) in parallel
+ * with r_internal.  Two ideal sources on one edge: the later one applies.
+ * Errors as fdtd_add_source. */
+int fdtd_add_voltage_source(fdtd_grid *g, int i, int j, int k, int axis, double r_internal, const double *voltage,
+                            int n_samples, int *source_id);
+
+/* Lumped resistor and / or capacitor on the edge from node (i,j,k) along
+ * +axis (the paper's lumped circuit elements, in the form of the textbook it
+ * cites): edge current E dx / R and C dx dE/dt, i.e. an extra conductivity
+ * 1 / (R dx) and permittivity C / dx on that edge (added after any thin-wire
+ * factor).  resistance (ohm) and capacitance (F) >= 0, 0 = absent, not both
+ * 0; several elements on one edge add in parallel.  FDTD_EINVAL for bad
+ * values or an edge on a wall; FDTD_ESTATE after fdtd_finalize. */
+int fdtd_add_lumped(fdtd_grid *g, int i, int j, int k, int axis, double resistance, double capacitance,
+                    int *element_id);
 
 /* Probe (Sec. 4 model files, "calculate(voltage|current, ...)"), one of
  * FDTD_PROBE_*.  For FDTD_PROBE_V, n_edges >= 1 edges from node (i,j,k)

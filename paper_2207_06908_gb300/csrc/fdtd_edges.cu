@@ -23,6 +23,7 @@ __device__ __forceinline__ void edge_body(const EdgeArgs &a)
     const long long n = n_s;
     for (int q = threadIdx.x; q < a.n_src; q += blockDim.x) {
         const SourceDesc sd = a.src[q];
+        if (sd.hard) continue;
         const float I = n < sd.n_samples ? a.samples[sd.sample_off + n] : 0.f;
         const float add = sd.coef * I;
         atomicAdd(a.E[sd.comp] + sd.idx, add);
@@ -32,6 +33,21 @@ __device__ __forceinline__ void edge_body(const EdgeArgs &a)
             for (int p = 0; p < a.npoles; ++p)
                 if (sd.be[p] != 0.f)
                     atomicAdd(a.J + (long long)(sd.comp * a.npoles + p) * a.jstride + sd.jidx, sd.be[p] * add);
+    }
+    __syncthreads();
+    // ideal voltage sources, after the current sources: E^{n+1} = -V / dx
+    // (and on a dispersive edge the currents take be_p times the change)
+    for (int q = threadIdx.x; q < a.n_src; q += blockDim.x) {
+        const SourceDesc sd = a.src[q];
+        if (!sd.hard) continue;
+        const float V = n < sd.n_samples ? a.samples[sd.sample_off + n] : 0.f;
+        float *e = a.E[sd.comp] + sd.idx;
+        const float old = *e, v = sd.vcoef * V;
+        *e = v;
+        if (sd.jidx >= 0 && a.J)
+            for (int p = 0; p < a.npoles; ++p)
+                if (sd.be[p] != 0.f)
+                    atomicAdd(a.J + (long long)(sd.comp * a.npoles + p) * a.jstride + sd.jidx, sd.be[p] * (v - old));
     }
     __syncthreads();
     if (n < a.capacity) {

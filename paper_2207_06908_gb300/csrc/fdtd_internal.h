@@ -130,6 +130,8 @@ struct SourceDesc {
     long long sample_off;    // offset into the sample table
     long long jidx;          // element index in the Debye current arrays, or -1
     float be[kMaxPoles];     // be of the edge's poles (dispersive edge)
+    int hard;                // ideal voltage source: samples are volts, E is set to vcoef * V
+    float vcoef;             // -1 / dx
 };
 
 struct DebyeArgs {

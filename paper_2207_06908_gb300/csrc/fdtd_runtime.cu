@@ -30,7 +30,8 @@ constexpr double kR0 = 0.23;        // intrinsic radius of a zero-E line, in cel
 constexpr int kGraphSteps = 32;     // steps per captured graph (even)
 
 struct Wire { int axis, p[3], n; double radius; };
-struct Source { int axis, p[3]; std::vector<float> cur; };
+struct Source { int axis, p[3]; std::vector<float> cur; int hard = 0; };   // hard: ideal voltage source
+struct Lump { int axis, p[3]; double e_add, s_add; };                      // extra eps (F/m), sigma (S/m) on an edge
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -87,6 +88,7 @@ struct fdtd_grid {
         std::vector<std::array<double, 2 * fdtd::kMaxPoles>>(256, {0, 0, 0, 0, 1, 1, 1, 1});
     std::vector<Wire> wires;
     std::vector<Source> srcs;
+    std::vector<Lump> lumps;
     std::vector<fdtd::ProbeDesc> probes;
     bool finalized = false;
     int capacity = 0;
@@ -235,6 +237,7 @@ uint64_t key(int comp, long long cell) { return ((uint64_t)comp << 56) | (uint64
 struct WireMods {
     std::unordered_map<uint64_t, double> fe, fh;   // (component, cell) -> factor
     std::unordered_map<uint64_t, char> pec;         // (E component, cell)
+    std::unordered_map<uint64_t, std::pair<double, double>> lump;   // (E component, cell) -> extra eps, sigma
     std::vector<uint8_t> touched;                   // per cell: any entry above
 };
 
@@ -268,6 +271,12 @@ WireMods wire_mods(const fdtd_grid *g)
         if (q[0] >= 0 && q[1] >= 0 && q[2] >= 0 && q[0] < g->nx && q[1] < g->ny && q[2] < g->nz)
             w.touched[cell_of(g, q)] = 1;
     };
+    for (const Lump &l : g->lumps) {
+        auto &v = w.lump[key(l.axis, cell_of(g, l.p))];
+        v.first += l.e_add;
+        v.second += l.s_add;
+        touch(l.p);
+    }
     for (const Wire &wr : g->wires) {
         const double m = std::log(1.0 / kR0) / std::log(g->dx / wr.radius);
         const int a = wr.axis;
@@ -303,10 +312,12 @@ WireMods wire_mods(const fdtd_grid *g)
 struct Coefs {
     const fdtd_grid *g;
     const WireMods *w;
-    double e_coef(double eps_r, double sigma, double f, double *cb) const
+    // e_add, s_add: lumped capacitance / dx and conductance / dx of the edge,
+    // added after the wire factor
+    double e_coef(double eps_r, double sigma, double f, double e_add, double s_add, double *cb) const
     {
-        const double e = kEps0 * eps_r * f;
-        const double s = sigma * f;
+        const double e = kEps0 * eps_r * f + e_add;
+        const double s = sigma * f + s_add;
         const double a = s * g->dt / (2.0 * e);
         *cb = g->dt / (e * g->dx) / (1.0 + a);
         return (1.0 - a) / (1.0 + a);
@@ -316,11 +327,11 @@ struct Coefs {
     // ca = (2 eps + sum beta_p - sigma dt) / D, cb = 2 dt / (D dx),
     // cj_p = -dt (1 + k_p) / D, k_p = (2 tau_p - dt) / (2 tau_p + dt),
     // be_p = beta_p / dt, beta_p = 2 eps0 deps_p dt / (2 tau_p + dt)
-    double e_coef_debye(double eps_r, double sigma, double f, const double *deps, const double *tau, double *cb,
-                        double *cj, double *kk, double *be) const
+    double e_coef_debye(double eps_r, double sigma, double f, double e_add, double s_add, const double *deps,
+                        const double *tau, double *cb, double *cj, double *kk, double *be) const
     {
         const double dt = g->dt;
-        const double e = kEps0 * eps_r * f, s = sigma * f;
+        const double e = kEps0 * eps_r * f + e_add, s = sigma * f + s_add;
         double beta[fdtd::kMaxPoles], sb = 0.0;
         for (int p = 0; p < fdtd::kMaxPoles; ++p) {
             beta[p] = 2.0 * kEps0 * deps[p] * f * dt / (2.0 * tau[p] + dt);
@@ -402,18 +413,20 @@ struct Coefs {
         if (debye) for (int t = 0; t < 3 * fdtd::kMaxPoles; ++t) debye[t] = 0.0;
         if (disp) *disp = false;
         if (!e_updated(g, c, q)) { *ca = 0; *cb = 0; return false; }
-        double f = 1.0;
+        double f = 1.0, e_add = 0.0, s_add = 0.0;
         if (w && w->touched[cell]) {
             if (w->pec.count(key(c, cell))) { *ca = 0; *cb = 0; return false; }
             auto it = w->fe.find(key(c, cell));
             if (it != w->fe.end()) f = it->second;
+            auto il = w->lump.find(key(c, cell));
+            if (il != w->lump.end()) { e_add = il->second.first; s_add = il->second.second; }
         }
         double eps, sig;
         e_mat(c, q[0], q[1], q[2], &eps, &sig);
         double deps[fdtd::kMaxPoles], tau[fdtd::kMaxPoles];
         if (g->npoles && e_poles(c, q[0], q[1], q[2], deps, tau)) {
             double cj[fdtd::kMaxPoles], kk[fdtd::kMaxPoles], be[fdtd::kMaxPoles];
-            *ca = e_coef_debye(eps, sig, f, deps, tau, cb, cj, kk, be);
+            *ca = e_coef_debye(eps, sig, f, e_add, s_add, deps, tau, cb, cj, kk, be);
             if (debye)
                 for (int p = 0; p < fdtd::kMaxPoles; ++p) {
                     debye[3 * p] = cj[p];
@@ -423,7 +436,7 @@ struct Coefs {
             if (disp) *disp = true;
             return true;
         }
-        *ca = e_coef(eps, sig, f, cb);
+        *ca = e_coef(eps, sig, f, e_add, s_add, cb);
         return true;
     }
     double h_of(int c, const int q[3], long long cell) const
@@ -972,15 +985,52 @@ int fdtd_add_source(fdtd_grid *g, int i, int j, int k, int axis, double r_intern
     if (int rc = check_open(g, false)) return rc;
     if (axis < 0 || axis > 2 || n_samples < 0 || (n_samples > 0 && !current))
         return fail(g, FDTD_EINVAL, "bad source arguments");
-    if (r_internal != 0.0) return fail(g, FDTD_EINVAL, "only ideal current sources (r_internal = 0)");
+    if (!(r_internal >= 0)) return fail(g, FDTD_EINVAL, "negative internal resistance");
     Source s;
     s.axis = axis;
     s.p[0] = i; s.p[1] = j; s.p[2] = k;
     if (!e_updated(g, axis, s.p)) return fail(g, FDTD_EINVAL, "source edge on a wall or outside the grid");
     s.cur.resize(n_samples);
     for (int t = 0; t < n_samples; ++t) s.cur[t] = (float)current[t];
+    if (r_internal > 0) g->lumps.push_back(Lump{axis, {i, j, k}, 0.0, 1.0 / (r_internal * g->dx)});
     g->srcs.push_back(std::move(s));
     if (source_id) *source_id = (int)g->srcs.size() - 1;
+    return FDTD_OK;
+}
+
+int fdtd_add_voltage_source(fdtd_grid *g, int i, int j, int k, int axis, double r_internal, const double *voltage,
+                            int n_samples, int *source_id)
+{
+    if (int rc = check_open(g, false)) return rc;
+    if (axis < 0 || axis > 2 || n_samples < 0 || (n_samples > 0 && !voltage) || !(r_internal >= 0))
+        return fail(g, FDTD_EINVAL, "bad voltage source arguments");
+    Source s;
+    s.axis = axis;
+    s.p[0] = i; s.p[1] = j; s.p[2] = k;
+    if (!e_updated(g, axis, s.p)) return fail(g, FDTD_EINVAL, "source edge on a wall or outside the grid");
+    s.cur.resize(n_samples);
+    if (r_internal == 0) {              // ideal: the edge's E is set to -V / dx
+        s.hard = 1;
+        for (int t = 0; t < n_samples; ++t) s.cur[t] = (float)voltage[t];
+    } else {                            // Norton equivalent: V / R in parallel with R
+        for (int t = 0; t < n_samples; ++t) s.cur[t] = (float)(voltage[t] / r_internal);
+        g->lumps.push_back(Lump{axis, {i, j, k}, 0.0, 1.0 / (r_internal * g->dx)});
+    }
+    g->srcs.push_back(std::move(s));
+    if (source_id) *source_id = (int)g->srcs.size() - 1;
+    return FDTD_OK;
+}
+
+int fdtd_add_lumped(fdtd_grid *g, int i, int j, int k, int axis, double resistance, double capacitance,
+                    int *element_id)
+{
+    if (int rc = check_open(g, false)) return rc;
+    if (axis < 0 || axis > 2 || !(resistance >= 0) || !(capacitance >= 0) || (resistance == 0 && capacitance == 0))
+        return fail(g, FDTD_EINVAL, "bad lumped element arguments");
+    const int p[3] = {i, j, k};
+    if (!e_updated(g, axis, p)) return fail(g, FDTD_EINVAL, "lumped element edge on a wall or outside the grid");
+    g->lumps.push_back(Lump{axis, {i, j, k}, capacitance / g->dx, resistance > 0 ? 1.0 / (resistance * g->dx) : 0.0});
+    if (element_id) *element_id = (int)g->lumps.size() - 1;
     return FDTD_OK;
 }
 
@@ -1102,6 +1152,8 @@ int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_by
             disp |= d.be[p2] != 0.f;
         }
         if (disp) d.jidx = d.idx - (long long)g->dz0 * g->plane;
+        d.hard = src.hard;
+        d.vcoef = (float)(-1.0 / g->dx);
         samples.insert(samples.end(), src.cur.begin(), src.cur.end());
         sd.push_back(d);
     }

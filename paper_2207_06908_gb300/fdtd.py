@@ -106,6 +106,22 @@ class Grid:
             len(cur), ctypes.byref(sid)), "add_source")
         return sid.value
 
+    def add_voltage_source(self, node, axis, voltage, r_internal=0.0):
+        """voltage source V = -E dx across the edge: ideal (r_internal = 0,
+        voltage[n] at t_{n+1}) or in series with r_internal (at t_{n+1/2})"""
+        v = np.ascontiguousarray(voltage, dtype=np.float64)
+        sid = ctypes.c_int()
+        check(self._lib, self._h, self._lib.fdtd_add_voltage_source(
+            self._h, *map(int, node), int(axis), float(r_internal), v.ctypes.data_as(ctypes.c_void_p), len(v),
+            ctypes.byref(sid)), "add_voltage_source")
+        return sid.value
+
+    def add_lumped(self, node, axis, resistance=0.0, capacitance=0.0):
+        lid = ctypes.c_int()
+        check(self._lib, self._h, self._lib.fdtd_add_lumped(self._h, *map(int, node), int(axis), float(resistance),
+                                                            float(capacitance), ctypes.byref(lid)), "add_lumped")
+        return lid.value
+
     def add_probe(self, kind, node, axis, n_edges=1):
         pid = ctypes.c_int()
         check(self._lib, self._h, self._lib.fdtd_add_probe(self._h, int(kind), *map(int, node), int(axis),
@@ -254,8 +270,13 @@ def from_scenario(sc, stream=None, probe_capacity=None, torch_arena=True, block=
         g.set_debye(mat, deps, tau)
     for p0, p1, r in sc.wires:
         g.add_wire(p0, p1, r)
-    for node, axis, cur in sc.sources:
-        g.add_source(node, axis, cur)
+    for src in sc.sources:
+        node, axis, cur = src[:3]
+        g.add_source(node, axis, cur, *(src[3:4]))
+    for node, axis, volt, r in getattr(sc, "vsources", None) or []:
+        g.add_voltage_source(node, axis, volt, r)
+    for node, axis, res, cap in getattr(sc, "lumped", None) or []:
+        g.add_lumped(node, axis, res, cap)
     for kind, node, axis, ne in sc.probes:
         g.add_probe(kind, node, axis, ne)
     g.finalize(sc.n_steps if probe_capacity is None else probe_capacity, torch_arena=torch_arena)

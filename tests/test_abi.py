@@ -63,7 +63,12 @@ def test_host_argument_checks():
         assert b"0.23" in lib.fdtd_last_error(h)
         cur = (ctypes.c_double * 4)(1, 2, 3, 4)
         assert lib.fdtd_add_source(h, 3, 3, 3, 2, 0.0, cur, 4, None) == 0
-        assert lib.fdtd_add_source(h, 3, 3, 3, 2, 50.0, cur, 4, None) == -1        # non-ideal
+        assert lib.fdtd_add_source(h, 3, 3, 3, 2, 50.0, cur, 4, None) == 0         # non-ideal (parallel R)
+        assert lib.fdtd_add_source(h, 3, 3, 3, 2, -1.0, cur, 4, None) == -1        # negative resistance
+        assert lib.fdtd_add_voltage_source(h, 3, 3, 3, 2, 0.0, cur, 4, None) == 0  # ideal voltage source
+        assert lib.fdtd_add_lumped(h, 3, 3, 4, 2, 50.0, 0.0, None) == 0
+        assert lib.fdtd_add_lumped(h, 3, 3, 4, 2, 0.0, 0.0, None) == -1            # no element
+        assert lib.fdtd_add_lumped(h, 0, 3, 4, 2, 50.0, 0.0, None) == -1           # wall edge
         assert lib.fdtd_add_source(h, 0, 3, 3, 2, 0.0, cur, 4, None) == -1         # wall edge
         assert lib.fdtd_add_probe(h, 0, 3, 3, 3, 2, 5, None) == 0
         assert lib.fdtd_add_probe(h, 0, 3, 3, 3, 2, 6, None) == -1                 # path leaves grid
