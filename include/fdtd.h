@@ -122,6 +122,19 @@ int fdtd_set_debye(fdtd_grid *g, int material, int n_poles, const double *delta_
 int fdtd_add_wire(fdtd_grid *g, int i0, int j0, int k0, int i1, int j1, int k1,
                   double radius, int *wire_id);
 
+/* Thin wire between two arbitrary nodes (i0,j0,k0) and (i1,j1,k1) as a
+ * staircase of grid-aligned wires (the staircase wire model the paper lists
+ * among its thin-wire techniques, Sec. 2.3): from the first node each unit
+ * step goes along the axis least advanced towards the second node,
+ * |c_u - a_u| / |b_u - a_u| smallest, ties to the lowest axis; each run of
+ * steps along one axis is one fdtd_add_wire() wire of the given radius.
+ * Wires that meet at a node form a junction (the thinner wire's factor
+ * applies where they share a component).  On an error (as fdtd_add_wire)
+ * no wire of the path is kept.  *n_segments (may be NULL) receives the
+ * number of wires added. */
+int fdtd_add_wire_path(fdtd_grid *g, int i0, int j0, int k0, int i1, int j1, int k1, double radius,
+                       int *n_segments);
+
 /* Current source (Sec. 2.1 sources: ideal and non-ideal current sources;
  * "source(current, ...)" in the Sec. 4 model files) on the edge from node
  * (i,j,k) along +axis (0,1,2): J = I / dx^2 along +axis, I(t_{n+1/2}) =

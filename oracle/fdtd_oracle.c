@@ -240,6 +240,48 @@ int orc_set_materials(orc_grid *g, const uint8_t *cell_mat, const double *eps_r,
     return 0;
 }
 
+/* Wire between two arbitrary nodes as a staircase of grid-aligned
+ * segments (the staircase wire model the paper lists among its thin-wire
+ * techniques): from a, each unit step goes along the axis whose progress
+ * towards b, |c_u - a_u| / |b_u - a_u|, is smallest (ties: lowest axis);
+ * runs of steps along one axis form one wire.  Returns the number of
+ * wires added, or a negative status. */
+int orc_add_wire(orc_grid *g, int i0, int j0, int k0, int i1, int j1, int k1, double radius);
+
+int orc_add_wire_path(orc_grid *g, int i0, int j0, int k0, int i1, int j1, int k1, double radius)
+{
+    if (g->finalized) return -8;
+    int a[3] = {i0, j0, k0}, b[3] = {i1, j1, k1}, c[3] = {i0, j0, k0};
+    int d[3], len = 0;
+    for (int u = 0; u < 3; u++) { d[u] = abs(b[u] - a[u]); len += d[u]; }
+    if (len == 0) return -1;
+    int run_axis = -1, run_start[3] = {0, 0, 0}, added = 0;
+    for (int s = 0; s <= len; s++) {
+        int best = -1;
+        if (s < len) {
+            double bp = 2.0;
+            for (int u = 0; u < 3; u++) {
+                if (c[u] == b[u]) continue;
+                double prog = (double)abs(c[u] - a[u]) / d[u];
+                if (prog < bp) { bp = prog; best = u; }
+            }
+        }
+        if (best != run_axis) {
+            if (run_axis >= 0) {            /* close the run from run_start to c */
+                int p0[3] = {run_start[0], run_start[1], run_start[2]}, p1[3] = {c[0], c[1], c[2]};
+                if (p1[run_axis] < p0[run_axis]) { int t = p0[run_axis]; p0[run_axis] = p1[run_axis]; p1[run_axis] = t; }
+                int rc = orc_add_wire(g, p0[0], p0[1], p0[2], p1[0], p1[1], p1[2], radius);
+                if (rc) return rc;
+                added++;
+            }
+            run_axis = best;
+            for (int u = 0; u < 3; u++) run_start[u] = c[u];
+        }
+        if (best >= 0) c[best] += b[best] > a[best] ? 1 : -1;
+    }
+    return added;
+}
+
 /* Debye poles of material `mat`: deps[p] (relative, >= 0) and tau[p] (s,
  * > 0), p < n_poles <= ORC_MAXP; later poles are cleared */
 int orc_set_debye(orc_grid *g, int mat, int n_poles, const double *deps, const double *tau)

@@ -90,6 +90,7 @@ def _load(f32: bool = False):
         lib.orc_add_source_r.argtypes = [P, I, I, I, I, D, dp, I]
         lib.orc_add_vsource.argtypes = [P, I, I, I, I, D, dp, I]
         lib.orc_add_lumped.argtypes = [P, I, I, I, I, D, D]
+        lib.orc_add_wire_path.argtypes = [P, I, I, I, I, I, I, D]
         lib.orc_get_debye_current.argtypes = [P, I, I, dp]
         lib.orc_set_debye_current.argtypes = [P, I, I, dp]
         _libs[f32] = lib
@@ -161,6 +162,14 @@ class OracleGrid:
         _check(self._lib.orc_set_materials(
             self._h, cm.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
             _dptr(e), _dptr(s), _dptr(m), len(e)), "set_materials")
+
+    def add_wire_path(self, p0, p1, radius):
+        """wire between two arbitrary nodes as a staircase of grid-aligned
+        segments; returns the number of segments"""
+        rc = self._lib.orc_add_wire_path(self._h, *map(int, p0), *map(int, p1), float(radius))
+        if rc < 0:
+            raise ValueError(f"oracle add_wire_path failed with status {rc}")
+        return rc
 
     def set_debye(self, material, deps, tau):
         """Debye poles (relative delta eps, tau in s) of one material"""
@@ -245,6 +254,8 @@ class OracleGrid:
             g.set_debye(mat, deps, tau)
         for p0, p1, r in sc.wires:
             g.add_wire(p0, p1, r)
+        for p0, p1, r in getattr(sc, "wire_paths", None) or []:
+            g.add_wire_path(p0, p1, r)
         for src in sc.sources:
             node, axis, cur = src[:3]
             g.add_source(node, axis, cur, *(src[3:4]))

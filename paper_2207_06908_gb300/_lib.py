@@ -85,6 +85,7 @@ def load():
             "fdtd_set_debye": (I, [P, I, I, P, P]),
             "fdtd_add_voltage_source": (I, [P, I, I, I, I, ctypes.c_double, P, I, P]),
             "fdtd_add_lumped": (I, [P, I, I, I, I, ctypes.c_double, ctypes.c_double, P]),
+            "fdtd_add_wire_path": (I, [P, I, I, I, I, I, I, ctypes.c_double, P]),
             "fdtd_save_state": (I, [P, P, ctypes.POINTER(ctypes.c_size_t)]),
             "fdtd_load_state": (I, [P, P, ctypes.c_size_t]),
             "fdtd_mlp_forward": (I, [P, I, I, I, P, P, I, I, P, P, P, P]),

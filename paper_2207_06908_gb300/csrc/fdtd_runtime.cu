@@ -979,6 +979,53 @@ int fdtd_add_wire(fdtd_grid *g, int i0, int j0, int k0, int i1, int j1, int k1, 
     return FDTD_OK;
 }
 
+int fdtd_add_wire_path(fdtd_grid *g, int i0, int j0, int k0, int i1, int j1, int k1, double radius,
+                       int *n_segments)
+{
+    if (int rc = check_open(g, false)) return rc;
+    const int a[3] = {i0, j0, k0}, b[3] = {i1, j1, k1};
+    int d[3], len = 0;
+    for (int u = 0; u < 3; ++u) {
+        d[u] = std::abs(b[u] - a[u]);
+        len += d[u];
+    }
+    if (len == 0) return fail(g, FDTD_EINVAL, "wire has zero length");
+    // unit steps: along the axis least advanced towards b, ties to the lowest
+    std::vector<int> steps;
+    int c[3] = {i0, j0, k0};
+    for (int s = 0; s < len; ++s) {
+        int best = -1;
+        double bp = 2.0;
+        for (int u = 0; u < 3; ++u) {
+            if (c[u] == b[u]) continue;
+            const double prog = (double)std::abs(c[u] - a[u]) / d[u];
+            if (prog < bp) { bp = prog; best = u; }
+        }
+        steps.push_back(best);
+        c[best] += b[best] > a[best] ? 1 : -1;
+    }
+    // runs along one axis become wires (from the lower node)
+    const size_t before = g->wires.size();
+    int at[3] = {i0, j0, k0}, added = 0;
+    for (size_t s = 0; s < steps.size();) {
+        const int u = steps[s];
+        size_t e = s;
+        while (e < steps.size() && steps[e] == u) ++e;
+        int p0[3] = {at[0], at[1], at[2]};
+        at[u] += (b[u] > a[u] ? 1 : -1) * (int)(e - s);
+        int p1[3] = {at[0], at[1], at[2]};
+        if (p1[u] < p0[u]) std::swap(p0[u], p1[u]);
+        if (int rc = fdtd_add_wire(g, p0[0], p0[1], p0[2], p1[0], p1[1], p1[2], radius, nullptr)) {
+            g->wires.resize(before);           // nothing of the path stays
+            return rc;
+        }
+        ++added;
+        s = e;
+    }
+    if (n_segments) *n_segments = added;
+    return FDTD_OK;
+}
+
 int fdtd_add_source(fdtd_grid *g, int i, int j, int k, int axis, double r_internal,
                     const double *current, int n_samples, int *source_id)
 {

@@ -98,6 +98,14 @@ class Grid:
                                                           float(radius), ctypes.byref(wid)), "add_wire")
         return wid.value
 
+    def add_wire_path(self, p0, p1, radius):
+        """thin wire between two arbitrary nodes as a staircase of
+        grid-aligned wires; returns the number of wires added"""
+        n = ctypes.c_int()
+        check(self._lib, self._h, self._lib.fdtd_add_wire_path(self._h, *map(int, p0), *map(int, p1),
+                                                               float(radius), ctypes.byref(n)), "add_wire_path")
+        return n.value
+
     def add_source(self, node, axis, current, r_internal=0.0):
         cur = np.ascontiguousarray(current, dtype=np.float64)
         sid = ctypes.c_int()
@@ -270,6 +278,8 @@ def from_scenario(sc, stream=None, probe_capacity=None, torch_arena=True, block=
         g.set_debye(mat, deps, tau)
     for p0, p1, r in sc.wires:
         g.add_wire(p0, p1, r)
+    for p0, p1, r in getattr(sc, "wire_paths", None) or []:
+        g.add_wire_path(p0, p1, r)
     for src in sc.sources:
         node, axis, cur = src[:3]
         g.add_source(node, axis, cur, *(src[3:4]))

@@ -47,6 +47,7 @@ class Scenario:
     debye: dict = dataclasses.field(default_factory=dict)     # {material: (deps [P], tau [P] s)}
     vsources: list = dataclasses.field(default_factory=list)  # [(node, axis, voltage[n], r_internal)]
     lumped: list = dataclasses.field(default_factory=list)    # [(node, axis, resistance, capacitance)]
+    wire_paths: list = dataclasses.field(default_factory=list)  # [(p0, p1, radius)] oblique, as staircases
 
     @property
     def cells(self) -> int:

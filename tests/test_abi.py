@@ -73,6 +73,10 @@ def test_host_argument_checks():
         assert lib.fdtd_add_probe(h, 0, 3, 3, 3, 2, 5, None) == 0
         assert lib.fdtd_add_probe(h, 0, 3, 3, 3, 2, 6, None) == -1                 # path leaves grid
         assert lib.fdtd_add_probe(h, 1, 0, 3, 3, 2, 1, None) == -1                 # loop needs i >= 1
+        ns = ctypes.c_int()
+        assert lib.fdtd_add_wire_path(h, 2, 2, 2, 5, 4, 6, 0.004, ctypes.byref(ns)) == 0 and ns.value >= 3
+        assert lib.fdtd_add_wire_path(h, 2, 2, 2, 2, 2, 2, 0.004, None) == -1       # zero length
+        assert lib.fdtd_add_wire_path(h, 2, 2, 2, 0, 5, 6, 0.004, None) == -1       # reaches a wall
         assert lib.fdtd_step(h, 1) == -8                                           # not finalized
         nbytes = ctypes.c_size_t()
         assert lib.fdtd_save_state(h, None, ctypes.byref(nbytes)) == -8            # not finalized
