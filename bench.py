@@ -78,6 +78,24 @@ def workload_config(sc, steps):
             "l2": f"inputs larger than L2 (about {gb:.2f} GB of fields, classes and CPML state per step)"}
 
 
+def slowest_over_ranks(value, world, device="cpu"):
+    """the largest of every rank's value (the slowest rank's time): an
+    all-reduce MAX across the process group when world > 1"""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, seconds):
+    """whole-job throughput of N independent replicas (weak scaling): all
+    ranks' units over the slowest rank's time"""
+    return world * units_per_rank / seconds
+
+
 def debye_bytes(sc):
     """algorithmic DRAM bytes of the dispersive-media kernel per step: a
     record byte per cell of the planes holding dispersive edges, and per
@@ -483,18 +501,14 @@ def main():
     torch.cuda.synchronize()
     barrier()
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = slowest_over_ranks(e0.elapsed_time(e1), world, "cuda")
     # sanity: the run stayed finite
     probe = g.read_probe(0, 0, K + Wm)
     finite = bool(all(math.isfinite(float(x)) for x in probe))
     g.close()
 
     cells = sc.cells
-    value = world * cells * K / (ms / 1e3) / 1e9
+    value = job_rate(world, cells * K, ms / 1e3) / 1e9
     bps = bytes_per_step(sc)
     peak, peak_kind = peaks()
     achieved = bps / (ms / K / 1e3) / 1e9
@@ -524,11 +538,8 @@ def main():
         h2d = (pitch * ny * nz + n_cls * 9 * 4 + 6 * 4 * (nx + ny + nz)
                + sum(len(s[2]) for s in sc.sources) * 4 + 32 * len(sc.sources) + 24 * len(sc.probes))
         d2h = sum(o.nbytes for o in outs)
-        if world > 1:
-            t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
-        e2e = {"value": world * cells * K / t_e2e / 1e9, "unit": UNIT,
+        t_e2e = slowest_over_ranks(t_e2e, world, "cuda")
+        e2e = {"value": job_rate(world, cells * K, t_e2e) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
                "seconds": t_e2e, "includes": "grid setup, class building, upload, K steps, probe readback"}
 
