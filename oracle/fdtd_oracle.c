@@ -48,6 +48,37 @@
  *     mean of its tau; a thin wire scales the whole complex permittivity
  *     (eps_inf, sigma and every deps_p) by its factor m.  The interface
  *     averaging of poles is parity unpinned against the paper.
+ *   - Sec. 2.3 (oblique wires, the Guiffaut formalism the paper cites;
+ *     the paper prints none of its equations, so this is a reading in the
+ *     Holland-Simpson family it belongs to): a straight wire between two
+ *     arbitrary points in node units, split into segments of about one
+ *     cell; currents I_s at segment centres (times n+1/2) and charges Q_m
+ *     at the wire nodes (times n).  Per unit length the wire carries the
+ *     in-cell inductance L' = mu/(2 pi) ln(R/a), capacitance C' = 2 pi
+ *     eps / ln(R/a) and leakage G' = 2 pi sigma / ln(R/a) between its
+ *     radius a and the radius R at which the grid itself sees a line
+ *     current: R = dx r0 exp(2 pi S), r0 = exp(-gamma) / (2 sqrt 2) (the
+ *     square-lattice Green's function, G(0) - G(r) -> (ln(r/r0))/(2 pi)),
+ *     S = sum over pairs i != j of w_i w_j (G(0) - G(r_ij)) for the
+ *     bilinear weights w of the segment centre across the line lattice of
+ *     its dominant axis (G(0) - G = 1/4 at one spacing, 1/pi on the
+ *     diagonal).  Steps: I_s += dt/L' [E_s - (V_b - V_a)/dl], V_m = Q_m /
+ *     (C' dl_m); the segment current enters Ampere's law at t_{n+1/2} as
+ *     edge currents I W_e / dx^2 and E_s = sum_e W_e E_e^n dx / dl is the
+ *     mean tangential E^n along it, with the same edge shares W_e both
+ *     ways (reciprocal exchange).  W_e follow the charge-conserving
+ *     deposition of particle codes (Villasenor and Buneman): the straight
+ *     path a -> b is cut at the cell faces and each piece spreads its
+ *     displacement over the 12 edges of its cell so that the grid's
+ *     discrete divergence equals the move of a unit charge between the
+ *     trilinear node weights of a and b; without it a steady current along
+ *     an oblique wire would pile up spurious grid charge; Q_m^{n+1} = Q_m^n + dt [sum of currents into m] -
+ *     (G'/C') dt (Q^{n+1} + Q^n)/2.  A source is a delta-gap EMF V(t_n) in
+ *     one segment: V / dl joins E_s in that segment's current update.  Wires
+ *     whose end points coincide share that node (junction, Kirchhoff's
+ *     current law); a node on an outer wall is grounded (V = 0).  The
+ *     in-cell radius is parity unpinned against the paper (pinned by
+ *     transmission-line impedance and rotation tests).
  *
  * Layout.  Every component is a node-indexed FP64 array of
  * (nx+1)(ny+1)(nz+1) entries, index (k*(ny+1)+j)*(nx+1)+i, holding
@@ -87,12 +118,35 @@ typedef ORC_REAL real;
 #define ORC_MAXP 4                 /* Debye poles per material */
 
 enum { EX = 0, EY, EZ, HX, HY, HZ };
-enum { PROBE_V = 0, PROBE_I = 1, PROBE_E = 2, PROBE_H = 3 };
+enum { PROBE_V = 0, PROBE_I = 1, PROBE_E = 2, PROBE_H = 3, PROBE_W = 4 };
 
 typedef struct { int axis, i, j, k, n; double radius; } orc_wire;
 typedef struct { int axis, i, j, k, n; real *cur; int hard; } orc_src;   /* hard: ideal voltage source */
 typedef struct { int axis, i, j, k; double e_add, s_add; } orc_lump;      /* extra eps (F/m), sigma (S/m) */
 typedef struct { int kind, axis, i, j, k, n_edges; } orc_probe;
+
+/* oblique wires: segments with their coupling edges, nodes, node sources */
+#define ORC_OW_EDGES 48            /* up to 4 cells x 12 edges */
+typedef struct {
+    int a, b;                      /* wire nodes at the ends; I flows a -> b */
+    double c[3], t[3], dl;         /* centre (node units), direction, length (m) */
+    double lam;                    /* ln(R / a) */
+    real cI;                       /* dt / L' */
+    int ne;                        /* coupling edges */
+    int comp[ORC_OW_EDGES];
+    size_t q[ORC_OW_EDGES];
+    double W[ORC_OW_EDGES];        /* edge share of the path (cell units, signed) */
+    real wg[ORC_OW_EDGES];         /* gather: W dx / dl (E_s = sum wg E) */
+    real ws[ORC_OW_EDGES];         /* scatter: cb_edge W / dx (E -= ws I) */
+} orc_oseg;
+typedef struct {
+    double p[3];                   /* node units */
+    double dlm, lam_sum;           /* wire length it carries (m); sum of ln(R/a) of its segments */
+    int nadj, grounded;
+    real cV, aQ, bQ;               /* V = cV Q; Q^{n+1} = aQ Q^n + bQ (net current in) */
+} orc_onode;
+typedef struct { int seg0, nseg; double radius; } orc_owire;
+typedef struct { int seg, n; real *emf; } orc_osrc;   /* delta-gap EMF in a segment */
 
 typedef struct orc_grid {
     int nx, ny, nz;
@@ -132,6 +186,13 @@ typedef struct orc_grid {
     int has_debye;
     real *dcj[3][ORC_MAXP], *dk[3][ORC_MAXP], *dbe[3][ORC_MAXP], *J[3][ORC_MAXP];
     real *eprev[3];
+    /* oblique wires: segments, nodes, wires, node current sources and the
+     * state I_s^{n-1/2} (before a step), Q_m^n */
+    orc_oseg *osegs; int n_osegs;
+    orc_onode *onodes; int n_onodes;
+    orc_owire *owires; int n_owires;
+    orc_osrc *osrcs; int n_osrcs;
+    double *oI, *oQ;
     int max_steps;
     double *probe_out;         /* [n_probes][max_steps] */
     long step;
@@ -187,6 +248,8 @@ void orc_destroy(orc_grid *g)
     for (int s = 0; s < g->n_srcs; s++) free(g->srcs[s].cur);
     free(g->srcs); free(g->wires); free(g->probes); free(g->src_coef); free(g->probe_out);
     free(g->lumps); free(g->hard_coef);
+    for (int s = 0; s < g->n_osrcs; s++) free(g->osrcs[s].emf);
+    free(g->osegs); free(g->onodes); free(g->owires); free(g->osrcs); free(g->oI); free(g->oQ);
     free(g->mat); free(g->m_eps); free(g->m_sig); free(g->m_mu);
     free(g);
 }
@@ -390,6 +453,7 @@ int orc_add_lumped(orc_grid *g, int i, int j, int k, int axis, double resistance
 int orc_add_probe(orc_grid *g, int kind, int i, int j, int k, int axis, int n_edges)
 {
     if (g->finalized) return -8;
+    if (kind == PROBE_W) return -1;    /* oblique-wire currents: orc_add_owire_probe */
     if (axis < 0 || axis > 2 || kind < 0 || kind > 3) return -1;
     int p[3] = {i, j, k}, nn[3] = {g->nx, g->ny, g->nz};
     for (int u = 0; u < 3; u++) if (p[u] < 0 || p[u] >= nn[u]) return -1;
@@ -408,6 +472,139 @@ int orc_add_probe(orc_grid *g, int kind, int i, int j, int k, int axis, int n_ed
 static double cell_eps(const orc_grid *g, int i, int j, int k) { return g->m_eps[g->mat[CELL(g, i, j, k)]]; }
 static double cell_sig(const orc_grid *g, int i, int j, int k) { return g->m_sig[g->mat[CELL(g, i, j, k)]]; }
 static double cell_mu(const orc_grid *g, int i, int j, int k) { return g->m_mu[g->mat[CELL(g, i, j, k)]]; }
+
+/* ---- oblique wires --------------------------------------------------------
+ * A straight wire from (x0,y0,z0) to (x1,y1,z1) in node units (point (i,j,k)
+ * is at (i dx, j dx, k dx)), radius in metres, split into round(length in
+ * cells) segments (at least one).  End points that coincide with a node of
+ * an earlier oblique wire join it (junction).  Returns the wire index. */
+static int onode_at(const orc_grid *g, const double p[3])
+{
+    for (int m = 0; m < g->n_onodes; m++)
+        if (fabs(g->onodes[m].p[0] - p[0]) < 1e-9 && fabs(g->onodes[m].p[1] - p[1]) < 1e-9 &&
+            fabs(g->onodes[m].p[2] - p[2]) < 1e-9)
+            return m;
+    return -1;
+}
+
+static int onode_new(orc_grid *g, const double p[3])
+{
+    g->onodes = (orc_onode *)realloc(g->onodes, (g->n_onodes + 1) * sizeof(orc_onode));
+    orc_onode nd;
+    memset(&nd, 0, sizeof nd);
+    int nn[3] = {g->nx, g->ny, g->nz};
+    for (int u = 0; u < 3; u++) {
+        nd.p[u] = p[u];
+        if (p[u] == 0.0 || p[u] == (double)nn[u]) nd.grounded = 1;
+    }
+    g->onodes[g->n_onodes] = nd;
+    return g->n_onodes++;
+}
+
+int orc_add_owire(orc_grid *g, double x0, double y0, double z0, double x1, double y1, double z1, double radius)
+{
+    if (g->finalized) return -8;
+    double A[3] = {x0, y0, z0}, B[3] = {x1, y1, z1};
+    int nn[3] = {g->nx, g->ny, g->nz};
+    double len = 0.0;
+    for (int u = 0; u < 3; u++) {
+        if (!(A[u] >= 0.0 && A[u] <= nn[u] && B[u] >= 0.0 && B[u] <= nn[u])) return -1;
+        len += (B[u] - A[u]) * (B[u] - A[u]);
+    }
+    len = sqrt(len);
+    if (!(len >= 0.5) || !(radius > 0.0) || radius > 0.1 * g->dx) return -1;
+    int N = (int)lround(len);
+    if (N < 1) N = 1;
+    g->owires = (orc_owire *)realloc(g->owires, (g->n_owires + 1) * sizeof(orc_owire));
+    orc_owire w = {g->n_osegs, N, radius};
+    g->owires[g->n_owires] = w;
+    int prev = onode_at(g, A);
+    if (prev < 0) prev = onode_new(g, A);
+    for (int sg = 0; sg < N; sg++) {
+        double P[3];
+        for (int u = 0; u < 3; u++) P[u] = A[u] + (B[u] - A[u]) * (double)(sg + 1) / N;
+        int next = -1;
+        if (sg == N - 1) { for (int u = 0; u < 3; u++) P[u] = B[u]; next = onode_at(g, B); }
+        if (next < 0) next = onode_new(g, P);
+        g->osegs = (orc_oseg *)realloc(g->osegs, (g->n_osegs + 1) * sizeof(orc_oseg));
+        orc_oseg *S = &g->osegs[g->n_osegs++];
+        memset(S, 0, sizeof *S);
+        S->a = prev;
+        S->b = next;
+        for (int u = 0; u < 3; u++) {
+            S->t[u] = (B[u] - A[u]) / len;
+            S->c[u] = A[u] + (B[u] - A[u]) * (sg + 0.5) / N;
+        }
+        S->dl = len * g->dx / N;
+        prev = next;
+    }
+    return g->n_owires++;
+}
+
+/* delta-gap EMF in segment seg of oblique wire w: volt[n] (V at t_n) drives
+ * the segment's current from its start node to its end node */
+int orc_add_owire_vsource(orc_grid *g, int w, int seg, const double *volt, int n)
+{
+    if (g->finalized) return -8;
+    if (w < 0 || w >= g->n_owires || seg < 0 || seg >= g->owires[w].nseg || n < 0) return -1;
+    g->osrcs = (orc_osrc *)realloc(g->osrcs, (g->n_osrcs + 1) * sizeof(orc_osrc));
+    orc_osrc sr = {g->owires[w].seg0 + seg, n, (real *)malloc((n > 0 ? n : 1) * sizeof(real))};
+    for (int q = 0; q < n; q++) sr.emf[q] = r32(g, volt[q]);
+    g->osrcs[g->n_osrcs++] = sr;
+    return 0;
+}
+
+/* probe of segment seg of oblique wire w: I_s at t_{n+1/2} */
+int orc_add_owire_probe(orc_grid *g, int w, int seg)
+{
+    if (g->finalized) return -8;
+    if (w < 0 || w >= g->n_owires || seg < 0 || seg >= g->owires[w].nseg) return -1;
+    g->probes = (orc_probe *)realloc(g->probes, (g->n_probes + 1) * sizeof(orc_probe));
+    orc_probe pr = {PROBE_W, 0, g->owires[w].seg0 + seg, 0, 0, 1};
+    g->probes[g->n_probes++] = pr;
+    return 0;
+}
+
+void orc_owire_counts(const orc_grid *g, int *n_seg, int *n_node)
+{
+    *n_seg = g->n_osegs;
+    *n_node = g->n_onodes;
+}
+
+/* state I_s (last half step) and Q_m (current integer step) */
+int orc_get_owire_state(const orc_grid *g, double *I, double *Q)
+{
+    if (!g->finalized) return -8;
+    for (int s = 0; s < g->n_osegs; s++) I[s] = g->oI[s];
+    for (int m = 0; m < g->n_onodes; m++) Q[m] = g->oQ[m];
+    return 0;
+}
+
+int orc_set_owire_state(orc_grid *g, const double *I, const double *Q)
+{
+    if (!g->finalized) return -8;
+    for (int s = 0; s < g->n_osegs; s++) g->oI[s] = I[s];
+    for (int m = 0; m < g->n_onodes; m++) g->oQ[m] = g->onodes[m].grounded ? 0.0 : Q[m];
+    return 0;
+}
+
+/* per segment L' dl (H) and per node 1 / (C' dl_m) (1/F; 0 when grounded),
+ * the quantities of the wire's stored energy */
+int orc_get_owire_coefs(const orc_grid *g, double *Ldl, double *cV)
+{
+    if (!g->finalized) return -8;
+    for (int s = 0; s < g->n_osegs; s++) {
+        const orc_oseg *S = &g->osegs[s];
+        int ci[3], nn[3] = {g->nx, g->ny, g->nz};
+        for (int u = 0; u < 3; u++) {
+            ci[u] = (int)floor(S->c[u]);
+            if (ci[u] > nn[u] - 1) ci[u] = nn[u] - 1;
+        }
+        Ldl[s] = ORC_MU0 * cell_mu(g, ci[0], ci[1], ci[2]) * S->lam / (2.0 * M_PI) * S->dl;
+    }
+    for (int m = 0; m < g->n_onodes; m++) cV[m] = g->onodes[m].grounded ? 0.0 : g->onodes[m].cV;
+    return 0;
+}
 
 /* the four cells around E edge comp at node (i,j,k) (the same cells whose
  * eps and sigma are averaged) */
@@ -578,6 +775,127 @@ static void e_stencil(int comp, const int q[3], int hc[4], int hp[4][3])
     hp[3][c] -= 1;
 }
 
+
+/* in-cell parameters and coupling edges of the oblique wires (after the
+ * E coefficients exist: the scatter uses each edge's cb) */
+static int build_owires(orc_grid *g)
+{
+    const double dx = g->dx, dt = g->dt;
+    const double r0 = exp(-0.57721566490153286) / (2.0 * sqrt(2.0));
+    int nn[3] = {g->nx, g->ny, g->nz};
+    for (int m = 0; m < g->n_onodes; m++) { g->onodes[m].dlm = 0.0; g->onodes[m].lam_sum = 0.0; g->onodes[m].nadj = 0; }
+    for (int w = 0; w < g->n_owires; w++)
+        for (int s = g->owires[w].seg0; s < g->owires[w].seg0 + g->owires[w].nseg; s++) {
+            orc_oseg *S = &g->osegs[s];
+            /* radius at which the grid sees the segment's current: the
+             * bilinear spread of its centre over the line lattice of its
+             * dominant axis */
+            int u = 0;
+            for (int v = 1; v < 3; v++) if (fabs(S->t[v]) > fabs(S->t[u])) u = v;
+            int v1 = (u + 1) % 3, v2 = (u + 2) % 3;
+            double f1 = S->c[v1] - floor(S->c[v1]), f2 = S->c[v2] - floor(S->c[v2]);
+            double w00 = (1 - f1) * (1 - f2), w10 = f1 * (1 - f2), w01 = (1 - f1) * f2, w11 = f1 * f2;
+            double S2 = 2.0 * ((w00 * w10 + w01 * w11 + w00 * w01 + w10 * w11) * 0.25 + (w00 * w11 + w10 * w01) / M_PI);
+            double R = dx * r0 * exp(2.0 * M_PI * S2);
+            double a = g->owires[w].radius;
+            S->lam = log(R / a);
+            if (!(S->lam > 0.0)) return -1;
+            int ci[3];
+            for (int q = 0; q < 3; q++) {
+                ci[q] = (int)floor(S->c[q]);
+                if (ci[q] > nn[q] - 1) ci[q] = nn[q] - 1;
+            }
+            double Lp = ORC_MU0 * cell_mu(g, ci[0], ci[1], ci[2]) * S->lam / (2.0 * M_PI);
+            S->cI = r32(g, dt / Lp);
+            /* charge-conserving coupling: the path a -> b split at the cell
+             * faces it crosses; each piece inside one cell spreads its
+             * displacement over the cell's 12 edges with the weights under
+             * which the grid divergence equals the move of a unit charge
+             * between the trilinear node weights of its two ends */
+            S->ne = 0;
+            const double *pa = g->onodes[S->a].p, *pb = g->onodes[S->b].p;
+            double cut[8];
+            int ncut = 0;
+            cut[ncut++] = 0.0;
+            for (int q = 0; q < 3; q++) {
+                double lo = pa[q] < pb[q] ? pa[q] : pb[q], hi = pa[q] < pb[q] ? pb[q] : pa[q];
+                for (double x = floor(lo) + 1.0; x < hi; x += 1.0) {
+                    if (ncut >= 7) return -1;
+                    cut[ncut++] = (x - pa[q]) / (pb[q] - pa[q]);
+                }
+            }
+            cut[ncut++] = 1.0;
+            for (int x = 1; x < ncut; x++)          /* sort the crossing fractions */
+                for (int y = x; y > 0 && cut[y] < cut[y - 1]; y--) { double t = cut[y]; cut[y] = cut[y - 1]; cut[y - 1] = t; }
+            for (int piece = 0; piece + 1 < ncut; piece++) {
+                double u0 = cut[piece], u1 = cut[piece + 1];
+                if (!(u1 > u0)) continue;
+                double mid[3], dd[3], fr[3];
+                int cell[3];
+                for (int q = 0; q < 3; q++) {
+                    double x0 = pa[q] + u0 * (pb[q] - pa[q]), x1 = pa[q] + u1 * (pb[q] - pa[q]);
+                    mid[q] = 0.5 * (x0 + x1);
+                    dd[q] = x1 - x0;
+                    cell[q] = (int)floor(mid[q]);
+                    if (cell[q] > nn[q] - 1) cell[q] = nn[q] - 1;
+                    fr[q] = mid[q] - cell[q];
+                }
+                for (int c = 0; c < 3; c++) {
+                    if (dd[c] == 0.0) continue;
+                    int v1 = (c + 1) % 3, v2 = (c + 2) % 3;
+                    for (int corner = 0; corner < 4; corner++) {
+                        int d1 = corner & 1, d2 = corner >> 1;
+                        double w1 = d1 ? fr[v1] : 1.0 - fr[v1], w2 = d2 ? fr[v2] : 1.0 - fr[v2];
+                        double wt = dd[c] * (w1 * w2 + (d1 == d2 ? 1.0 : -1.0) * dd[v1] * dd[v2] / 12.0);
+                        int id[3];
+                        id[c] = cell[c];
+                        id[v1] = cell[v1] + d1;
+                        id[v2] = cell[v2] + d2;
+                        if (id[c] < 0 || id[c] > nn[c] - 1 || id[v1] < 1 || id[v1] > nn[v1] - 1 || id[v2] < 1 ||
+                            id[v2] > nn[v2] - 1 || wt == 0.0)
+                            continue;
+                        size_t qi = IDX(g, id[0], id[1], id[2]);
+                        int e = 0;
+                        while (e < S->ne && !(S->comp[e] == c && S->q[e] == qi)) e++;
+                        if (e == S->ne) {
+                            if (S->ne >= ORC_OW_EDGES) return -1;
+                            S->ne++;
+                            S->comp[e] = c;
+                            S->q[e] = qi;
+                            S->W[e] = 0.0;
+                        }
+                        S->W[e] += wt;
+                    }
+                }
+            }
+            for (int e = 0; e < S->ne; e++) {
+                S->wg[e] = r32(g, S->W[e] * dx / S->dl);
+                S->ws[e] = r32(g, (double)g->cb[S->comp[e]][S->q[e]] * S->W[e] / dx);
+            }
+            orc_onode *A = &g->onodes[S->a], *Bn = &g->onodes[S->b];
+            A->dlm += 0.5 * S->dl; Bn->dlm += 0.5 * S->dl;
+            A->lam_sum += S->lam; Bn->lam_sum += S->lam;
+            A->nadj++; Bn->nadj++;
+        }
+    for (int m = 0; m < g->n_onodes; m++) {
+        orc_onode *nd = &g->onodes[m];
+        int ci[3];
+        for (int q = 0; q < 3; q++) {
+            ci[q] = (int)floor(nd->p[q]);
+            if (ci[q] > nn[q] - 1) ci[q] = nn[q] - 1;
+        }
+        double eps = ORC_EPS0 * cell_eps(g, ci[0], ci[1], ci[2]), sig = cell_sig(g, ci[0], ci[1], ci[2]);
+        double lam = nd->lam_sum / nd->nadj;
+        double r = sig * dt / (2.0 * eps);
+        nd->cV = r32(g, lam / (2.0 * M_PI * eps * nd->dlm));
+        nd->aQ = r32(g, (1.0 - r) / (1.0 + r));
+        nd->bQ = r32(g, dt / (1.0 + r));
+    }
+    g->oI = (double *)calloc(g->n_osegs > 0 ? g->n_osegs : 1, sizeof(double));
+    g->oQ = (double *)calloc(g->n_onodes > 0 ? g->n_onodes : 1, sizeof(double));
+    return 0;
+}
+
 int orc_finalize(orc_grid *g, int max_steps)
 {
     if (g->finalized) return -8;
@@ -744,6 +1062,7 @@ int orc_finalize(orc_grid *g, int max_steps)
     for (int c = 0; c < 3; c++) { free(le[c]); free(ls[c]); }
     for (int c = 0; c < 3; c++) { free(eps[c]); free(sig[c]); free(mu[c]); free(pec[c]); free(fac_e[c]); free(fac_h[c]); }
     build_cpml(g);
+    if (g->n_owires > 0 && (g->has_debye || build_owires(g) != 0)) return -1;
     g->max_steps = max_steps;
     g->probe_out = (double *)calloc((size_t)(g->n_probes > 0 ? g->n_probes : 1) * (max_steps > 0 ? max_steps : 1), sizeof(double));
     g->finalized = 1;
@@ -840,6 +1159,54 @@ static inline real debye_add(const orc_grid *g, int c, size_t q, real e)
     return e;
 }
 
+
+/* oblique wires, first half: I_s^{n+1/2} from E^n along the segment, the
+ * node potentials V_m^n = cV Q_m^n (zero at grounded nodes) and the
+ * delta-gap EMFs at t_n */
+static void owire_current(orc_grid *g)
+{
+    for (int s = 0; s < g->n_osegs; s++) {
+        const orc_oseg *S = &g->osegs[s];
+        double es = 0.0;
+        for (int e = 0; e < S->ne; e++) es += (double)S->wg[e] * g->f[S->comp[e]][S->q[e]];
+        const orc_onode *A = &g->onodes[S->a], *B = &g->onodes[S->b];
+        double va = A->grounded ? 0.0 : (double)A->cV * g->oQ[S->a];
+        double vb = B->grounded ? 0.0 : (double)B->cV * g->oQ[S->b];
+        g->oI[s] += (double)S->cI * (es - (vb - va) / S->dl);
+    }
+    for (int q = 0; q < g->n_osrcs; q++) {
+        const orc_osrc *sr = &g->osrcs[q];
+        if (g->step < sr->n) g->oI[sr->seg] += (double)g->osegs[sr->seg].cI * sr->emf[g->step] / g->osegs[sr->seg].dl;
+    }
+}
+
+/* the segment currents in Ampere's law: E^{n+1} -= cb dx J on the coupling
+ * edges */
+static void owire_inject(orc_grid *g)
+{
+    for (int s = 0; s < g->n_osegs; s++) {
+        const orc_oseg *S = &g->osegs[s];
+        for (int e = 0; e < S->ne; e++) g->f[S->comp[e]][S->q[e]] -= (double)S->ws[e] * g->oI[s];
+    }
+}
+
+/* second half: Q_m^{n+1} from the net segment current into each node at
+ * t_{n+1/2}, with the medium's relaxation */
+static void owire_charge(orc_grid *g)
+{
+    if (g->n_onodes == 0) return;
+    double *net = (double *)calloc(g->n_onodes, sizeof(double));
+    for (int s = 0; s < g->n_osegs; s++) {
+        net[g->osegs[s].b] += g->oI[s];
+        net[g->osegs[s].a] -= g->oI[s];
+    }
+    for (int m = 0; m < g->n_onodes; m++) {
+        const orc_onode *nd = &g->onodes[m];
+        g->oQ[m] = nd->grounded ? 0.0 : (double)nd->aQ * g->oQ[m] + (double)nd->bQ * net[m];
+    }
+    free(net);
+}
+
 static void update_e(orc_grid *g)
 {
     int nx = g->nx, ny = g->ny, nz = g->nz;
@@ -882,8 +1249,10 @@ static void update_e(orc_grid *g)
                 Ez[q] = g->ca[2][q] * Ez[q] + g->cb[2][q] * (tx - ty);
                 if (deb) Ez[q] = debye_add(g, 2, q, Ez[q]);
             }
-    /* current sources: -cb/dx * I(t_{n+1/2}) on the source edge; then ideal
-     * voltage sources force E^{n+1} = -V(t_{n+1}) / dx */
+    /* oblique-wire currents, then current sources: -cb/dx * I(t_{n+1/2}) on
+     * the source edge; then ideal voltage sources force E^{n+1} =
+     * -V(t_{n+1}) / dx */
+    owire_inject(g);
     for (int s = 0; s < g->n_srcs; s++) {
         orc_src *sr = &g->srcs[s];
         if (sr->hard) continue;
@@ -946,6 +1315,7 @@ int orc_get_debye_current(const orc_grid *g, int comp, int pole, double *cells)
 static double probe_value(const orc_grid *g, const orc_probe *p)
 {
     double dx = g->dx;
+    if (p->kind == PROBE_W) return g->oI[p->i];
     if (p->kind == PROBE_E) return g->f[p->axis][IDX(g, p->i, p->j, p->k)];
     if (p->kind == PROBE_H) return g->f[3 + p->axis][IDX(g, p->i, p->j, p->k)];
     if (p->kind == PROBE_V) {
@@ -967,17 +1337,21 @@ static double probe_value(const orc_grid *g, const orc_probe *p)
     return dx * (Hx[IDX(g, i, j, k)] - Hx[IDX(g, i, j, k - 1)] - Hz[IDX(g, i, j, k)] + Hz[IDX(g, i - 1, j, k)]);
 }
 
-/* advance n full steps: H to n+1/2, record I/H probes, E to n+1 (with the
- * sources at n+1/2), record V/E probes */
+/* advance n full steps: H to n+1/2, oblique-wire currents to n+1/2, record
+ * I/H/wire probes, E to n+1 (with the wire and source currents at n+1/2),
+ * wire charges to n+1, record V/E probes */
 int orc_step(orc_grid *g, int n)
 {
     if (!g->finalized) return -8;
     for (int s = 0; s < n; s++) {
         update_h(g);
+        owire_current(g);
         for (int p = 0; p < g->n_probes; p++)
-            if ((g->probes[p].kind == PROBE_I || g->probes[p].kind == PROBE_H) && g->step < g->max_steps)
+            if ((g->probes[p].kind == PROBE_I || g->probes[p].kind == PROBE_H || g->probes[p].kind == PROBE_W) &&
+                g->step < g->max_steps)
                 g->probe_out[(size_t)p * g->max_steps + g->step] = probe_value(g, &g->probes[p]);
         update_e(g);
+        owire_charge(g);
         for (int p = 0; p < g->n_probes; p++)
             if ((g->probes[p].kind == PROBE_V || g->probes[p].kind == PROBE_E) && g->step < g->max_steps)
                 g->probe_out[(size_t)p * g->max_steps + g->step] = probe_value(g, &g->probes[p]);

@@ -6,8 +6,9 @@ library never imports this module and this module never imports the
 library.
 
 The C file follows the paper's Sec. 2.1 (Eq. maxwell, maxwelle, maxwellh,
-fdtdex, fdtdhx), Sec. 2.2 (CPML), Sec. 2.3 (thin wires) and the "calculate"
-probes of the Sec. 4 model files; see its header for the readings taken.
+fdtdex, fdtdhx), Sec. 2.2 (CPML), Sec. 2.3 (thin wires, axis-aligned and
+oblique) and the "calculate" probes of the Sec. 4 model files; see its
+header for the readings taken.
 """
 from __future__ import annotations
 
@@ -93,6 +94,15 @@ def _load(f32: bool = False):
         lib.orc_add_wire_path.argtypes = [P, I, I, I, I, I, I, D]
         lib.orc_get_debye_current.argtypes = [P, I, I, dp]
         lib.orc_set_debye_current.argtypes = [P, I, I, dp]
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.orc_add_owire.argtypes = [P, D, D, D, D, D, D, D]
+        lib.orc_add_owire_vsource.argtypes = [P, I, I, dp, I]
+        lib.orc_add_owire_probe.argtypes = [P, I, I]
+        lib.orc_owire_counts.argtypes = [P, ip, ip]
+        lib.orc_owire_counts.restype = None
+        lib.orc_get_owire_state.argtypes = [P, dp, dp]
+        lib.orc_set_owire_state.argtypes = [P, dp, dp]
+        lib.orc_get_owire_coefs.argtypes = [P, dp, dp]
         _libs[f32] = lib
         return lib
 
@@ -210,6 +220,51 @@ class OracleGrid:
         _check(self._lib.orc_add_lumped(self._h, *map(int, node), int(axis), float(resistance),
                                         float(capacitance)), "add_lumped")
 
+    def add_oblique_wire(self, p0, p1, radius):
+        """straight wire between two points in node units (any
+        orientation, floats allowed); returns its index"""
+        rc = self._lib.orc_add_owire(self._h, *map(float, p0), *map(float, p1), float(radius))
+        if rc < 0:
+            _check(rc, "add_oblique_wire")
+        return rc
+
+    def add_wire_voltage_source(self, wire, segment, voltage):
+        """delta-gap EMF (V at t_n) in one segment of an oblique wire,
+        driving current from the segment's start towards its end"""
+        v = np.ascontiguousarray(voltage, dtype=np.float64)
+        _check(self._lib.orc_add_owire_vsource(self._h, int(wire), int(segment), _dptr(v), len(v)),
+               "add_wire_voltage_source")
+
+    def add_wire_probe(self, wire, segment):
+        """current of one segment of an oblique wire at t_{n+1/2}"""
+        _check(self._lib.orc_add_owire_probe(self._h, int(wire), int(segment)), "add_wire_probe")
+        self.n_probes += 1
+        return self.n_probes - 1
+
+    def wire_counts(self):
+        ns, nn = ctypes.c_int(), ctypes.c_int()
+        self._lib.orc_owire_counts(self._h, ctypes.byref(ns), ctypes.byref(nn))
+        return ns.value, nn.value
+
+    def get_wire_state(self):
+        """(I_s at the last half step, Q_m at the current step)"""
+        ns, nn = self.wire_counts()
+        I, Q = np.zeros(max(ns, 1)), np.zeros(max(nn, 1))
+        _check(self._lib.orc_get_owire_state(self._h, _dptr(I), _dptr(Q)), "get_wire_state")
+        return I[:ns], Q[:nn]
+
+    def set_wire_state(self, I, Q):
+        I = np.ascontiguousarray(I, dtype=np.float64)
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        _check(self._lib.orc_set_owire_state(self._h, _dptr(I), _dptr(Q)), "set_wire_state")
+
+    def get_wire_coefs(self):
+        """per segment L' dl (H), per node 1 / (C' dl_m) (0 when grounded)"""
+        ns, nn = self.wire_counts()
+        L, cV = np.zeros(max(ns, 1)), np.zeros(max(nn, 1))
+        _check(self._lib.orc_get_owire_coefs(self._h, _dptr(L), _dptr(cV)), "get_wire_coefs")
+        return L[:ns], cV[:nn]
+
     def add_probe(self, kind, node, axis, n_edges=1):
         _check(self._lib.orc_add_probe(self._h, int(kind), *map(int, node), int(axis),
                                        int(n_edges)), "add_probe")
@@ -263,8 +318,14 @@ class OracleGrid:
             g.add_voltage_source(node, axis, volt, r)
         for node, axis, res, cap in getattr(sc, "lumped", None) or []:
             g.add_lumped(node, axis, res, cap)
+        for p0, p1, r in getattr(sc, "owires", None) or []:
+            g.add_oblique_wire(p0, p1, r)
+        for w, seg, volt in getattr(sc, "owire_sources", None) or []:
+            g.add_wire_voltage_source(w, seg, volt)
         for kind, node, axis, ne in sc.probes:
             g.add_probe(kind, node, axis, ne)
+        for w, seg in getattr(sc, "owire_probes", None) or []:
+            g.add_wire_probe(w, seg)
         g.finalize(sc.n_steps)
         if sc.fields is not None:
             # start from the FP32-rounded fields the GPU starts from

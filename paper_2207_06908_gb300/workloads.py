@@ -48,6 +48,9 @@ class Scenario:
     vsources: list = dataclasses.field(default_factory=list)  # [(node, axis, voltage[n], r_internal)]
     lumped: list = dataclasses.field(default_factory=list)    # [(node, axis, resistance, capacitance)]
     wire_paths: list = dataclasses.field(default_factory=list)  # [(p0, p1, radius)] oblique, as staircases
+    owires: list = dataclasses.field(default_factory=list)      # [(p0, p1, radius)] oblique wires, node units
+    owire_sources: list = dataclasses.field(default_factory=list)  # [(wire, segment, emf[n])] delta gaps
+    owire_probes: list = dataclasses.field(default_factory=list)   # [(wire, segment)] segment currents
 
     @property
     def cells(self) -> int:

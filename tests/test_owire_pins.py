@@ -1,0 +1,192 @@
+"""Pins of the oracle's oblique thin wires (Sec. 2.3; the Guiffaut
+formalism the paper cites, read in the Holland-Simpson form stated in the
+oracle's header) against invariants and closed forms (CPU only).
+
+- energy: with the grid-wire exchange reciprocal, the discrete energy of
+  the fields plus 1/2 L' dl I I + 1/2 Q^2 / (C' dl) is an exact invariant of
+  a lossless PEC box (catches a sign, a dropped term or unequal gather and
+  scatter weights anywhere in the coupling, the junction or the grounding);
+- charge: the total wire charge changes only by the medium's relaxation;
+- relaxation: on a closed ring with uniform charge nothing drives a current
+  and the charge decays by the medium's semi-implicit relaxation factor;
+- accuracy: a wire over a ground plane carries a wave with V / I equal to
+  the transmission-line impedance of radius a, along an axis and along an
+  oblique direction (this is what pins the in-cell radius).
+"""
+import math
+
+import numpy as np
+
+from oracle.oracle import C0, EPS0, MU0, EX, EY, EZ, HX, HY, HZ, OracleGrid
+from test_oracle_pins import edge_eps, energy, random_fields, random_materials
+
+ETA0 = math.sqrt(MU0 / EPS0)
+
+
+def wire_energy(I_m, I_p, Q, Ldl, cV):
+    return 0.5 * float(np.sum(Ldl * I_m * I_p)) + 0.5 * float(np.sum(cV * Q * Q))
+
+
+def _wired_box(rng, n, dx, grounded=True):
+    cm, eps, sig, mu = random_materials(rng, n, 4)
+    g = OracleGrid(*n, dx, parity=False)
+    g.set_materials(cm, eps, sig, mu)
+    g.add_oblique_wire((3.3, 4.1, 3.7), (11.2, 9.6, 8.4), 0.002)
+    g.add_oblique_wire((11.2, 9.6, 8.4), (12.5, 3.2, 5.0), 0.003)     # junction at the shared end
+    g.add_oblique_wire((11.2, 9.6, 8.4), (6.0, 10.0, 10.5), 0.002)    # third branch at the same node
+    if grounded:
+        g.add_oblique_wire((5.0, 5.0, 0.0), (5.0, 5.0, 4.0), 0.004)   # axis-aligned, grounded on z = 0
+    return g, cm, eps, mu
+
+
+def test_energy_invariant_with_oblique_wires_and_junction():
+    rng = np.random.default_rng(11)
+    n, dx = (16, 14, 12), 0.1
+    g, cm, eps, mu = _wired_box(rng, n, dx)
+    g.finalize()
+    ns, nn = g.wire_counts()
+    assert ns >= 20 and nn == ns + 2           # two trees: three branches joined at one node, and the grounded wire
+    f0 = random_fields(rng, n)
+    for c in range(6):
+        g.set_field(c, f0[c])
+    I0 = rng.standard_normal(ns) * 0.01
+    Q0 = rng.standard_normal(nn) * 1e-13
+    g.set_wire_state(I0, Q0)
+    _, Q0 = g.get_wire_state()                 # grounded nodes hold no charge
+    Ldl, cV = g.get_wire_coefs()
+    w = edge_eps(cm, eps)[:3] + edge_eps(cm, mu)[3:]
+    g.step(1)
+    H1 = [g.get_field(c) for c in (HX, HY, HZ)]
+    I1, _ = g.get_wire_state()
+    W0 = energy(f0[:3], f0[3:], H1, w, dx) + wire_energy(I0, I1, Q0, Ldl, cV)
+    g.step(1499)
+    E = [g.get_field(c) for c in (EX, EY, EZ)]
+    Hm = [g.get_field(c) for c in (HX, HY, HZ)]
+    Im, Q = g.get_wire_state()
+    g.step(1)
+    Hp = [g.get_field(c) for c in (HX, HY, HZ)]
+    Ip, _ = g.get_wire_state()
+    W = energy(E, Hm, Hp, w, dx) + wire_energy(Im, Ip, Q, Ldl, cV)
+    assert abs(W - W0) <= 1e-10 * W0, (W, W0)
+    # the wire really exchanged energy with the grid
+    assert float(np.max(np.abs(Ip))) > 1e-4
+
+
+def test_wire_charge_is_conserved_and_relaxes_with_the_medium():
+    """No grounded node: each segment current leaves one node and enters
+    another (Kirchhoff at the junction), so the total wire charge changes
+    only by the medium's relaxation factor per step, whatever the grid, the
+    EMF and the currents do"""
+    rng = np.random.default_rng(12)
+    n, dx = (16, 14, 12), 0.1
+    for sigma in (0.0, 0.01):
+        g = OracleGrid(*n, dx, parity=False)
+        eps_r = 5.0
+        g.set_materials(np.zeros((n[2], n[1], n[0]), np.uint8), [eps_r], [sigma], [1.0])
+        g.add_oblique_wire((3.3, 4.1, 3.7), (11.2, 9.6, 8.4), 0.002)
+        g.add_oblique_wire((11.2, 9.6, 8.4), (12.5, 3.2, 5.0), 0.003)
+        g.add_oblique_wire((11.2, 9.6, 8.4), (6.0, 10.0, 10.5), 0.002)
+        steps = 300
+        g.add_wire_voltage_source(0, 2, 50.0 * np.sin(np.arange(steps) * 0.05))
+        g.finalize(steps)
+        f0 = random_fields(rng, n)
+        for c in range(6):
+            g.set_field(c, f0[c])
+        ns, nn = g.wire_counts()
+        Q0 = rng.standard_normal(nn) * 1e-12
+        g.set_wire_state(np.zeros(ns), Q0)
+        r = sigma * g.dt / (2 * EPS0 * eps_r)
+        for n_done in (1, 17, 300):
+            g.step(n_done - g.step_count)
+            I, Q = g.get_wire_state()
+            expect = float(np.sum(Q0)) * ((1 - r) / (1 + r)) ** n_done
+            assert abs(float(np.sum(Q)) - expect) <= 1e-9 * float(np.sum(np.abs(Q0))), (sigma, n_done)
+            assert float(np.max(np.abs(I))) > 0
+
+
+def test_closed_ring_charge_relaxes_at_the_medium_rate():
+    n, dx = (14, 14, 10), 0.2
+    eps_r, sigma = 6.0, 0.02
+    g = OracleGrid(*n, dx, parity=False)
+    g.set_materials(np.zeros((n[2], n[1], n[0]), np.uint8), [eps_r], [sigma], [1.0])
+    corners = [(4, 4, 5), (10, 4, 5), (10, 10, 5), (4, 10, 5)]
+    for q in range(4):
+        g.add_oblique_wire(corners[q], corners[(q + 1) % 4], 0.003)
+    g.finalize()
+    ns, nn = g.wire_counts()
+    assert ns == 24 and nn == 24               # a closed ring: as many nodes as segments
+    Q0 = np.full(nn, 3e-12)
+    g.set_wire_state(np.zeros(ns), Q0)
+    dt = g.dt
+    r = sigma * dt / (2 * EPS0 * eps_r)
+    g.step(400)
+    I, Q = g.get_wire_state()
+    assert np.max(np.abs(I)) == 0.0
+    np.testing.assert_allclose(Q, Q0 * ((1 - r) / (1 + r)) ** 400, rtol=1e-12)
+    for c in range(6):
+        assert np.max(np.abs(g.get_field(c))) == 0.0
+
+
+def _line_impedance(direction, n=(84, 48, 40), h=4, a=0.002, dx=0.1, steps=150, window=(100, 150)):
+    """a grounded riser from the z = 0 plane up to height h (cells) with a
+    delta-gap EMF in its bottom segment, then a horizontal wire along
+    `direction`; returns the mean of V / I over the window at the
+    horizontal wire's middle node, V = -sum Ez dz from the plane to the wire
+    (bilinear between the four vertical lines around the node) plus the
+    node's in-cell potential, I the mean current of its two segments"""
+    g = OracleGrid(*n, dx, parity=False)
+    base = np.array([6.0, 8.0 if direction[1] else n[1] / 2, 0.0])
+    p0 = base + [0.0, 0.0, h]
+    d = np.asarray(direction, float) / np.linalg.norm(direction)
+    p1 = p0 + 64.0 * d
+    g.add_oblique_wire(tuple(base), tuple(p0), a)
+    g.add_oblique_wire(tuple(p0), tuple(p1), a)
+    t = np.arange(steps)
+    g.add_wire_voltage_source(0, 0, 100.0 * np.where(t < 24, 0.5 - 0.5 * np.cos(np.pi * t / 24), 1.0))
+    g.finalize(steps)
+    ns, nn = g.wire_counts()
+    _, cV = g.get_wire_coefs()
+    nh = ns - h                                # segments of the horizontal wire
+    m = h + nh // 2                            # its middle node (riser nodes come first)
+    pm = p0 + (p1 - p0) * (nh // 2) / nh
+    i0, j0 = int(math.floor(pm[0])), int(math.floor(pm[1]))
+    fx, fy = pm[0] - i0, pm[1] - j0
+    zs = []
+    for s in range(steps):
+        g.step(1)
+        if window[0] <= s < window[1]:
+            Ez = g.get_field(EZ)
+            I, Q = g.get_wire_state()
+            col = lambda i, j: -float(np.sum(Ez[:h, j, i])) * dx
+            vg = ((1 - fx) * (1 - fy) * col(i0, j0) + fx * (1 - fy) * col(i0 + 1, j0) +
+                  (1 - fx) * fy * col(i0, j0 + 1) + fx * fy * col(i0 + 1, j0 + 1))
+            zs.append((vg + cV[m] * Q[m]) / (0.5 * (I[m - 1] + I[m])))
+    return float(np.mean(zs))
+
+
+def _z0_two_planes(h, H, a):
+    """wire at height h between conducting planes at 0 and H (H >> a)"""
+    return ETA0 / (2 * math.pi) * math.log(2 * H / (math.pi * a) * math.tan(math.pi * h / H))
+
+
+GRID = (84, 64, 40)
+
+
+def test_line_impedance_axis_aligned_wire():
+    dx, h, a = 0.1, 4, 0.002
+    z = _line_impedance((1, 0, 0), n=GRID, h=h, a=a, dx=dx)
+    z0 = _z0_two_planes(h * dx, GRID[2] * dx, a)
+    assert abs(z / z0 - 1) < 0.02, (z, z0)
+
+
+def test_line_impedance_independent_of_direction():
+    """the same line along two oblique directions: the in-cell radius of
+    off-node segments and the charge-conserving coupling keep V / I within
+    1 % of the axis-aligned line and within 2 % of the closed form"""
+    dx, h, a = 0.1, 4, 0.002
+    z0 = _z0_two_planes(h * dx, GRID[2] * dx, a)
+    z_axis = _line_impedance((1, 0, 0), n=GRID, h=h, a=a, dx=dx)
+    for d in ((2, 1, 0), (1, 1, 0)):
+        z = _line_impedance(d, n=GRID, h=h, a=a, dx=dx)
+        assert abs(z / z_axis - 1) < 0.01, (d, z, z_axis)
+        assert abs(z / z0 - 1) < 0.02, (d, z, z0)
