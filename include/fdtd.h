@@ -79,7 +79,8 @@ enum {
     FDTD_PROBE_V = 0,     /* voltage -sum E_axis dx over n_edges edges from node (i,j,k) along +axis, at t_{n+1} */
     FDTD_PROBE_I = 1,     /* current: loop integral of H around the edge from node (i,j,k) along +axis, at t_{n+1/2} */
     FDTD_PROBE_E = 2,     /* E component `axis` owned by cell (i,j,k), at t_{n+1} */
-    FDTD_PROBE_H = 3      /* H component `axis` owned by cell (i,j,k), at t_{n+1/2} */
+    FDTD_PROBE_H = 3,     /* H component `axis` owned by cell (i,j,k), at t_{n+1/2} */
+    FDTD_PROBE_WIRE = 4   /* current of one oblique-wire segment, at t_{n+1/2} (fdtd_add_wire_probe) */
 };
 
 /* Create a grid of nx*ny*nz cells of edge dx metres.  The time step is
@@ -134,6 +135,55 @@ int fdtd_add_wire(fdtd_grid *g, int i0, int j0, int k0, int i1, int j1, int k1,
  * number of wires added. */
 int fdtd_add_wire_path(fdtd_grid *g, int i0, int j0, int k0, int i1, int j1, int k1, double radius,
                        int *n_segments);
+
+/* Oblique thin wire (Sec. 2.3: the Guiffaut formalism the paper cites for
+ * arbitrarily oriented wires and multiwire junctions; the paper prints none
+ * of its equations, and this is the Holland-Simpson form of it).  A straight
+ * wire from point (x0,y0,z0) to (x1,y1,z1) in node units (node (i,j,k) sits
+ * at (i dx, j dx, k dx); any real coordinates in [0, n] per axis), length
+ * >= 0.5 cell, radius 0 < radius <= 0.1 dx metres, split into
+ * max(1, round(length in cells)) equal segments.  It carries its own
+ * unknowns: a current per segment (t_{n+1/2}) and a charge per node (t_n),
+ * with in-cell inductance, capacitance and leakage per unit length
+ * mu ln(R/a) / (2 pi), 2 pi eps / ln(R/a), 2 pi sigma / ln(R/a), R the
+ * radius at which the grid itself sees a line current at the segment's
+ * sub-cell position (from the square-lattice Green's function), and the
+ * medium of the cell holding the segment's centre or the node.  The grid
+ * and the wire exchange E^n and the segment currents through the same edge
+ * shares, those of the charge-conserving (Villasenor-Buneman) deposition of
+ * the straight path between the segment's end nodes.  An end point equal
+ * (within 1e-9) to a node of an earlier oblique wire joins that node
+ * (junction: the currents of all segments at a node change its charge).  A
+ * node on an outer wall is grounded (potential 0).  Not allowed with Debye
+ * media (fdtd_finalize fails with FDTD_EINVAL) or in batches
+ * (fdtd_batch_create fails).  *wire_id (may be NULL) receives the index. */
+int fdtd_add_oblique_wire(fdtd_grid *g, double x0, double y0, double z0, double x1, double y1, double z1,
+                          double radius, int *wire_id);
+
+/* Delta-gap EMF in segment `segment` (0-based from the wire's first point)
+ * of oblique wire `wire_id`: voltage[n] volts at t_n (0 after the last
+ * sample) drive the segment's current from its first towards its second
+ * point.  voltage (n doubles, host) is copied and rounded to FP32.
+ * *source_id (may be NULL) receives the index among such sources. */
+int fdtd_add_wire_voltage_source(fdtd_grid *g, int wire_id, int segment, const double *voltage, int n,
+                                 int *source_id);
+
+/* Probe of the current of one oblique-wire segment at t_{n+1/2} (positive
+ * from the wire's first point towards its second), read with
+ * fdtd_read_probes; probe ids are shared with fdtd_add_probe. */
+int fdtd_add_wire_probe(fdtd_grid *g, int wire_id, int segment, int *probe_id);
+
+/* Number of oblique-wire segments and nodes (all wires, in the order
+ * added; a wire's segments are consecutive, its interior nodes follow its
+ * first point's node unless that point joined an earlier node). */
+int fdtd_wire_counts(const fdtd_grid *g, int *n_segments, int *n_nodes);
+
+/* Oblique-wire state after fdtd_finalize: I = segment currents of the last
+ * half step (A, n_segments floats), Q = node charges (C, n_nodes floats);
+ * host buffers.  get synchronises the grid's stream; set writes grounded
+ * nodes as 0. */
+int fdtd_get_wire_state(fdtd_grid *g, float *I, float *Q);
+int fdtd_set_wire_state(fdtd_grid *g, const float *I, const float *Q);
 
 /* Current source (Sec. 2.1 sources: ideal and non-ideal current sources;
  * "source(current, ...)" in the Sec. 4 model files) on the edge from node
@@ -293,8 +343,8 @@ int fdtd_selftest_wait(double seconds, void *cuda_stream);
 /* Checkpoint / resume of a finalized grid (a library addition; the paper's
  * solver has no counterpart).  The state is everything the step reads that
  * changes while stepping: the six fields, the twelve CPML auxiliaries (when
- * the grid has a CPML), the probe record [n_probes x probe_capacity] and the
- * step count.  Stepping a grid after fdtd_load_state continues bit for bit
+ * the grid has a CPML), the Debye currents, the oblique-wire currents and
+ * charges, the probe record [n_probes x probe_capacity] and the step count.  Stepping a grid after fdtd_load_state continues bit for bit
  * as the grid that saved the state did.
  *   fdtd_save_state: host_buf NULL -> *bytes = the size needed, FDTD_OK;
  *     otherwise *bytes is the buffer size on entry (FDTD_EINVAL, with the

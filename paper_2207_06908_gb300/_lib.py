@@ -86,6 +86,12 @@ def load():
             "fdtd_add_voltage_source": (I, [P, I, I, I, I, ctypes.c_double, P, I, P]),
             "fdtd_add_lumped": (I, [P, I, I, I, I, ctypes.c_double, ctypes.c_double, P]),
             "fdtd_add_wire_path": (I, [P, I, I, I, I, I, I, ctypes.c_double, P]),
+            "fdtd_add_oblique_wire": (I, [P, D, D, D, D, D, D, D, ip]),
+            "fdtd_add_wire_voltage_source": (I, [P, I, I, P, I, ip]),
+            "fdtd_add_wire_probe": (I, [P, I, I, ip]),
+            "fdtd_wire_counts": (I, [P, ip, ip]),
+            "fdtd_get_wire_state": (I, [P, P, P]),
+            "fdtd_set_wire_state": (I, [P, P, P]),
             "fdtd_save_state": (I, [P, P, ctypes.POINTER(ctypes.c_size_t)]),
             "fdtd_load_state": (I, [P, P, ctypes.c_size_t]),
             "fdtd_mlp_forward": (I, [P, I, I, I, P, P, I, I, P, P, P, P]),

@@ -3,6 +3,11 @@
 // ("calculate": voltage = -sum E dl along a path, current = loop integral of
 // H around an edge), applied right after the step kernel (and, with Debye
 // media, the dispersive-media kernel) of the same step.
+// Oblique thin wires (Sec. 2.3, the Guiffaut formalism read in
+// Holland-Simpson form) advance here too, before the sources: segment
+// currents to t_{n+1/2} from E^n gathered along each segment and the node
+// potentials, the currents into E^{n+1} through the same edge shares, node
+// charges to t_{n+1}.
 // One CTA; a device-side step counter indexes the source samples and the
 // probe slots, so the launch can be replayed inside a CUDA graph.
 #include "fdtd_internal.h"
@@ -15,12 +20,56 @@ __device__ __forceinline__ long long eidx(const EdgeArgs &a, int i, int j, int k
     return (long long)k * a.plane + (long long)j * a.pitch + i;
 }
 
+// one step of the oblique wires (all threads of the CTA); every sum runs
+// in a fixed order, so a run repeats bit for bit
+__device__ __forceinline__ void wire_body(const EdgeArgs &a, long long n)
+{
+    const WireArgs &w = a.w;
+    // L' dI/dt = E_s - dV/dl + EMF / dl, centred at t_n
+    for (int s = threadIdx.x; s < w.n_seg; s += blockDim.x) {
+        const OSeg sg = w.seg[s];
+        float es = 0.f;
+        for (int e = sg.e0; e < sg.e0 + sg.ne; ++e) {
+            const OEdge ed = w.edge[e];
+            es += ed.wg * a.Ein[ed.comp][ed.idx];
+        }
+        const ONode na = w.node[sg.a], nb = w.node[sg.b];
+        const float va = na.grounded ? 0.f : na.cV * w.Q[sg.a];
+        const float vb = nb.grounded ? 0.f : nb.cV * w.Q[sg.b];
+        float I = w.I[s] + (sg.cI * es - sg.cIV * (vb - va));
+        for (int q = sg.s0; q < sg.s0 + sg.ns; ++q) {
+            const OSrc sr = w.src[q];
+            if (n < sr.n) I += sr.cIV * w.samples[sr.off + n];
+        }
+        w.I[s] = I;
+    }
+    __syncthreads();
+    // the segment currents in Ampere's law at t_{n+1/2}; dQ/dt = net current in
+    for (int u = threadIdx.x; u < w.n_scat; u += blockDim.x) {
+        const OScat sc = w.scat[u];
+        float sum = 0.f;
+        for (int t = sc.t0; t < sc.t0 + sc.nt; ++t) sum += w.term[t].ws * w.I[w.term[t].seg];
+        a.E[sc.comp][sc.idx] -= sum;
+    }
+    for (int m = threadIdx.x; m < w.n_node; m += blockDim.x) {
+        const ONode nd = w.node[m];
+        float net = 0.f;
+        for (int q = nd.adj0; q < nd.adj0 + nd.nadj; ++q) {
+            const int t = w.adj[q];
+            net += (t & 1) ? w.I[t >> 1] : -w.I[t >> 1];
+        }
+        w.Q[m] = nd.grounded ? 0.f : nd.aQ * w.Q[m] + nd.bQ * net;
+    }
+    __syncthreads();
+}
+
 __device__ __forceinline__ void edge_body(const EdgeArgs &a)
 {
     __shared__ long long n_s;
     if (threadIdx.x == 0) n_s = *a.step;
     __syncthreads();
     const long long n = n_s;
+    if (a.w.n_seg > 0) wire_body(a, n);
     for (int q = threadIdx.x; q < a.n_src; q += blockDim.x) {
         const SourceDesc sd = a.src[q];
         if (sd.hard) continue;
@@ -54,7 +103,9 @@ __device__ __forceinline__ void edge_body(const EdgeArgs &a)
         for (int p = threadIdx.x; p < a.n_probes; p += blockDim.x) {
             const ProbeDesc pr = a.probes[p];
             float v = 0.f;
-            if (pr.kind == 2) {
+            if (pr.kind == 4) {
+                v = a.w.I[pr.i];                // oblique-wire segment current
+            } else if (pr.kind == 2) {
                 v = a.E[pr.axis][eidx(a, pr.i, pr.j, pr.k)];
             } else if (pr.kind == 3) {
                 v = a.H[pr.axis][eidx(a, pr.i, pr.j, pr.k)];
@@ -91,7 +142,7 @@ __global__ void edge_batch_kernel(const EdgeArgs *e, int parity)
     __shared__ EdgeArgs a;
     if (threadIdx.x == 0) a = e[2 * blockIdx.x + parity];
     __syncthreads();
-    if (a.n_src > 0 || a.n_probes > 0) edge_body(a);
+    if (a.n_src > 0 || a.n_probes > 0 || a.w.n_seg > 0) edge_body(a);
 }
 
 }  // namespace

@@ -151,6 +151,53 @@ struct ProbeDesc {
     int i, j, k, n_edges;
 };
 
+// Oblique thin wires (Sec. 2.3, the Guiffaut formalism in Holland-Simpson
+// form): segment currents I_s (t_{n+1/2}) and node charges Q_m (t_n).
+struct OSeg {
+    int a, b;                // end nodes; I flows a -> b
+    int e0, ne;              // gather edges e0 .. e0+ne-1
+    int s0, ns;              // its delta-gap sources s0 .. s0+ns-1
+    float cI, cIV;           // dt / L', dt / (L' dl)
+};
+struct OEdge {
+    long long idx;           // element index in the field arrays
+    int comp;                // E component
+    float wg;                // E_s += wg E
+};
+struct OScat {               // one coupled edge: E -= sum over its terms of ws I_seg
+    long long idx;
+    int comp;
+    int t0, nt;              // terms t0 .. t0+nt-1, in segment order
+};
+struct OTerm {
+    int seg;
+    float ws;
+};
+struct ONode {
+    float cV, aQ, bQ;        // V = cV Q; Q^{n+1} = aQ Q^n + bQ (net current in)
+    int grounded;
+    int adj0, nadj;          // adjacency entries (segment << 1 | current flows in)
+};
+struct OSrc {
+    int n;                   // samples (V at t_n)
+    long long off;           // offset into the wire sample table
+    float cIV;               // dt / (L' dl) of its segment
+};
+struct WireArgs {
+    const OSeg *seg;
+    int n_seg;
+    const OEdge *edge;
+    const OScat *scat;
+    int n_scat;
+    const OTerm *term;
+    const ONode *node;
+    int n_node;
+    const int *adj;
+    float *I, *Q;
+    const OSrc *src;
+    const float *samples;
+};
+
 struct EdgeArgs {
     int nx, ny, nz, pitch;
     long long plane;
@@ -168,6 +215,8 @@ struct EdgeArgs {
     float *J;                // Debye currents (sources on dispersive edges), or null
     long long jstride;
     int npoles;
+    const float *Ein[3];     // E^n, the step's input (oblique wires read it)
+    WireArgs w;              // oblique wires (n_seg = 0: none)
 };
 
 // fdtd_step.cu

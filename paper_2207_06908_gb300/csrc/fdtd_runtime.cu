@@ -33,6 +33,19 @@ struct Wire { int axis, p[3], n; double radius; };
 struct Source { int axis, p[3]; std::vector<float> cur; int hard = 0; };   // hard: ideal voltage source
 struct Lump { int axis, p[3]; double e_add, s_add; };                      // extra eps (F/m), sigma (S/m) on an edge
 
+// Oblique thin wires: geometry fixed when a wire is added.  Edge shares W
+// (cell units, signed) per segment, keyed by E component and edge position.
+struct OEdgeH { int comp, q[3]; double W; };
+struct OSegH {
+    int a, b;                 // end nodes; I flows a -> b
+    double dl, lam;           // length (m), ln(R / radius)
+    int cell[3];              // cell holding the centre (its mu)
+    std::vector<OEdgeH> edges;
+};
+struct ONodeH { double p[3]; int grounded; };
+struct OWireH { int seg0, nseg; };
+struct OSrcH { int seg; std::vector<float> emf; };
+
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 }  // namespace
@@ -90,6 +103,10 @@ struct fdtd_grid {
     std::vector<Source> srcs;
     std::vector<Lump> lumps;
     std::vector<fdtd::ProbeDesc> probes;
+    std::vector<OWireH> owires;
+    std::vector<OSegH> osegs;
+    std::vector<ONodeH> onodes;
+    std::vector<OSrcH> osrcs;
     bool finalized = false;
     int capacity = 0;
     int pitch = 0;
@@ -139,6 +156,17 @@ struct fdtd_grid {
     // element and the record table
     int npoles = 0, dz0 = 0, dz1 = 0, n_drec = 0;
     float *J = nullptr;
+    // oblique wires on the device
+    fdtd::OSeg *oseg_d = nullptr;
+    fdtd::OEdge *oedge_d = nullptr;
+    fdtd::OScat *oscat_d = nullptr;
+    fdtd::OTerm *oterm_d = nullptr;
+    int n_oscat = 0;
+    fdtd::ONode *onode_d = nullptr;
+    int *oadj_d = nullptr;
+    float *oI_d = nullptr, *oQ_d = nullptr;
+    fdtd::OSrc *osrc_d = nullptr;
+    float *osamp_d = nullptr;
     uint8_t *dcls_d = nullptr;
     float *dtable_d = nullptr;
     cudaGraphExec_t graph = nullptr;
@@ -161,7 +189,7 @@ int cuda_fail(fdtd_grid *g, cudaError_t e, const char *what)
 // ---- device arena plan -------------------------------------------------
 struct Plan {
     size_t field, cls, table, prof[3], psi[fdtd::PSI_COUNT], src, samples, probes, out, step, work, slot, items,
-        J, dcls, dtable, total;
+        J, dcls, dtable, oseg, oedge, oscat, oterm, onode, oadj, oI, oQ, osrc, osamp, total;
 };
 
 // poles used by the grid (the largest pole count of a material some cell
@@ -223,6 +251,20 @@ Plan make_plan(const fdtd_grid *g, int capacity)
     p.J = take(std::max<size_t>(1, 3 * (size_t)P * box) * sizeof(float));
     p.dcls = take(std::max<size_t>(1, box));
     p.dtable = take(fdtd::kMaxClasses * fdtd::kDebyeRec * sizeof(float));
+    size_t n_edge = 0, n_samp = 0;
+    for (const OSegH &sg : g->osegs) n_edge += sg.edges.size();
+    for (const OSrcH &sr : g->osrcs) n_samp += sr.emf.size();
+    const size_t n_os = std::max<size_t>(1, g->osegs.size()), n_on = std::max<size_t>(1, g->onodes.size());
+    p.oseg = take(n_os * sizeof(fdtd::OSeg));
+    p.oedge = take(std::max<size_t>(1, n_edge) * sizeof(fdtd::OEdge));
+    p.oscat = take(std::max<size_t>(1, n_edge) * sizeof(fdtd::OScat));
+    p.oterm = take(std::max<size_t>(1, n_edge) * sizeof(fdtd::OTerm));
+    p.onode = take(n_on * sizeof(fdtd::ONode));
+    p.oadj = take(2 * n_os * sizeof(int));
+    p.oI = take(n_os * sizeof(float));
+    p.oQ = take(n_on * sizeof(float));
+    p.osrc = take(std::max<size_t>(1, g->osrcs.size()) * sizeof(fdtd::OSrc));
+    p.osamp = take(std::max<size_t>(1, n_samp) * sizeof(float));
     p.total = off;
     return p;
 }
@@ -307,6 +349,164 @@ WireMods wire_mods(const fdtd_grid *g)
         }
     }
     return w;
+}
+
+
+// ---- oblique thin wires ---------------------------------------------------
+// Radius at which the grid itself sees the current of a segment: the line
+// lattice of the segment's dominant axis carries it spread bilinearly over
+// the four lines around its centre, and on the square lattice the potential
+// of a unit line current falls off as ln(r / r0) / (2 pi) with r0 =
+// exp(-gamma) / (2 sqrt 2) cells, while lines one spacing apart interact
+// 1/4 less and diagonal ones 1/pi less than a line with itself.
+double lattice_radius(double dx, const double c[3], const double t[3])
+{
+    int u = 0;
+    for (int v = 1; v < 3; ++v)
+        if (std::fabs(t[v]) > std::fabs(t[u])) u = v;
+    const double f1 = c[(u + 1) % 3] - std::floor(c[(u + 1) % 3]);
+    const double f2 = c[(u + 2) % 3] - std::floor(c[(u + 2) % 3]);
+    const double w[4] = {(1 - f1) * (1 - f2), f1 * (1 - f2), (1 - f1) * f2, f1 * f2};   // (0,0) (1,0) (0,1) (1,1)
+    const double side = w[0] * w[1] + w[2] * w[3] + w[0] * w[2] + w[1] * w[3];
+    const double diag = w[0] * w[3] + w[1] * w[2];
+    const double S = 2.0 * (0.25 * side + diag / M_PI);
+    return dx * std::exp(-0.57721566490153286) / (2.0 * std::sqrt(2.0)) * std::exp(2.0 * M_PI * S);
+}
+
+// Edge shares of the straight path pa -> pb (node units): cut at every cell
+// face it crosses; a piece with displacement dd and midpoint fractions fr in
+// its cell gives the edge of component c at the two transverse offsets
+// (dv, dw) the share dd_c (w_v w_w +- dd_v dd_w / 12) (+ where dv == dw),
+// which makes the grid's discrete divergence of the edge currents equal the
+// move of a unit charge between the trilinear node weights of the piece's
+// ends (the charge-conserving deposition of particle codes).  Edges the E
+// update never touches (the walls) are left out.
+std::vector<OEdgeH> path_edges(const fdtd_grid *g, const double pa[3], const double pb[3])
+{
+    std::vector<double> cut{0.0, 1.0};
+    for (int a = 0; a < 3; ++a) {
+        const double lo = std::min(pa[a], pb[a]), hi = std::max(pa[a], pb[a]);
+        for (double x = std::floor(lo) + 1.0; x < hi; x += 1.0) cut.push_back((x - pa[a]) / (pb[a] - pa[a]));
+    }
+    std::sort(cut.begin(), cut.end());
+    const int n[3] = {g->nx, g->ny, g->nz};
+    std::map<std::array<int, 4>, double> share;
+    for (size_t q = 0; q + 1 < cut.size(); ++q) {
+        if (!(cut[q + 1] > cut[q])) continue;
+        double dd[3], fr[3];
+        int cell[3];
+        for (int a = 0; a < 3; ++a) {
+            const double x0 = pa[a] + cut[q] * (pb[a] - pa[a]), x1 = pa[a] + cut[q + 1] * (pb[a] - pa[a]);
+            const double mid = 0.5 * (x0 + x1);
+            dd[a] = x1 - x0;
+            cell[a] = std::min((int)std::floor(mid), n[a] - 1);
+            fr[a] = mid - cell[a];
+        }
+        for (int c = 0; c < 3; ++c) {
+            if (dd[c] == 0.0) continue;
+            const int v = (c + 1) % 3, w = (c + 2) % 3;
+            for (int dv = 0; dv < 2; ++dv)
+                for (int dw = 0; dw < 2; ++dw) {
+                    const double W = dd[c] * ((dv ? fr[v] : 1.0 - fr[v]) * (dw ? fr[w] : 1.0 - fr[w]) +
+                                              (dv == dw ? 1.0 : -1.0) * dd[v] * dd[w] / 12.0);
+                    int e[3];
+                    e[c] = cell[c];
+                    e[v] = cell[v] + dv;
+                    e[w] = cell[w] + dw;
+                    if (W != 0.0 && e_updated(g, c, e)) share[{c, e[0], e[1], e[2]}] += W;
+                }
+        }
+    }
+    std::vector<OEdgeH> out;
+    for (const auto &kv : share) out.push_back(OEdgeH{kv.first[0], {kv.first[1], kv.first[2], kv.first[3]}, kv.second});
+    return out;
+}
+
+struct WireDev {
+    std::vector<fdtd::OSeg> seg;
+    std::vector<fdtd::OEdge> edge;
+    std::vector<fdtd::OScat> scat;
+    std::vector<fdtd::OTerm> term;
+    std::vector<fdtd::ONode> node;
+    std::vector<int> adj;
+    std::vector<fdtd::OSrc> src;
+    std::vector<float> samples;
+};
+
+// in-cell parameters (Sec. 2.3 oblique wires, per unit length: L' = mu ln(R/a)
+// / (2 pi) on a segment, C' = 2 pi eps / ln(R/a) and G' = 2 pi sigma /
+// ln(R/a) at a node, with the node's ln(R/a) the mean of its segments') and
+// coupling coefficients; cb of each coupling edge from the class table.
+// The scatter is transposed to one entry per coupled edge with its segments
+// in order, and each segment lists its sources, so the device sums in a
+// fixed order.
+WireDev wire_device(const fdtd_grid *g, const std::vector<uint8_t> &cls, const std::vector<float> &table)
+{
+    WireDev d;
+    const double dx = g->dx, dt = g->dt;
+    const int n[3] = {g->nx, g->ny, g->nz};
+    auto material = [&](const int c[3]) -> const fdtd_material & {
+        return g->table[g->mat[((size_t)c[2] * g->ny + c[1]) * g->nx + c[0]]];
+    };
+    std::vector<double> lam(g->onodes.size(), 0.0), dlm(g->onodes.size(), 0.0);
+    std::vector<int> deg(g->onodes.size(), 0);
+    std::vector<std::vector<int>> adj(g->onodes.size());
+    std::vector<std::vector<int>> seg_src(g->osegs.size());
+    for (size_t q = 0; q < g->osrcs.size(); ++q) seg_src[g->osrcs[q].seg].push_back((int)q);
+    std::map<std::pair<int, long long>, std::vector<fdtd::OTerm>> scat;   // (comp, idx) -> terms
+    for (size_t s = 0; s < g->osegs.size(); ++s) {
+        const OSegH &sg = g->osegs[s];
+        const double Lp = kMu0 * material(sg.cell).mu_r * sg.lam / (2.0 * M_PI);
+        fdtd::OSeg o{};
+        o.a = sg.a;
+        o.b = sg.b;
+        o.e0 = (int)d.edge.size();
+        o.ne = (int)sg.edges.size();
+        o.cI = (float)(dt / Lp);
+        o.cIV = (float)(dt / (Lp * sg.dl));
+        for (const OEdgeH &e : sg.edges) {
+            const long long idx = (long long)e.q[2] * g->plane + (long long)e.q[1] * g->pitch + e.q[0];
+            const double cb = table[(size_t)cls[idx] * fdtd::kNumCoef + 3 + e.comp];
+            d.edge.push_back(fdtd::OEdge{idx, e.comp, (float)(e.W * dx / sg.dl)});
+            scat[{e.comp, idx}].push_back(fdtd::OTerm{(int)s, (float)(cb * e.W / dx)});
+        }
+        o.s0 = (int)d.src.size();
+        o.ns = (int)seg_src[s].size();
+        for (int q : seg_src[s]) {
+            const OSrcH &sr = g->osrcs[q];
+            d.src.push_back(fdtd::OSrc{(int)sr.emf.size(), (long long)d.samples.size(), o.cIV});
+            d.samples.insert(d.samples.end(), sr.emf.begin(), sr.emf.end());
+        }
+        d.seg.push_back(o);
+        for (int end = 0; end < 2; ++end) {
+            const int m = end ? sg.b : sg.a;
+            lam[m] += sg.lam;
+            dlm[m] += 0.5 * sg.dl;
+            deg[m] += 1;
+            adj[m].push_back((int)(s << 1) | end);
+        }
+    }
+    for (auto &kv : scat) {
+        d.scat.push_back(fdtd::OScat{kv.first.second, kv.first.first, (int)d.term.size(), (int)kv.second.size()});
+        d.term.insert(d.term.end(), kv.second.begin(), kv.second.end());
+    }
+    for (size_t m = 0; m < g->onodes.size(); ++m) {
+        const ONodeH &nd = g->onodes[m];
+        int c[3];
+        for (int a = 0; a < 3; ++a) c[a] = std::min((int)std::floor(nd.p[a]), n[a] - 1);
+        const fdtd_material &mt = material(c);
+        const double eps = kEps0 * mt.eps_r, r = mt.sigma * dt / (2.0 * eps);
+        fdtd::ONode o{};
+        o.cV = (float)(lam[m] / deg[m] / (2.0 * M_PI * eps * dlm[m]));
+        o.aQ = (float)((1.0 - r) / (1.0 + r));
+        o.bQ = (float)(dt / (1.0 + r));
+        o.grounded = nd.grounded;
+        o.adj0 = (int)d.adj.size();
+        o.nadj = (int)adj[m].size();
+        d.adj.insert(d.adj.end(), adj[m].begin(), adj[m].end());
+        d.node.push_back(o);
+    }
+    return d;
 }
 
 struct Coefs {
@@ -647,8 +847,24 @@ fdtd::EdgeArgs edge_args(const fdtd_grid *g, int parity)
     e.J = g->npoles ? g->J : nullptr;
     e.jstride = (long long)(g->dz1 - g->dz0) * g->plane;
     e.npoles = g->npoles;
+    for (int c = 0; c < 3; ++c) e.Ein[c] = g->F[parity][c];
+    e.w.seg = g->oseg_d;
+    e.w.n_seg = (int)g->osegs.size();
+    e.w.edge = g->oedge_d;
+    e.w.scat = g->oscat_d;
+    e.w.n_scat = g->n_oscat;
+    e.w.term = g->oterm_d;
+    e.w.node = g->onode_d;
+    e.w.n_node = (int)g->onodes.size();
+    e.w.adj = g->oadj_d;
+    e.w.I = g->oI_d;
+    e.w.Q = g->oQ_d;
+    e.w.src = g->osrc_d;
+    e.w.samples = g->osamp_d;
     return e;
 }
+
+bool has_edge_work(const fdtd_grid *g) { return !g->srcs.empty() || !g->probes.empty() || !g->osegs.empty(); }
 
 fdtd::DebyeArgs debye_args(const fdtd_grid *g, int parity)
 {
@@ -710,7 +926,7 @@ cudaError_t enqueue_step(fdtd_grid *g, int parity, cudaStream_t s)
     }
     if (e == cudaSuccess && g->npoles) e = fdtd::launch_debye(debye_args(g, parity), s);
     if (e != cudaSuccess) return e;
-    if (!g->srcs.empty() || !g->probes.empty()) e = fdtd::launch_edges(edge_args(g, parity), s);
+    if (has_edge_work(g)) e = fdtd::launch_edges(edge_args(g, parity), s);
     return e;
 }
 
@@ -874,7 +1090,7 @@ int step_with_scratch(fdtd_grid *g, int n, int *scratch, int scratch_ints)
             e = launch_step(single_args(g, g->parity, l), grid_launch(g, g->parity, l, scratch + 2 * l, g->noalloc_err),
                             g->lc[l].grid, g->stream);
         if (e == cudaSuccess && g->npoles) e = launch_debye(debye_args(g, g->parity), g->stream);
-        if (e == cudaSuccess && (!g->srcs.empty() || !g->probes.empty()))
+        if (e == cudaSuccess && has_edge_work(g))
             e = launch_edges(edge_args(g, g->parity), g->stream);
         if (e != cudaSuccess) return cuda_fail(g, e, "step launch");
         g->parity ^= 1;
@@ -1101,6 +1317,119 @@ int fdtd_add_probe(fdtd_grid *g, int kind, int i, int j, int k, int axis, int n_
     return FDTD_OK;
 }
 
+int fdtd_add_oblique_wire(fdtd_grid *g, double x0, double y0, double z0, double x1, double y1, double z1,
+                          double radius, int *wire_id)
+{
+    if (int rc = check_open(g, false)) return rc;
+    const double A[3] = {x0, y0, z0}, B[3] = {x1, y1, z1};
+    const int n[3] = {g->nx, g->ny, g->nz};
+    double len2 = 0.0;
+    for (int u = 0; u < 3; ++u) {
+        if (!(A[u] >= 0.0 && A[u] <= n[u] && B[u] >= 0.0 && B[u] <= n[u]))
+            return fail(g, FDTD_EINVAL, "oblique wire outside the grid");
+        len2 += (B[u] - A[u]) * (B[u] - A[u]);
+    }
+    const double len = std::sqrt(len2);
+    if (!(len >= 0.5)) return fail(g, FDTD_EINVAL, "oblique wire shorter than half a cell");
+    if (!(radius > 0.0) || radius > 0.1 * g->dx) return fail(g, FDTD_EINVAL, "oblique wire radius outside (0, 0.1 dx]");
+    const int N = (int)std::max(1L, std::lround(len));
+    auto node_at = [&](const double p[3]) {
+        for (size_t m = 0; m < g->onodes.size(); ++m)
+            if (std::fabs(g->onodes[m].p[0] - p[0]) < 1e-9 && std::fabs(g->onodes[m].p[1] - p[1]) < 1e-9 &&
+                std::fabs(g->onodes[m].p[2] - p[2]) < 1e-9)
+                return (int)m;
+        return -1;
+    };
+    auto new_node = [&](const double p[3]) {
+        ONodeH nd{{p[0], p[1], p[2]}, 0};
+        for (int u = 0; u < 3; ++u) nd.grounded |= (p[u] == 0.0 || p[u] == (double)n[u]);
+        g->onodes.push_back(nd);
+        return (int)g->onodes.size() - 1;
+    };
+    g->owires.push_back(OWireH{(int)g->osegs.size(), N});
+    int prev = node_at(A);
+    if (prev < 0) prev = new_node(A);
+    for (int sg = 0; sg < N; ++sg) {
+        double P[3], c[3], t[3];
+        for (int u = 0; u < 3; ++u) {
+            P[u] = sg == N - 1 ? B[u] : A[u] + (B[u] - A[u]) * (double)(sg + 1) / N;
+            c[u] = A[u] + (B[u] - A[u]) * (sg + 0.5) / N;
+            t[u] = (B[u] - A[u]) / len;
+        }
+        int next = sg == N - 1 ? node_at(B) : -1;
+        if (next < 0) next = new_node(P);
+        OSegH seg;
+        seg.a = prev;
+        seg.b = next;
+        seg.dl = len * g->dx / N;
+        seg.lam = std::log(lattice_radius(g->dx, c, t) / radius);
+        for (int u = 0; u < 3; ++u) seg.cell[u] = std::min((int)std::floor(c[u]), n[u] - 1);
+        const ONodeH pa = g->onodes[prev], pb = g->onodes[next];
+        seg.edges = path_edges(g, pa.p, pb.p);
+        g->osegs.push_back(std::move(seg));
+        prev = next;
+    }
+    if (wire_id) *wire_id = (int)g->owires.size() - 1;
+    return FDTD_OK;
+}
+
+int fdtd_add_wire_voltage_source(fdtd_grid *g, int wire_id, int segment, const double *voltage, int n,
+                                 int *source_id)
+{
+    if (int rc = check_open(g, false)) return rc;
+    if (wire_id < 0 || wire_id >= (int)g->owires.size() || segment < 0 || segment >= g->owires[wire_id].nseg)
+        return fail(g, FDTD_EINVAL, "no such oblique-wire segment");
+    if (n < 0 || (n > 0 && !voltage)) return fail(g, FDTD_EINVAL, "bad voltage samples");
+    OSrcH sr{g->owires[wire_id].seg0 + segment, std::vector<float>(voltage, voltage + n)};
+    g->osrcs.push_back(std::move(sr));
+    if (source_id) *source_id = (int)g->osrcs.size() - 1;
+    return FDTD_OK;
+}
+
+int fdtd_add_wire_probe(fdtd_grid *g, int wire_id, int segment, int *probe_id)
+{
+    if (int rc = check_open(g, false)) return rc;
+    if (wire_id < 0 || wire_id >= (int)g->owires.size() || segment < 0 || segment >= g->owires[wire_id].nseg)
+        return fail(g, FDTD_EINVAL, "no such oblique-wire segment");
+    g->probes.push_back(fdtd::ProbeDesc{FDTD_PROBE_WIRE, 0, g->owires[wire_id].seg0 + segment, 0, 0, 1});
+    if (probe_id) *probe_id = (int)g->probes.size() - 1;
+    return FDTD_OK;
+}
+
+int fdtd_wire_counts(const fdtd_grid *g, int *n_segments, int *n_nodes)
+{
+    if (!g || !n_segments || !n_nodes) return FDTD_EINVAL;
+    *n_segments = (int)g->osegs.size();
+    *n_nodes = (int)g->onodes.size();
+    return FDTD_OK;
+}
+
+int fdtd_get_wire_state(fdtd_grid *g, float *I, float *Q)
+{
+    if (int rc = check_open(g, true)) return rc;
+    if ((!I && !g->osegs.empty()) || (!Q && !g->onodes.empty())) return fail(g, FDTD_EINVAL, "null buffer");
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e == cudaSuccess && !g->osegs.empty())
+        e = cudaMemcpy(I, g->oI_d, g->osegs.size() * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && !g->onodes.empty())
+        e = cudaMemcpy(Q, g->oQ_d, g->onodes.size() * sizeof(float), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? FDTD_OK : cuda_fail(g, e, "wire state read");
+}
+
+int fdtd_set_wire_state(fdtd_grid *g, const float *I, const float *Q)
+{
+    if (int rc = check_open(g, true)) return rc;
+    if ((!I && !g->osegs.empty()) || (!Q && !g->onodes.empty())) return fail(g, FDTD_EINVAL, "null buffer");
+    std::vector<float> q(Q, Q + g->onodes.size());
+    for (size_t m = 0; m < q.size(); ++m)
+        if (g->onodes[m].grounded) q[m] = 0.f;       // grounded nodes hold no charge
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e == cudaSuccess && !g->osegs.empty())
+        e = cudaMemcpy(g->oI_d, I, g->osegs.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !q.empty()) e = cudaMemcpy(g->oQ_d, q.data(), q.size() * sizeof(float), cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? FDTD_OK : cuda_fail(g, e, "wire state write");
+}
+
 int fdtd_set_block(fdtd_grid *g, int planes)
 {
     if (int rc = check_open(g, false)) return rc;
@@ -1125,6 +1454,8 @@ int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_by
     std::vector<double> src_cb;
     std::vector<std::array<double, 3 * fdtd::kMaxPoles>> src_debye;
     if (int rc = build_classes(g, cls, table, src_cb, dcls, dtable, src_debye)) return rc;
+    if (!g->osegs.empty() && g->npoles)
+        return fail(g, FDTD_EINVAL, "oblique wires in dispersive media are not supported");
 
     const Plan p = make_plan(g, probe_capacity);
     if (arena) {
@@ -1162,6 +1493,16 @@ int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_by
     g->J = (float *)(base + p.J);
     g->dcls_d = (uint8_t *)(base + p.dcls);
     g->dtable_d = (float *)(base + p.dtable);
+    g->oseg_d = (fdtd::OSeg *)(base + p.oseg);
+    g->oedge_d = (fdtd::OEdge *)(base + p.oedge);
+    g->oscat_d = (fdtd::OScat *)(base + p.oscat);
+    g->oterm_d = (fdtd::OTerm *)(base + p.oterm);
+    g->onode_d = (fdtd::ONode *)(base + p.onode);
+    g->oadj_d = (int *)(base + p.oadj);
+    g->oI_d = (float *)(base + p.oI);
+    g->oQ_d = (float *)(base + p.oQ);
+    g->osrc_d = (fdtd::OSrc *)(base + p.osrc);
+    g->osamp_d = (float *)(base + p.osamp);
     g->capacity = probe_capacity;
 
 
@@ -1211,6 +1552,20 @@ int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_by
     if (e == cudaSuccess && !g->probes.empty())
         e = cudaMemcpyAsync(g->probes_d, g->probes.data(), g->probes.size() * sizeof(fdtd::ProbeDesc),
                             cudaMemcpyHostToDevice, s);
+    WireDev wd;
+    if (!g->osegs.empty()) wd = wire_device(g, cls, table);
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+    };
+    up(g->oseg_d, wd.seg.data(), wd.seg.size() * sizeof(fdtd::OSeg));
+    up(g->oedge_d, wd.edge.data(), wd.edge.size() * sizeof(fdtd::OEdge));
+    up(g->oscat_d, wd.scat.data(), wd.scat.size() * sizeof(fdtd::OScat));
+    up(g->oterm_d, wd.term.data(), wd.term.size() * sizeof(fdtd::OTerm));
+    g->n_oscat = (int)wd.scat.size();
+    up(g->onode_d, wd.node.data(), wd.node.size() * sizeof(fdtd::ONode));
+    up(g->oadj_d, wd.adj.data(), wd.adj.size() * sizeof(int));
+    up(g->osrc_d, wd.src.data(), wd.src.size() * sizeof(fdtd::OSrc));
+    up(g->osamp_d, wd.samples.data(), wd.samples.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(g, e, "upload");
     if (int rc = setup_step_kernel(g)) return rc;
@@ -1347,10 +1702,10 @@ int fdtd_num_classes(const fdtd_grid *g) { return g ? g->n_classes : -1; }
 // ---- checkpoint / resume ----------------------------------------------------
 namespace {
 constexpr uint32_t kStateMagic = 0x53544446u;     // "FDTS"
-constexpr uint32_t kStateVersion = 2;
+constexpr uint32_t kStateVersion = 3;
 struct StateHeader {
     uint32_t magic, version;
-    int32_t nx, ny, nz, d, n_probes, capacity, n_psi, npoles, dz0, dz1;
+    int32_t nx, ny, nz, d, n_probes, capacity, n_psi, npoles, dz0, dz1, n_oseg, n_onode;
     int64_t step;
 };
 
@@ -1360,7 +1715,8 @@ size_t state_bytes(const fdtd_grid *g, int n_psi)
 {
     const size_t cells = (size_t)g->nx * g->ny * g->nz;
     return sizeof(StateHeader) + (6 + (size_t)n_psi) * cells * sizeof(float) +
-           g->probes.size() * (size_t)g->capacity * sizeof(float) + debye_elems(g) * sizeof(float);
+           g->probes.size() * (size_t)g->capacity * sizeof(float) + debye_elems(g) * sizeof(float) +
+           (g->osegs.size() + g->onodes.size()) * sizeof(float);
 }
 
 // one cell-owned array between host (dense) and device (row pitch)
@@ -1389,7 +1745,8 @@ int fdtd_save_state(fdtd_grid *g, void *host_buf, size_t *bytes)
     }
     if (int rc = fdtd_synchronize(g)) return rc;
     StateHeader h{kStateMagic, kStateVersion, g->nx, g->ny, g->nz, g->d, (int32_t)g->probes.size(), g->capacity,
-                  n_psi, g->npoles, g->dz0, g->dz1, (int64_t)g->step};
+                  n_psi, g->npoles, g->dz0, g->dz1, (int32_t)g->osegs.size(), (int32_t)g->onodes.size(),
+                  (int64_t)g->step};
     char *p = static_cast<char *>(host_buf);
     std::memcpy(p, &h, sizeof h);
     p += sizeof h;
@@ -1401,6 +1758,12 @@ int fdtd_save_state(fdtd_grid *g, void *host_buf, size_t *bytes)
     if (e == cudaSuccess && pbytes) e = cudaMemcpy(p, g->probe_out, pbytes, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && debye_elems(g))
         e = cudaMemcpy(p + pbytes, g->J, debye_elems(g) * sizeof(float), cudaMemcpyDeviceToHost);
+    char *pw = p + pbytes + debye_elems(g) * sizeof(float);
+    if (e == cudaSuccess && !g->osegs.empty())
+        e = cudaMemcpy(pw, g->oI_d, g->osegs.size() * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && !g->onodes.empty())
+        e = cudaMemcpy(pw + g->osegs.size() * sizeof(float), g->oQ_d, g->onodes.size() * sizeof(float),
+                       cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(g, e, "state copy");
     *bytes = need;
     return FDTD_OK;
@@ -1416,7 +1779,7 @@ int fdtd_load_state(fdtd_grid *g, const void *host_buf, size_t bytes)
     if (h.magic != kStateMagic || h.version != kStateVersion) return fail(g, FDTD_EINVAL, "not a saved state");
     if (h.nx != g->nx || h.ny != g->ny || h.nz != g->nz || h.d != g->d || h.n_probes != (int)g->probes.size() ||
         h.capacity != g->capacity || h.n_psi != n_psi || h.npoles != g->npoles || h.dz0 != g->dz0 ||
-        h.dz1 != g->dz1 || h.step < 0)
+        h.dz1 != g->dz1 || h.n_oseg != (int)g->osegs.size() || h.n_onode != (int)g->onodes.size() || h.step < 0)
         return fail(g, FDTD_EINVAL, "state was saved from a differently shaped grid");
     if (bytes < state_bytes(g, n_psi)) return fail(g, FDTD_EINVAL, "state truncated");
     if (int rc = fdtd_synchronize(g)) return rc;
@@ -1430,6 +1793,12 @@ int fdtd_load_state(fdtd_grid *g, const void *host_buf, size_t bytes)
     if (e == cudaSuccess && pbytes) e = cudaMemcpy(g->probe_out, q, pbytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && debye_elems(g))
         e = cudaMemcpy(g->J, q + pbytes, debye_elems(g) * sizeof(float), cudaMemcpyHostToDevice);
+    const char *qw = q + pbytes + debye_elems(g) * sizeof(float);
+    if (e == cudaSuccess && !g->osegs.empty())
+        e = cudaMemcpy(g->oI_d, qw, g->osegs.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !g->onodes.empty())
+        e = cudaMemcpy(g->oQ_d, qw + g->osegs.size() * sizeof(float), g->onodes.size() * sizeof(float),
+                       cudaMemcpyHostToDevice);
     const long long step = h.step;
     if (e == cudaSuccess) e = cudaMemcpy(g->step_d, &step, sizeof step, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(g, e, "state copy");
@@ -1534,6 +1903,7 @@ int fdtd_batch_create(int n, fdtd_grid *const *grids, void *cuda_stream, fdtd_ba
         fdtd_grid *g = grids[q];
         if (!g || !g->finalized) { delete b; return FDTD_ESTATE; }
         if (g->npoles) { delete b; return FDTD_EINVAL; }      // dispersive media run on their own
+        if (!g->osegs.empty()) { delete b; return FDTD_EINVAL; }   // so do oblique wires
         if (g->parity != grids[0]->parity || g->step != grids[0]->step) { delete b; return FDTD_ESTATE; }
         b->grids.push_back(g);
     }

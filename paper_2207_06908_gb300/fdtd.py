@@ -15,7 +15,7 @@ from . import _lib
 from ._lib import CpmlParams, FdtdError, Material, check
 
 EX, EY, EZ, HX, HY, HZ = range(6)
-PROBE_V, PROBE_I, PROBE_E, PROBE_H = 0, 1, 2, 3
+PROBE_V, PROBE_I, PROBE_E, PROBE_H, PROBE_WIRE = 0, 1, 2, 3, 4
 
 
 def _stream_ptr(stream):
@@ -105,6 +105,54 @@ class Grid:
         check(self._lib, self._h, self._lib.fdtd_add_wire_path(self._h, *map(int, p0), *map(int, p1),
                                                                float(radius), ctypes.byref(n)), "add_wire_path")
         return n.value
+
+    def add_oblique_wire(self, p0, p1, radius):
+        """oblique thin wire between two points in node units (any real
+        coordinates); returns its id"""
+        wid = ctypes.c_int()
+        check(self._lib, self._h, self._lib.fdtd_add_oblique_wire(self._h, *map(float, p0), *map(float, p1),
+                                                                 float(radius), ctypes.byref(wid)),
+              "add_oblique_wire")
+        return wid.value
+
+    def add_wire_voltage_source(self, wire, segment, voltage):
+        """delta-gap EMF (V at t_n) in one segment of an oblique wire"""
+        v = np.ascontiguousarray(voltage, dtype=np.float64)
+        sid = ctypes.c_int()
+        check(self._lib, self._h, self._lib.fdtd_add_wire_voltage_source(
+            self._h, int(wire), int(segment), v.ctypes.data_as(ctypes.c_void_p), len(v), ctypes.byref(sid)),
+            "add_wire_voltage_source")
+        return sid.value
+
+    def add_wire_probe(self, wire, segment):
+        """current of one oblique-wire segment at t_{n+1/2}; returns the probe id"""
+        pid = ctypes.c_int()
+        check(self._lib, self._h, self._lib.fdtd_add_wire_probe(self._h, int(wire), int(segment),
+                                                               ctypes.byref(pid)), "add_wire_probe")
+        return pid.value
+
+    def wire_counts(self):
+        ns, nn = ctypes.c_int(), ctypes.c_int()
+        check(self._lib, self._h, self._lib.fdtd_wire_counts(self._h, ctypes.byref(ns), ctypes.byref(nn)),
+              "wire_counts")
+        return ns.value, nn.value
+
+    def get_wire_state(self):
+        """(segment currents of the last half step, node charges)"""
+        ns, nn = self.wire_counts()
+        I, Q = np.zeros(max(ns, 1), np.float32), np.zeros(max(nn, 1), np.float32)
+        check(self._lib, self._h, self._lib.fdtd_get_wire_state(self._h, I.ctypes.data_as(ctypes.c_void_p),
+                                                               Q.ctypes.data_as(ctypes.c_void_p)), "get_wire_state")
+        return I[:ns], Q[:nn]
+
+    def set_wire_state(self, I, Q):
+        ns, nn = self.wire_counts()
+        I = np.ascontiguousarray(I, dtype=np.float32)
+        Q = np.ascontiguousarray(Q, dtype=np.float32)
+        if I.shape != (ns,) or Q.shape != (nn,):
+            raise ValueError("wire state shapes do not match the wire counts")
+        check(self._lib, self._h, self._lib.fdtd_set_wire_state(self._h, I.ctypes.data_as(ctypes.c_void_p),
+                                                               Q.ctypes.data_as(ctypes.c_void_p)), "set_wire_state")
 
     def add_source(self, node, axis, current, r_internal=0.0):
         cur = np.ascontiguousarray(current, dtype=np.float64)
@@ -287,11 +335,17 @@ def from_scenario(sc, stream=None, probe_capacity=None, torch_arena=True, block=
         g.add_voltage_source(node, axis, volt, r)
     for node, axis, res, cap in getattr(sc, "lumped", None) or []:
         g.add_lumped(node, axis, res, cap)
+    for p0, p1, r in getattr(sc, "owires", None) or []:
+        g.add_oblique_wire(p0, p1, r)
+    for w, seg, volt in getattr(sc, "owire_sources", None) or []:
+        g.add_wire_voltage_source(w, seg, volt)
     for kind, node, axis, ne in sc.probes:
         g.add_probe(kind, node, axis, ne)
+    for w, seg in getattr(sc, "owire_probes", None) or []:
+        g.add_wire_probe(w, seg)
     g.finalize(sc.n_steps if probe_capacity is None else probe_capacity, torch_arena=torch_arena)
     return g
 
 
 __all__ = ["Grid", "Batch", "FdtdError", "from_scenario", "EX", "EY", "EZ", "HX", "HY", "HZ",
-           "PROBE_V", "PROBE_I", "PROBE_E", "PROBE_H"]
+           "PROBE_V", "PROBE_I", "PROBE_E", "PROBE_H", "PROBE_WIRE"]

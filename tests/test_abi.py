@@ -104,3 +104,57 @@ def test_too_many_classes_rejected_before_any_device_work():
         assert lib.fdtd_set_materials(h, cm.ctypes.data_as(ctypes.c_void_p), mats, 30) == -1
     finally:
         lib.fdtd_destroy(h)
+
+
+def test_oblique_wire_host_checks():
+    """Oblique wires (host only): argument checks, segment counts
+    (round(length in cells)), junctions join coinciding end points, the
+    segment and probe ids, and errors for bad segments."""
+    from paper_2207_06908_gb300 import _lib as L
+    lib = L.load()
+    h = ctypes.c_void_p()
+    assert lib.fdtd_create_grid(20, 18, 16, 0.1, 0.99, None, None, ctypes.byref(h)) == 0
+    try:
+        wid, ns, nn = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ok = lib.fdtd_add_oblique_wire
+        assert ok(h, 3.0, 4.0, 5.0, 3.0, 4.0, 5.2, 0.002, None) == -1          # shorter than half a cell
+        assert ok(h, 3.0, 4.0, 5.0, 21.0, 4.0, 5.0, 0.002, None) == -1         # leaves the grid
+        assert ok(h, 3.0, 4.0, 5.0, 9.0, 4.0, 5.0, 0.011, None) == -1          # radius above 0.1 dx
+        assert ok(h, 3.3, 4.1, 3.7, 11.2, 9.6, 8.4, 0.002, ctypes.byref(wid)) == 0 and wid.value == 0
+        assert lib.fdtd_wire_counts(h, ctypes.byref(ns), ctypes.byref(nn)) == 0
+        length = ((11.2 - 3.3) ** 2 + (9.6 - 4.1) ** 2 + (8.4 - 3.7) ** 2) ** 0.5
+        assert ns.value == round(length) and nn.value == ns.value + 1
+        assert ok(h, 11.2, 9.6, 8.4, 12.5, 3.2, 5.0, 0.003, ctypes.byref(wid)) == 0 and wid.value == 1
+        lib.fdtd_wire_counts(h, ctypes.byref(ns), ctypes.byref(nn))
+        assert nn.value == ns.value + 1                                        # one tree: the end point joined
+        assert ok(h, 5.0, 5.0, 0.0, 5.0, 5.0, 4.0, 0.004, None) == 0           # grounded on z = 0
+        v = (ctypes.c_double * 4)(1.0, 2.0, 3.0, 4.0)
+        sid, pid = ctypes.c_int(), ctypes.c_int()
+        assert lib.fdtd_add_wire_voltage_source(h, 1, 0, v, 4, ctypes.byref(sid)) == 0 and sid.value == 0
+        assert lib.fdtd_add_wire_voltage_source(h, 1, 99, v, 4, None) == -1
+        assert lib.fdtd_add_wire_voltage_source(h, 7, 0, v, 4, None) == -1
+        assert lib.fdtd_add_probe(h, 0, 2, 2, 2, 2, 1, ctypes.byref(pid)) == 0 and pid.value == 0
+        assert lib.fdtd_add_wire_probe(h, 0, 3, ctypes.byref(pid)) == 0 and pid.value == 1
+        assert lib.fdtd_add_wire_probe(h, 2, 4, None) == -1                    # the grounded wire has 4
+    finally:
+        lib.fdtd_destroy(h)
+
+
+def test_oblique_wires_rejected_in_dispersive_grids_before_device_work():
+    import numpy as np
+    from paper_2207_06908_gb300._lib import Material
+    from paper_2207_06908_gb300 import _lib as L
+    lib = L.load()
+    h = ctypes.c_void_p()
+    assert lib.fdtd_create_grid(12, 12, 12, 0.1, 0.99, None, None, ctypes.byref(h)) == 0
+    try:
+        cm = np.zeros(12 ** 3, np.uint8)
+        mats = (Material * 1)(Material(4.0, 0.001, 1.0))
+        assert lib.fdtd_set_materials(h, cm.ctypes.data_as(ctypes.c_void_p), mats, 1) == 0
+        deps, tau = (ctypes.c_double * 1)(5.0), (ctypes.c_double * 1)(1e-8)
+        assert lib.fdtd_set_debye(h, 0, 1, deps, tau) == 0
+        assert lib.fdtd_add_oblique_wire(h, 3.2, 3.1, 3.0, 8.5, 7.9, 6.0, 0.002, None) == 0
+        assert lib.fdtd_finalize(h, 0, None, 0) == -1
+        assert b"dispersive" in lib.fdtd_last_error(h)
+    finally:
+        lib.fdtd_destroy(h)

@@ -1,0 +1,131 @@
+"""Oblique thin wires (Sec. 2.3, the Guiffaut formalism in Holland-Simpson
+form) through the CUDA library against the FP64 oracle in parity mode:
+fields within 1e-5, probes and the wire currents and charges within 1e-4
+(relative L2), on ragged PEC and CPML grids with a three-branch junction, a
+grounded riser, a delta-gap EMF and wire probes; graph and direct stepping
+agree bit for bit, and a checkpoint resumes bit for bit."""
+import numpy as np
+import pytest
+
+from paper_2207_06908_gb300 import workloads as W
+from _scenario import oracle_from_scenario, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fdtd():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2207_06908_gb300 import fdtd as F
+    return F
+
+
+def owire_scenario(seed, n, cpml, steps, fields=True):
+    sc = W.random_scenario(seed, n=n, cpml=cpml, n_wires=0, n_sources=1, n_probes=4, n_steps=steps,
+                           fields=fields)
+    rng = np.random.default_rng(seed + 100)
+    lo = cpml + 1.5
+
+    def point():
+        return tuple(float(round(rng.uniform(lo, m - lo), 3)) for m in n)
+
+    J = point()
+    sc.owires = [(point(), J, 0.004), (J, point(), 0.002), (J, point(), 0.006)]
+    if cpml == 0:
+        x, y = float(round(rng.uniform(2, n[0] - 2), 3)), float(round(rng.uniform(2, n[1] - 2), 3))
+        sc.owires.append(((x, y, 0.0), (x, y, 3.0), 0.004))           # grounded on z = 0
+    t = np.arange(steps)
+    sc.owire_sources = [(0, 1, 200.0 * np.sin(0.07 * t) * (1 - np.exp(-t / 10.0)))]
+    sc.owire_probes = [(0, 0), (1, 1), (2, 0)]
+    return sc
+
+
+def compare(F, sc, steps, field_tol=1e-5):
+    g = F.from_scenario(sc, probe_capacity=steps)
+    if sc.fields is not None:
+        for c, f in enumerate(sc.fields):
+            g.set_field(c, f)
+    g.step(steps)
+    o = oracle_from_scenario(sc, parity=True)
+    o.step(steps)
+    for c in range(6):
+        ref = o.get_field(c)
+        if np.linalg.norm(ref) > 0:
+            assert rel_l2(g.get_field(c), ref) <= field_tol, c
+    n_probes = len(sc.probes) + len(sc.owire_probes)
+    for p in range(n_probes):
+        ref = o.read_probe(p)
+        if np.linalg.norm(ref) > 0:
+            assert rel_l2(g.read_probe(p), ref) <= 1e-4, p
+    I, Q = g.get_wire_state()
+    Io, Qo = o.get_wire_state()
+    assert I.shape == Io.shape and Q.shape == Qo.shape
+    assert rel_l2(I, Io) <= 1e-4
+    assert rel_l2(Q, Qo) <= 1e-4
+    assert float(np.max(np.abs(Io))) > 0
+    return g
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_oblique_wires_pec_ragged(fdtd, seed):
+    g = compare(fdtd, owire_scenario(seed, (19, 17, 15), 0, 60), 60)
+    g.close()
+
+
+def test_oblique_wires_cpml(fdtd):
+    g = compare(fdtd, owire_scenario(5, (27, 22, 20), 4, 50), 50)
+    g.close()
+
+
+def test_oblique_wires_from_rest_driven_by_the_emf(fdtd):
+    """no initial fields: everything comes from the delta-gap EMF"""
+    g = compare(fdtd, owire_scenario(9, (24, 21, 18), 0, 150, fields=False), 150)
+    g.close()
+
+
+def test_oblique_wires_graph_direct_and_checkpoint_bitwise(fdtd):
+    sc = owire_scenario(3, (20, 18, 16), 0, 80)
+
+    def build():
+        g = fdtd.from_scenario(sc, probe_capacity=80)
+        for c, f in enumerate(sc.fields):
+            g.set_field(c, f)
+        return g
+    a = build()
+    a.step(70)                      # one 32-step graph, twice, then direct launches
+    b = build()
+    for _ in range(70):
+        b.step(1)
+    for c in range(6):
+        assert np.array_equal(a.get_field(c), b.get_field(c))
+    Ia, Qa = a.get_wire_state()
+    Ib, Qb = b.get_wire_state()
+    assert np.array_equal(Ia, Ib) and np.array_equal(Qa, Qb)
+    c = build()
+    c.step(30)
+    state = c.save_state()
+    c.step(40)
+    d = build()
+    d.load_state(state)
+    d.step(40)
+    for comp in range(6):
+        assert np.array_equal(c.get_field(comp), d.get_field(comp))
+    Ic, Qc = c.get_wire_state()
+    Id, Qd = d.get_wire_state()
+    assert np.array_equal(Ic, Id) and np.array_equal(Qc, Qd)
+    for p in range(len(sc.probes) + len(sc.owire_probes)):
+        assert np.array_equal(c.read_probe(p), d.read_probe(p))
+    for g in (a, b, c, d):
+        g.close()
+
+
+def test_batches_reject_oblique_wires(fdtd):
+    sc = owire_scenario(4, (16, 16, 16), 0, 10)
+    g = fdtd.from_scenario(sc, probe_capacity=10)
+    h = fdtd.from_scenario(W.random_scenario(2, n=(12, 10, 9), n_steps=10), probe_capacity=10)
+    with pytest.raises(fdtd.FdtdError):
+        fdtd.Batch([g, h])
+    g.close()
+    h.close()
