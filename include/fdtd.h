@@ -154,7 +154,8 @@ int fdtd_add_wire_path(fdtd_grid *g, int i0, int j0, int k0, int i1, int j1, int
  * the straight path between the segment's end nodes.  An end point equal
  * (within 1e-9) to a node of an earlier oblique wire joins that node
  * (junction: the currents of all segments at a node change its charge).  A
- * node on an outer wall is grounded (potential 0).  Not allowed with Debye
+ * node on an outer wall is grounded (potential 0).  Thick wires lower the
+ * stable Courant number (fdtd_wire_courant_limit).  Not allowed with Debye
  * media (fdtd_finalize fails with FDTD_EINVAL) or in batches
  * (fdtd_batch_create fails).  *wire_id (may be NULL) receives the index. */
 int fdtd_add_oblique_wire(fdtd_grid *g, double x0, double y0, double z0, double x1, double y1, double z1,
@@ -172,6 +173,15 @@ int fdtd_add_wire_voltage_source(fdtd_grid *g, int wire_id, int segment, const d
  * from the wire's first point towards its second), read with
  * fdtd_read_probes; probe ids are shared with fdtd_add_probe. */
 int fdtd_add_wire_probe(fdtd_grid *g, int wire_id, int segment, int *probe_id);
+
+/* Largest Courant number at which the grid's oblique wires keep the
+ * coupled leapfrog stable: min over segments of
+ * 1 / sqrt(1 + 2 |w|^2 exp(-1.89 ln(R/a))), |w|^2 the sum of the squared
+ * edge shares of the segment (1 for a segment along a node line), a bound
+ * set below the measured stability limit of wires along node lines.  1 when
+ * there are none.  fdtd_finalize fails with FDTD_ECOURANT when the grid's
+ * courant exceeds it.  Host only; any time before or after finalize. */
+int fdtd_wire_courant_limit(const fdtd_grid *g, double *courant);
 
 /* Number of oblique-wire segments and nodes (all wires, in the order
  * added; a wire's segments are consecutive, its interior nodes follow its

@@ -90,6 +90,7 @@ def load():
             "fdtd_add_wire_voltage_source": (I, [P, I, I, P, I, ip]),
             "fdtd_add_wire_probe": (I, [P, I, I, ip]),
             "fdtd_wire_counts": (I, [P, ip, ip]),
+            "fdtd_wire_courant_limit": (I, [P, ctypes.POINTER(D)]),
             "fdtd_get_wire_state": (I, [P, P, P]),
             "fdtd_set_wire_state": (I, [P, P, P]),
             "fdtd_save_state": (I, [P, P, ctypes.POINTER(ctypes.c_size_t)]),

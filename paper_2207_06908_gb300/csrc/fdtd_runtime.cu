@@ -422,6 +422,26 @@ std::vector<OEdgeH> path_edges(const fdtd_grid *g, const double pa[3], const dou
     return out;
 }
 
+// Courant number up to which the leapfrog of grid and oblique wires stays
+// stable.  A segment couples to the grid through the rank-one exchange of
+// its edge shares w, whose stiffness adds to the grid's on those edges; it
+// grows with |w|^2 and with the in-cell coupling as the wire thickens
+// (small Lambda = ln(R/a)).  Measured limits of the stiffest case, a wire
+// along a node line (|w|^2 = 1): 1/S^2 - 1 = 0.458, 0.243, 0.138, 0.079,
+// 0.039, 0.013 at Lambda = 0.7, 1.0, 1.3, 1.6, 2.0, 2.6, close to
+// 1.71 exp(-1.89 Lambda); the bound takes 2.0 |w|^2 exp(-1.89 Lambda) per
+// segment, the smallest over the segments.
+double wire_courant_limit(const fdtd_grid *g)
+{
+    double lim = 1.0;
+    for (const OSegH &sg : g->osegs) {
+        double w2 = 0.0;
+        for (const OEdgeH &e : sg.edges) w2 += e.W * e.W;
+        lim = std::min(lim, 1.0 / std::sqrt(1.0 + 2.0 * w2 * std::exp(-1.89 * sg.lam)));
+    }
+    return lim;
+}
+
 struct WireDev {
     std::vector<fdtd::OSeg> seg;
     std::vector<fdtd::OEdge> edge;
@@ -1396,6 +1416,13 @@ int fdtd_add_wire_probe(fdtd_grid *g, int wire_id, int segment, int *probe_id)
     return FDTD_OK;
 }
 
+int fdtd_wire_courant_limit(const fdtd_grid *g, double *courant)
+{
+    if (!g || !courant) return FDTD_EINVAL;
+    *courant = wire_courant_limit(g);
+    return FDTD_OK;
+}
+
 int fdtd_wire_counts(const fdtd_grid *g, int *n_segments, int *n_nodes)
 {
     if (!g || !n_segments || !n_nodes) return FDTD_EINVAL;
@@ -1456,6 +1483,12 @@ int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_by
     if (int rc = build_classes(g, cls, table, src_cb, dcls, dtable, src_debye)) return rc;
     if (!g->osegs.empty() && g->npoles)
         return fail(g, FDTD_EINVAL, "oblique wires in dispersive media are not supported");
+    if (!g->osegs.empty() && g->courant > wire_courant_limit(g)) {
+        char msg[160];
+        std::snprintf(msg, sizeof msg, "the oblique wires need courant <= %.4f (thinner wires or a smaller step)",
+                      wire_courant_limit(g));
+        return fail(g, FDTD_ECOURANT, msg);
+    }
 
     const Plan p = make_plan(g, probe_capacity);
     if (arena) {

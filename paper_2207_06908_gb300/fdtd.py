@@ -137,6 +137,13 @@ class Grid:
               "wire_counts")
         return ns.value, nn.value
 
+    def wire_courant_limit(self):
+        """largest Courant number the oblique wires added so far allow"""
+        c = ctypes.c_double()
+        check(self._lib, self._h, self._lib.fdtd_wire_courant_limit(self._h, ctypes.byref(c)),
+              "wire_courant_limit")
+        return c.value
+
     def get_wire_state(self):
         """(segment currents of the last half step, node charges)"""
         ns, nn = self.wire_counts()

@@ -158,3 +158,25 @@ def test_oblique_wires_rejected_in_dispersive_grids_before_device_work():
         assert b"dispersive" in lib.fdtd_last_error(h)
     finally:
         lib.fdtd_destroy(h)
+
+
+def test_thick_oblique_wire_needs_a_smaller_courant_number():
+    """a wire along a node line with ln(R/a) = 1 caps the Courant number
+    below 0.99: finalize refuses before any device work and names the cap"""
+    import math
+    from paper_2207_06908_gb300 import _lib as L
+    lib = L.load()
+    a = 0.1 * math.exp(-0.57721566490153286) / (2 * math.sqrt(2)) / math.e
+    for courant, rc in ((0.99, -2), (0.85, None)):
+        h = ctypes.c_void_p()
+        assert lib.fdtd_create_grid(14, 14, 14, 0.1, courant, None, None, ctypes.byref(h)) == 0
+        try:
+            assert lib.fdtd_add_oblique_wire(h, 1.0, 7.0, 7.0, 13.0, 7.0, 7.0, a, None) == 0
+            lim = ctypes.c_double()
+            assert lib.fdtd_wire_courant_limit(h, ctypes.byref(lim)) == 0
+            assert abs(lim.value - 1 / math.sqrt(1 + 2 * math.exp(-1.89))) < 1e-9
+            if rc is not None:
+                assert lib.fdtd_finalize(h, 0, None, 0) == rc
+                assert b"courant" in lib.fdtd_last_error(h)
+        finally:
+            lib.fdtd_destroy(h)

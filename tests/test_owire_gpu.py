@@ -24,7 +24,7 @@ def fdtd():
 
 def owire_scenario(seed, n, cpml, steps, fields=True):
     sc = W.random_scenario(seed, n=n, cpml=cpml, n_wires=0, n_sources=1, n_probes=4, n_steps=steps,
-                           fields=fields)
+                           fields=fields, courant=0.95)    # below the wires' Courant limit
     rng = np.random.default_rng(seed + 100)
     lo = cpml + 1.5
 

@@ -29,7 +29,7 @@ def wire_energy(I_m, I_p, Q, Ldl, cV):
 
 def _wired_box(rng, n, dx, grounded=True):
     cm, eps, sig, mu = random_materials(rng, n, 4)
-    g = OracleGrid(*n, dx, parity=False)
+    g = OracleGrid(*n, dx, courant=0.95, parity=False)      # below the grounded wire's Courant limit
     g.set_materials(cm, eps, sig, mu)
     g.add_oblique_wire((3.3, 4.1, 3.7), (11.2, 9.6, 8.4), 0.002)
     g.add_oblique_wire((11.2, 9.6, 8.4), (12.5, 3.2, 5.0), 0.003)     # junction at the shared end
@@ -80,7 +80,7 @@ def test_wire_charge_is_conserved_and_relaxes_with_the_medium():
     rng = np.random.default_rng(12)
     n, dx = (16, 14, 12), 0.1
     for sigma in (0.0, 0.01):
-        g = OracleGrid(*n, dx, parity=False)
+        g = OracleGrid(*n, dx, courant=0.95, parity=False)
         eps_r = 5.0
         g.set_materials(np.zeros((n[2], n[1], n[0]), np.uint8), [eps_r], [sigma], [1.0])
         g.add_oblique_wire((3.3, 4.1, 3.7), (11.2, 9.6, 8.4), 0.002)
@@ -134,7 +134,7 @@ def _line_impedance(direction, n=(84, 48, 40), h=4, a=0.002, dx=0.1, steps=150, 
     horizontal wire's middle node, V = -sum Ez dz from the plane to the wire
     (bilinear between the four vertical lines around the node) plus the
     node's in-cell potential, I the mean current of its two segments"""
-    g = OracleGrid(*n, dx, parity=False)
+    g = OracleGrid(*n, dx, courant=0.95, parity=False)     # below the riser's Courant limit
     base = np.array([6.0, 8.0 if direction[1] else n[1] / 2, 0.0])
     p0 = base + [0.0, 0.0, h]
     d = np.asarray(direction, float) / np.linalg.norm(direction)
