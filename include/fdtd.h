@@ -80,7 +80,8 @@ enum {
     FDTD_PROBE_I = 1,     /* current: loop integral of H around the edge from node (i,j,k) along +axis, at t_{n+1/2} */
     FDTD_PROBE_E = 2,     /* E component `axis` owned by cell (i,j,k), at t_{n+1} */
     FDTD_PROBE_H = 3,     /* H component `axis` owned by cell (i,j,k), at t_{n+1/2} */
-    FDTD_PROBE_WIRE = 4   /* current of one oblique-wire segment, at t_{n+1/2} (fdtd_add_wire_probe) */
+    FDTD_PROBE_WIRE = 4,  /* current of one oblique-wire segment, at t_{n+1/2} (fdtd_add_wire_probe) */
+    FDTD_PROBE_WIRE_V = 5 /* in-cell potential of an oblique-wire node, at t_{n+1} (fdtd_add_wire_node_probe) */
 };
 
 /* Create a grid of nx*ny*nz cells of edge dx metres.  The time step is
@@ -154,7 +155,11 @@ int fdtd_add_wire_path(fdtd_grid *g, int i0, int j0, int k0, int i1, int j1, int
  * the straight path between the segment's end nodes.  An end point equal
  * (within 1e-9) to a node of an earlier oblique wire joins that node
  * (junction: the currents of all segments at a node change its charge).  A
- * node on an outer wall is grounded (potential 0).  Thick wires lower the
+ * node on an outer wall is grounded (potential 0).  Inside a CPML a wire
+ * is a matched lossy line (series resistance and shunt conductance per unit
+ * length L' nu and C' nu, nu = sum_u t_u^2 sigma_u / (kappa_u eps0) at the
+ * segment, t its direction), so a wire may run into the layer and end
+ * there.  Thick wires lower the
  * stable Courant number (fdtd_wire_courant_limit).  Not allowed with Debye
  * media (fdtd_finalize fails with FDTD_EINVAL) or in batches
  * (fdtd_batch_create fails).  *wire_id (may be NULL) receives the index. */
@@ -162,17 +167,27 @@ int fdtd_add_oblique_wire(fdtd_grid *g, double x0, double y0, double z0, double 
                           double radius, int *wire_id);
 
 /* Delta-gap EMF in segment `segment` (0-based from the wire's first point)
- * of oblique wire `wire_id`: voltage[n] volts at t_n (0 after the last
+ * of oblique wire `wire_id`, in series with r_internal >= 0 ohm (a lightning
+ * channel: the channel impedance): voltage[n] volts at t_n (0 after the last
  * sample) drive the segment's current from its first towards its second
- * point.  voltage (n doubles, host) is copied and rounded to FP32.
- * *source_id (may be NULL) receives the index among such sources. */
-int fdtd_add_wire_voltage_source(fdtd_grid *g, int wire_id, int segment, const double *voltage, int n,
-                                 int *source_id);
+ * point, L' dl dI/dt = E_s dl - (V_b - V_a) + V - r I with the r I term at
+ * the mean of the two half steps.  voltage (n doubles, host) is copied and
+ * rounded to FP32.  *source_id (may be NULL) receives the index among such
+ * sources. */
+int fdtd_add_wire_voltage_source(fdtd_grid *g, int wire_id, int segment, double r_internal, const double *voltage,
+                                 int n, int *source_id);
 
 /* Probe of the current of one oblique-wire segment at t_{n+1/2} (positive
  * from the wire's first point towards its second), read with
  * fdtd_read_probes; probe ids are shared with fdtd_add_probe. */
 int fdtd_add_wire_probe(fdtd_grid *g, int wire_id, int segment, int *probe_id);
+
+/* Probe of the in-cell potential Q / (C' dl) of the oblique-wire node at
+ * point (x, y, z) (node units; it must be a node of a wire added earlier),
+ * at t_{n+1}.  The grid does not hold that part of a thin wire's potential:
+ * a voltage from the grid to the wire is a FDTD_PROBE_V path ending at the
+ * node plus this probe. */
+int fdtd_add_wire_node_probe(fdtd_grid *g, double x, double y, double z, int *probe_id);
 
 /* Largest Courant number at which the grid's oblique wires keep the
  * coupled leapfrog stable: min over segments of

@@ -74,7 +74,13 @@
  *     trilinear node weights of a and b; without it a steady current along
  *     an oblique wire would pile up spurious grid charge; Q_m^{n+1} = Q_m^n + dt [sum of currents into m] -
  *     (G'/C') dt (Q^{n+1} + Q^n)/2.  A source is a delta-gap EMF V(t_n) in
- *     one segment: V / dl joins E_s in that segment's current update.  Wires
+ *     one segment with a series resistance R: L' dl dI/dt = E_s dl - (V_b -
+ *     V_a) + V - R I, the R I term at the mean of I^{n-1/2} and I^{n+1/2}
+ *     (stable for any R).  Inside the CPML the wire is a matched lossy
+ *     line, R'/L' = G'/C' = nu = sum_u t_u^2 sigma_u / (kappa_u eps0) (the
+ *     layer's attenuation of a wave running along the wire; equal ratios
+ *     keep its impedance), so its own wave is absorbed with the grid's;
+ *     this is a reading, the paper is silent on wires in the layer.  Wires
  *     whose end points coincide share that node (junction, Kirchhoff's
  *     current law); a node on an outer wall is grounded (V = 0).  The
  *     in-cell radius is parity unpinned against the paper (pinned by
@@ -118,7 +124,7 @@ typedef ORC_REAL real;
 #define ORC_MAXP 4                 /* Debye poles per material */
 
 enum { EX = 0, EY, EZ, HX, HY, HZ };
-enum { PROBE_V = 0, PROBE_I = 1, PROBE_E = 2, PROBE_H = 3, PROBE_W = 4 };
+enum { PROBE_V = 0, PROBE_I = 1, PROBE_E = 2, PROBE_H = 3, PROBE_W = 4, PROBE_WV = 5 };
 
 typedef struct { int axis, i, j, k, n; double radius; } orc_wire;
 typedef struct { int axis, i, j, k, n; real *cur; int hard; } orc_src;   /* hard: ideal voltage source */
@@ -132,6 +138,9 @@ typedef struct {
     double c[3], t[3], dl;         /* centre (node units), direction, length (m) */
     double lam;                    /* ln(R / a) */
     real cI;                       /* dt / L' */
+    double R;                      /* series resistance of its sources (ohm) */
+    double nu;                     /* CPML loss rate along it (1/s) */
+    real rk, rd;                   /* (1 - k) / (1 + k), 1 / (1 + k), k = dt (R / (L' dl) + nu) / 2 */
     int ne;                        /* coupling edges */
     int comp[ORC_OW_EDGES];
     size_t q[ORC_OW_EDGES];
@@ -141,12 +150,12 @@ typedef struct {
 } orc_oseg;
 typedef struct {
     double p[3];                   /* node units */
-    double dlm, lam_sum;           /* wire length it carries (m); sum of ln(R/a) of its segments */
+    double dlm, lam_sum, nu_sum;   /* wire length it carries (m); sums of ln(R/a) and CPML rate of its segments */
     int nadj, grounded;
     real cV, aQ, bQ;               /* V = cV Q; Q^{n+1} = aQ Q^n + bQ (net current in) */
 } orc_onode;
 typedef struct { int seg0, nseg; double radius; } orc_owire;
-typedef struct { int seg, n; real *emf; } orc_osrc;   /* delta-gap EMF in a segment */
+typedef struct { int seg, n; real *emf; double r; } orc_osrc;   /* delta-gap EMF with series resistance r */
 
 typedef struct orc_grid {
     int nx, ny, nz;
@@ -453,7 +462,7 @@ int orc_add_lumped(orc_grid *g, int i, int j, int k, int axis, double resistance
 int orc_add_probe(orc_grid *g, int kind, int i, int j, int k, int axis, int n_edges)
 {
     if (g->finalized) return -8;
-    if (kind == PROBE_W) return -1;    /* oblique-wire currents: orc_add_owire_probe */
+    if (kind >= PROBE_W) return -1;    /* oblique-wire probes have their own calls */
     if (axis < 0 || axis > 2 || kind < 0 || kind > 3) return -1;
     int p[3] = {i, j, k}, nn[3] = {g->nx, g->ny, g->nz};
     for (int u = 0; u < 3; u++) if (p[u] < 0 || p[u] >= nn[u]) return -1;
@@ -541,14 +550,15 @@ int orc_add_owire(orc_grid *g, double x0, double y0, double z0, double x1, doubl
     return g->n_owires++;
 }
 
-/* delta-gap EMF in segment seg of oblique wire w: volt[n] (V at t_n) drives
- * the segment's current from its start node to its end node */
-int orc_add_owire_vsource(orc_grid *g, int w, int seg, const double *volt, int n)
+/* delta-gap EMF in segment seg of oblique wire w with series resistance r
+ * (ohm, >= 0): volt[n] (V at t_n) drives the segment's current from its start
+ * node to its end node */
+int orc_add_owire_vsource(orc_grid *g, int w, int seg, double r, const double *volt, int n)
 {
     if (g->finalized) return -8;
-    if (w < 0 || w >= g->n_owires || seg < 0 || seg >= g->owires[w].nseg || n < 0) return -1;
+    if (w < 0 || w >= g->n_owires || seg < 0 || seg >= g->owires[w].nseg || n < 0 || !(r >= 0.0)) return -1;
     g->osrcs = (orc_osrc *)realloc(g->osrcs, (g->n_osrcs + 1) * sizeof(orc_osrc));
-    orc_osrc sr = {g->owires[w].seg0 + seg, n, (real *)malloc((n > 0 ? n : 1) * sizeof(real))};
+    orc_osrc sr = {g->owires[w].seg0 + seg, n, (real *)malloc((n > 0 ? n : 1) * sizeof(real)), r};
     for (int q = 0; q < n; q++) sr.emf[q] = r32(g, volt[q]);
     g->osrcs[g->n_osrcs++] = sr;
     return 0;
@@ -561,6 +571,21 @@ int orc_add_owire_probe(orc_grid *g, int w, int seg)
     if (w < 0 || w >= g->n_owires || seg < 0 || seg >= g->owires[w].nseg) return -1;
     g->probes = (orc_probe *)realloc(g->probes, (g->n_probes + 1) * sizeof(orc_probe));
     orc_probe pr = {PROBE_W, 0, g->owires[w].seg0 + seg, 0, 0, 1};
+    g->probes[g->n_probes++] = pr;
+    return 0;
+}
+
+/* probe of the in-cell potential Q_m / (C' dl_m) of the oblique-wire node at
+ * (x, y, z) (node units), at t_{n+1}: added to a grid voltage path that ends
+ * at the node it gives the wire's own potential */
+int orc_add_owire_node_probe(orc_grid *g, double x, double y, double z)
+{
+    if (g->finalized) return -8;
+    double P[3] = {x, y, z};
+    int m = onode_at(g, P);
+    if (m < 0) return -1;
+    g->probes = (orc_probe *)realloc(g->probes, (g->n_probes + 1) * sizeof(orc_probe));
+    orc_probe pr = {PROBE_WV, 0, m, 0, 0, 1};
     g->probes[g->n_probes++] = pr;
     return 0;
 }
@@ -776,6 +801,20 @@ static void e_stencil(int comp, const int q[3], int hc[4], int hp[4][3])
 }
 
 
+/* CPML attenuation rate sigma/(kappa eps0) along axis u at position x (cells) */
+static double cpml_rate(const orc_grid *g, int u, double x)
+{
+    if (g->d == 0) return 0.0;
+    int nn[3] = {g->nx, g->ny, g->nz};
+    double rho = 0.0;
+    if (x < g->d) rho = g->d - x;
+    else if (x > nn[u] - g->d) rho = x - (nn[u] - g->d);
+    if (rho <= 0.0) return 0.0;
+    double r = rho / g->d;
+    double sig = g->sigma_max * pow(r, g->order), kap = 1.0 + (g->kappa_max - 1.0) * pow(r, g->order);
+    return sig / (kap * ORC_EPS0);
+}
+
 /* in-cell parameters and coupling edges of the oblique wires (after the
  * E coefficients exist: the scatter uses each edge's cb) */
 static int build_owires(orc_grid *g)
@@ -783,7 +822,9 @@ static int build_owires(orc_grid *g)
     const double dx = g->dx, dt = g->dt;
     const double r0 = exp(-0.57721566490153286) / (2.0 * sqrt(2.0));
     int nn[3] = {g->nx, g->ny, g->nz};
-    for (int m = 0; m < g->n_onodes; m++) { g->onodes[m].dlm = 0.0; g->onodes[m].lam_sum = 0.0; g->onodes[m].nadj = 0; }
+    for (int m = 0; m < g->n_onodes; m++) {
+        g->onodes[m].dlm = 0.0; g->onodes[m].lam_sum = 0.0; g->onodes[m].nu_sum = 0.0; g->onodes[m].nadj = 0;
+    }
     for (int w = 0; w < g->n_owires; w++)
         for (int s = g->owires[w].seg0; s < g->owires[w].seg0 + g->owires[w].nseg; s++) {
             orc_oseg *S = &g->osegs[s];
@@ -807,6 +848,14 @@ static int build_owires(orc_grid *g)
             }
             double Lp = ORC_MU0 * cell_mu(g, ci[0], ci[1], ci[2]) * S->lam / (2.0 * M_PI);
             S->cI = r32(g, dt / Lp);
+            S->R = 0.0;
+            for (int q = 0; q < g->n_osrcs; q++)
+                if (g->osrcs[q].seg == s) S->R += g->osrcs[q].r;
+            S->nu = 0.0;
+            for (int q = 0; q < 3; q++) S->nu += S->t[q] * S->t[q] * cpml_rate(g, q, S->c[q]);
+            double k = 0.5 * dt * (S->R / (Lp * S->dl) + S->nu);
+            S->rk = r32(g, (1.0 - k) / (1.0 + k));
+            S->rd = r32(g, 1.0 / (1.0 + k));
             /* charge-conserving coupling: the path a -> b split at the cell
              * faces it crosses; each piece inside one cell spreads its
              * displacement over the cell's 12 edges with the weights under
@@ -875,6 +924,7 @@ static int build_owires(orc_grid *g)
             orc_onode *A = &g->onodes[S->a], *Bn = &g->onodes[S->b];
             A->dlm += 0.5 * S->dl; Bn->dlm += 0.5 * S->dl;
             A->lam_sum += S->lam; Bn->lam_sum += S->lam;
+            A->nu_sum += S->nu; Bn->nu_sum += S->nu;
             A->nadj++; Bn->nadj++;
         }
     for (int m = 0; m < g->n_onodes; m++) {
@@ -886,7 +936,7 @@ static int build_owires(orc_grid *g)
         }
         double eps = ORC_EPS0 * cell_eps(g, ci[0], ci[1], ci[2]), sig = cell_sig(g, ci[0], ci[1], ci[2]);
         double lam = nd->lam_sum / nd->nadj;
-        double r = sig * dt / (2.0 * eps);
+        double r = (sig / eps + nd->nu_sum / nd->nadj) * dt / 2.0;
         nd->cV = r32(g, lam / (2.0 * M_PI * eps * nd->dlm));
         nd->aQ = r32(g, (1.0 - r) / (1.0 + r));
         nd->bQ = r32(g, dt / (1.0 + r));
@@ -1165,6 +1215,11 @@ static inline real debye_add(const orc_grid *g, int c, size_t q, real e)
  * delta-gap EMFs at t_n */
 static void owire_current(orc_grid *g)
 {
+    double *drive = (double *)calloc(g->n_osegs > 0 ? g->n_osegs : 1, sizeof(double));
+    for (int q = 0; q < g->n_osrcs; q++) {
+        const orc_osrc *sr = &g->osrcs[q];
+        if (g->step < sr->n) drive[sr->seg] += sr->emf[g->step];
+    }
     for (int s = 0; s < g->n_osegs; s++) {
         const orc_oseg *S = &g->osegs[s];
         double es = 0.0;
@@ -1172,12 +1227,10 @@ static void owire_current(orc_grid *g)
         const orc_onode *A = &g->onodes[S->a], *B = &g->onodes[S->b];
         double va = A->grounded ? 0.0 : (double)A->cV * g->oQ[S->a];
         double vb = B->grounded ? 0.0 : (double)B->cV * g->oQ[S->b];
-        g->oI[s] += (double)S->cI * (es - (vb - va) / S->dl);
+        double inc = (double)S->cI * (es - (vb - va) / S->dl + drive[s] / S->dl);
+        g->oI[s] = (double)S->rk * g->oI[s] + (double)S->rd * inc;
     }
-    for (int q = 0; q < g->n_osrcs; q++) {
-        const orc_osrc *sr = &g->osrcs[q];
-        if (g->step < sr->n) g->oI[sr->seg] += (double)g->osegs[sr->seg].cI * sr->emf[g->step] / g->osegs[sr->seg].dl;
-    }
+    free(drive);
 }
 
 /* the segment currents in Ampere's law: E^{n+1} -= cb dx J on the coupling
@@ -1316,6 +1369,7 @@ static double probe_value(const orc_grid *g, const orc_probe *p)
 {
     double dx = g->dx;
     if (p->kind == PROBE_W) return g->oI[p->i];
+    if (p->kind == PROBE_WV) return g->onodes[p->i].grounded ? 0.0 : (double)g->onodes[p->i].cV * g->oQ[p->i];
     if (p->kind == PROBE_E) return g->f[p->axis][IDX(g, p->i, p->j, p->k)];
     if (p->kind == PROBE_H) return g->f[3 + p->axis][IDX(g, p->i, p->j, p->k)];
     if (p->kind == PROBE_V) {
@@ -1353,7 +1407,8 @@ int orc_step(orc_grid *g, int n)
         update_e(g);
         owire_charge(g);
         for (int p = 0; p < g->n_probes; p++)
-            if ((g->probes[p].kind == PROBE_V || g->probes[p].kind == PROBE_E) && g->step < g->max_steps)
+            if ((g->probes[p].kind == PROBE_V || g->probes[p].kind == PROBE_E || g->probes[p].kind == PROBE_WV) &&
+                g->step < g->max_steps)
                 g->probe_out[(size_t)p * g->max_steps + g->step] = probe_value(g, &g->probes[p]);
         g->step++;
     }

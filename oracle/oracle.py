@@ -96,8 +96,9 @@ def _load(f32: bool = False):
         lib.orc_set_debye_current.argtypes = [P, I, I, dp]
         ip = ctypes.POINTER(ctypes.c_int)
         lib.orc_add_owire.argtypes = [P, D, D, D, D, D, D, D]
-        lib.orc_add_owire_vsource.argtypes = [P, I, I, dp, I]
+        lib.orc_add_owire_vsource.argtypes = [P, I, I, D, dp, I]
         lib.orc_add_owire_probe.argtypes = [P, I, I]
+        lib.orc_add_owire_node_probe.argtypes = [P, D, D, D]
         lib.orc_owire_counts.argtypes = [P, ip, ip]
         lib.orc_owire_counts.restype = None
         lib.orc_get_owire_state.argtypes = [P, dp, dp]
@@ -228,16 +229,23 @@ class OracleGrid:
             _check(rc, "add_oblique_wire")
         return rc
 
-    def add_wire_voltage_source(self, wire, segment, voltage):
-        """delta-gap EMF (V at t_n) in one segment of an oblique wire,
-        driving current from the segment's start towards its end"""
+    def add_wire_voltage_source(self, wire, segment, voltage, r_internal=0.0):
+        """delta-gap EMF (V at t_n) with series resistance r_internal in one
+        segment of an oblique wire, driving current from the segment's start
+        towards its end"""
         v = np.ascontiguousarray(voltage, dtype=np.float64)
-        _check(self._lib.orc_add_owire_vsource(self._h, int(wire), int(segment), _dptr(v), len(v)),
-               "add_wire_voltage_source")
+        _check(self._lib.orc_add_owire_vsource(self._h, int(wire), int(segment), float(r_internal), _dptr(v),
+                                               len(v)), "add_wire_voltage_source")
 
     def add_wire_probe(self, wire, segment):
         """current of one segment of an oblique wire at t_{n+1/2}"""
         _check(self._lib.orc_add_owire_probe(self._h, int(wire), int(segment)), "add_wire_probe")
+        self.n_probes += 1
+        return self.n_probes - 1
+
+    def add_wire_node_probe(self, point):
+        """in-cell potential of the oblique-wire node at point, at t_{n+1}"""
+        _check(self._lib.orc_add_owire_node_probe(self._h, *map(float, point)), "add_wire_node_probe")
         self.n_probes += 1
         return self.n_probes - 1
 
@@ -320,12 +328,15 @@ class OracleGrid:
             g.add_lumped(node, axis, res, cap)
         for p0, p1, r in getattr(sc, "owires", None) or []:
             g.add_oblique_wire(p0, p1, r)
-        for w, seg, volt in getattr(sc, "owire_sources", None) or []:
-            g.add_wire_voltage_source(w, seg, volt)
+        for src in getattr(sc, "owire_sources", None) or []:
+            g.add_wire_voltage_source(*src)
         for kind, node, axis, ne in sc.probes:
             g.add_probe(kind, node, axis, ne)
-        for w, seg in getattr(sc, "owire_probes", None) or []:
-            g.add_wire_probe(w, seg)
+        for pr in getattr(sc, "owire_probes", None) or []:
+            if len(pr) == 3:
+                g.add_wire_node_probe(pr)
+            else:
+                g.add_wire_probe(*pr)
         g.finalize(sc.n_steps)
         if sc.fields is not None:
             # start from the FP32-rounded fields the GPU starts from

@@ -87,8 +87,9 @@ def load():
             "fdtd_add_lumped": (I, [P, I, I, I, I, ctypes.c_double, ctypes.c_double, P]),
             "fdtd_add_wire_path": (I, [P, I, I, I, I, I, I, ctypes.c_double, P]),
             "fdtd_add_oblique_wire": (I, [P, D, D, D, D, D, D, D, ip]),
-            "fdtd_add_wire_voltage_source": (I, [P, I, I, P, I, ip]),
+            "fdtd_add_wire_voltage_source": (I, [P, I, I, D, P, I, ip]),
             "fdtd_add_wire_probe": (I, [P, I, I, ip]),
+            "fdtd_add_wire_node_probe": (I, [P, D, D, D, ip]),
             "fdtd_wire_counts": (I, [P, ip, ip]),
             "fdtd_wire_courant_limit": (I, [P, ctypes.POINTER(D)]),
             "fdtd_get_wire_state": (I, [P, P, P]),

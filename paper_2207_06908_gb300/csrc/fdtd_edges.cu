@@ -25,7 +25,8 @@ __device__ __forceinline__ long long eidx(const EdgeArgs &a, int i, int j, int k
 __device__ __forceinline__ void wire_body(const EdgeArgs &a, long long n)
 {
     const WireArgs &w = a.w;
-    // L' dI/dt = E_s - dV/dl + EMF / dl, centred at t_n
+    // L' dl dI/dt = E_s dl - (V_b - V_a) + EMF - R I, centred at t_n (the
+    // R I term at the mean of the two half steps)
     for (int s = threadIdx.x; s < w.n_seg; s += blockDim.x) {
         const OSeg sg = w.seg[s];
         float es = 0.f;
@@ -36,12 +37,12 @@ __device__ __forceinline__ void wire_body(const EdgeArgs &a, long long n)
         const ONode na = w.node[sg.a], nb = w.node[sg.b];
         const float va = na.grounded ? 0.f : na.cV * w.Q[sg.a];
         const float vb = nb.grounded ? 0.f : nb.cV * w.Q[sg.b];
-        float I = w.I[s] + (sg.cI * es - sg.cIV * (vb - va));
+        float inc = sg.cI * es - sg.cIV * (vb - va);
         for (int q = sg.s0; q < sg.s0 + sg.ns; ++q) {
             const OSrc sr = w.src[q];
-            if (n < sr.n) I += sr.cIV * w.samples[sr.off + n];
+            if (n < sr.n) inc += sr.cIV * w.samples[sr.off + n];
         }
-        w.I[s] = I;
+        w.I[s] = sg.rk * w.I[s] + sg.rd * inc;
     }
     __syncthreads();
     // the segment currents in Ampere's law at t_{n+1/2}; dQ/dt = net current in
@@ -105,6 +106,9 @@ __device__ __forceinline__ void edge_body(const EdgeArgs &a)
             float v = 0.f;
             if (pr.kind == 4) {
                 v = a.w.I[pr.i];                // oblique-wire segment current
+            } else if (pr.kind == 5) {
+                const ONode nd = a.w.node[pr.i];  // oblique-wire node: in-cell potential
+                v = nd.grounded ? 0.f : nd.cV * a.w.Q[pr.i];
             } else if (pr.kind == 2) {
                 v = a.E[pr.axis][eidx(a, pr.i, pr.j, pr.k)];
             } else if (pr.kind == 3) {

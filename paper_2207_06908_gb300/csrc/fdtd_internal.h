@@ -158,6 +158,8 @@ struct OSeg {
     int e0, ne;              // gather edges e0 .. e0+ne-1
     int s0, ns;              // its delta-gap sources s0 .. s0+ns-1
     float cI, cIV;           // dt / L', dt / (L' dl)
+    float rk, rd;            // series resistance R of its sources, k = cIV R / 2:
+                             // I^{n+1/2} = rk I^{n-1/2} + rd (increment), rk = (1-k)/(1+k), rd = 1/(1+k)
 };
 struct OEdge {
     long long idx;           // element index in the field arrays

@@ -39,12 +39,13 @@ struct OEdgeH { int comp, q[3]; double W; };
 struct OSegH {
     int a, b;                 // end nodes; I flows a -> b
     double dl, lam;           // length (m), ln(R / radius)
+    double c[3], t[3];        // centre (node units), direction
     int cell[3];              // cell holding the centre (its mu)
     std::vector<OEdgeH> edges;
 };
 struct ONodeH { double p[3]; int grounded; };
 struct OWireH { int seg0, nseg; };
-struct OSrcH { int seg; std::vector<float> emf; };
+struct OSrcH { int seg; std::vector<float> emf; double r; };   // r: series resistance (ohm)
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -423,23 +424,43 @@ std::vector<OEdgeH> path_edges(const fdtd_grid *g, const double pa[3], const dou
 }
 
 // Courant number up to which the leapfrog of grid and oblique wires stays
-// stable.  A segment couples to the grid through the rank-one exchange of
-// its edge shares w, whose stiffness adds to the grid's on those edges; it
-// grows with |w|^2 and with the in-cell coupling as the wire thickens
-// (small Lambda = ln(R/a)).  Measured limits of the stiffest case, a wire
-// along a node line (|w|^2 = 1): 1/S^2 - 1 = 0.458, 0.243, 0.138, 0.079,
-// 0.039, 0.013 at Lambda = 0.7, 1.0, 1.3, 1.6, 2.0, 2.6, close to
-// 1.71 exp(-1.89 Lambda); the bound takes 2.0 |w|^2 exp(-1.89 Lambda) per
-// segment, the smallest over the segments.
+// stable.  Each segment adds to the grid's stiffness a rank-one term
+// c_s w_s w_s^T on the edges it couples to (w_s its edge shares); c_s grows
+// as the wire thickens (small Lambda = ln(R/a)).  Measured limits of the
+// stiffest single case, a wire along a node line (w = one edge of share 1):
+// 1/S^2 - 1 = 0.458, 0.243, 0.138, 0.079, 0.039, 0.013 at Lambda = 0.7, 1.0,
+// 1.3, 1.6, 2.0, 2.6, close to 1.71 exp(-1.89 Lambda); the bound takes c_s =
+// 2.0 exp(-1.89 Lambda_s) and, since segments that share edges (wires
+// converging at a sharp angle) add their terms, the largest row sum over
+// the edges of the summed terms: 1/S^2 - 1 = max_e sum_s |w_se| |w_s|_1 c_s
+// (equal to c_s for a lone segment on a node line).
 double wire_courant_limit(const fdtd_grid *g)
 {
-    double lim = 1.0;
+    std::map<std::pair<int, long long>, double> row;   // (component, cell) -> row sum
     for (const OSegH &sg : g->osegs) {
-        double w2 = 0.0;
-        for (const OEdgeH &e : sg.edges) w2 += e.W * e.W;
-        lim = std::min(lim, 1.0 / std::sqrt(1.0 + 2.0 * w2 * std::exp(-1.89 * sg.lam)));
+        double l1 = 0.0;
+        for (const OEdgeH &e : sg.edges) l1 += std::fabs(e.W);
+        const double c = 2.0 * std::exp(-1.89 * sg.lam);
+        for (const OEdgeH &e : sg.edges) {
+            const long long cell = ((long long)e.q[2] * g->ny + e.q[1]) * g->nx + e.q[0];
+            row[{e.comp, cell}] += std::fabs(e.W) * l1 * c;
+        }
     }
-    return lim;
+    double worst = 0.0;
+    for (const auto &kv : row) worst = std::max(worst, kv.second);
+    return 1.0 / std::sqrt(1.0 + worst);
+}
+
+// CPML attenuation sigma / (kappa eps0) along axis u at position x (cells)
+double cpml_rate(const fdtd_grid *g, int u, double x)
+{
+    if (g->d == 0) return 0.0;
+    const int n = u == 0 ? g->nx : (u == 1 ? g->ny : g->nz), d = g->d;
+    const double rho = x < d ? d - x : (x > n - d ? x - (n - d) : 0.0);
+    if (rho <= 0.0) return 0.0;
+    const double r = rho / d;
+    const fdtd_cpml &p = g->cpml;
+    return p.sigma_max * std::pow(r, p.order) / ((1.0 + (p.kappa_max - 1.0) * std::pow(r, p.order)) * kEps0);
 }
 
 struct WireDev {
@@ -468,7 +489,7 @@ WireDev wire_device(const fdtd_grid *g, const std::vector<uint8_t> &cls, const s
     auto material = [&](const int c[3]) -> const fdtd_material & {
         return g->table[g->mat[((size_t)c[2] * g->ny + c[1]) * g->nx + c[0]]];
     };
-    std::vector<double> lam(g->onodes.size(), 0.0), dlm(g->onodes.size(), 0.0);
+    std::vector<double> lam(g->onodes.size(), 0.0), dlm(g->onodes.size(), 0.0), nu(g->onodes.size(), 0.0);
     std::vector<int> deg(g->onodes.size(), 0);
     std::vector<std::vector<int>> adj(g->onodes.size());
     std::vector<std::vector<int>> seg_src(g->osegs.size());
@@ -484,6 +505,14 @@ WireDev wire_device(const fdtd_grid *g, const std::vector<uint8_t> &cls, const s
         o.ne = (int)sg.edges.size();
         o.cI = (float)(dt / Lp);
         o.cIV = (float)(dt / (Lp * sg.dl));
+        double R = 0.0;
+        for (int q : seg_src[s]) R += g->osrcs[q].r;
+        // inside the CPML the wire is a matched lossy line, R'/L' = G'/C' = nu
+        double nu_s = 0.0;
+        for (int u = 0; u < 3; ++u) nu_s += sg.t[u] * sg.t[u] * cpml_rate(g, u, sg.c[u]);
+        const double k = 0.5 * dt * (R / (Lp * sg.dl) + nu_s);
+        o.rk = (float)((1.0 - k) / (1.0 + k));
+        o.rd = (float)(1.0 / (1.0 + k));
         for (const OEdgeH &e : sg.edges) {
             const long long idx = (long long)e.q[2] * g->plane + (long long)e.q[1] * g->pitch + e.q[0];
             const double cb = table[(size_t)cls[idx] * fdtd::kNumCoef + 3 + e.comp];
@@ -501,6 +530,7 @@ WireDev wire_device(const fdtd_grid *g, const std::vector<uint8_t> &cls, const s
         for (int end = 0; end < 2; ++end) {
             const int m = end ? sg.b : sg.a;
             lam[m] += sg.lam;
+            nu[m] += nu_s;
             dlm[m] += 0.5 * sg.dl;
             deg[m] += 1;
             adj[m].push_back((int)(s << 1) | end);
@@ -515,7 +545,7 @@ WireDev wire_device(const fdtd_grid *g, const std::vector<uint8_t> &cls, const s
         int c[3];
         for (int a = 0; a < 3; ++a) c[a] = std::min((int)std::floor(nd.p[a]), n[a] - 1);
         const fdtd_material &mt = material(c);
-        const double eps = kEps0 * mt.eps_r, r = mt.sigma * dt / (2.0 * eps);
+        const double eps = kEps0 * mt.eps_r, r = (mt.sigma / eps + nu[m] / deg[m]) * dt / 2.0;
         fdtd::ONode o{};
         o.cV = (float)(lam[m] / deg[m] / (2.0 * M_PI * eps * dlm[m]));
         o.aQ = (float)((1.0 - r) / (1.0 + r));
@@ -1383,6 +1413,7 @@ int fdtd_add_oblique_wire(fdtd_grid *g, double x0, double y0, double z0, double 
         seg.b = next;
         seg.dl = len * g->dx / N;
         seg.lam = std::log(lattice_radius(g->dx, c, t) / radius);
+        for (int u = 0; u < 3; ++u) { seg.c[u] = c[u]; seg.t[u] = t[u]; }
         for (int u = 0; u < 3; ++u) seg.cell[u] = std::min((int)std::floor(c[u]), n[u] - 1);
         const ONodeH pa = g->onodes[prev], pb = g->onodes[next];
         seg.edges = path_edges(g, pa.p, pb.p);
@@ -1393,14 +1424,15 @@ int fdtd_add_oblique_wire(fdtd_grid *g, double x0, double y0, double z0, double 
     return FDTD_OK;
 }
 
-int fdtd_add_wire_voltage_source(fdtd_grid *g, int wire_id, int segment, const double *voltage, int n,
-                                 int *source_id)
+int fdtd_add_wire_voltage_source(fdtd_grid *g, int wire_id, int segment, double r_internal, const double *voltage,
+                                 int n, int *source_id)
 {
     if (int rc = check_open(g, false)) return rc;
     if (wire_id < 0 || wire_id >= (int)g->owires.size() || segment < 0 || segment >= g->owires[wire_id].nseg)
         return fail(g, FDTD_EINVAL, "no such oblique-wire segment");
     if (n < 0 || (n > 0 && !voltage)) return fail(g, FDTD_EINVAL, "bad voltage samples");
-    OSrcH sr{g->owires[wire_id].seg0 + segment, std::vector<float>(voltage, voltage + n)};
+    if (!(r_internal >= 0.0) || !std::isfinite(r_internal)) return fail(g, FDTD_EINVAL, "bad internal resistance");
+    OSrcH sr{g->owires[wire_id].seg0 + segment, std::vector<float>(voltage, voltage + n), r_internal};
     g->osrcs.push_back(std::move(sr));
     if (source_id) *source_id = (int)g->osrcs.size() - 1;
     return FDTD_OK;
@@ -1414,6 +1446,19 @@ int fdtd_add_wire_probe(fdtd_grid *g, int wire_id, int segment, int *probe_id)
     g->probes.push_back(fdtd::ProbeDesc{FDTD_PROBE_WIRE, 0, g->owires[wire_id].seg0 + segment, 0, 0, 1});
     if (probe_id) *probe_id = (int)g->probes.size() - 1;
     return FDTD_OK;
+}
+
+int fdtd_add_wire_node_probe(fdtd_grid *g, double x, double y, double z, int *probe_id)
+{
+    if (int rc = check_open(g, false)) return rc;
+    for (size_t m = 0; m < g->onodes.size(); ++m)
+        if (std::fabs(g->onodes[m].p[0] - x) < 1e-9 && std::fabs(g->onodes[m].p[1] - y) < 1e-9 &&
+            std::fabs(g->onodes[m].p[2] - z) < 1e-9) {
+            g->probes.push_back(fdtd::ProbeDesc{FDTD_PROBE_WIRE_V, 0, (int)m, 0, 0, 1});
+            if (probe_id) *probe_id = (int)g->probes.size() - 1;
+            return FDTD_OK;
+        }
+    return fail(g, FDTD_EINVAL, "no oblique-wire node at that point");
 }
 
 int fdtd_wire_courant_limit(const fdtd_grid *g, double *courant)

@@ -15,7 +15,7 @@ from . import _lib
 from ._lib import CpmlParams, FdtdError, Material, check
 
 EX, EY, EZ, HX, HY, HZ = range(6)
-PROBE_V, PROBE_I, PROBE_E, PROBE_H, PROBE_WIRE = 0, 1, 2, 3, 4
+PROBE_V, PROBE_I, PROBE_E, PROBE_H, PROBE_WIRE, PROBE_WIRE_V = 0, 1, 2, 3, 4, 5
 
 
 def _stream_ptr(stream):
@@ -115,13 +115,14 @@ class Grid:
               "add_oblique_wire")
         return wid.value
 
-    def add_wire_voltage_source(self, wire, segment, voltage):
-        """delta-gap EMF (V at t_n) in one segment of an oblique wire"""
+    def add_wire_voltage_source(self, wire, segment, voltage, r_internal=0.0):
+        """delta-gap EMF (V at t_n) in one segment of an oblique wire, in
+        series with r_internal ohm"""
         v = np.ascontiguousarray(voltage, dtype=np.float64)
         sid = ctypes.c_int()
         check(self._lib, self._h, self._lib.fdtd_add_wire_voltage_source(
-            self._h, int(wire), int(segment), v.ctypes.data_as(ctypes.c_void_p), len(v), ctypes.byref(sid)),
-            "add_wire_voltage_source")
+            self._h, int(wire), int(segment), float(r_internal), v.ctypes.data_as(ctypes.c_void_p), len(v),
+            ctypes.byref(sid)), "add_wire_voltage_source")
         return sid.value
 
     def add_wire_probe(self, wire, segment):
@@ -129,6 +130,13 @@ class Grid:
         pid = ctypes.c_int()
         check(self._lib, self._h, self._lib.fdtd_add_wire_probe(self._h, int(wire), int(segment),
                                                                ctypes.byref(pid)), "add_wire_probe")
+        return pid.value
+
+    def add_wire_node_probe(self, point):
+        """in-cell potential of the oblique-wire node at point (t_{n+1}); returns the probe id"""
+        pid = ctypes.c_int()
+        check(self._lib, self._h, self._lib.fdtd_add_wire_node_probe(self._h, *map(float, point),
+                                                                    ctypes.byref(pid)), "add_wire_node_probe")
         return pid.value
 
     def wire_counts(self):
@@ -344,15 +352,18 @@ def from_scenario(sc, stream=None, probe_capacity=None, torch_arena=True, block=
         g.add_lumped(node, axis, res, cap)
     for p0, p1, r in getattr(sc, "owires", None) or []:
         g.add_oblique_wire(p0, p1, r)
-    for w, seg, volt in getattr(sc, "owire_sources", None) or []:
-        g.add_wire_voltage_source(w, seg, volt)
+    for src in getattr(sc, "owire_sources", None) or []:
+        g.add_wire_voltage_source(*src)
     for kind, node, axis, ne in sc.probes:
         g.add_probe(kind, node, axis, ne)
-    for w, seg in getattr(sc, "owire_probes", None) or []:
-        g.add_wire_probe(w, seg)
+    for pr in getattr(sc, "owire_probes", None) or []:
+        if len(pr) == 3:
+            g.add_wire_node_probe(pr)
+        else:
+            g.add_wire_probe(*pr)
     g.finalize(sc.n_steps if probe_capacity is None else probe_capacity, torch_arena=torch_arena)
     return g
 
 
 __all__ = ["Grid", "Batch", "FdtdError", "from_scenario", "EX", "EY", "EZ", "HX", "HY", "HZ",
-           "PROBE_V", "PROBE_I", "PROBE_E", "PROBE_H", "PROBE_WIRE"]
+           "PROBE_V", "PROBE_I", "PROBE_E", "PROBE_H", "PROBE_WIRE", "PROBE_WIRE_V"]

@@ -130,9 +130,11 @@ def test_oblique_wire_host_checks():
         assert ok(h, 5.0, 5.0, 0.0, 5.0, 5.0, 4.0, 0.004, None) == 0           # grounded on z = 0
         v = (ctypes.c_double * 4)(1.0, 2.0, 3.0, 4.0)
         sid, pid = ctypes.c_int(), ctypes.c_int()
-        assert lib.fdtd_add_wire_voltage_source(h, 1, 0, v, 4, ctypes.byref(sid)) == 0 and sid.value == 0
-        assert lib.fdtd_add_wire_voltage_source(h, 1, 99, v, 4, None) == -1
-        assert lib.fdtd_add_wire_voltage_source(h, 7, 0, v, 4, None) == -1
+        assert lib.fdtd_add_wire_voltage_source(h, 1, 0, 0.0, v, 4, ctypes.byref(sid)) == 0 and sid.value == 0
+        assert lib.fdtd_add_wire_voltage_source(h, 1, 0, 400.0, v, 4, ctypes.byref(sid)) == 0 and sid.value == 1
+        assert lib.fdtd_add_wire_voltage_source(h, 1, 0, -1.0, v, 4, None) == -1
+        assert lib.fdtd_add_wire_voltage_source(h, 1, 99, 0.0, v, 4, None) == -1
+        assert lib.fdtd_add_wire_voltage_source(h, 7, 0, 0.0, v, 4, None) == -1
         assert lib.fdtd_add_probe(h, 0, 2, 2, 2, 2, 1, ctypes.byref(pid)) == 0 and pid.value == 0
         assert lib.fdtd_add_wire_probe(h, 0, 3, ctypes.byref(pid)) == 0 and pid.value == 1
         assert lib.fdtd_add_wire_probe(h, 2, 4, None) == -1                    # the grounded wire has 4

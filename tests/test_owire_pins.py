@@ -190,3 +190,46 @@ def test_line_impedance_independent_of_direction():
         z = _line_impedance(d, n=GRID, h=h, a=a, dx=dx)
         assert abs(z / z_axis - 1) < 0.01, (d, z, z_axis)
         assert abs(z / z0 - 1) < 0.02, (d, z, z0)
+
+
+def test_series_resistance_sets_the_steady_ring_current():
+    """a closed ring driven by a delta-gap EMF V behind a resistance R:
+    around the loop the node potentials cancel and at steady state the flux
+    no longer changes, so every segment carries exactly V / R"""
+    n, dx = (14, 14, 10), 0.1
+    for R in (200.0, 50.0):
+        g = OracleGrid(*n, dx, courant=0.95, parity=False)
+        corners = [(4, 4, 5), (10, 4, 5), (10, 10, 5), (4, 10, 5)]
+        for q in range(4):
+            g.add_oblique_wire(corners[q], corners[(q + 1) % 4], 0.002)
+        steps = 6000
+        V0 = 10.0
+        g.add_wire_voltage_source(0, 2, V0 * np.minimum(1.0, np.arange(steps) / 100.0), R)
+        g.finalize(steps)
+        g.step(steps)
+        I, _ = g.get_wire_state()
+        np.testing.assert_allclose(I, V0 / R, rtol=2e-4)
+
+
+def _feed_current(nx, x_end, steps=300):
+    g = OracleGrid(nx, 26, 26, 0.1, courant=0.95, parity=False)
+    g.set_cpml(8)
+    w = g.add_oblique_wire((12.0, 13.0, 13.0), (x_end, 13.0, 13.0), 0.002)
+    t = np.arange(steps)
+    g.add_wire_voltage_source(w, 0, 100.0 * np.exp(-((t - 40) / 12.0) ** 2))
+    g.add_wire_probe(w, 0)
+    g.finalize(steps)
+    g.step(steps)
+    return g.read_probe(0)
+
+
+def test_wire_ending_in_the_cpml_is_absorbed():
+    """a wire running into the CPML (matched lossy line there) feeds like an
+    endless one: the feed current over the window matches a wire too long
+    for its end to be seen, within 1 %; an open end at the same place
+    without the layer differs by far more"""
+    ref = _feed_current(150, 140.0)
+    into_layer = _feed_current(62, 60.0)
+    open_end = _feed_current(150, 60.0)
+    assert np.linalg.norm(into_layer - ref) / np.linalg.norm(ref) < 0.01
+    assert np.linalg.norm(open_end - ref) / np.linalg.norm(ref) > 0.1
