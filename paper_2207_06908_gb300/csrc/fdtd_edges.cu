@@ -20,44 +20,80 @@ __device__ __forceinline__ long long eidx(const EdgeArgs &a, int i, int j, int k
     return (long long)k * a.plane + (long long)j * a.pitch + i;
 }
 
+constexpr int kWireSegShared = 4096;  // segment currents kept in shared memory for the scatter
+
 // one step of the oblique wires (all threads of the CTA); every sum runs
-// in a fixed order, so a run repeats bit for bit
+// in a fixed order, so a run repeats bit for bit.  The gather is flattened
+// over (segment, edge) entries, staged in shared memory a chunk of whole
+// segments at a time, so the loads of all threads are in flight together.
 __device__ __forceinline__ void wire_body(const EdgeArgs &a, long long n)
 {
     const WireArgs &w = a.w;
-    // L' dl dI/dt = E_s dl - (V_b - V_a) + EMF - R I, centred at t_n (the
-    // R I term at the mean of the two half steps)
-    for (int s = threadIdx.x; s < w.n_seg; s += blockDim.x) {
-        const OSeg sg = w.seg[s];
-        float es = 0.f;
-        for (int e = sg.e0; e < sg.e0 + sg.ne; ++e) {
-            const OEdge ed = w.edge[e];
-            es += ed.wg * a.Ein[ed.comp][ed.idx];
+    __shared__ float prod[kWireChunk];
+    __shared__ float Ish[kWireSegShared];
+    for (int c = 0; c < w.n_chunk; ++c) {
+        // chunks of whole segments (host-built): segments own consecutive entry ranges
+        const int lo = w.chunk[c], hi = w.chunk[c + 1];
+        const int e_lo = w.seg[lo].e0;
+        const int n_e = w.seg[hi - 1].e0 + w.seg[hi - 1].ne - e_lo;
+#pragma unroll 4
+        for (int q = threadIdx.x; q < n_e; q += blockDim.x) {
+            const OEdge ed = w.edge[e_lo + q];
+            prod[q] = ed.wg * a.Ein[ed.comp][ed.idx];
         }
-        const ONode na = w.node[sg.a], nb = w.node[sg.b];
-        const float va = na.grounded ? 0.f : na.cV * w.Q[sg.a];
-        const float vb = nb.grounded ? 0.f : nb.cV * w.Q[sg.b];
-        float inc = sg.cI * es - sg.cIV * (vb - va);
-        for (int q = sg.s0; q < sg.s0 + sg.ns; ++q) {
-            const OSrc sr = w.src[q];
-            if (n < sr.n) inc += sr.cIV * w.samples[sr.off + n];
+        __syncthreads();
+        // L' dl dI/dt = E_s dl - (V_b - V_a) + EMF - R I, centred at t_n (the
+        // R I term at the mean of the two half steps)
+        for (int s = lo + threadIdx.x; s < hi; s += blockDim.x) {
+            const OSeg sg = w.seg[s];
+            float es = 0.f;
+            for (int e = sg.e0 - e_lo; e < sg.e0 - e_lo + sg.ne; ++e) es += prod[e];
+            const ONode na = w.node[sg.a], nb = w.node[sg.b];
+            const float va = na.grounded ? 0.f : na.cV * w.Q[sg.a];
+            const float vb = nb.grounded ? 0.f : nb.cV * w.Q[sg.b];
+            float inc = sg.cI * es - sg.cIV * (vb - va);
+            for (int q = sg.s0; q < sg.s0 + sg.ns; ++q) {
+                const OSrc sr = w.src[q];
+                if (n < sr.n) inc += sr.cIV * w.samples[sr.off + n];
+            }
+            const float I = sg.rk * w.I[s] + sg.rd * inc;
+            w.I[s] = I;
+            if (s < kWireSegShared) Ish[s] = I;
         }
-        w.I[s] = sg.rk * w.I[s] + sg.rd * inc;
+        __syncthreads();
     }
-    __syncthreads();
-    // the segment currents in Ampere's law at t_{n+1/2}; dQ/dt = net current in
-    for (int u = threadIdx.x; u < w.n_scat; u += blockDim.x) {
-        const OScat sc = w.scat[u];
-        float sum = 0.f;
-        for (int t = sc.t0; t < sc.t0 + sc.nt; ++t) sum += w.term[t].ws * w.I[w.term[t].seg];
-        a.E[sc.comp][sc.idx] -= sum;
+    auto cur = [&](int s) { return s < kWireSegShared ? Ish[s] : w.I[s]; };
+    // the segment currents in Ampere's law at t_{n+1/2}: four coupled edges
+    // per thread per pass, their field loads in flight together
+    for (int base = threadIdx.x; base < w.n_scat; base += 4 * blockDim.x) {
+        OScat sc[4];
+        float ev[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int u = base + k * blockDim.x;
+            if (u < w.n_scat) {
+                sc[k] = w.scat[u];
+                ev[k] = a.E[sc[k].comp][sc[k].idx];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (base + k * blockDim.x >= w.n_scat) break;
+            float sum = 0.f;
+            for (int t = sc[k].t0; t < sc[k].t0 + sc[k].nt; ++t) {
+                const OTerm tm = w.term[t];
+                sum += tm.ws * cur(tm.seg);
+            }
+            a.E[sc[k].comp][sc[k].idx] = ev[k] - sum;
+        }
     }
+    // dQ/dt = net current in
     for (int m = threadIdx.x; m < w.n_node; m += blockDim.x) {
         const ONode nd = w.node[m];
         float net = 0.f;
         for (int q = nd.adj0; q < nd.adj0 + nd.nadj; ++q) {
             const int t = w.adj[q];
-            net += (t & 1) ? w.I[t >> 1] : -w.I[t >> 1];
+            net += (t & 1) ? cur(t >> 1) : -cur(t >> 1);
         }
         w.Q[m] = nd.grounded ? 0.f : nd.aQ * w.Q[m] + nd.bQ * net;
     }
@@ -153,7 +189,9 @@ __global__ void edge_batch_kernel(const EdgeArgs *e, int parity)
 
 cudaError_t launch_edges(const EdgeArgs &a, cudaStream_t s)
 {
-    edge_kernel<<<1, 128, 0, s>>>(a);
+    // oblique wires are latency-bound loops over their segments and edges:
+    // a full CTA keeps enough loads in flight
+    edge_kernel<<<1, a.w.n_seg > 0 ? 1024 : 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -185,9 +185,12 @@ struct OSrc {
     long long off;           // offset into the wire sample table
     float cIV;               // dt / (L' dl) of its segment
 };
+constexpr int kWireChunk = 4096;      // gather entries the source/probe kernel stages at a time
 struct WireArgs {
     const OSeg *seg;
     int n_seg;
+    const int *chunk;        // [n_chunk + 1] first segment of each chunk of whole segments whose
+    int n_chunk;             // gather entries fit kWireChunk, then n_seg
     const OEdge *edge;
     const OScat *scat;
     int n_scat;

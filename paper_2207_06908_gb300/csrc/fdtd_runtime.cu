@@ -159,6 +159,8 @@ struct fdtd_grid {
     float *J = nullptr;
     // oblique wires on the device
     fdtd::OSeg *oseg_d = nullptr;
+    int *ochunk_d = nullptr;
+    int n_ochunk = 0;
     fdtd::OEdge *oedge_d = nullptr;
     fdtd::OScat *oscat_d = nullptr;
     fdtd::OTerm *oterm_d = nullptr;
@@ -190,7 +192,7 @@ int cuda_fail(fdtd_grid *g, cudaError_t e, const char *what)
 // ---- device arena plan -------------------------------------------------
 struct Plan {
     size_t field, cls, table, prof[3], psi[fdtd::PSI_COUNT], src, samples, probes, out, step, work, slot, items,
-        J, dcls, dtable, oseg, oedge, oscat, oterm, onode, oadj, oI, oQ, osrc, osamp, total;
+        J, dcls, dtable, oseg, ochunk, oedge, oscat, oterm, onode, oadj, oI, oQ, osrc, osamp, total;
 };
 
 // poles used by the grid (the largest pole count of a material some cell
@@ -257,6 +259,7 @@ Plan make_plan(const fdtd_grid *g, int capacity)
     for (const OSrcH &sr : g->osrcs) n_samp += sr.emf.size();
     const size_t n_os = std::max<size_t>(1, g->osegs.size()), n_on = std::max<size_t>(1, g->onodes.size());
     p.oseg = take(n_os * sizeof(fdtd::OSeg));
+    p.ochunk = take((n_os + 1) * sizeof(int));
     p.oedge = take(std::max<size_t>(1, n_edge) * sizeof(fdtd::OEdge));
     p.oscat = take(std::max<size_t>(1, n_edge) * sizeof(fdtd::OScat));
     p.oterm = take(std::max<size_t>(1, n_edge) * sizeof(fdtd::OTerm));
@@ -464,6 +467,7 @@ double cpml_rate(const fdtd_grid *g, int u, double x)
 }
 
 struct WireDev {
+    std::vector<int> chunk;          // first segment of each gather chunk, then n_seg
     std::vector<fdtd::OSeg> seg;
     std::vector<fdtd::OEdge> edge;
     std::vector<fdtd::OScat> scat;
@@ -536,6 +540,10 @@ WireDev wire_device(const fdtd_grid *g, const std::vector<uint8_t> &cls, const s
             adj[m].push_back((int)(s << 1) | end);
         }
     }
+    for (size_t s = 0; s < d.seg.size(); ++s)
+        if (d.chunk.empty() || d.seg[s].e0 + d.seg[s].ne - d.seg[d.chunk.back()].e0 > fdtd::kWireChunk)
+            d.chunk.push_back((int)s);
+    d.chunk.push_back((int)d.seg.size());
     for (auto &kv : scat) {
         d.scat.push_back(fdtd::OScat{kv.first.second, kv.first.first, (int)d.term.size(), (int)kv.second.size()});
         d.term.insert(d.term.end(), kv.second.begin(), kv.second.end());
@@ -900,6 +908,8 @@ fdtd::EdgeArgs edge_args(const fdtd_grid *g, int parity)
     for (int c = 0; c < 3; ++c) e.Ein[c] = g->F[parity][c];
     e.w.seg = g->oseg_d;
     e.w.n_seg = (int)g->osegs.size();
+    e.w.chunk = g->ochunk_d;
+    e.w.n_chunk = g->n_ochunk;
     e.w.edge = g->oedge_d;
     e.w.scat = g->oscat_d;
     e.w.n_scat = g->n_oscat;
@@ -1572,6 +1582,7 @@ int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_by
     g->dcls_d = (uint8_t *)(base + p.dcls);
     g->dtable_d = (float *)(base + p.dtable);
     g->oseg_d = (fdtd::OSeg *)(base + p.oseg);
+    g->ochunk_d = (int *)(base + p.ochunk);
     g->oedge_d = (fdtd::OEdge *)(base + p.oedge);
     g->oscat_d = (fdtd::OScat *)(base + p.oscat);
     g->oterm_d = (fdtd::OTerm *)(base + p.oterm);
@@ -1636,6 +1647,8 @@ int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_by
         if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
     };
     up(g->oseg_d, wd.seg.data(), wd.seg.size() * sizeof(fdtd::OSeg));
+    up(g->ochunk_d, wd.chunk.data(), wd.chunk.size() * sizeof(int));
+    g->n_ochunk = wd.chunk.empty() ? 0 : (int)wd.chunk.size() - 1;
     up(g->oedge_d, wd.edge.data(), wd.edge.size() * sizeof(fdtd::OEdge));
     up(g->oscat_d, wd.scat.data(), wd.scat.size() * sizeof(fdtd::OScat));
     up(g->oterm_d, wd.term.data(), wd.term.size() * sizeof(fdtd::OTerm));
