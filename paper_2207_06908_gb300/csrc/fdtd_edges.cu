@@ -29,8 +29,9 @@ constexpr int kWireSegShared = 4096;  // segment currents kept in shared memory 
 __device__ __forceinline__ void wire_body(const EdgeArgs &a, long long n)
 {
     const WireArgs &w = a.w;
-    __shared__ float prod[kWireChunk];
-    __shared__ float Ish[kWireSegShared];
+    // dynamic shared memory (only launches with oblique wires have it)
+    extern __shared__ float wire_smem[];
+    float *prod = wire_smem, *Ish = wire_smem + kWireChunk;
     for (int c = 0; c < w.n_chunk; ++c) {
         // chunks of whole segments (host-built): segments own consecutive entry ranges
         const int lo = w.chunk[c], hi = w.chunk[c + 1];
@@ -191,7 +192,9 @@ cudaError_t launch_edges(const EdgeArgs &a, cudaStream_t s)
 {
     // oblique wires are latency-bound loops over their segments and edges:
     // a full CTA keeps enough loads in flight
-    edge_kernel<<<1, a.w.n_seg > 0 ? 1024 : 128, 0, s>>>(a);
+    const bool wires = a.w.n_seg > 0;
+    const size_t smem = wires ? (kWireChunk + kWireSegShared) * sizeof(float) : 0;
+    edge_kernel<<<1, wires ? 1024 : 128, smem, s>>>(a);
     return cudaGetLastError();
 }
 

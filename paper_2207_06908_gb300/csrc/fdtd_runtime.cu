@@ -13,6 +13,7 @@
 #include <mutex>
 #include <array>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -202,9 +203,12 @@ struct Plan {
 int debye_extent(const fdtd_grid *g, int *z0, int *z1)
 {
     std::vector<int> np(g->table.size(), 0);
+    bool any = false;
     for (size_t m = 0; m < g->table.size(); ++m)
         for (int p = 0; p < fdtd::kMaxPoles; ++p)
-            if (g->poles[m][p] > 0) np[m] = p + 1;
+            if (g->poles[m][p] > 0) { np[m] = p + 1; any = true; }
+    *z0 = *z1 = 0;
+    if (!any) return 0;
     int P = 0, kmin = g->nz, kmax = -1;
     const size_t per = (size_t)g->nx * g->ny;
     for (size_t c = 0; c < g->mat.size(); ++c) {
@@ -734,68 +738,125 @@ int build_classes(fdtd_grid *g, std::vector<uint8_t> &cls, std::vector<float> &t
 {
     g->npoles = debye_extent(g, &g->dz0, &g->dz1);
     using Rec = std::array<uint32_t, fdtd::kDebyeRec>;
-    std::map<Rec, int> dids;
-    dtable.assign(fdtd::kDebyeRec, 0.f);          // record 0: no dispersive component
-    dids.emplace(Rec{}, 0);
-    auto did_of = [&](const float r[fdtd::kDebyeRec]) -> int {
-        Rec t;
-        std::memcpy(t.data(), r, sizeof t);
-        auto it = dids.find(t);
-        if (it != dids.end()) return it->second;
-        const int id = (int)dids.size();
-        dids.emplace(t, id);
-        dtable.insert(dtable.end(), r, r + fdtd::kDebyeRec);
-        return id;
-    };
-    dcls.assign((size_t)g->plane * g->nz, 0);
     WireMods w = wire_mods(g);
     Coefs C{g, &w};
-    std::map<Tuple, int> ids;
-    table.clear();
-    auto id_of = [&](const float v[fdtd::kNumCoef]) -> int {
-        Tuple t;
-        std::memcpy(t.data(), v, sizeof t);
-        auto it = ids.find(t);
-        if (it != ids.end()) return it->second;
-        const int id = (int)ids.size();
-        ids.emplace(t, id);
-        table.insert(table.end(), v, v + fdtd::kNumCoef);
-        return id;
-    };
-    // class of a cell inside a uniform block of one material, per material
-    std::vector<int> uniform_id(g->table.size(), -1), uniform_did(g->table.size(), 0);
-    cls.assign((size_t)g->plane * g->nz, 0);
     const int nx = g->nx, ny = g->ny, nz = g->nz;
-    for (int k = 0; k < nz; ++k)
-        for (int j = 0; j < ny; ++j)
-            for (int i = 0; i < nx; ++i) {
-                const size_t c = ((size_t)k * ny + j) * nx + i;
-                const uint8_t m0 = g->mat[c];
-                bool uni = i > 0 && j > 0 && k > 0 && !w.touched[c];
-                if (uni) {
+    cls.assign((size_t)g->plane * nz, 0);
+    dcls.assign((size_t)g->plane * nz, 0);
+    // Slabs of planes in parallel: each numbers its distinct coefficient sets
+    // (and Debye records) in first-encounter order and writes those local
+    // ids; merging the slabs in order then gives every set the id a single
+    // scan in k, j, i order would, whatever the thread count.
+    struct Slab {
+        std::vector<Tuple> tup;
+        std::vector<Rec> rec{Rec{}};        // local record 0: no dispersive component
+        bool over_cls = false, over_rec = false;
+    };
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int nth = std::max(1, std::min({(int)hw, 32, nz}));
+    std::vector<Slab> slabs(nth);
+    auto work = [&](int t) {
+        Slab &S = slabs[t];
+        std::map<Tuple, int> ids;
+        std::map<Rec, int> dids{{Rec{}, 0}};
+        std::vector<int> uniform_id(g->table.size(), -1), uniform_did(g->table.size(), 0);
+        const size_t sx = 1, sy = nx, sz = (size_t)nx * ny;
+        for (int k = nz * t / nth; k < nz * (t + 1) / nth; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    const size_t c = ((size_t)k * ny + j) * nx + i;
+                    const uint8_t m0 = g->mat[c];
                     // every cell that any owned component averages over
-                    const size_t sx = 1, sy = nx, sz = (size_t)nx * ny;
-                    uni = g->mat[c - sx] == m0 && g->mat[c - sy] == m0 && g->mat[c - sz] == m0 &&
-                          g->mat[c - sx - sy] == m0 && g->mat[c - sx - sz] == m0 &&
-                          g->mat[c - sy - sz] == m0;
+                    const bool uni = i > 0 && j > 0 && k > 0 && !w.touched[c] && g->mat[c - sx] == m0 &&
+                                     g->mat[c - sy] == m0 && g->mat[c - sz] == m0 && g->mat[c - sx - sy] == m0 &&
+                                     g->mat[c - sx - sz] == m0 && g->mat[c - sy - sz] == m0;
+                    int id, did = 0;
+                    if (uni && uniform_id[m0] >= 0) {
+                        id = uniform_id[m0];
+                        did = uniform_did[m0];
+                    } else {
+                        float v[fdtd::kNumCoef], r[fdtd::kDebyeRec];
+                        if (C.cell(i, j, k, v, r)) {
+                            Rec key;
+                            std::memcpy(key.data(), r, sizeof key);
+                            auto it = dids.find(key);
+                            if (it == dids.end()) {
+                                it = dids.emplace(key, (int)S.rec.size()).first;
+                                S.rec.push_back(key);
+                            }
+                            did = it->second;
+                        }
+                        Tuple key;
+                        std::memcpy(key.data(), v, sizeof key);
+                        auto it = ids.find(key);
+                        if (it == ids.end()) {
+                            it = ids.emplace(key, (int)S.tup.size()).first;
+                            S.tup.push_back(key);
+                        }
+                        id = it->second;
+                        if (uni) { uniform_id[m0] = id; uniform_did[m0] = did; }
+                    }
+                    if (id >= fdtd::kMaxClasses) { S.over_cls = true; return; }
+                    if (did >= fdtd::kMaxClasses) { S.over_rec = true; return; }
+                    cls[(size_t)k * g->plane + (size_t)j * g->pitch + i] = (uint8_t)id;
+                    dcls[(size_t)k * g->plane + (size_t)j * g->pitch + i] = (uint8_t)did;
                 }
-                int id, did = 0;
-                if (uni && uniform_id[m0] >= 0) {
-                    id = uniform_id[m0];
-                    did = uniform_did[m0];
-                } else {
-                    float v[fdtd::kNumCoef], r[fdtd::kDebyeRec];
-                    if (C.cell(i, j, k, v, r)) did = did_of(r);
-                    id = id_of(v);
-                    if (uni) { uniform_id[m0] = id; uniform_did[m0] = did; }
-                }
-                if (id >= fdtd::kMaxClasses)
-                    return fail(g, FDTD_ECLASSES, "more than 256 distinct coefficient classes");
-                if (did >= fdtd::kMaxClasses)
-                    return fail(g, FDTD_ECLASSES, "more than 255 distinct dispersive-media records");
-                cls[(size_t)k * g->plane + (size_t)j * g->pitch + i] = (uint8_t)id;
-                dcls[(size_t)k * g->plane + (size_t)j * g->pitch + i] = (uint8_t)did;
+    };
+    {
+        std::vector<std::thread> pool;
+        for (int t = 1; t < nth; ++t) pool.emplace_back(work, t);
+        work(0);
+        for (auto &th : pool) th.join();
+    }
+    std::map<Tuple, int> ids;
+    std::map<Rec, int> dids{{Rec{}, 0}};
+    table.clear();
+    dtable.assign(fdtd::kDebyeRec, 0.f);
+    std::vector<std::array<uint8_t, fdtd::kMaxClasses>> remap(nth), dremap(nth);
+    for (int t = 0; t < nth; ++t) {
+        const Slab &S = slabs[t];
+        if (S.over_cls) return fail(g, FDTD_ECLASSES, "more than 256 distinct coefficient classes");
+        if (S.over_rec) return fail(g, FDTD_ECLASSES, "more than 255 distinct dispersive-media records");
+        for (size_t q = 0; q < S.tup.size(); ++q) {
+            auto it = ids.find(S.tup[q]);
+            if (it == ids.end()) {
+                it = ids.emplace(S.tup[q], (int)ids.size()).first;
+                const float *v = reinterpret_cast<const float *>(S.tup[q].data());
+                table.insert(table.end(), v, v + fdtd::kNumCoef);
             }
+            if (it->second >= fdtd::kMaxClasses)
+                return fail(g, FDTD_ECLASSES, "more than 256 distinct coefficient classes");
+            remap[t][q] = (uint8_t)it->second;
+        }
+        for (size_t q = 0; q < S.rec.size(); ++q) {
+            auto it = dids.find(S.rec[q]);
+            if (it == dids.end()) {
+                it = dids.emplace(S.rec[q], (int)dids.size()).first;
+                const float *r = reinterpret_cast<const float *>(S.rec[q].data());
+                dtable.insert(dtable.end(), r, r + fdtd::kDebyeRec);
+            }
+            if (it->second >= fdtd::kMaxClasses)
+                return fail(g, FDTD_ECLASSES, "more than 255 distinct dispersive-media records");
+            dremap[t][q] = (uint8_t)it->second;
+        }
+    }
+    {
+        auto relabel = [&](int t) {
+            for (int k = nz * t / nth; k < nz * (t + 1) / nth; ++k)
+                for (int j = 0; j < ny; ++j) {
+                    uint8_t *cr = cls.data() + (size_t)k * g->plane + (size_t)j * g->pitch;
+                    uint8_t *dr = dcls.data() + (size_t)k * g->plane + (size_t)j * g->pitch;
+                    for (int i = 0; i < nx; ++i) {
+                        cr[i] = remap[t][cr[i]];
+                        dr[i] = dremap[t][dr[i]];
+                    }
+                }
+        };
+        std::vector<std::thread> pool;
+        for (int t = 1; t < nth; ++t) pool.emplace_back(relabel, t);
+        relabel(0);
+        for (auto &th : pool) th.join();
+    }
     g->n_classes = (int)ids.size();
     g->n_drec = (int)dids.size();
     src_cb.clear();
