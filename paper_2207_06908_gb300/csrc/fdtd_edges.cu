@@ -4,10 +4,11 @@
 // H around an edge), applied right after the step kernel (and, with Debye
 // media, the dispersive-media kernel) of the same step.
 // Oblique thin wires (Sec. 2.3, the Guiffaut formalism read in
-// Holland-Simpson form) advance here too, before the sources: segment
-// currents to t_{n+1/2} from E^n gathered along each segment and the node
-// potentials, the currents into E^{n+1} through the same edge shares, node
-// charges to t_{n+1}.
+// Holland-Simpson form): a separate kernel, concurrent with the step
+// kernels, takes the segment currents to t_{n+1/2} from E^n gathered along
+// each segment and the node potentials; this kernel, before the sources,
+// adds those currents to E^{n+1} through the same edge shares and takes the
+// node charges to t_{n+1}.
 // One CTA; a device-side step counter indexes the source samples and the
 // probe slots, so the launch can be replayed inside a CUDA graph.
 #include "fdtd_internal.h"
@@ -22,16 +23,18 @@ __device__ __forceinline__ long long eidx(const EdgeArgs &a, int i, int j, int k
 
 constexpr int kWireSegShared = 4096;  // segment currents kept in shared memory for the scatter
 
-// one step of the oblique wires (all threads of the CTA); every sum runs
-// in a fixed order, so a run repeats bit for bit.  The gather is flattened
-// over (segment, edge) entries, staged in shared memory a chunk of whole
-// segments at a time, so the loads of all threads are in flight together.
-__device__ __forceinline__ void wire_body(const EdgeArgs &a, long long n)
+// Oblique wires, first half of a step (all threads of the CTA): segment
+// currents to t_{n+1/2} from E^n (the step's input, which the step kernels
+// only read) and Q^n, so this runs concurrently with the step kernels.  Every
+// sum has a fixed order, so a run repeats bit for bit.  The gather is
+// flattened over (segment, edge) entries and staged in shared memory a
+// chunk of whole segments at a time, so the loads of all threads are in
+// flight together.
+__device__ __forceinline__ void wire_gather_body(const EdgeArgs &a, long long n)
 {
     const WireArgs &w = a.w;
-    // dynamic shared memory (only launches with oblique wires have it)
     extern __shared__ float wire_smem[];
-    float *prod = wire_smem, *Ish = wire_smem + kWireChunk;
+    float *prod = wire_smem;
     for (int c = 0; c < w.n_chunk; ++c) {
         // chunks of whole segments (host-built): segments own consecutive entry ranges
         const int lo = w.chunk[c], hi = w.chunk[c + 1];
@@ -57,15 +60,23 @@ __device__ __forceinline__ void wire_body(const EdgeArgs &a, long long n)
                 const OSrc sr = w.src[q];
                 if (n < sr.n) inc += sr.cIV * w.samples[sr.off + n];
             }
-            const float I = sg.rk * w.I[s] + sg.rd * inc;
-            w.I[s] = I;
-            if (s < kWireSegShared) Ish[s] = I;
+            w.I[s] = sg.rk * w.I[s] + sg.rd * inc;
         }
         __syncthreads();
     }
+}
+
+// second half, after the step kernels: the segment currents in Ampere's law
+// at t_{n+1/2} (four coupled edges per thread per pass, their field loads in
+// flight together), then the node charges to t_{n+1}
+__device__ __forceinline__ void wire_scatter_body(const EdgeArgs &a)
+{
+    const WireArgs &w = a.w;
+    extern __shared__ float wire_smem[];
+    float *Ish = wire_smem;
+    for (int s = threadIdx.x; s < w.n_seg && s < kWireSegShared; s += blockDim.x) Ish[s] = w.I[s];
+    __syncthreads();
     auto cur = [&](int s) { return s < kWireSegShared ? Ish[s] : w.I[s]; };
-    // the segment currents in Ampere's law at t_{n+1/2}: four coupled edges
-    // per thread per pass, their field loads in flight together
     for (int base = threadIdx.x; base < w.n_scat; base += 4 * blockDim.x) {
         OScat sc[4];
         float ev[4];
@@ -88,7 +99,6 @@ __device__ __forceinline__ void wire_body(const EdgeArgs &a, long long n)
             a.E[sc[k].comp][sc[k].idx] = ev[k] - sum;
         }
     }
-    // dQ/dt = net current in
     for (int m = threadIdx.x; m < w.n_node; m += blockDim.x) {
         const ONode nd = w.node[m];
         float net = 0.f;
@@ -107,7 +117,7 @@ __device__ __forceinline__ void edge_body(const EdgeArgs &a)
     if (threadIdx.x == 0) n_s = *a.step;
     __syncthreads();
     const long long n = n_s;
-    if (a.w.n_seg > 0) wire_body(a, n);
+    if (a.w.n_seg > 0) wire_scatter_body(a);
     for (int q = threadIdx.x; q < a.n_src; q += blockDim.x) {
         const SourceDesc sd = a.src[q];
         if (sd.hard) continue;
@@ -178,6 +188,14 @@ __device__ __forceinline__ void edge_body(const EdgeArgs &a)
 
 __global__ void edge_kernel(const EdgeArgs a) { edge_body(a); }
 
+__global__ void wire_gather_kernel(const EdgeArgs a)
+{
+    __shared__ long long n_s;
+    if (threadIdx.x == 0) n_s = *a.step;
+    __syncthreads();
+    wire_gather_body(a, n_s);
+}
+
 __global__ void edge_batch_kernel(const EdgeArgs *e, int parity)
 {
     __shared__ EdgeArgs a;
@@ -193,8 +211,15 @@ cudaError_t launch_edges(const EdgeArgs &a, cudaStream_t s)
     // oblique wires are latency-bound loops over their segments and edges:
     // a full CTA keeps enough loads in flight
     const bool wires = a.w.n_seg > 0;
-    const size_t smem = wires ? (kWireChunk + kWireSegShared) * sizeof(float) : 0;
-    edge_kernel<<<1, wires ? 1024 : 128, smem, s>>>(a);
+    edge_kernel<<<1, wires ? 1024 : 128, wires ? kWireSegShared * sizeof(float) : 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wire_gather(const EdgeArgs &a, cudaStream_t s)
+{
+    // latency-bound loops over segments and edges: a full CTA keeps enough
+    // loads in flight
+    wire_gather_kernel<<<1, 1024, kWireChunk * sizeof(float), s>>>(a);
     return cudaGetLastError();
 }
 

@@ -237,6 +237,9 @@ void step_region(const PsiGeom &pg, int zxy, int *region, int *ox, int *oy);
 const void *step_kernel_ptr(int nh, bool batch);
 // fdtd_edges.cu
 cudaError_t launch_edges(const EdgeArgs &a, cudaStream_t s);
+// oblique wires: segment currents to t_{n+1/2}; needs only the step's inputs,
+// so it may run concurrently with the step kernels, and before launch_edges
+cudaError_t launch_wire_gather(const EdgeArgs &a, cudaStream_t s);
 cudaError_t launch_debye(const DebyeArgs &a, cudaStream_t s);
 // one CTA per domain: e[2 * d + parity]
 cudaError_t launch_edges_batch(const EdgeArgs *e, int n_domains, int parity, cudaStream_t s);

@@ -1040,9 +1040,17 @@ cudaError_t enqueue_step(fdtd_grid *g, int parity, cudaStream_t s)
                                      g->lc[l].grid, st);
         };
     };
-    if (g->n_launch == 2 && g->fk.side) {
-        e = g->fk.run(s, launch(1), launch(0));
+    const bool wires = !g->osegs.empty();
+    if (g->fk.side && (g->n_launch == 2 || wires)) {
+        // side stream: the oblique wires' gather, then the z-layer launch
+        auto side = [g, parity, wires, &launch](cudaStream_t st) {
+            cudaError_t r = wires ? fdtd::launch_wire_gather(edge_args(g, parity), st) : cudaSuccess;
+            if (r == cudaSuccess && g->n_launch == 2) r = launch(1)(st);
+            return r;
+        };
+        e = g->fk.run(s, side, launch(0));
     } else {
+        if (wires) e = fdtd::launch_wire_gather(edge_args(g, parity), s);
         for (int l = 0; l < g->n_launch && e == cudaSuccess; ++l) e = launch(l)(s);
     }
     if (e == cudaSuccess && g->npoles) e = fdtd::launch_debye(debye_args(g, parity), s);
@@ -1207,6 +1215,7 @@ int step_with_scratch(fdtd_grid *g, int n, int *scratch, int scratch_ints)
     if (e != cudaSuccess) return cuda_fail(g, e, "scratch clear");
     g->noalloc_err = scratch + 2 * g->n_launch;
     for (; n > 0; --n) {
+        if (!g->osegs.empty()) e = launch_wire_gather(edge_args(g, g->parity), g->stream);
         for (int l = 0; l < g->n_launch && e == cudaSuccess; ++l)
             e = launch_step(single_args(g, g->parity, l), grid_launch(g, g->parity, l, scratch + 2 * l, g->noalloc_err),
                             g->lc[l].grid, g->stream);
@@ -1721,7 +1730,7 @@ int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_by
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(g, e, "upload");
     if (int rc = setup_step_kernel(g)) return rc;
-    if (g->n_launch == 2 && !g->fk.side) {
+    if ((g->n_launch == 2 || !g->osegs.empty()) && !g->fk.side) {
         e = g->fk.init();
         if (e != cudaSuccess) return cuda_fail(g, e, "side stream");
     }
