@@ -42,9 +42,12 @@ def args_parse():
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="single", choices=["single", "config3", "debye", "batch", "surrogate"],
+    ap.add_argument("--workload", default="single",
+                    choices=["single", "config3", "debye", "tower", "batch", "surrogate"],
                     help="single: the 256^3 grid (headline); config3: the 512x512x384 buried-mesh grid; "
-                         "batch: 256 grounding domains in one batch; surrogate: the learned surrogate vs FDTD")
+                         "debye: the 256^3 grid over four-pole Debye soil; tower: a lightning strike to a "
+                         "lattice tower of oblique wires (160x160x200); batch: 256 grounding domains in one "
+                         "batch; surrogate: the learned surrogate vs FDTD")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n", type=int, default=256,
@@ -60,6 +63,9 @@ def workload(n_steps, n=256, name="single"):
         return workloads.config3(n_steps=n_steps)
     if name == "debye":
         return workloads.debye_soil(n_steps=n_steps, n=n)
+    if name == "tower":
+        # the lightning-strike workload in a domain whose state exceeds L2
+        return workloads.lightning_tower("oblique", n_steps=n_steps, n=(160, 160, 200))
     return workloads.config2(n_steps=n_steps, n=n)
 
 
@@ -68,6 +74,10 @@ def workload_config(sc, steps):
     if getattr(sc, "debye", None):
         desc = (f"{sc.n[0]}^3 Yee grid dx=0.5m, 10-cell CPML, air over a four-pole Debye soil (eps_inf 16.381, "
                 "sigma 2.684 mS/m, the paper's measured-soil fit), 30 m thin wire r=5mm, 1.2/50us 10kA source, 6 probes")
+    elif sc.name.startswith("lightning_tower"):
+        desc = (f"{sc.n[0]}x{sc.n[1]}x{sc.n[2]} Yee grid dx=0.5m, 10-cell CPML, lossy soil (eps_r 10, sigma 2 mS/m), "
+                "30 m lattice tower of oblique thin wires (r=2cm), phase conductor, lightning channel "
+                "(10 kA Heidler behind 400 ohm), insulator voltage and channel current probes")
     elif sc.n == (512, 512, 384):
         desc = ("512x512x384 Yee grid dx=0.25m, 12-cell CPML, two-layer soil, buried 8x8 thin-wire mesh "
                 "(r=6mm) with down-conductor, current and voltage leads, 1 kA 0.5us ramp source")
@@ -237,7 +247,8 @@ def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    sc = workload(a.steps + a.warmup, a.n, a.workload if a.workload in ("single", "config3", "debye") else "single")
+    sc = workload(a.steps + a.warmup, a.n,
+                  a.workload if a.workload in ("single", "config3", "debye", "tower") else "single")
     from oracle import oracle as O
     o = O.OracleGrid.from_scenario(sc, parity=False)
     w = 2
@@ -552,7 +563,8 @@ def main():
                 "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic", "config": workload_config(sc, K),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": (4 if getattr(sc, "debye", None) else 3) * K, "finite": finite}
+                "gpu_launches": (3 + bool(getattr(sc, "debye", None)) + bool(getattr(sc, "owires", None))) * K,
+                "finite": finite}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

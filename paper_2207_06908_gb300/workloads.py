@@ -514,7 +514,8 @@ def tower_members(x0=36, y0=36, zs=20):
 def lightning_tower(model="oblique", n_steps=3000, i0=10e3, n=(72, 72, 100)):
     """Direct strike to a lattice tower over lossy soil (the lightning
     overvoltage example of the paper, with a synthetic tower): soil eps_r 10,
-    sigma 2 mS/m below the node plane 20, 10-cell CPML, dx = 0.5 m; the tower
+    sigma 2 mS/m below the node plane 20, 10-cell CPML, dx = 0.5 m, the tower
+    at the centre of the n[0] x n[1] plan (72 x 72 x 100 cells by default); the tower
     of tower_members() in the oblique wire model or as staircase wires; a
     phase conductor along y 2 m below the +x arm tip (axis-aligned thin wire
     in both cases, into the CPML); a vertical lightning channel from the
@@ -525,8 +526,8 @@ def lightning_tower(model="oblique", n_steps=3000, i0=10e3, n=(72, 72, 100)):
     arm tip's in-cell potential (the insulator voltage is the sum of the
     first and the last).  Courant 0.93 (below the oblique members' limit,
     used for both models)."""
-    x0, y0, zs = 36, 36, 20
     nx, ny, nz = n
+    x0, y0, zs = nx // 2, ny // 2, 20
     cm = np.zeros((nz, ny, nx), np.uint8)
     cm[:zs] = 1
     mats = [(1.0, 0.0, 1.0), (10.0, 2e-3, 1.0)]
