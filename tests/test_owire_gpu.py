@@ -158,3 +158,37 @@ def test_lightning_tower_oblique_matches_oracle_and_staircase(fdtd):
     assert np.linalg.norm(vo - vs) / np.linalg.norm(vs) < 0.2
     go.close()
     gs.close()
+
+
+def test_oblique_wire_edge_cases(fdtd):
+    """a wire lying in the z = 0 wall (every node grounded, no edge to couple
+    to: the fields are those of the same grid without it), a one-segment
+    wire, and a wire from corner to corner through the CPML, against the
+    oracle"""
+    steps = 40
+    base = W.random_scenario(61, n=(18, 16, 14), cpml=3, n_wires=0, n_steps=steps, courant=0.9)
+    sc = W.random_scenario(61, n=(18, 16, 14), cpml=3, n_wires=0, n_steps=steps, courant=0.9)
+    sc.owires = [((2.0, 3.0, 0.0), (15.0, 12.0, 0.0), 0.003),          # in the wall
+                 ((8.2, 7.6, 6.1), (9.0, 8.1, 6.7), 0.002),            # one segment
+                 ((0.5, 0.5, 0.5), (17.5, 15.5, 13.5), 0.002)]         # corner to corner
+    t = np.arange(steps)
+    sc.owire_sources = [(1, 0, 80.0 * np.sin(0.2 * t)), (2, 3, 40.0 * np.cos(0.1 * t), 20.0)]
+    sc.owire_probes = [(0, 2), (1, 0), (2, 10), (8.2, 7.6, 6.1)]
+    g = compare(fdtd, sc, steps)
+    I, Q = g.get_wire_state()
+    n0 = round(((15 - 2) ** 2 + (12 - 3) ** 2) ** 0.5)
+    assert np.all(Q[: n0 + 1] == 0)                                   # the wall wire's nodes are grounded
+    g.close()
+    # the wall wire alone changes nothing
+    wall = W.random_scenario(61, n=(18, 16, 14), cpml=3, n_wires=0, n_steps=steps, courant=0.9)
+    wall.owires = [sc.owires[0]]
+    a = fdtd.from_scenario(base, probe_capacity=steps)
+    b = fdtd.from_scenario(wall, probe_capacity=steps)
+    for gg in (a, b):
+        for c, f in enumerate(base.fields):
+            gg.set_field(c, f)
+        gg.step(steps)
+    for c in range(6):
+        assert np.array_equal(a.get_field(c), b.get_field(c))
+    a.close()
+    b.close()
