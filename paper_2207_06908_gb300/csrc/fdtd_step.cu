@@ -113,7 +113,7 @@ struct Layout {
 
 __host__ __device__ inline int smem_bytes(int n_classes, int d, int region, int nh)
 {
-    return Layout(region, nh).tab + al128(sizeof(StepArgs)) + n_classes * kTabStride * 4 + 3 * PR_COUNT * 2 * d * 4 +
+    return Layout(region, nh).tab + al128(sizeof(StepArgs)) + n_classes * kTabStride * 4 + 3 * 2 * 2 * d * 16 +
            128;
 }
 
@@ -224,13 +224,15 @@ __device__ __forceinline__ int slab_of(int i, int n, int d) { return i < d ? i :
 
 // CPML convolution of the two differences along one axis (Sec. 2.2): with
 // the profile b, c, 1/kappa of the cell's slab entry s,
-// psi <- b psi + c dif, dif <- dif / kappa + psi.  The profile values are
-// read once for both differences, before any store.
+// psi <- b psi + c dif, dif <- dif / kappa + psi.  The profile row holds
+// {b, c, 1/kappa, -} per slab entry, read with one 16-byte load for both
+// differences, before any store.
 template <bool WRITE>
-__device__ __forceinline__ void cpml2(float &d0, float &d1, const float *pr, int s, int d2, float o0, float o1,
+__device__ __forceinline__ void cpml2(float &d0, float &d1, const float4 *pr, int s, float o0, float o1,
                                       float *out0, float *out1, long long g)
 {
-    const float b = pr[s], c = pr[d2 + s], ki = pr[2 * d2 + s];
+    const float4 pv = pr[s];
+    const float b = pv.x, c = pv.y, ki = pv.z;
     const float p0 = b * o0 + c * d0, p1 = b * o1 + c * d1;
     if (WRITE) {
         out0[g] = p0;
@@ -238,6 +240,13 @@ __device__ __forceinline__ void cpml2(float &d0, float &d1, const float *pr, int
     }
     d0 = d0 * ki + p0;
     d1 = d1 * ki + p1;
+}
+
+// profile row of axis u at E (h = 0) or H (h = 1) positions in the staged
+// profiles: [axis][E, H][2d slab entries] x {b, c, 1/kappa, -}
+__device__ __forceinline__ const float4 *prow(const float *prof, int u, int h, int d2)
+{
+    return reinterpret_cast<const float4 *>(prof) + (u * 2 + h) * d2;
 }
 
 // H^{n+1/2} of cell (i,j,k) from E^n around it (Eq. fdtdhx and its cyclic
@@ -258,24 +267,24 @@ __device__ __forceinline__ void h_core(const StepArgs &a, const float4 *t, const
     float hy_x = ez_x1 - ez, hy_z = ex_z1 - ex;
     float hz_y = ex_y1 - ex, hz_x = ey_x1 - ey;
     if (CPML) {
-        const int d2 = 2 * a.d, per = PR_COUNT * d2;
+        const int d2 = 2 * a.d;
         if (L.sx >= 0) {
             const int q = a.pg.xb >> 2;
             const float o0 = (STAGED || L.xo >= 0) ? L.base[L.xo] : __ldg(a.psi_in[PSI_HY_X] + g);
             const float o1 = (STAGED || L.xo >= 0) ? L.base[L.xo + q] : __ldg(a.psi_in[PSI_HZ_X] + g);
-            cpml2<WRITE>(hy_x, hz_x, prof + PR_BH * d2, L.sx, d2, o0, o1, a.psi_out[PSI_HY_X], a.psi_out[PSI_HZ_X], g);
+            cpml2<WRITE>(hy_x, hz_x, prow(prof, 0, 1, d2), L.sx, o0, o1, a.psi_out[PSI_HY_X], a.psi_out[PSI_HZ_X], g);
         }
         if (L.sy >= 0) {
             const int q = a.pg.yb >> 2;
             const float o0 = (STAGED || L.yo >= 0) ? L.base[L.yo] : __ldg(a.psi_in[PSI_HX_Y] + g);
             const float o1 = (STAGED || L.yo >= 0) ? L.base[L.yo + q] : __ldg(a.psi_in[PSI_HZ_Y] + g);
-            cpml2<WRITE>(hx_y, hz_y, prof + per + PR_BH * d2, L.sy, d2, o0, o1, a.psi_out[PSI_HX_Y],
+            cpml2<WRITE>(hx_y, hz_y, prow(prof, 1, 1, d2), L.sy, o0, o1, a.psi_out[PSI_HX_Y],
                        a.psi_out[PSI_HZ_Y], g);
         }
         if (L.sz >= 0) {
             const float o0 = (STAGED || L.zo >= 0) ? L.base[L.zo] : __ldg(a.psi_in[PSI_HX_Z] + g);
             const float o1 = (STAGED || L.zo >= 0) ? L.base[L.zo + H_COMP / 4] : __ldg(a.psi_in[PSI_HY_Z] + g);
-            cpml2<WRITE>(hx_z, hy_z, prof + 2 * per + PR_BH * d2, L.sz, d2, o0, o1, a.psi_out[PSI_HX_Z],
+            cpml2<WRITE>(hx_z, hy_z, prow(prof, 2, 1, d2), L.sz, o0, o1, a.psi_out[PSI_HX_Z],
                        a.psi_out[PSI_HY_Z], g);
         }
     }
@@ -298,19 +307,19 @@ __device__ __forceinline__ void e_core(const StepArgs &a, const float4 *t, const
     float ey_z = hx - hx_zm, ey_x = hz - hz_xm;
     float ez_x = hy - hy_xm, ez_y = hx - hx_ym;
     if (CPML) {
-        const int d2 = 2 * a.d, per = PR_COUNT * d2;
+        const int d2 = 2 * a.d;
         if (L.sx >= 0) {
             const int q = a.pg.xb >> 2;
-            cpml2<true>(ey_x, ez_x, prof + PR_BE * d2, L.sx, d2, L.base[L.xo + 2 * q], L.base[L.xo + 3 * q],
+            cpml2<true>(ey_x, ez_x, prow(prof, 0, 0, d2), L.sx, L.base[L.xo + 2 * q], L.base[L.xo + 3 * q],
                         a.psi_out[PSI_EY_X], a.psi_out[PSI_EZ_X], g);
         }
         if (L.sy >= 0) {
             const int q = a.pg.yb >> 2;
-            cpml2<true>(ex_y, ez_y, prof + per + PR_BE * d2, L.sy, d2, L.base[L.yo + 2 * q], L.base[L.yo + 3 * q],
+            cpml2<true>(ex_y, ez_y, prow(prof, 1, 0, d2), L.sy, L.base[L.yo + 2 * q], L.base[L.yo + 3 * q],
                         a.psi_out[PSI_EX_Y], a.psi_out[PSI_EZ_Y], g);
         }
         if (L.sz >= 0)
-            cpml2<true>(ex_z, ey_z, prof + 2 * per + PR_BE * d2, L.sz, d2, L.base[L.zeo],
+            cpml2<true>(ex_z, ey_z, prow(prof, 2, 0, d2), L.sz, L.base[L.zeo],
                         L.base[L.zeo + PE_BYTES / 4], a.psi_out[PSI_EX_Z], a.psi_out[PSI_EY_Z], g);
     }
     const float4 ca = t[1], cb = t[2];
@@ -651,7 +660,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
     const Layout Lo(B.region, NH);
     StepArgs *sa = reinterpret_cast<StepArgs *>(smem + Lo.tab);          // current domain's arguments
     float *tab = reinterpret_cast<float *>(smem + Lo.tab + al128(sizeof(StepArgs)));
-    float *prof = tab + B.max_classes * kTabStride;  // [axis][PR_COUNT][2d], slab entries only
+    float *prof = tab + B.max_classes * kTabStride;  // [axis][E, H][2d] x {b, c, 1/kappa, -}, slab entries only
     float *hnew = reinterpret_cast<float *>(smem + Lo.hnew);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + Lo.bar);
     volatile int *abort = reinterpret_cast<volatile int *>(smem + Lo.misc);
@@ -674,7 +683,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
                 const int u = q / per, w = (q - u * per) / d2, sl = q - u * per - w * d2;
                 const int n = u == 0 ? ga.nx : (u == 1 ? ga.ny : ga.nz);
                 const int i = sl < ga.d ? sl : n - d2 + sl;
-                prof[q] = __ldg(ga.prof[u] + w * n + i);
+                prof[(((u * 2 + w / 3) * d2 + sl) << 2) + w % 3] = __ldg(ga.prof[u] + w * n + i);
             }
         }
     }
@@ -816,7 +825,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
                         const int u = q / per, w = (q - u * per) / d2, sl = q - u * per - w * d2;
                         const int n = u == 0 ? ga.nx : (u == 1 ? ga.ny : ga.nz);
                         const int i = sl < ga.d ? sl : n - d2 + sl;
-                        prof[q] = __ldg(ga.prof[u] + w * n + i);
+                        prof[(((u * 2 + w / 3) * d2 + sl) << 2) + w % 3] = __ldg(ga.prof[u] + w * n + i);
                     }
                 }
                 cur = dom;
