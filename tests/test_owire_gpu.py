@@ -192,3 +192,31 @@ def test_oblique_wire_edge_cases(fdtd):
         assert np.array_equal(a.get_field(c), b.get_field(c))
     a.close()
     b.close()
+
+
+def test_lightning_tower_at_bench_size(fdtd):
+    """the tower workload as the benchmark times it (160 x 160 x 200 cells,
+    state above L2), 600 steps from rest: the probes and wire state within
+    1e-4 of the oracle; the fields within the from-rest bar, max(1e-5, 2x
+    the error of the same algorithm with FP32 storage on the CPU) — the
+    strike's near field dwarfs the field left elsewhere, so rounding its
+    FP32 stores already costs about 1e-5"""
+    from oracle.oracle import OracleGrid
+    steps = 600
+    sc = W.lightning_tower("oblique", n_steps=steps, n=(160, 160, 200))
+    g = fdtd.from_scenario(sc, probe_capacity=steps)
+    g.step(steps)
+    o = oracle_from_scenario(sc, parity=True)
+    o.step(steps)
+    y = OracleGrid.from_scenario(sc, parity=True, f32=True)
+    y.step(steps)
+    for c in range(6):
+        ref = o.get_field(c)
+        bar = max(1e-5, 2.0 * rel_l2(y.get_field(c), ref))
+        assert rel_l2(g.get_field(c), ref) <= bar, c
+    for p in range(3):
+        assert rel_l2(g.read_probe(p), o.read_probe(p)) <= 1e-4, p
+    I, Q = g.get_wire_state()
+    Io, Qo = o.get_wire_state()
+    assert rel_l2(I, Io) <= 1e-4 and rel_l2(Q, Qo) <= 1e-4
+    g.close()

@@ -94,3 +94,35 @@ def test_training_learns_fdtd_waveforms(env):
     S.fit(net, F[:256], T[:256], w[:256], epochs=400, batch=64, lr=1e-3)
     e_tr, e_ho = err(0, 256), err(256, 320)
     assert e_tr <= 0.05 and e_ho <= 0.1 and e_ho <= e0 / 5, (e0, e_tr, e_ho)
+
+
+def test_full_batch_inference_matches_network_oracle(env):
+    """The inference the benchmark times (batch 4096 replayed from the
+    captured graph): on 64 sampled rows the waveform network and the error
+    head agree with the FP64 network oracle on the same BF16 weights and
+    BF16-rounded inputs within 1e-2 (relative L2)"""
+    torch, S, W = env
+    from oracle import mlp_oracle as M
+    from paper_2207_06908_gb300 import mlp
+    sur = S.Surrogate.load(S.WEIGHTS)
+    B = 4096
+    f = S.features(held_out(W, S, B))
+    x, replay, (wave, log_err) = sur.predict_graph(B)
+    x.copy_(torch.from_numpy(np.ascontiguousarray(f, dtype=np.float32)))
+    replay()
+    torch.cuda.synchronize()
+    wave, log_err = wave.cpu().numpy(), log_err.cpu().numpy()
+    rows = np.random.default_rng(5).choice(B, 64, replace=False)
+    xin = M.bf16(np.asarray(f, np.float32)[rows].astype(np.float64))
+
+    def reference(net):
+        layers = [(Wb.float().cpu().numpy().astype(np.float64), b.cpu().numpy().astype(np.float64))
+                  for Wb, b in zip(net.Wb, net.b)]
+        acts = ["gelu" if a == mlp.ACT_GELU else "none" for a in net.acts]
+        return M.forward(xin, layers, acts)[2]
+
+    ref_wave = reference(sur.main) * S.Y_UNIT
+    got = wave[rows].astype(np.float64)
+    assert np.linalg.norm(got - ref_wave) / np.linalg.norm(ref_wave) <= 1e-2
+    ref_err = reference(sur.head).reshape(-1)
+    assert np.linalg.norm(log_err[rows] - ref_err) / np.linalg.norm(ref_err) <= 1e-2
