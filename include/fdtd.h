@@ -155,13 +155,15 @@ int fdtd_add_wire_path(fdtd_grid *g, int i0, int j0, int k0, int i1, int j1, int
  * the straight path between the segment's end nodes.  An end point equal
  * (within 1e-9) to a node of an earlier oblique wire joins that node
  * (junction: the currents of all segments at a node change its charge).  A
- * node on an outer wall is grounded (potential 0).  Inside a CPML a wire
+ * node on an outer wall is grounded (potential 0).  In Debye media the
+ * in-cell capacitance takes the node medium's poles: K Q = eps0 eps_inf V +
+ * sum_p P_p, K = ln(R/a) / (2 pi dl), tau_p dP_p/dt + P_p = eps0 deps_p V,
+ * with the conduction sigma V K drawn from the charge.  Inside a CPML a wire
  * is a matched lossy line (series resistance and shunt conductance per unit
  * length L' nu and C' nu, nu = sum_u t_u^2 sigma_u / (kappa_u eps0) at the
  * segment, t its direction), so a wire may run into the layer and end
  * there.  Thick wires lower the
- * stable Courant number (fdtd_wire_courant_limit).  Not allowed with Debye
- * media (fdtd_finalize fails with FDTD_EINVAL) or in batches
+ * stable Courant number (fdtd_wire_courant_limit).  Not allowed in batches
  * (fdtd_batch_create fails).  *wire_id (may be NULL) receives the index. */
 int fdtd_add_oblique_wire(fdtd_grid *g, double x0, double y0, double z0, double x1, double y1, double z1,
                           double radius, int *wire_id);
@@ -206,7 +208,7 @@ int fdtd_wire_counts(const fdtd_grid *g, int *n_segments, int *n_nodes);
 /* Oblique-wire state after fdtd_finalize: I = segment currents of the last
  * half step (A, n_segments floats), Q = node charges (C, n_nodes floats);
  * host buffers.  get synchronises the grid's stream; set writes grounded
- * nodes as 0. */
+ * nodes as 0 and starts every node without medium polarisation. */
 int fdtd_get_wire_state(fdtd_grid *g, float *I, float *Q);
 int fdtd_set_wire_state(fdtd_grid *g, const float *I, const float *Q);
 

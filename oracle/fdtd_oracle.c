@@ -80,7 +80,13 @@
  *     line, R'/L' = G'/C' = nu = sum_u t_u^2 sigma_u / (kappa_u eps0) (the
  *     layer's attenuation of a wave running along the wire; equal ratios
  *     keep its impedance), so its own wave is absorbed with the grid's;
- *     this is a reading, the paper is silent on wires in the layer.  Wires
+ *     this is a reading, the paper is silent on wires in the layer.  In a
+ *     Debye medium the in-cell capacitance takes the medium's dispersion
+ *     (the Debye extension of thin wires the paper cites, in this form):
+ *     K Q = eps0 eps_inf V + sum_p P_p with K = ln(R/a) / (2 pi dl_m),
+ *     tau_p dP_p/dt + P_p = eps0 deps_p V, dQ/dt = (net current in) -
+ *     (sigma / K) V, the last two by the trapezoidal rule; without poles
+ *     this is the charge update above.  Wires
  *     whose end points coincide share that node (junction, Kirchhoff's
  *     current law); a node on an outer wall is grounded (V = 0).  The
  *     in-cell radius is parity unpinned against the paper (pinned by
@@ -152,7 +158,11 @@ typedef struct {
     double p[3];                   /* node units */
     double dlm, lam_sum, nu_sum;   /* wire length it carries (m); sums of ln(R/a) and CPML rate of its segments */
     int nadj, grounded;
-    real cV, aQ, bQ;               /* V = cV Q; Q^{n+1} = aQ Q^n + bQ (net current in) */
+    /* in-cell medium: K Q = e0 V + sum_p P_p (K = ln(R/a) / (2 pi dl_m));
+     * Q^{n+1} = Q^n + dt (net current in) - (cs / K)(V^{n+1} + V^n);
+     * P_p^{n+1} = pa_p P_p^n + pb_p (V^{n+1} + V^n) */
+    real K, e0, cs, pa[ORC_MAXP], pb[ORC_MAXP];
+    double cV;                     /* K / e0 (V per unit charge without poles) */
 } orc_onode;
 typedef struct { int seg0, nseg; double radius; } orc_owire;
 typedef struct { int seg, n; real *emf; double r; } orc_osrc;   /* delta-gap EMF with series resistance r */
@@ -201,7 +211,7 @@ typedef struct orc_grid {
     orc_onode *onodes; int n_onodes;
     orc_owire *owires; int n_owires;
     orc_osrc *osrcs; int n_osrcs;
-    double *oI, *oQ;
+    double *oI, *oQ, *oV, *oP;     /* oP: [node][ORC_MAXP] */
     int max_steps;
     double *probe_out;         /* [n_probes][max_steps] */
     long step;
@@ -259,6 +269,7 @@ void orc_destroy(orc_grid *g)
     free(g->lumps); free(g->hard_coef);
     for (int s = 0; s < g->n_osrcs; s++) free(g->osrcs[s].emf);
     free(g->osegs); free(g->onodes); free(g->owires); free(g->osrcs); free(g->oI); free(g->oQ);
+    free(g->oV); free(g->oP);
     free(g->mat); free(g->m_eps); free(g->m_sig); free(g->m_mu);
     free(g);
 }
@@ -609,7 +620,13 @@ int orc_set_owire_state(orc_grid *g, const double *I, const double *Q)
 {
     if (!g->finalized) return -8;
     for (int s = 0; s < g->n_osegs; s++) g->oI[s] = I[s];
-    for (int m = 0; m < g->n_onodes; m++) g->oQ[m] = g->onodes[m].grounded ? 0.0 : Q[m];
+    for (int m = 0; m < g->n_onodes; m++) {
+        /* the charge with its medium polarisation-free: V = K Q / e0 */
+        const orc_onode *nd = &g->onodes[m];
+        g->oQ[m] = nd->grounded ? 0.0 : Q[m];
+        g->oV[m] = nd->grounded ? 0.0 : (double)nd->K * g->oQ[m] / (double)nd->e0;
+        for (int p = 0; p < ORC_MAXP; p++) g->oP[(size_t)m * ORC_MAXP + p] = 0.0;
+    }
     return 0;
 }
 
@@ -934,15 +951,26 @@ static int build_owires(orc_grid *g)
             ci[q] = (int)floor(nd->p[q]);
             if (ci[q] > nn[q] - 1) ci[q] = nn[q] - 1;
         }
-        double eps = ORC_EPS0 * cell_eps(g, ci[0], ci[1], ci[2]), sig = cell_sig(g, ci[0], ci[1], ci[2]);
+        int mat = g->mat[CELL(g, ci[0], ci[1], ci[2])];
+        double eps = ORC_EPS0 * g->m_eps[mat], sig = g->m_sig[mat];
         double lam = nd->lam_sum / nd->nadj;
-        double r = (sig / eps + nd->nu_sum / nd->nadj) * dt / 2.0;
-        nd->cV = r32(g, lam / (2.0 * M_PI * eps * nd->dlm));
-        nd->aQ = r32(g, (1.0 - r) / (1.0 + r));
-        nd->bQ = r32(g, dt / (1.0 + r));
+        double K = lam / (2.0 * M_PI * nd->dlm);
+        /* the CPML's loss acts as an extra conductance eps nu */
+        double sig_eff = sig + eps * nd->nu_sum / nd->nadj;
+        nd->K = r32(g, K);
+        nd->e0 = r32(g, eps);
+        nd->cs = r32(g, dt * sig_eff / 2.0);
+        for (int p = 0; p < ORC_MAXP; p++) {
+            double de = g->m_deps[mat][p], tau = g->m_tau[mat][p];
+            nd->pa[p] = de > 0 ? r32(g, (2.0 * tau - dt) / (2.0 * tau + dt)) : 0.0;
+            nd->pb[p] = de > 0 ? r32(g, dt * ORC_EPS0 * de / (2.0 * tau + dt)) : 0.0;
+        }
+        nd->cV = K / eps;
     }
     g->oI = (double *)calloc(g->n_osegs > 0 ? g->n_osegs : 1, sizeof(double));
     g->oQ = (double *)calloc(g->n_onodes > 0 ? g->n_onodes : 1, sizeof(double));
+    g->oV = (double *)calloc(g->n_onodes > 0 ? g->n_onodes : 1, sizeof(double));
+    g->oP = (double *)calloc((size_t)(g->n_onodes > 0 ? g->n_onodes : 1) * ORC_MAXP, sizeof(double));
     return 0;
 }
 
@@ -1112,7 +1140,7 @@ int orc_finalize(orc_grid *g, int max_steps)
     for (int c = 0; c < 3; c++) { free(le[c]); free(ls[c]); }
     for (int c = 0; c < 3; c++) { free(eps[c]); free(sig[c]); free(mu[c]); free(pec[c]); free(fac_e[c]); free(fac_h[c]); }
     build_cpml(g);
-    if (g->n_owires > 0 && (g->has_debye || build_owires(g) != 0)) return -1;
+    if (g->n_owires > 0 && build_owires(g) != 0) return -1;
     g->max_steps = max_steps;
     g->probe_out = (double *)calloc((size_t)(g->n_probes > 0 ? g->n_probes : 1) * (max_steps > 0 ? max_steps : 1), sizeof(double));
     g->finalized = 1;
@@ -1225,8 +1253,8 @@ static void owire_current(orc_grid *g)
         double es = 0.0;
         for (int e = 0; e < S->ne; e++) es += (double)S->wg[e] * g->f[S->comp[e]][S->q[e]];
         const orc_onode *A = &g->onodes[S->a], *B = &g->onodes[S->b];
-        double va = A->grounded ? 0.0 : (double)A->cV * g->oQ[S->a];
-        double vb = B->grounded ? 0.0 : (double)B->cV * g->oQ[S->b];
+        double va = A->grounded ? 0.0 : g->oV[S->a];
+        double vb = B->grounded ? 0.0 : g->oV[S->b];
         double inc = (double)S->cI * (es - (vb - va) / S->dl + drive[s] / S->dl);
         g->oI[s] = (double)S->rk * g->oI[s] + (double)S->rd * inc;
     }
@@ -1255,7 +1283,17 @@ static void owire_charge(orc_grid *g)
     }
     for (int m = 0; m < g->n_onodes; m++) {
         const orc_onode *nd = &g->onodes[m];
-        g->oQ[m] = nd->grounded ? 0.0 : (double)nd->aQ * g->oQ[m] + (double)nd->bQ * net[m];
+        if (nd->grounded) { g->oQ[m] = 0.0; g->oV[m] = 0.0; continue; }
+        /* V^{n+1} from K Q^{n+1} = e0 V^{n+1} + sum_p P_p^{n+1} with the
+         * charge and polarisation updates substituted */
+        double *P = g->oP + (size_t)m * ORC_MAXP;
+        double V = g->oV[m], spb = 0.0, spa = 0.0;
+        for (int p = 0; p < ORC_MAXP; p++) { spb += nd->pb[p]; spa += (double)nd->pa[p] * P[p]; }
+        double Vn = ((double)nd->K * (g->oQ[m] + g->dt * net[m]) - ((double)nd->cs + spb) * V - spa) /
+                    ((double)nd->e0 + spb + (double)nd->cs);
+        for (int p = 0; p < ORC_MAXP; p++) P[p] = (double)nd->pa[p] * P[p] + (double)nd->pb[p] * (Vn + V);
+        g->oQ[m] += g->dt * net[m] - (double)nd->cs / (double)nd->K * (Vn + V);
+        g->oV[m] = Vn;
     }
     free(net);
 }
@@ -1369,7 +1407,7 @@ static double probe_value(const orc_grid *g, const orc_probe *p)
 {
     double dx = g->dx;
     if (p->kind == PROBE_W) return g->oI[p->i];
-    if (p->kind == PROBE_WV) return g->onodes[p->i].grounded ? 0.0 : (double)g->onodes[p->i].cV * g->oQ[p->i];
+    if (p->kind == PROBE_WV) return g->onodes[p->i].grounded ? 0.0 : g->oV[p->i];
     if (p->kind == PROBE_E) return g->f[p->axis][IDX(g, p->i, p->j, p->k)];
     if (p->kind == PROBE_H) return g->f[3 + p->axis][IDX(g, p->i, p->j, p->k)];
     if (p->kind == PROBE_V) {

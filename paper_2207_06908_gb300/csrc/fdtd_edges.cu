@@ -52,9 +52,8 @@ __device__ __forceinline__ void wire_gather_body(const EdgeArgs &a, long long n)
             const OSeg sg = w.seg[s];
             float es = 0.f;
             for (int e = sg.e0 - e_lo; e < sg.e0 - e_lo + sg.ne; ++e) es += prod[e];
-            const ONode na = w.node[sg.a], nb = w.node[sg.b];
-            const float va = na.grounded ? 0.f : na.cV * w.Q[sg.a];
-            const float vb = nb.grounded ? 0.f : nb.cV * w.Q[sg.b];
+            const float va = w.node[sg.a].grounded ? 0.f : w.V[sg.a];
+            const float vb = w.node[sg.b].grounded ? 0.f : w.V[sg.b];
             float inc = sg.cI * es - sg.cIV * (vb - va);
             for (int q = sg.s0; q < sg.s0 + sg.ns; ++q) {
                 const OSrc sr = w.src[q];
@@ -101,12 +100,31 @@ __device__ __forceinline__ void wire_scatter_body(const EdgeArgs &a)
     }
     for (int m = threadIdx.x; m < w.n_node; m += blockDim.x) {
         const ONode nd = w.node[m];
+        if (nd.grounded) {
+            w.Q[m] = 0.f;
+            w.V[m] = 0.f;
+            continue;
+        }
         float net = 0.f;
         for (int q = nd.adj0; q < nd.adj0 + nd.nadj; ++q) {
             const int t = w.adj[q];
             net += (t & 1) ? cur(t >> 1) : -cur(t >> 1);
         }
-        w.Q[m] = nd.grounded ? 0.f : nd.aQ * w.Q[m] + nd.bQ * net;
+        // V^{n+1} from K Q^{n+1} = e0 V^{n+1} + sum_p P_p^{n+1}, the charge
+        // and polarisation updates substituted
+        float *P = w.P + (size_t)m * 4;
+        const float V = w.V[m], Q = w.Q[m];
+        float spb = 0.f, spa = 0.f;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            spb += nd.pb[p];
+            spa += nd.pa[p] * P[p];
+        }
+        const float Vn = (nd.K * (Q + a.dt * net) - (nd.cs + spb) * V - spa) / (nd.e0 + spb + nd.cs);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) P[p] = nd.pa[p] * P[p] + nd.pb[p] * (Vn + V);
+        w.Q[m] = Q + a.dt * net - nd.cs / nd.K * (Vn + V);
+        w.V[m] = Vn;
     }
     __syncthreads();
 }
@@ -117,7 +135,7 @@ __device__ __forceinline__ void edge_body(const EdgeArgs &a)
     if (threadIdx.x == 0) n_s = *a.step;
     __syncthreads();
     const long long n = n_s;
-    if (a.w.n_seg > 0) wire_scatter_body(a);
+    if (a.w.n_seg > 0 && !a.wire_done) wire_scatter_body(a);
     for (int q = threadIdx.x; q < a.n_src; q += blockDim.x) {
         const SourceDesc sd = a.src[q];
         if (sd.hard) continue;
@@ -154,8 +172,7 @@ __device__ __forceinline__ void edge_body(const EdgeArgs &a)
             if (pr.kind == 4) {
                 v = a.w.I[pr.i];                // oblique-wire segment current
             } else if (pr.kind == 5) {
-                const ONode nd = a.w.node[pr.i];  // oblique-wire node: in-cell potential
-                v = nd.grounded ? 0.f : nd.cV * a.w.Q[pr.i];
+                v = a.w.V[pr.i];                // oblique-wire node: in-cell potential
             } else if (pr.kind == 2) {
                 v = a.E[pr.axis][eidx(a, pr.i, pr.j, pr.k)];
             } else if (pr.kind == 3) {
@@ -188,6 +205,8 @@ __device__ __forceinline__ void edge_body(const EdgeArgs &a)
 
 __global__ void edge_kernel(const EdgeArgs a) { edge_body(a); }
 
+__global__ void wire_finish_kernel(const EdgeArgs a) { wire_scatter_body(a); }
+
 __global__ void wire_gather_kernel(const EdgeArgs a)
 {
     __shared__ long long n_s;
@@ -212,6 +231,12 @@ cudaError_t launch_edges(const EdgeArgs &a, cudaStream_t s)
     // a full CTA keeps enough loads in flight
     const bool wires = a.w.n_seg > 0;
     edge_kernel<<<1, wires ? 1024 : 128, wires ? kWireSegShared * sizeof(float) : 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wire_finish(const EdgeArgs &a, cudaStream_t s)
+{
+    wire_finish_kernel<<<1, 1024, kWireSegShared * sizeof(float), s>>>(a);
     return cudaGetLastError();
 }
 

@@ -176,7 +176,10 @@ struct OTerm {
     float ws;
 };
 struct ONode {
-    float cV, aQ, bQ;        // V = cV Q; Q^{n+1} = aQ Q^n + bQ (net current in)
+    // in-cell medium: K Q = e0 V + sum_p P_p; Q^{n+1} = Q^n + dt (net current
+    // in) - (cs / K)(V^{n+1} + V^n); P_p^{n+1} = pa_p P_p^n + pb_p (V^{n+1} + V^n)
+    float K, e0, cs;
+    float pa[4], pb[4];      // Debye poles of the node's medium (0: none)
     int grounded;
     int adj0, nadj;          // adjacency entries (segment << 1 | current flows in)
 };
@@ -198,7 +201,8 @@ struct WireArgs {
     const ONode *node;
     int n_node;
     const int *adj;
-    float *I, *Q;
+    float *I, *Q, *V;        // segment currents, node charges and in-cell potentials
+    float *P;                // [n_node][4] node polarisations (Debye media)
     const OSrc *src;
     const float *samples;
 };
@@ -206,7 +210,7 @@ struct WireArgs {
 struct EdgeArgs {
     int nx, ny, nz, pitch;
     long long plane;
-    float dx;
+    float dx, dt;
     float *E[3];             // fields after the stencil (t_{n+1}, t_{n+1/2})
     const float *H[3];
     const SourceDesc *src;
@@ -222,6 +226,7 @@ struct EdgeArgs {
     int npoles;
     const float *Ein[3];     // E^n, the step's input (oblique wires read it)
     WireArgs w;              // oblique wires (n_seg = 0: none)
+    int wire_done;           // the wires' scatter and charges ran before the Debye kernel
 };
 
 // fdtd_step.cu
@@ -240,6 +245,9 @@ cudaError_t launch_edges(const EdgeArgs &a, cudaStream_t s);
 // oblique wires: segment currents to t_{n+1/2}; needs only the step's inputs,
 // so it may run concurrently with the step kernels, and before launch_edges
 cudaError_t launch_wire_gather(const EdgeArgs &a, cudaStream_t s);
+// oblique wires in Debye media: their scatter into E^{n+1} and node charges,
+// before the dispersive-media kernel (which then sees the wire currents)
+cudaError_t launch_wire_finish(const EdgeArgs &a, cudaStream_t s);
 cudaError_t launch_debye(const DebyeArgs &a, cudaStream_t s);
 // one CTA per domain: e[2 * d + parity]
 cudaError_t launch_edges_batch(const EdgeArgs *e, int n_domains, int parity, cudaStream_t s);

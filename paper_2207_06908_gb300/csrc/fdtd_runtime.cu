@@ -168,7 +168,7 @@ struct fdtd_grid {
     int n_oscat = 0;
     fdtd::ONode *onode_d = nullptr;
     int *oadj_d = nullptr;
-    float *oI_d = nullptr, *oQ_d = nullptr;
+    float *oI_d = nullptr, *oQ_d = nullptr, *oV_d = nullptr, *oP_d = nullptr;
     fdtd::OSrc *osrc_d = nullptr;
     float *osamp_d = nullptr;
     uint8_t *dcls_d = nullptr;
@@ -193,7 +193,7 @@ int cuda_fail(fdtd_grid *g, cudaError_t e, const char *what)
 // ---- device arena plan -------------------------------------------------
 struct Plan {
     size_t field, cls, table, prof[3], psi[fdtd::PSI_COUNT], src, samples, probes, out, step, work, slot, items,
-        J, dcls, dtable, oseg, ochunk, oedge, oscat, oterm, onode, oadj, oI, oQ, osrc, osamp, total;
+        J, dcls, dtable, oseg, ochunk, oedge, oscat, oterm, onode, oadj, oI, oQ, oV, oP, osrc, osamp, total;
 };
 
 // poles used by the grid (the largest pole count of a material some cell
@@ -271,6 +271,8 @@ Plan make_plan(const fdtd_grid *g, int capacity)
     p.oadj = take(2 * n_os * sizeof(int));
     p.oI = take(n_os * sizeof(float));
     p.oQ = take(n_on * sizeof(float));
+    p.oV = take(n_on * sizeof(float));
+    p.oP = take(4 * n_on * sizeof(float));
     p.osrc = take(std::max<size_t>(1, g->osrcs.size()) * sizeof(fdtd::OSrc));
     p.osamp = take(std::max<size_t>(1, n_samp) * sizeof(float));
     p.total = off;
@@ -557,11 +559,18 @@ WireDev wire_device(const fdtd_grid *g, const std::vector<uint8_t> &cls, const s
         int c[3];
         for (int a = 0; a < 3; ++a) c[a] = std::min((int)std::floor(nd.p[a]), n[a] - 1);
         const fdtd_material &mt = material(c);
-        const double eps = kEps0 * mt.eps_r, r = (mt.sigma / eps + nu[m] / deg[m]) * dt / 2.0;
+        const int mat = g->mat[((size_t)c[2] * g->ny + c[1]) * g->nx + c[0]];
+        const double eps = kEps0 * mt.eps_r;
         fdtd::ONode o{};
-        o.cV = (float)(lam[m] / deg[m] / (2.0 * M_PI * eps * dlm[m]));
-        o.aQ = (float)((1.0 - r) / (1.0 + r));
-        o.bQ = (float)(dt / (1.0 + r));
+        // K Q = e0 V + sum_p P_p; the CPML's loss acts as an extra conductance eps nu
+        o.K = (float)(lam[m] / deg[m] / (2.0 * M_PI * dlm[m]));
+        o.e0 = (float)eps;
+        o.cs = (float)(dt * (mt.sigma + eps * nu[m] / deg[m]) / 2.0);
+        for (int p2 = 0; p2 < fdtd::kMaxPoles; ++p2) {
+            const double de = g->poles[mat][p2], tau = g->poles[mat][fdtd::kMaxPoles + p2];
+            o.pa[p2] = de > 0 ? (float)((2.0 * tau - dt) / (2.0 * tau + dt)) : 0.f;
+            o.pb[p2] = de > 0 ? (float)(dt * kEps0 * de / (2.0 * tau + dt)) : 0.f;
+        }
         o.grounded = nd.grounded;
         o.adj0 = (int)d.adj.size();
         o.nadj = (int)adj[m].size();
@@ -951,6 +960,7 @@ fdtd::EdgeArgs edge_args(const fdtd_grid *g, int parity)
     e.nx = g->nx; e.ny = g->ny; e.nz = g->nz;
     e.pitch = g->pitch; e.plane = g->plane;
     e.dx = (float)g->dx;
+    e.dt = (float)g->dt;
     for (int c = 0; c < 3; ++c) {
         e.E[c] = g->F[1 - parity][c];
         e.H[c] = g->F[1 - parity][3 + c];
@@ -980,6 +990,9 @@ fdtd::EdgeArgs edge_args(const fdtd_grid *g, int parity)
     e.w.adj = g->oadj_d;
     e.w.I = g->oI_d;
     e.w.Q = g->oQ_d;
+    e.w.V = g->oV_d;
+    e.w.P = g->oP_d;
+    e.wire_done = g->npoles > 0 && !g->osegs.empty();
     e.w.src = g->osrc_d;
     e.w.samples = g->osamp_d;
     return e;
@@ -1053,6 +1066,9 @@ cudaError_t enqueue_step(fdtd_grid *g, int parity, cudaStream_t s)
         if (wires) e = fdtd::launch_wire_gather(edge_args(g, parity), s);
         for (int l = 0; l < g->n_launch && e == cudaSuccess; ++l) e = launch(l)(s);
     }
+    // in Debye media the wires' currents reach E^{n+1} before the polarisation
+    // currents advance from it
+    if (e == cudaSuccess && g->npoles && wires) e = fdtd::launch_wire_finish(edge_args(g, parity), s);
     if (e == cudaSuccess && g->npoles) e = fdtd::launch_debye(debye_args(g, parity), s);
     if (e != cudaSuccess) return e;
     if (has_edge_work(g)) e = fdtd::launch_edges(edge_args(g, parity), s);
@@ -1219,6 +1235,8 @@ int step_with_scratch(fdtd_grid *g, int n, int *scratch, int scratch_ints)
         for (int l = 0; l < g->n_launch && e == cudaSuccess; ++l)
             e = launch_step(single_args(g, g->parity, l), grid_launch(g, g->parity, l, scratch + 2 * l, g->noalloc_err),
                             g->lc[l].grid, g->stream);
+        if (e == cudaSuccess && g->npoles && !g->osegs.empty())
+            e = launch_wire_finish(edge_args(g, g->parity), g->stream);
         if (e == cudaSuccess && g->npoles) e = launch_debye(debye_args(g, g->parity), g->stream);
         if (e == cudaSuccess && has_edge_work(g))
             e = launch_edges(edge_args(g, g->parity), g->stream);
@@ -1572,13 +1590,20 @@ int fdtd_set_wire_state(fdtd_grid *g, const float *I, const float *Q)
 {
     if (int rc = check_open(g, true)) return rc;
     if ((!I && !g->osegs.empty()) || (!Q && !g->onodes.empty())) return fail(g, FDTD_EINVAL, "null buffer");
-    std::vector<float> q(Q, Q + g->onodes.size());
-    for (size_t m = 0; m < q.size(); ++m)
-        if (g->onodes[m].grounded) q[m] = 0.f;       // grounded nodes hold no charge
+    std::vector<float> q(Q, Q + g->onodes.size()), v(g->onodes.size()), p(4 * g->onodes.size(), 0.f);
+    std::vector<fdtd::ONode> nd(g->onodes.size());
     cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e == cudaSuccess && !nd.empty())
+        e = cudaMemcpy(nd.data(), g->onode_d, nd.size() * sizeof(fdtd::ONode), cudaMemcpyDeviceToHost);
+    for (size_t m = 0; m < q.size(); ++m) {
+        if (g->onodes[m].grounded) q[m] = 0.f;       // grounded nodes hold no charge
+        v[m] = nd.empty() ? 0.f : nd[m].K * q[m] / nd[m].e0;   // polarisation-free
+    }
     if (e == cudaSuccess && !g->osegs.empty())
         e = cudaMemcpy(g->oI_d, I, g->osegs.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !q.empty()) e = cudaMemcpy(g->oQ_d, q.data(), q.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !v.empty()) e = cudaMemcpy(g->oV_d, v.data(), v.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !p.empty()) e = cudaMemcpy(g->oP_d, p.data(), p.size() * sizeof(float), cudaMemcpyHostToDevice);
     return e == cudaSuccess ? FDTD_OK : cuda_fail(g, e, "wire state write");
 }
 
@@ -1606,8 +1631,6 @@ int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_by
     std::vector<double> src_cb;
     std::vector<std::array<double, 3 * fdtd::kMaxPoles>> src_debye;
     if (int rc = build_classes(g, cls, table, src_cb, dcls, dtable, src_debye)) return rc;
-    if (!g->osegs.empty() && g->npoles)
-        return fail(g, FDTD_EINVAL, "oblique wires in dispersive media are not supported");
     if (!g->osegs.empty() && g->courant > wire_courant_limit(g)) {
         char msg[160];
         std::snprintf(msg, sizeof msg, "the oblique wires need courant <= %.4f (thinner wires or a smaller step)",
@@ -1660,6 +1683,8 @@ int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_by
     g->oadj_d = (int *)(base + p.oadj);
     g->oI_d = (float *)(base + p.oI);
     g->oQ_d = (float *)(base + p.oQ);
+    g->oV_d = (float *)(base + p.oV);
+    g->oP_d = (float *)(base + p.oP);
     g->osrc_d = (fdtd::OSrc *)(base + p.osrc);
     g->osamp_d = (float *)(base + p.osamp);
     g->capacity = probe_capacity;
@@ -1863,7 +1888,7 @@ int fdtd_num_classes(const fdtd_grid *g) { return g ? g->n_classes : -1; }
 // ---- checkpoint / resume ----------------------------------------------------
 namespace {
 constexpr uint32_t kStateMagic = 0x53544446u;     // "FDTS"
-constexpr uint32_t kStateVersion = 3;
+constexpr uint32_t kStateVersion = 4;
 struct StateHeader {
     uint32_t magic, version;
     int32_t nx, ny, nz, d, n_probes, capacity, n_psi, npoles, dz0, dz1, n_oseg, n_onode;
@@ -1877,7 +1902,7 @@ size_t state_bytes(const fdtd_grid *g, int n_psi)
     const size_t cells = (size_t)g->nx * g->ny * g->nz;
     return sizeof(StateHeader) + (6 + (size_t)n_psi) * cells * sizeof(float) +
            g->probes.size() * (size_t)g->capacity * sizeof(float) + debye_elems(g) * sizeof(float) +
-           (g->osegs.size() + g->onodes.size()) * sizeof(float);
+           (g->osegs.size() + 6 * g->onodes.size()) * sizeof(float);
 }
 
 // one cell-owned array between host (dense) and device (row pitch)
@@ -1922,9 +1947,13 @@ int fdtd_save_state(fdtd_grid *g, void *host_buf, size_t *bytes)
     char *pw = p + pbytes + debye_elems(g) * sizeof(float);
     if (e == cudaSuccess && !g->osegs.empty())
         e = cudaMemcpy(pw, g->oI_d, g->osegs.size() * sizeof(float), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && !g->onodes.empty())
-        e = cudaMemcpy(pw + g->osegs.size() * sizeof(float), g->oQ_d, g->onodes.size() * sizeof(float),
-                       cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && !g->onodes.empty()) {
+        char *pn = pw + g->osegs.size() * sizeof(float);
+        const size_t nb = g->onodes.size() * sizeof(float);
+        e = cudaMemcpy(pn, g->oQ_d, nb, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(pn + nb, g->oV_d, nb, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(pn + 2 * nb, g->oP_d, 4 * nb, cudaMemcpyDeviceToHost);
+    }
     if (e != cudaSuccess) return cuda_fail(g, e, "state copy");
     *bytes = need;
     return FDTD_OK;
@@ -1957,9 +1986,13 @@ int fdtd_load_state(fdtd_grid *g, const void *host_buf, size_t bytes)
     const char *qw = q + pbytes + debye_elems(g) * sizeof(float);
     if (e == cudaSuccess && !g->osegs.empty())
         e = cudaMemcpy(g->oI_d, qw, g->osegs.size() * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !g->onodes.empty())
-        e = cudaMemcpy(g->oQ_d, qw + g->osegs.size() * sizeof(float), g->onodes.size() * sizeof(float),
-                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !g->onodes.empty()) {
+        const char *qn = qw + g->osegs.size() * sizeof(float);
+        const size_t nb = g->onodes.size() * sizeof(float);
+        e = cudaMemcpy(g->oQ_d, qn, nb, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(g->oV_d, qn + nb, nb, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(g->oP_d, qn + 2 * nb, 4 * nb, cudaMemcpyHostToDevice);
+    }
     const long long step = h.step;
     if (e == cudaSuccess) e = cudaMemcpy(g->step_d, &step, sizeof step, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(g, e, "state copy");

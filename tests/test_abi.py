@@ -142,26 +142,6 @@ def test_oblique_wire_host_checks():
         lib.fdtd_destroy(h)
 
 
-def test_oblique_wires_rejected_in_dispersive_grids_before_device_work():
-    import numpy as np
-    from paper_2207_06908_gb300._lib import Material
-    from paper_2207_06908_gb300 import _lib as L
-    lib = L.load()
-    h = ctypes.c_void_p()
-    assert lib.fdtd_create_grid(12, 12, 12, 0.1, 0.99, None, None, ctypes.byref(h)) == 0
-    try:
-        cm = np.zeros(12 ** 3, np.uint8)
-        mats = (Material * 1)(Material(4.0, 0.001, 1.0))
-        assert lib.fdtd_set_materials(h, cm.ctypes.data_as(ctypes.c_void_p), mats, 1) == 0
-        deps, tau = (ctypes.c_double * 1)(5.0), (ctypes.c_double * 1)(1e-8)
-        assert lib.fdtd_set_debye(h, 0, 1, deps, tau) == 0
-        assert lib.fdtd_add_oblique_wire(h, 3.2, 3.1, 3.0, 8.5, 7.9, 6.0, 0.002, None) == 0
-        assert lib.fdtd_finalize(h, 0, None, 0) == -1
-        assert b"dispersive" in lib.fdtd_last_error(h)
-    finally:
-        lib.fdtd_destroy(h)
-
-
 def test_thick_oblique_wire_needs_a_smaller_courant_number():
     """a wire along a node line with ln(R/a) = 1 caps the Courant number
     below 0.99: finalize refuses before any device work and names the cap"""

@@ -220,3 +220,48 @@ def test_lightning_tower_at_bench_size(fdtd):
     Io, Qo = o.get_wire_state()
     assert rel_l2(I, Io) <= 1e-4 and rel_l2(Q, Qo) <= 1e-4
     g.close()
+
+
+def debye_owire_scenario(seed, n, cpml, steps):
+    sc = owire_scenario(seed, n, cpml, steps)
+    return W.with_random_debye(sc, seed + 7, materials=(0, 1, 2, 3), max_poles=3)
+
+
+@pytest.mark.parametrize("seed,cpml", [(12, 0), (13, 3)])
+def test_oblique_wires_in_debye_media(fdtd, seed, cpml):
+    """oblique wires whose nodes sit in multi-pole Debye media (the in-cell
+    capacitance takes the poles) on a dispersive grid: fields, probes and
+    wire state against the oracle"""
+    g = compare(fdtd, debye_owire_scenario(seed, (22, 19, 17), cpml, 60), 60)
+    g.close()
+
+
+def test_oblique_wires_in_debye_media_graph_direct_checkpoint(fdtd):
+    sc = debye_owire_scenario(14, (20, 18, 16), 2, 80)
+
+    def build():
+        g = fdtd.from_scenario(sc, probe_capacity=80)
+        for c, f in enumerate(sc.fields):
+            g.set_field(c, f)
+        return g
+    a, b = build(), build()
+    a.step(70)
+    for _ in range(70):
+        b.step(1)
+    for c in range(6):
+        assert np.array_equal(a.get_field(c), b.get_field(c))
+    c = build()
+    c.step(30)
+    state = c.save_state()
+    c.step(40)
+    d = build()
+    d.load_state(state)
+    d.step(40)
+    for comp in range(6):
+        assert np.array_equal(c.get_field(comp), d.get_field(comp))
+    for x, y in zip(c.get_wire_state(), d.get_wire_state()):
+        assert np.array_equal(x, y)
+    for p in range(len(sc.probes) + len(sc.owire_probes)):
+        assert np.array_equal(c.read_probe(p), d.read_probe(p))
+    for g in (a, b, c, d):
+        g.close()

@@ -233,3 +233,66 @@ def test_wire_ending_in_the_cpml_is_absorbed():
     open_end = _feed_current(150, 60.0)
     assert np.linalg.norm(into_layer - ref) / np.linalg.norm(ref) < 0.01
     assert np.linalg.norm(open_end - ref) / np.linalg.norm(ref) > 0.1
+
+
+def _debye_ring(courant, eps_inf, sigma, deps, tau, Q0=3e-12):
+    n, dx = (14, 14, 10), 0.2
+    g = OracleGrid(*n, dx, courant=courant, parity=False)
+    g.set_materials(np.zeros((n[2], n[1], n[0]), np.uint8), [eps_inf], [sigma], [1.0])
+    g.set_debye(0, deps, tau)
+    corners = [(4, 4, 5), (10, 4, 5), (10, 10, 5), (4, 10, 5)]
+    for q in range(4):
+        g.add_oblique_wire(corners[q], corners[(q + 1) % 4], 0.003)
+    return g, corners[0], Q0
+
+
+def _ring_potential(courant, t_end, eps_inf, sigma, deps, tau):
+    g, node, Q0 = _debye_ring(courant, eps_inf, sigma, deps, tau)
+    steps = int(round(t_end / (courant * 0.2 / (C0 * math.sqrt(3.0)))))
+    g.add_wire_node_probe(node)
+    g.finalize(steps)
+    ns, nn = g.wire_counts()
+    g.set_wire_state(np.zeros(ns), np.full(nn, Q0))
+    g.step(steps)
+    I, _ = g.get_wire_state()
+    assert np.max(np.abs(I)) == 0.0
+    return g.read_probe(0)[-1], g.dt * steps, Q0
+
+
+def test_dispersive_wire_node_converges_to_the_debye_relaxation():
+    """A closed ring with uniform charge in uniform two-pole Debye soil with
+    conduction: no current flows, and each node's in-cell potential obeys
+    K Q = eps0 eps_inf V + sum P_p, tau_p P_p' + P_p = eps0 deps_p V,
+    Q' = -(sigma/K) V exactly; the discrete scheme converges to the matrix
+    exponential of that linear system at second order."""
+    from scipy.linalg import expm
+    eps_inf, sigma, deps, tau = 5.0, 0.002, [20.0, 8.0], [3e-9, 2e-8]
+    t_end = 6e-8
+    errs = []
+    for courant in (0.9, 0.45, 0.225):
+        v, t, Q0 = _ring_potential(courant, t_end, eps_inf, sigma, deps, tau)
+        # K from the model: a node on node lines, one spacing each way
+        r0 = math.exp(-0.57721566490153286) / (2 * math.sqrt(2))
+        K = math.log(0.2 * r0 / 0.003) / (2 * math.pi * 0.2)
+        e0 = EPS0 * eps_inf
+        A = np.zeros((3, 3))
+        # V = (K Q - P1 - P2) / e0
+        dv = np.array([K, -1.0, -1.0]) / e0
+        A[0] = -(sigma / K) * dv
+        for p in range(2):
+            A[1 + p] = EPS0 * deps[p] * dv / tau[p]
+            A[1 + p, 1 + p] -= 1.0 / tau[p]
+        x = expm(A * t) @ np.array([Q0, 0.0, 0.0])
+        errs.append(abs(v - dv @ x) / abs(dv @ x))
+    assert errs[0] < 1e-3
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5, errs
+
+
+def test_dispersive_wire_node_reaches_the_static_permittivity():
+    """without conduction the ring's potential settles exactly where the
+    static permittivity eps_inf + sum deps puts it"""
+    eps_inf, deps, tau = 4.0, [12.0, 30.0], [2e-9, 5e-9]
+    v, _, Q0 = _ring_potential(0.9, 4e-7, eps_inf, 0.0, deps, tau)
+    r0 = math.exp(-0.57721566490153286) / (2 * math.sqrt(2))
+    K = math.log(0.2 * r0 / 0.003) / (2 * math.pi * 0.2)
+    assert abs(v - K * Q0 / (EPS0 * (eps_inf + sum(deps)))) <= 1e-9 * abs(v)
