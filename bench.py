@@ -153,29 +153,36 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_hash():
-    """hash of the step kernel and of the runtime that sets its launch
-    shapes: recorded DRAM traffic is valid only for the same sources"""
+def kernel_hash(files=None):
+    """hash of the kernels a traffic record covers and of the runtime that
+    sets their launch shapes (default: the step kernel and the runtime):
+    recorded DRAM traffic is valid only for the same sources"""
     h = hashlib.sha256()
-    for path in KERNEL_SRC:
+    for path in files or KERNEL_SRC:
         with open(path, "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(cells, scenario):
-    """DRAM bytes per launch of the step kernel from the committed ncu
-    summary, scaled to this grid; None when the kernel changed since."""
-    try:
-        with open(TRAFFIC_FILE) as f:
-            t = json.load(f)
-    except Exception:
-        return None
-    if t.get("kernel_sha") != kernel_hash():
-        return None
-    if t.get("cells") != cells or t.get("scenario") != scenario:
-        return None
-    return t["dram_bytes_per_step"]
+    """DRAM bytes per step of the timed kernels from the committed ncu
+    summary of this workload (profiles/step_kernel_traffic.json for the
+    256^3 workload, step_kernel_traffic_<scenario>.json for the others);
+    None when the kernels changed since"""
+    for path in (TRAFFIC_FILE, os.path.join(ROOT, "profiles", f"step_kernel_traffic_{scenario}.json")):
+        try:
+            with open(path) as f:
+                t = json.load(f)
+        except Exception:
+            continue
+        if t.get("cells") != cells or t.get("scenario") != scenario:
+            continue
+        srcs = [os.path.join(ROOT, "paper_2207_06908_gb300", "csrc", n)
+                for n in t.get("sources", ["fdtd_step.cu", "fdtd_runtime.cu"])]
+        if t.get("kernel_sha") != kernel_hash(srcs):
+            return None
+        return t["dram_bytes_per_step"]
+    return None
 
 
 class Clocks:
@@ -539,7 +546,7 @@ def main():
         t0 = time.perf_counter()
         g2 = fdtd.from_scenario(sc, probe_capacity=K)
         g2.step(K)
-        outs = [g2.read_probe(p, 0, K) for p in range(len(sc.probes))]
+        outs = [g2.read_probe(p, 0, K) for p in range(len(sc.probes) + len(getattr(sc, "owire_probes", None) or []))]
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
         n_cls = g2.num_classes
