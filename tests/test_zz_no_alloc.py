@@ -63,15 +63,19 @@ def test_step_noalloc_rejects_unfinalized_grid():
     g.close()
 
 
-def test_step_noalloc_with_oblique_wires_matches_step():
-    """grids with oblique wires: the no-alloc entry runs the wires' current
-    update before the step kernels (the graph runs it beside them); both
-    order the same arithmetic, so the results are equal bit for bit"""
+@pytest.mark.parametrize("debye", [False, True])
+def test_step_noalloc_with_oblique_wires_matches_step(debye):
+    """grids with oblique wires (and Debye media): the no-alloc entry runs
+    the wires' current update before the step kernels (the graph runs it
+    beside them); both order the same arithmetic, so the results are equal
+    bit for bit"""
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2207_06908_gb300 import fdtd
     sc = W.random_scenario(43, n=(24, 20, 18), cpml=3, n_wires=0, n_steps=70, courant=0.9)
+    if debye:
+        sc = W.with_random_debye(sc, 5, materials=(0, 1, 2, 3), max_poles=2)
     J = (11.5, 9.25, 8.75)
     sc.owires = [((5.0, 5.5, 5.0), J, 0.004), (J, (18.5, 14.0, 12.5), 0.002), (J, (6.5, 15.5, 13.0), 0.003)]
     t = np.arange(70)
