@@ -1,7 +1,6 @@
-// fdtd_edges.cu -- ideal current sources (Kuklin, arXiv 2207.06908,
-// Sec. 2.1, J = I/dx^2 on one edge) and the probes of the Sec. 4 model files
-// ("calculate": voltage = -sum E dl along a path, current = loop integral of
-// H around an edge), applied right after the step kernel (and, with Debye
+// fdtd_edges.cu -- the source/probe kernel: the ideal sources (Kuklin,
+// arXiv 2207.06908, Sec. 2.1) and the probes of the Sec. 4 model files
+// (fdtd_srcprobe.cuh), applied right after the step kernels (and, with Debye
 // media, the dispersive-media kernel) of the same step.
 // Oblique thin wires (Sec. 2.3, the Guiffaut formalism read in
 // Holland-Simpson form): a separate kernel, concurrent with the step
@@ -11,15 +10,10 @@
 // node charges to t_{n+1}.
 // One CTA; a device-side step counter indexes the source samples and the
 // probe slots, so the launch can be replayed inside a CUDA graph.
-#include "fdtd_internal.h"
+#include "fdtd_srcprobe.cuh"
 
 namespace fdtd {
 namespace {
-
-__device__ __forceinline__ long long eidx(const EdgeArgs &a, int i, int j, int k)
-{
-    return (long long)k * a.plane + (long long)j * a.pitch + i;
-}
 
 constexpr int kWireSegShared = 4096;  // segment currents kept in shared memory for the scatter
 
@@ -132,75 +126,11 @@ __device__ __forceinline__ void wire_scatter_body(const EdgeArgs &a)
 __device__ __forceinline__ void edge_body(const EdgeArgs &a)
 {
     __shared__ long long n_s;
-    if (threadIdx.x == 0) n_s = *a.step;
+    if (threadIdx.x == 0) n_s = __ldcg(a.step);
     __syncthreads();
     const long long n = n_s;
     if (a.w.n_seg > 0 && !a.wire_done) wire_scatter_body(a);
-    for (int q = threadIdx.x; q < a.n_src; q += blockDim.x) {
-        const SourceDesc sd = a.src[q];
-        if (sd.hard) continue;
-        const float I = n < sd.n_samples ? a.samples[sd.sample_off + n] : 0.f;
-        const float add = sd.coef * I;
-        atomicAdd(a.E[sd.comp] + sd.idx, add);
-        // a dispersive edge: the currents already advanced with E^{n+1}
-        // before the source; they take its share, be_p times the increment
-        if (sd.jidx >= 0 && a.J)
-            for (int p = 0; p < a.npoles; ++p)
-                if (sd.be[p] != 0.f)
-                    atomicAdd(a.J + (long long)(sd.comp * a.npoles + p) * a.jstride + sd.jidx, sd.be[p] * add);
-    }
-    __syncthreads();
-    // ideal voltage sources, after the current sources: E^{n+1} = -V / dx
-    // (and on a dispersive edge the currents take be_p times the change)
-    for (int q = threadIdx.x; q < a.n_src; q += blockDim.x) {
-        const SourceDesc sd = a.src[q];
-        if (!sd.hard) continue;
-        const float V = n < sd.n_samples ? a.samples[sd.sample_off + n] : 0.f;
-        float *e = a.E[sd.comp] + sd.idx;
-        const float old = *e, v = sd.vcoef * V;
-        *e = v;
-        if (sd.jidx >= 0 && a.J)
-            for (int p = 0; p < a.npoles; ++p)
-                if (sd.be[p] != 0.f)
-                    atomicAdd(a.J + (long long)(sd.comp * a.npoles + p) * a.jstride + sd.jidx, sd.be[p] * (v - old));
-    }
-    __syncthreads();
-    if (n < a.capacity) {
-        for (int p = threadIdx.x; p < a.n_probes; p += blockDim.x) {
-            const ProbeDesc pr = a.probes[p];
-            float v = 0.f;
-            if (pr.kind == 4) {
-                v = a.w.I[pr.i];                // oblique-wire segment current
-            } else if (pr.kind == 5) {
-                v = a.w.V[pr.i];                // oblique-wire node: in-cell potential
-            } else if (pr.kind == 2) {
-                v = a.E[pr.axis][eidx(a, pr.i, pr.j, pr.k)];
-            } else if (pr.kind == 3) {
-                v = a.H[pr.axis][eidx(a, pr.i, pr.j, pr.k)];
-            } else if (pr.kind == 0) {
-                int q[3] = {pr.i, pr.j, pr.k};
-                for (int e = 0; e < pr.n_edges; ++e) {
-                    v -= a.E[pr.axis][eidx(a, q[0], q[1], q[2])] * a.dx;
-                    q[pr.axis]++;
-                }
-            } else {
-                const float *Hx = a.H[0], *Hy = a.H[1], *Hz = a.H[2];
-                const int i = pr.i, j = pr.j, k = pr.k;
-                if (pr.axis == 2)
-                    v = a.dx * ((Hy[eidx(a, i, j, k)] - Hy[eidx(a, i - 1, j, k)]) -
-                                (Hx[eidx(a, i, j, k)] - Hx[eidx(a, i, j - 1, k)]));
-                else if (pr.axis == 0)
-                    v = a.dx * ((Hz[eidx(a, i, j, k)] - Hz[eidx(a, i, j - 1, k)]) -
-                                (Hy[eidx(a, i, j, k)] - Hy[eidx(a, i, j, k - 1)]));
-                else
-                    v = a.dx * ((Hx[eidx(a, i, j, k)] - Hx[eidx(a, i, j, k - 1)]) -
-                                (Hz[eidx(a, i, j, k)] - Hz[eidx(a, i - 1, j, k)]));
-            }
-            a.probe_out[(long long)p * a.capacity + n] = v;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) *a.step = n + 1;
+    src_probe_body(a, n);
 }
 
 __global__ void edge_kernel(const EdgeArgs a) { edge_body(a); }
