@@ -163,8 +163,9 @@ int fdtd_add_wire_path(fdtd_grid *g, int i0, int j0, int k0, int i1, int j1, int
  * length L' nu and C' nu, nu = sum_u t_u^2 sigma_u / (kappa_u eps0) at the
  * segment, t its direction), so a wire may run into the layer and end
  * there.  Thick wires lower the
- * stable Courant number (fdtd_wire_courant_limit).  Not allowed in batches
- * (fdtd_batch_create fails).  *wire_id (may be NULL) receives the index. */
+ * stable Courant number (fdtd_wire_courant_limit).  In a batch each domain's
+ * wires run as when it steps alone.  *wire_id (may be NULL) receives the
+ * index. */
 int fdtd_add_oblique_wire(fdtd_grid *g, double x0, double y0, double z0, double x1, double y1, double z1,
                           double radius, int *wire_id);
 
@@ -329,7 +330,10 @@ int fdtd_field_device(fdtd_grid *g, int component, void **dptr, int *row_pitch,
  * wires, layers) advanced together -- the soil and grounding sweeps of
  * Sec. 4.1.  Every step is one persistent launch of the step kernel over the
  * work items of all domains (plus one over their CPML z-layer planes when
- * they have a CPML) and one source / probe launch with a CTA per domain;
+ * they have a CPML) and one source / probe launch with a CTA per domain
+ * (which also adds the oblique wires' currents to E and updates their node
+ * charges); when a domain has oblique wires, a launch with a CTA per domain
+ * takes their segment currents to t_{n+1/2} beside the step kernel.
  * fdtd_batch_step replays a captured CUDA graph of 32 steps.  The results
  * are those of stepping each grid alone with fdtd_step. */
 typedef struct fdtd_batch fdtd_batch;
@@ -339,7 +343,7 @@ typedef struct fdtd_batch fdtd_batch;
  * must outlive it and must not be stepped by other calls meanwhile).
  * cuda_stream: the stream the batch queues on.  Allocates a small device
  * table (about 7 KB per domain).  FDTD_ESTATE if a grid is not finalized or
- * the step counts differ. */
+ * the step counts differ; FDTD_EINVAL for a grid with Debye poles. */
 int fdtd_batch_create(int n_grids, fdtd_grid *const *grids, void *cuda_stream, fdtd_batch **out);
 
 /* Queue n steps of every domain on the batch stream (asynchronous).  Each

@@ -153,6 +153,19 @@ __global__ void edge_batch_kernel(const EdgeArgs *e, int parity)
     if (a.n_src > 0 || a.n_probes > 0 || a.w.n_seg > 0) edge_body(a);
 }
 
+// one CTA per domain of a batch: the oblique wires' first half of the step
+__global__ void wire_gather_batch_kernel(const EdgeArgs *e, int parity)
+{
+    __shared__ EdgeArgs a;
+    __shared__ long long n_s;
+    if (threadIdx.x == 0) {
+        a = e[2 * blockIdx.x + parity];
+        if (a.w.n_seg > 0) n_s = __ldcg(a.step);
+    }
+    __syncthreads();
+    if (a.w.n_seg > 0) wire_gather_body(a, n_s);
+}
+
 }  // namespace
 
 cudaError_t launch_edges(const EdgeArgs &a, cudaStream_t s)
@@ -178,9 +191,16 @@ cudaError_t launch_wire_gather(const EdgeArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_edges_batch(const EdgeArgs *e, int n_domains, int parity, cudaStream_t s)
+cudaError_t launch_edges_batch(const EdgeArgs *e, int n_domains, int parity, bool wires, cudaStream_t s)
 {
-    edge_batch_kernel<<<n_domains, 128, 0, s>>>(e, parity);
+    if (wires) edge_batch_kernel<<<n_domains, 1024, kWireSegShared * sizeof(float), s>>>(e, parity);
+    else edge_batch_kernel<<<n_domains, 128, 0, s>>>(e, parity);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wire_gather_batch(const EdgeArgs *e, int n_domains, int parity, cudaStream_t s)
+{
+    wire_gather_batch_kernel<<<n_domains, 1024, kWireChunk * sizeof(float), s>>>(e, parity);
     return cudaGetLastError();
 }
 

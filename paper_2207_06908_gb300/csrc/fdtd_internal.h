@@ -249,8 +249,11 @@ cudaError_t launch_wire_gather(const EdgeArgs &a, cudaStream_t s);
 // before the dispersive-media kernel (which then sees the wire currents)
 cudaError_t launch_wire_finish(const EdgeArgs &a, cudaStream_t s);
 cudaError_t launch_debye(const DebyeArgs &a, cudaStream_t s);
-// one CTA per domain: e[2 * d + parity]
-cudaError_t launch_edges_batch(const EdgeArgs *e, int n_domains, int parity, cudaStream_t s);
+// one CTA per domain: e[2 * d + parity]; wires: some domain has oblique wires
+cudaError_t launch_edges_batch(const EdgeArgs *e, int n_domains, int parity, bool wires, cudaStream_t s);
+// one CTA per domain, the oblique wires' segment currents (domains without
+// wires return at once); may run concurrently with the step kernels
+cudaError_t launch_wire_gather_batch(const EdgeArgs *e, int n_domains, int parity, cudaStream_t s);
 
 }  // namespace fdtd
 

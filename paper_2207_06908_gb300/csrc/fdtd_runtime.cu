@@ -2032,8 +2032,9 @@ struct fdtd_batch {
     int nitems[2] = {}, grid[2] = {}, region[2] = {}, nh[2] = {};
     int max_classes = 0, max_d = 0, n_launch = 0;
     bool has_edges = false;
+    bool has_wires = false;         // some domain has oblique wires
     cudaStream_t cap = nullptr;
-    Fork fk;                        // concurrent z-layer launch
+    Fork fk;                        // concurrent z-layer launch and oblique-wire gather
     cudaGraphExec_t graph = nullptr;
     int parity = 0;
     long step = 0;
@@ -2070,15 +2071,25 @@ cudaError_t batch_launch(const fdtd_batch *b, int parity, int l, cudaStream_t s)
 cudaError_t batch_enqueue(fdtd_batch *b, int parity, cudaStream_t s)
 {
     cudaError_t e = cudaSuccess;
-    auto launch = [b, parity](int l) { return [b, parity, l](cudaStream_t st) { return batch_launch(b, parity, l, st); }; };
+    const int nd = (int)b->grids.size();
+    auto launch = [b, parity](int l) {
+        return [b, parity, l](cudaStream_t st) {
+            return l < b->n_launch && b->nitems[l] > 0 ? batch_launch(b, parity, l, st) : cudaSuccess;
+        };
+    };
     if (b->fk.side) {
-        e = b->fk.run(s, launch(1), launch(0));
+        // side stream: the oblique wires' gather, then the z-layer launch
+        auto side = [b, parity, nd, &launch](cudaStream_t st) {
+            cudaError_t r = b->has_wires ? fdtd::launch_wire_gather_batch(b->edges, nd, parity, st) : cudaSuccess;
+            if (r == cudaSuccess) r = launch(1)(st);
+            return r;
+        };
+        e = b->fk.run(s, side, launch(0));
     } else {
-        for (int l = 0; l < b->n_launch && e == cudaSuccess; ++l)
-            if (b->nitems[l] > 0) e = launch(l)(s);
+        if (b->has_wires) e = fdtd::launch_wire_gather_batch(b->edges, nd, parity, s);
+        for (int l = 0; l < b->n_launch && e == cudaSuccess; ++l) e = launch(l)(s);
     }
-    if (e == cudaSuccess && b->has_edges)
-        e = fdtd::launch_edges_batch(b->edges, (int)b->grids.size(), parity, s);
+    if (e == cudaSuccess && b->has_edges) e = fdtd::launch_edges_batch(b->edges, nd, parity, b->has_wires, s);
     return e;
 }
 
@@ -2097,7 +2108,6 @@ int fdtd_batch_create(int n, fdtd_grid *const *grids, void *cuda_stream, fdtd_ba
         fdtd_grid *g = grids[q];
         if (!g || !g->finalized) { delete b; return FDTD_ESTATE; }
         if (g->npoles) { delete b; return FDTD_EINVAL; }      // dispersive media run on their own
-        if (!g->osegs.empty()) { delete b; return FDTD_EINVAL; }   // so do oblique wires
         if (g->parity != grids[0]->parity || g->step != grids[0]->step) { delete b; return FDTD_ESTATE; }
         b->grids.push_back(g);
     }
@@ -2110,7 +2120,8 @@ int fdtd_batch_create(int n, fdtd_grid *const *grids, void *cuda_stream, fdtd_ba
         b->max_classes = std::max(b->max_classes, g->n_classes);
         b->max_d = std::max(b->max_d, g->d);
         b->n_launch = std::max(b->n_launch, g->n_launch);
-        b->has_edges = b->has_edges || !g->srcs.empty() || !g->probes.empty();
+        b->has_edges = b->has_edges || has_edge_work(g);
+        b->has_wires = b->has_wires || !g->osegs.empty();
         for (int l = 0; l < 2; ++l) {
             const int items = l < g->n_launch ? g->lc[l].nitems : 0;
             starts[l].push_back(starts[l].back() + items);
@@ -2174,7 +2185,8 @@ int fdtd_batch_create(int n, fdtd_grid *const *grids, void *cuda_stream, fdtd_ba
     // the grids' own work must be finished before the batch reads them
     for (fdtd_grid *g : b->grids)
         if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
-    if (e == cudaSuccess && b->n_launch == 2 && b->nitems[0] > 0 && b->nitems[1] > 0) e = b->fk.init();
+    if (e == cudaSuccess && ((b->n_launch == 2 && b->nitems[0] > 0 && b->nitems[1] > 0) || b->has_wires))
+        e = b->fk.init();
     if (e != cudaSuccess) { cudaFree(b->mem); delete b; return FDTD_ECUDA; }
     *out = b;
     return FDTD_OK;

@@ -122,14 +122,50 @@ def test_oblique_wires_graph_direct_and_checkpoint_bitwise(fdtd):
         g.close()
 
 
-def test_batches_reject_oblique_wires(fdtd):
-    sc = owire_scenario(4, (16, 16, 16), 0, 10)
-    g = fdtd.from_scenario(sc, probe_capacity=10)
-    h = fdtd.from_scenario(W.random_scenario(2, n=(12, 10, 9), n_steps=10), probe_capacity=10)
-    with pytest.raises(fdtd.FdtdError):
-        fdtd.Batch([g, h])
-    g.close()
-    h.close()
+def _start(F, sc, steps):
+    g = F.from_scenario(sc, probe_capacity=steps)
+    if sc.fields is not None:
+        for c, f in enumerate(sc.fields):
+            g.set_field(c, f)
+    return g
+
+
+@pytest.mark.parametrize("cpml", [0, 4])
+def test_batch_with_oblique_wires_equals_individual_grids(fdtd, cpml):
+    """domains with and without oblique wires (junctions, EMFs behind a
+    resistance, a grounded wire without a CPML) in one batch, 45 steps (one
+    32-step graph + direct launches): fields, probes and wire state bitwise
+    equal to stepping each grid alone.  Without a CPML the side stream
+    carries the wire gather alone."""
+    steps = 45
+    scs = [owire_scenario(31, (24, 20, 22), cpml, steps),
+           W.random_scenario(32, n=(19, 23, 17), cpml=cpml, n_steps=steps),
+           owire_scenario(33, (18, 26, 20), cpml, steps, fields=False)]
+    alone = []
+    for sc in scs:
+        g = _start(fdtd, sc, steps)
+        g.step(steps)
+        n_probes = len(sc.probes) + len(sc.owire_probes)
+        alone.append(([g.get_field(c) for c in range(6)], [g.read_probe(p) for p in range(n_probes)],
+                      g.get_wire_state() if sc.owires else None))
+        g.close()
+    grids = [_start(fdtd, sc, steps) for sc in scs]
+    b = fdtd.Batch(grids)
+    b.step(steps)
+    b.synchronize()
+    for g, sc, (fa, pa, wa) in zip(grids, scs, alone):
+        assert g.step_count == steps
+        for c in range(6):
+            assert np.array_equal(g.get_field(c), fa[c]), c
+        for p, ref in enumerate(pa):
+            assert np.array_equal(g.read_probe(p), ref), p
+        if wa is not None:
+            I, Q = g.get_wire_state()
+            assert np.array_equal(I, wa[0]) and np.array_equal(Q, wa[1])
+            assert np.abs(I).max() > 0
+    b.close()
+    for g in grids:
+        g.close()
 
 
 def test_lightning_tower_oblique_matches_oracle_and_staircase(fdtd):
