@@ -88,7 +88,10 @@
  *     (sigma / K) V, the last two by the trapezoidal rule; without poles
  *     this is the charge update above.  Wires
  *     whose end points coincide share that node (junction, Kirchhoff's
- *     current law); a node on an outer wall is grounded (V = 0).  The
+ *     current law); a node on an outer wall is grounded (V = 0), and so
+ *     is a node on the node line of an axis-aligned wire: it joins that
+ *     conductor, its charge handed to the grid (the PEC line carries it).
+ *     The
  *     in-cell radius is parity unpinned against the paper (pinned by
  *     transmission-line impedance and rotation tests).
  *
@@ -834,6 +837,20 @@ static double cpml_rate(const orc_grid *g, int u, double x)
 
 /* in-cell parameters and coupling edges of the oblique wires (after the
  * E coefficients exist: the scatter uses each edge's cb) */
+/* does point p (node units) lie on the node line of axis-aligned wire w */
+static int on_axis_wire(const orc_wire *w, const double p[3])
+{
+    const int c[3] = {w->i, w->j, w->k};
+    for (int u = 0; u < 3; u++) {
+        if (u == w->axis) {
+            if (p[u] < c[u] - 1e-9 || p[u] > c[u] + w->n + 1e-9) return 0;
+        } else if (fabs(p[u] - c[u]) > 1e-9) {
+            return 0;
+        }
+    }
+    return 1;
+}
+
 static int build_owires(orc_grid *g)
 {
     const double dx = g->dx, dt = g->dt;
@@ -841,6 +858,10 @@ static int build_owires(orc_grid *g)
     int nn[3] = {g->nx, g->ny, g->nz};
     for (int m = 0; m < g->n_onodes; m++) {
         g->onodes[m].dlm = 0.0; g->onodes[m].lam_sum = 0.0; g->onodes[m].nu_sum = 0.0; g->onodes[m].nadj = 0;
+        /* a node on an axis-aligned wire joins that conductor: grounded to
+         * it like a node on the wall, its charge handed to the grid */
+        for (int w = 0; w < g->n_wires; w++)
+            if (on_axis_wire(&g->wires[w], g->onodes[m].p)) g->onodes[m].grounded = 1;
     }
     for (int w = 0; w < g->n_owires; w++)
         for (int s = g->owires[w].seg0; s < g->owires[w].seg0 + g->owires[w].nseg; s++) {
