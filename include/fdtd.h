@@ -155,7 +155,10 @@ int fdtd_add_wire_path(fdtd_grid *g, int i0, int j0, int k0, int i1, int j1, int
  * the straight path between the segment's end nodes.  An end point equal
  * (within 1e-9) to a node of an earlier oblique wire joins that node
  * (junction: the currents of all segments at a node change its charge).  A
- * node on an outer wall is grounded (potential 0).  In Debye media the
+ * node on an outer wall is grounded (potential 0), and so is a node on the
+ * node line of an axis-aligned wire (fdtd_add_wire, added before or after):
+ * it joins that conductor, its charge handed to the grid, where the PEC
+ * line carries it.  In Debye media the
  * in-cell capacitance takes the node medium's poles: K Q = eps0 eps_inf V +
  * sum_p P_p, K = ln(R/a) / (2 pi dl), tau_p dP_p/dt + P_p = eps0 deps_p V,
  * with the conduction sigma V K drawn from the charge.  Inside a CPML a wire

@@ -1631,6 +1631,17 @@ int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_by
     std::vector<double> src_cb;
     std::vector<std::array<double, 3 * fdtd::kMaxPoles>> src_debye;
     if (int rc = build_classes(g, cls, table, src_cb, dcls, dtable, src_debye)) return rc;
+    // an oblique-wire node on the node line of an axis-aligned wire joins that
+    // conductor: grounded to it like a node on the wall, its charge handed to
+    // the grid, where the PEC line carries it
+    for (ONodeH &nd : g->onodes)
+        for (const Wire &w : g->wires) {
+            bool on = true;
+            for (int u = 0; u < 3; ++u)
+                on = on && (u == w.axis ? nd.p[u] >= w.p[u] - 1e-9 && nd.p[u] <= w.p[u] + w.n + 1e-9
+                                        : std::fabs(nd.p[u] - w.p[u]) <= 1e-9);
+            if (on) nd.grounded = 1;
+        }
     if (!g->osegs.empty() && g->courant > wire_courant_limit(g)) {
         char msg[160];
         std::snprintf(msg, sizeof msg, "the oblique wires need courant <= %.4f (thinner wires or a smaller step)",

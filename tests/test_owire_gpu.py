@@ -122,6 +122,32 @@ def test_oblique_wires_graph_direct_and_checkpoint_bitwise(fdtd):
         g.close()
 
 
+def junction_scenario(seed, n, cpml, steps):
+    """oblique wires joined to an axis-aligned thin wire: a T junction
+    mid-line and a wire leaving the line's top end, driven by EMFs; the H-loop
+    probes around the thin wire's edges below and above the T junction see
+    the current the oblique branch hands over"""
+    sc = W.random_scenario(seed, n=n, cpml=cpml, n_wires=0, n_sources=1, n_probes=4, n_steps=steps,
+                           fields=True, courant=0.9)
+    x, y = cpml + 5, cpml + 6
+    sc.wires = [((x, y, cpml + 3), (x, y, n[2] - cpml - 5), 0.004)]
+    kt = cpml + 8
+    sc.owires = [((float(x), float(y), float(kt)), (n[0] - cpml - 3.6, n[1] - cpml - 4.3, kt + 2.7), 0.002),
+                 ((float(x), float(y), float(n[2] - cpml - 5)), (n[0] - cpml - 5.2, cpml + 2.9, n[2] - cpml - 3.4),
+                  0.003)]
+    t = np.arange(steps)
+    sc.owire_sources = [(0, 2, 150.0 * np.sin(0.09 * t) * (1 - np.exp(-t / 8.0))),
+                        (1, 1, 80.0 * (1 - np.exp(-t / 15.0)), 50.0)]
+    sc.owire_probes = [(0, 0), (1, 0), (0, 3)]
+    sc.probes = list(sc.probes) + [(1, (x, y, kt - 1), 2, 1), (1, (x, y, kt), 2, 1)]
+    return sc
+
+
+@pytest.mark.parametrize("cpml", [0, 6])
+def test_oblique_wires_joined_to_a_thin_wire_match_oracle(fdtd, cpml):
+    compare(fdtd, junction_scenario(7 + cpml, (26, 24, 28), cpml, 300), 300).close()
+
+
 def _start(F, sc, steps):
     g = F.from_scenario(sc, probe_capacity=steps)
     if sc.fields is not None:
