@@ -43,11 +43,12 @@ def args_parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="single",
-                    choices=["single", "config3", "debye", "tower", "batch", "surrogate"],
+                    choices=["single", "config3", "debye", "tower", "batch", "batch_inclined", "surrogate"],
                     help="single: the 256^3 grid (headline); config3: the 512x512x384 buried-mesh grid; "
                          "debye: the 256^3 grid over four-pole Debye soil; tower: a lightning strike to a "
                          "lattice tower of oblique wires (160x160x200); batch: 256 grounding domains in one "
-                         "batch; surrogate: the learned surrogate vs FDTD")
+                         "batch; batch_inclined: the same with inclined rods (oblique wires); surrogate: the "
+                         "learned surrogate vs FDTD")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n", type=int, default=256,
@@ -278,16 +279,17 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
-def run_batch_bench(a):
+def run_batch_bench(a, inclined=False):
     """256 grounding-rod domains (side 48..128, 8-cell CPML) advanced by the
-    batched engine; value = domains finished per second."""
+    batched engine; value = domains finished per second.  inclined: rods
+    leaning 15..60 degrees (oblique wires joined to the risers)."""
     import torch
     from paper_2207_06908_gb300 import _build, fdtd, grounding, workloads as W
     _build.build()
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     K = a.steps if a.steps != 4000 else W.GROUND_STEPS
     Wm = max(3, a.warmup)
-    scs = W.config4(n_steps=K + Wm)
+    scs = (W.config4_inclined if inclined else W.config4)(n_steps=K + Wm)
     t0 = time.perf_counter()
     blocks = {}
     for sc in scs:
@@ -318,7 +320,8 @@ def run_batch_bench(a):
             "n_gpus": 1, "steps": K, "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{len(scs)} grounding-rod domains, side 48..128, dx 0.25 m, 8-cell CPML, "
-                                   f"random soil, rod + riser + leads, 1 kA ramp; {W.GROUND_STEPS} steps per sim",
+                                   f"random soil, {'inclined rod (oblique wire, 15..60 deg)' if inclined else 'rod'} "
+                                   f"+ riser + leads, 1 kA ramp; {W.GROUND_STEPS} steps per sim",
                        "domains": len(scs), "cells": cells, "tile_depths": blocks,
                        "l2": "inputs larger than L2"},
             "gcell_updates_per_s": cells * K / (ms / 1e3) / 1e9,
@@ -326,7 +329,7 @@ def run_batch_bench(a):
                          "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
                          "bytes_per_step": bps},
             "setup_s": setup, "ctas": [b.launch_info(0), b.launch_info(1)], "clocks": clocks,
-            "gpu_launches": 3 * K}
+            "gpu_launches": (4 if inclined else 3) * K}
     print(json.dumps(line), flush=True)
     b.close()
     for g in grids:
@@ -469,8 +472,8 @@ def main():
     if a.impl == "reference":
         run_reference(a)
         return
-    if a.workload == "batch":
-        run_batch_bench(a)
+    if a.workload in ("batch", "batch_inclined"):
+        run_batch_bench(a, inclined=a.workload == "batch_inclined")
         return
     if a.workload == "surrogate":
         run_surrogate_bench(a)

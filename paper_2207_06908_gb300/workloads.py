@@ -395,7 +395,8 @@ def grounding_cells(length, depth):
     return max(1, int(round(length / GROUND_DX))), int(round(depth / GROUND_DX))
 
 
-def grounding_domain(n, eps_r, sigma, length, radius, depth, rise, n_steps=GROUND_STEPS, name="ground"):
+def grounding_domain(n, eps_r, sigma, length, radius, depth, rise, n_steps=GROUND_STEPS, name="ground",
+                     incline=0.0, courant=0.99):
     """One grounding-electrode domain of n^3 cells, dx = 0.25 m, 8-cell CPML:
     soil (eps_r, sigma) below the surface node n - 14, air above; a vertical
     rod of the given length and radius whose top is `depth` m below the
@@ -404,30 +405,37 @@ def grounding_domain(n, eps_r, sigma, length, radius, depth, rise, n_steps=GROUN
     two cells out and a voltage lead along +y with a one-cell probe gap two
     cells out, both running into the CPML (the layout of the paper's
     ground-potential-rise model file); a 1 kA linear ramp of the given rise
-    time on the source gap.  Probes: gap voltage and source current."""
+    time on the source gap.  Probes: gap voltage and source current.
+    incline > 0 (rad from the vertical): the rod is an oblique wire of the
+    same length leaning towards -x from the riser's bottom node, which joins
+    it to the riser (run below the oblique wire's Courant limit)."""
     dx = GROUND_DX
     d = GROUND_CPML
     c = n // 2
     ks = n - 14                                    # surface node
     lc, dc = grounding_cells(length, depth)
     kd = ks - dc                                   # rod top node
-    kb = kd - lc                                   # rod bottom node
-    if kb < d + 2:
+    kb = kd - lc * math.cos(incline)               # rod bottom (node units)
+    xb = c - lc * math.sin(incline)
+    if kb < d + 2 or xb < d + 2:
         raise ValueError("rod does not fit the domain")
     kt = ks + 4                                    # riser top, 1 m above the surface
     cm = paint_blocks((n, n, n), [((0, 0, 0), (n, n, ks), 1)])
     mats = [(1.0, 0.0, 1.0), (float(eps_r), float(sigma), 1.0)]
-    wires = [((c, c, kb), (c, c, kd), radius),     # rod
-             ((c, c, kd), (c, c, kt), radius),     # riser
+    rod = [((c, c, kd - lc), (c, c, kd), radius)] if incline == 0 else []
+    wires = rod + [((c, c, kd), (c, c, kt), radius),     # riser
              ((c, c, kt), (c + 2, c, kt), LEAD_RADIUS),
              ((c + 3, c, kt), (n - d, c, kt), LEAD_RADIUS),
              ((c, c, kt), (c, c + 2, kt), LEAD_RADIUS),
              ((c, c + 3, kt), (c, n - d, kt), LEAD_RADIUS)]
-    cur = ramp(sample_times(n_steps, dx, 0.99), 1e3, rise)
-    return Scenario(name, (n, n, n), dx, 0.99, d, cm, mats, wires=wires,
-                    sources=[((c + 2, c, kt), 0, cur)],
-                    probes=[(PROBE_V, (c, c + 2, kt), 1, 1), (PROBE_I, (c + 2, c, kt), 0, 1)],
-                    n_steps=n_steps)
+    cur = ramp(sample_times(n_steps, dx, courant), 1e3, rise)
+    sc = Scenario(name, (n, n, n), dx, courant, d, cm, mats, wires=wires,
+                  sources=[((c + 2, c, kt), 0, cur)],
+                  probes=[(PROBE_V, (c, c + 2, kt), 1, 1), (PROBE_I, (c + 2, c, kt), 0, 1)],
+                  n_steps=n_steps)
+    if incline != 0:
+        sc.owires = [((float(c), float(c), float(kd)), (xb, float(c), kb), radius)]
+    return sc
 
 
 def config4(n_domains=256, seed=0, n_steps=GROUND_STEPS, n_range=(48, 128)):
@@ -443,6 +451,27 @@ def config4(n_domains=256, seed=0, n_steps=GROUND_STEPS, n_range=(48, 128)):
         lmax = min(10.0, GROUND_DX * (n - 28))
         length = float(rng.uniform(1.0, lmax))
         out.append(grounding_domain(n, eps, sig, length, 0.008, 0.0, 0.25e-6, n_steps, name=f"rod{q}_n{n}"))
+    return out
+
+
+INCLINED_COURANT = 0.95   # below the 8 mm oblique rod's Courant limit (about 0.978 at dx 0.25 m)
+
+
+def config4_inclined(n_domains=256, seed=0, n_steps=GROUND_STEPS, n_range=(48, 128)):
+    """The batched workload with inclined rods: as config4, each rod leaning
+    at U[15, 60] degrees from the vertical (an oblique wire joined to the
+    riser), L capped so it stays inside the domain; Courant number 0.95."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for q in range(n_domains):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        eps = float(rng.uniform(4.0, 40.0))
+        sig = float(10 ** rng.uniform(-4.0, -1.0))
+        th = math.radians(float(rng.uniform(15.0, 60.0)))
+        lmax = min(10.0, GROUND_DX * (n - 28), GROUND_DX * (n // 2 - 11) / math.sin(th))
+        length = float(rng.uniform(1.0, lmax))
+        out.append(grounding_domain(n, eps, sig, length, 0.008, 0.0, 0.25e-6, n_steps, name=f"incl{q}_n{n}",
+                                    incline=th, courant=INCLINED_COURANT))
     return out
 
 

@@ -162,3 +162,30 @@ def test_thick_oblique_wire_needs_a_smaller_courant_number():
                 assert b"courant" in lib.fdtd_last_error(h)
         finally:
             lib.fdtd_destroy(h)
+
+
+def test_inclined_grounding_domains_fit_and_stay_below_the_wire_limit():
+    """every domain of the inclined-rod batched workload: the riser and leads
+    are accepted, the inclined rod lies inside the domain and joins the
+    riser's bottom node, and the Courant number the workload runs at is
+    below the domain's oblique-wire limit (so finalize accepts it)"""
+    from paper_2207_06908_gb300 import workloads as W
+    lib = _lib()
+    scs = W.config4_inclined(n_steps=10)
+    assert len(scs) == 256
+    for sc in scs:
+        (p0, p1, r), = sc.owires
+        riser = sc.wires[0]
+        assert riser[0] == tuple(int(v) for v in p0) and riser[0][:2] == riser[1][:2]   # rod top = riser bottom
+        assert all(sc.cpml + 2 <= v <= m - sc.cpml - 2 for v, m in zip(p1, sc.n))
+        h = ctypes.c_void_p()
+        assert lib.fdtd_create_grid(*sc.n, sc.dx, sc.courant, None, None, ctypes.byref(h)) == 0
+        try:
+            for q0, q1, rr in sc.wires:
+                assert lib.fdtd_add_wire(h, *q0, *q1, rr, None) == 0
+            assert lib.fdtd_add_oblique_wire(h, *p0, *p1, r, None) == 0
+            lim = ctypes.c_double()
+            assert lib.fdtd_wire_courant_limit(h, ctypes.byref(lim)) == 0
+            assert sc.courant < lim.value, (sc.name, lim.value)
+        finally:
+            lib.fdtd_destroy(h)

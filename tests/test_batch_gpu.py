@@ -78,6 +78,36 @@ def test_batch_grounding_domains_vs_oracle(fdtd):
         g.close()
 
 
+def test_batch_inclined_grounding_domains_vs_oracle(fdtd):
+    """three domains of the inclined-rod batched workload (rods of 1.5..4 m
+    leaning 20..60 degrees: oblique wires joined to the risers), 300 steps
+    from rest in one batch: gap voltage, source current, the rod's segment
+    currents and node charges within 1e-4 of the FP64 oracle"""
+    import math
+    rng = np.random.default_rng(8)
+    scs = []
+    for n, deg in ((48, 20), (52, 45), (56, 60)):
+        scs.append(W.grounding_domain(n, rng.uniform(4, 40), 10 ** rng.uniform(-4, -1), rng.uniform(1.5, 4.0),
+                                      0.008, 0.0, 0.25e-6, n_steps=300, incline=math.radians(deg),
+                                      courant=W.INCLINED_COURANT))
+    grids = [fdtd.from_scenario(sc, probe_capacity=300) for sc in scs]
+    b = fdtd.Batch(grids)
+    b.step(300)
+    b.synchronize()
+    for g, sc in zip(grids, scs):
+        o = oracle_from_scenario(sc, parity=True)
+        o.step(300)
+        for p in range(len(sc.probes)):
+            assert rel_l2(g.read_probe(p), o.read_probe(p)) <= 1e-4
+        I, Q = g.get_wire_state()
+        Io, Qo = o.get_wire_state()
+        assert rel_l2(I, Io) <= 1e-4 and rel_l2(Q, Qo) <= 1e-4
+        assert float(np.abs(Io).max()) > 100.0                 # the rod carries the feed current
+    b.close()
+    for g in grids:
+        g.close()
+
+
 def test_batch_rejects_mismatched_steps(fdtd):
     a = build(fdtd, W.random_scenario(1, n=(10, 10, 10), n_steps=4), 4)
     c = build(fdtd, W.random_scenario(2, n=(12, 10, 9), n_steps=4), 4)
