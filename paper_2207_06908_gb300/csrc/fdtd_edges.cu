@@ -8,8 +8,9 @@
 // each segment and the node potentials; this kernel, before the sources,
 // adds those currents to E^{n+1} through the same edge shares and takes the
 // node charges to t_{n+1}.
-// One CTA; a device-side step counter indexes the source samples and the
-// probe slots, so the launch can be replayed inside a CUDA graph.
+// One CTA per grid (one per domain in a batch, for the gather as well); a
+// device-side step counter indexes the source samples and the probe slots,
+// so the launches can be replayed inside a CUDA graph.
 #include "fdtd_srcprobe.cuh"
 
 namespace fdtd {
