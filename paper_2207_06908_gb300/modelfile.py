@@ -151,7 +151,7 @@ def parse(text: str, courant: float = 0.99, name: str = "model") -> Model:
     """Read a model file into a Model (scenario, output interval, probes)."""
     cmds = []
     for ln, raw in enumerate(text.splitlines(), 1):
-        s = re.split(r"[#%]", raw, 1)[0].strip()
+        s = re.split(r"[#%]", raw, maxsplit=1)[0].strip()
         if not s:
             continue
         m = _CMD.match(s)
