@@ -93,3 +93,24 @@ def test_weighted_mse_is_sum_of_squared_relative_errors():
         ym[r, c] -= h
         fd = (M.mse(yp, t, 0.5, w)[0] - M.mse(ym, t, 0.5, w)[0]) / (2 * h)
         assert dy[r, c] == pytest.approx(fd, rel=1e-7)
+
+
+def test_adam_bias_corrections_hold_at_every_step():
+    """with a constant gradient the bias-corrected moments are g and g^2 at
+    every step t, so each step is exactly -lr sign(g) (eps -> 0): after T
+    steps w = -T lr sign(g)"""
+    g = np.array([0.7, -1.3, 2e-3])
+    w, m, v = np.zeros(3), np.zeros(3), np.zeros(3)
+    for t in range(1, 26):
+        w, m, v = M.adam(w, m, v, g, 0.01, 0.9, 0.999, 1e-15, 0.0, t)
+    np.testing.assert_allclose(w, -25 * 0.01 * np.sign(g), rtol=1e-9)
+
+
+def test_adam_weight_decay_is_decoupled():
+    """with zero gradients the moments stay zero and decoupled weight decay
+    alone acts: w_t = w_0 (1 - lr wd)^t"""
+    w0 = np.array([1.0, -2.0, 0.5])
+    w, m, v = w0.copy(), np.zeros(3), np.zeros(3)
+    for t in range(1, 11):
+        w, m, v = M.adam(w, m, v, np.zeros(3), 0.01, 0.9, 0.999, 1e-8, 0.1, t)
+    np.testing.assert_allclose(w, w0 * (1 - 0.01 * 0.1) ** 10, rtol=1e-12)
