@@ -71,7 +71,7 @@ enum {
     FDTD_ECUDA = -4,      /* a CUDA call failed */
     FDTD_ECLASSES = -5,   /* more than 256 distinct coefficient classes */
     FDTD_ETIMEOUT = -6,   /* a bounded device wait ran out */
-    FDTD_EDIVERGED = -7,  /* non-finite field detected */
+    FDTD_EDIVERGED = -7,  /* non-finite field detected (reserved: no call returns it yet) */
     FDTD_ESTATE = -8      /* call not allowed in the grid's current state */
 };
 
