@@ -259,8 +259,8 @@ def run_reference(a):
                   a.workload if a.workload in ("single", "config3", "debye", "tower") else "single")
     from oracle import oracle as O
     o = O.OracleGrid.from_scenario(sc, parity=False)
-    w = 2
-    o.step(1)
+    w = max(3, a.warmup)                # untimed steps; the last one sizes the timed sample
+    o.step(w - 1)
     t0 = time.perf_counter()
     o.step(1)
     t1 = time.perf_counter() - t0
