@@ -118,3 +118,20 @@ def test_cli_parse_only(tmp_path, capsys):
     assert M.main([str(p), "--parse-only", "--courant", "0.9"]) == 0
     out = capsys.readouterr().out
     assert "30x25x20 cells" in out and "1 thin + 1 oblique" in out and "2 probes" in out
+
+
+def test_probe_orientation_follows_the_file():
+    """a current probe and a voltage path written from the second point to
+    the first read, after the model's sign, exactly what the forward ones
+    read (oracle run)"""
+    text = MODEL + """
+calculate (current, 1.5, 1.2, 0.8, 1.5, 1.2, 0.9)
+calculate (voltage, 1.5, 1.6, 1.3, 1.5, 1.3, 1.3)
+"""
+    m = M.parse(text, courant=0.9)
+    assert [s for _, _, s in m.probe_names] == [-1, 1, 1, -1]
+    o = oracle_from_scenario(m.scenario, parity=True)
+    o.step(80)
+    p = [s * o.read_probe(q) for q, (_, _, s) in enumerate(m.probe_names)]
+    assert np.array_equal(p[0], p[2]) and np.array_equal(p[1], p[3])
+    assert float(np.abs(p[1]).max()) > 0 and float(np.abs(p[0]).max()) > 0
