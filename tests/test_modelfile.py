@@ -121,9 +121,9 @@ def test_cli_parse_only(tmp_path, capsys):
 
 
 def test_probe_orientation_follows_the_file():
-    """a current probe and a voltage path written from the second point to
-    the first read, after the model's sign, exactly what the forward ones
-    read (oracle run)"""
+    """the same current probe and voltage path written in both directions
+    read, after the model's sign, exact opposites: each measures from its
+    first point to its second (oracle run)"""
     text = MODEL + """
 calculate (current, 1.5, 1.2, 0.8, 1.5, 1.2, 0.9)
 calculate (voltage, 1.5, 1.6, 1.3, 1.5, 1.3, 1.3)
@@ -133,5 +133,5 @@ calculate (voltage, 1.5, 1.6, 1.3, 1.5, 1.3, 1.3)
     o = oracle_from_scenario(m.scenario, parity=True)
     o.step(80)
     p = [s * o.read_probe(q) for q, (_, _, s) in enumerate(m.probe_names)]
-    assert np.array_equal(p[0], p[2]) and np.array_equal(p[1], p[3])
+    assert np.array_equal(p[0], -p[2]) and np.array_equal(p[1], -p[3])
     assert float(np.abs(p[1]).max()) > 0 and float(np.abs(p[0]).max()) > 0
