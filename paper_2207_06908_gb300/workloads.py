@@ -130,13 +130,15 @@ def double_exponential(t, i0, alpha, beta, k):
     return i0 * k * (np.exp(-alpha * t) - np.exp(-beta * t))
 
 
-def heidler(t, i0, tau1, tau2, n):
+def heidler(t, i0, tau1, tau2, n, eta=None, t0=0.0):
     """Heidler lightning-current function (Heidler and Cvetic, the waveform
-    class the paper's lightning examples use):
-    i(t) = (i0 / eta) (t/tau1)^n / (1 + (t/tau1)^n) exp(-t/tau2) for t > 0,
-    eta = exp(-(tau1/tau2) (n tau2/tau1)^(1/n)) the peak correction."""
-    t = np.asarray(t, dtype=np.float64)
-    eta = math.exp(-(tau1 / tau2) * (n * tau2 / tau1) ** (1.0 / n))
+    class the paper's lightning examples use), started at t0:
+    i(t) = (i0 / eta) s^n / (1 + s^n) exp(-(t - t0)/tau2), s = (t - t0)/tau1,
+    for t > t0; eta None: the peak correction
+    exp(-(tau1/tau2) (n tau2/tau1)^(1/n)), which makes the peak about i0."""
+    t = np.asarray(t, dtype=np.float64) - t0
+    if eta is None:
+        eta = math.exp(-(tau1 / tau2) * (n * tau2 / tau1) ** (1.0 / n))
     x = np.where(t > 0, t / tau1, 0.0) ** n
     return np.where(t > 0, i0 / eta * x / (1.0 + x) * np.exp(-np.maximum(t, 0.0) / tau2), 0.0)
 
@@ -346,7 +348,12 @@ PAPER_LAYERS = [
 ]
 
 
-def three_layer_array(n_steps=400, rise=0.37e-6):
+# the array model file's source function (Sec. 4.3): Heidler, tau1 0.37 us,
+# tau2 14 us, i0 1 A, n 10, eta 1 (no peak correction), started at 0.185 us
+ARRAY_HEIDLER = dict(i0=1.0, tau1=3.7e-7, tau2=1.4e-5, n=10, eta=1.0, t0=1.85e-7)
+
+
+def three_layer_array(n_steps=3000):
     """The electrode-array example of the paper's apparent-resistivity
     section: a 5 x 5 x 4 m domain at dx = 0.05 m (100 x 100 x 80 cells),
     10-cell CPML, three 1 m Debye soil layers (PAPER_LAYERS, top layer
@@ -355,9 +362,9 @@ def three_layer_array(n_steps=400, rise=0.37e-6):
     lead (r = 3 mm) from the first rod's top towards the second with a
     one-cell source gap at x = 1.45 m, and a voltage lead from the third rod
     towards the fourth with a one-cell probe gap at y = 3.45 m.  The source
-    is a 1 A linear ramp of the given rise time (the paper drives a Heidler
-    pulse).  Probes: voltage across the probe gap, current in the source
-    gap."""
+    is the model file's Heidler pulse (ARRAY_HEIDLER), which starts at
+    0.185 us, step 1941 of dt = 95.3 ps.  Probes: voltage across the probe
+    gap, current in the source gap."""
     dx = 0.05
     n = (100, 100, 80)
     ks = 60                                       # surface node (3 m)
@@ -372,7 +379,7 @@ def three_layer_array(n_steps=400, rise=0.37e-6):
              ((80, 60, kb), (80, 60, kt), rod), ((80, 80, kb), (80, 80, kt), rod),
              ((20, 20, kt), (29, 20, kt), lead), ((30, 20, kt), (40, 20, kt), lead),
              ((80, 60, kt), (80, 69, kt), lead), ((80, 70, kt), (80, 80, kt), lead)]
-    cur = ramp(sample_times(n_steps, dx, 0.99), 1.0, rise)
+    cur = heidler(sample_times(n_steps, dx, 0.99), **ARRAY_HEIDLER)
     sc = Scenario("three_layer_array", n, dx, 0.99, 10, cm, mats, wires=wires,
                   sources=[((29, 20, kt), 0, cur)],
                   probes=[(PROBE_V, (80, 69, kt), 1, 1), (PROBE_I, (29, 20, kt), 0, 1)],

@@ -13,3 +13,30 @@ def rel_l2(a, b):
     b = np.asarray(b, dtype=np.float64)
     nb = np.linalg.norm(b)
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+# ---- record of achieved parity errors ---------------------------------------
+# When FDTD_PARITY_RECORD names a file, every comparison that goes through
+# record() appends one JSON line to it: the case, the quantity compared, the
+# relative L2 error achieved, the bar it was held to and, for runs from rest,
+# the error of the same algorithm with FP32 storage (the yardstick of the
+# from-rest bar).  tests/parity_summary.py turns the file into a table.
+def record(case, quantity, err, bar, fp32_yardstick=None, steps=None):
+    import json
+    import os
+    path = os.environ.get("FDTD_PARITY_RECORD")
+    if not path:
+        return
+    if case is None:
+        case = os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0].split("::")[-1]
+    line = {"case": case, "quantity": quantity, "rel_l2": float(err), "bar": float(bar),
+            "stated_bar": 1e-5 if quantity.startswith("field") else 1e-4}
+    if fp32_yardstick is not None:
+        line["fp32_yardstick"] = float(fp32_yardstick)
+    if steps is not None:
+        line["steps"] = int(steps)
+    with open(path, "a") as f:
+        f.write(json.dumps(line) + "\n")
+
+
+COMPONENTS = ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz")
