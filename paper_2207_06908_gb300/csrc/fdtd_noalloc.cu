@@ -20,9 +20,9 @@
 namespace {
 
 // Step-kernel scratch shared by every fdtd_step_noalloc() call on a device:
-// [0, 2 * launches) work counters, then the error flag.  Every GPU that loads
-// the library holds these FDTD_NOALLOC_SCRATCH_INTS ints until the process
-// exits.
+// [0, 2 * launches) work counters of the grid being stepped; the last int is
+// the error flag, a slot no grid uses as a counter.  Every GPU that loads the
+// library holds these FDTD_NOALLOC_SCRATCH_INTS ints until the process exits.
 static __device__ __align__(256) int g_step_scratch[FDTD_NOALLOC_SCRATCH_INTS];
 
 constexpr int kMaxDevices = 64;

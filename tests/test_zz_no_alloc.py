@@ -16,17 +16,6 @@ from paper_2207_06908_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-FIELD_TOL = 1e-5
-PROBE_TOL = 1e-4
-
-
-def rel(a, b):
-    a = np.asarray(a, np.float64)
-    b = np.asarray(b, np.float64)
-    n = np.linalg.norm(b)
-    return np.linalg.norm(a - b) / (n if n > 0 else 1.0)
-
-
 def test_step_noalloc_matches_step_over_two_calls():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
@@ -45,12 +34,57 @@ def test_step_noalloc_matches_step_over_two_calls():
     assert lib.fdtd_step_noalloc(new._h, ctypes.c_int(33)) == 0
     new.synchronize()
     assert new.step_count == ref.step_count == 50
+    # the same kernels on the same inputs: equal bit for bit (the graph runs
+    # the z-layer launch beside the interior one, this entry point after it;
+    # they write disjoint planes)
     for c in range(6):
-        assert rel(new.get_field(c), ref.get_field(c)) <= FIELD_TOL
+        assert np.array_equal(new.get_field(c), ref.get_field(c))
     for p in range(len(sc.probes)):
-        assert rel(new.read_probe(p), ref.read_probe(p)) <= PROBE_TOL
+        assert np.array_equal(new.read_probe(p), ref.read_probe(p))
     ref.close()
     new.close()
+
+
+def test_step_noalloc_alternating_grids_on_two_streams():
+    """a grid with a CPML (two step launches, four counters) and one without
+    (one launch, two counters) stepped in turn through the shared static
+    scratch, each on its own stream: the error flag has a slot of its own, so
+    synchronising one grid while the other's steps run reads no live counter
+    and reports nothing, and both grids end equal to fdtd_step bit for bit"""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2207_06908_gb300 import fdtd
+    sa = W.random_scenario(44, n=(40, 23, 30), cpml=4, n_steps=90)
+    sb = W.random_scenario(45, n=(33, 20, 17), n_steps=90)
+    st_a, st_b = torch.cuda.Stream(), torch.cuda.Stream()
+    refs, news = [], []
+    for sc, st in ((sa, st_a), (sb, st_b)):
+        r = fdtd.from_scenario(sc, probe_capacity=90)
+        n = fdtd.from_scenario(sc, stream=st, probe_capacity=90)
+        for g in (r, n):
+            for c, f in enumerate(sc.fields):
+                g.set_field(c, f)
+        r.step(90)
+        refs.append(r)
+        news.append(n)
+    a, b = news
+    lib = a._lib
+    for na, nb in ((30, 20), (25, 40), (35, 30)):
+        assert lib.fdtd_step_noalloc(b._h, ctypes.c_int(nb)) == 0
+        assert lib.fdtd_synchronize(b._h) == 0
+        # a's steps are queued on its own stream while b synchronises
+        assert lib.fdtd_step_noalloc(a._h, ctypes.c_int(na)) == 0
+        assert lib.fdtd_synchronize(b._h) == 0
+        assert lib.fdtd_synchronize(a._h) == 0
+    for sc, r, n in zip((sa, sb), refs, news):
+        assert n.step_count == r.step_count == 90
+        for c in range(6):
+            assert np.array_equal(n.get_field(c), r.get_field(c))
+        for p in range(len(sc.probes)):
+            assert np.array_equal(n.read_probe(p), r.read_probe(p))
+        r.close()
+        n.close()
 
 
 def test_step_noalloc_rejects_unfinalized_grid():
