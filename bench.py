@@ -10,6 +10,12 @@ probes; --steps defaults to the workload's 4000 steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+The default line also carries the metric's second half as two sub-records
+measured in the same process (one GPU): "batch" (the 256-domain grounding
+batch, K timed steps, sims/s) and "surrogate" (K timed inference batches of
+4096, sims/s with the FDTD fallback, waveform error against FDTD on 64 of
+the inputs), each with its own ms_per_step, roofline and clocks.
+
 Multi-GPU: the path does not shard; N ranks run N independent replicas
 (weak scaling), value = all ranks' cell updates / the slowest rank's time.
 --impl reference times the FP64 CPU oracle on the host cores instead.
@@ -51,6 +57,8 @@ def args_parse():
                          "learned surrogate vs FDTD")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="leave out the batch and surrogate sub-records of the default line")
     ap.add_argument("--n", type=int, default=256,
                     help="grid edge; 256 is the workload, smaller grids only for profiling")
     ap.add_argument("--cpu-seconds", type=float, default=20.0,
@@ -279,16 +287,14 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
-def run_batch_bench(a, inclined=False):
+def batch_record(K, Wm, inclined=False):
     """256 grounding-rod domains (side 48..128, 8-cell CPML) advanced by the
-    batched engine; value = domains finished per second.  inclined: rods
-    leaning 15..60 degrees (oblique wires joined to the risers)."""
+    batched engine for K timed steps after Wm untimed ones; value = domains
+    finished per second (K steps of the 2000 each domain runs).  inclined:
+    rods leaning 15..60 degrees (oblique wires joined to the risers)."""
     import torch
     from paper_2207_06908_gb300 import _build, fdtd, grounding, workloads as W
     _build.build()
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    K = a.steps if a.steps != 4000 else W.GROUND_STEPS
-    Wm = max(3, a.warmup)
     scs = (W.config4_inclined if inclined else W.config4)(n_steps=K + Wm)
     t0 = time.perf_counter()
     blocks = {}
@@ -316,24 +322,37 @@ def run_batch_bench(a, inclined=False):
     bps = 49 * cells + 32 * slab
     peak, peak_kind = peaks()
     achieved = bps / (ms / K / 1e3) / 1e9
-    line = {"metric": "batched sims/s", "value": len(scs) / (ms / 1e3) * (K / W.GROUND_STEPS), "unit": "sims/s",
-            "n_gpus": 1, "steps": K, "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{len(scs)} grounding-rod domains, side 48..128, dx 0.25 m, 8-cell CPML, "
-                                   f"random soil, {'inclined rod (oblique wire, 15..60 deg)' if inclined else 'rod'} "
-                                   f"+ riser + leads, 1 kA ramp; {W.GROUND_STEPS} steps per sim",
-                       "domains": len(scs), "cells": cells, "tile_depths": blocks,
-                       "l2": "inputs larger than L2"},
-            "gcell_updates_per_s": cells * K / (ms / 1e3) / 1e9,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
-                         "bytes_per_step": bps},
-            "setup_s": setup, "ctas": [b.launch_info(0), b.launch_info(1)], "clocks": clocks,
-            "gpu_launches": (4 if inclined else 3) * K}
-    print(json.dumps(line), flush=True)
+    rec = {"metric": "batched sims/s", "value": len(scs) / (ms / 1e3) * (K / W.GROUND_STEPS), "unit": "sims/s",
+           "steps": K, "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": f"{len(scs)} grounding-rod domains, side 48..128, dx 0.25 m, 8-cell CPML, "
+                                  f"random soil, {'inclined rod (oblique wire, 15..60 deg)' if inclined else 'rod'} "
+                                  f"+ riser + leads, 1 kA ramp; {W.GROUND_STEPS} steps per sim",
+                      "domains": len(scs), "cells": cells, "tile_depths": blocks,
+                      "l2": "inputs larger than L2"},
+           "gcell_updates_per_s": cells * K / (ms / 1e3) / 1e9,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                        "kernel": "batched step kernel (per-step time incl. the batch source/probe kernel)",
+                        "bytes_per_step": bps},
+           "setup_s": setup, "ctas": [b.launch_info(0), b.launch_info(1)], "clocks": clocks,
+           "gpu_launches": (4 if inclined else 3) * K}
     b.close()
     for g in grids:
         g.close()
+    return rec
+
+
+def run_batch_bench(a, inclined=False):
+    """--workload batch / batch_inclined: the batch record as the bench line"""
+    import torch
+    from paper_2207_06908_gb300 import workloads as W
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    K = a.steps if a.steps != 4000 else W.GROUND_STEPS
+    rec = batch_record(K, max(3, a.warmup), inclined)
+    line = dict(rec)
+    line.update({"n_gpus": 1, "scaling": "weak", "vs_baseline": None})
+    print(json.dumps(line), flush=True)
 
 
 def l2_flusher(torch):
@@ -344,22 +363,23 @@ def l2_flusher(torch):
     return lambda: buf.fill_(1.0)
 
 
-def run_surrogate_bench(a):
+def surrogate_record(K, Wm, cpu_seconds=10.0, n_eval=512, e2e=True, cpu=True):
     """Learned surrogate of the 64^3 grounding-rod runs against the batched
-    FDTD engine on the same inputs.  value = sims/s of surrogate plus FDTD
-    fallback: 1 / ((1 - f) / S_sur + f / S_fdtd), f the fallback fraction."""
+    FDTD engine on the same inputs: K timed inference batches of 4096 after
+    Wm untimed ones, FDTD runs of n_eval of the inputs for the waveform error
+    and the FDTD rate.  value = sims/s of surrogate plus FDTD fallback:
+    1 / ((1 - f) / S_sur + f / S_fdtd), f the fallback fraction.  e2e: also
+    time the public predict_with_fallback call; cpu: time the FP64 network
+    oracle on the host cores."""
     import numpy as np
     import torch
     from oracle import mlp_oracle as MO
     from paper_2207_06908_gb300 import _build, mlp, surrogate as S, workloads as W
     _build.build()
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     if not os.path.exists(S.WEIGHTS):
         raise SystemExit(f"surrogate weights missing: {S.WEIGHTS}")
     sur = S.Surrogate.load(S.WEIGHTS)
     B = 4096
-    K = a.steps if a.steps != 4000 else 200
-    Wm = max(3, a.warmup)
     stream = torch.cuda.current_stream()
     # held-out-distribution inputs (seeds after the training seeds)
     X = np.stack([W.surrogate_inputs(s) for s in range(S.HELDOUT_SEEDS[0], S.HELDOUT_SEEDS[0] + B)])
@@ -405,7 +425,6 @@ def run_surrogate_bench(a):
         tpeak, tsrc = 1900.0, "fallback"
     tach = flops_layer / (lay_ms / 1e3) / 1e12
     # batched FDTD on a held-out sample of the same inputs: waveform error and FDTD sims/s
-    n_eval = 512
     t0 = time.perf_counter()
     Yf = S.generate(X[:n_eval])
     t_fdtd = time.perf_counter() - t0
@@ -417,54 +436,66 @@ def run_surrogate_bench(a):
     acc = acc_all[:n_eval]
     final = np.where(acc, rel, 0.0)
     value = 1.0 / ((1.0 - f_fb) / s_sur + f_fb / s_fdtd)
-    # end to end through the public call: host parameters in, host
-    # waveforms out, the rejected inputs re-run by the FDTD engine inside
-    # the call (the first call is untimed: graph capture, tile tuning)
-    sur.predict_with_fallback(X)
-    e2e_t, n_fb = [], 0
-    for i in range(3):
-        torch.cuda.synchronize()
+    e2e_rec, n_fb, reps_e2e = None, 0, 0
+    if e2e:
+        # end to end through the public call: host parameters in, host
+        # waveforms out, the rejected inputs re-run by the FDTD engine inside
+        # the call (the first call is untimed: graph capture, tile tuning)
+        sur.predict_with_fallback(X)
+        e2e_t = []
+        for i in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            wv, acc_e = sur.predict_with_fallback(X)
+            e2e_t.append(time.perf_counter() - t0)
+            n_fb += int((~acc_e).sum())
+        reps_e2e = len(e2e_t)
+        e2e_rec = {"value": B * reps_e2e / sum(e2e_t), "unit": "sims/s", "h2d_bytes_per_step": B * 6 * 4,
+                   "d2h_bytes_per_step": B * 512 * 4 + B * 4,
+                   "includes": f"predict_with_fallback on the {B} inputs: host feature encoding, upload, both "
+                               f"networks, readback, and FDTD runs (build, upload, {W.GROUND_STEPS} steps, "
+                               f"probe readback) of the {n_fb // reps_e2e} rejected inputs per call"}
+    cpu_rec = None
+    if cpu:
+        # FP64 network oracle on the host cores, bounded sample
+        layers = [(w.astype(np.float64), b.astype(np.float64)) for w, b in
+                  zip([(np.asarray(Wb.float().cpu())) for Wb in net.Wb], [b.cpu().numpy() for b in net.b])]
+        fx = S.features(X).astype(np.float64)
         t0 = time.perf_counter()
-        wv, acc_e = sur.predict_with_fallback(X)
-        e2e_t.append(time.perf_counter() - t0)
-        n_fb += int((~acc_e).sum())
-    e2e_s = B * len(e2e_t) / sum(e2e_t)
-    # FP64 network oracle on the host cores, bounded sample
-    layers = [(w.astype(np.float64), b.astype(np.float64)) for w, b in
-              zip([(np.asarray(Wb.float().cpu())) for Wb in net.Wb], [b.cpu().numpy() for b in net.b])]
-    fx = S.features(X).astype(np.float64)
-    t0 = time.perf_counter()
-    reps = 0
-    while time.perf_counter() - t0 < min(a.cpu_seconds, 10.0):
-        MO.forward(fx, layers, ["gelu", "gelu", "gelu", "none"])
-        reps += 1
-    cpu_rate = B * reps / (time.perf_counter() - t0)
-    line = {"metric": "surrogate sims/s at <=2% waveform error (FDTD fallback)", "value": value,
-            "unit": "sims/s", "n_gpus": 1, "steps": K, "warmup": Wm, "ms_per_step": ms / K,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
-            "data": "synthetic",
-            "config": {"workload": f"grounding-rod surrogate, MLP 6-256-256-256-512 GELU + error head 6-64-64-1, "
-                                   f"inference batch {B}; FDTD comparison on {n_eval} of the same inputs "
-                                   f"(64^3 domains, dx 0.25 m, 8-cell CPML, {W.GROUND_STEPS} steps)",
-                       "batch": B, "l2": "flushed between timed iterations (1 GB write)"},
-            "surrogate_sims_s": s_sur, "fdtd_sims_s": s_fdtd, "fallback_fraction": f_fb,
-            "speedup_vs_fdtd": value / s_fdtd,
-            "waveform_rel_l2": {"n": n_eval, "median": float(np.median(rel)), "mean": float(rel.mean()),
-                                "max": float(rel.max()), "max_accepted": float(rel[acc].max()) if acc.any() else None,
-                                "mean_with_fallback": float(final.mean())},
-            "roofline": {"bound": "tensor", "achieved": tach, "peak": tpeak, "unit": "TFLOP/s",
-                         "frac": tach / tpeak, "traffic": None, "peak_source": tsrc,
-                         "kernel": f"gemm_kernel, {B}x256 @ 256x512 output layer, {lay_ms * 1e3:.1f} us"},
-            "e2e": {"value": e2e_s, "unit": "sims/s", "h2d_bytes_per_step": B * 6 * 4,
-                    "d2h_bytes_per_step": B * 512 * 4 + B * 4,
-                    "includes": f"predict_with_fallback on the {B} inputs: host feature encoding, upload, both "
-                                f"networks, readback, and FDTD runs (build, upload, {W.GROUND_STEPS} steps, "
-                                f"probe readback) of the {n_fb // 3} rejected inputs per call"},
-            "cpu_baseline": {"value": cpu_rate, "unit": "sims/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"{reps} FP64 forward passes of the waveform network over the {B} inputs"},
-            "clocks": clocks, "gpu_launches": 8 * K}
-    print(json.dumps(line), flush=True)
+        reps = 0
+        while time.perf_counter() - t0 < min(cpu_seconds, 10.0):
+            MO.forward(fx, layers, ["gelu", "gelu", "gelu", "none"])
+            reps += 1
+        cpu_rec = {"value": B * reps / (time.perf_counter() - t0), "unit": "sims/s", "cores": os.cpu_count(),
+                   "kind": "oracle", "sample": f"{reps} FP64 forward passes of the waveform network over the {B} inputs"}
+    rec = {"metric": "surrogate sims/s at <=2% waveform error (FDTD fallback)", "value": value,
+           "unit": "sims/s", "steps": K, "warmup": Wm, "ms_per_step": ms / K,
+           "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+           "config": {"workload": f"grounding-rod surrogate, MLP 6-256-256-256-512 GELU + error head 6-64-64-1, "
+                                  f"inference batch {B}; FDTD comparison on {n_eval} of the same inputs "
+                                  f"(64^3 domains, dx 0.25 m, 8-cell CPML, {W.GROUND_STEPS} steps)",
+                      "batch": B, "l2": "flushed between timed iterations (1 GB write)"},
+           "surrogate_sims_s": s_sur, "fdtd_sims_s": s_fdtd, "fallback_fraction": f_fb,
+           "speedup_vs_fdtd": value / s_fdtd,
+           "waveform_rel_l2": {"n": n_eval, "median": float(np.median(rel)), "mean": float(rel.mean()),
+                               "max": float(rel.max()), "max_accepted": float(rel[acc].max()) if acc.any() else None,
+                               "mean_with_fallback": float(final.mean())},
+           "roofline": {"bound": "tensor", "achieved": tach, "peak": tpeak, "unit": "TFLOP/s",
+                        "frac": tach / tpeak, "traffic": None, "peak_source": tsrc,
+                        "kernel": f"gemm_kernel, {B}x256 @ 256x512 output layer, {lay_ms * 1e3:.1f} us"},
+           "e2e": e2e_rec, "cpu_baseline": cpu_rec, "clocks": clocks, "gpu_launches": 8 * K}
     del replay
+    return rec
+
+
+def run_surrogate_bench(a):
+    """--workload surrogate: the surrogate record as the bench line"""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    K = a.steps if a.steps != 4000 else 200
+    line = dict(surrogate_record(K, max(3, a.warmup), a.cpu_seconds))
+    line.update({"n_gpus": 1, "scaling": "weak", "vs_baseline": None})
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -568,6 +599,14 @@ def main():
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = cpu_baseline(sc, a.cpu_seconds)
 
+    # the metric's second half on the same GPU (one process only): the
+    # 256-domain batch for K steps and surrogate inference for K batches,
+    # with the surrogate's waveform error against FDTD on 64 of its inputs
+    sub = {}
+    if rank == 0 and world == 1 and a.workload == "single" and not a.no_sub:
+        sub["batch"] = batch_record(K, Wm)
+        sub["surrogate"] = surrogate_record(K, Wm, n_eval=64, e2e=False, cpu=False)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
                 "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -575,6 +614,7 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": (3 + bool(getattr(sc, "debye", None)) + bool(getattr(sc, "owires", None))) * K,
                 "finite": finite}
+        line.update(sub)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -71,7 +71,7 @@ enum {
     FDTD_ECUDA = -4,      /* a CUDA call failed */
     FDTD_ECLASSES = -5,   /* more than 256 distinct coefficient classes */
     FDTD_ETIMEOUT = -6,   /* a bounded device wait ran out */
-    FDTD_EDIVERGED = -7,  /* non-finite field detected (reserved: no call returns it yet) */
+    FDTD_EDIVERGED = -7,  /* the watchdog found a NaN or an infinity in the fields */
     FDTD_ESTATE = -8      /* call not allowed in the grid's current state */
 };
 
@@ -261,6 +261,21 @@ int fdtd_add_probe(fdtd_grid *g, int kind, int i, int j, int k, int axis, int n_
  * Before fdtd_finalize(); FDTD_EINVAL outside 0..256. */
 int fdtd_set_block(fdtd_grid *g, int planes);
 
+/* fdtd_set_watchdog: the divergence watchdog of fdtd_step().  The leapfrog
+ * of Sec. 2.1 is stable only under the Courant bound; an unstable run grows
+ * without bound, overflows FP32 and spreads NaN.  Every time the grid's
+ * step count crosses a multiple of `every` during fdtd_step() (checked after
+ * each 32-step graph replay or direct step), one streaming kernel reads the
+ * six field arrays on the grid's stream and sets a device flag if any value
+ * is a NaN or an infinity; the next fdtd_synchronize() (and every call that
+ * synchronises: fdtd_read_probes, fdtd_get_field, ...) returns
+ * FDTD_EDIVERGED and clears the flag, so a grid that keeps diverging
+ * reports again at the next check.  A check reads 48 bytes per cell once;
+ * with the default period of 1024 steps that is under 0.1 % of the steps'
+ * traffic.  every = 0 turns the watchdog off.  Batches and
+ * fdtd_step_noalloc() run no check.  Any time; FDTD_EINVAL if every < 0. */
+int fdtd_set_watchdog(fdtd_grid *g, int every);
+
 /* Device bytes fdtd_finalize() needs for probe_capacity recorded steps. */
 int fdtd_arena_bytes(const fdtd_grid *g, int probe_capacity, size_t *bytes);
 
@@ -303,11 +318,17 @@ int fdtd_synchronize(fdtd_grid *g);
  * The first call on a device looks the array's device address up
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  Every call on a device shares the array and
- * keeps the last call's contents: each call clears the counters on the
- * grid's stream before its first launch, and the error flag is read (and
- * cleared) by fdtd_synchronize() on a grid that used this entry point.
- * Calls that overlap on the GPU (grids stepped through this entry point on
- * different streams at the same time) race on the array.
+ * keeps the last call's contents: the counters sit at the start of the
+ * array and each call clears them on the grid's stream before its first
+ * launch; the error flag is the array's last int, the same slot for every
+ * grid, which no call clears on entry.  fdtd_synchronize() on a grid that
+ * used this entry point reads the flag and clears it on the grid's stream.
+ * Because the flag is shared, that call reports a timeout of any earlier
+ * fdtd_step_noalloc() call on the device that no fdtd_synchronize() has
+ * reported yet, whichever grid it stepped: synchronise each grid after its
+ * own calls to tell whose steps gave up.  Calls that overlap on the GPU
+ * (grids stepped through this entry point on different streams at the same
+ * time) race on the counters.
  *
  * Returns FDTD_EINVAL if the grid needs more scratch than the array holds,
  * FDTD_ESTATE before fdtd_finalize(), FDTD_ECUDA on a launch error. */

@@ -61,6 +61,7 @@ def load():
             "fdtd_add_source": (I, [P, I, I, I, I, D, P, I, ip]),
             "fdtd_add_probe": (I, [P, I, I, I, I, I, I, ip]),
             "fdtd_set_block": (I, [P, I]),
+            "fdtd_set_watchdog": (I, [P, I]),
             "fdtd_arena_bytes": (I, [P, I, ctypes.POINTER(S)]),
             "fdtd_finalize": (I, [P, I, P, S]),
             "fdtd_step": (I, [P, I]),

@@ -127,7 +127,7 @@ __device__ __forceinline__ void wire_scatter_body(const EdgeArgs &a)
 __device__ __forceinline__ void edge_body(const EdgeArgs &a)
 {
     __shared__ long long n_s;
-    if (threadIdx.x == 0) n_s = __ldcg(a.step);
+    if (threadIdx.x == 0) n_s = __ldcg(a.step) + a.step_t;
     __syncthreads();
     const long long n = n_s;
     if (a.w.n_seg > 0 && !a.wire_done) wire_scatter_body(a);
@@ -141,7 +141,7 @@ __global__ void wire_finish_kernel(const EdgeArgs a) { wire_scatter_body(a); }
 __global__ void wire_gather_kernel(const EdgeArgs a)
 {
     __shared__ long long n_s;
-    if (threadIdx.x == 0) n_s = *a.step;
+    if (threadIdx.x == 0) n_s = *a.step + a.step_t;
     __syncthreads();
     wire_gather_body(a, n_s);
 }
@@ -161,7 +161,7 @@ __global__ void wire_gather_batch_kernel(const EdgeArgs *e, int parity)
     __shared__ long long n_s;
     if (threadIdx.x == 0) {
         a = e[2 * blockIdx.x + parity];
-        if (a.w.n_seg > 0) n_s = __ldcg(a.step);
+        if (a.w.n_seg > 0) n_s = __ldcg(a.step) + a.step_t;
     }
     __syncthreads();
     if (a.w.n_seg > 0) wire_gather_body(a, n_s);

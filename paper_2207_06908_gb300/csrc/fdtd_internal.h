@@ -60,6 +60,24 @@ struct PsiGeom {
     int xb, yb;              // bytes of one x / y box slot (128-aligned)
 };
 
+// Debye media: up to kMaxPoles poles per edge; per cell one record of
+// [E component][pole]{cj, k, be} (E^{n+1} += cj J^n, J^{n+1} = k J^n +
+// be (E^{n+1} - E^n)); record 0 = no dispersive component
+constexpr int kMaxPoles = 4;
+constexpr int kDebyeRec = 3 * kMaxPoles * 3;
+
+struct SourceDesc {
+    int comp;                // 0..2
+    long long idx;           // element index in the field arrays
+    float coef;              // -cb / dx of the edge
+    int n_samples;
+    long long sample_off;    // offset into the sample table
+    long long jidx;          // element index in the Debye current arrays, or -1
+    float be[kMaxPoles];     // be of the edge's poles (dispersive edge)
+    int hard;                // ideal voltage source: samples are volts, E is set to vcoef * V
+    float vcoef;             // -1 / dx
+};
+
 struct StepArgs {
     int nx, ny, nz;
     int pitch;               // row pitch in elements (multiple of 4)
@@ -84,6 +102,15 @@ struct StepArgs {
     int region;              // bytes of the staged-auxiliary region this domain needs
     int ox, oy;              // byte offsets of the x and y box groups in that region
     int zxy;                 // 1: stage the z layer together with x / y
+    // current sources applied in the E update of the items that own their
+    // edges (single-grid steps only; n_isrc = 0: the source/probe kernel
+    // applies them): source q lies in launch isrc_loc[q].x, item .y
+    int n_isrc;
+    const int2 *isrc_loc;
+    const SourceDesc *src;
+    const float *samples;
+    const long long *step;   // device step counter; this step's sample is *step + step_t
+    int step_t;
 };
 
 // One domain of a step launch, in device memory (the launch reads the
@@ -116,23 +143,7 @@ struct BatchArgs {
     int nh;                  // slots of the H / class / CPML ring (2 or 3)
 };
 
-// Debye media: up to kMaxPoles poles per edge; per cell one record of
-// [E component][pole]{cj, k, be} (E^{n+1} += cj J^n, J^{n+1} = k J^n +
-// be (E^{n+1} - E^n)); record 0 = no dispersive component
-constexpr int kMaxPoles = 4;
-constexpr int kDebyeRec = 3 * kMaxPoles * 3;
 
-struct SourceDesc {
-    int comp;                // 0..2
-    long long idx;           // element index in the field arrays
-    float coef;              // -cb / dx of the edge
-    int n_samples;
-    long long sample_off;    // offset into the sample table
-    long long jidx;          // element index in the Debye current arrays, or -1
-    float be[kMaxPoles];     // be of the edge's poles (dispersive edge)
-    int hard;                // ideal voltage source: samples are volts, E is set to vcoef * V
-    float vcoef;             // -1 / dx
-};
 
 struct DebyeArgs {
     const float *Ein[3];     // E^n (the step's input buffers)
@@ -227,7 +238,19 @@ struct EdgeArgs {
     const float *Ein[3];     // E^n, the step's input (oblique wires read it)
     WireArgs w;              // oblique wires (n_seg = 0: none)
     int wire_done;           // the wires' scatter and charges ran before the Debye kernel
+    int step_t;              // this launch serves step *step + step_t
+    int advance;             // 1: set *step to that step + 1 when done
+    int skip_src;            // the current sources ran in the step kernel
 };
+
+// the six field arrays of one state (Ex Ey Ez Hx Hy Hz)
+struct FieldPtrs {
+    const float *p[6];
+};
+
+// fdtd_watch.cu: sets *flag to 1 if any of the six arrays (n_elems floats
+// each, a multiple of 4, 16-byte aligned) holds a NaN or an infinity
+cudaError_t launch_finite_check(const FieldPtrs &f, long long n_elems, int *flag, int blocks, cudaStream_t s);
 
 // fdtd_step.cu
 cudaError_t launch_step(const SingleArgs &one, const BatchArgs &b, int grid, cudaStream_t s);

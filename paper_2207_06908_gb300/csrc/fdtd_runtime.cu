@@ -18,6 +18,7 @@
 #include <vector>
 
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "fdtd.h"
 #include "fdtd_internal.h"
@@ -29,6 +30,7 @@ constexpr double kEps0 = 8.8541878128e-12;
 constexpr double kMu0 = 1.25663706212e-6;
 constexpr double kR0 = 0.23;        // intrinsic radius of a zero-E line, in cells
 constexpr int kGraphSteps = 32;     // steps per captured graph (even)
+constexpr int kWatchSteps = 1024;   // default period of the divergence watchdog
 
 struct Wire { int axis, p[3], n; double radius; };
 struct Source { int axis, p[3]; std::vector<float> cur; int hard = 0; };   // hard: ideal voltage source
@@ -130,9 +132,17 @@ struct fdtd_grid {
     long long *step_d = nullptr;
     int *work_d = nullptr;          // [2 per launch] step-kernel work counters
     int *err_d = nullptr;           // bounded-wait failure flag
+    int *div_d = nullptr;           // watchdog flag: a field held a NaN or an infinity
+    int watch = kWatchSteps;        // watchdog period in steps (0 = off)
+    int sms = 0;                    // SMs of the grid's device
     fdtd::TmaMaps maps[2];          // TMA descriptors of each input parity
     fdtd::DomainSlot *slot_d = nullptr;   // this grid as a one-domain step launch
     int *item_start_d = nullptr;          // [launch][2]: {0, items}
+    int2 *isrc_d = nullptr;               // per current source: {launch, work item} of its edge
+    // single-grid steps apply the current sources in the step kernel and read
+    // the probes of step n beside step n + 1 (no Debye media, no oblique
+    // wires, no ideal voltage sources, at most 32 sources)
+    bool fast = false;
     fdtd::DomainSlot slot_h;              // host copy (also read by batches)
     fdtd::EdgeArgs edge_h[2];             // edge-kernel arguments per input parity
     fdtd::PsiGeom pg{};             // staged CPML box geometry
@@ -192,7 +202,7 @@ int cuda_fail(fdtd_grid *g, cudaError_t e, const char *what)
 
 // ---- device arena plan -------------------------------------------------
 struct Plan {
-    size_t field, cls, table, prof[3], psi[fdtd::PSI_COUNT], src, samples, probes, out, step, work, slot, items,
+    size_t field, cls, table, prof[3], psi[fdtd::PSI_COUNT], src, samples, probes, out, step, work, slot, items, isrc,
         J, dcls, dtable, oseg, ochunk, oedge, oscat, oterm, onode, oadj, oI, oQ, oV, oP, osrc, osamp, total;
 };
 
@@ -252,6 +262,7 @@ Plan make_plan(const fdtd_grid *g, int capacity)
     p.work = take(8 * sizeof(int));
     p.slot = take(sizeof(fdtd::DomainSlot));
     p.items = take(4 * sizeof(int));
+    p.isrc = take(std::max<size_t>(1, g->srcs.size()) * sizeof(int2));
     int z0, z1;
     const int P = debye_extent(g, &z0, &z1);
     const size_t box = (size_t)(z1 - z0) * g->plane;
@@ -995,6 +1006,9 @@ fdtd::EdgeArgs edge_args(const fdtd_grid *g, int parity)
     e.wire_done = g->npoles > 0 && !g->osegs.empty();
     e.w.src = g->osrc_d;
     e.w.samples = g->osamp_d;
+    e.step_t = 0;
+    e.advance = 1;
+    e.skip_src = 0;
     return e;
 }
 
@@ -1025,6 +1039,20 @@ fdtd::SingleArgs single_args(const fdtd_grid *g, int parity, int l)
     return one;
 }
 
+// the same, for a single-grid step that applies the current sources in the
+// step kernel: step t of a sequence that began at the device counter
+fdtd::SingleArgs single_args_fast(const fdtd_grid *g, int parity, int l, int t)
+{
+    fdtd::SingleArgs one = single_args(g, parity, l);
+    one.a.n_isrc = (int)g->srcs.size();
+    one.a.isrc_loc = g->isrc_d;
+    one.a.src = g->src_d;
+    one.a.samples = g->samples_d;
+    one.a.step = g->step_d;
+    one.a.step_t = t;
+    return one;
+}
+
 // launch l of one step of this grid alone
 fdtd::BatchArgs grid_launch(const fdtd_grid *g, int parity, int l, int *work, int *err)
 {
@@ -1044,8 +1072,53 @@ fdtd::BatchArgs grid_launch(const fdtd_grid *g, int parity, int l, int *work, in
     return b;
 }
 
-cudaError_t enqueue_step(fdtd_grid *g, int parity, cudaStream_t s)
+// One step with the current sources in the step kernel (g->fast): step t of
+// a sequence whose first step is the device counter's value.  The probes of
+// the previous step (t > 0) read that step's output -- this step's input,
+// which nothing writes now -- on the side stream beside the step kernels;
+// the last step of the sequence (last) reads its own probes after its step
+// kernels and advances the counter by t + 1.
+cudaError_t enqueue_step_fast(fdtd_grid *g, int parity, cudaStream_t s, int t, bool last)
 {
+    auto launch = [g, parity, t](int l) {
+        return [g, parity, t, l](cudaStream_t st) {
+            return fdtd::launch_step(single_args_fast(g, parity, l, t),
+                                     grid_launch(g, parity, l, g->lc[l].work, g->err_d), g->lc[l].grid, st);
+        };
+    };
+    const bool prev = t > 0 && !g->probes.empty();
+    cudaError_t e = cudaSuccess;
+    if (g->fk.side && (g->n_launch == 2 || prev)) {
+        auto side = [g, parity, t, prev, &launch](cudaStream_t st) {
+            cudaError_t r = g->n_launch == 2 ? launch(1)(st) : cudaSuccess;
+            if (r == cudaSuccess && prev) {
+                fdtd::EdgeArgs pa = edge_args(g, parity ^ 1);     // step t - 1's output
+                pa.n_src = 0;
+                pa.skip_src = 1;
+                pa.step_t = t - 1;
+                pa.advance = 0;
+                r = fdtd::launch_edges(pa, st);
+            }
+            return r;
+        };
+        e = g->fk.run(s, side, launch(0));
+    } else {
+        for (int l = 0; l < g->n_launch && e == cudaSuccess; ++l) e = launch(l)(s);
+    }
+    if (e == cudaSuccess && last) {
+        fdtd::EdgeArgs pa = edge_args(g, parity);
+        pa.n_src = 0;
+        pa.skip_src = 1;
+        pa.step_t = t;
+        pa.advance = 1;
+        e = fdtd::launch_edges(pa, s);
+    }
+    return e;
+}
+
+cudaError_t enqueue_step(fdtd_grid *g, int parity, cudaStream_t s, int t = 0, bool last = true)
+{
+    if (g->fast) return enqueue_step_fast(g, parity, s, t, last);
     cudaError_t e = cudaSuccess;
     auto launch = [g, parity](int l) {
         return [g, parity, l](cudaStream_t st) {
@@ -1199,6 +1272,59 @@ int setup_step_kernel(fdtd_grid *g)
         if (occ < 1) return fail(g, FDTD_ECUDA, "step kernel does not fit on an SM");
         L.grid = std::max(1, std::min(sms * occ, L.nitems));
     }
+    g->sms = sms;
+    return FDTD_OK;
+}
+
+// the watchdog's check of the current state, queued on s
+cudaError_t enqueue_watch(fdtd_grid *g, cudaStream_t s)
+{
+    fdtd::FieldPtrs f{};
+    for (int c = 0; c < 6; ++c) f.p[c] = g->F[g->parity][c];
+    return fdtd::launch_finite_check(f, (long long)g->plane * g->nz, g->div_d, 4 * std::max(g->sms, 1), s);
+}
+
+// n steps: 32-step graph replays (captured once) while the parity allows,
+// direct launches otherwise; the watchdog's check after every replay or step
+// that crosses a multiple of its period
+int step_queue(fdtd_grid *g, int n)
+{
+    while (n > 0) {
+        const long before = g->step;
+        if (g->parity == 0 && n >= kGraphSteps) {
+            if (!g->graph) {
+                nvtxRangePushA("fdtd_step graph capture");
+                cudaError_t e = cudaSuccess;
+                if (!g->cap_stream) e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
+                cudaGraph_t graph = nullptr;
+                if (e == cudaSuccess) e = cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    for (int t = 0; t < kGraphSteps && e == cudaSuccess; ++t)
+                        e = enqueue_step(g, t & 1, g->cap_stream, t, t == kGraphSteps - 1);
+                    cudaError_t e2 = cudaStreamEndCapture(g->cap_stream, &graph);
+                    if (e == cudaSuccess) e = e2;
+                }
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&g->graph, graph, 0);
+                if (graph) cudaGraphDestroy(graph);
+                nvtxRangePop();
+                if (e != cudaSuccess) { g->graph = nullptr; return cuda_fail(g, e, "graph capture"); }
+            }
+            cudaError_t e = cudaGraphLaunch(g->graph, g->stream);
+            if (e != cudaSuccess) return cuda_fail(g, e, "graph launch");
+            n -= kGraphSteps;
+            g->step += kGraphSteps;
+        } else {
+            cudaError_t e = enqueue_step(g, g->parity, g->stream);
+            if (e != cudaSuccess) return cuda_fail(g, e, "step launch");
+            g->parity ^= 1;
+            n -= 1;
+            g->step += 1;
+        }
+        if (g->watch > 0 && g->step / g->watch != before / g->watch) {
+            cudaError_t e = enqueue_watch(g, g->stream);
+            if (e != cudaSuccess) return cuda_fail(g, e, "watchdog launch");
+        }
+    }
     return FDTD_OK;
 }
 
@@ -1217,19 +1343,20 @@ namespace fdtd {
 int set_error(fdtd_grid *g, int code, const char *msg) { return fail(g, code, msg); }
 
 // n steps by direct launches, with the step kernel's work counters (two per
-// launch) and its error flag taken from `scratch` (scratch_ints ints) instead
-// of the grid's arena; nothing is allocated.  The counters are cleared on the
-// grid's stream first; the error flag is left for fdtd_synchronize().
+// launch, scratch[0 .. 2 * launches)) and its error flag (the last int,
+// scratch[scratch_ints - 1], the same slot for every grid) taken from
+// `scratch` instead of the grid's arena; nothing is allocated.  The counters
+// are cleared on the grid's stream first; the error flag is left for
+// fdtd_synchronize(), which reads and clears it.
 int step_with_scratch(fdtd_grid *g, int n, int *scratch, int scratch_ints)
 {
     if (int rc = check_open(g, true)) return rc;
     if (n < 0) return fail(g, FDTD_EINVAL, "negative step count");
-    const int need = 2 * g->n_launch + 1;
-    if (need > scratch_ints)
+    if (2 * g->n_launch > scratch_ints - 1)
         return fail(g, FDTD_EINVAL, "the step needs more scratch than the static array holds");
     cudaError_t e = cudaMemsetAsync(scratch, 0, 2 * g->n_launch * sizeof(int), g->stream);
     if (e != cudaSuccess) return cuda_fail(g, e, "scratch clear");
-    g->noalloc_err = scratch + 2 * g->n_launch;
+    g->noalloc_err = scratch + (scratch_ints - 1);
     for (; n > 0; --n) {
         if (!g->osegs.empty()) e = launch_wire_gather(edge_args(g, g->parity), g->stream);
         for (int l = 0; l < g->n_launch && e == cudaSuccess; ++l)
@@ -1615,6 +1742,14 @@ int fdtd_set_block(fdtd_grid *g, int planes)
     return FDTD_OK;
 }
 
+int fdtd_set_watchdog(fdtd_grid *g, int every)
+{
+    if (!g) return FDTD_EINVAL;
+    if (every < 0) return fail(g, FDTD_EINVAL, "negative watchdog period");
+    g->watch = every;
+    return FDTD_OK;
+}
+
 int fdtd_arena_bytes(const fdtd_grid *g, int probe_capacity, size_t *bytes)
 {
     if (!g || !bytes || probe_capacity < 0) return FDTD_EINVAL;
@@ -1680,8 +1815,10 @@ int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_by
     g->step_d = (long long *)(base + p.step);
     g->work_d = (int *)(base + p.work);
     g->err_d = g->work_d + 4;
+    g->div_d = g->work_d + 5;
     g->slot_d = (fdtd::DomainSlot *)(base + p.slot);
     g->item_start_d = (int *)(base + p.items);
+    g->isrc_d = (int2 *)(base + p.isrc);
     g->J = (float *)(base + p.J);
     g->dcls_d = (uint8_t *)(base + p.dcls);
     g->dtable_d = (float *)(base + p.dtable);
@@ -1766,7 +1903,32 @@ int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_by
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(g, e, "upload");
     if (int rc = setup_step_kernel(g)) return rc;
-    if ((g->n_launch == 2 || !g->osegs.empty()) && !g->fk.side) {
+    // current sources in the step kernel: each source's launch and work item
+    g->fast = g->npoles == 0 && g->osegs.empty() && g->srcs.size() <= 32 && has_edge_work(g);
+    for (const Source &src : g->srcs) g->fast = g->fast && !src.hard;
+    if (g->fast && !g->srcs.empty()) {
+        using namespace fdtd::geom;
+        std::vector<int2> loc;
+        for (const Source &src : g->srcs) {
+            const int i = src.p[0], j = src.p[1], k = src.p[2];
+            const int col = (j / TY) * g->ncx + i / TX;
+            int2 at{-1, -1};
+            for (int l = 0; l < g->n_launch; ++l) {
+                const auto &L = g->lc[l];
+                const int nzb1 = (L.zhi - L.zlo + L.kz - 1) / L.kz;
+                int zb = -1;
+                if (k >= L.zlo && k < L.zhi) zb = (k - L.zlo) / L.kz;
+                else if (k >= L.zlo2 && k < L.zhi2) zb = nzb1 + (k - L.zlo2) / L.kz;
+                if (zb >= 0) at = int2{l, zb * g->ncx * g->ncy + col};
+            }
+            if (at.x < 0) return fail(g, FDTD_EINVAL, "a source edge lies outside every step launch");
+            loc.push_back(at);
+        }
+        e = cudaMemcpyAsync(g->isrc_d, loc.data(), loc.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(g, e, "upload of the source locations");
+    }
+    if ((g->n_launch == 2 || !g->osegs.empty() || (g->fast && !g->probes.empty())) && !g->fk.side) {
         e = g->fk.init();
         if (e != cudaSuccess) return cuda_fail(g, e, "side stream");
     }
@@ -1792,35 +1954,10 @@ int fdtd_step(fdtd_grid *g, int n)
 {
     if (int rc = check_open(g, true)) return rc;
     if (n < 0) return fail(g, FDTD_EINVAL, "negative step count");
-    while (n > 0) {
-        if (g->parity == 0 && n >= kGraphSteps) {
-            if (!g->graph) {
-                cudaError_t e = cudaSuccess;
-                if (!g->cap_stream) e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
-                cudaGraph_t graph = nullptr;
-                if (e == cudaSuccess) e = cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal);
-                if (e == cudaSuccess) {
-                    for (int t = 0; t < kGraphSteps && e == cudaSuccess; ++t) e = enqueue_step(g, t & 1, g->cap_stream);
-                    cudaError_t e2 = cudaStreamEndCapture(g->cap_stream, &graph);
-                    if (e == cudaSuccess) e = e2;
-                }
-                if (e == cudaSuccess) e = cudaGraphInstantiate(&g->graph, graph, 0);
-                if (graph) cudaGraphDestroy(graph);
-                if (e != cudaSuccess) { g->graph = nullptr; return cuda_fail(g, e, "graph capture"); }
-            }
-            cudaError_t e = cudaGraphLaunch(g->graph, g->stream);
-            if (e != cudaSuccess) return cuda_fail(g, e, "graph launch");
-            n -= kGraphSteps;
-            g->step += kGraphSteps;
-        } else {
-            cudaError_t e = enqueue_step(g, g->parity, g->stream);
-            if (e != cudaSuccess) return cuda_fail(g, e, "step launch");
-            g->parity ^= 1;
-            n -= 1;
-            g->step += 1;
-        }
-    }
-    return FDTD_OK;
+    nvtxRangePushA("fdtd_step");
+    const int rc = step_queue(g, n);
+    nvtxRangePop();
+    return rc;
 }
 
 int fdtd_synchronize(fdtd_grid *g)
@@ -1833,11 +1970,25 @@ int fdtd_synchronize(fdtd_grid *g)
         e = cudaMemcpy(&flag, g->err_d, sizeof flag, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(g, e, "error flag read");
         if (flag) return fail(g, FDTD_ETIMEOUT, "a bounded wait in the step kernel gave up");
+        e = cudaMemcpy(&flag, g->div_d, sizeof flag, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(g, e, "watchdog flag read");
+        if (flag) {
+            // reported once per detection; a later check finds it again if the fields still diverge
+            e = cudaMemsetAsync(g->div_d, 0, sizeof flag, g->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+            if (e != cudaSuccess) return cuda_fail(g, e, "watchdog flag clear");
+            return fail(g, FDTD_EDIVERGED, "the watchdog found a NaN or an infinity in the fields");
+        }
         if (g->noalloc_err) {
-            e = cudaMemcpy(&flag, g->noalloc_err, sizeof flag, cudaMemcpyDeviceToHost);
+            // the shared flag of fdtd_step_noalloc(): read and cleared on this
+            // grid's stream (it never holds a work counter)
+            e = cudaMemcpyAsync(&flag, g->noalloc_err, sizeof flag, cudaMemcpyDeviceToHost, g->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
             if (e != cudaSuccess) return cuda_fail(g, e, "error flag read");
             if (flag) {
-                cudaMemset(g->noalloc_err, 0, sizeof flag);
+                e = cudaMemsetAsync(g->noalloc_err, 0, sizeof flag, g->stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+                if (e != cudaSuccess) return cuda_fail(g, e, "error flag clear");
                 return fail(g, FDTD_ETIMEOUT, "a bounded wait in the step kernel gave up (fdtd_step_noalloc)");
             }
         }
@@ -2104,6 +2255,49 @@ cudaError_t batch_enqueue(fdtd_batch *b, int parity, cudaStream_t s)
     return e;
 }
 
+// n batch steps: graph replays while the parity allows, direct launches otherwise
+int batch_queue(fdtd_batch *b, int n)
+{
+    const int n0 = n;
+    while (n > 0) {
+        if (b->parity == 0 && n >= kGraphSteps) {
+            if (!b->graph) {
+                nvtxRangePushA("fdtd_batch_step graph capture");
+                cudaError_t e = cudaSuccess;
+                if (!b->cap) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+                cudaGraph_t graph = nullptr;
+                if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    for (int t = 0; t < kGraphSteps && e == cudaSuccess; ++t) e = batch_enqueue(b, t & 1, b->cap);
+                    cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+                    if (e == cudaSuccess) e = e2;
+                }
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, graph, 0);
+                if (graph) cudaGraphDestroy(graph);
+                nvtxRangePop();
+                if (e != cudaSuccess) {
+                    b->graph = nullptr;
+                    return bfail(b, FDTD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+                }
+            }
+            cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+            if (e != cudaSuccess) return bfail(b, FDTD_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+            n -= kGraphSteps;
+        } else {
+            cudaError_t e = batch_enqueue(b, b->parity, b->stream);
+            if (e != cudaSuccess) return bfail(b, FDTD_ECUDA, std::string("step launch: ") + cudaGetErrorString(e));
+            b->parity ^= 1;
+            n -= 1;
+        }
+    }
+    b->step += n0;
+    for (fdtd_grid *g : b->grids) {
+        g->parity = b->parity;
+        g->step = b->step;
+    }
+    return FDTD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -2207,42 +2401,10 @@ int fdtd_batch_step(fdtd_batch *b, int n)
 {
     if (!b) return FDTD_EINVAL;
     if (n < 0) return bfail(b, FDTD_EINVAL, "negative step count");
-    const int n0 = n;
-    while (n > 0) {
-        if (b->parity == 0 && n >= kGraphSteps) {
-            if (!b->graph) {
-                cudaError_t e = cudaSuccess;
-                if (!b->cap) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
-                cudaGraph_t graph = nullptr;
-                if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
-                if (e == cudaSuccess) {
-                    for (int t = 0; t < kGraphSteps && e == cudaSuccess; ++t) e = batch_enqueue(b, t & 1, b->cap);
-                    cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
-                    if (e == cudaSuccess) e = e2;
-                }
-                if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, graph, 0);
-                if (graph) cudaGraphDestroy(graph);
-                if (e != cudaSuccess) {
-                    b->graph = nullptr;
-                    return bfail(b, FDTD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-                }
-            }
-            cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
-            if (e != cudaSuccess) return bfail(b, FDTD_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
-            n -= kGraphSteps;
-        } else {
-            cudaError_t e = batch_enqueue(b, b->parity, b->stream);
-            if (e != cudaSuccess) return bfail(b, FDTD_ECUDA, std::string("step launch: ") + cudaGetErrorString(e));
-            b->parity ^= 1;
-            n -= 1;
-        }
-    }
-    b->step += n0;
-    for (fdtd_grid *g : b->grids) {
-        g->parity = b->parity;
-        g->step = b->step;
-    }
-    return FDTD_OK;
+    nvtxRangePushA("fdtd_batch_step");
+    const int rc = batch_queue(b, n);
+    nvtxRangePop();
+    return rc;
 }
 
 int fdtd_batch_synchronize(fdtd_batch *b)

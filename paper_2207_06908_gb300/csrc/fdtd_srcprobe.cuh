@@ -30,7 +30,8 @@ __device__ __forceinline__ void src_probe_body(const EdgeArgs &a, long long n)
     if (t < a.n_probes) pd0 = a.probes[t];
     float I0 = 0.f;
     if (t < a.n_src && n < sd0.n_samples) I0 = __ldg(a.samples + sd0.sample_off + n);
-    for (int q = t; q < a.n_src; q += blockDim.x) {
+    const int n_cur = a.skip_src ? 0 : a.n_src;     // current sources already applied by the step kernel
+    for (int q = t; q < n_cur; q += blockDim.x) {
         const SourceDesc sd = q == t ? sd0 : a.src[q];
         if (sd.hard) continue;
         const float I = q == t ? I0 : (n < sd.n_samples ? __ldg(a.samples + sd.sample_off + n) : 0.f);
@@ -96,7 +97,7 @@ __device__ __forceinline__ void src_probe_body(const EdgeArgs &a, long long n)
         }
     }
     __syncthreads();
-    if (t == 0) *a.step = n + 1;
+    if (t == 0 && a.advance) *a.step = n + 1;
 }
 
 }  // namespace

@@ -328,6 +328,36 @@ __device__ __forceinline__ void e_core(const StepArgs &a, const float4 *t, const
     ez1 = ca.z * ez + cb.z * (ez_x - ez_y);
 }
 
+// Current sources of the grid whose edges lie in a finished work item (Sec.
+// 2.1, J = I / dx^2 on one edge, I at t_{n+1/2}): E^{n+1} += coef I on each
+// edge, rounded as a separate product and sum (the arithmetic of the source
+// kernel's add to the stored E).  The item's consumers stored those E^{n+1}
+// before the barrier that precedes this; no other CTA touches them in this
+// step.  m: bit q set for each source q in the item.
+__device__ __forceinline__ void add_sources(const StepArgs &a, uint32_t m)
+{
+    const long long n = __ldcg(a.step) + a.step_t;
+    while (m) {
+        const int q = __ffs(m) - 1;
+        m &= m - 1;
+        const SourceDesc &sd = a.src[q];
+        const float I = n < sd.n_samples ? __ldg(a.samples + sd.sample_off + n) : 0.f;
+        float *e = a.Eout[sd.comp] + sd.idx;
+        *e = __fadd_rn(__ldcg(e), __fmul_rn(sd.coef, I));
+    }
+}
+
+// sources that lie in work item `item` of launch `launch` (bit q: source q)
+__device__ __forceinline__ uint32_t item_sources(const StepArgs &a, int launch, int item)
+{
+    uint32_t m = 0;
+    for (int q = 0; q < a.n_isrc; ++q) {
+        const int2 L = __ldg(a.isrc_loc + q);
+        if (L.x == launch && L.y == item) m |= 1u << q;
+    }
+    return m;
+}
+
 // ---- shared-memory views ----------------------------------------------------
 struct EView {
     char *p;
@@ -840,6 +870,14 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
             const bool done = item_in_cpml(a, it) ? run_item<true, NH>(C, it, ce, ch, hb)
                                                   : run_item<false, NH>(C, it, ce, ch, hb);
             if (!done) break;
+            if (!BATCH && a.n_isrc > 0) {
+                // current sources on the item's edges, after all its E stores
+                const uint32_t m = item_sources(a, B.launch, item);
+                if (m) {
+                    consumer_sync();
+                    if (tid == 0) add_sources(a, m);
+                }
+            }
             ce += (uint32_t)(it.kb - it.ka) + 2;
             ch += (uint32_t)(it.kb - it.ka) + 1;
         }

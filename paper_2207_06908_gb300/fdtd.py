@@ -203,6 +203,12 @@ class Grid:
         """planes per work item of the step kernel (tuning; 0 = default)"""
         check(self._lib, self._h, self._lib.fdtd_set_block(self._h, int(planes)), "set_block")
 
+    def set_watchdog(self, every):
+        """divergence watchdog period in steps (0 = off): synchronising
+        calls raise FdtdError(FDTD_EDIVERGED) after a check that found a NaN
+        or an infinity"""
+        check(self._lib, self._h, self._lib.fdtd_set_watchdog(self._h, int(every)), "set_watchdog")
+
     def arena_bytes(self, probe_capacity):
         b = ctypes.c_size_t()
         check(self._lib, self._h, self._lib.fdtd_arena_bytes(self._h, int(probe_capacity), ctypes.byref(b)),

@@ -41,3 +41,41 @@ def test_bounded_wait_times_out_and_context_survives(fdtd):
     g.synchronize()
     assert all(np.isfinite(g.get_field(c)).all() for c in range(6))
     g.close()
+
+
+def test_watchdog_reports_divergence_within_its_period(fdtd):
+    """a NaN written into one field from the host (no fault: an ordinary
+    upload) is found by the watchdog's next check; the synchronising call
+    returns FDTD_EDIVERGED once, within one period, and a clean grid beside
+    it with the same period reports nothing"""
+    from paper_2207_06908_gb300._lib import FdtdError
+    sc = W.random_scenario(5, n=(24, 17, 20), cpml=3, n_steps=128)
+    bad = fdtd.from_scenario(sc, probe_capacity=128)
+    good = fdtd.from_scenario(sc, probe_capacity=128)
+    for g in (bad, good):
+        g.set_watchdog(32)
+        for c, f in enumerate(sc.fields):
+            g.set_field(c, f)
+    # 40 clean steps: one check at step 32, nothing to report
+    bad.step(40)
+    bad.synchronize()
+    ez = bad.get_field(2)
+    ez[10, 8, 12] = np.nan
+    bad.set_field(2, ez)
+    # steps 40 .. 63: the next check (step 64) has not run yet
+    bad.step(23)
+    bad.synchronize()
+    bad.step(1)                             # reaches 64: the check runs after this step
+    with pytest.raises(FdtdError) as ei:
+        bad.synchronize()
+    assert ei.value.code == -7              # FDTD_EDIVERGED
+    bad.synchronize()                       # reported once per detection
+    good.step(128)
+    good.synchronize()
+    assert all(np.isfinite(good.get_field(c)).all() for c in range(6))
+    # off: no report
+    bad.set_watchdog(0)
+    bad.step(64)
+    bad.synchronize()
+    bad.close()
+    good.close()
