@@ -102,6 +102,7 @@ struct StepArgs {
     int region;              // bytes of the staged-auxiliary region this domain needs
     int ox, oy;              // byte offsets of the x and y box groups in that region
     int zxy;                 // 1: stage the z layer together with x / y
+    const int *col_order;    // [ncx * ncy] column tile of each position in a z block (costliest first)
     // current sources applied in the E update of the items that own their
     // edges (single-grid steps only; n_isrc = 0: the source/probe kernel
     // applies them): source q lies in launch isrc_loc[q].x, item .y

@@ -139,6 +139,8 @@ struct fdtd_grid {
     fdtd::DomainSlot *slot_d = nullptr;   // this grid as a one-domain step launch
     int *item_start_d = nullptr;          // [launch][2]: {0, items}
     int2 *isrc_d = nullptr;               // per current source: {launch, work item} of its edge
+    int *order_d = nullptr;               // column tiles in the order a z block hands them out
+    std::vector<int> order_pos;           // position of each column tile in that order
     // single-grid steps apply the current sources in the step kernel and read
     // the probes of step n beside step n + 1 (no Debye media, no oblique
     // wires, no ideal voltage sources, at most 32 sources)
@@ -203,6 +205,7 @@ int cuda_fail(fdtd_grid *g, cudaError_t e, const char *what)
 // ---- device arena plan -------------------------------------------------
 struct Plan {
     size_t field, cls, table, prof[3], psi[fdtd::PSI_COUNT], src, samples, probes, out, step, work, slot, items, isrc,
+        order,
         J, dcls, dtable, oseg, ochunk, oedge, oscat, oterm, onode, oadj, oI, oQ, oV, oP, osrc, osamp, total;
 };
 
@@ -263,6 +266,9 @@ Plan make_plan(const fdtd_grid *g, int capacity)
     p.slot = take(sizeof(fdtd::DomainSlot));
     p.items = take(4 * sizeof(int));
     p.isrc = take(std::max<size_t>(1, g->srcs.size()) * sizeof(int2));
+    const size_t ncols = (size_t)((g->nx + fdtd::geom::TX - 1) / fdtd::geom::TX) *
+                         ((g->ny + fdtd::geom::TY - 1) / fdtd::geom::TY);
+    p.order = take(ncols * sizeof(int));
     int z0, z1;
     const int P = debye_extent(g, &z0, &z1);
     const size_t box = (size_t)(z1 - z0) * g->plane;
@@ -962,6 +968,7 @@ fdtd::StepArgs step_args(const fdtd_grid *g, int parity, int launch)
     a.ox = L.ox;
     a.oy = L.oy;
     a.zxy = L.zxy;
+    a.col_order = g->order_d;
     return a;
 }
 
@@ -1819,6 +1826,7 @@ int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_by
     g->slot_d = (fdtd::DomainSlot *)(base + p.slot);
     g->item_start_d = (int *)(base + p.items);
     g->isrc_d = (int2 *)(base + p.isrc);
+    g->order_d = (int *)(base + p.order);
     g->J = (float *)(base + p.J);
     g->dcls_d = (uint8_t *)(base + p.dcls);
     g->dtable_d = (float *)(base + p.dtable);
@@ -1903,6 +1911,26 @@ int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_by
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(g, e, "upload");
     if (int rc = setup_step_kernel(g)) return rc;
+    {
+        // column tiles of a z block, costliest first: those meeting an x and a
+        // y layer, then one layer, then none (in tile order within each class)
+        using namespace fdtd::geom;
+        std::vector<int> order, cost;
+        for (int cy = 0; cy < g->ncy; ++cy)
+            for (int cx = 0; cx < g->ncx; ++cx) {
+                const int x0 = cx * TX, y0 = cy * TY, d = g->d;
+                const bool tx = d > 0 && (std::max(x0 - 1, 0) < d || std::min(x0 + TX, g->nx) - 1 >= g->nx - d);
+                const bool ty = d > 0 && (std::max(y0 - 1, 0) < d || std::min(y0 + TY, g->ny) - 1 >= g->ny - d);
+                order.push_back(cy * g->ncx + cx);
+                cost.push_back((int)tx + (int)ty);
+            }
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+        g->order_pos.assign(order.size(), 0);
+        for (size_t q = 0; q < order.size(); ++q) g->order_pos[order[q]] = (int)q;
+        e = cudaMemcpyAsync(g->order_d, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(g, e, "upload of the column order");
+    }
     // current sources in the step kernel: each source's launch and work item
     g->fast = g->npoles == 0 && g->osegs.empty() && g->srcs.size() <= 32 && has_edge_work(g);
     for (const Source &src : g->srcs) g->fast = g->fast && !src.hard;
@@ -1911,7 +1939,7 @@ int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_by
         std::vector<int2> loc;
         for (const Source &src : g->srcs) {
             const int i = src.p[0], j = src.p[1], k = src.p[2];
-            const int col = (j / TY) * g->ncx + i / TX;
+            const int col = g->order_pos[(j / TY) * g->ncx + i / TX];
             int2 at{-1, -1};
             for (int l = 0; l < g->n_launch; ++l) {
                 const auto &L = g->lc[l];

@@ -8,6 +8,8 @@
 //     order, handed out by an atomic counter to a persistent grid of
 //     (SMs x resident CTAs); all CTAs march near the same z, so the halo
 //     planes one CTA loads are still in L2 when its neighbours load them.
+//     Within a z block the column tiles that meet a CPML layer come first:
+//     the last items of a launch are the quick ones.
 //   - One producer warp streams, plane by plane, TMA 3D boxes into two
 //     shared-memory rings tracked by mbarriers: E^n (tile + 1-cell halo on
 //     every side, x start rounded down to a 16-byte boundary) into a
@@ -443,7 +445,11 @@ struct Item {
 __device__ __forceinline__ Item decode(const StepArgs &a, int item)
 {
     const int ncols = a.ncx * a.ncy;
-    const int zb = item / ncols, col = item - zb * ncols;
+    const int zb = item / ncols;
+    // within a z block the column tiles that meet a CPML layer (the slowest
+    // items) come first, so the items handed out last in a launch are the
+    // quickest and the launch's tail is short
+    const int col = __ldg(a.col_order + (item - zb * ncols));
     Item it;
     it.x0 = (col % a.ncx) * TX;
     it.y0 = (col / a.ncx) * TY;
