@@ -1,14 +1,17 @@
 // fdtd_mlp.cu -- surrogate-network kernels (BF16 operands, FP32 accumulate).
 //
-// Forward layers (x wt^T + bias, GELU) run on the fifth-generation tensor
-// cores: one CTA per 128 x 128 output tile stages the whole K extent of
-// both operands in shared memory (no-swizzle K-major core-matrix layout),
-// one thread issues the tcgen05.mma chain into a TMEM accumulator, and the
-// four warps read it back with tcgen05.ld for the bias / GELU epilogue.
-// The gradients (dz wt and dz^T x, whose operands are not K-major in
-// memory) use a tiled mma.sync m16n8k16 GEMM that addresses its operands
-// through element strides.  Small element-wise kernels form
-// dz = dy * act'(z), the bias gradient, the losses and the Adam update.
+// Every contraction runs on the fifth-generation tensor cores
+// (tcgen05.mma, BF16 x BF16 -> FP32 in TMEM).  Forward layers (x wt^T +
+// bias, GELU) with k <= 256: one CTA per 128 x 64 output tile stages the
+// whole K extent of both operands in shared memory (no-swizzle K-major
+// core-matrix layout), one thread issues the MMA chain into a TMEM
+// accumulator, and the eight warps read it back with tcgen05.ld for the
+// bias / GELU epilogue.  The gradients (dz wt and dz^T x, whose operands
+// are not K-major in memory) and forward layers with larger k use the same
+// tile and epilogue with the reduction in chunks, each chunk staged through
+// registers from operands addressed by element strides.  Small element-wise
+// kernels form dz = dy * act'(z), the bias gradient, the losses and the Adam
+// update.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -20,9 +23,6 @@
 #include "fdtd_mlp.h"
 
 namespace {
-
-constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
-constexpr int GT = 128;                       // 4 warps, 2 x 2, each 32 x 32
 
 template <typename T>
 __device__ __forceinline__ __nv_bfloat16 to_bf16(T v);
@@ -46,86 +46,6 @@ struct Epi {
     float *zf;
     int ldc;
 };
-
-// C[M x N] = A[M x K] B[K x N] with A(m,k) = A[m*sam + k*sak],
-// B(k,n) = B[k*sbk + n*sbn]
-template <typename TA, typename TB>
-__global__ void __launch_bounds__(GT) gemm_kernel(const TA *__restrict__ A, long long sam, long long sak,
-                                                  const TB *__restrict__ B, long long sbk, long long sbn, int M,
-                                                  int N, int K, Epi ep)
-{
-    __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PAD];
-    __shared__ __align__(16) __nv_bfloat16 Bs[BN][BK + PAD];   // n-major: k contiguous
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g = lane >> 2, t = lane & 3;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    float acc[2][4][4];
-    for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 4; ++b)
-            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
-    const bool a_kfast = (sak == 1), b_kfast = (sbk == 1);
-    for (int k0 = 0; k0 < K; k0 += BK) {
-        for (int q = tid; q < BM * BK; q += GT) {
-            int i, j;
-            if (a_kfast) { i = q / BK; j = q % BK; }
-            else { j = q / BM; i = q % BM; }
-            const int m = m0 + i, k = k0 + j;
-            As[i][j] = (m < M && k < K) ? to_bf16(A[m * sam + k * sak]) : __float2bfloat16_rn(0.f);
-        }
-        for (int q = tid; q < BN * BK; q += GT) {
-            int jj, j;
-            if (b_kfast) { jj = q / BK; j = q % BK; }
-            else { j = q / BN; jj = q % BN; }
-            const int n = n0 + jj, k = k0 + j;
-            Bs[jj][j] = (n < N && k < K) ? to_bf16(B[k * sbk + n * sbn]) : __float2bfloat16_rn(0.f);
-        }
-        __syncthreads();
-        for (int kk = 0; kk < BK; kk += 16) {
-            uint32_t af[2][4], bf[4][2];
-            for (int mi = 0; mi < 2; ++mi) {
-                const int r = wm + mi * 16 + g, c = kk + 2 * t;
-                af[mi][0] = *reinterpret_cast<const uint32_t *>(&As[r][c]);
-                af[mi][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][c]);
-                af[mi][2] = *reinterpret_cast<const uint32_t *>(&As[r][c + 8]);
-                af[mi][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][c + 8]);
-            }
-            for (int ni = 0; ni < 4; ++ni) {
-                const int n = wn + ni * 8 + g, c = kk + 2 * t;
-                bf[ni][0] = *reinterpret_cast<const uint32_t *>(&Bs[n][c]);
-                bf[ni][1] = *reinterpret_cast<const uint32_t *>(&Bs[n][c + 8]);
-            }
-            for (int mi = 0; mi < 2; ++mi)
-                for (int ni = 0; ni < 4; ++ni)
-                    asm volatile(
-                        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-                        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-                        : "+f"(acc[mi][ni][0]), "+f"(acc[mi][ni][1]), "+f"(acc[mi][ni][2]), "+f"(acc[mi][ni][3])
-                        : "r"(af[mi][0]), "r"(af[mi][1]), "r"(af[mi][2]), "r"(af[mi][3]), "r"(bf[ni][0]),
-                          "r"(bf[ni][1]));
-        }
-        __syncthreads();
-    }
-    for (int mi = 0; mi < 2; ++mi)
-        for (int ni = 0; ni < 4; ++ni)
-            for (int h = 0; h < 2; ++h)
-                for (int e = 0; e < 2; ++e) {
-                    const int m = m0 + wm + mi * 16 + g + 8 * h;
-                    const int n = n0 + wn + ni * 8 + 2 * t + e;
-                    if (m >= M || n >= N) continue;
-                    const float v = acc[mi][ni][2 * h + e];
-                    const long long o = (long long)m * ep.ldc + n;
-                    if (ep.mode == 1) {
-                        ep.yf[o] = v;
-                    } else {
-                        const float z = v + (ep.bias ? ep.bias[n] : 0.f);
-                        const float y = ep.act == FDTD_ACT_GELU ? gelu(z) : z;
-                        if (ep.zf) ep.zf[o] = z;
-                        if (ep.yf) ep.yf[o] = y;
-                        if (ep.yb) ep.yb[o] = __float2bfloat16_rn(y);
-                    }
-                }
-}
 
 __global__ void act_grad_kernel(const float *__restrict__ dy, const float *__restrict__ z, float *__restrict__ dz,
                                 long long count, int act)
@@ -494,6 +414,169 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     }
 }
 
+// ---- tcgen05 gradient GEMM ---------------------------------------------------
+// C[M x N] (FP32, row pitch N) = sum_k A(m, k) B(k, n) with
+// A(m, k) = A[m sam + k sak] and B(k, n) = B[k sbk + n sbn], FP32 or BF16
+// operands with any element strides (the gradients dz^T x and dz wt read
+// their operands transposed).  One CTA per 128 x 64 output tile; the
+// reduction runs in chunks of GC_K: all threads stage a chunk of both
+// operands into the K-major core-matrix layout (rounded to BF16 in
+// registers; threads walk the operand's contiguous index so the loads
+// coalesce), one thread issues its MMA chain into the TMEM accumulator and
+// commits it to an mbarrier, and every thread waits (bounded) before the
+// next chunk overwrites the tiles.  The epilogue is the forward layer's.
+constexpr int GC_K = 128;
+constexpr int GC_SMEM = 1024 + 1024 + (TC_M + TC_N) * GC_K * 2;
+
+template <typename T>
+__device__ __forceinline__ float elem(const T *p)
+{
+    if constexpr (sizeof(T) == 2) return __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(p));
+    else return *reinterpret_cast<const float *>(p);
+}
+
+// rows r0 .. r0 + R - 1 (row index fast in memory when s_row == 1) and
+// reduction indices k0 .. k0 + GC_K - 1 of X(row, k) = X[row s_row + k s_k]
+// (zero outside rows x K) into the core-matrix layout of a GC_K chunk:
+// 8 elements of one row at (r / 8) (GC_K 16) + (k / 8) 128 + (r % 8) 16
+template <typename T>
+__device__ __forceinline__ void stage_strided(char *dst, const T *X, long long s_row, long long s_k, int rows,
+                                              int K, int r0, int R, int k0, int tid)
+{
+    constexpr int kgs = GC_K / 8;
+    for (int q = tid; q < R * kgs; q += TC_THREADS) {
+        int r, g;
+        if (s_row == 1) { r = q % R; g = q / R; }
+        else { r = q / kgs; g = q % kgs; }
+        const int row = r0 + r, k = k0 + g * 8;
+        float f[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            f[j] = (row < rows && k + j < K) ? elem(X + row * s_row + (long long)(k + j) * s_k) : 0.f;
+        *reinterpret_cast<uint4 *>(dst + (r >> 3) * (GC_K * 16) + g * 128 + (r & 7) * 16) =
+            make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
+    }
+}
+
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(TC_THREADS, 2)
+    tc_grad_kernel(const TA *__restrict__ A, long long sam, long long sak, const TB *__restrict__ B, long long sbk,
+                   long long sbn, int M, int N, int K, Epi ep)
+{
+    extern __shared__ __align__(1024) char smraw[];
+    char *sm = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + 8);
+    char *As = sm + 1024;
+    char *Bs = As + TC_M * GC_K * 2;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * TC_N;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(TC_N));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 32) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    const uint32_t sbo = GC_K * 16;
+    bool ok = true;
+    const int nchunk = (K + GC_K - 1) / GC_K;
+    for (int c = 0; c < nchunk && ok; ++c) {
+        const int k0 = c * GC_K;
+        // A rows are m, B rows are n (B(k, n) read as row n of B^T)
+        stage_strided(As, A, sam, sak, M, K, m0, TC_M, k0, tid);
+        stage_strided(Bs, B, sbn, sbk, N, K, n0, TC_N, k0, tid);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+            for (int kk = 0; kk < GC_K; kk += 16) {
+                const uint64_t ad = smem_desc(a0 + kk * 16, 128, sbo), bd = smem_desc(b0 + kk * 16, 128, sbo);
+                const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(bar))
+                         : "memory");
+        }
+        // the tiles are free again (and, after the last chunk, the accumulator complete)
+        bool done = mbar_wait_bounded(smem_u32(bar), (uint32_t)(c & 1));
+        ok = __syncthreads_and(done);
+        if (!ok) {
+            if (tid == 0) atomicExch(&g_mlp_err, 1);
+            mbar_wait_bounded(smem_u32(bar), (uint32_t)(c & 1));   // the chain still in flight, bounded again
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    if (ok) {
+        const int lg = warp & 3, cc = (warp >> 2) * 32;
+        float *T = reinterpret_cast<float *>(As) + warp * 32 * TC_TS;
+        const int mrow = m0 + lg * 32;
+        if (n0 + cc < N) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)cc, v);
+            if (ep.mode == 1) {
+                float y[32];
+                for (int j = 0; j < 32; ++j) y[j] = __uint_as_float(v[j]);
+                store_f32(T, y, ep.yf, mrow, M, n0 + cc, N, lane);
+            } else {
+                float z[32], y[32];
+                for (int j = 0; j < 32; ++j) {
+                    const int n = n0 + cc + j;
+                    z[j] = __uint_as_float(v[j]) + ((ep.bias && n < N) ? __ldg(ep.bias + n) : 0.f);
+                    y[j] = ep.act == FDTD_ACT_GELU ? gelu(z[j]) : z[j];
+                }
+                if (ep.zf) store_f32(T, z, ep.zf, mrow, M, n0 + cc, N, lane);
+                if (ep.yf) store_f32(T, y, ep.yf, mrow, M, n0 + cc, N, lane);
+                if (ep.yb) store_bf16(T, y, ep.yb, mrow, M, n0 + cc, N, lane);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N) : "memory");
+    }
+}
+
+static_assert(TC_THREADS / 32 * 32 * TC_TS * 4 <= (TC_M + TC_N) * GC_K * 2, "transpose buffers fit the tile area");
+
+template <typename TA, typename TB>
+cudaError_t tc_grad(const TA *A, long long sam, long long sak, const TB *B, long long sbk, long long sbn, int M, int N,
+                    int K, const Epi &ep, cudaStream_t s)
+{
+    static std::mutex mu;
+    static bool ready[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 64) return cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!ready[dev]) {
+            e = cudaFuncSetAttribute(tc_grad_kernel<TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, GC_SMEM);
+            if (e != cudaSuccess) return e;
+            ready[dev] = true;
+        }
+    }
+    dim3 grid((M + TC_M - 1) / TC_M, (N + TC_N - 1) / TC_N);
+    tc_grad_kernel<TA, TB><<<grid, TC_THREADS, GC_SMEM, s>>>(A, sam, sak, B, sbk, sbn, M, N, K, ep);
+    return cudaGetLastError();
+}
+
 template <typename TA>
 cudaError_t tc_forward(const TA *x, int rows, int K, const __nv_bfloat16 *wt, const float *bias, int N, int act,
                        __nv_bfloat16 *yb, float *yf, float *zf, cudaStream_t s)
@@ -521,15 +604,6 @@ cudaError_t tc_forward(const TA *x, int rows, int K, const __nv_bfloat16 *wt, co
     return cudaGetLastError();
 }
 
-template <typename TA, typename TB>
-cudaError_t gemm(const TA *A, long long sam, long long sak, const TB *B, long long sbk, long long sbn, int M, int N,
-                 int K, const Epi &ep, cudaStream_t s)
-{
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
-    gemm_kernel<TA, TB><<<grid, GT, 0, s>>>(A, sam, sak, B, sbk, sbn, M, N, K, ep);
-    return cudaGetLastError();
-}
-
 int rc(cudaError_t e) { return e == cudaSuccess ? FDTD_OK : FDTD_ECUDA; }
 int grid1d(long long n) { return (int)std::min<long long>((n + 255) / 256, 4096); }
 
@@ -552,10 +626,10 @@ int fdtd_mlp_forward(const void *x, int x_is_bf16, int rows, int k, const void *
         return rc(tc_forward(static_cast<const float *>(x), rows, k, w, bias, n, act,
                              static_cast<__nv_bfloat16 *>(y_bf16), y_f32, z_f32, s));
     }
-    // B(k, n) = wt[n * k + k']
+    // larger k: the chunked tensor-core GEMM, B(k, n) = wt[n * k + k']
     if (x_is_bf16)
-        return rc(gemm(static_cast<const __nv_bfloat16 *>(x), k, 1, w, 1, k, rows, n, k, ep, s));
-    return rc(gemm(static_cast<const float *>(x), k, 1, w, 1, k, rows, n, k, ep, s));
+        return rc(tc_grad(static_cast<const __nv_bfloat16 *>(x), k, 1, w, 1, k, rows, n, k, ep, s));
+    return rc(tc_grad(static_cast<const float *>(x), k, 1, w, 1, k, rows, n, k, ep, s));
 }
 
 int fdtd_mlp_check(void *cuda_stream)
@@ -591,14 +665,14 @@ int fdtd_mlp_backward(const void *x, int x_is_bf16, const float *z, const float 
         // dw[n x k] = dz^T x: A(m=o, kk=r) = dz[r * n + o]; B(kk=r, c) = x[r * k + c]
         Epi ep{1, nullptr, 0, nullptr, dw, nullptr, k};
         if (x_is_bf16)
-            e = gemm(dz, 1, n, static_cast<const __nv_bfloat16 *>(x), k, 1, n, k, rows, ep, s);
+            e = tc_grad(dz, 1, n, static_cast<const __nv_bfloat16 *>(x), k, 1, n, k, rows, ep, s);
         else
-            e = gemm(dz, 1, n, static_cast<const float *>(x), k, 1, n, k, rows, ep, s);
+            e = tc_grad(dz, 1, n, static_cast<const float *>(x), k, 1, n, k, rows, ep, s);
     }
     if (e == cudaSuccess && dx) {
         // dx[rows x k] = dz wt: A(r, o) = dz[r * n + o]; B(o, c) = wt[o * k + c]
         Epi ep{1, nullptr, 0, nullptr, dx, nullptr, k};
-        e = gemm(dz, n, 1, static_cast<const __nv_bfloat16 *>(wt), k, 1, rows, k, n, ep, s);
+        e = tc_grad(dz, n, 1, static_cast<const __nv_bfloat16 *>(wt), k, 1, rows, k, n, ep, s);
     }
     return rc(e);
 }

@@ -1,5 +1,6 @@
-"""Surrogate-network kernels (BF16 operands, FP32 accumulation, mma.sync)
-against the FP64 oracle on the same BF16-rounded weights and inputs.
+"""Surrogate-network kernels (BF16 operands, FP32 accumulation, tcgen05
+tensor cores for every contraction) against the FP64 oracle on the same
+BF16-rounded weights and inputs.
 FP32 outputs of exact BF16 products: 1e-4 relative L2; outputs that pass
 through BF16 (stored activations, dz entering the weight / input gradient
 GEMMs): 1e-2."""
@@ -51,7 +52,8 @@ def test_forward_layer(env, rows, k, n, act):
     assert rel(yb.float().cpu().numpy(), y) <= 1e-2
 
 
-@pytest.mark.parametrize("rows,k,n,act", [(300, 70, 130, 1), (512, 256, 512, 0), (77, 6, 256, 1)])
+@pytest.mark.parametrize("rows,k,n,act", [(300, 70, 130, 1), (512, 256, 512, 0), (77, 6, 256, 1),
+                                          (1000, 256, 256, 1), (9, 33, 3, 0)])
 def test_backward_layer(env, rows, k, n, act):
     torch, mlp = env
     rng = np.random.default_rng(3 * rows + k)
