@@ -89,7 +89,10 @@ enum {
  * (Sec. 2.1) scaled by courant in (0, 1].  cpml may be NULL (PEC box).
  * cuda_stream: a cudaStream_t (NULL = the legacy default stream) on which
  * all device work of this grid is queued.  Every material starts as vacuum.
- * nx, ny, nz >= 2 (>= 2*cells + 2 with a CPML).  *out receives the handle. */
+ * nx, ny, nz >= 2 (>= 2*cells + 2 with a CPML).  With a CPML each of its
+ * compact auxiliary arrays (the layer cells of one axis) must stay below
+ * 2^31 elements (FDTD_EINVAL otherwise; about 10^4 cells per side for a
+ * 10-cell layer).  *out receives the handle. */
 int fdtd_create_grid(int nx, int ny, int nz, double dx, double courant,
                      const fdtd_cpml *cpml, void *cuda_stream, fdtd_grid **out);
 

@@ -14,9 +14,11 @@ namespace fdtd {
 constexpr int kNumCoef = 9;
 constexpr int kMaxClasses = 256;
 
-// Auxiliary CPML fields, one per (component, derivative axis), stored as
-// full arrays with the fields' pitch (only entries inside the layer of their
-// axis are ever read or written), so TMA boxes address them like the fields.
+// Auxiliary CPML fields, one per (component, derivative axis), stored
+// compactly: only the cells of their axis's two layers, indexed by the slab
+// entry (0 .. d-1 the low layer, d .. 2d-1 the high one) along that axis --
+// x [nz][ny][px] (px = 2d rounded up to a multiple of 4), y [nz][2d][pitch],
+// z [2d][ny][pitch] -- so TMA boxes address them like the fields.
 enum Psi {
     PSI_HY_X = 0, PSI_HZ_X, PSI_EY_X, PSI_EZ_X,
     PSI_HX_Y, PSI_HZ_Y, PSI_EX_Y, PSI_EZ_Y,
@@ -55,8 +57,8 @@ struct TmaMaps {
 
 // geometry of the staged CPML boxes (host-computed for the grid's layer)
 struct PsiGeom {
-    int w;                   // x-layer box width (cells, multiple of 4)
-    int hy;                  // y-layer box height (rows)
+    int w;                   // x-layer box width (slab entries, multiple of 4)
+    int hy;                  // y-layer box height (slab rows)
     int xb, yb;              // bytes of one x / y box slot (128-aligned)
 };
 
@@ -91,8 +93,9 @@ struct StepArgs {
     int n_classes;
     int d;                   // CPML cells (0 = none)
     const float *prof[3];    // per axis: PR_COUNT arrays of n_axis floats
-    const float *psi_in[PSI_COUNT];
+    const float *psi_in[PSI_COUNT];  // compact: x [nz][ny][px], y [nz][2d][pitch], z [2d][ny][pitch]
     float *psi_out[PSI_COUNT];
+    int px;                  // row pitch of the x-layer auxiliaries (2d rounded up to a multiple of 4)
     int kz;                  // planes per z block of a work item
     int zlo, zhi;            // planes of this launch: [zlo, zhi) and [zlo2, zhi2)
     int zlo2, zhi2;

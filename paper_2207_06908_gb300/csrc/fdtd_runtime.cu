@@ -238,9 +238,17 @@ int debye_extent(const fdtd_grid *g, int *z0, int *z1)
     return P;
 }
 
-size_t psi_elems(const fdtd_grid *g, int)
+// compact auxiliaries: only their axis's two layers (fdtd_internal.h)
+int psi_px(const fdtd_grid *g) { return (2 * g->d + 3) / 4 * 4; }
+size_t psi_elems(const fdtd_grid *g, int q)
 {
-    return g->d == 0 ? 0 : (size_t)g->plane * g->nz;
+    if (g->d == 0) return 0;
+    const size_t d2 = 2 * (size_t)g->d;
+    switch (q / 4) {
+    case 0: return (size_t)g->nz * g->ny * psi_px(g);
+    case 1: return (size_t)g->nz * d2 * g->pitch;
+    default: return d2 * (size_t)g->plane;
+    }
 }
 
 Plan make_plan(const fdtd_grid *g, int capacity)
@@ -954,6 +962,7 @@ fdtd::StepArgs step_args(const fdtd_grid *g, int parity, int launch)
         a.psi_in[q] = g->psi[parity][q];
         a.psi_out[q] = g->psi[1 - parity][q];
     }
+    a.px = psi_px(g);
     const auto &L = g->lc[launch];
     a.kz = L.kz;
     a.zlo = L.zlo;
@@ -1170,18 +1179,26 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-// 3D tiled map over one pitched array (x fastest); out-of-range box
+// 3D tiled map over one array of extent x0 x y0 x z0 with row pitch
+// `pitch` elements and y0 rows per plane (x fastest); out-of-range box
 // elements read as zero
-bool encode_map(CUtensorMap *m, void *base, CUtensorMapDataType dt, int esize, const fdtd_grid *g, int bx, int by)
+bool encode_map3(CUtensorMap *m, void *base, CUtensorMapDataType dt, int esize, int x0, int y0, int z0, int pitch,
+                 int bx, int by)
 {
     auto fn = encode_fn();
     if (!fn) return false;
-    cuuint64_t dims[3] = {(cuuint64_t)g->nx, (cuuint64_t)g->ny, (cuuint64_t)g->nz};
-    cuuint64_t strides[2] = {(cuuint64_t)g->pitch * esize, (cuuint64_t)g->plane * esize};
+    cuuint64_t dims[3] = {(cuuint64_t)x0, (cuuint64_t)y0, (cuuint64_t)z0};
+    cuuint64_t strides[2] = {(cuuint64_t)pitch * esize, (cuuint64_t)pitch * y0 * esize};
     cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
     cuuint32_t es[3] = {1, 1, 1};
     return fn(m, dt, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// 3D tiled map over one field-shaped array (the fields, the class bytes)
+bool encode_map(CUtensorMap *m, void *base, CUtensorMapDataType dt, int esize, const fdtd_grid *g, int bx, int by)
+{
+    return encode_map3(m, base, dt, esize, g->nx, g->ny, g->nz, g->pitch, bx, by);
 }
 
 // Raise (never lower) a step kernel's dynamic shared-memory limit: grids and
@@ -1217,6 +1234,8 @@ int setup_step_kernel(fdtd_grid *g)
             using namespace fdtd;
             const auto F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
             const int w = g->pg.w, hy = g->pg.hy;
+            // compact layouts: x [nz][ny][px], y [nz][2d][pitch], z [2d][ny][pitch]
+            const int px = psi_px(g), d2 = 2 * g->d;
             struct { CUtensorMap *m; int psi, bx, by; } maps[12] = {
                 {&g->maps[p].zh[0], PSI_HX_Z, HBX, HBY}, {&g->maps[p].zh[1], PSI_HY_Z, HBX, HBY},
                 {&g->maps[p].ze[0], PSI_EX_Z, TX, TY},   {&g->maps[p].ze[1], PSI_EY_Z, TX, TY},
@@ -1224,9 +1243,15 @@ int setup_step_kernel(fdtd_grid *g)
                 {&g->maps[p].xe[0], PSI_EY_X, w, HBY},   {&g->maps[p].xe[1], PSI_EZ_X, w, HBY},
                 {&g->maps[p].yh[0], PSI_HX_Y, HBX, hy},  {&g->maps[p].yh[1], PSI_HZ_Y, HBX, hy},
                 {&g->maps[p].ye[0], PSI_EX_Y, HBX, hy},  {&g->maps[p].ye[1], PSI_EZ_Y, HBX, hy}};
-            for (auto &mm : maps)
-                if (!encode_map(mm.m, g->psi[p][mm.psi], F32, 4, g, mm.bx, mm.by))
-                    return fail(g, FDTD_ECUDA, "cuTensorMapEncodeTiled failed for a CPML array");
+            for (auto &mm : maps) {
+                const int axis = mm.psi / 4;
+                const bool ok = axis == 0   ? encode_map3(mm.m, g->psi[p][mm.psi], F32, 4, px, g->ny, g->nz, px, mm.bx, mm.by)
+                                : axis == 1 ? encode_map3(mm.m, g->psi[p][mm.psi], F32, 4, g->nx, d2, g->nz, g->pitch,
+                                                          mm.bx, mm.by)
+                                            : encode_map3(mm.m, g->psi[p][mm.psi], F32, 4, g->nx, g->ny, d2, g->pitch,
+                                                          mm.bx, mm.by);
+                if (!ok) return fail(g, FDTD_ECUDA, "cuTensorMapEncodeTiled failed for a CPML array");
+            }
         }
     }
     g->ncx = (g->nx + TX - 1) / TX;
@@ -1395,6 +1420,13 @@ int fdtd_create_grid(int nx, int ny, int nz, double dx, double courant, const fd
     int d = cpml ? cpml->cells : 0;
     if (d < 0) return FDTD_EINVAL;
     if (d > 0 && (nx < 2 * d + 2 || ny < 2 * d + 2 || nz < 2 * d + 2)) return FDTD_EINVAL;
+    // the step kernel indexes the compact CPML auxiliaries with 32-bit integers
+    if (d > 0) {
+        const double pitch = (nx + 15) / 16 * 16, px = (2 * d + 3) / 4 * 4, d2 = 2.0 * d;
+        if ((double)nz * ny * px >= 2147483647.0 || nz * d2 * pitch >= 2147483647.0 ||
+            d2 * ny * pitch >= 2147483647.0)
+            return FDTD_EINVAL;
+    }
     if (d > 0 && (cpml->kappa_max < 1.0 || cpml->alpha_max < 0 || cpml->order < 0)) return FDTD_EINVAL;
     fdtd_grid *g = new (std::nothrow) fdtd_grid();
     if (!g) return FDTD_ENOMEM;
@@ -2078,7 +2110,7 @@ int fdtd_num_classes(const fdtd_grid *g) { return g ? g->n_classes : -1; }
 // ---- checkpoint / resume ----------------------------------------------------
 namespace {
 constexpr uint32_t kStateMagic = 0x53544446u;     // "FDTS"
-constexpr uint32_t kStateVersion = 4;
+constexpr uint32_t kStateVersion = 5;             // 5: the CPML auxiliaries in their compact layout
 struct StateHeader {
     uint32_t magic, version;
     int32_t nx, ny, nz, d, n_probes, capacity, n_psi, npoles, dz0, dz1, n_oseg, n_onode;
@@ -2087,10 +2119,17 @@ struct StateHeader {
 
 size_t debye_elems(const fdtd_grid *g) { return 3 * (size_t)g->npoles * (size_t)(g->dz1 - g->dz0) * g->plane; }
 
+size_t psi_state_elems(const fdtd_grid *g, int n_psi)
+{
+    size_t n = 0;
+    for (int q = 0; q < n_psi; ++q) n += psi_elems(g, q);
+    return n;
+}
+
 size_t state_bytes(const fdtd_grid *g, int n_psi)
 {
     const size_t cells = (size_t)g->nx * g->ny * g->nz;
-    return sizeof(StateHeader) + (6 + (size_t)n_psi) * cells * sizeof(float) +
+    return sizeof(StateHeader) + 6 * cells * sizeof(float) + psi_state_elems(g, n_psi) * sizeof(float) +
            g->probes.size() * (size_t)g->capacity * sizeof(float) + debye_elems(g) * sizeof(float) +
            (g->osegs.size() + 6 * g->onodes.size()) * sizeof(float);
 }
@@ -2129,7 +2168,12 @@ int fdtd_save_state(fdtd_grid *g, void *host_buf, size_t *bytes)
     const size_t arr = (size_t)g->nx * g->ny * g->nz * sizeof(float);
     cudaError_t e = cudaSuccess;
     for (int c = 0; c < 6 && e == cudaSuccess; ++c, p += arr) e = copy_array(g, g->F[g->parity][c], p, true);
-    for (int q = 0; q < n_psi && e == cudaSuccess; ++q, p += arr) e = copy_array(g, g->psi[g->parity][q], p, true);
+    // the auxiliaries as stored (compact layout, row padding included)
+    for (int q = 0; q < n_psi && e == cudaSuccess; ++q) {
+        const size_t nb = psi_elems(g, q) * sizeof(float);
+        e = cudaMemcpy(p, g->psi[g->parity][q], nb, cudaMemcpyDeviceToHost);
+        p += nb;
+    }
     const size_t pbytes = g->probes.size() * (size_t)g->capacity * sizeof(float);
     if (e == cudaSuccess && pbytes) e = cudaMemcpy(p, g->probe_out, pbytes, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && debye_elems(g))
@@ -2168,7 +2212,11 @@ int fdtd_load_state(fdtd_grid *g, const void *host_buf, size_t bytes)
     char *q = const_cast<char *>(p);
     cudaError_t e = cudaSuccess;
     for (int c = 0; c < 6 && e == cudaSuccess; ++c, q += arr) e = copy_array(g, g->F[g->parity][c], q, false);
-    for (int a = 0; a < n_psi && e == cudaSuccess; ++a, q += arr) e = copy_array(g, g->psi[g->parity][a], q, false);
+    for (int a = 0; a < n_psi && e == cudaSuccess; ++a) {
+        const size_t nb = psi_elems(g, a) * sizeof(float);
+        e = cudaMemcpy(g->psi[g->parity][a], q, nb, cudaMemcpyHostToDevice);
+        q += nb;
+    }
     const size_t pbytes = g->probes.size() * (size_t)g->capacity * sizeof(float);
     if (e == cudaSuccess && pbytes) e = cudaMemcpy(g->probe_out, q, pbytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && debye_elems(g))

@@ -16,11 +16,11 @@
 //     4-slot ring (two planes in use, two in flight), and H^{n-1/2} (tile +
 //     low halo), the class bytes and, in a CPML layer, the auxiliary fields
 //     of one axis into a 3-slot ring (one in use, two in flight).
-//   - Eight row warps: lane = x column, each warp two rows.  Per plane k
-//     they form H^{n+1/2}(k) of their cells and store it, then E^{n+1}(k)
-//     from that H plane and the owned column's H of plane k-1 kept in
-//     registers; E^n(k+1) of the owned cells stays in registers for the
-//     next plane.  A ninth warp recomputes (never exchanges) H^{n+1/2} of
+//   - Eight row warps: lane = x column, warp w owns rows w and w + 8 of the
+//     tile (so a y layer's rows spread over all warps).  Per plane k they
+//     form H^{n+1/2}(k) of their cells and store it, then E^{n+1}(k) from
+//     that H plane and the owned column's H of plane k-1 kept in registers;
+//     E^n(k+1) of the owned cells stays in registers for the next plane.  A ninth warp recomputes (never exchanges) H^{n+1/2} of
 //     the low-y row and low-x column halo meanwhile, so every warp has the
 //     same work between the two per-plane barriers.
 //   - Items that touch no CPML layer run a variant compiled without any
@@ -42,7 +42,7 @@ namespace {
 
 using geom::TX;                        // tile width: one lane per column
 using geom::TY;                        // tile height
-constexpr int RW = 2;                  // rows per consumer warp
+constexpr int RW = 2;                  // rows per consumer warp (w and w + NCW)
 constexpr int NCW = TY / RW;           // row warps
 constexpr int NCONS = (NCW + 1) * 32;  // row warps + the halo warp
 constexpr int NTHREADS = NCONS + 32;   // + the producer warp
@@ -231,8 +231,9 @@ __device__ __forceinline__ int slab_of(int i, int n, int d) { return i < d ? i :
 // differences, before any store.
 template <bool WRITE>
 __device__ __forceinline__ void cpml2(float &d0, float &d1, const float4 *pr, int s, float o0, float o1,
-                                      float *out0, float *out1, long long g)
+                                      float *out0, float *out1, int g)
 {
+    // g: the cell's element in its axis's compact auxiliary arrays
     const float4 pv = pr[s];
     const float b = pv.x, c = pv.y, ki = pv.z;
     const float p0 = b * o0 + c * d0, p1 = b * o1 + c * d1;
@@ -242,6 +243,21 @@ __device__ __forceinline__ void cpml2(float &d0, float &d1, const float4 *pr, in
     }
     d0 = d0 * ki + p0;
     d1 = d1 * ki + p1;
+}
+
+// Element of cell (i, j, k) in the compact auxiliaries of each axis, which
+// hold only the layer: x [nz][ny][px] by slab column sx, y [nz][2d][pitch]
+// by slab row sy, z [2d][ny][pitch] by slab plane sz (px = 2d rounded up to
+// a multiple of 4, so rows stay 16-byte aligned for TMA).
+// The host keeps every compact array below 2^31 elements, so 32-bit indices.
+__device__ __forceinline__ int psi_x(const StepArgs &a, int sx, int j, int k) { return (k * a.ny + j) * a.px + sx; }
+__device__ __forceinline__ int psi_y(const StepArgs &a, int i, int sy, int k)
+{
+    return (k * (2 * a.d) + sy) * a.pitch + i;
+}
+__device__ __forceinline__ int psi_z(const StepArgs &a, int i, int j, int sz)
+{
+    return (sz * a.ny + j) * a.pitch + i;
 }
 
 // profile row of axis u at E (h = 0) or H (h = 1) positions in the staged
@@ -261,7 +277,7 @@ __device__ __forceinline__ const float4 *prow(const float *prof, int u, int h, i
 // are recomputed only).
 template <bool CPML, bool STAGED, bool WRITE>
 __device__ __forceinline__ void h_core(const StepArgs &a, const float4 *t, const float *prof, const Slab &L,
-                                       long long g, float ex, float ey, float ez, float ey_x1, float ez_x1,
+                                       int i, int j, int k, float ex, float ey, float ez, float ey_x1, float ez_x1,
                                        float ex_y1, float ez_y1, float ex_z1, float ey_z1, float hx0, float hy0,
                                        float hz0, float &hx, float &hy, float &hz)
 {
@@ -272,18 +288,21 @@ __device__ __forceinline__ void h_core(const StepArgs &a, const float4 *t, const
         const int d2 = 2 * a.d;
         if (L.sx >= 0) {
             const int q = a.pg.xb >> 2;
+            const int g = psi_x(a, L.sx, j, k);
             const float o0 = (STAGED || L.xo >= 0) ? L.base[L.xo] : __ldg(a.psi_in[PSI_HY_X] + g);
             const float o1 = (STAGED || L.xo >= 0) ? L.base[L.xo + q] : __ldg(a.psi_in[PSI_HZ_X] + g);
             cpml2<WRITE>(hy_x, hz_x, prow(prof, 0, 1, d2), L.sx, o0, o1, a.psi_out[PSI_HY_X], a.psi_out[PSI_HZ_X], g);
         }
         if (L.sy >= 0) {
             const int q = a.pg.yb >> 2;
+            const int g = psi_y(a, i, L.sy, k);
             const float o0 = (STAGED || L.yo >= 0) ? L.base[L.yo] : __ldg(a.psi_in[PSI_HX_Y] + g);
             const float o1 = (STAGED || L.yo >= 0) ? L.base[L.yo + q] : __ldg(a.psi_in[PSI_HZ_Y] + g);
             cpml2<WRITE>(hx_y, hz_y, prow(prof, 1, 1, d2), L.sy, o0, o1, a.psi_out[PSI_HX_Y],
                        a.psi_out[PSI_HZ_Y], g);
         }
         if (L.sz >= 0) {
+            const int g = psi_z(a, i, j, L.sz);
             const float o0 = (STAGED || L.zo >= 0) ? L.base[L.zo] : __ldg(a.psi_in[PSI_HX_Z] + g);
             const float o1 = (STAGED || L.zo >= 0) ? L.base[L.zo + H_COMP / 4] : __ldg(a.psi_in[PSI_HY_Z] + g);
             cpml2<WRITE>(hx_z, hy_z, prow(prof, 2, 1, d2), L.sz, o0, o1, a.psi_out[PSI_HX_Z],
@@ -301,7 +320,7 @@ __device__ __forceinline__ void h_core(const StepArgs &a, const float4 *t, const
 // updates, whose auxiliaries are staged.
 template <bool CPML>
 __device__ __forceinline__ void e_core(const StepArgs &a, const float4 *t, const float *prof, const Slab &L,
-                                       long long g, float ex, float ey, float ez, float hx, float hy, float hz,
+                                       int i, int j, int k, float ex, float ey, float ez, float hx, float hy, float hz,
                                        float hz_ym, float hx_ym, float hz_xm, float hy_xm, float hx_zm,
                                        float hy_zm, float &ex1, float &ey1, float &ez1)
 {
@@ -313,16 +332,16 @@ __device__ __forceinline__ void e_core(const StepArgs &a, const float4 *t, const
         if (L.sx >= 0) {
             const int q = a.pg.xb >> 2;
             cpml2<true>(ey_x, ez_x, prow(prof, 0, 0, d2), L.sx, L.base[L.xo + 2 * q], L.base[L.xo + 3 * q],
-                        a.psi_out[PSI_EY_X], a.psi_out[PSI_EZ_X], g);
+                        a.psi_out[PSI_EY_X], a.psi_out[PSI_EZ_X], psi_x(a, L.sx, j, k));
         }
         if (L.sy >= 0) {
             const int q = a.pg.yb >> 2;
             cpml2<true>(ex_y, ez_y, prow(prof, 1, 0, d2), L.sy, L.base[L.yo + 2 * q], L.base[L.yo + 3 * q],
-                        a.psi_out[PSI_EX_Y], a.psi_out[PSI_EZ_Y], g);
+                        a.psi_out[PSI_EX_Y], a.psi_out[PSI_EZ_Y], psi_y(a, i, L.sy, k));
         }
         if (L.sz >= 0)
             cpml2<true>(ex_z, ey_z, prow(prof, 2, 0, d2), L.sz, L.base[L.zeo],
-                        L.base[L.zeo + PE_BYTES / 4], a.psi_out[PSI_EX_Z], a.psi_out[PSI_EY_Z], g);
+                        L.base[L.zeo + PE_BYTES / 4], a.psi_out[PSI_EX_Z], a.psi_out[PSI_EY_Z], psi_z(a, i, j, L.sz));
     }
     const float4 ca = t[1], cb = t[2];
     ex1 = ca.x * ex + cb.x * (ex_y - ex_z);
@@ -386,14 +405,13 @@ struct Stg {
 // depend on the tile only, so they are formed once per item.
 __device__ __forceinline__ int x_off(const StepArgs &a, const Stg &sg, int i, int row)
 {
-    return (slab_of(i, a.nx, a.d) >= 0 && i >= sg.xs && i < sg.xs + a.pg.w) ? a.ox / 4 + row * a.pg.w + (i - sg.xs)
-                                                                             : -1;
+    const int sx = slab_of(i, a.nx, a.d);
+    return (sx >= 0 && sx >= sg.xs && sx < sg.xs + a.pg.w) ? a.ox / 4 + row * a.pg.w + (sx - sg.xs) : -1;
 }
 __device__ __forceinline__ int y_off(const StepArgs &a, const Stg &sg, int x0, int i, int j)
 {
-    return (slab_of(j, a.ny, a.d) >= 0 && j >= sg.ys && j < sg.ys + a.pg.hy)
-               ? a.oy / 4 + (j - sg.ys) * HBX + (i - (x0 - XO))
-               : -1;
+    const int sy = slab_of(j, a.ny, a.d);
+    return (sy >= 0 && sy >= sg.ys && sy < sg.ys + a.pg.hy) ? a.oy / 4 + (sy - sg.ys) * HBX + (i - (x0 - XO)) : -1;
 }
 
 // the staging of one plane applied to a cell's precomputed offsets
@@ -408,16 +426,24 @@ __device__ __forceinline__ Slab slab_in(const Stg &sg, const HView &hv, int sx, 
 // the layer and where the box narrowed to the layer starts
 __device__ __forceinline__ int tile_boxes(const StepArgs &a, int x0, int y0, int &xs, int &ys)
 {
+    // the layer cells among x0-1 .. x0+TX-1 (y0-1 .. y0+TY-1) form one run of
+    // slab entries (the low layer's, then the high layer's, contiguous in
+    // the compact arrays); the x box starts at the first, rounded down to a
+    // 16-byte boundary, the y box at the first
     const int d = a.d;
     int f = 0;
     xs = 0;
     ys = 0;
     const int xl = max(x0 - 1, 0), xh = min(x0 + TX, a.nx) - 1;
-    if (xl < d) { f |= F_X; xs = x0 - XO; }
-    else if (xh >= a.nx - d) { f |= F_X; xs = max(x0 - 1, a.nx - d) & ~3; }
+    if (xl < d || xh >= a.nx - d) {
+        f |= F_X;
+        xs = slab_of(xl < d ? xl : max(xl, a.nx - d), a.nx, d) & ~3;
+    }
     const int yl = max(y0 - 1, 0), yh = min(y0 + TY, a.ny) - 1;
-    if (yl < d) { f |= F_Y; ys = y0 - 1; }
-    else if (yh >= a.ny - d) { f |= F_Y; ys = max(y0 - 1, a.ny - d); }
+    if (yl < d || yh >= a.ny - d) {
+        f |= F_Y;
+        ys = slab_of(yl < d ? yl : max(yl, a.ny - d), a.ny, d);
+    }
     return f;
 }
 
@@ -522,7 +548,7 @@ __device__ __forceinline__ bool run_item(const Cons<NH> &C, const Item &it, uint
     Stg tb(0, 0, 0);                // the tile's x / y layer boxes
     if (CPML) tb.f = tile_boxes(a, it.x0, it.y0, tb.xs, tb.ys);
     for (int r = 0; r < RW; ++r) {
-        const int row = 1 + C.warp * RW + r, j = it.y0 + C.warp * RW + r;
+        const int row = 1 + C.warp + r * NCW, j = it.y0 + C.warp + r * NCW;
         sy[r] = CPML ? slab_of(j, a.ny, d) : -1;
         xo[r] = (CPML && (tb.f & F_X)) ? x_off(a, tb, i, row) : -1;
         yo[r] = (CPML && (tb.f & F_Y)) ? y_off(a, tb, it.x0, i, j) : -1;
@@ -548,20 +574,19 @@ __device__ __forceinline__ bool run_item(const Cons<NH> &C, const Item &it, uint
         const HView h0 = C.hv(qh0);
         // owned E^n(ka) and, below the block, the owned Hx, Hy of plane ka-1
         for (int r = 0; r < RW; ++r) {
-            const int row = 1 + C.warp * RW + r;
+            const int row = 1 + C.warp + r * NCW;
             for (int c = 0; c < 3; ++c) ecur[c][r] = e1.e(c, row, lx);
         }
         if (it.ka > 0) {
             const int k = it.ka - 1;
             for (int r = 0; r < RW; ++r) {
-                const int row = 1 + C.warp * RW + r, j = it.y0 + C.warp * RW + r;
+                const int row = 1 + C.warp + r * NCW, j = it.y0 + C.warp + r * NCW;
                 if (i < a.nx && j < a.ny) {
                     float hz;
                     const Slab L = CPML ? slab_in(Stg(e0.hdr()), h0, sx, sy[r], slab_of(k, a.nz, d), xo[r], yo[r],
                                                   row * HBX + lx, -1)
                                         : Slab{-1, -1, -1, nullptr, -1, -1, -1, -1};
-                    const long long g = (long long)k * a.plane + (long long)j * a.pitch + i;
-                    h_core<CPML, false, false>(a, C.coef(h0.cls(row, clx)), C.prof, L, g, e0.e(0, row, lx),
+                    h_core<CPML, false, false>(a, C.coef(h0.cls(row, clx)), C.prof, L, i, j, k, e0.e(0, row, lx),
                                  e0.e(1, row, lx), e0.e(2, row, lx), e0.e(1, row, lx + 1), e0.e(2, row, lx + 1),
                                  e0.e(0, row + 1, lx), e0.e(2, row + 1, lx), ecur[0][r], ecur[1][r],
                                  h0.h(0, row, lx), h0.h(1, row, lx), h0.h(2, row, lx), hxp[r], hyp[r], hz);
@@ -585,18 +610,18 @@ __device__ __forceinline__ bool run_item(const Cons<NH> &C, const Item &it, uint
         int cl[RW];
         if (ok && !C.halo) {
             for (int r = 0; r < RW; ++r) {
-                const int row = 1 + C.warp * RW + r, j = it.y0 + C.warp * RW + r;
+                const int row = 1 + C.warp + r * NCW, j = it.y0 + C.warp + r * NCW;
                 for (int c = 0; c < 3; ++c) enx[c][r] = ek1.e(c, row, lx);
                 cl[r] = hk.cls(row, clx);
-                const float ex_y1 = (r + 1 < RW) ? ecur[0][r + 1] : ek.e(0, row + 1, lx);
-                const float ez_y1 = (r + 1 < RW) ? ecur[2][r + 1] : ek.e(2, row + 1, lx);
+                const float ex_y1 = ek.e(0, row + 1, lx);
+                const float ez_y1 = ek.e(2, row + 1, lx);
                 float hx = 0.f, hy = 0.f, hz = 0.f;
                 if (i < a.nx && j < a.ny) {
                     const long long g = (long long)k * a.plane + (long long)j * a.pitch + i;
                     const Slab L = CPML ? slab_in(sg, hk, sx, sy[r], sz, xo[r], yo[r], row * HBX + lx,
                                                   (2 * H_COMP) / 4 + (row - 1) * TX + lane)
                                         : Slab{-1, -1, -1, nullptr, -1, -1, -1, -1};
-                    h_core<CPML, true, true>(a, C.coef(cl[r]), C.prof, L, g, ecur[0][r], ecur[1][r],
+                    h_core<CPML, true, true>(a, C.coef(cl[r]), C.prof, L, i, j, k, ecur[0][r], ecur[1][r],
                                  ecur[2][r], ek.e(1, row, lx + 1), ek.e(2, row, lx + 1), ex_y1, ez_y1, enx[0][r],
                                  enx[1][r], hk.h(0, row, lx), hk.h(1, row, lx), hk.h(2, row, lx), hx, hy, hz);
                     a.Hout[0][g] = hx;
@@ -619,11 +644,10 @@ __device__ __forceinline__ bool run_item(const Cons<NH> &C, const Item &it, uint
                 if (pass == 1 && lane >= TY) break;
                 float hx = 0.f, hy = 0.f, hz = 0.f;
                 if (hi >= 0 && hj >= 0 && hi < a.nx && hj < a.ny) {
-                    const long long g = (long long)k * a.plane + (long long)hj * a.pitch + hi;
                     const Slab L = CPML ? slab_in(sg, hk, slab_of(hi, a.nx, d), slab_of(hj, a.ny, d), sz, hxo[pass],
                                                   hyo[pass], hrow * HBX + hcol, -1)
                                         : Slab{-1, -1, -1, nullptr, -1, -1, -1, -1};
-                    h_core<CPML, false, false>(a, C.coef(hk.cls(hrow, hcol - XO + CXO)), C.prof, L, g,
+                    h_core<CPML, false, false>(a, C.coef(hk.cls(hrow, hcol - XO + CXO)), C.prof, L, hi, hj, k,
                                  ek.e(0, hrow, hcol), ek.e(1, hrow, hcol), ek.e(2, hrow, hcol),
                                  ek.e(1, hrow, hcol + 1), ek.e(2, hrow, hcol + 1), ek.e(0, hrow + 1, hcol),
                                  ek.e(2, hrow + 1, hcol), ek1.e(0, hrow, hcol), ek1.e(1, hrow, hcol),
@@ -642,16 +666,16 @@ __device__ __forceinline__ bool run_item(const Cons<NH> &C, const Item &it, uint
         }
         if (!C.halo) {
             for (int r = 0; r < RW; ++r) {
-                const int row = 1 + C.warp * RW + r, j = it.y0 + C.warp * RW + r;
+                const int row = 1 + C.warp + r * NCW, j = it.y0 + C.warp + r * NCW;
                 if (i < a.nx && j < a.ny) {
-                    const float hz_ym = r > 0 ? hnw[2][r - 1] : C.hn(hb, 2, row - 1, lx);
-                    const float hx_ym = r > 0 ? hnw[0][r - 1] : C.hn(hb, 0, row - 1, lx);
+                    const float hz_ym = C.hn(hb, 2, row - 1, lx);
+                    const float hx_ym = C.hn(hb, 0, row - 1, lx);
                     const long long g = (long long)k * a.plane + (long long)j * a.pitch + i;
                     const Slab L = CPML ? slab_in(sg, hk, sx, sy[r], sz, xo[r], yo[r], row * HBX + lx,
                                                   (2 * H_COMP) / 4 + (row - 1) * TX + lane)
                                         : Slab{-1, -1, -1, nullptr, -1, -1, -1, -1};
                     float ex1, ey1, ez1;
-                    e_core<CPML>(a, C.coef(cl[r]), C.prof, L, g, ecur[0][r], ecur[1][r], ecur[2][r],
+                    e_core<CPML>(a, C.coef(cl[r]), C.prof, L, i, j, k, ecur[0][r], ecur[1][r], ecur[2][r],
                                  hnw[0][r], hnw[1][r], hnw[2][r], hz_ym, hx_ym, C.hn(hb, 2, row, lx - 1),
                                  C.hn(hb, 1, row, lx - 1), hxp[r], hyp[r], ex1, ey1, ez1);
                     a.Eout[0][g] = ex1;
@@ -782,8 +806,9 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
                     char *ps = hs + OFF_PSI;
                     if (f & F_Z) {
                         for (int q = 0; q < 2; ++q) {
-                            tma_load_3d(smem_u32(ps + q * H_COMP), &m.zh[q], it.x0 - XO, it.y0 - 1, z, fb);
-                            tma_load_3d(smem_u32(ps + 2 * H_COMP + q * PE_BYTES), &m.ze[q], it.x0, it.y0, z, fb);
+                            const int sz = slab_of(z, a.nz, a.d);     // plane of the compact z arrays
+                            tma_load_3d(smem_u32(ps + q * H_COMP), &m.zh[q], it.x0 - XO, it.y0 - 1, sz, fb);
+                            tma_load_3d(smem_u32(ps + 2 * H_COMP + q * PE_BYTES), &m.ze[q], it.x0, it.y0, sz, fb);
                         }
                     }
                     if (f & F_X) {
@@ -918,16 +943,27 @@ PsiGeom step_psi_geom(int d, int nx, int ny)
 {
     PsiGeom pg{};
     if (d == 0) return pg;
-    // a tile that meets both layers of an axis (grids narrower than about a
-    // tile plus two layers) stages its whole H box along that axis, so the
-    // staged boxes always hold every auxiliary of the cells an item updates
-    bool both_x = false, both_y = false;
-    for (int x0 = 0; x0 < nx; x0 += TX)
-        both_x |= std::max(x0 - 1, 0) < d && std::min(x0 + TX, nx) - 1 >= nx - d;
-    for (int y0 = 0; y0 < ny; y0 += TY)
-        both_y |= std::max(y0 - 1, 0) < d && std::min(y0 + TY, ny) - 1 >= ny - d;
-    pg.w = both_x ? HBX : std::min(HBX, (d + 4 + 3) / 4 * 4);
-    pg.hy = both_y ? HBY : std::min(HBY, d + 1);
+    // the x (y) box of a tile spans the slab entries of the layer cells
+    // among x0-1 .. x0+TX-1 (y0-1 .. y0+TY-1), from the first (rounded down
+    // to a multiple of 4 along x) to the last: the largest span over the tiles
+    auto slab = [d](int i, int n) { return i < d ? i : (i >= n - d ? i - (n - 2 * d) : -1); };
+    int w = 0, hy = 0;
+    for (int x0 = 0; x0 < nx; x0 += TX) {
+        const int xl = std::max(x0 - 1, 0), xh = std::min(x0 + TX, nx) - 1;
+        if (!(xl < d || xh >= nx - d)) continue;
+        const int first = slab(xl < d ? xl : std::max(xl, nx - d), nx) & ~3;
+        const int last = slab(xh >= nx - d ? xh : std::min(xh, d - 1), nx);
+        w = std::max(w, (last - first + 1 + 3) / 4 * 4);
+    }
+    for (int y0 = 0; y0 < ny; y0 += TY) {
+        const int yl = std::max(y0 - 1, 0), yh = std::min(y0 + TY, ny) - 1;
+        if (!(yl < d || yh >= ny - d)) continue;
+        const int first = slab(yl < d ? yl : std::max(yl, ny - d), ny);
+        const int last = slab(yh >= ny - d ? yh : std::min(yh, d - 1), ny);
+        hy = std::max(hy, last - first + 1);
+    }
+    pg.w = w;
+    pg.hy = hy;
     pg.xb = al128(pg.w * HBY * 4);
     pg.yb = al128(HBX * pg.hy * 4);
     return pg;
