@@ -370,7 +370,8 @@ typedef struct fdtd_batch fdtd_batch;
  * must outlive it and must not be stepped by other calls meanwhile).
  * cuda_stream: the stream the batch queues on.  Allocates a small device
  * table (about 7 KB per domain).  FDTD_ESTATE if a grid is not finalized or
- * the step counts differ; FDTD_EINVAL for a grid with Debye poles. */
+ * the step counts differ; FDTD_EINVAL for a grid with Debye poles or a
+ * grid of 2^31 cells or more (batch domains use 32-bit indices). */
 int fdtd_batch_create(int n_grids, fdtd_grid *const *grids, void *cuda_stream, fdtd_batch **out);
 
 /* Queue n steps of every domain on the batch stream (asynchronous).  Each

@@ -145,6 +145,7 @@ struct BatchArgs {
     int max_classes, max_d;  // shared-memory sizing over the domains
     int region;              // staged-auxiliary region (max over the domains)
     int nh;                  // slots of the H / class / CPML ring (2 or 3)
+    int wide;                // single grid of 2^31 elements or more: 64-bit field indices
 };
 
 
@@ -266,7 +267,7 @@ PsiGeom step_psi_geom(int d, int nx, int ny);
 // region size and box-group offsets for a launch that stages z alone
 // (zxy = 0) or z together with the x / y layers (zxy = 1)
 void step_region(const PsiGeom &pg, int zxy, int *region, int *ox, int *oy);
-const void *step_kernel_ptr(int nh, bool batch);
+const void *step_kernel_ptr(int nh, bool batch, bool wide);
 // fdtd_edges.cu
 cudaError_t launch_edges(const EdgeArgs &a, cudaStream_t s);
 // oblique wires: segment currents to t_{n+1/2}; needs only the step's inputs,

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -236,6 +237,18 @@ int debye_extent(const fdtd_grid *g, int *z0, int *z1)
     *z0 = P ? kmin : 0;
     *z1 = P ? std::min(g->nz, kmax + 2) : 0;
     return P;
+}
+
+// a grid whose field arrays hold 2^31 elements or more needs 64-bit indices;
+// FDTD_WIDE_INDEX=1 in the environment selects them for any single grid
+// (the tests compare both instantiations on small grids)
+bool grid_is_wide(const fdtd_grid *g)
+{
+    static const bool forced = [] {
+        const char *v = std::getenv("FDTD_WIDE_INDEX");
+        return v && v[0] == '1';
+    }();
+    return (double)g->plane * g->nz >= 2147483647.0 || forced;
 }
 
 // compact auxiliaries: only their axis's two layers (fdtd_internal.h)
@@ -1085,6 +1098,7 @@ fdtd::BatchArgs grid_launch(const fdtd_grid *g, int parity, int l, int *work, in
     b.max_d = g->d;
     b.region = g->lc[l].region;
     b.nh = g->lc[l].nh;
+    b.wide = grid_is_wide(g);
     return b;
 }
 
@@ -1293,12 +1307,13 @@ int setup_step_kernel(fdtd_grid *g)
         max_smem = std::max(max_smem, fdtd::step_smem_bytes(g->n_classes, d, L.region, L.nh));
         g->n_launch = l + 1;
     }
-    for (int nh = 2; nh <= 3 && e == cudaSuccess; ++nh) e = ensure_smem(fdtd::step_kernel_ptr(nh, false), max_smem);
+    const bool wide = grid_is_wide(g);
+    for (int nh = 2; nh <= 3 && e == cudaSuccess; ++nh) e = ensure_smem(fdtd::step_kernel_ptr(nh, false, wide), max_smem);
     if (e != cudaSuccess) return cuda_fail(g, e, "step kernel setup");
     for (int l = 0; l < g->n_launch; ++l) {
         auto &L = g->lc[l];
         int occ = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fdtd::step_kernel_ptr(L.nh, false), fdtd::step_threads(),
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fdtd::step_kernel_ptr(L.nh, false, wide), fdtd::step_threads(),
                                                           fdtd::step_smem_bytes(g->n_classes, d, L.region, L.nh));
         if (e != cudaSuccess) return cuda_fail(g, e, "step kernel occupancy");
         if (occ < 1) return fail(g, FDTD_ECUDA, "step kernel does not fit on an SM");
@@ -2389,6 +2404,7 @@ int fdtd_batch_create(int n, fdtd_grid *const *grids, void *cuda_stream, fdtd_ba
         fdtd_grid *g = grids[q];
         if (!g || !g->finalized) { delete b; return FDTD_ESTATE; }
         if (g->npoles) { delete b; return FDTD_EINVAL; }      // dispersive media run on their own
+        if ((double)g->plane * g->nz >= 2147483647.0) { delete b; return FDTD_EINVAL; }  // 32-bit indices
         if (g->parity != grids[0]->parity || g->step != grids[0]->step) { delete b; return FDTD_ESTATE; }
         b->grids.push_back(g);
     }
@@ -2422,11 +2438,11 @@ int fdtd_batch_create(int n, fdtd_grid *const *grids, void *cuda_stream, fdtd_ba
             b->nh[l] = 2;
         max_smem = std::max(max_smem, fdtd::step_smem_bytes(b->max_classes, b->max_d, b->region[l], b->nh[l]));
     }
-    for (int nh = 2; nh <= 3 && e == cudaSuccess; ++nh) e = ensure_smem(fdtd::step_kernel_ptr(nh, true), max_smem);
+    for (int nh = 2; nh <= 3 && e == cudaSuccess; ++nh) e = ensure_smem(fdtd::step_kernel_ptr(nh, true, false), max_smem);
     for (int l = 0; l < b->n_launch && e == cudaSuccess; ++l) {
         int occ = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &occ, fdtd::step_kernel_ptr(b->nh[l], true), fdtd::step_threads(),
+            &occ, fdtd::step_kernel_ptr(b->nh[l], true, false), fdtd::step_threads(),
             fdtd::step_smem_bytes(b->max_classes, b->max_d, b->region[l], b->nh[l]));
         if (e == cudaSuccess && occ < 1) { delete b; return FDTD_ECUDA; }
         b->grid[l] = std::max(1, std::min(sms * std::max(occ, 1), b->nitems[l]));

@@ -33,6 +33,7 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "fdtd.h"
 #include "fdtd_internal.h"
@@ -534,9 +535,12 @@ struct Cons {
 // one work item.  Its planes ka-1 .. kb occupy E slots qe0 .. qe0+kb-ka+1
 // and planes ka-1 .. kb-1 H slots qh0 .. qh0+kb-ka.  Returns false when a
 // wait gave up (the CTA then aborts).
-template <bool CPML, int NH>
+// WIDE: 64-bit element indices for the field stores (grids of 2^31
+// elements or more); 32-bit otherwise, fewer registers in the plane loop
+template <bool CPML, int NH, bool WIDE>
 __device__ __forceinline__ bool run_item(const Cons<NH> &C, const Item &it, uint32_t qe0, uint32_t qh0, uint32_t &hb)
 {
+    using Idx = typename std::conditional<WIDE, long long, int>::type;
     const StepArgs &a = *C.a;
     const int lane = C.lane;
     const int lx = XO + lane, clx = CXO + lane;
@@ -617,7 +621,7 @@ __device__ __forceinline__ bool run_item(const Cons<NH> &C, const Item &it, uint
                 const float ez_y1 = ek.e(2, row + 1, lx);
                 float hx = 0.f, hy = 0.f, hz = 0.f;
                 if (i < a.nx && j < a.ny) {
-                    const long long g = (long long)k * a.plane + (long long)j * a.pitch + i;
+                    const Idx g = (Idx)k * (Idx)a.plane + (Idx)j * a.pitch + i;
                     const Slab L = CPML ? slab_in(sg, hk, sx, sy[r], sz, xo[r], yo[r], row * HBX + lx,
                                                   (2 * H_COMP) / 4 + (row - 1) * TX + lane)
                                         : Slab{-1, -1, -1, nullptr, -1, -1, -1, -1};
@@ -670,7 +674,7 @@ __device__ __forceinline__ bool run_item(const Cons<NH> &C, const Item &it, uint
                 if (i < a.nx && j < a.ny) {
                     const float hz_ym = C.hn(hb, 2, row - 1, lx);
                     const float hx_ym = C.hn(hb, 0, row - 1, lx);
-                    const long long g = (long long)k * a.plane + (long long)j * a.pitch + i;
+                    const Idx g = (Idx)k * (Idx)a.plane + (Idx)j * a.pitch + i;
                     const Slab L = CPML ? slab_in(sg, hk, sx, sy[r], sz, xo[r], yo[r], row * HBX + lx,
                                                   (2 * H_COMP) / 4 + (row - 1) * TX + lane)
                                         : Slab{-1, -1, -1, nullptr, -1, -1, -1, -1};
@@ -709,7 +713,7 @@ __device__ __forceinline__ int find_domain(const int *item_start, int n, int q)
 // BATCH = false: one domain whose arguments and descriptors are the kernel's
 // own parameters (constant bank); BATCH = true: a table of domains in global
 // memory, the current domain's arguments staged in shared memory.
-template <int NH, bool BATCH>
+template <int NH, bool BATCH, bool WIDE>
 __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_constant__ SingleArgs S,
                                                               const BatchArgs B)
 {
@@ -898,8 +902,8 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
             if (!ok) *abort = 1;
             consumer_sync();
             if (*abort) break;
-            const bool done = item_in_cpml(a, it) ? run_item<true, NH>(C, it, ce, ch, hb)
-                                                  : run_item<false, NH>(C, it, ce, ch, hb);
+            const bool done = item_in_cpml(a, it) ? run_item<true, NH, WIDE>(C, it, ce, ch, hb)
+                                                  : run_item<false, NH, WIDE>(C, it, ce, ch, hb);
             if (!done) break;
             if (!BATCH && a.n_isrc > 0) {
                 // current sources on the item's edges, after all its E stores
@@ -983,10 +987,11 @@ void step_region(const PsiGeom &pg, int zxy, int *region, int *ox, int *oy)
         *region = std::max(Z_BYTES, *oy + 4 * pg.yb);
     }
 }
-const void *step_kernel_ptr(int nh, bool batch)
+const void *step_kernel_ptr(int nh, bool batch, bool wide)
 {
-    if (batch) return nh == 2 ? (const void *)step_tma_kernel<2, true> : (const void *)step_tma_kernel<3, true>;
-    return nh == 2 ? (const void *)step_tma_kernel<2, false> : (const void *)step_tma_kernel<3, false>;
+    if (batch) return nh == 2 ? (const void *)step_tma_kernel<2, true, false> : (const void *)step_tma_kernel<3, true, false>;
+    if (wide) return nh == 2 ? (const void *)step_tma_kernel<2, false, true> : (const void *)step_tma_kernel<3, false, true>;
+    return nh == 2 ? (const void *)step_tma_kernel<2, false, false> : (const void *)step_tma_kernel<3, false, false>;
 }
 
 cudaError_t launch_step(const SingleArgs &one, const BatchArgs &b, int grid, cudaStream_t s)
@@ -994,11 +999,13 @@ cudaError_t launch_step(const SingleArgs &one, const BatchArgs &b, int grid, cud
     const int smem = smem_bytes(b.max_classes, b.max_d, b.region, b.nh);
     const bool batch = b.doms != nullptr;
     if (b.nh == 2) {
-        if (batch) step_tma_kernel<2, true><<<grid, NTHREADS, smem, s>>>(one, b);
-        else step_tma_kernel<2, false><<<grid, NTHREADS, smem, s>>>(one, b);
+        if (batch) step_tma_kernel<2, true, false><<<grid, NTHREADS, smem, s>>>(one, b);
+        else if (b.wide) step_tma_kernel<2, false, true><<<grid, NTHREADS, smem, s>>>(one, b);
+        else step_tma_kernel<2, false, false><<<grid, NTHREADS, smem, s>>>(one, b);
     } else {
-        if (batch) step_tma_kernel<3, true><<<grid, NTHREADS, smem, s>>>(one, b);
-        else step_tma_kernel<3, false><<<grid, NTHREADS, smem, s>>>(one, b);
+        if (batch) step_tma_kernel<3, true, false><<<grid, NTHREADS, smem, s>>>(one, b);
+        else if (b.wide) step_tma_kernel<3, false, true><<<grid, NTHREADS, smem, s>>>(one, b);
+        else step_tma_kernel<3, false, false><<<grid, NTHREADS, smem, s>>>(one, b);
     }
     return cudaGetLastError();
 }

@@ -4,6 +4,8 @@
 Tolerances: relative L2 <= 1e-5 on every field component and <= 1e-4 on
 every probe waveform, on the same seeded inputs.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -11,6 +13,8 @@ from paper_2207_06908_gb300 import workloads as W
 from _scenario import COMPONENTS, field_errors, oracle_from_scenario, record, rel_l2
 
 pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 FIELD_TOL = 1e-5
 PROBE_TOL = 1e-4
@@ -199,3 +203,34 @@ def test_config2_scaled_long_run(fdtd):
     test_config1_full)"""
     sc = W.config2(n_steps=800, n=64)
     compare_from_rest(sc, 800, *run_gpu(fdtd, sc, 800), *run_oracle(sc, 800))
+
+
+def test_wide_index_instantiation_is_bitwise_equal():
+    """grids of 2^31 elements or more step with 64-bit field indices (another
+    instantiation of the step kernel); forced on a small CPML grid in a
+    child process (FDTD_WIDE_INDEX=1), it gives bit for bit the fields and
+    probes of the 32-bit instantiation"""
+    import subprocess
+    import sys
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    code = (
+        "import sys, numpy as np; sys.path.insert(0, %r); sys.path.insert(0, %r)\n"
+        "from paper_2207_06908_gb300 import fdtd as F, workloads as W\n"
+        "sc = W.random_scenario(52, n=(45, 21, 27), cpml=5, n_steps=70)\n"
+        "g = F.from_scenario(sc, probe_capacity=70)\n"
+        "[g.set_field(c, f) for c, f in enumerate(sc.fields)]\n"
+        "g.step(70)\n"
+        "np.savez(sys.argv[1], *[g.get_field(c) for c in range(6)], *[g.read_probe(p) for p in range(len(sc.probes))])\n"
+    ) % (ROOT, os.path.join(ROOT, "tests"))
+    outs = []
+    for wide in ("0", "1"):
+        path = os.path.join(os.environ.get("TMPDIR", "/tmp"), f"fdtd_wide_{os.getpid()}_{wide}.npz")
+        env = dict(os.environ, FDTD_WIDE_INDEX=wide)
+        subprocess.run([sys.executable, "-c", code, path], check=True, env=env)
+        z = np.load(path)
+        outs.append([z[k] for k in z.files])
+        os.remove(path)
+    for x, y in zip(*outs):
+        assert np.array_equal(x, y)
