@@ -567,7 +567,7 @@ def main():
     traffic = recorded_traffic(cells, sc.name)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": peak_kind,
-                "kernel": "step_kernel (per-step time incl. the source/probe kernel)",
+                "kernel": "step kernels (per-step time incl. the probe kernel)",
                 "bytes_per_step": bps}
 
     e2e = None

@@ -369,9 +369,11 @@ typedef struct fdtd_batch fdtd_batch;
  * device; the batch reads their device state and keeps pointers to them (they
  * must outlive it and must not be stepped by other calls meanwhile).
  * cuda_stream: the stream the batch queues on.  Allocates a small device
- * table (about 7 KB per domain).  FDTD_ESTATE if a grid is not finalized or
- * the step counts differ; FDTD_EINVAL for a grid with Debye poles or a
- * grid of 2^31 cells or more (batch domains use 32-bit indices). */
+ * table (about 16 KB per domain: launch arguments, tensor maps and the
+ * staging images the step kernel copies into shared memory).  FDTD_ESTATE
+ * if a grid is not finalized or the step counts differ; FDTD_EINVAL for a
+ * grid with Debye poles or a grid of 2^31 cells or more (batch domains use
+ * 32-bit indices). */
 int fdtd_batch_create(int n_grids, fdtd_grid *const *grids, void *cuda_stream, fdtd_batch **out);
 
 /* Queue n steps of every domain on the batch stream (asynchronous).  Each

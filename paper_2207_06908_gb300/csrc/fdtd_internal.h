@@ -146,7 +146,17 @@ struct BatchArgs {
     int region;              // staged-auxiliary region (max over the domains)
     int nh;                  // slots of the H / class / CPML ring (2 or 3)
     int wide;                // single grid of 2^31 elements or more: 64-bit field indices
+    // batches: per (domain, launch, parity) {offset, length} in int4 of the
+    // domain's staging image in img -- its StepArgs, table rows and CPML
+    // profile rows in the layout of their shared-memory copy
+    const int4 *img;
+    const int2 *img_ref;
 };
+
+// shared-memory layout of a domain's staging image (and of the step
+// kernel's copy): StepArgs, then from byte step_tab_offset() the class table
+// (max_classes rows of 12 floats: {db xyz, 0}, {ca xyz, 0}, {cb xyz, 0}),
+// then the CPML profiles ([axis][E, H][2d] x {b, c, 1/kappa, 0})
 
 
 
@@ -263,6 +273,7 @@ int step_tile_x();
 int step_tile_y();
 int step_threads();
 int step_smem_bytes(int n_classes, int d, int region, int nh);
+int step_tab_offset();      // bytes from the start of the StepArgs copy to the class table
 PsiGeom step_psi_geom(int d, int nx, int ny);
 // region size and box-group offsets for a launch that stages z alone
 // (zxy = 0) or z together with the x / y layers (zxy = 1)

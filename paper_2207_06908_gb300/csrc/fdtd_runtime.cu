@@ -2282,6 +2282,8 @@ struct fdtd_batch {
     fdtd::EdgeArgs *edges = nullptr;
     int *work = nullptr;            // [2 per launch]
     int *errf = nullptr;
+    int4 *img = nullptr;            // domains' staging images (fdtd_internal.h)
+    int2 *img_ref = nullptr;        // [domain][launch][parity] {offset, length} in int4
     int nitems[2] = {}, grid[2] = {}, region[2] = {}, nh[2] = {};
     int max_classes = 0, max_d = 0, n_launch = 0;
     bool has_edges = false;
@@ -2317,6 +2319,8 @@ cudaError_t batch_launch(const fdtd_batch *b, int parity, int l, cudaStream_t s)
     a.max_d = b->max_d;
     a.region = b->region[l];
     a.nh = b->nh[l];
+    a.img = b->img;
+    a.img_ref = b->img_ref;
     static const fdtd::SingleArgs none{};
     return fdtd::launch_step(none, a, b->grid[l], s);
 }
@@ -2450,6 +2454,49 @@ int fdtd_batch_create(int n, fdtd_grid *const *grids, void *cuda_stream, fdtd_ba
     if (e != cudaSuccess) { delete b; return FDTD_ECUDA; }
     // device tables
     const size_t nd = b->grids.size();
+    // staging images: per domain, launch and input parity its StepArgs, then
+    // its class table rows spaced for max_classes, then its CPML profile rows,
+    // exactly as the step kernel lays them out in shared memory
+    std::vector<int4> img;
+    std::vector<int2> img_ref(4 * nd);
+    {
+        const size_t tab_off = fdtd::step_tab_offset();
+        for (size_t q = 0; q < nd && e == cudaSuccess; ++q) {
+            fdtd_grid *g = b->grids[q];
+            std::vector<float> table(g->n_classes * (size_t)fdtd::kNumCoef);
+            e = cudaMemcpy(table.data(), g->table_d, table.size() * sizeof(float), cudaMemcpyDeviceToHost);
+            const int d2 = 2 * g->d;
+            const size_t bytes = tab_off + (size_t)b->max_classes * 48 + (g->d > 0 ? 3 * 2 * (size_t)d2 * 16 : 0);
+            std::vector<char> im((bytes + 15) / 16 * 16, 0);
+            float *tab = reinterpret_cast<float *>(im.data() + tab_off);
+            for (int cl = 0; cl < g->n_classes; ++cl)
+                for (int c = 0; c < 3; ++c) {
+                    tab[cl * 12 + c] = table[cl * fdtd::kNumCoef + 6 + c];       // db
+                    tab[cl * 12 + 4 + c] = table[cl * fdtd::kNumCoef + c];       // ca
+                    tab[cl * 12 + 8 + c] = table[cl * fdtd::kNumCoef + 3 + c];   // cb
+                }
+            if (g->d > 0) {
+                float *prof = tab + (size_t)b->max_classes * 12;
+                const int n[3] = {g->nx, g->ny, g->nz};
+                for (int u = 0; u < 3; ++u) {
+                    const std::vector<float> pr = cpml_profile(g, n[u]);
+                    for (int w = 0; w < fdtd::PR_COUNT; ++w)
+                        for (int sl = 0; sl < d2; ++sl) {
+                            const int i = sl < g->d ? sl : n[u] - d2 + sl;
+                            prof[(((u * 2 + w / 3) * d2 + sl) << 2) + w % 3] = pr[(size_t)w * n[u] + i];
+                        }
+                }
+            }
+            for (int l = 0; l < 2; ++l)
+                for (int par = 0; par < 2; ++par) {
+                    std::memcpy(im.data(), &g->slot_h.a[l][par], sizeof(fdtd::StepArgs));
+                    img_ref[(q * 2 + l) * 2 + par] = int2{(int)img.size(), (int)(im.size() / 16)};
+                    const int4 *v = reinterpret_cast<const int4 *>(im.data());
+                    img.insert(img.end(), v, v + im.size() / 16);
+                }
+        }
+        if (e != cudaSuccess) { delete b; return FDTD_ECUDA; }
+    }
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t at = off; off = align_up(off + bytes, 256); return at; };
     const size_t o_doms = take(nd * sizeof(fdtd::DomainSlot));
@@ -2457,6 +2504,8 @@ int fdtd_batch_create(int n, fdtd_grid *const *grids, void *cuda_stream, fdtd_ba
     const size_t o_s1 = take((nd + 1) * sizeof(int));
     const size_t o_edges = take(2 * nd * sizeof(fdtd::EdgeArgs));
     const size_t o_work = take(8 * sizeof(int));
+    const size_t o_img = take(img.size() * sizeof(int4));
+    const size_t o_ref = take(img_ref.size() * sizeof(int2));
     if (cudaMalloc(&b->mem, off) != cudaSuccess) { delete b; return FDTD_ENOMEM; }
     char *base = (char *)b->mem;
     b->doms = (fdtd::DomainSlot *)(base + o_doms);
@@ -2465,6 +2514,8 @@ int fdtd_batch_create(int n, fdtd_grid *const *grids, void *cuda_stream, fdtd_ba
     b->edges = (fdtd::EdgeArgs *)(base + o_edges);
     b->work = (int *)(base + o_work);
     b->errf = b->work + 4;
+    b->img = (int4 *)(base + o_img);
+    b->img_ref = (int2 *)(base + o_ref);
     std::vector<fdtd::DomainSlot> slots(nd);
     std::vector<fdtd::EdgeArgs> edges(2 * nd);
     for (size_t q = 0; q < nd; ++q) {
@@ -2478,6 +2529,9 @@ int fdtd_batch_create(int n, fdtd_grid *const *grids, void *cuda_stream, fdtd_ba
     for (int l = 0; l < 2 && e == cudaSuccess; ++l)
         e = cudaMemcpyAsync(b->item_start[l], starts[l].data(), (nd + 1) * sizeof(int), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->edges, edges.data(), 2 * nd * sizeof(fdtd::EdgeArgs), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->img, img.data(), img.size() * sizeof(int4), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->img_ref, img_ref.data(), img_ref.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     // the grids' own work must be finished before the batch reads them
     for (fdtd_grid *g : b->grids)

@@ -874,25 +874,14 @@ __global__ void __launch_bounds__(NTHREADS, 2) step_tma_kernel(const __grid_cons
             const int item = hdr[0], dom = hdr[5];
             if (item < 0) break;
             if (BATCH && dom != cur) {
-                // stage this domain's arguments, coefficient table and CPML profiles
-                const DomainSlot &D = B.doms[dom];
-                const int *src = reinterpret_cast<const int *>(&D.a[B.launch][B.parity]);
-                int *dst = reinterpret_cast<int *>(sa);
-                for (int q = tid; q < (int)(sizeof(StepArgs) / 4); q += NCONS) dst[q] = __ldg(src + q);
-                const StepArgs &ga = D.a[B.launch][B.parity];
-                for (int q = tid; q < ga.n_classes * kTabStride; q += NCONS) {
-                    const int cl = q / kTabStride, src = tab_src(q - cl * kTabStride);
-                    tab[q] = src < 0 ? 0.f : __ldg(ga.table + cl * kNumCoef + src);
-                }
-                if (ga.d > 0) {
-                    const int d2 = 2 * ga.d, per = PR_COUNT * d2;
-                    for (int q = tid; q < 3 * per; q += NCONS) {
-                        const int u = q / per, w = (q - u * per) / d2, sl = q - u * per - w * d2;
-                        const int n = u == 0 ? ga.nx : (u == 1 ? ga.ny : ga.nz);
-                        const int i = sl < ga.d ? sl : n - d2 + sl;
-                        prof[(((u * 2 + w / 3) * d2 + sl) << 2) + w % 3] = __ldg(ga.prof[u] + w * n + i);
-                    }
-                }
+                // stage this domain's image -- its arguments, coefficient
+                // table rows and CPML profile rows, which the host laid out
+                // exactly as their shared-memory copy -- in one round of
+                // independent 16-byte loads
+                const int2 ref = __ldg(B.img_ref + (dom * 2 + B.launch) * 2 + B.parity);
+                const int4 *src = B.img + ref.x;
+                int4 *dst = reinterpret_cast<int4 *>(sa);
+                for (int q = tid; q < ref.y; q += NCONS) dst[q] = __ldg(src + q);
                 cur = dom;
                 consumer_sync();
             }
@@ -942,6 +931,7 @@ int step_tile_x() { return TX; }
 int step_tile_y() { return TY; }
 int step_threads() { return NTHREADS; }
 int step_smem_bytes(int n_classes, int d, int region, int nh) { return smem_bytes(n_classes, d, region, nh); }
+int step_tab_offset() { return al128(sizeof(StepArgs)); }
 
 PsiGeom step_psi_geom(int d, int nx, int ny)
 {
