@@ -268,7 +268,7 @@ int fdtd_set_block(fdtd_grid *g, int planes);
  * of Sec. 2.1 is stable only under the Courant bound; an unstable run grows
  * without bound, overflows FP32 and spreads NaN.  Every time the grid's
  * step count crosses a multiple of `every` during fdtd_step() (checked after
- * each 32-step graph replay or direct step), one streaming kernel reads the
+ * each graph replay or direct step), one streaming kernel reads the
  * six field arrays on the grid's stream and sets a device flag if any value
  * is a NaN or an infinity; the next fdtd_synchronize() (and every call that
  * synchronises: fdtd_read_probes, fdtd_get_field, ...) returns
@@ -292,7 +292,9 @@ int fdtd_arena_bytes(const fdtd_grid *g, int probe_capacity, size_t *bytes);
 int fdtd_finalize(fdtd_grid *g, int probe_capacity, void *arena, size_t arena_bytes);
 
 /* Queue n full time steps (H to n+1/2, E to n+1 with the sources, probes)
- * on the grid's stream.  Returns launch errors only; does not synchronise. */
+ * on the grid's stream: replays of captured CUDA graphs of 32, 16, 8, 4 and
+ * 2 steps (each captured on first use), a lone step launched directly.
+ * Returns launch errors only; does not synchronise. */
 int fdtd_step(fdtd_grid *g, int n);
 
 /* Wait for the grid's queued work; reports asynchronous CUDA errors. */
@@ -361,8 +363,9 @@ int fdtd_field_device(fdtd_grid *g, int component, void **dptr, int *row_pitch,
  * (which also adds the oblique wires' currents to E and updates their node
  * charges); when a domain has oblique wires, a launch with a CTA per domain
  * takes their segment currents to t_{n+1/2} beside the step kernel.
- * fdtd_batch_step replays a captured CUDA graph of 32 steps.  The results
- * are those of stepping each grid alone with fdtd_step. */
+ * fdtd_batch_step replays captured CUDA graphs of 32, 16, 8, 4 and 2
+ * steps (each captured on first use) and launches a lone step directly.
+ * The results are those of stepping each grid alone with fdtd_step. */
 typedef struct fdtd_batch fdtd_batch;
 
 /* grids: n_grids finalized grids, all at the same step count, on the current

@@ -24,12 +24,6 @@
 
 namespace {
 
-template <typename T>
-__device__ __forceinline__ __nv_bfloat16 to_bf16(T v);
-template <>
-__device__ __forceinline__ __nv_bfloat16 to_bf16<__nv_bfloat16>(__nv_bfloat16 v) { return v; }
-template <>
-__device__ __forceinline__ __nv_bfloat16 to_bf16<float>(float v) { return __float2bfloat16_rn(v); }
 
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float z)

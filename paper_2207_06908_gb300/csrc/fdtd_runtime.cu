@@ -30,7 +30,6 @@ constexpr double kC0 = 299792458.0;
 constexpr double kEps0 = 8.8541878128e-12;
 constexpr double kMu0 = 1.25663706212e-6;
 constexpr double kR0 = 0.23;        // intrinsic radius of a zero-E line, in cells
-constexpr int kGraphSteps = 32;     // steps per captured graph (even)
 constexpr int kWatchSteps = 1024;   // default period of the divergence watchdog
 
 struct Wire { int axis, p[3], n; double radius; };
@@ -186,7 +185,7 @@ struct fdtd_grid {
     float *osamp_d = nullptr;
     uint8_t *dcls_d = nullptr;
     float *dtable_d = nullptr;
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph[6] = {};    // captured graphs of 2^k steps (k = 1..5) from parity 0
     std::string err;
 };
 
@@ -1331,35 +1330,48 @@ cudaError_t enqueue_watch(fdtd_grid *g, cudaStream_t s)
     return fdtd::launch_finite_check(f, (long long)g->plane * g->nz, g->div_d, 4 * std::max(g->sms, 1), s);
 }
 
-// n steps: 32-step graph replays (captured once) while the parity allows,
-// direct launches otherwise; the watchdog's check after every replay or step
-// that crosses a multiple of its period
+// Capture the graphs of 2, 4, 8, 16 and 32 steps from parity 0 (all at the
+// first call that needs one, so no later call pays a capture)
+int capture_graphs(fdtd_grid *g)
+{
+    nvtxRangePushA("fdtd_step graph capture");
+    cudaError_t e = cudaSuccess;
+    if (!g->cap_stream) e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
+    for (int k = 1; k <= 5 && e == cudaSuccess; ++k) {
+        const int len = 1 << k;
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            for (int t = 0; t < len && e == cudaSuccess; ++t) e = enqueue_step(g, t & 1, g->cap_stream, t, t == len - 1);
+            cudaError_t e2 = cudaStreamEndCapture(g->cap_stream, &graph);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&g->graph[k], graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) g->graph[k] = nullptr;
+    }
+    nvtxRangePop();
+    return e == cudaSuccess ? FDTD_OK : cuda_fail(g, e, "graph capture");
+}
+
+// n steps: graph replays of 32, 16, 8, 4 or 2 steps (from parity 0, the
+// largest that fits) while the parity allows, direct launches otherwise; the
+// watchdog's check after every replay or step that crosses a multiple of its
+// period
 int step_queue(fdtd_grid *g, int n)
 {
     while (n > 0) {
         const long before = g->step;
-        if (g->parity == 0 && n >= kGraphSteps) {
-            if (!g->graph) {
-                nvtxRangePushA("fdtd_step graph capture");
-                cudaError_t e = cudaSuccess;
-                if (!g->cap_stream) e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
-                cudaGraph_t graph = nullptr;
-                if (e == cudaSuccess) e = cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal);
-                if (e == cudaSuccess) {
-                    for (int t = 0; t < kGraphSteps && e == cudaSuccess; ++t)
-                        e = enqueue_step(g, t & 1, g->cap_stream, t, t == kGraphSteps - 1);
-                    cudaError_t e2 = cudaStreamEndCapture(g->cap_stream, &graph);
-                    if (e == cudaSuccess) e = e2;
-                }
-                if (e == cudaSuccess) e = cudaGraphInstantiate(&g->graph, graph, 0);
-                if (graph) cudaGraphDestroy(graph);
-                nvtxRangePop();
-                if (e != cudaSuccess) { g->graph = nullptr; return cuda_fail(g, e, "graph capture"); }
-            }
-            cudaError_t e = cudaGraphLaunch(g->graph, g->stream);
+        if (g->parity == 0 && n >= 2) {
+            int k = 1;
+            while (k < 5 && (2 << k) <= n) ++k;          // largest 2^k <= min(n, 32)
+            const int len = 1 << k;
+            if (!g->graph[k])
+                if (int rc = capture_graphs(g)) return rc;
+            cudaError_t e = cudaGraphLaunch(g->graph[k], g->stream);
             if (e != cudaSuccess) return cuda_fail(g, e, "graph launch");
-            n -= kGraphSteps;
-            g->step += kGraphSteps;
+            n -= len;
+            g->step += len;
         } else {
             cudaError_t e = enqueue_step(g, g->parity, g->stream);
             if (e != cudaSuccess) return cuda_fail(g, e, "step launch");
@@ -2259,7 +2271,8 @@ void fdtd_destroy(fdtd_grid *g)
 {
     if (!g) return;
     if (g->finalized) cudaStreamSynchronize(g->stream);
-    if (g->graph) cudaGraphExecDestroy(g->graph);
+    for (cudaGraphExec_t gr : g->graph)
+        if (gr) cudaGraphExecDestroy(gr);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     g->fk.destroy();
     if (g->own_arena && g->arena) cudaFree(g->arena);
@@ -2290,7 +2303,7 @@ struct fdtd_batch {
     bool has_wires = false;         // some domain has oblique wires
     cudaStream_t cap = nullptr;
     Fork fk;                        // concurrent z-layer launch and oblique-wire gather
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph[6] = {};  // captured graphs of 2^k steps (k = 1..5) from parity 0
     int parity = 0;
     long step = 0;
     std::string err;
@@ -2350,34 +2363,39 @@ cudaError_t batch_enqueue(fdtd_batch *b, int parity, cudaStream_t s)
     return e;
 }
 
-// n batch steps: graph replays while the parity allows, direct launches otherwise
+// n batch steps: graph replays of 32, 16, 8, 4 or 2 steps (each captured
+// once, from parity 0) while the parity allows, direct launches otherwise
 int batch_queue(fdtd_batch *b, int n)
 {
     const int n0 = n;
     while (n > 0) {
-        if (b->parity == 0 && n >= kGraphSteps) {
-            if (!b->graph) {
+        if (b->parity == 0 && n >= 2) {
+            int k = 1;
+            while (k < 5 && (2 << k) <= n) ++k;
+            const int len = 1 << k;
+            if (!b->graph[k]) {
+                // all five sizes at once, so no later call pays a capture
                 nvtxRangePushA("fdtd_batch_step graph capture");
                 cudaError_t e = cudaSuccess;
                 if (!b->cap) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
-                cudaGraph_t graph = nullptr;
-                if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
-                if (e == cudaSuccess) {
-                    for (int t = 0; t < kGraphSteps && e == cudaSuccess; ++t) e = batch_enqueue(b, t & 1, b->cap);
-                    cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
-                    if (e == cudaSuccess) e = e2;
+                for (int kk = 1; kk <= 5 && e == cudaSuccess; ++kk) {
+                    cudaGraph_t graph = nullptr;
+                    e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+                    if (e == cudaSuccess) {
+                        for (int t = 0; t < (1 << kk) && e == cudaSuccess; ++t) e = batch_enqueue(b, t & 1, b->cap);
+                        cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+                        if (e == cudaSuccess) e = e2;
+                    }
+                    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph[kk], graph, 0);
+                    if (graph) cudaGraphDestroy(graph);
+                    if (e != cudaSuccess) b->graph[kk] = nullptr;
                 }
-                if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, graph, 0);
-                if (graph) cudaGraphDestroy(graph);
                 nvtxRangePop();
-                if (e != cudaSuccess) {
-                    b->graph = nullptr;
-                    return bfail(b, FDTD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-                }
+                if (e != cudaSuccess) return bfail(b, FDTD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
             }
-            cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+            cudaError_t e = cudaGraphLaunch(b->graph[k], b->stream);
             if (e != cudaSuccess) return bfail(b, FDTD_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
-            n -= kGraphSteps;
+            n -= len;
         } else {
             cudaError_t e = batch_enqueue(b, b->parity, b->stream);
             if (e != cudaSuccess) return bfail(b, FDTD_ECUDA, std::string("step launch: ") + cudaGetErrorString(e));
@@ -2579,7 +2597,8 @@ void fdtd_batch_destroy(fdtd_batch *b)
 {
     if (!b) return;
     cudaStreamSynchronize(b->stream);
-    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (cudaGraphExec_t gr : b->graph)
+        if (gr) cudaGraphExecDestroy(gr);
     if (b->cap) cudaStreamDestroy(b->cap);
     b->fk.destroy();
     if (b->mem) cudaFree(b->mem);
