@@ -80,9 +80,10 @@
  *     line, R'/L' = G'/C' = nu = sum_u t_u^2 sigma_u / (kappa_u eps0) (the
  *     layer's attenuation of a wave running along the wire; equal ratios
  *     keep its impedance), so its own wave is absorbed with the grid's;
- *     this is a reading, the paper is silent on wires in the layer, and
- *     its t_u^2 weighting is parity unpinned (the pins do not separate it
- *     from |t_u|).  In a
+ *     this is a reading, the paper is silent on wires in the layer; its
+ *     t_u^2 weighting is pinned by isotropy: in a layer stretched alike
+ *     along two axes a wire's wave decays alike in every direction of
+ *     their plane (tests/test_owire_pins.py), which |t_u| would break.  In a
  *     Debye medium the in-cell capacitance takes the medium's dispersion
  *     (the Debye extension of thin wires the paper cites, in this form):
  *     K Q = eps0 eps_inf V + sum_p P_p with K = ln(R/a) / (2 pi dl_m),
