@@ -279,6 +279,20 @@ int fdtd_set_block(fdtd_grid *g, int planes);
  * fdtd_step_noalloc() run no check.  Any time; FDTD_EINVAL if every < 0. */
 int fdtd_set_watchdog(fdtd_grid *g, int every);
 
+/* fdtd_bounds_report: the record of the bounds-checked build (a debugging
+ * aid with no counterpart in the paper: the library compiled with
+ * -DFDTD_BOUNDS, e.g. by _build.build_bounds()).  In that build every
+ * global access of the step and source/probe kernels (field, CPML auxiliary,
+ * source, probe and oblique-wire edge indices) tests its element index
+ * against the array's extent and skips an access outside it.  The
+ * grid's record holds the number of skipped accesses (*count) and the site
+ * of the first (*site: 1 H store, 2 E store, 3 CPML auxiliary store, 4 CPML
+ * auxiliary read, 5 in-kernel source, 6 source edge, 7 probe read, 8 wire
+ * gather, 9 wire scatter).  Synchronises.  Returns FDTD_OK in the
+ * bounds-checked build, 1 in the release build (nothing is checked there and
+ * the record stays zero). */
+int fdtd_bounds_report(fdtd_grid *g, int *site, int *count);
+
 /* Device bytes fdtd_finalize() needs for probe_capacity recorded steps. */
 int fdtd_arena_bytes(const fdtd_grid *g, int probe_capacity, size_t *bytes);
 

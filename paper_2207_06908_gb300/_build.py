@@ -33,22 +33,35 @@ def _deps():
         glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+BOUNDS_LIB = os.path.join(BUILD, "bounds", "libfdtd_gb300.so")
+
+
+def build_bounds(force: bool = False) -> str:
+    """The bounds-checked build (a debugging aid, not the product path):
+    the same sources compiled with -DFDTD_BOUNDS into _build/bounds/, where
+    every global access of the step and source/probe kernels tests its index
+    (fdtd_bounds_report reads the record).  Load it by setting FDTD_LIBRARY
+    to the returned path before the binding loads the library."""
+    return build(force=force, extra=["-DFDTD_BOUNDS"], lib=BOUNDS_LIB)
+
+
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, lib: str = LIB) -> str:
+    if not force and up_to_date(lib):
+        return lib
+    bdir = os.path.dirname(lib)
+    os.makedirs(bdir, exist_ok=True)
     extra = list(extra or [])
     procs = []
     objs = []
     for src in _sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
         cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
@@ -63,11 +76,11 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
             failed.append(cmd[-3])
     if failed:
         raise RuntimeError("nvcc failed for: " + ", ".join(failed))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [NVCC, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

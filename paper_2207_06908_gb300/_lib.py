@@ -38,7 +38,9 @@ class Material(ctypes.Structure):
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """the release library, or the build FDTD_LIBRARY names (the
+    bounds-checked build of _build.build_bounds)"""
+    return os.environ.get("FDTD_LIBRARY") or _build.LIB
 
 
 def load():
@@ -62,6 +64,7 @@ def load():
             "fdtd_add_probe": (I, [P, I, I, I, I, I, I, ip]),
             "fdtd_set_block": (I, [P, I]),
             "fdtd_set_watchdog": (I, [P, I]),
+            "fdtd_bounds_report": (I, [P, ip, ip]),
             "fdtd_arena_bytes": (I, [P, I, ctypes.POINTER(S)]),
             "fdtd_finalize": (I, [P, I, P, S]),
             "fdtd_step": (I, [P, I]),

@@ -38,7 +38,7 @@ __device__ __forceinline__ void wire_gather_body(const EdgeArgs &a, long long n)
 #pragma unroll 4
         for (int q = threadIdx.x; q < n_e; q += blockDim.x) {
             const OEdge ed = w.edge[e_lo + q];
-            prod[q] = ed.wg * a.Ein[ed.comp][ed.idx];
+            prod[q] = in_bounds(ed.idx, a.plane * a.nz, 8, a.bounds) ? ed.wg * a.Ein[ed.comp][ed.idx] : 0.f;
         }
         __syncthreads();
         // L' dl dI/dt = E_s dl - (V_b - V_a) + EMF - R I, centred at t_n (the
@@ -79,6 +79,7 @@ __device__ __forceinline__ void wire_scatter_body(const EdgeArgs &a)
             const int u = base + k * blockDim.x;
             if (u < w.n_scat) {
                 sc[k] = w.scat[u];
+                if (!in_bounds(sc[k].idx, a.plane * a.nz, 9, a.bounds)) sc[k].idx = 0;   // bounds-checked build only
                 ev[k] = a.E[sc[k].comp][sc[k].idx];
             }
         }

@@ -115,6 +115,7 @@ struct StepArgs {
     const float *samples;
     const long long *step;   // device step counter; this step's sample is *step + step_t
     int step_t;
+    int *bounds;             // bounds-checked build: {first site, count} of skipped accesses
 };
 
 // One domain of a step launch, in device memory (the launch reads the
@@ -256,7 +257,27 @@ struct EdgeArgs {
     int step_t;              // this launch serves step *step + step_t
     int advance;             // 1: set *step to that step + 1 when done
     int skip_src;            // the current sources ran in the step kernel
+    int *bounds;             // bounds-checked build: {first site, count} of skipped accesses
 };
+
+// Bounds-checked build (compiled with -DFDTD_BOUNDS, a debugging aid): the
+// global accesses of the step and source/probe kernels test their element
+// index against the array's extent; an access outside it is skipped and
+// counted in bounds[1], the first site recorded in bounds[0].  In the
+// release build the test is the constant true.
+#ifdef FDTD_BOUNDS
+__device__ __forceinline__ bool in_bounds(long long idx, long long n, int site, int *bounds)
+{
+    if (idx >= 0 && idx < n) return true;
+    if (bounds) {
+        atomicCAS(bounds, 0, site);
+        atomicAdd(bounds + 1, 1);
+    }
+    return false;
+}
+#else
+__device__ __forceinline__ bool in_bounds(long long, long long, int, int *) { return true; }
+#endif
 
 // the six field arrays of one state (Ex Ey Ez Hx Hy Hz)
 struct FieldPtrs {

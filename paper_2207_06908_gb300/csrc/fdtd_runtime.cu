@@ -990,6 +990,7 @@ fdtd::StepArgs step_args(const fdtd_grid *g, int parity, int launch)
     a.oy = L.oy;
     a.zxy = L.zxy;
     a.col_order = g->order_d;
+    a.bounds = g->work_d + 6;
     return a;
 }
 
@@ -1037,6 +1038,7 @@ fdtd::EdgeArgs edge_args(const fdtd_grid *g, int parity)
     e.step_t = 0;
     e.advance = 1;
     e.skip_src = 0;
+    e.bounds = g->work_d + 6;
     return e;
 }
 
@@ -1806,6 +1808,22 @@ int fdtd_set_block(fdtd_grid *g, int planes)
     if (planes < 0 || planes > 256) return fail(g, FDTD_EINVAL, "planes per work item outside 0..256");
     g->block = planes;
     return FDTD_OK;
+}
+
+int fdtd_bounds_report(fdtd_grid *g, int *site, int *count)
+{
+    if (int rc = check_open(g, true)) return rc;
+    if (int rc = fdtd_synchronize(g)) return rc;
+    int v[2] = {0, 0};
+    cudaError_t e = cudaMemcpy(v, g->work_d + 6, sizeof v, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(g, e, "bounds record read");
+    if (site) *site = v[0];
+    if (count) *count = v[1];
+#ifdef FDTD_BOUNDS
+    return FDTD_OK;
+#else
+    return 1;                    // not the bounds-checked build: nothing was checked
+#endif
 }
 
 int fdtd_set_watchdog(fdtd_grid *g, int every)

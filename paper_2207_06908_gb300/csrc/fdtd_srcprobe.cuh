@@ -36,6 +36,7 @@ __device__ __forceinline__ void src_probe_body(const EdgeArgs &a, long long n)
         if (sd.hard) continue;
         const float I = q == t ? I0 : (n < sd.n_samples ? __ldg(a.samples + sd.sample_off + n) : 0.f);
         const float add = sd.coef * I;
+        if (!in_bounds(sd.idx, a.plane * a.nz, 6, a.bounds)) continue;
         atomicAdd(a.E[sd.comp] + sd.idx, add);
         // a dispersive edge: the currents already advanced with E^{n+1}
         // before the source; they take its share, be_p times the increment
@@ -52,6 +53,7 @@ __device__ __forceinline__ void src_probe_body(const EdgeArgs &a, long long n)
         const SourceDesc sd = q == t ? sd0 : a.src[q];
         if (!sd.hard) continue;
         const float V = q == t ? I0 : (n < sd.n_samples ? __ldg(a.samples + sd.sample_off + n) : 0.f);
+        if (!in_bounds(sd.idx, a.plane * a.nz, 6, a.bounds)) continue;
         float *e = a.E[sd.comp] + sd.idx;
         const float old = __ldcg(e), v = sd.vcoef * V;
         *e = v;
@@ -70,19 +72,26 @@ __device__ __forceinline__ void src_probe_body(const EdgeArgs &a, long long n)
                 v = __ldcg(a.w.I + pr.i);       // oblique-wire segment current
             } else if (pr.kind == 5) {
                 v = __ldcg(a.w.V + pr.i);       // oblique-wire node: in-cell potential
-            } else if (pr.kind == 2) {
-                v = __ldcg(a.E[pr.axis] + eidx(a, pr.i, pr.j, pr.k));
-            } else if (pr.kind == 3) {
-                v = __ldcg(a.H[pr.axis] + eidx(a, pr.i, pr.j, pr.k));
+            } else if (pr.kind == 2 || pr.kind == 3) {
+                const long long o = eidx(a, pr.i, pr.j, pr.k);
+                if (in_bounds(o, a.plane * a.nz, 7, a.bounds)) v = __ldcg((pr.kind == 2 ? a.E : a.H)[pr.axis] + o);
             } else if (pr.kind == 0) {
                 // consecutive edges along the path's axis, summed in path order
                 const float *Ep = a.E[pr.axis] + eidx(a, pr.i, pr.j, pr.k);
                 const long long st = pr.axis == 0 ? 1 : (pr.axis == 1 ? (long long)a.pitch : a.plane);
 #pragma unroll 4
-                for (int e = 0; e < pr.n_edges; ++e) v -= __ldcg(Ep + e * st) * a.dx;
+                for (int e = 0; e < pr.n_edges; ++e)
+                    if (in_bounds(eidx(a, pr.i, pr.j, pr.k) + e * st, a.plane * a.nz, 7, a.bounds))
+                        v -= __ldcg(Ep + e * st) * a.dx;
             } else {
                 const float *Hx = a.H[0], *Hy = a.H[1], *Hz = a.H[2];
                 const int i = pr.i, j = pr.j, k = pr.k;
+                // the loop reads the edge's cell and its neighbour below along the
+                // two other axes (lowest: one row below for a z edge, one plane
+                // below otherwise)
+                const long long o = eidx(a, i, j, k), lo = o - (pr.axis == 2 ? (long long)a.pitch : a.plane);
+                if (!in_bounds(o, a.plane * a.nz, 7, a.bounds) || !in_bounds(lo, a.plane * a.nz, 7, a.bounds))
+                    continue;
                 if (pr.axis == 2)
                     v = a.dx * ((__ldcg(Hy + eidx(a, i, j, k)) - __ldcg(Hy + eidx(a, i - 1, j, k))) -
                                 (__ldcg(Hx + eidx(a, i, j, k)) - __ldcg(Hx + eidx(a, i, j - 1, k))));

@@ -232,13 +232,13 @@ __device__ __forceinline__ int slab_of(int i, int n, int d) { return i < d ? i :
 // differences, before any store.
 template <bool WRITE>
 __device__ __forceinline__ void cpml2(float &d0, float &d1, const float4 *pr, int s, float o0, float o1,
-                                      float *out0, float *out1, int g)
+                                      float *out0, float *out1, int g, long long n, int *bounds)
 {
-    // g: the cell's element in its axis's compact auxiliary arrays
+    // g: the cell's element in its axis's compact auxiliary arrays (n elements)
     const float4 pv = pr[s];
     const float b = pv.x, c = pv.y, ki = pv.z;
     const float p0 = b * o0 + c * d0, p1 = b * o1 + c * d1;
-    if (WRITE) {
+    if (WRITE && in_bounds(g, n, 3, bounds)) {
         out0[g] = p0;
         out1[g] = p1;
     }
@@ -259,6 +259,11 @@ __device__ __forceinline__ int psi_y(const StepArgs &a, int i, int sy, int k)
 __device__ __forceinline__ int psi_z(const StepArgs &a, int i, int j, int sz)
 {
     return (sz * a.ny + j) * a.pitch + i;
+}
+// elements of the compact x, y, z arrays (extents for the bounds-checked build)
+__device__ __forceinline__ long long psi_n(const StepArgs &a, int u)
+{
+    return u == 0 ? (long long)a.nz * a.ny * a.px : (long long)(2 * a.d) * a.pitch * (u == 1 ? a.nz : a.ny);
 }
 
 // profile row of axis u at E (h = 0) or H (h = 1) positions in the staged
@@ -290,24 +295,31 @@ __device__ __forceinline__ void h_core(const StepArgs &a, const float4 *t, const
         if (L.sx >= 0) {
             const int q = a.pg.xb >> 2;
             const int g = psi_x(a, L.sx, j, k);
-            const float o0 = (STAGED || L.xo >= 0) ? L.base[L.xo] : __ldg(a.psi_in[PSI_HY_X] + g);
-            const float o1 = (STAGED || L.xo >= 0) ? L.base[L.xo + q] : __ldg(a.psi_in[PSI_HZ_X] + g);
-            cpml2<WRITE>(hy_x, hz_x, prow(prof, 0, 1, d2), L.sx, o0, o1, a.psi_out[PSI_HY_X], a.psi_out[PSI_HZ_X], g);
+            const float o0 = (STAGED || L.xo >= 0) ? L.base[L.xo]
+                                    : (in_bounds(g, psi_n(a, 0), 4, a.bounds) ? __ldg(a.psi_in[PSI_HY_X] + g) : 0.f);
+            const float o1 = (STAGED || L.xo >= 0) ? L.base[L.xo + q]
+                                    : (in_bounds(g, psi_n(a, 0), 4, a.bounds) ? __ldg(a.psi_in[PSI_HZ_X] + g) : 0.f);
+            cpml2<WRITE>(hy_x, hz_x, prow(prof, 0, 1, d2), L.sx, o0, o1, a.psi_out[PSI_HY_X], a.psi_out[PSI_HZ_X], g,
+                         psi_n(a, 0), a.bounds);
         }
         if (L.sy >= 0) {
             const int q = a.pg.yb >> 2;
             const int g = psi_y(a, i, L.sy, k);
-            const float o0 = (STAGED || L.yo >= 0) ? L.base[L.yo] : __ldg(a.psi_in[PSI_HX_Y] + g);
-            const float o1 = (STAGED || L.yo >= 0) ? L.base[L.yo + q] : __ldg(a.psi_in[PSI_HZ_Y] + g);
+            const float o0 = (STAGED || L.yo >= 0) ? L.base[L.yo]
+                                    : (in_bounds(g, psi_n(a, 1), 4, a.bounds) ? __ldg(a.psi_in[PSI_HX_Y] + g) : 0.f);
+            const float o1 = (STAGED || L.yo >= 0) ? L.base[L.yo + q]
+                                    : (in_bounds(g, psi_n(a, 1), 4, a.bounds) ? __ldg(a.psi_in[PSI_HZ_Y] + g) : 0.f);
             cpml2<WRITE>(hx_y, hz_y, prow(prof, 1, 1, d2), L.sy, o0, o1, a.psi_out[PSI_HX_Y],
-                       a.psi_out[PSI_HZ_Y], g);
+                         a.psi_out[PSI_HZ_Y], g, psi_n(a, 1), a.bounds);
         }
         if (L.sz >= 0) {
             const int g = psi_z(a, i, j, L.sz);
-            const float o0 = (STAGED || L.zo >= 0) ? L.base[L.zo] : __ldg(a.psi_in[PSI_HX_Z] + g);
-            const float o1 = (STAGED || L.zo >= 0) ? L.base[L.zo + H_COMP / 4] : __ldg(a.psi_in[PSI_HY_Z] + g);
+            const float o0 = (STAGED || L.zo >= 0) ? L.base[L.zo]
+                                    : (in_bounds(g, psi_n(a, 2), 4, a.bounds) ? __ldg(a.psi_in[PSI_HX_Z] + g) : 0.f);
+            const float o1 = (STAGED || L.zo >= 0) ? L.base[L.zo + H_COMP / 4]
+                                    : (in_bounds(g, psi_n(a, 2), 4, a.bounds) ? __ldg(a.psi_in[PSI_HY_Z] + g) : 0.f);
             cpml2<WRITE>(hx_z, hy_z, prow(prof, 2, 1, d2), L.sz, o0, o1, a.psi_out[PSI_HX_Z],
-                       a.psi_out[PSI_HY_Z], g);
+                         a.psi_out[PSI_HY_Z], g, psi_n(a, 2), a.bounds);
         }
     }
     const float4 db = t[0];
@@ -333,16 +345,17 @@ __device__ __forceinline__ void e_core(const StepArgs &a, const float4 *t, const
         if (L.sx >= 0) {
             const int q = a.pg.xb >> 2;
             cpml2<true>(ey_x, ez_x, prow(prof, 0, 0, d2), L.sx, L.base[L.xo + 2 * q], L.base[L.xo + 3 * q],
-                        a.psi_out[PSI_EY_X], a.psi_out[PSI_EZ_X], psi_x(a, L.sx, j, k));
+                        a.psi_out[PSI_EY_X], a.psi_out[PSI_EZ_X], psi_x(a, L.sx, j, k), psi_n(a, 0), a.bounds);
         }
         if (L.sy >= 0) {
             const int q = a.pg.yb >> 2;
             cpml2<true>(ex_y, ez_y, prow(prof, 1, 0, d2), L.sy, L.base[L.yo + 2 * q], L.base[L.yo + 3 * q],
-                        a.psi_out[PSI_EX_Y], a.psi_out[PSI_EZ_Y], psi_y(a, i, L.sy, k));
+                        a.psi_out[PSI_EX_Y], a.psi_out[PSI_EZ_Y], psi_y(a, i, L.sy, k), psi_n(a, 1), a.bounds);
         }
         if (L.sz >= 0)
             cpml2<true>(ex_z, ey_z, prow(prof, 2, 0, d2), L.sz, L.base[L.zeo],
-                        L.base[L.zeo + PE_BYTES / 4], a.psi_out[PSI_EX_Z], a.psi_out[PSI_EY_Z], psi_z(a, i, j, L.sz));
+                        L.base[L.zeo + PE_BYTES / 4], a.psi_out[PSI_EX_Z], a.psi_out[PSI_EY_Z], psi_z(a, i, j, L.sz),
+                        psi_n(a, 2), a.bounds);
     }
     const float4 ca = t[1], cb = t[2];
     ex1 = ca.x * ex + cb.x * (ex_y - ex_z);
@@ -364,6 +377,7 @@ __device__ __forceinline__ void add_sources(const StepArgs &a, uint32_t m)
         m &= m - 1;
         const SourceDesc &sd = a.src[q];
         const float I = n < sd.n_samples ? __ldg(a.samples + sd.sample_off + n) : 0.f;
+        if (!in_bounds(sd.idx, (long long)a.plane * a.nz, 5, a.bounds)) continue;
         float *e = a.Eout[sd.comp] + sd.idx;
         *e = __fadd_rn(__ldcg(e), __fmul_rn(sd.coef, I));
     }
@@ -628,9 +642,11 @@ __device__ __forceinline__ bool run_item(const Cons<NH> &C, const Item &it, uint
                     h_core<CPML, true, true>(a, C.coef(cl[r]), C.prof, L, i, j, k, ecur[0][r], ecur[1][r],
                                  ecur[2][r], ek.e(1, row, lx + 1), ek.e(2, row, lx + 1), ex_y1, ez_y1, enx[0][r],
                                  enx[1][r], hk.h(0, row, lx), hk.h(1, row, lx), hk.h(2, row, lx), hx, hy, hz);
-                    a.Hout[0][g] = hx;
-                    a.Hout[1][g] = hy;
-                    a.Hout[2][g] = hz;
+                    if (in_bounds(g, (long long)a.plane * a.nz, 1, a.bounds)) {
+                        a.Hout[0][g] = hx;
+                        a.Hout[1][g] = hy;
+                        a.Hout[2][g] = hz;
+                    }
                 }
                 hnw[0][r] = hx;
                 hnw[1][r] = hy;
@@ -682,9 +698,11 @@ __device__ __forceinline__ bool run_item(const Cons<NH> &C, const Item &it, uint
                     e_core<CPML>(a, C.coef(cl[r]), C.prof, L, i, j, k, ecur[0][r], ecur[1][r], ecur[2][r],
                                  hnw[0][r], hnw[1][r], hnw[2][r], hz_ym, hx_ym, C.hn(hb, 2, row, lx - 1),
                                  C.hn(hb, 1, row, lx - 1), hxp[r], hyp[r], ex1, ey1, ez1);
-                    a.Eout[0][g] = ex1;
-                    a.Eout[1][g] = ey1;
-                    a.Eout[2][g] = ez1;
+                    if (in_bounds(g, (long long)a.plane * a.nz, 2, a.bounds)) {
+                        a.Eout[0][g] = ex1;
+                        a.Eout[1][g] = ey1;
+                        a.Eout[2][g] = ez1;
+                    }
                 }
                 hxp[r] = hnw[0][r];
                 hyp[r] = hnw[1][r];
