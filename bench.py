@@ -61,6 +61,8 @@ def args_parse():
                     help="leave out the batch and surrogate sub-records of the default line")
     ap.add_argument("--n", type=int, default=256,
                     help="grid edge; 256 is the workload, smaller grids only for profiling")
+    ap.add_argument("--domains", type=int, default=256,
+                    help="domains of the batch workloads; 256 is the workload, fewer only for profiling")
     ap.add_argument("--cpu-seconds", type=float, default=20.0,
                     help="bound on the oracle's timed CPU work")
     return ap.parse_args()
@@ -287,15 +289,16 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
-def batch_record(K, Wm, inclined=False):
+def batch_record(K, Wm, inclined=False, n_domains=256):
     """256 grounding-rod domains (side 48..128, 8-cell CPML) advanced by the
     batched engine for K timed steps after Wm untimed ones; value = domains
     finished per second (K steps of the 2000 each domain runs).  inclined:
-    rods leaning 15..60 degrees (oblique wires joined to the risers)."""
+    rods leaning 15..60 degrees (oblique wires joined to the risers).
+    n_domains: the first n of the 256 domains (fewer only for profiling)."""
     import torch
     from paper_2207_06908_gb300 import _build, fdtd, grounding, workloads as W
     _build.build()
-    scs = (W.config4_inclined if inclined else W.config4)(n_steps=K + Wm)
+    scs = (W.config4_inclined if inclined else W.config4)(n_steps=K + Wm)[:n_domains]
     t0 = time.perf_counter()
     blocks = {}
     for sc in scs:
@@ -349,7 +352,7 @@ def run_batch_bench(a, inclined=False):
     from paper_2207_06908_gb300 import workloads as W
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     K = a.steps if a.steps != 4000 else W.GROUND_STEPS
-    rec = batch_record(K, max(3, a.warmup), inclined)
+    rec = batch_record(K, max(3, a.warmup), inclined, a.domains)
     line = dict(rec)
     line.update({"n_gpus": 1, "scaling": "weak", "vs_baseline": None})
     print(json.dumps(line), flush=True)
