@@ -405,22 +405,20 @@ def surrogate_record(K, Wm, cpu_seconds=10.0, n_eval=512, e2e=True, cpu=True):
     clocks = clk.stop()
     ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
     s_sur = B * K / (ms / 1e3)
-    # dominant kernel: the 256 -> 512 output layer, timed alone per launch
+    # dominant kernel: the waveform network in one launch, timed alone
     net = sur.main
-    h3 = torch.empty((B, 256), dtype=torch.bfloat16, device="cuda")
     y = torch.empty((B, 512), dtype=torch.float32, device="cuda")
-    h3.normal_()
     lay = []
     for _ in range(20):
         flush()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        mlp.forward(h3, net.Wb[3], net.b[3], mlp.ACT_NONE, None, y, None)
+        mlp.net_forward(x_dev, net.sizes, net.acts, net._image, net.b, y, S.Y_UNIT)
         e1.record(stream)
         lay.append((e0, e1))
     torch.cuda.synchronize()
     lay_ms = sum(e0.elapsed_time(e1) for e0, e1 in lay) / len(lay)
-    flops_layer = 2.0 * B * 256 * 512
+    flops_layer = 2.0 * B * sum(k * n for k, n in zip(net.sizes[:-1], net.sizes[1:]))
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             tpeak, tsrc = float(json.load(f)["bf16_tflops"]), "measured"
@@ -485,8 +483,9 @@ def surrogate_record(K, Wm, cpu_seconds=10.0, n_eval=512, e2e=True, cpu=True):
                                "mean_with_fallback": float(final.mean())},
            "roofline": {"bound": "tensor", "achieved": tach, "peak": tpeak, "unit": "TFLOP/s",
                         "frac": tach / tpeak, "traffic": None, "peak_source": tsrc,
-                        "kernel": f"gemm_kernel, {B}x256 @ 256x512 output layer, {lay_ms * 1e3:.1f} us"},
-           "e2e": e2e_rec, "cpu_baseline": cpu_rec, "clocks": clocks, "gpu_launches": 8 * K}
+                        "kernel": f"net_forward_kernel, the 6-256-256-256-512 network on {B} rows in one "
+                                  f"launch (128 four-CTA clusters), {lay_ms * 1e3:.1f} us"},
+           "e2e": e2e_rec, "cpu_baseline": cpu_rec, "clocks": clocks, "gpu_launches": 2 * K}
     del replay
     return rec
 

@@ -24,6 +24,8 @@
 #ifndef FDTD_GB300_MLP_H
 #define FDTD_GB300_MLP_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -77,6 +79,27 @@ int fdtd_mlp_scale_rows(float *y, const float *scale, int rows, int cols, void *
  * network kernel ran out since the last call: FDTD_OK, FDTD_ETIMEOUT (-6,
  * the flag is then cleared) or FDTD_ECUDA. */
 int fdtd_mlp_check(void *cuda_stream);
+
+/* A whole network in one launch (inference).  Layers l = 0 .. n_layers-1
+ * map sizes[l] inputs to sizes[l+1] outputs, y = act_l(x wt_l^T + bias_l);
+ * the last layer's output is multiplied by out_scale and stored as FP32.
+ * Limits: 1 <= n_layers <= 6, every layer input sizes[0 .. n_layers-1] <=
+ * 256, and the weights must fit the kernel's shared memory (each CTA of a
+ * four-CTA cluster holds a quarter of every layer's rows: about 130 KB for
+ * 6 -> 256 -> 256 -> 256 -> 512); otherwise FDTD_EINVAL.
+ * The weights enter as a packed image (device memory, 16-byte aligned,
+ * fdtd_mlp_net_pack_bytes bytes, written by fdtd_mlp_net_pack from the
+ * BF16 wt_l [sizes[l+1] x sizes[l]]; re-pack after the weights change).
+ * x: rows x sizes[0] FP32 (rounded to BF16 on load); y: rows x
+ * sizes[n_layers] FP32; acts: host array of n_layers activation codes;
+ * bias: host array of n_layers device pointers (NULL array or entry = no
+ * bias).  Each output equals, bit for bit, the chain of fdtd_mlp_forward
+ * layers (BF16 hidden activations) followed by the scaling.  Its waits are
+ * bounded as in fdtd_mlp_forward (fdtd_mlp_check reports a timeout). */
+int fdtd_mlp_net_pack_bytes(const int *sizes, int n_layers, size_t *bytes);
+int fdtd_mlp_net_pack(const int *sizes, int n_layers, const void *const *wt, void *image, void *cuda_stream);
+int fdtd_mlp_net_forward(const float *x, int rows, const int *sizes, int n_layers, const int *acts,
+                         const void *image, const float *const *bias, float out_scale, float *y, void *cuda_stream);
 
 /* FP32 -> BF16 conversion (round to nearest even) of count elements. */
 int fdtd_mlp_to_bf16(const float *src, void *dst, int count, void *cuda_stream);

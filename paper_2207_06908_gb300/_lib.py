@@ -110,6 +110,9 @@ def load():
             "fdtd_mlp_scale_rows": (I, [P, P, I, I, P]),
             "fdtd_mlp_to_bf16": (I, [P, P, I, P]),
             "fdtd_mlp_check": (I, [P]),
+            "fdtd_mlp_net_pack_bytes": (I, [ip, I, ctypes.POINTER(S)]),
+            "fdtd_mlp_net_pack": (I, [ip, I, ctypes.POINTER(P), P, P]),
+            "fdtd_mlp_net_forward": (I, [P, I, ip, I, ip, P, ctypes.POINTER(P), ctypes.c_float, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)

@@ -598,6 +598,279 @@ cudaError_t tc_forward(const TA *x, int rows, int K, const __nv_bfloat16 *wt, co
     return cudaGetLastError();
 }
 
+// ---- whole network in one launch: a cluster of four CTAs per 128 rows ------
+// Each CTA of a cluster owns a quarter of every layer's outputs (ns columns,
+// a multiple of 16) and keeps its slices of all weight matrices resident in
+// shared memory (one bulk copy per layer from a packed image, issued at
+// launch).  Per layer one thread issues the MMA chain (A = the cluster's
+// shared activations of the 128 rows, B = the CTA's weight slice, D = TMEM),
+// the eight warps read the accumulator back (bias, activation, BF16) and
+// store their columns, in the next layer's K-major core-matrix layout,
+// into the activation buffer of every CTA of the cluster (distributed
+// shared memory); two cluster barriers per layer separate the MMAs that
+// read a buffer from the stores that overwrite it.  The last layer writes
+// FP32 rows to global memory.  The arithmetic of each output element is the
+// per-layer kernel's (same BF16 roundings, same K = 16 MMA steps, bias then
+// activation in FP32), so the two paths agree bit for bit.
+constexpr int NF_MAX_LAYERS = 6;
+constexpr int NF_CLUSTER = 4;
+constexpr int NF_THREADS = 256;                      // 8 warps: 4 TMEM lane groups x 2 column halves
+constexpr int NF_SMEM_MAX = 227 * 1024;
+
+struct NetArgs {
+    int n_layers;
+    int k[NF_MAX_LAYERS + 1];      // sizes: k[0] inputs, k[l + 1] outputs of layer l
+    int kp[NF_MAX_LAYERS + 1];     // sizes rounded up to 16 (the K extent of the layer they feed)
+    int ns[NF_MAX_LAYERS];         // output columns of layer l per cluster rank (multiple of 16)
+    long long woff[NF_MAX_LAYERS]; // byte offset of layer l's rank-0 slice in the packed image
+    int wsm[NF_MAX_LAYERS];        // byte offset of layer l's slice in shared memory
+    int act[NF_MAX_LAYERS];
+    const float *bias[NF_MAX_LAYERS];
+    const char *image;
+    int act_bytes;                 // activation buffer: 128 rows x the largest K, BF16
+    int tmem_cols;
+    float out_scale;
+};
+
+// byte offset of element (n, k) of a rows x kp matrix in the K-major
+// core-matrix layout: 8 x 8 blocks of 128 bytes, k blocks adjacent
+__host__ __device__ __forceinline__ long long core_off(int n, int k, int kp)
+{
+    return (long long)(n >> 3) * (kp * 16) + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
+}
+
+// the image: per layer, per rank, the rank's ns x kp slice of wt (zero
+// outside n x k) in the core-matrix layout
+__global__ void net_pack_kernel(const __nv_bfloat16 *__restrict__ wt, int n, int k, int ns, int kp, char *dst)
+{
+    const long long per = (long long)ns * kp, total = per * NF_CLUSTER;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(q / per);
+        const int nl = (int)((q - r * per) / kp), kk = (int)(q - r * per - (long long)nl * kp);
+        const int ng = r * ns + nl;
+        const __nv_bfloat16 v = (ng < n && kk < k) ? wt[(long long)ng * k + kk] : __float2bfloat16_rn(0.f);
+        *reinterpret_cast<__nv_bfloat16 *>(dst + r * per * 2 + core_off(nl, kk, kp)) = v;
+    }
+}
+
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t addr, uint32_t (&v)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(NF_THREADS, 1)
+    net_forward_kernel(const float *__restrict__ x, int rows, const __grid_constant__ NetArgs P, float *__restrict__ y)
+{
+    extern __shared__ __align__(1024) char smraw[];
+    char *sm = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
+    uint64_t *wbar = reinterpret_cast<uint64_t *>(sm);        // weight slices landed
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + 8);    // a layer's MMA chain done
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + 16);
+    char *act = sm + 1024;
+    char *wsm = act + P.act_bytes;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t rank = cluster_rank();
+    const int m0 = (blockIdx.x / NF_CLUSTER) * TC_M;
+    const int L = P.n_layers;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(P.tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 32) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(wbar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 32) {
+        // this CTA's weight slices, one bulk copy per layer
+        uint32_t bytes = 0;
+        for (int l = 0; l < L; ++l) bytes += (uint32_t)P.ns[l] * P.kp[l] * 2;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(wbar)), "r"(bytes)
+                     : "memory");
+        for (int l = 0; l < L; ++l) {
+            const uint32_t sz = (uint32_t)P.ns[l] * P.kp[l] * 2;
+            const char *src = P.image + P.woff[l] + (long long)rank * sz;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_u32(wsm + P.wsm[l])),
+                "l"(src), "r"(sz), "r"(smem_u32(wbar))
+                : "memory");
+        }
+    }
+    // the 128 input rows, rounded to BF16, as layer 0's A operand (every CTA
+    // of the cluster stages its own copy)
+    {
+        const int kgs = P.kp[0] / 8;
+        for (int q = tid; q < TC_M * kgs; q += NF_THREADS) {
+            const int r = q / kgs, g = q - r * kgs;
+            *reinterpret_cast<uint4 *>(act + core_off(r, g * 8, P.kp[0])) = load8(x, rows, P.k[0], m0 + r, g * 8, false);
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    cluster_sync();                 // every CTA of the cluster runs (its shared memory may be written)
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    bool ok = true;
+    if (tid == 0) ok = mbar_wait_bounded(smem_u32(wbar), 0);
+    ok = __syncthreads_and(ok);
+    const bool loaded = ok;
+    int fail = -1;                  // layer whose MMA chain a wait gave up on
+    if (!ok && tid == 0) atomicExch(&g_mlp_err, 1);
+    const int lg = warp & 3, half = warp >> 2, r = lg * 32 + lane;   // this thread's TMEM lane = tile row
+    uint32_t dst[NF_CLUSTER];       // the activation buffer in each CTA of the cluster
+    for (int c = 0; c < NF_CLUSTER; ++c)
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(dst[c]) : "r"(smem_u32(act)), "r"(c));
+    for (int l = 0; l < L; ++l) {
+        const int ns = P.ns[l], kp = P.kp[l], N = P.k[l + 1];
+        const bool last = l == L - 1;
+        if (ok && tid == 0) {
+            const uint32_t idesc =
+                (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(ns >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+            const uint32_t a0 = smem_u32(act), b0 = smem_u32(wsm + P.wsm[l]), sbo = (uint32_t)kp * 16;
+            // the activations stored through the generic proxy (this CTA's
+            // or, across the cluster barrier, the other CTAs') are read by
+            // the tensor cores' asynchronous proxy
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            for (int k0 = 0; k0 < kp; k0 += 16) {
+                const uint64_t ad = smem_desc(a0 + k0 * 16, 128, sbo), bd = smem_desc(b0 + k0 * 16, 128, sbo);
+                const uint32_t acc = k0 > 0 ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(mbar))
+                         : "memory");
+        }
+        bool done = !ok || mbar_wait_bounded(smem_u32(mbar), (uint32_t)(l & 1));
+        done = __syncthreads_and(done);
+        if (ok && !done) {
+            ok = false;
+            fail = l;
+            if (tid == 0) atomicExch(&g_mlp_err, 1);
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int c0 = half * (ns / 2), n0 = (int)rank * ns;
+        if (!last) {
+            cluster_sync();         // every CTA's MMAs of this layer have read its activation buffer
+            const int kpn = P.kp[l + 1];
+            for (int c = c0; ok && c < c0 + ns / 2; c += 8) {
+                const int nb = n0 + c;          // first of the 8 columns (a multiple of 8)
+                if (nb >= kpn) break;
+                uint32_t v[8];
+                tmem_ld8(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)c, v);
+                float f[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int n = nb + j;
+                    const float z = __uint_as_float(v[j]) + ((P.bias[l] && n < N) ? __ldg(P.bias[l] + n) : 0.f);
+                    f[j] = P.act[l] == FDTD_ACT_GELU ? gelu(z) : z;
+                }
+                const uint4 q = make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
+                const uint32_t off = (uint32_t)core_off(r, nb, kpn);
+                for (int t = 0; t < NF_CLUSTER; ++t)
+                    asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(dst[t] + off), "r"(q.x),
+                                 "r"(q.y), "r"(q.z), "r"(q.w)
+                                 : "memory");
+            }
+            asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            cluster_sync();         // the next layer's A operand is complete in every CTA
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        } else if (ok) {
+            const int m = m0 + r;
+            for (int c = c0; c < c0 + ns / 2; c += 8) {
+                const int nb = n0 + c;
+                if (nb >= N) break;
+                uint32_t v[8];
+                tmem_ld8(tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)c, v);
+                if (m >= rows) continue;
+                float f[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int n = nb + j;
+                    const float z = __uint_as_float(v[j]) + ((P.bias[l] && n < N) ? __ldg(P.bias[l] + n) : 0.f);
+                    f[j] = (P.act[l] == FDTD_ACT_GELU ? gelu(z) : z) * P.out_scale;
+                }
+                float *o = y + (long long)m * N + nb;
+                if (nb + 8 <= N && (N & 3) == 0 && (reinterpret_cast<uintptr_t>(y) & 15) == 0) {
+                    reinterpret_cast<float4 *>(o)[0] = make_float4(f[0], f[1], f[2], f[3]);
+                    reinterpret_cast<float4 *>(o)[1] = make_float4(f[4], f[5], f[6], f[7]);
+                } else {
+                    for (int j = 0; j < 8 && nb + j < N; ++j) o[j] = f[j];
+                }
+            }
+        }
+    }
+    // copies or an MMA chain still in flight after a wait gave up: wait
+    // (bounded) before the shared memory and TMEM are given back
+    if (tid == 0 && !loaded) mbar_wait_bounded(smem_u32(wbar), 0);
+    if (tid == 0 && fail >= 0) mbar_wait_bounded(smem_u32(mbar), (uint32_t)(fail & 1));
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P.tmem_cols) : "memory");
+    }
+    cluster_sync();                 // no CTA leaves while another may still address its shared memory
+}
+
+// layout of a network's packed image and of the kernel's shared memory;
+// false when the sizes are outside what the kernel supports
+bool net_layout(const int *sizes, int L, NetArgs &P, size_t &image_bytes, int &smem)
+{
+    if (!sizes || L < 1 || L > NF_MAX_LAYERS) return false;
+    P = NetArgs{};
+    P.n_layers = L;
+    int kmax = 0, nsmax = 0;
+    long long off = 0;
+    int wbytes = 0;
+    for (int l = 0; l <= L; ++l) {
+        if (sizes[l] < 1) return false;
+        P.k[l] = sizes[l];
+        P.kp[l] = (sizes[l] + 15) / 16 * 16;
+    }
+    for (int l = 0; l < L; ++l) {
+        if (P.k[l] > TC_KMAX) return false;                 // every layer's K fits the activation buffer
+        const int q = (P.k[l + 1] + NF_CLUSTER - 1) / NF_CLUSTER;
+        P.ns[l] = (q + 15) / 16 * 16;
+        if (P.ns[l] > 256) return false;                    // one MMA N extent
+        P.woff[l] = off;
+        P.wsm[l] = wbytes;
+        off += (long long)NF_CLUSTER * P.ns[l] * P.kp[l] * 2;
+        wbytes += P.ns[l] * P.kp[l] * 2;
+        kmax = std::max(kmax, P.kp[l]);
+        nsmax = std::max(nsmax, P.ns[l]);
+    }
+    P.act_bytes = TC_M * kmax * 2;
+    P.tmem_cols = 32;
+    while (P.tmem_cols < nsmax) P.tmem_cols *= 2;
+    image_bytes = (size_t)off;
+    smem = 1024 + 1024 + P.act_bytes + wbytes;
+    return smem <= NF_SMEM_MAX;
+}
+
 int rc(cudaError_t e) { return e == cudaSuccess ? FDTD_OK : FDTD_ECUDA; }
 int grid1d(long long n) { return (int)std::min<long long>((n + 255) / 256, 4096); }
 
@@ -624,6 +897,81 @@ int fdtd_mlp_forward(const void *x, int x_is_bf16, int rows, int k, const void *
     if (x_is_bf16)
         return rc(tc_grad(static_cast<const __nv_bfloat16 *>(x), k, 1, w, 1, k, rows, n, k, ep, s));
     return rc(tc_grad(static_cast<const float *>(x), k, 1, w, 1, k, rows, n, k, ep, s));
+}
+
+int fdtd_mlp_net_pack_bytes(const int *sizes, int n_layers, size_t *bytes)
+{
+    NetArgs P;
+    size_t b = 0;
+    int smem = 0;
+    if (!bytes || !net_layout(sizes, n_layers, P, b, smem)) return FDTD_EINVAL;
+    *bytes = b;
+    return FDTD_OK;
+}
+
+int fdtd_mlp_net_pack(const int *sizes, int n_layers, const void *const *wt, void *image, void *cuda_stream)
+{
+    NetArgs P;
+    size_t b = 0;
+    int smem = 0;
+    if (!wt || !image || (reinterpret_cast<uintptr_t>(image) & 15) || !net_layout(sizes, n_layers, P, b, smem))
+        return FDTD_EINVAL;
+    for (int l = 0; l < n_layers; ++l)
+        if (!wt[l]) return FDTD_EINVAL;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    for (int l = 0; l < n_layers; ++l) {
+        const long long total = (long long)NF_CLUSTER * P.ns[l] * P.kp[l];
+        net_pack_kernel<<<grid1d(total), 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(wt[l]), P.k[l + 1], P.k[l],
+                                                      P.ns[l], P.kp[l], static_cast<char *>(image) + P.woff[l]);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return FDTD_ECUDA;
+    }
+    return FDTD_OK;
+}
+
+int fdtd_mlp_net_forward(const float *x, int rows, const int *sizes, int n_layers, const int *acts,
+                         const void *image, const float *const *bias, float out_scale, float *y, void *cuda_stream)
+{
+    NetArgs P;
+    size_t b = 0;
+    int smem = 0;
+    if (!x || !y || !image || !acts || rows < 0 || (reinterpret_cast<uintptr_t>(image) & 15) ||
+        !net_layout(sizes, n_layers, P, b, smem))
+        return FDTD_EINVAL;
+    for (int l = 0; l < n_layers; ++l) {
+        if (acts[l] != FDTD_ACT_NONE && acts[l] != FDTD_ACT_GELU) return FDTD_EINVAL;
+        P.act[l] = acts[l];
+        P.bias[l] = bias ? bias[l] : nullptr;
+    }
+    if (rows == 0) return FDTD_OK;
+    P.image = static_cast<const char *>(image);
+    P.out_scale = out_scale;
+    static std::mutex mu;
+    static int ready_smem[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev >= 64) return FDTD_ECUDA;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (ready_smem[dev] < smem) {
+            e = cudaFuncSetAttribute(net_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, NF_SMEM_MAX);
+            if (e != cudaSuccess) return FDTD_ECUDA;
+            ready_smem[dev] = NF_SMEM_MAX;
+        }
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(((rows + TC_M - 1) / TC_M) * NF_CLUSTER));
+    cfg.blockDim = dim3(NF_THREADS);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = (cudaStream_t)cuda_stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = NF_CLUSTER;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return rc(cudaLaunchKernelEx(&cfg, net_forward_kernel, x, rows, P, y));
 }
 
 int fdtd_mlp_check(void *cuda_stream)

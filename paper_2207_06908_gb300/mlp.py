@@ -82,3 +82,34 @@ def check():
     """synchronise the current stream; raise if a bounded wait inside a
     network kernel ran out since the last check"""
     _check(_lib.load().fdtd_mlp_check(_stream()), "mlp kernels")
+
+
+def _ints(v):
+    return (ctypes.c_int * len(v))(*[int(a) for a in v])
+
+
+def net_pack_bytes(sizes):
+    """bytes of the packed weight image of a network with these layer sizes"""
+    lib = _lib.load()
+    n = ctypes.c_size_t(0)
+    _check(lib.fdtd_mlp_net_pack_bytes(_ints(sizes), len(sizes) - 1, ctypes.byref(n)), "mlp_net_pack_bytes")
+    return n.value
+
+
+def net_pack(sizes, wts, image):
+    """pack the BF16 weights wts[l] [sizes[l+1], sizes[l]] into image (a
+    uint8 CUDA tensor of net_pack_bytes(sizes) bytes)"""
+    lib = _lib.load()
+    L = len(sizes) - 1
+    ptrs = (ctypes.c_void_p * L)(*[w.data_ptr() for w in wts])
+    _check(lib.fdtd_mlp_net_pack(_ints(sizes), L, ptrs, _p(image), _stream()), "mlp_net_pack")
+
+
+def net_forward(x, sizes, acts, image, biases, y, out_scale=1.0):
+    """y = the whole network on x (FP32 [rows, sizes[0]]) in one launch;
+    y FP32 [rows, sizes[-1]]"""
+    lib = _lib.load()
+    L = len(sizes) - 1
+    bp = (ctypes.c_void_p * L)(*[(b.data_ptr() if b is not None else None) for b in biases])
+    _check(lib.fdtd_mlp_net_forward(_p(x), x.shape[0], _ints(sizes), L, _ints(acts), _p(image), bp,
+                                    float(out_scale), _p(y), _stream()), "mlp_net_forward")

@@ -96,6 +96,8 @@ class Network:
         self.g = [torch.zeros_like(p) for p in self.params]
         self.t = 0
         self._bufs = {}
+        self._image, self._image_t = None, None     # packed weights of forward_fused, and their Adam step
+        self._fused_out = {}
 
     def _buffers(self, rows):
         """activation and gradient buffers, one set per row count and kept
@@ -128,6 +130,25 @@ class Network:
                              self.out if last else None, self.z[l] if keep else None)
             h = None if last else self.hb[l]
         return self.out
+
+    def forward_fused(self, x, out_scale=1.0):
+        """Inference: the whole network in one launch (mlp.net_forward), bit
+        for bit the per-layer chain, the output times out_scale.  x: [rows,
+        k0] FP32.  Returns an FP32 [rows, n_last] buffer kept per row count
+        (overwritten by the next call).  The packed weight image is rebuilt
+        when Adam has changed the weights since it was packed."""
+        torch = self.torch
+        if self._image_t != self.t:
+            if self._image is None:
+                self._image = torch.empty(self.mlp.net_pack_bytes(self.sizes), dtype=torch.uint8, device="cuda")
+            self.mlp.net_pack(self.sizes, self.Wb, self._image)
+            self._image_t = self.t
+        rows = x.shape[0]
+        if rows not in self._fused_out:
+            self._fused_out[rows] = torch.empty((rows, self.sizes[-1]), dtype=torch.float32, device="cuda")
+        y = self._fused_out[rows]
+        self.mlp.net_forward(x, self.sizes, self.acts, self._image, self.b, y, out_scale)
+        return y
 
     def backward(self, dy):
         """gradients of every parameter from dL/d(output) [rows, n_last]"""
@@ -235,21 +256,17 @@ class Surrogate:
     def __init__(self, main, head, threshold, meta=None):
         self.main, self.head, self.threshold = main, head, float(threshold)
         self.meta = dict(meta or {})
-        self._units = {}                # output scale per batch size (kept: graphs point at them)
         self._graphs = {}
+        self._graphs_t = None           # the networks' Adam steps when the graphs were captured
 
     # -- inference ---------------------------------------------------------
     def predict_device(self, f_dev):
         """f_dev: encoded features [B, 6] on the device.  Returns device
-        tensors (waveforms [B, 512] in ohm, predicted relative error [B])."""
-        import torch
-        from . import mlp
-        B = f_dev.shape[0]
-        if B not in self._units:
-            self._units[B] = torch.full((B,), Y_UNIT, dtype=torch.float32, device="cuda")
-        wave = self.main.forward(f_dev, keep=False)
-        mlp.scale_rows(wave, self._units[B])
-        log_err = self.head.forward(f_dev, keep=False)
+        tensors (waveforms [B, 512] in ohm, predicted relative error [B]):
+        each network in one launch, the waveform scaled to ohm in its
+        output layer."""
+        wave = self.main.forward_fused(f_dev, out_scale=Y_UNIT)
+        log_err = self.head.forward_fused(f_dev)
         return wave, log_err.reshape(-1)
 
     def predict_graph(self, batch):
@@ -258,6 +275,11 @@ class Surrogate:
         encoded features into the input buffer, call replay(), read the
         outputs (device tensors, overwritten by the next replay)."""
         import torch
+        if self._graphs_t != (self.main.t, self.head.t):
+            # weights changed since the capture: the graphs would replay the
+            # packed images of the old ones
+            self._graphs = {}
+            self._graphs_t = (self.main.t, self.head.t)
         if batch not in self._graphs:
             x = torch.zeros((batch, N_IN), dtype=torch.float32, device="cuda")
             side = torch.cuda.Stream()

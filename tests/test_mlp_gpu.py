@@ -193,3 +193,73 @@ def test_forward_layer_fp32_input(env):
     mlp.check()
     _, _, y = M.forward(M.bf16(x), [(W, b)], ["gelu"])
     assert rel(yf.cpu().numpy(), y) <= 1e-4
+
+
+def _layer_chain(torch, mlp, x, Wd, bd, acts, out_scale):
+    """the per-layer path: BF16 hidden activations, FP32 output, then scaled"""
+    h = x
+    for l, (w, b) in enumerate(zip(Wd, bd)):
+        n = w.shape[0]
+        if l < len(Wd) - 1:
+            nxt = torch.empty((x.shape[0], n), dtype=torch.bfloat16, device="cuda")
+            mlp.forward(h, w, b, acts[l], nxt, None, None)
+            h = nxt
+        else:
+            y = torch.empty((x.shape[0], n), dtype=torch.float32, device="cuda")
+            mlp.forward(h, w, b, acts[l], None, y, None)
+    return (y.cpu().numpy() * np.float32(out_scale)).astype(np.float32)
+
+
+@pytest.mark.parametrize("sizes,acts,rows,scale", [
+    ([6, 256, 256, 256, 512], [1, 1, 1, 0], 4096, 1000.0),   # the waveform network at the benchmark's batch
+    ([6, 256, 256, 256, 512], [1, 1, 1, 0], 300, 1.0),       # ragged last row tile
+    ([6, 64, 64, 1], [1, 1, 0], 129, 1.0),                   # the error head (one output column)
+    ([13, 100, 37, 5], [0, 1, 1], 1, 0.5),                   # unaligned widths, a linear hidden layer
+    ([256, 256], [1], 257, 1.0),                             # one layer, the largest K
+    ([24, 48, 200, 96, 64, 32, 16], [1, 1, 1, 1, 1, 0], 520, 2.0),   # six layers
+])
+def test_fused_network_matches_layer_chain(env, sizes, acts, rows, scale):
+    """The whole network in one clustered launch equals, bit for bit, the
+    chain of per-layer launches (same BF16 roundings and K steps), and the
+    FP64 network oracle within the BF16-activation bar"""
+    torch, mlp = env
+    rng = np.random.default_rng(sum(sizes) + rows)
+    x = rng.standard_normal((rows, sizes[0])).astype(np.float32)
+    Ws = [M.bf16(rng.standard_normal((n, k)) / np.sqrt(k)) for k, n in zip(sizes[:-1], sizes[1:])]
+    bs = [rng.standard_normal(n).astype(np.float32).astype(np.float64) * 0.1 for n in sizes[1:]]
+    xd = torch.tensor(x, device="cuda")
+    Wd = [dev(torch, w, torch.bfloat16) for w in Ws]
+    bd = [dev(torch, b, torch.float32) for b in bs]
+    image = torch.empty(mlp.net_pack_bytes(sizes), dtype=torch.uint8, device="cuda")
+    mlp.net_pack(sizes, Wd, image)
+    y = torch.empty((rows, sizes[-1]), dtype=torch.float32, device="cuda")
+    mlp.net_forward(xd, sizes, acts, image, bd, y, scale)
+    mlp.check()
+    got = y.cpu().numpy()
+    want = _layer_chain(torch, mlp, xd, Wd, bd, acts, scale)
+    mlp.check()
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32)), np.abs(got - want).max()
+    names = ["gelu" if a else "none" for a in acts]
+    ref = M.forward(M.bf16(x.astype(np.float64)), list(zip(Ws, bs)), names)[2] * scale
+    assert rel(got, ref) <= 1e-2
+
+
+def test_fused_network_twice_and_without_bias(env):
+    """back-to-back launches on one image give the same outputs; a null bias
+    entry is no bias"""
+    torch, mlp = env
+    sizes, acts = [6, 64, 64, 8], [1, 1, 0]
+    rng = np.random.default_rng(9)
+    x = torch.tensor(rng.standard_normal((200, 6)).astype(np.float32), device="cuda")
+    Wd = [dev(torch, M.bf16(rng.standard_normal((n, k)) / np.sqrt(k)), torch.bfloat16)
+          for k, n in zip(sizes[:-1], sizes[1:])]
+    zero = [torch.zeros(n, dtype=torch.float32, device="cuda") for n in sizes[1:]]
+    image = torch.empty(mlp.net_pack_bytes(sizes), dtype=torch.uint8, device="cuda")
+    mlp.net_pack(sizes, Wd, image)
+    ys = []
+    for biases in ([None, None, None], zero, [None, zero[1], None]):
+        y = torch.empty((200, 8), dtype=torch.float32, device="cuda")
+        mlp.net_forward(x, sizes, acts, image, biases, y)
+        ys.append(y.cpu().numpy())
+    mlp.check()
+    assert np.array_equal(ys[0], ys[1]) and np.array_equal(ys[0], ys[2])
