@@ -604,7 +604,7 @@ cudaError_t tc_forward(const TA *x, int rows, int K, const __nv_bfloat16 *wt, co
 // shared memory (one bulk copy per layer from a packed image, issued at
 // launch).  Per layer one thread issues the MMA chain (A = the cluster's
 // shared activations of the 128 rows, B = the CTA's weight slice, D = TMEM),
-// the eight warps read the accumulator back (bias, activation, BF16) and
+// the sixteen warps read the accumulator back (bias, activation, BF16) and
 // store their columns, in the next layer's K-major core-matrix layout,
 // into the activation buffer of every CTA of the cluster (distributed
 // shared memory); two cluster barriers per layer separate the MMAs that
@@ -614,7 +614,8 @@ cudaError_t tc_forward(const TA *x, int rows, int K, const __nv_bfloat16 *wt, co
 // activation in FP32), so the two paths agree bit for bit.
 constexpr int NF_MAX_LAYERS = 6;
 constexpr int NF_CLUSTER = 4;
-constexpr int NF_THREADS = 256;                      // 8 warps: 4 TMEM lane groups x 2 column halves
+constexpr int NF_WARPS = 16;                         // 4 TMEM lane groups x 4 column quarters
+constexpr int NF_THREADS = NF_WARPS * 32;
 constexpr int NF_SMEM_MAX = 227 * 1024;
 
 struct NetArgs {
@@ -627,6 +628,8 @@ struct NetArgs {
     int act[NF_MAX_LAYERS];
     const float *bias[NF_MAX_LAYERS];
     const char *image;
+    int boff[NF_MAX_LAYERS];       // first float of layer l's bias slice in the staged biases
+    int bias_bytes;                // staged biases of this rank's columns, all layers
     int act_bytes;                 // activation buffer: 128 rows x the largest K, BF16
     int tmem_cols;
     float out_scale;
@@ -682,7 +685,8 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
     uint64_t *wbar = reinterpret_cast<uint64_t *>(sm);        // weight slices landed
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + 8);    // a layer's MMA chain done
     uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + 16);
-    char *act = sm + 1024;
+    float *bsm = reinterpret_cast<float *>(sm + 1024);
+    char *act = sm + 1024 + P.bias_bytes;
     char *wsm = act + P.act_bytes;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t rank = cluster_rank();
@@ -715,6 +719,12 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
                 : "memory");
         }
     }
+    // this rank's bias columns of every layer (zero past the layer's outputs)
+    for (int l = 0; l < L; ++l)
+        for (int c = tid; c < P.ns[l]; c += NF_THREADS) {
+            const int n = (int)rank * P.ns[l] + c;
+            bsm[P.boff[l] + c] = (P.bias[l] && n < P.k[l + 1]) ? __ldg(P.bias[l] + n) : 0.f;
+        }
     // the 128 input rows, rounded to BF16, as layer 0's A operand (every CTA
     // of the cluster stages its own copy)
     {
@@ -735,7 +745,9 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
     const bool loaded = ok;
     int fail = -1;                  // layer whose MMA chain a wait gave up on
     if (!ok && tid == 0) atomicExch(&g_mlp_err, 1);
-    const int lg = warp & 3, half = warp >> 2, r = lg * 32 + lane;   // this thread's TMEM lane = tile row
+    // warp: TMEM lane group lg (its 32 tile rows) and column chunks of 8
+    // starting at 8 quarter, every fourth chunk
+    const int lg = warp & 3, quarter = warp >> 2, r = lg * 32 + lane;
     uint32_t dst[NF_CLUSTER];       // the activation buffer in each CTA of the cluster
     for (int c = 0; c < NF_CLUSTER; ++c)
         asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(dst[c]) : "r"(smem_u32(act)), "r"(c));
@@ -771,11 +783,12 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
             if (tid == 0) atomicExch(&g_mlp_err, 1);
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int c0 = half * (ns / 2), n0 = (int)rank * ns;
+        const int n0 = (int)rank * ns;
+        const float *bl = bsm + P.boff[l];
         if (!last) {
             cluster_sync();         // every CTA's MMAs of this layer have read its activation buffer
             const int kpn = P.kp[l + 1];
-            for (int c = c0; ok && c < c0 + ns / 2; c += 8) {
+            for (int c = quarter * 8; ok && c < ns; c += 32) {
                 const int nb = n0 + c;          // first of the 8 columns (a multiple of 8)
                 if (nb >= kpn) break;
                 uint32_t v[8];
@@ -783,8 +796,7 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
                 float f[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const int n = nb + j;
-                    const float z = __uint_as_float(v[j]) + ((P.bias[l] && n < N) ? __ldg(P.bias[l] + n) : 0.f);
+                    const float z = __uint_as_float(v[j]) + bl[c + j];
                     f[j] = P.act[l] == FDTD_ACT_GELU ? gelu(z) : z;
                 }
                 const uint4 q = make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
@@ -800,7 +812,7 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         } else if (ok) {
             const int m = m0 + r;
-            for (int c = c0; c < c0 + ns / 2; c += 8) {
+            for (int c = quarter * 8; c < ns; c += 32) {
                 const int nb = n0 + c;
                 if (nb >= N) break;
                 uint32_t v[8];
@@ -809,8 +821,7 @@ __global__ void __launch_bounds__(NF_THREADS, 1)
                 float f[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const int n = nb + j;
-                    const float z = __uint_as_float(v[j]) + ((P.bias[l] && n < N) ? __ldg(P.bias[l] + n) : 0.f);
+                    const float z = __uint_as_float(v[j]) + bl[c + j];
                     f[j] = (P.act[l] == FDTD_ACT_GELU ? gelu(z) : z) * P.out_scale;
                 }
                 float *o = y + (long long)m * N + nb;
@@ -843,7 +854,7 @@ bool net_layout(const int *sizes, int L, NetArgs &P, size_t &image_bytes, int &s
     if (!sizes || L < 1 || L > NF_MAX_LAYERS) return false;
     P = NetArgs{};
     P.n_layers = L;
-    int kmax = 0, nsmax = 0;
+    int kmax = 0, nsmax = 0, nbias = 0;
     long long off = 0;
     int wbytes = 0;
     for (int l = 0; l <= L; ++l) {
@@ -858,16 +869,19 @@ bool net_layout(const int *sizes, int L, NetArgs &P, size_t &image_bytes, int &s
         if (P.ns[l] > 256) return false;                    // one MMA N extent
         P.woff[l] = off;
         P.wsm[l] = wbytes;
+        P.boff[l] = nbias;
+        nbias += P.ns[l];
         off += (long long)NF_CLUSTER * P.ns[l] * P.kp[l] * 2;
         wbytes += P.ns[l] * P.kp[l] * 2;
         kmax = std::max(kmax, P.kp[l]);
         nsmax = std::max(nsmax, P.ns[l]);
     }
     P.act_bytes = TC_M * kmax * 2;
+    P.bias_bytes = (nbias * 4 + 1023) / 1024 * 1024;
     P.tmem_cols = 32;
     while (P.tmem_cols < nsmax) P.tmem_cols *= 2;
     image_bytes = (size_t)off;
-    smem = 1024 + 1024 + P.act_bytes + wbytes;
+    smem = 1024 + 1024 + P.bias_bytes + P.act_bytes + wbytes;
     return smem <= NF_SMEM_MAX;
 }
 
