@@ -161,3 +161,28 @@ def test_config4_full_batch_sampled_domains(fdtd):
     b.close()
     for g in grids:
         g.close()
+
+
+def test_one_domain_batch_between_single_steps(fdtd):
+    """a grid stepped 3 times alone (odd parity), then as a one-domain batch
+    for 30 steps (direct launches until the parity allows a graph), then 5
+    more times alone, equals the same grid stepped 38 times alone, bit for
+    bit (fields and every probe sample)"""
+    sc = W.random_scenario(321, n=(37, 29, 23), cpml=4, n_steps=38)
+    ref = build(fdtd, sc, 38)
+    ref.step(38)
+    want = [ref.get_field(c) for c in range(6)], [ref.read_probe(p) for p in range(len(sc.probes))]
+    ref.close()
+    g = build(fdtd, sc, 38)
+    g.step(3)
+    b = fdtd.Batch([g])
+    b.step(30)
+    b.synchronize()
+    b.close()
+    g.step(5)
+    assert g.step_count == 38
+    for c in range(6):
+        assert np.array_equal(g.get_field(c), want[0][c])
+    for p in range(len(sc.probes)):
+        assert np.array_equal(g.read_probe(p), want[1][p])
+    g.close()
