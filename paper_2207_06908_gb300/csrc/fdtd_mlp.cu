@@ -9,9 +9,11 @@
 // bias / GELU epilogue.  The gradients (dz wt and dz^T x, whose operands
 // are not K-major in memory) and forward layers with larger k use the same
 // tile and epilogue with the reduction in chunks, each chunk staged through
-// registers from operands addressed by element strides.  Small element-wise
-// kernels form dz = dy * act'(z), the bias gradient, the losses and the Adam
-// update.
+// registers from operands addressed by element strides.  Inference runs a
+// whole network in one launch (net_forward_kernel: a cluster of four CTAs per
+// 128 rows, weights resident in shared memory, activations exchanged through
+// distributed shared memory).  Small element-wise kernels form
+// dz = dy * act'(z), the bias gradient, the losses and the Adam update.
 #include <cuda_bf16.h>
 #include <math.h>
 
